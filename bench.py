@@ -1,0 +1,378 @@
+"""Throughput of the greedy Green's-function optimizer step on GB300.
+
+A step is one pass of the whole hot path on the 192x192 2x2-brush workload with a
+complex128 G (N = 36864 pixels, n = N+1 = 36865, 72962 candidates, G = 21.7 GB):
+evaluate every candidate's exact dFOM, select the best, and apply the rank-p update to G
+and E.  The metric is accepted flips per second (one accepted brush per step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (each step a bounded
+row/candidate sample of the same workload, scaled to a full step).  Under torchrun every rank
+runs an independent replica of the problem (the path has no exchange step on one GPU);
+value = flips of all ranks / max wall time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+from paper_2202_05388_gb300 import workloads as W
+
+METRIC = "accepted flips/s (greedy step: dFOM of every 2x2 brush + select + rank-p G/E update)"
+UNIT = "flips/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="brush_192")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
+    return ap.parse_args()
+
+
+def workload(name):
+    return {"brush_192": W.brush_192, "plain_32": W.plain_32, "brush_64": W.brush_64}[name]()
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                pw.append(float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit count x max clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def oracle_step_sample(wl, budget_s, rng_seed=0):
+    """Time the FP64 oracle on a bounded sample of one greedy step of workload `wl` and scale
+    it to a full step.  Sample: (a) every candidate of a strip of image rows of the design
+    (the oracle's vectorised evaluation on a sub-grid with the same nx, dx and monitor),
+    scaled by the candidate count; (b) the oracle's Eq. 10 row update on a block of rows of
+    the full n x n G, scaled by n / rows.  Returns (seconds per full step, description)."""
+    from oracle import gf_oracle as O
+    g = wl.geoms[0]
+    spec = wl.spec
+    n = g.N + 1
+    # (a) candidate evaluation on a strip of `sy` image rows (same nx, dx, monitor)
+    sy = 6
+    gs = W.Geometry(g.nx, sy, g.dx, g.wavelength, g.mon_x, g.mon_y, g.eps_bg, g.eps_mat)
+    strip = O.OracleProblem([gs], spec)
+    t0 = time.perf_counter()
+    d = strip.evaluate()
+    t_eval = time.perf_counter() - t0
+    ncand_strip = d.size
+    ncand_full = O.num_candidates(g, spec)
+    eval_full = t_eval * ncand_full / ncand_strip
+    # (b) Eq. 10 on a row block of the full G (rows built from G0, p = 4 columns)
+    rng = np.random.default_rng(rng_seed)
+    p = 4 if spec.kind == W.KIND_BRUSH2 else 1
+    pts = O.points(g)
+    rows = 256
+    V = rng.choice(g.N, size=p, replace=False)
+
+    def g0_rows(r0, r1):
+        d2 = pts[r0:r1, None, :] - pts[None, :, :]
+        r = np.sqrt(d2[..., 0] ** 2 + d2[..., 1] ** 2)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            M = O.g0_pair(g, r)
+        for i in range(r0, r1):
+            if i < g.N:
+                M[i - r0, i] = O.g0_self(g)
+            else:
+                M[i - r0, i] = 0.0
+        return M
+
+    Grows = g0_rows(0, rows)
+    R = g0_rows(0, p)                    # stands in for A^{-1} G[V, :] (same shape and scale)
+    C = Grows[:, V].copy()
+    dchi = np.full(p, g.eps_mat - g.eps_bg)
+    reps, t_upd = 0, 0.0
+    while t_upd < 0.5 * budget_s and reps < 64:
+        t0 = time.perf_counter()
+        _ = O.update_rows(Grows, C, dchi, R)
+        t_upd += time.perf_counter() - t0
+        reps += 1
+    upd_full = (t_upd / reps) * n / rows
+    # (c) selection over all candidates
+    dd = np.random.default_rng(1).normal(size=ncand_full)
+    t0 = time.perf_counter()
+    _ = O.select_best(dd, spec.tie_rel)
+    t_sel = time.perf_counter() - t0
+    step = eval_full + upd_full + t_sel
+    desc = (f"oracle dFOM of all {ncand_strip} candidates of a {g.nx}x{sy} strip scaled x"
+            f"{ncand_full / ncand_strip:.1f}; Eq. 10 update of {rows} of {n} rows (x{reps}) scaled "
+            f"x{n / rows:.0f}; selection over {ncand_full}")
+    return step, desc, {"eval_s": eval_full, "update_s": upd_full, "select_s": t_sel}
+
+
+def blas_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] or [1])
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(wl, budget_s):
+    step, desc, parts = oracle_step_sample(wl, budget_s)
+    return {"value": 1.0 / step, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": desc, "seconds_per_step": step, "parts_s": parts}
+
+
+# ------------------------------------------------------------------------------ dist
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_step_sample(wl, 2.0)
+    times = []
+    desc = ""
+    for _ in range(args.steps):
+        s, desc, _ = oracle_step_sample(wl, 2.0)
+        times.append(s)
+    total = sum(times)
+    value = args.steps / total
+    g = wl.geoms[0]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "nx": g.nx, "ny": g.ny, "n": g.N + 1,
+                       "candidates": W.CandidateSpec(wl.spec.kind, wl.spec.dir_mask).ncand(g)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ native
+def run_native(args):
+    import torch
+    from paper_2202_05388_gb300 import build as BLD
+    from paper_2202_05388_gb300 import gfopt as B
+    from paper_2202_05388_gb300.optimizer import GreedyOptimizer
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    if rank == 0:
+        BLD.build()
+    if world > 1:
+        torch.distributed.barrier()
+    wl = workload(args.workload)
+    g = wl.geoms[0]
+    opt = GreedyOptimizer(wl.geoms, wl.spec, dtype=wl.dtype, device=dev)
+    opt.fill()
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        opt.step()
+    accepted = torch.zeros(1, dtype=torch.int64, device=f"cuda:{dev}")
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    nlam = len(wl.geoms)
+    opt.h.gf_profile_begin(args.steps * nlam + 4)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        opt.step()
+        accepted += (opt.status == B.GF_OK).to(torch.int64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kern_ms, kern_launches, kern_bytes, kern_flops = opt.h.gf_profile_end()
+    clk = clocks.stop()
+    flips = int(accepted.item())
+    t_max = ms
+    flips_total = flips
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=f"cuda:{dev}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        ff = torch.tensor([flips], device=f"cuda:{dev}", dtype=torch.int64)
+        dist.all_reduce(ff)
+        flips_total = int(ff.item())
+    value = flips_total / (t_max / 1e3)
+
+    # ---- end to end through the public API: host input -> device -> K steps -> host results
+    e2e = None
+    if not args.no_e2e:
+        host_state = torch.zeros(g.N, dtype=torch.uint8).pin_memory()
+        host_out = torch.empty(2 * max(1, wl.spec.k) + 2, dtype=torch.float64).pin_memory()
+        opt2 = opt
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        opt2.state.copy_(host_state, non_blocking=True)       # job input: the design state
+        opt2.fill()
+        acc2 = 0
+        for _ in range(args.steps):
+            opt2.step()
+            k = max(1, wl.spec.k)
+            packed = torch.cat([opt2.idx[:k].to(torch.float64), opt2.val[:k],
+                                opt2.status.to(torch.float64), opt2.fom])
+            host_out.copy_(packed, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            acc2 += int(host_out[2 * k].item() == B.GF_OK)
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": acc2 / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": g.N / args.steps,
+               "d2h_bytes_per_step": host_out.numel() * 8,
+               "note": "timed: H2D of the design state, gf_fill_g0, then K x (step + D2H of "
+                       "the step result) through GreedyOptimizer"}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    peak_hbm, peak_kind = measured_peaks()
+    kern_avg_ms = kern_ms / max(kern_launches, 1)
+    bytes_per_launch = kern_bytes / max(kern_launches, 1)
+    flops_per_launch = kern_flops / max(kern_launches, 1)
+    achieved_gbs = bytes_per_launch / (kern_avg_ms * 1e-3) / 1e9
+    achieved_tfl = flops_per_launch / (kern_avg_ms * 1e-3) / 1e12
+    if wl.dtype == "c128":
+        roof = {"bound": "alu", "achieved": achieved_tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tfl / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_rank_update_f64 (native DFMA)",
+                "peak_kind": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "hbm_achieved_gbs": achieved_gbs, "hbm_frac": achieved_gbs / peak_hbm,
+                "hbm_peak_gbs": peak_hbm, "hbm_peak_kind": peak_kind}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
+                "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind}
+    roof["algorithmic_bytes_per_launch"] = bytes_per_launch
+    roof["kernel_ms_avg"] = kern_avg_ms
+    roof["kernel_share_of_step"] = kern_ms / ms
+    per_step_launches = 4 + 2 * nlam + 1          # eval, select, capacitance, panels, finish + per-wavelength update and bands
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.dtype == "c128" else "f32",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "nx": g.nx, "ny": g.ny, "n": g.N + 1,
+                       "candidates": opt.ncand, "G_GB": opt.G[0].numel() * opt.G[0].element_size() / 1e9,
+                       "storage": wl.dtype, "l2": "inputs larger than L2 (G is 21.7 GB per replica)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "candidate_evals_per_s": opt.ncand * args.steps * world / (t_max / 1e3),
+            "g_update_GBps": achieved_gbs,
+            "accepted_flips": flips_total,
+            "roofline": roof,
+            "gpu_launches": per_step_launches * args.steps,
+            "clocks": clk,
+            "e2e": e2e}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

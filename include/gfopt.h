@@ -1,0 +1,172 @@
+/*
+ * libgfopt -- C ABI of the GB300 (sm_103a) hot path of the Green's-function
+ * pixel-by-pixel optimizer (Wang et al., arXiv:2202.05388).
+ *
+ * One greedy step (Sec. II, Fig. 1; partitioned form of Sec. III) is
+ *   gf_eval_candidates  -> exact dFOM of every candidate flip     (Eqs. 4-9, Eq. 1)
+ *   gf_select_topk      -> the reduction to the chosen flip(s)     (Sec. III reduction)
+ *   gf_apply_update     -> rank-p update of G and update of E      (Eqs. 10-14, Eq. 4)
+ * and gf_fill_g0 builds the analytic background G0 and E_inc      (Sec. II-B, Sec. IV).
+ *
+ * Problem statement in this library's variables (2-D scalar E_z restatement):
+ *   Points: N = nx*ny pixels, row-major j = iy*nx + ix with centre ((ix+1/2)dx, (iy+1/2)dx),
+ *   then the monitor point at index N; n = N + 1.
+ *   G is a dense n x n complex matrix, row-major with leading dimension ldg (entries).  The
+ *   paper's b = k0^2 d_eps dV is folded into G, so a flip changes the contrast chi_j of pixel
+ *   j by d_chi = +-(eps_mat - eps_bg).  E is the field at the n points (complex128).
+ *   Background (vacuum) values written by gf_fill_g0, with k = 2 pi / wavelength:
+ *     G_ij = (i/4) k^2 dx^2 H0(k |r_i - r_j|)  (i != j),
+ *     G_jj = (i pi/2) k a H1(k a) - 1, a = dx / sqrt(pi),  G_NN = 0,  E_j = exp(i k y_j).
+ *
+ * Conventions for every call:
+ *   - Return value is a host-side status (GF_OK or an error); the message of the last error
+ *     on a handle is returned by gf_last_error().  Arguments are validated on the host
+ *     before anything is launched; an invalid argument launches nothing.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).  No call synchronises the device.
+ *   - All array arguments are device pointers owned by the caller unless stated; the library
+ *     allocates no device memory in any call.  Scratch space is the caller's `ws` buffer of
+ *     at least gf_workspace_size() bytes (256-byte aligned).
+ *   - Data-dependent outcomes (no improving candidate, singular capacitance matrix) are
+ *     written to the caller's device status word (int32), so no host round trip is needed;
+ *     later calls in the same step read it and turn into no-ops when it is not GF_OK.
+ *   - Pointers must be 16-byte aligned; ldg >= n and ldg even.
+ *   - A handle is not thread safe; use one handle per host thread / stream.
+ */
+#ifndef GFOPT_H
+#define GFOPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gf_status;
+#define GF_OK          0
+#define GF_EINVAL      1   /* invalid argument (host check) */
+#define GF_ECUDA       2   /* a CUDA runtime call failed */
+#define GF_ESINGULAR   3   /* device status: capacitance matrix I - G_VV D singular (Sec. II-A) */
+#define GF_ENOIMPROVE  4   /* device status: no candidate increases the FOM (Sec. IV stop rule) */
+#define GF_ETIMEOUT    5   /* device status: a bounded wait gave up */
+#define GF_ENOMEM      6   /* workspace too small */
+
+#define GF_C128 0          /* G stored as complex128 (interleaved re, im doubles) */
+#define GF_C64  1          /* G stored as complex64 (interleaved re, im floats) */
+
+#define GF_KIND_SINGLE 0   /* candidate id = pixel j */
+#define GF_KIND_BRUSH2 1   /* candidate id = dir*P + iy*(nx-1) + ix, P = (nx-1)(ny-1) */
+#define GF_DIR_FILL  1     /* eps_bg -> eps_mat allowed */
+#define GF_DIR_CLEAR 2     /* eps_mat -> eps_bg allowed */
+
+#define GF_NBANDS 9        /* G entries of each pixel row with its 3x3 neighbourhood */
+
+/* Design-region geometry for one wavelength (Sec. III notation: nx, ny; monitor r_m).
+ * eps_bg must be 1 (vacuum background with the analytic G0 of Sec. IV). The monitor must
+ * lie outside the closed design rectangle [0, nx dx] x [0, ny dx] (Sec. III). */
+typedef struct gf_geom {
+  int32_t nx, ny;
+  double dx;
+  double wavelength;
+  double eps_bg, eps_mat;
+  double mon_x, mon_y;
+} gf_geom;
+
+/* One wavelength's state.  G: n x ldg entries of the storage dtype.  E: n complex128.
+ * bands: GF_NBANDS * N complex128, band b at bands + b*N, entry i = G[i, i + off_b] with
+ * off = {0, +1, -1, nx-1, -(nx-1), nx, -nx, nx+1, -(nx+1)} (0 where the neighbour pixel is
+ * outside the grid); they are the G_VV entries that brush candidates need (Eq. 8). */
+typedef struct gf_problem {
+  gf_geom geom;
+  void* G;
+  int64_t ldg;
+  void* E;
+  void* bands;
+} gf_problem;
+
+/* Candidate family (Sec. II-A "shapes and sizes for region V"; Sec. IV 2x2 brushes).
+ * k > 1 accepts up to k non-conflicting candidates per step (conflict: Chebyshev distance of
+ * anchors <= excl_radius).  Ties: lowest id among dFOM >= max - tie_rel*|max|. */
+typedef struct gf_cand_spec {
+  int32_t kind;
+  int32_t dir_mask;
+  int32_t k;
+  int32_t excl_radius;
+  double tie_rel;
+} gf_cand_spec;
+
+typedef struct gf_handle gf_handle;
+
+/* Create a handle bound to CUDA device `device`.  Returns GF_ECUDA if it does not exist. */
+gf_status gf_create(gf_handle** h, int32_t device);
+void gf_destroy(gf_handle* h);
+/* Message of the last error on h (never NULL; "" when none).  h may be NULL for the last
+ * gf_create failure of this thread. */
+const char* gf_last_error(const gf_handle* h);
+const char* gf_status_string(gf_status s);
+/* Library version string. */
+const char* gf_version(void);
+
+/* Number of candidate ids for a geometry and candidate family (N, or 2(nx-1)(ny-1)). */
+int64_t gf_num_candidates(const gf_geom* geom, const gf_cand_spec* spec);
+/* Workspace bytes needed by gf_fill_g0 / gf_select_topk / gf_apply_update for nlam
+ * wavelengths of this geometry, storage dtype and candidate family (0 on bad arguments). */
+size_t gf_workspace_size(const gf_geom* geom, int32_t nlam, int32_t dtype,
+                         const gf_cand_spec* spec);
+
+/* Background Green's matrix, incident field and bands of one wavelength (Sec. II-B: the
+ * initial G of a vacuum background is known analytically; Sec. IV).  Writes all n x ldg
+ * entries of G (padding columns zero), E[0..n) and the bands.  Hankel functions are
+ * evaluated once per distinct pixel offset (a Toeplitz table in ws) and expanded. */
+gf_status gf_fill_g0(gf_handle* h, const gf_problem* prob, int32_t dtype,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* Re-extract the bands of one wavelength from its G (used after external edits of G). */
+gf_status gf_extract_bands(gf_handle* h, const gf_problem* prob, int32_t dtype, void* stream);
+
+/* Exact dFOM of every candidate (Eqs. 4-9 at the monitor, then Eq. 1 with
+ * FOM = sum over wavelengths of |E(r_m)|^2), written to dfom[0..ncand) in FP64; -inf for a
+ * candidate that changes no pixel, whose direction is not enabled, or whose capacitance
+ * matrix is singular (|pivot| < 1e-13 ||A||_inf).  state: N bytes, 0 = eps_bg, 1 = eps_mat.
+ * probs: host array of nlam problems sharing nx, ny, dx and the monitor. */
+gf_status gf_eval_candidates(gf_handle* h, const gf_problem* probs, int32_t nlam,
+                             int32_t dtype, const uint8_t* state, const gf_cand_spec* spec,
+                             double* dfom, void* stream);
+
+/* Reduction of dFOM to the accepted candidate ids (Sec. III, CombineGlobally).  k == 1:
+ * idx[0] = the lowest id with dfom >= m - tie_rel*|m| where m = max dfom.  k > 1: up to k
+ * ids in (-dfom, id) order skipping conflicts; unused slots are -1.  val[] gets their dFOM.
+ * *status (device) = GF_OK, or GF_ENOIMPROVE when m <= 0 (idx[0] = -1). */
+gf_status gf_select_topk(gf_handle* h, const gf_geom* geom, const gf_cand_spec* spec,
+                         const double* dfom, int64_t ncand, int32_t* idx, double* val,
+                         int32_t* status, void* ws, size_t ws_bytes, void* stream);
+
+/* Apply the candidates idx[0..k) (device; -1 ends the list) to every wavelength:
+ * snapshot rows G[V,:] and columns G[:,V], solve A R = G[V,:] with A = I - G_VV D (Eq. 14,
+ * FP64, partial pivoting), then G <- G + G[:,V] D R (Eq. 10) and E <- E + G[:,V] D y with
+ * y = A^{-1} E_V (Eqs. 4, 9); flip state at V, re-extract bands and write the new
+ * FOM (sum over wavelengths of |E_N|^2) to *fom_out (device double).  With more than one
+ * candidate, the union is applied only if its joint dFOM is positive; otherwise idx[0]
+ * alone (the best one) is applied.  No-op when *status != GF_OK on entry; sets
+ * *status = GF_ESINGULAR (and changes nothing) when A is singular. */
+gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, int32_t dtype,
+                          uint8_t* state, const gf_cand_spec* spec, const int32_t* idx,
+                          int32_t* status, double* fom_out, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/* Kernel timing (no counterpart in the paper; it backs the per-step timers of the bench).
+ * gf_profile_begin arms up to max_records CUDA-event pairs that the library records on the
+ * launching stream around every launch of the G-update kernel.  gf_profile_end waits for the
+ * last recorded event, returns the summed kernel time in ms, the number of timed launches and
+ * the algorithmic bytes (read + write of every G entry) and flops of those launches, and
+ * disarms.  Launches beyond max_records are not timed.  Not for use inside graph capture. */
+gf_status gf_profile_begin(gf_handle* h, int32_t max_records);
+gf_status gf_profile_end(gf_handle* h, double* ms_total, int64_t* launches, double* bytes_total,
+                         double* flops_total);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFOPT_H */

@@ -280,6 +280,13 @@ def select_topk(g: Geometry, spec: CandidateSpec, dfom: np.ndarray) -> List[int]
 
 
 # --------------------------------------------------------------------------- update
+def update_rows(G_rows: np.ndarray, C_rows: np.ndarray, dchi: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """Eq. 10 for a block of rows r: G_new[r, :] = G_old[r, :] + G_old[r, V] D R, where
+    R = G_new[V, :] from Eq. 14.  Rows are independent, which is what lets the paper
+    partition G by rows (Sec. III, Fig. 2)."""
+    return G_rows + C_rows @ (dchi[:, None] * R)
+
+
 def apply_update(G: np.ndarray, E: np.ndarray, V, dchi) -> Tuple[np.ndarray, np.ndarray, bool]:
     """Eq. 14 then Eq. 10 for G and Eq. 4 for E, from snapshots of G's rows and columns
     at V (no symmetry shortcut).  Returns (G_new, E_new, ok)."""
@@ -291,7 +298,7 @@ def apply_update(G: np.ndarray, E: np.ndarray, V, dchi) -> Tuple[np.ndarray, np.
     if not (ok1 and ok2):
         return G, E, False
     C = G[:, V].copy()
-    Gn = G + C @ (dchi[:, None] * R)
+    Gn = update_rows(G, C, dchi, R)
     En = E + C @ (dchi * y)
     return Gn, En, True
 

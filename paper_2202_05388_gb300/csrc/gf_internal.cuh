@@ -1,0 +1,150 @@
+// Internal declarations shared by the libgfopt translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/gfopt.h"
+
+namespace gf {
+
+// ----------------------------------------------------------------------------- complex
+struct cplx {
+  double re, im;
+};
+
+__host__ __device__ __forceinline__ cplx mk(double r, double i) { return cplx{r, i}; }
+__host__ __device__ __forceinline__ cplx operator+(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__host__ __device__ __forceinline__ cplx operator-(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__host__ __device__ __forceinline__ cplx operator*(cplx a, cplx b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__host__ __device__ __forceinline__ cplx operator*(double s, cplx a) { return {s * a.re, s * a.im}; }
+__host__ __device__ __forceinline__ double abs2(cplx a) { return a.re * a.re + a.im * a.im; }
+__host__ __device__ __forceinline__ double cabs1(cplx a) { return sqrt(abs2(a)); }
+// a / b by scaling with 1/|b|^2 (b is a pivot bounded away from 0 by the singularity test)
+__host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  double d = 1.0 / abs2(b);
+  return {(a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d};
+}
+// acc + a*b with fused multiply-adds
+__device__ __forceinline__ cplx cfma(cplx a, cplx b, cplx acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+
+__device__ __forceinline__ cplx ldc(const void* base, int64_t idx) {
+  double2 v = reinterpret_cast<const double2*>(base)[idx];
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void stc(void* base, int64_t idx, cplx v) {
+  reinterpret_cast<double2*>(base)[idx] = make_double2(v.re, v.im);
+}
+// G entry (i, j) of either storage type, widened to FP64
+__device__ __forceinline__ cplx ldG(const void* G, int32_t dtype, int64_t ldg, int64_t i, int64_t j) {
+  if (dtype == GF_C128) return ldc(G, i * ldg + j);
+  float2 v = reinterpret_cast<const float2*>(G)[i * ldg + j];
+  return {(double)v.x, (double)v.y};
+}
+
+// ----------------------------------------------------------------------------- constants
+constexpr double kSingularRel = 1e-13;     // |pivot| < kSingularRel * ||A||_inf => singular
+constexpr int kMaxPixelsPerCand = 4;       // 2x2 brush
+
+// Band offsets in pixel units (dx, dy), matching the ABI's off_b list.
+__host__ __device__ __forceinline__ void band_offset(int b, int& ddx, int& ddy) {
+  const int tx[GF_NBANDS] = {0, 1, -1, -1, 1, 0, 0, 1, -1};
+  const int ty[GF_NBANDS] = {0, 0, 0, 1, -1, 1, -1, 1, -1};
+  ddx = tx[b];
+  ddy = ty[b];
+}
+
+// ----------------------------------------------------------------------------- workspace
+// Per-step control block written by the capacitance kernel, read by the panel/update kernels.
+struct UpdCtl {
+  int32_t skip;       // 1: nothing is applied this step
+  int32_t nv;         // number of flipped pixels (0 < nv <= pmax)
+  int32_t ncand;      // number of candidates applied
+  int32_t pad;
+  double joint_dfom;  // dFOM of the applied set (FP64)
+};
+
+struct WsLayout {
+  int pmax;           // pixel slots
+  int64_t n;
+  size_t ctl, V, dchi;        // shared
+  size_t lu, piv, yd;         // per wavelength, strides lu_s, piv_s, yd_s
+  size_t lu_s, piv_s, yd_s;
+  size_t C0, S, panel_s;      // per wavelength, C0 (n x pmax), S (pmax x n), stride panel_s
+  size_t sel;                 // selection scratch
+  size_t table;               // fill: Toeplitz table + monitor vector
+  size_t total;
+};
+
+WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& spec);
+
+// ----------------------------------------------------------------------------- kernels
+void launch_fill_table(const gf_geom& g, cplx* table, cudaStream_t st);
+void launch_fill_expand(const gf_geom& g, int dtype, void* G, int64_t ldg, const cplx* table,
+                        cplx* E, cudaStream_t st);
+void launch_bands(const gf_geom& g, int dtype, const void* G, int64_t ldg, cplx* bands,
+                  cudaStream_t st);
+
+struct EvalLam {     // one wavelength as seen by the candidate kernels
+  const void* G;
+  int64_t ldg;
+  const cplx* E;
+  const cplx* bands;
+};
+constexpr int kMaxLam = 8;
+struct EvalArgs {
+  int nlam;
+  int dtype;
+  int nx, ny;
+  double chi;           // eps_mat - eps_bg
+  EvalLam lam[kMaxLam];
+};
+void launch_eval(const EvalArgs& a, const uint8_t* state, const gf_cand_spec& spec, double* dfom,
+                 cudaStream_t st);
+
+void launch_select(const gf_geom& g, const gf_cand_spec& spec, const double* dfom, int64_t ncand,
+                   int32_t* idx, double* val, int32_t* status, void* ws, cudaStream_t st);
+
+struct UpdLam {
+  void* G;
+  int64_t ldg;
+  cplx* E;
+  cplx* bands;
+};
+struct UpdArgs {
+  int nlam;
+  int dtype;
+  int nx, ny;
+  double chi;
+  int pmax;
+  UpdLam lam[kMaxLam];
+};
+// CUDA-event timer of the G-update kernel launches (armed by gf_profile_begin).  Each record
+// holds an event pair and the rank p that the launch applied (written by the kernel into
+// mapped host memory, since p is only known on the device).
+struct KernelTimer {
+  bool on = false;
+  int max = 0, used = 0;
+  cudaEvent_t* ev0 = nullptr;
+  cudaEvent_t* ev1 = nullptr;
+  int32_t* p_host = nullptr;     // mapped pinned host memory, one int per record
+  int32_t* p_dev = nullptr;      // its device alias
+  double* n2 = nullptr;          // n*n entries updated by each record (host)
+  int* bytes_per_entry = nullptr;
+  void release();
+};
+
+void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state,
+                   const gf_cand_spec& spec, const int32_t* idx, int32_t* status, double* fom_out,
+                   cudaStream_t st, KernelTimer* timer);
+
+}  // namespace gf

@@ -1,0 +1,449 @@
+// Update of G and E after a selection (Sec. II-B, Eqs. 10-14 and Eq. 4; Sec. III's
+// filter + broadcast of the selected rows followed by every partition's update).
+//
+//   k_capacitance : V and d_chi from the chosen ids, A = I - G_VV D per wavelength, LU with
+//                   partial pivoting (FP64), y = A^{-1} E_V, joint dFOM and fallback.
+//   k_panels      : snapshots C0 = G[:, V] (n x p) and S = D A^{-1} G[V, :] (p x n), i.e. the
+//                   new rows of Eq. 14 scaled by D -- the data the paper broadcasts.
+//   k_rank_update : G <- G + C0 S (Eq. 10), every entry read and written once.
+//   k_finish      : E <- E + C0 (D y) (Eq. 4), state flip, FOM = sum |E_N|^2.
+#include <math.h>
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+// ----------------------------------------------------------------------------- capacitance
+struct CapArgs {
+  UpdArgs u;
+  int kind, dir_mask, k;
+  int pmax;
+};
+
+// Pixels and contrast changes of candidate c given the current state (same rule as the
+// candidate kernels).  Appends to V/dchi; returns the number appended.
+__device__ int cand_pixels(int64_t c, int kind, int dir_mask, int nx, int ny, double chi,
+                           const uint8_t* state, int32_t* V, double* dchi) {
+  const int64_t N = (int64_t)nx * ny;
+  if (kind == GF_KIND_SINGLE) {
+    if (c < 0 || c >= N) return 0;
+    uint8_t s = state[c];
+    if (s == 0 && (dir_mask & GF_DIR_FILL)) { V[0] = (int32_t)c; dchi[0] = chi; return 1; }
+    if (s != 0 && (dir_mask & GF_DIR_CLEAR)) { V[0] = (int32_t)c; dchi[0] = -chi; return 1; }
+    return 0;
+  }
+  const int64_t P = (int64_t)(nx - 1) * (ny - 1);
+  if (c < 0 || c >= 2 * P) return 0;
+  const int dir = (int)(c / P);
+  const int64_t a = c - dir * P;
+  if (!(dir_mask & (dir == 0 ? GF_DIR_FILL : GF_DIR_CLEAR))) return 0;
+  const int ay = (int)(a / (nx - 1)), ax = (int)(a - (int64_t)ay * (nx - 1));
+  const int64_t j0 = (int64_t)ay * nx + ax;
+  const int64_t q[4] = {j0, j0 + 1, j0 + nx, j0 + nx + 1};
+  int m = 0;
+  for (int u = 0; u < 4; ++u) {
+    if (state[q[u]] == (dir == 0 ? 0 : 1)) {
+      V[m] = (int32_t)q[u];
+      dchi[m] = dir == 0 ? chi : -chi;
+      ++m;
+    }
+  }
+  return m;
+}
+
+// Single CTA.  The p x p matrices live in the workspace (p can reach 4k).
+__global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __restrict__ state,
+                              const int32_t* __restrict__ idx, int32_t* status) {
+  UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
+  int32_t* V = reinterpret_cast<int32_t*>(ws + L.V);
+  double* dchi = reinterpret_cast<double*>(ws + L.dchi);
+  __shared__ int s_nv, s_ncand, s_fail;
+  __shared__ double s_red[32];
+  const int tid = threadIdx.x;
+  const int64_t N = (int64_t)a.u.nx * a.u.ny;
+
+  if (tid == 0) {
+    s_fail = 0;
+    s_ncand = 0;
+    s_nv = 0;
+    if (*status != GF_OK) {
+      s_fail = 1;
+    } else {
+      int nv = 0, nc = 0;
+      for (int c = 0; c < a.k; ++c) {
+        int32_t id = idx[c];
+        if (id < 0) break;
+        int m = cand_pixels(id, a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V + nv, dchi + nv);
+        if (m == 0) continue;
+        nv += m;
+        ++nc;
+      }
+      s_nv = nv;
+      s_ncand = nc;
+      if (nv == 0) s_fail = 2;
+    }
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) {
+      ctl->skip = 1;
+      ctl->nv = 0;
+      ctl->ncand = 0;
+      ctl->joint_dfom = 0.0;
+    }
+    return;
+  }
+
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const int p = s_nv;
+    double total = 0.0;
+    bool singular = false;
+    for (int l = 0; l < a.u.nlam; ++l) {
+      const UpdLam& U = a.u.lam[l];
+      cplx* A = reinterpret_cast<cplx*>(ws + L.lu + l * L.lu_s);
+      int32_t* piv = reinterpret_cast<int32_t*>(ws + L.piv + l * L.piv_s);
+      cplx* y = reinterpret_cast<cplx*>(ws + L.yd + l * L.yd_s);
+      // A = I - G_VV D, row-major p x p;  y = E_V
+      for (int t = tid; t < p * p; t += blockDim.x) {
+        int r = t / p, c = t % p;
+        cplx g = ldG(U.G, a.u.dtype, U.ldg, V[r], V[c]);
+        cplx e = mk(r == c ? 1.0 : 0.0, 0.0);
+        A[t] = e - dchi[c] * g;
+      }
+      for (int t = tid; t < p; t += blockDim.x) y[t] = U.E[V[t]];
+      __syncthreads();
+      // ||A||_inf
+      double rs = 0.0;
+      for (int r = tid; r < p; r += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < p; ++c) s += cabs1(A[r * p + c]);
+        rs = fmax(rs, s);
+      }
+      for (int o = 16; o > 0; o >>= 1) rs = fmax(rs, __shfl_down_sync(0xffffffffu, rs, o));
+      if ((tid & 31) == 0) s_red[tid >> 5] = rs;
+      __syncthreads();
+      if (tid == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[w]);
+        s_red[0] = m;
+      }
+      __syncthreads();
+      const double thresh = kSingularRel * s_red[0];
+      __syncthreads();
+      // LU with partial pivoting (row-major, in place; L below the diagonal, unit diagonal)
+      __shared__ int s_piv;
+      __shared__ int s_bad;
+      if (tid == 0) s_bad = 0;
+      for (int c = 0; c < p; ++c) {
+        if (tid == 0) {
+          int r = c;
+          double best = cabs1(A[c * p + c]);
+          for (int rr = c + 1; rr < p; ++rr) {
+            double m = cabs1(A[rr * p + c]);
+            if (m > best) { best = m; r = rr; }
+          }
+          if (!(best >= thresh)) s_bad = 1;
+          s_piv = r;
+          piv[c] = r;
+        }
+        __syncthreads();
+        const int r = s_piv;
+        if (s_bad) break;
+        if (r != c) {
+          for (int v = tid; v < p; v += blockDim.x) {
+            cplx t0 = A[c * p + v];
+            A[c * p + v] = A[r * p + v];
+            A[r * p + v] = t0;
+          }
+          if (tid == 0) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
+        }
+        __syncthreads();
+        const cplx pv = A[c * p + c];
+        for (int rr = c + 1 + tid; rr < p; rr += blockDim.x) {
+          cplx f = cdiv(A[rr * p + c], pv);
+          for (int v = c + 1; v < p; ++v) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
+          A[rr * p + c] = f;
+          y[rr] = y[rr] - f * y[c];
+        }
+        __syncthreads();
+      }
+      __syncthreads();
+      if (s_bad) { singular = true; break; }
+      // back substitution for y (serial; p is small)
+      if (tid == 0) {
+        for (int c = p - 1; c >= 0; --c) {
+          cplx acc = y[c];
+          for (int v = c + 1; v < p; ++v) acc = acc - A[c * p + v] * y[v];
+          y[c] = cdiv(acc, A[c * p + c]);
+        }
+        cplx EN = U.E[N];
+        cplx dE = mk(0.0, 0.0);
+        for (int u = 0; u < p; ++u) dE = dE + dchi[u] * (ldG(U.G, a.u.dtype, U.ldg, N, V[u]) * y[u]);
+        cplx Em = EN + dE;
+        s_red[0] = abs2(Em) - abs2(EN);
+        // store D y for the field update
+        for (int u = 0; u < p; ++u) y[u] = dchi[u] * y[u];
+      }
+      __syncthreads();
+      total += s_red[0];
+      __syncthreads();
+    }
+    if (singular) {
+      if (tid == 0) {
+        *status = GF_ESINGULAR;
+        ctl->skip = 1;
+        ctl->nv = 0;
+        ctl->ncand = 0;
+        ctl->joint_dfom = 0.0;
+      }
+      return;
+    }
+    if (s_ncand > 1 && !(total > 0.0) && attempt == 0) {
+      // the joint set does not improve the FOM: apply the best candidate alone
+      __syncthreads();
+      if (tid == 0) {
+        int m = cand_pixels(idx[0], a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V, dchi);
+        s_nv = m;
+        s_ncand = 1;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (tid == 0) {
+      ctl->skip = 0;
+      ctl->nv = s_nv;
+      ctl->ncand = s_ncand;
+      ctl->joint_dfom = total;
+    }
+    return;
+  }
+}
+
+// ----------------------------------------------------------------------------- panels
+// Column j: R[:, j] = A^{-1} G[V, j] (Eq. 14) and S[:, j] = D R[:, j]; row j: C0[j, :] = G[j, V].
+__global__ void k_panels(UpdArgs a, WsLayout L, char* ws) {
+  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
+  if (ctl->skip) return;
+  const int p = ctl->nv;
+  const int32_t* V = reinterpret_cast<const int32_t*>(ws + L.V);
+  const double* dchi = reinterpret_cast<const double*>(ws + L.dchi);
+  const int64_t n = L.n;
+  for (int l = 0; l < a.nlam; ++l) {
+    const UpdLam& U = a.lam[l];
+    const cplx* A = reinterpret_cast<const cplx*>(ws + L.lu + l * L.lu_s);
+    const int32_t* piv = reinterpret_cast<const int32_t*>(ws + L.piv + l * L.piv_s);
+    cplx* C0 = reinterpret_cast<cplx*>(ws + L.C0 + l * L.panel_s);
+    cplx* S = reinterpret_cast<cplx*>(ws + L.S + l * L.panel_s);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+      for (int u = 0; u < p; ++u) C0[j * L.pmax + u] = ldG(U.G, a.dtype, U.ldg, j, V[u]);
+      if (p <= kMaxPixelsPerCand) {
+        cplx x[kMaxPixelsPerCand];
+#pragma unroll
+        for (int u = 0; u < kMaxPixelsPerCand; ++u)
+          if (u < p) x[u] = ldG(U.G, a.dtype, U.ldg, V[u], j);
+        // P A = L U with full-row interchanges: apply all interchanges in order first,
+        // then the unit-lower solve, then the upper solve
+#pragma unroll
+        for (int c = 0; c < kMaxPixelsPerCand; ++c) {
+          if (c < p) {
+            int r = piv[c];
+#pragma unroll
+            for (int rr = 0; rr < kMaxPixelsPerCand; ++rr)
+              if (rr == r && rr != c) { cplx t = x[c]; x[c] = x[rr]; x[rr] = t; }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < kMaxPixelsPerCand; ++c) {
+          if (c < p) {
+#pragma unroll
+            for (int rr = c + 1; rr < kMaxPixelsPerCand; ++rr)
+              if (rr < p) x[rr] = x[rr] - A[rr * p + c] * x[c];
+          }
+        }
+#pragma unroll
+        for (int c = kMaxPixelsPerCand - 1; c >= 0; --c) {
+          if (c < p) {
+            cplx acc = x[c];
+#pragma unroll
+            for (int v = c + 1; v < kMaxPixelsPerCand; ++v)
+              if (v < p) acc = acc - A[c * p + v] * x[v];
+            x[c] = cdiv(acc, A[c * p + c]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kMaxPixelsPerCand; ++u)
+          if (u < p) S[(int64_t)u * n + j] = dchi[u] * x[u];
+      } else {
+        // general p: the column of R lives in S itself (row stride n)
+        for (int u = 0; u < p; ++u) S[(int64_t)u * n + j] = ldG(U.G, a.dtype, U.ldg, V[u], j);
+        for (int c = 0; c < p; ++c) {
+          int r = piv[c];
+          if (r != c) {
+            cplx t = S[(int64_t)c * n + j];
+            S[(int64_t)c * n + j] = S[(int64_t)r * n + j];
+            S[(int64_t)r * n + j] = t;
+          }
+        }
+        for (int c = 0; c < p; ++c) {
+          cplx xc = S[(int64_t)c * n + j];
+          for (int rr = c + 1; rr < p; ++rr)
+            S[(int64_t)rr * n + j] = S[(int64_t)rr * n + j] - A[rr * p + c] * xc;
+        }
+        for (int c = p - 1; c >= 0; --c) {
+          cplx acc = S[(int64_t)c * n + j];
+          for (int v = c + 1; v < p; ++v) acc = acc - A[c * p + v] * S[(int64_t)v * n + j];
+          S[(int64_t)c * n + j] = cdiv(acc, A[c * p + c]);
+        }
+        for (int u = 0; u < p; ++u) S[(int64_t)u * n + j] = dchi[u] * S[(int64_t)u * n + j];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- rank-p (FP64)
+constexpr int kUpdThreads = 256;
+constexpr int kUpdRows = 16;
+
+// G[i, j] += sum_u C0[i, u] S[u, j] for one wavelength, complex128 storage, native DFMA.
+// P > 0: compile-time rank; P == 0: runtime rank p.
+template <int P>
+__device__ __forceinline__ void rank_update_f64_body(double2* __restrict__ G, int64_t ldg, int64_t n,
+                                                     int pmax, int p, const cplx* __restrict__ C0,
+                                                     const cplx* __restrict__ S, int64_t j) {
+  cplx s[P > 0 ? P : 1];
+  if (P > 0) {
+#pragma unroll
+    for (int u = 0; u < P; ++u) s[u] = S[(int64_t)u * n + j];
+  }
+  for (int64_t i0 = (int64_t)blockIdx.y * kUpdRows; i0 < n; i0 += (int64_t)gridDim.y * kUpdRows) {
+    const int64_t iend = i0 + kUpdRows < n ? i0 + kUpdRows : n;
+    for (int64_t i = i0; i < iend; ++i) {
+      double2 g = G[i * ldg + j];
+      cplx acc = mk(g.x, g.y);
+      if (P > 0) {
+#pragma unroll
+        for (int u = 0; u < P; ++u) acc = cfma(C0[i * pmax + u], s[u], acc);
+      } else {
+        for (int u = 0; u < p; ++u) acc = cfma(C0[i * pmax + u], S[(int64_t)u * n + j], acc);
+      }
+      G[i * ldg + j] = make_double2(acc.re, acc.im);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kUpdThreads) k_rank_update_f64(double2* __restrict__ G, int64_t ldg,
+                                                                 int64_t n, int pmax,
+                                                                 const cplx* __restrict__ C0,
+                                                                 const cplx* __restrict__ S,
+                                                                 const UpdCtl* __restrict__ ctl,
+                                                                 int32_t* __restrict__ prof_p) {
+  const int p = ctl->skip ? 0 : ctl->nv;
+  if (prof_p && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *prof_p = p;
+  if (p == 0) return;
+  const int64_t j = blockIdx.x * (int64_t)kUpdThreads + threadIdx.x;
+  if (j >= n) return;
+  switch (p) {
+    case 1: rank_update_f64_body<1>(G, ldg, n, pmax, p, C0, S, j); break;
+    case 2: rank_update_f64_body<2>(G, ldg, n, pmax, p, C0, S, j); break;
+    case 3: rank_update_f64_body<3>(G, ldg, n, pmax, p, C0, S, j); break;
+    case 4: rank_update_f64_body<4>(G, ldg, n, pmax, p, C0, S, j); break;
+    default: rank_update_f64_body<0>(G, ldg, n, pmax, p, C0, S, j); break;
+  }
+}
+
+// complex64 storage: same update, FP64 arithmetic on the FP64 panels, rounded once on store.
+__global__ void __launch_bounds__(kUpdThreads) k_rank_update_c64_ref(float2* __restrict__ G, int64_t ldg,
+                                                                     int64_t n, int pmax,
+                                                                     const cplx* __restrict__ C0,
+                                                                     const cplx* __restrict__ S,
+                                                                     const UpdCtl* __restrict__ ctl,
+                                                                     int32_t* __restrict__ prof_p) {
+  const int p = ctl->skip ? 0 : ctl->nv;
+  if (prof_p && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *prof_p = p;
+  if (p == 0) return;
+  const int64_t j = blockIdx.x * (int64_t)kUpdThreads + threadIdx.x;
+  if (j >= n) return;
+  for (int64_t i0 = (int64_t)blockIdx.y * kUpdRows; i0 < n; i0 += (int64_t)gridDim.y * kUpdRows) {
+    const int64_t iend = i0 + kUpdRows < n ? i0 + kUpdRows : n;
+    for (int64_t i = i0; i < iend; ++i) {
+      float2 g = G[i * ldg + j];
+      cplx acc = mk(0.0, 0.0);
+      for (int u = 0; u < p; ++u) acc = cfma(C0[i * pmax + u], S[(int64_t)u * n + j], acc);
+      G[i * ldg + j] = make_float2((float)((double)g.x + acc.re), (float)((double)g.y + acc.im));
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- field, state, FOM
+__global__ void k_finish(UpdArgs a, WsLayout L, char* ws, uint8_t* __restrict__ state,
+                         double* __restrict__ fom_out) {
+  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
+  const int64_t n = L.n;
+  const int64_t N = n - 1;
+  const bool skip = ctl->skip != 0;
+  const int p = skip ? 0 : ctl->nv;
+  const int32_t* V = reinterpret_cast<const int32_t*>(ws + L.V);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double f = 0.0;
+    for (int l = 0; l < a.nlam; ++l) {
+      const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + l * L.panel_s);
+      const cplx* yd = reinterpret_cast<const cplx*>(ws + L.yd + l * L.yd_s);
+      cplx e = a.lam[l].E[i];
+      for (int u = 0; u < p; ++u) e = cfma(C0[i * L.pmax + u], yd[u], e);
+      if (p > 0) a.lam[l].E[i] = e;
+      f += abs2(e);
+    }
+    if (i == N) *fom_out = f;
+  }
+  if (blockIdx.x == 0) {
+    for (int t = threadIdx.x; t < p; t += blockDim.x) state[V[t]] ^= 1;
+  }
+}
+
+void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state,
+                   const gf_cand_spec& spec, const int32_t* idx, int32_t* status, double* fom_out,
+                   cudaStream_t st, KernelTimer* timer) {
+  CapArgs ca;
+  ca.u = a;
+  ca.kind = spec.kind;
+  ca.dir_mask = spec.dir_mask;
+  ca.k = spec.k < 1 ? 1 : spec.k;
+  ca.pmax = L.pmax;
+  k_capacitance<<<1, 256, 0, st>>>(ca, L, ws, state, idx, status);
+  const int64_t n = L.n;
+  {
+    int64_t b = (n + 255) / 256;
+    k_panels<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(a, L, ws);
+  }
+  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
+  dim3 grid((unsigned)((n + kUpdThreads - 1) / kUpdThreads),
+            (unsigned)(((n + kUpdRows - 1) / kUpdRows) < 65535 ? (n + kUpdRows - 1) / kUpdRows : 65535));
+  for (int l = 0; l < a.nlam; ++l) {
+    const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + l * L.panel_s);
+    const cplx* S = reinterpret_cast<const cplx*>(ws + L.S + l * L.panel_s);
+    const bool rec = timer && timer->on && timer->used < timer->max;
+    int32_t* prof_p = rec ? timer->p_dev + timer->used : nullptr;
+    if (rec) cudaEventRecord(timer->ev0[timer->used], st);
+    if (a.dtype == GF_C128) {
+      double2* G = reinterpret_cast<double2*>(a.lam[l].G);
+      k_rank_update_f64<<<grid, kUpdThreads, 0, st>>>(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl, prof_p);
+    } else {
+      k_rank_update_c64_ref<<<grid, kUpdThreads, 0, st>>>(reinterpret_cast<float2*>(a.lam[l].G),
+                                                          a.lam[l].ldg, n, L.pmax, C0, S, ctl, prof_p);
+    }
+    if (rec) {
+      cudaEventRecord(timer->ev1[timer->used], st);
+      timer->n2[timer->used] = (double)n * (double)n;
+      timer->bytes_per_entry[timer->used] = a.dtype == GF_C128 ? 32 : 16;
+      timer->used++;
+    }
+  }
+  {
+    int64_t b = (n + 255) / 256;
+    k_finish<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(a, L, ws, state, fom_out);
+  }
+}
+
+}  // namespace gf

@@ -1,0 +1,198 @@
+"""ctypes binding of libgfopt (argument marshalling only; every step runs in the CUDA
+library).  Function names mirror the C ABI in include/gfopt.h.  Device buffers are passed as
+torch tensors (their data_ptr) or raw integer addresses; streams as torch.cuda.Stream or
+integer cudaStream_t handles.
+
+The library is loaded from the package's _lib directory on first use; if it has not been
+built, every call raises GfError -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libgfopt.so")
+
+GF_OK, GF_EINVAL, GF_ECUDA, GF_ESINGULAR, GF_ENOIMPROVE, GF_ETIMEOUT, GF_ENOMEM = range(7)
+GF_C128, GF_C64 = 0, 1
+GF_KIND_SINGLE, GF_KIND_BRUSH2 = 0, 1
+GF_DIR_FILL, GF_DIR_CLEAR = 1, 2
+GF_NBANDS = 9
+
+STATUS_NAMES = {GF_OK: "GF_OK", GF_EINVAL: "GF_EINVAL", GF_ECUDA: "GF_ECUDA",
+                GF_ESINGULAR: "GF_ESINGULAR", GF_ENOIMPROVE: "GF_ENOIMPROVE",
+                GF_ETIMEOUT: "GF_ETIMEOUT", GF_ENOMEM: "GF_ENOMEM"}
+
+EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_version",
+           "gf_num_candidates", "gf_workspace_size", "gf_fill_g0", "gf_extract_bands",
+           "gf_eval_candidates", "gf_select_topk", "gf_apply_update", "gf_profile_begin",
+           "gf_profile_end"]
+
+
+class GfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gf_geom(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dx", C.c_double),
+                ("wavelength", C.c_double), ("eps_bg", C.c_double), ("eps_mat", C.c_double),
+                ("mon_x", C.c_double), ("mon_y", C.c_double)]
+
+
+class gf_problem(C.Structure):
+    _fields_ = [("geom", gf_geom), ("G", C.c_void_p), ("ldg", C.c_int64), ("E", C.c_void_p),
+                ("bands", C.c_void_p)]
+
+
+class gf_cand_spec(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dir_mask", C.c_int32), ("k", C.c_int32),
+                ("excl_radius", C.c_int32), ("tie_rel", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libgfopt.so (once) and declare the signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise GfError(GF_EINVAL, f"{path} is missing: build it with __graft_entry__.build() "
+                                     "(there is no CPU fallback)")
+        lib = C.CDLL(path)
+        P = C.c_void_p
+        sig = {
+            "gf_create": (C.c_int32, [C.POINTER(P), C.c_int32]),
+            "gf_destroy": (None, [P]),
+            "gf_last_error": (C.c_char_p, [P]),
+            "gf_status_string": (C.c_char_p, [C.c_int32]),
+            "gf_version": (C.c_char_p, []),
+            "gf_num_candidates": (C.c_int64, [C.POINTER(gf_geom), C.POINTER(gf_cand_spec)]),
+            "gf_workspace_size": (C.c_size_t, [C.POINTER(gf_geom), C.c_int32, C.c_int32,
+                                               C.POINTER(gf_cand_spec)]),
+            "gf_fill_g0": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, P, C.c_size_t, P]),
+            "gf_extract_bands": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, P]),
+            "gf_eval_candidates": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, C.c_int32, P,
+                                               C.POINTER(gf_cand_spec), P, P]),
+            "gf_select_topk": (C.c_int32, [P, C.POINTER(gf_geom), C.POINTER(gf_cand_spec), P,
+                                           C.c_int64, P, P, P, P, C.c_size_t, P]),
+            "gf_apply_update": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, C.c_int32, P,
+                                            C.POINTER(gf_cand_spec), P, P, P, P, C.c_size_t, P]),
+            "gf_profile_begin": (C.c_int32, [P, C.c_int32]),
+            "gf_profile_end": (C.c_int32, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def geom_struct(g) -> gf_geom:
+    return gf_geom(int(g.nx), int(g.ny), float(g.dx), float(g.wavelength), float(g.eps_bg),
+                   float(g.eps_mat), float(g.mon_x), float(g.mon_y))
+
+
+def spec_struct(s) -> gf_cand_spec:
+    return gf_cand_spec(int(s.kind), int(s.dir_mask), int(s.k), int(s.excl_radius), float(s.tie_rel))
+
+
+def problem_struct(g, G, ldg, E, bands) -> gf_problem:
+    return gf_problem(geom_struct(g), _ptr(G), int(ldg), _ptr(E), _ptr(bands))
+
+
+class Handle:
+    """Owns a gf_handle bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.gf_create(C.byref(h), int(device))
+        if st != GF_OK:
+            raise GfError(st, self.lib.gf_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != GF_OK:
+            raise GfError(st, self.lib.gf_last_error(self.h).decode())
+
+    # ---- ABI mirrors
+    def gf_num_candidates(self, geom, spec) -> int:
+        g, s = geom_struct(geom), spec_struct(spec)
+        return int(self.lib.gf_num_candidates(C.byref(g), C.byref(s)))
+
+    def gf_workspace_size(self, geom, nlam, dtype, spec) -> int:
+        g, s = geom_struct(geom), spec_struct(spec)
+        return int(self.lib.gf_workspace_size(C.byref(g), int(nlam), int(dtype), C.byref(s)))
+
+    def gf_fill_g0(self, prob: gf_problem, dtype, ws, ws_bytes, stream=None):
+        self._check(self.lib.gf_fill_g0(self.h, C.byref(prob), int(dtype), _ptr(ws), int(ws_bytes),
+                                        _stream(stream)))
+
+    def gf_extract_bands(self, prob: gf_problem, dtype, stream=None):
+        self._check(self.lib.gf_extract_bands(self.h, C.byref(prob), int(dtype), _stream(stream)))
+
+    def gf_eval_candidates(self, probs, dtype, state, spec, dfom, stream=None):
+        arr = (gf_problem * len(probs))(*probs)
+        s = spec_struct(spec)
+        self._check(self.lib.gf_eval_candidates(self.h, arr, len(probs), int(dtype), _ptr(state),
+                                                C.byref(s), _ptr(dfom), _stream(stream)))
+
+    def gf_select_topk(self, geom, spec, dfom, ncand, idx, val, status, ws, ws_bytes, stream=None):
+        g, s = geom_struct(geom), spec_struct(spec)
+        self._check(self.lib.gf_select_topk(self.h, C.byref(g), C.byref(s), _ptr(dfom), int(ncand),
+                                            _ptr(idx), _ptr(val), _ptr(status), _ptr(ws),
+                                            int(ws_bytes), _stream(stream)))
+
+    def gf_apply_update(self, probs, dtype, state, spec, idx, status, fom_out, ws, ws_bytes,
+                        stream=None):
+        arr = (gf_problem * len(probs))(*probs)
+        s = spec_struct(spec)
+        self._check(self.lib.gf_apply_update(self.h, arr, len(probs), int(dtype), _ptr(state),
+                                             C.byref(s), _ptr(idx), _ptr(status), _ptr(fom_out),
+                                             _ptr(ws), int(ws_bytes), _stream(stream)))
+
+    def gf_profile_begin(self, max_records: int):
+        self._check(self.lib.gf_profile_begin(self.h, int(max_records)))
+
+    def gf_profile_end(self):
+        """Returns (ms_total, launches, bytes_total, flops_total) of the timed G updates."""
+        ms, n, b, f = C.c_double(), C.c_int64(), C.c_double(), C.c_double()
+        self._check(self.lib.gf_profile_end(self.h, C.byref(ms), C.byref(n), C.byref(b), C.byref(f)))
+        return ms.value, n.value, b.value, f.value

@@ -1,0 +1,120 @@
+"""GreedyOptimizer: the public Python entry point that owns one design problem's device
+state (G, E and the bands per wavelength, the design state and the step buffers, all torch
+CUDA tensors) and drives the libgfopt C ABI for each greedy step (Fig. 1 of the paper:
+evaluate every candidate, select, update).  Everything runs asynchronously on the current
+torch stream; only ``read_step``/``run`` copy the small step result back to the host.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import gfopt as B
+from .workloads import CandidateSpec, Geometry
+
+
+@dataclass
+class StepResult:
+    ids: List[int]          # candidate ids selected (before the joint-dFOM fallback)
+    dfom: List[float]       # their individual dFOM
+    status: int             # GF_OK, GF_ENOIMPROVE or GF_ESINGULAR
+    fom: float              # FOM after the step
+
+
+class GreedyOptimizer:
+    def __init__(self, geoms: Sequence[Geometry], spec: CandidateSpec, dtype: str = "c128",
+                 device: int = 0, handle: Optional[B.Handle] = None):
+        if not torch.cuda.is_available():
+            raise B.GfError(B.GF_ECUDA, "GreedyOptimizer needs a CUDA device (no CPU fallback)")
+        self.geoms = list(geoms)
+        self.spec = spec
+        self.dtype = B.GF_C128 if dtype == "c128" else B.GF_C64
+        self.device = torch.device("cuda", device)
+        self.h = handle or B.Handle(device)
+        g = self.geoms[0]
+        N, n = g.N, g.N + 1
+        self.N, self.n = N, n
+        self.ldg = n + (n & 1)
+        tdt = torch.complex128 if self.dtype == B.GF_C128 else torch.complex64
+        dev = self.device
+        nlam = len(self.geoms)
+        self.G = [torch.empty((n, self.ldg), dtype=tdt, device=dev) for _ in range(nlam)]
+        self.E = [torch.empty(n, dtype=torch.complex128, device=dev) for _ in range(nlam)]
+        self.bands = [torch.empty(B.GF_NBANDS * N, dtype=torch.complex128, device=dev)
+                      for _ in range(nlam)]
+        self.state = torch.zeros(N, dtype=torch.uint8, device=dev)
+        self.ncand = self.h.gf_num_candidates(g, spec)
+        self.dfom = torch.empty(self.ncand, dtype=torch.float64, device=dev)
+        k = max(1, spec.k)
+        self.idx = torch.full((k,), -1, dtype=torch.int32, device=dev)
+        self.val = torch.empty(k, dtype=torch.float64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.fom = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.ws_bytes = self.h.gf_workspace_size(g, nlam, self.dtype, spec)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.probs = [B.problem_struct(gg, self.G[l], self.ldg, self.E[l], self.bands[l])
+                      for l, gg in enumerate(self.geoms)]
+
+    # ---- stages (asynchronous on the current stream)
+    def _st(self):
+        return torch.cuda.current_stream(self.device)
+
+    def fill(self):
+        for p in self.probs:
+            self.h.gf_fill_g0(p, self.dtype, self.ws, self.ws_bytes, self._st())
+        self.state.zero_()
+        self.fom.copy_(sum((E[-1].abs() ** 2) for E in self.E).reshape(1))
+
+    def evaluate(self):
+        self.h.gf_eval_candidates(self.probs, self.dtype, self.state, self.spec, self.dfom, self._st())
+
+    def select(self):
+        self.h.gf_select_topk(self.geoms[0], self.spec, self.dfom, self.ncand, self.idx, self.val,
+                              self.status, self.ws, self.ws_bytes, self._st())
+
+    def update(self):
+        self.h.gf_apply_update(self.probs, self.dtype, self.state, self.spec, self.idx, self.status,
+                               self.fom, self.ws, self.ws_bytes, self._st())
+
+    def step(self):
+        self.evaluate()
+        self.select()
+        self.update()
+
+    def force(self, ids: Sequence[int], spec: Optional[CandidateSpec] = None):
+        """Apply the given candidate ids regardless of their dFOM (tests, replays)."""
+        spec = spec or self.spec
+        k = max(1, spec.k)
+        idx = torch.full((k,), -1, dtype=torch.int32)
+        idx[:len(ids)] = torch.tensor(list(ids), dtype=torch.int32)
+        if self.idx.numel() < k:
+            self.idx = torch.full((k,), -1, dtype=torch.int32, device=self.device)
+        self.idx[:k].copy_(idx.to(self.device))
+        self.status.zero_()
+        self.h.gf_apply_update(self.probs, self.dtype, self.state, spec, self.idx, self.status,
+                               self.fom, self.ws, self.ws_bytes, self._st())
+
+    # ---- host readback
+    def read_step(self) -> StepResult:
+        k = max(1, self.spec.k)
+        packed = torch.cat([self.idx[:k].to(torch.float64), self.val[:k],
+                            self.status.to(torch.float64), self.fom]).cpu().numpy()
+        ids = [int(x) for x in packed[:k] if x >= 0]
+        return StepResult(ids, [float(x) for x in packed[k:k + len(ids)]], int(packed[2 * k]),
+                          float(packed[2 * k + 1]))
+
+    def run(self, steps: int) -> List[StepResult]:
+        out = []
+        for _ in range(steps):
+            self.step()
+            r = self.read_step()
+            out.append(r)
+            if r.status != B.GF_OK:
+                break
+        return out
+
+    def state_host(self) -> np.ndarray:
+        return self.state.cpu().numpy()

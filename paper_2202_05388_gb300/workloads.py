@@ -98,6 +98,17 @@ def brush_192() -> Workload:
                     CandidateSpec(KIND_BRUSH2, DIR_FILL | DIR_CLEAR, 1), 2000, "c128")
 
 
+def brush_64() -> Workload:
+    """64x64 pixels, dx = lambda/20, 2x2 brush toggles, focus 2 lambda beyond the centre:
+    a profiling-size member of the brush family (G = 269 MB, larger than L2)."""
+    nx = ny = 64
+    dx = 0.05
+    mx, my = _centre_line_monitor(nx, ny, dx, beyond_centre=2.0)
+    g = Geometry(nx, ny, dx, 1.0, mx, my)
+    return Workload("brush_64x64_p4_c128", (g,),
+                    CandidateSpec(KIND_BRUSH2, DIR_FILL | DIR_CLEAR, 1), 200, "c128")
+
+
 def brush_320_topk() -> Workload:
     """320x320 pixels, complex64 G (about 84 GB), top-32 brushes with a 3-pixel
     exclusion radius accepted per step as one rank-128 update, 1500 steps."""

@@ -1,0 +1,72 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for sm_103a, loads,
+exports every function include/gfopt.h declares, and its pure host functions work."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2202_05388_gb300 import build as BLD
+from paper_2202_05388_gb300 import gfopt as B
+from paper_2202_05388_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    BLD.build()
+    return B.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "gfopt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gf_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(B.EXPORTS) <= set(names)
+
+
+def test_version_and_status_strings(lib):
+    assert b"sm_103a" in lib.gf_version()
+    assert lib.gf_status_string(B.GF_ESINGULAR) == b"singular capacitance matrix"
+    assert lib.gf_status_string(99) == b"unknown status"
+
+
+def test_num_candidates_and_workspace(lib):
+    g = W.brush_192().geoms[0]
+    s = W.brush_192().spec
+    gs, ss = B.geom_struct(g), B.spec_struct(s)
+    assert lib.gf_num_candidates(C.byref(gs), C.byref(ss)) == 2 * 191 * 191
+    s1 = B.spec_struct(W.plain_32().spec)
+    g1 = B.geom_struct(W.plain_32().geoms[0])
+    assert lib.gf_num_candidates(C.byref(g1), C.byref(s1)) == 1024
+    ws = lib.gf_workspace_size(C.byref(gs), 1, B.GF_C128, C.byref(ss))
+    n = g.N + 1
+    assert ws >= 2 * n * 4 * 16          # C0 and S panels of p = 4 complex128 columns
+    assert ws % 256 == 0
+    assert lib.gf_workspace_size(C.byref(gs), 0, B.GF_C128, C.byref(ss)) == 0
+    assert lib.gf_workspace_size(C.byref(gs), 1, 7, C.byref(ss)) == 0
+
+
+def test_null_handle_is_rejected(lib):
+    g = W.plain_32().geoms[0]
+    p = B.problem_struct(g, 16, g.n + 1, 16, 16)
+    assert lib.gf_fill_g0(None, C.byref(p), B.GF_C128, None, 0, None) == B.GF_EINVAL
+    assert lib.gf_extract_bands(None, C.byref(p), B.GF_C128, None) == B.GF_EINVAL
+
+
+def test_create_without_gpu_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    st = lib.gf_create(C.byref(h), 0)
+    assert st == B.GF_ECUDA
+    assert len(lib.gf_last_error(None)) > 0

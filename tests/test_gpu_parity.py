@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element,
+on seeded synthetic inputs (relative error <= 1e-10 on G, E, FOM and dFOM; identical flip
+sequence except where the oracle itself sees a near tie, then lock-step)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import gf_oracle as O
+from paper_2202_05388_gb300 import build as BLD
+from paper_2202_05388_gb300 import gfopt as B
+from paper_2202_05388_gb300 import workloads as W
+from paper_2202_05388_gb300.optimizer import GreedyOptimizer
+
+from gpu_parity import (TOL, compare_dfom, compare_state, gpu_E, gpu_G, rel_err, run_parity)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BLD.build()
+
+
+@pytest.mark.parametrize("nx,ny,ratio", [(1, 1, 20), (3, 1, 20), (7, 5, 16), (32, 32, 20), (17, 23, 24)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_fill_g0_matches_oracle(nx, ny, ratio, dtype):
+    wl = W.small(nx, ny, ratio=ratio)
+    g = wl.geoms[0]
+    opt = GreedyOptimizer(wl.geoms, wl.spec, dtype=dtype)
+    opt.fill()
+    torch.cuda.synchronize()
+    G0 = O.g0_matrix(g)
+    Gg = gpu_G(opt)
+    tol = 1e-12 if dtype == "c128" else 1e-7
+    assert rel_err(Gg, G0) <= tol
+    # padding columns are zero
+    if opt.ldg > opt.n:
+        assert torch.count_nonzero(opt.G[0][:, opt.n:]).item() == 0
+    assert rel_err(gpu_E(opt), O.incident_field(g)) <= 1e-13
+    bands = opt.bands[0].cpu().numpy().reshape(B.GF_NBANDS, -1)
+    offs = [(0, 0), (1, 0), (-1, 0), (-1, 1), (1, -1), (0, 1), (0, -1), (1, 1), (-1, -1)]
+    for b, (ddx, ddy) in enumerate(offs):
+        for i in range(g.N):
+            ix, iy = i % nx, i // nx
+            jx, jy = ix + ddx, iy + ddy
+            ref = G0[i, jy * nx + jx] if (0 <= jx < nx and 0 <= jy < ny) else 0.0
+            assert abs(bands[b, i] - ref) <= tol * max(1e-300, np.max(np.abs(G0))), (b, i)
+
+
+@pytest.mark.parametrize("kind,dir_mask,seed", [
+    (W.KIND_SINGLE, W.DIR_FILL, None),
+    (W.KIND_SINGLE, W.DIR_FILL | W.DIR_CLEAR, 5),
+    (W.KIND_SINGLE, W.DIR_CLEAR, 6),
+    (W.KIND_BRUSH2, W.DIR_FILL | W.DIR_CLEAR, 7),
+    (W.KIND_BRUSH2, W.DIR_FILL, 8),
+    (W.KIND_BRUSH2, W.DIR_CLEAR, 9),
+])
+def test_eval_candidates_matches_oracle(kind, dir_mask, seed):
+    wl = W.small(13, 11, kind=kind, dir_mask=dir_mask)
+    g = wl.geoms[0]
+    state = None if seed is None else W.random_state(g.N, seed=seed, fill=0.35)
+    orc = O.OracleProblem(wl.geoms, wl.spec, state)
+    opt = GreedyOptimizer(wl.geoms, wl.spec)
+    opt.fill()
+    if state is not None:
+        from gpu_parity import reach_state
+        orc2 = O.OracleProblem(wl.geoms, wl.spec)
+        reach_state(opt, orc2, state)
+    opt.evaluate()
+    torch.cuda.synchronize()
+    compare_dfom(opt.dfom.cpu().numpy(), orc.evaluate())
+
+
+def test_plain_32x32_single_fill_100_steps():
+    """The 32x32 single-pixel workload in full: up to 100 greedy steps (the greedy run stops
+    early when no fill improves the FOM; both sides must stop at the same step), G/E/FOM
+    compared every 10 steps."""
+    wl = W.plain_32()
+    done, lock = run_parity(wl, wl.steps, check_every=10)
+    assert done >= 50
+    assert lock <= 10
+
+
+@pytest.mark.parametrize("nx,ny,seed,steps", [(12, 10, 21, 12), (9, 14, 22, 10)])
+def test_brush_trajectory(nx, ny, seed, steps):
+    wl = W.small(nx, ny, kind=W.KIND_BRUSH2, dir_mask=3, steps=steps)
+    state = W.random_state(nx * ny, seed=seed, fill=0.3)
+    done, lock = run_parity(wl, steps, state=state)
+    assert done >= 3
+
+
+def test_single_toggle_trajectory_ragged():
+    wl = W.small(19, 7, kind=W.KIND_SINGLE, dir_mask=3, steps=15)
+    state = W.random_state(19 * 7, seed=23, fill=0.25)
+    done, _ = run_parity(wl, 15, state=state)
+    assert done >= 5
+
+
+def test_topk_trajectory():
+    wl = W.small(14, 12, kind=W.KIND_BRUSH2, dir_mask=3, k=3, excl_radius=3, steps=5)
+    state = W.random_state(14 * 12, seed=24, fill=0.3)
+    done, _ = run_parity(wl, 5, state=state)
+    assert done >= 2
+
+
+def test_multi_wavelength_trajectory():
+    wl = W.small(10, 6, kind=W.KIND_BRUSH2, dir_mask=3, wavelengths=(0.9, 1.0, 1.1), steps=5)
+    state = W.random_state(60, seed=25, fill=0.3)
+    done, _ = run_parity(wl, 5, state=state)
+    assert done >= 2
+
+
+def test_no_improving_candidate_sets_status_and_changes_nothing():
+    # From vacuum, no 2x2 brush of eps = 12.25 helps this small lens: the oracle stops at once.
+    wl = W.small(12, 10, kind=W.KIND_BRUSH2, dir_mask=3)
+    orc = O.OracleProblem(wl.geoms, wl.spec)
+    assert orc.choose(orc.evaluate()) == []
+    opt = GreedyOptimizer(wl.geoms, wl.spec)
+    opt.fill()
+    G_before = opt.G[0].clone()
+    opt.step()
+    r = opt.read_step()
+    assert r.status == B.GF_ENOIMPROVE and r.ids == []
+    assert torch.equal(opt.G[0], G_before)
+    assert abs(r.fom - orc.fom()) <= 1e-15
+
+
+def test_singular_capacitance_is_reported_not_applied():
+    # Host-side fault injection: make 1 - G_jj d_chi = 0 for pixel j by editing G on the device.
+    wl = W.small(6, 5, kind=W.KIND_SINGLE, dir_mask=W.DIR_FILL)
+    g = wl.geoms[0]
+    opt = GreedyOptimizer(wl.geoms, wl.spec)
+    opt.fill()
+    j = 7
+    chi = g.eps_mat - g.eps_bg
+    opt.G[0][j, j] = complex(1.0 / chi, 0.0)
+    opt.h.gf_extract_bands(opt.probs[0], opt.dtype, torch.cuda.current_stream())
+    opt.evaluate()
+    d = opt.dfom.cpu().numpy()
+    assert d[j] == -math.inf and np.isfinite(np.delete(d, j)).all()
+    G_before = opt.G[0].clone()
+    opt.force([j])
+    torch.cuda.synchronize()
+    assert int(opt.status.cpu()[0]) == B.GF_ESINGULAR
+    assert torch.equal(opt.G[0], G_before)
+    assert opt.state.cpu().numpy()[j] == 0
+
+
+def test_host_validation_rejects_bad_arguments():
+    wl = W.plain_32()
+    opt = GreedyOptimizer(wl.geoms, wl.spec)
+    g = wl.geoms[0]
+    bad = B.problem_struct(g, opt.G[0], opt.n - 1, opt.E[0], opt.bands[0])      # ldg < n
+    with pytest.raises(B.GfError) as e:
+        opt.h.gf_fill_g0(bad, opt.dtype, opt.ws, opt.ws_bytes)
+    assert e.value.status == B.GF_EINVAL and "ldg" in str(e.value)
+    inside = W.with_monitor(g, 0.5, 0.5)
+    p = B.problem_struct(inside, opt.G[0], opt.ldg, opt.E[0], opt.bands[0])
+    with pytest.raises(B.GfError, match="inside the design region"):
+        opt.h.gf_fill_g0(p, opt.dtype, opt.ws, opt.ws_bytes)
+    with pytest.raises(B.GfError) as e:
+        opt.h.gf_fill_g0(opt.probs[0], opt.dtype, opt.ws, 64)
+    assert e.value.status == B.GF_ENOMEM
+    with pytest.raises(B.GfError):
+        opt.h.gf_select_topk(g, wl.spec, opt.dfom, opt.ncand + 1, opt.idx, opt.val, opt.status,
+                             opt.ws, opt.ws_bytes)
+    bad_spec = W.CandidateSpec(kind=5)
+    with pytest.raises(B.GfError):
+        opt.h.gf_eval_candidates(opt.probs, opt.dtype, opt.state, bad_spec, opt.dfom)
+    # misaligned pointer
+    off = B.problem_struct(g, opt.G[0].data_ptr() + 8, opt.ldg, opt.E[0], opt.bands[0])
+    with pytest.raises(B.GfError, match="aligned"):
+        opt.h.gf_extract_bands(off, opt.dtype)
