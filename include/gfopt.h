@@ -155,6 +155,15 @@ gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, i
                           int32_t* status, double* fom_out, void* ws, size_t ws_bytes,
                           void* stream);
 
+/* Arithmetic of the complex128 G update (Eq. 10).  GF_UPDATE_TC (default): exact digit
+ * products on the tensor cores with an integer recombination (FP64-accurate to ~2^-50 of
+ * |C0||S|; used for p <= 4, larger p falls back to DFMA).  GF_UPDATE_DFMA: native FP64 FMA.
+ * Both match the FP64 oracle within 1e-10; they differ only in speed on GB300 (whose FP64
+ * pipe is 1/64 of its FP32 rate).  Applies to later gf_apply_update calls on h. */
+#define GF_UPDATE_TC   0
+#define GF_UPDATE_DFMA 1
+gf_status gf_set_update_algo(gf_handle* h, int32_t algo);
+
 /* Kernel timing (no counterpart in the paper; it backs the per-step timers of the bench).
  * gf_profile_begin arms up to max_records CUDA-event pairs that the library records on the
  * launching stream around every launch of the G-update kernel.  gf_profile_end waits for the

@@ -150,7 +150,7 @@ def anchor(g: Geometry, spec: CandidateSpec, cid: int) -> Tuple[int, int]:
 def gauss_pp(A: np.ndarray, B: np.ndarray) -> Tuple[np.ndarray, bool]:
     """Solve A X = B by Gaussian elimination with partial pivoting (the inversion of the
     small capacitance matrix of Eqs. 9 and 14).  Returns (X, ok); ok is False when a
-    pivot falls below SINGULAR_REL * ||A||_inf."""
+    pivot is zero or falls below SINGULAR_REL * ||A||_inf."""
     A = np.array(A, dtype=np.complex128)
     X = np.array(B, dtype=np.complex128)
     vec = X.ndim == 1
@@ -160,7 +160,7 @@ def gauss_pp(A: np.ndarray, B: np.ndarray) -> Tuple[np.ndarray, bool]:
     thresh = SINGULAR_REL * np.max(np.sum(np.abs(A), axis=1))
     for c in range(p):
         r = c + int(np.argmax(np.abs(A[c:, c])))
-        if not abs(A[r, c]) >= thresh:
+        if not (abs(A[r, c]) >= thresh and abs(A[r, c]) > 0.0):
             return X[:, 0] if vec else X, False
         if r != c:
             A[[c, r]] = A[[r, c]]
@@ -185,7 +185,7 @@ def gauss_pp_batch(A: np.ndarray, B: np.ndarray) -> Tuple[np.ndarray, np.ndarray
     for c in range(p):
         r = c + np.argmax(np.abs(A[:, c:, c]), axis=1)
         piv = A[rows, r, c]
-        ok &= np.abs(piv) >= thresh
+        ok &= (np.abs(piv) >= thresh) & (np.abs(piv) > 0.0)
         Ar, Ac = A[rows, r].copy(), A[rows, c].copy()
         A[rows, c], A[rows, r] = Ar, Ac
         Xr, Xc = X[rows, r].copy(), X[rows, c].copy()

@@ -13,6 +13,7 @@
 struct gf_handle {
   int device;
   int sm_count;
+  int update_algo;
   char err[512];
   gf::KernelTimer timer;
 };
@@ -144,6 +145,11 @@ WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& sp
   L.C0 = o; o += L.panel_s * nlam;
   L.S = o; o += L.panel_s * nlam;
   L.sel = o; o = up256(o + 4096);
+  const OzLayout oz = oz_layout(L.n);
+  L.ozA = o; o = up256(o + oz.bytesA);
+  L.ozE = o; o = up256(o + oz.bytesE);
+  L.ozB = o; o = up256(o + oz.bytesB);
+  L.ozF = o; o = up256(o + oz.bytesF);
   L.total = o;
   // the fill's Toeplitz table reuses the start of the workspace
   L.table = 0;
@@ -188,6 +194,7 @@ gf_status gf_create(gf_handle** out, int32_t device) {
   if (!h) return fail(nullptr, GF_ENOMEM, "out of host memory");
   h->device = device;
   h->sm_count = sms;
+  h->update_algo = GF_UPDATE_TC;
   h->err[0] = 0;
   *out = h;
   return GF_OK;
@@ -302,6 +309,8 @@ gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, i
   a.ny = probs[0].geom.ny;
   a.chi = probs[0].geom.eps_mat - probs[0].geom.eps_bg;
   a.pmax = L.pmax;
+  a.algo = h->update_algo;
+  a.sm_count = h->sm_count;
   for (int l = 0; l < nlam; ++l) {
     a.lam[l].G = probs[l].G;
     a.lam[l].ldg = probs[l].ldg;
@@ -313,6 +322,13 @@ gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, i
   for (int l = 0; l < nlam; ++l)
     gf::launch_bands(probs[l].geom, dtype, probs[l].G, probs[l].ldg, reinterpret_cast<gf::cplx*>(probs[l].bands), st);
   return cuda_check(h, "gf_apply_update launch");
+}
+
+gf_status gf_set_update_algo(gf_handle* h, int32_t algo) {
+  if (!h) return GF_EINVAL;
+  if (algo != GF_UPDATE_TC && algo != GF_UPDATE_DFMA) return fail(h, GF_EINVAL, "unknown update algorithm %d", algo);
+  h->update_algo = algo;
+  return GF_OK;
 }
 
 gf_status gf_profile_begin(gf_handle* h, int32_t max_records) {

@@ -13,7 +13,8 @@ namespace gf {
 // Solve A y = b for a 4x4 complex system by Gaussian elimination with partial pivoting.
 // Rows u with active[u] == false are identity rows with b[u] = 0, which reproduces the
 // elimination of the reduced system over the active pixels (same pivots, same arithmetic on
-// the active entries).  Returns false when a pivot is below kSingularRel * ||A_active||_inf.
+// the active entries).  Returns false when a pivot is zero or below
+// kSingularRel * ||A_active||_inf.
 template <int P>
 __device__ __forceinline__ bool solve_small(cplx (&A)[P][P], cplx (&b)[P], const bool (&active)[P]) {
   double norm = 0.0;
@@ -36,7 +37,7 @@ __device__ __forceinline__ bool solve_small(cplx (&A)[P][P], cplx (&b)[P], const
       double m = cabs1(A[rr][c]);
       if (m > best) { best = m; r = rr; }
     }
-    if (!(best >= thresh)) ok = false;
+    if (!(best >= thresh) || !(best > 0.0)) ok = false;
 #pragma unroll
     for (int rr = c + 1; rr < P; ++rr) {
       if (rr == r) {
@@ -83,7 +84,7 @@ __global__ void k_eval_single(EvalArgs a, const uint8_t* __restrict__ state, int
       cplx EN = L.E[N];
       cplx gNj = ldG(L.G, a.dtype, L.ldg, N, j);
       cplx A = mk(1.0 - gjj.re * d, -gjj.im * d);
-      if (!(cabs1(A) >= kSingularRel * cabs1(A))) { valid = false; break; }
+      if (!(cabs1(A) > 0.0)) { valid = false; break; }   // 1x1: singular only when zero
       cplx y = cdiv(Ej, A);
       cplx Em = EN + d * (gNj * y);
       total += abs2(Em) - abs2(EN);

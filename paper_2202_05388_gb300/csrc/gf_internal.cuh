@@ -81,9 +81,17 @@ struct WsLayout {
   size_t lu_s, piv_s, yd_s;
   size_t C0, S, panel_s;      // per wavelength, C0 (n x pmax), S (pmax x n), stride panel_s
   size_t sel;                 // selection scratch
+  size_t ozA, ozE, ozB, ozF;  // tensor-core update: digit slices and scale exponents (wavelength-shared)
   size_t table;               // fill: Toeplitz table + monitor vector
   size_t total;
 };
+
+// Digit-slice buffers of the tensor-core complex128 update for an n x n G.
+struct OzLayout {
+  int64_t nrow_tiles, ncol_tiles;
+  size_t bytesA, bytesE, bytesB, bytesF;
+};
+OzLayout oz_layout(int64_t n);
 
 WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& spec);
 
@@ -126,6 +134,8 @@ struct UpdArgs {
   int nx, ny;
   double chi;
   int pmax;
+  int algo;            // GF_UPDATE_TC or GF_UPDATE_DFMA
+  int sm_count;
   UpdLam lam[kMaxLam];
 };
 // CUDA-event timer of the G-update kernel launches (armed by gf_profile_begin).  Each record
@@ -142,6 +152,11 @@ struct KernelTimer {
   int* bytes_per_entry = nullptr;
   void release();
 };
+
+void launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0,
+                              const cplx* S, const UpdCtl* ctl, uint8_t* ozA, int32_t* ozE,
+                              uint8_t* ozB, int32_t* ozF, int32_t* status, int32_t* prof_p,
+                              int sm_count, cudaStream_t st);
 
 void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state,
                    const gf_cand_spec& spec, const int32_t* idx, int32_t* status, double* fom_out,

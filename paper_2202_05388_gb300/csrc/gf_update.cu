@@ -142,7 +142,7 @@ __global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __
             double m = cabs1(A[rr * p + c]);
             if (m > best) { best = m; r = rr; }
           }
-          if (!(best >= thresh)) s_bad = 1;
+          if (!(best >= thresh) || !(best > 0.0)) s_bad = 1;
           s_piv = r;
           piv[c] = r;
         }
@@ -337,10 +337,11 @@ __global__ void __launch_bounds__(kUpdThreads) k_rank_update_f64(double2* __rest
                                                                  const cplx* __restrict__ C0,
                                                                  const cplx* __restrict__ S,
                                                                  const UpdCtl* __restrict__ ctl,
+                                                                 int only_above,
                                                                  int32_t* __restrict__ prof_p) {
   const int p = ctl->skip ? 0 : ctl->nv;
+  if (p <= only_above) return;
   if (prof_p && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *prof_p = p;
-  if (p == 0) return;
   const int64_t j = blockIdx.x * (int64_t)kUpdThreads + threadIdx.x;
   if (j >= n) return;
   switch (p) {
@@ -425,10 +426,23 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
     const cplx* S = reinterpret_cast<const cplx*>(ws + L.S + l * L.panel_s);
     const bool rec = timer && timer->on && timer->used < timer->max;
     int32_t* prof_p = rec ? timer->p_dev + timer->used : nullptr;
-    if (rec) cudaEventRecord(timer->ev0[timer->used], st);
+    if (rec) {
+      timer->p_host[timer->used] = 0;
+      cudaEventRecord(timer->ev0[timer->used], st);
+    }
     if (a.dtype == GF_C128) {
       double2* G = reinterpret_cast<double2*>(a.lam[l].G);
-      k_rank_update_f64<<<grid, kUpdThreads, 0, st>>>(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl, prof_p);
+      int only_above = 0;
+      if (a.algo == GF_UPDATE_TC) {
+        // p <= 4 on the tensor cores; the DFMA kernel below takes p > 4
+        launch_rank_update_ozaki(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl,
+                                 reinterpret_cast<uint8_t*>(ws + L.ozA), reinterpret_cast<int32_t*>(ws + L.ozE),
+                                 reinterpret_cast<uint8_t*>(ws + L.ozB), reinterpret_cast<int32_t*>(ws + L.ozF),
+                                 status, prof_p, a.sm_count, st);
+        only_above = 4;
+      }
+      if (a.algo != GF_UPDATE_TC || L.pmax > 4)
+        k_rank_update_f64<<<grid, kUpdThreads, 0, st>>>(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl, only_above, prof_p);
     } else {
       k_rank_update_c64_ref<<<grid, kUpdThreads, 0, st>>>(reinterpret_cast<float2*>(a.lam[l].G),
                                                           a.lam[l].ldg, n, L.pmax, C0, S, ctl, prof_p);

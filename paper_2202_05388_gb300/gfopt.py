@@ -20,6 +20,7 @@ GF_C128, GF_C64 = 0, 1
 GF_KIND_SINGLE, GF_KIND_BRUSH2 = 0, 1
 GF_DIR_FILL, GF_DIR_CLEAR = 1, 2
 GF_NBANDS = 9
+GF_UPDATE_TC, GF_UPDATE_DFMA = 0, 1
 
 STATUS_NAMES = {GF_OK: "GF_OK", GF_EINVAL: "GF_EINVAL", GF_ECUDA: "GF_ECUDA",
                 GF_ESINGULAR: "GF_ESINGULAR", GF_ENOIMPROVE: "GF_ENOIMPROVE",
@@ -28,7 +29,7 @@ STATUS_NAMES = {GF_OK: "GF_OK", GF_EINVAL: "GF_EINVAL", GF_ECUDA: "GF_ECUDA",
 EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_version",
            "gf_num_candidates", "gf_workspace_size", "gf_fill_g0", "gf_extract_bands",
            "gf_eval_candidates", "gf_select_topk", "gf_apply_update", "gf_profile_begin",
-           "gf_profile_end"]
+           "gf_profile_end", "gf_set_update_algo"]
 
 
 class GfError(RuntimeError):
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
             "gf_apply_update": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, C.c_int32, P,
                                             C.POINTER(gf_cand_spec), P, P, P, P, C.c_size_t, P]),
             "gf_profile_begin": (C.c_int32, [P, C.c_int32]),
+            "gf_set_update_algo": (C.c_int32, [P, C.c_int32]),
             "gf_profile_end": (C.c_int32, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         }
@@ -187,6 +189,9 @@ class Handle:
         self._check(self.lib.gf_apply_update(self.h, arr, len(probs), int(dtype), _ptr(state),
                                              C.byref(s), _ptr(idx), _ptr(status), _ptr(fom_out),
                                              _ptr(ws), int(ws_bytes), _stream(stream)))
+
+    def gf_set_update_algo(self, algo: int):
+        self._check(self.lib.gf_set_update_algo(self.h, int(algo)))
 
     def gf_profile_begin(self, max_records: int):
         self._check(self.lib.gf_profile_begin(self.h, int(max_records)))

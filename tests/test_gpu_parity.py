@@ -131,9 +131,12 @@ def test_no_improving_candidate_sets_status_and_changes_nothing():
 
 
 def test_singular_capacitance_is_reported_not_applied():
-    # Host-side fault injection: make 1 - G_jj d_chi = 0 for pixel j by editing G on the device.
-    wl = W.small(6, 5, kind=W.KIND_SINGLE, dir_mask=W.DIR_FILL)
-    g = wl.geoms[0]
+    # Host-side fault injection: make 1 - G_jj d_chi = 0 exactly for pixel j by editing G on
+    # the device (eps_mat = 9, so d_chi = 8 and G_jj = 1/8 are exact in FP64).
+    import dataclasses
+    wl0 = W.small(6, 5, kind=W.KIND_SINGLE, dir_mask=W.DIR_FILL)
+    g = dataclasses.replace(wl0.geoms[0], eps_mat=9.0)
+    wl = dataclasses.replace(wl0, geoms=(g,))
     opt = GreedyOptimizer(wl.geoms, wl.spec)
     opt.fill()
     j = 7
@@ -176,3 +179,34 @@ def test_host_validation_rejects_bad_arguments():
     off = B.problem_struct(g, opt.G[0].data_ptr() + 8, opt.ldg, opt.E[0], opt.bands[0])
     with pytest.raises(B.GfError, match="aligned"):
         opt.h.gf_extract_bands(off, opt.dtype)
+
+
+@pytest.mark.parametrize("nx,ny", [(24, 20), (47, 33)])
+def test_tensor_core_update_matches_dfma_update(nx, ny):
+    """The tensor-core digit-product update and the native-DFMA update agree to ~1e-15 on
+    ragged sizes (n not a multiple of the 128-row / 16-column tiles)."""
+    wl = W.small(nx, ny, kind=W.KIND_BRUSH2, dir_mask=3)
+    state = W.random_state(nx * ny, seed=31, fill=0.3)
+    a = GreedyOptimizer(wl.geoms, wl.spec)
+    b = GreedyOptimizer(wl.geoms, wl.spec)
+    b.h.gf_set_update_algo(B.GF_UPDATE_DFMA)
+    a.fill()
+    b.fill()
+    single = W.CandidateSpec(W.KIND_SINGLE, 3, 1)
+    for j in np.flatnonzero(state)[:40]:
+        a.force([int(j)], single)
+        b.force([int(j)], single)
+    torch.cuda.synchronize()
+    assert rel_err(gpu_G(a), gpu_G(b)) <= 1e-14
+    for t in range(6):
+        a.evaluate()
+        a.select()
+        b.idx.copy_(a.idx)
+        b.status.copy_(a.status)
+        a.update()
+        b.update()
+        torch.cuda.synchronize()
+        e = rel_err(gpu_G(a), gpu_G(b))
+        assert e <= 1e-14, (t, e)
+        assert rel_err(gpu_E(a), gpu_E(b)) <= 1e-14
+    assert int(a.status.cpu()[0]) in (B.GF_OK, B.GF_ENOIMPROVE)

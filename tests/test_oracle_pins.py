@@ -88,6 +88,10 @@ def test_gauss_pp_matches_lapack_and_flags_singular():
     S = np.array([[1.0, 2.0], [0.5, 1.0]], dtype=complex)
     assert not O.gauss_pp(S, np.ones(2))[1]
     assert not O.gauss_pp_batch(S[None], np.ones((1, 2)))[1][0]
+    # an exactly zero matrix is singular (its relative threshold is zero too)
+    Z = np.zeros((1, 1), dtype=complex)
+    assert not O.gauss_pp(Z, np.ones(1))[1]
+    assert not O.gauss_pp_batch(Z[None], np.ones((1, 1)))[1][0]
 
 
 def _brute_dfom(g, state, V, d_sign):
