@@ -153,7 +153,7 @@ struct KernelTimer {
   void release();
 };
 
-void launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0,
+bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0,
                               const cplx* S, const UpdCtl* ctl, uint8_t* ozA, int32_t* ozE,
                               uint8_t* ozB, int32_t* ozF, int32_t* status, int32_t* prof_p,
                               int sm_count, cudaStream_t st);

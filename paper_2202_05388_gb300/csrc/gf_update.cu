@@ -435,13 +435,14 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
       int only_above = 0;
       if (a.algo == GF_UPDATE_TC) {
         // p <= 4 on the tensor cores; the DFMA kernel below takes p > 4
-        launch_rank_update_ozaki(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl,
-                                 reinterpret_cast<uint8_t*>(ws + L.ozA), reinterpret_cast<int32_t*>(ws + L.ozE),
-                                 reinterpret_cast<uint8_t*>(ws + L.ozB), reinterpret_cast<int32_t*>(ws + L.ozF),
-                                 status, prof_p, a.sm_count, st);
-        only_above = 4;
+        // without a tensor map (driver too old) the DFMA kernel below takes every p
+        if (launch_rank_update_ozaki(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl,
+                                     reinterpret_cast<uint8_t*>(ws + L.ozA), reinterpret_cast<int32_t*>(ws + L.ozE),
+                                     reinterpret_cast<uint8_t*>(ws + L.ozB), reinterpret_cast<int32_t*>(ws + L.ozF),
+                                     status, prof_p, a.sm_count, st))
+          only_above = 4;
       }
-      if (a.algo != GF_UPDATE_TC || L.pmax > 4)
+      if (a.algo != GF_UPDATE_TC || L.pmax > 4 || only_above == 0)
         k_rank_update_f64<<<grid, kUpdThreads, 0, st>>>(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl, only_above, prof_p);
     } else {
       k_rank_update_c64_ref<<<grid, kUpdThreads, 0, st>>>(reinterpret_cast<float2*>(a.lam[l].G),

@@ -23,6 +23,11 @@
 // tolerance of the FP64 path, and uses the FP64 pipe for 2 adds per entry instead of 16 FMAs.
 #include <math.h>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "gf_internal.cuh"
 #include "gf_tc.cuh"
 
@@ -38,10 +43,8 @@ constexpr int kOzSliceA = kOzM * kOzK * 4;      // bytes of one digit slice of a
 constexpr int kOzSliceB = kOzN * kOzK * 4;      // bytes of one digit slice of a B tile
 constexpr int kOzTileA = kOzS * kOzSliceA;      // 24 KB
 constexpr int kOzTileB = kOzS * kOzSliceB;      // 6 KB
-constexpr int kOzTmemCols = 256;                // >= kOzLv * kOzN, power of two
-constexpr int kOzThreads = 128;
-constexpr int kOzSmem = 100 * 1024;             // dynamic smem request (limits to 2 CTAs/SM: TMEM)
 constexpr uint64_t kOzTimeoutNs = 2000000000ull;
+constexpr int kOzBBlockG = kOzTileB + 64;       // B digit slices + 16 column exponents (global block)
 
 // byte offset of element (r, k) inside one K-major, no-swizzle digit slice (8x16-byte core
 // matrices; K-direction core-matrix stride 128 B, row-group stride 256 B)
@@ -102,8 +105,7 @@ __global__ void k_oz_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n,
 }
 
 __global__ void k_oz_prep_cols(const cplx* __restrict__ S, int64_t n, int64_t ncols_pad,
-                               const UpdCtl* __restrict__ ctl, uint8_t* __restrict__ ozB,
-                               int32_t* __restrict__ ozF) {
+                               const UpdCtl* __restrict__ ctl, uint8_t* __restrict__ ozB) {
   if (ctl->skip || ctl->nv > 4) return;
   const int p = ctl->nv;
   // one thread per complex column j; writes real columns 2j and 2j+1
@@ -120,7 +122,6 @@ __global__ void k_oz_prep_cols(const cplx* __restrict__ S, int64_t n, int64_t nc
 #pragma unroll
     for (int k = 0; k < 4; ++k) m = fmax(m, fmax(fabs(sr[k]), fabs(si[k])));
     const int F = oz_exponent(m);
-    ozF[j] = F;
     float dr[4][kOzS], di[4][kOzS];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -128,8 +129,9 @@ __global__ void k_oz_prep_cols(const cplx* __restrict__ S, int64_t n, int64_t nc
       oz_digits(ldexp(si[k], -F), di[k]);
     }
     const int64_t c_re = 2 * j;
-    uint8_t* tile = ozB + (c_re / kOzN) * (int64_t)kOzTileB;
+    uint8_t* tile = ozB + (c_re / kOzN) * (int64_t)kOzBBlockG;
     const int c = (int)(c_re % kOzN);            // even; c + 1 is the imaginary column
+    reinterpret_cast<int32_t*>(tile + kOzTileB)[c / 2] = F;
 #pragma unroll
     for (int a = 0; a < kOzS; ++a) {
       uint8_t* sl = tile + a * kOzSliceB;
@@ -142,162 +144,282 @@ __global__ void k_oz_prep_cols(const cplx* __restrict__ S, int64_t n, int64_t nc
 }
 
 // ---- epilogue arithmetic --------------------------------------------------------------------
-// exact FP32 integer (|x| <= 2^22) -> int32
-__device__ __forceinline__ int32_t oz_f2i(float x) {
-  return (int32_t)__float_as_uint(x + 12582912.0f) - 0x4B400000;
-}
-
-// sum_L acc_L 2^(-9 (L+2)) in units of 2^-59 (levels 2..7)
+// Exact recombination of the six FP32 levels (each an integer below 2^22 in its own unit
+// 2^(-9 (L+2))) into one int64 in units of 2^-59.  Adjacent levels are first joined in int32:
+// |acc_L| <= 2^21.8, so |acc_L 2^9 + acc_(L+1)| < 2^31.  The float -> int conversion adds
+// 1.5 * 2^23 so that the integer sits in the low mantissa bits.
 __device__ __forceinline__ long long oz_combine(const float (&acc)[kOzLv]) {
-  long long D = oz_f2i(acc[0]);
-#pragma unroll
-  for (int L = 1; L < kOzLv - 1; ++L) D = D * 512 + oz_f2i(acc[L]);
-  return D * 32 + ((oz_f2i(acc[kOzLv - 1]) + 8) >> 4);
+  constexpr int32_t M = 0x4B400000;            // bit pattern of 1.5 * 2^23
+  const int32_t b0 = __float_as_int(acc[0] + 12582912.0f) - M;
+  const int32_t b1 = __float_as_int(acc[1] + 12582912.0f) - M;
+  const int32_t b2 = __float_as_int(acc[2] + 12582912.0f) - M;
+  const int32_t b3 = __float_as_int(acc[3] + 12582912.0f) - M;
+  const int32_t b4 = __float_as_int(acc[4] + 12582912.0f) - M;
+  const int32_t b5 = __float_as_int(acc[5] + 12582912.0f) - M;
+  const int32_t P1 = (b0 << 9) + b1;           // units 2^-27
+  const int32_t P2 = (b2 << 9) + b3;           // units 2^-45
+  const int32_t P3 = (b4 << 9) + b5;           // units 2^-63
+  return ((long long)P1 << 32) + ((long long)P2 << 14) + (long long)((P3 + 8) >> 4);
 }
 
-// D * 2^u as a double, built with integer operations (|D| < 2^62)
+// D * 2^u as a double, built with integer operations (|D| < 2^62; the 53-bit mantissa is
+// truncated, an error below 2^-52 of |D 2^u|).
 __device__ __forceinline__ double oz_to_double(long long D, int u) {
-  if (D == 0) return 0.0;
-  const unsigned long long sign = D < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned long long M = D < 0 ? (unsigned long long)(-D) : (unsigned long long)D;
+  const long long sg = D >> 63;                                   // 0 or -1
+  unsigned long long M = (unsigned long long)((D ^ sg) - sg);     // |D|
   const int lz = __clzll(M);
-  M <<= lz;                                        // leading one at bit 63
-  const unsigned long long mant = (M >> 11) + ((M >> 10) & 1ull);   // 53 bits, rounded
-  const long long e = 63 - lz + u;                 // exponent of the leading one
-  const unsigned long long bits = ((unsigned long long)(e + 1022) << 52) + mant;
-  return __longlong_as_double((long long)(bits | sign));
+  M <<= (lz & 63);
+  const unsigned long long mant = M >> 11;                        // leading one at bit 52
+  const long long e = 63 - lz + u;
+  unsigned long long bits = ((unsigned long long)(e + 1022) << 52) + mant;
+  bits |= (unsigned long long)sg & 0x8000000000000000ull;
+  return D == 0 ? 0.0 : __longlong_as_double((long long)bits);
 }
 
 // ---- the update kernel ----------------------------------------------------------------------
-// grid.x: 128-row tiles; grid.y: column chunks.  One CTA = 4 warps; thread t owns tile row t
-// (= TMEM lane t).  Thread 0 issues the MMAs.
-__global__ void __launch_bounds__(kOzThreads, 1)
-k_rank_update_ozaki(double2* __restrict__ G, int64_t ldg, int64_t n, int64_t ncol_tiles,
+// Persistent, warp-specialised.  Work = the (128-row tile, 16-complex-column tile) grid in
+// row-major order, split into equal contiguous ranges, one per CTA.
+//   warp 16      producer: TMA copies of the A digit tile when the row tile changes, and per
+//                tile the G tile (two 128-row x 128-byte boxes through a tensor map, 128B
+//                swizzle) plus the B digit block into a 4-stage shared-memory ring;
+//   warp 17      MMA issuer: 21 tcgen05.mma per tile into one of two TMEM buffers;
+//   warps 0..15  epilogue: TMEM -> registers, exact recombination, G += delta in shared
+//                memory;
+//   warp 18      storer: once all epilogue threads have written a tile, TMA-stores its two
+//                boxes back to HBM (the tensor map clips ragged edges) and frees the stage
+//                when the stores have read shared memory.
+// Every wait is bounded (globaltimer) and can be aborted; a timeout sets GF_ETIMEOUT.
+constexpr int kOzNS = 4;                          // shared-memory stages
+constexpr int kOzBox = kOzM * 128;                // one TMA box: 128 rows x 128 B (8 complex128)
+constexpr int kOzGTile = 2 * kOzBox;              // 32768: the tile's two boxes, 128B-swizzled
+constexpr int kOzBBlock = kOzTileB + 64;          // digit slices + 16 column exponents
+constexpr int kOzStage = 39936;                   // kOzGTile + kOzBBlock, 1024-aligned
+constexpr int kOzBarOff = 2 * kOzTileA + kOzNS * kOzStage;
+constexpr int kOzSmemV2 = kOzBarOff + 256;
+constexpr int kOzEpiThreads = 512;
+constexpr int kOzThreadsV2 = 608;
+constexpr int kOzTmemColsV2 = 512;                // two accumulator sets of kOzLv * kOzN columns
+constexpr int kEpiWarps = kOzEpiThreads / 32;    // 16
+constexpr int kWarpProd = kEpiWarps, kWarpMma = kEpiWarps + 1, kWarpStore = kEpiWarps + 2;
+constexpr int kOzColsPerThread = 4;               // complex columns per epilogue thread per tile
+static_assert(kOzThreadsV2 == 32 * (kEpiWarps + 3), "warp roles");
+static_assert(kEpiWarps / 4 * kOzColsPerThread == kOzN / 2, "column split");
+static_assert(kOzGTile + kOzBBlock <= kOzStage, "stage layout");
+static_assert(kOzLv * kOzN <= 256, "TMEM buffer");
+
+struct OzBars {
+  uint64_t full[kOzNS], empty[kOzNS], ebar[kOzNS];
+  uint64_t afull[2], aempty[2], tfull[2], tempty[2];
+  uint32_t tslot;
+  int abort;
+};
+
+__global__ void __launch_bounds__(kOzThreadsV2, 1)
+k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restrict__ G, int64_t ldg,
+                    int64_t n, int64_t nrt, int64_t nct,
                     const uint8_t* __restrict__ ozA, const int32_t* __restrict__ ozE,
-                    const uint8_t* __restrict__ ozB, const int32_t* __restrict__ ozF,
-                    const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status,
-                    int32_t* __restrict__ prof_p) {
+                    const uint8_t* __restrict__ ozB, const UpdCtl* __restrict__ ctl,
+                    int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int p = ctl->skip ? 0 : ctl->nv;
-  if (prof_p && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *prof_p = (p >= 1 && p <= 4) ? p : 0;
+  if (prof_p && blockIdx.x == 0 && threadIdx.x == 0 && p >= 1 && p <= 4) *prof_p = p;
   if (p < 1 || p > 4) return;
 
-  uint8_t* As = smem;                              // kOzTileA
-  uint8_t* Bs = smem + kOzTileA;                   // kOzTileB
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kOzTileA + kOzTileB);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kOzTileA + kOzTileB + 8);
-  const int t = threadIdx.x, warp = t >> 5;
-  const int64_t rt = blockIdx.x;
-  const int64_t i = rt * kOzM + t;
+  OzBars* bars = reinterpret_cast<OzBars*>(smem + kOzBarOff);
+  uint8_t* Abuf = smem;                                       // 2 x kOzTileA
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  volatile int* abort = &bars->abort;
 
-  if (warp == 0) {
-    tc::tmem_alloc(tslot, kOzTmemCols);
+  if (warp == kWarpMma) {
+    tc::tmem_alloc(&bars->tslot, kOzTmemColsV2);
     tc::tmem_relinquish();
   }
-  if (t == 0) {
-    tc::mbar_init(mbar, 1);
+  if (tid == 0) {
+    for (int q = 0; q < kOzNS; ++q) {
+      tc::mbar_init(&bars->full[q], 1);
+      tc::mbar_init(&bars->empty[q], 2);
+      tc::mbar_init(&bars->ebar[q], kOzEpiThreads);
+    }
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&bars->afull[q], 1);
+      tc::mbar_init(&bars->aempty[q], 1);
+      tc::mbar_init(&bars->tfull[q], 1);
+      tc::mbar_init(&bars->tempty[q], kOzEpiThreads / 32);
+    }
+    bars->abort = 0;
     tc::fence_mbar_init();
   }
-  {  // A digit slices of this row tile -> smem
-    const uint4* src = reinterpret_cast<const uint4*>(ozA + rt * (int64_t)kOzTileA);
-    uint4* dst = reinterpret_cast<uint4*>(As);
-    for (int q = t; q < kOzTileA / 16; q += kOzThreads) dst[q] = src[q];
-  }
-  const int Ei = ozE[rt * kOzM + t];
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tbase = *tslot;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  const uint32_t idesc = tc::idesc_tf32(kOzM, kOzN);
-  const uint32_t sA = tc::smem_u32(As), sB = tc::smem_u32(Bs);
+  const uint32_t tbase = bars->tslot;
 
-  // column tiles of this chunk
-  const int64_t per = (ncol_tiles + gridDim.y - 1) / gridDim.y;
-  const int64_t ct0 = blockIdx.y * per;
-  const int64_t ct1 = ct0 + per < ncol_tiles ? ct0 + per : ncol_tiles;
-  uint32_t phase = 0;
-  bool failed = false;
-  for (int64_t ct = ct0; ct < ct1; ++ct) {
-    {  // B digit slices of this column tile -> smem
-      const uint4* src = reinterpret_cast<const uint4*>(ozB + ct * (int64_t)kOzTileB);
-      uint4* dst = reinterpret_cast<uint4*>(Bs);
-      for (int q = t; q < kOzTileB / 16; q += kOzThreads) dst[q] = src[q];
-    }
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (t == 0) {
-      int first[kOzLv];
-#pragma unroll
-      for (int L = 0; L < kOzLv; ++L) first[L] = 1;
-#pragma unroll
-      for (int a = 0; a < kOzS; ++a) {
-#pragma unroll
-        for (int b = 0; b < kOzS; ++b) {
-          if (a + b <= kOzLv - 1) {
-            const int L = a + b;
-            const uint64_t da = tc::smem_desc(sA + a * kOzSliceA, 128, 256);
-            const uint64_t db = tc::smem_desc(sB + b * kOzSliceB, 128, 256);
-            tc::mma_tf32(tbase + (uint32_t)(L * kOzN), da, db, idesc, first[L] ? 0u : 1u);
-            first[L] = 0;
+  const int64_t T = nrt * nct;
+  const int64_t tb = T * blockIdx.x / gridDim.x;
+  const int64_t te = T * (blockIdx.x + 1) / gridDim.x;
+
+  if (warp == kWarpProd) {
+    // ------------------------------------------------------------------ producer
+    int64_t cur_rt = -1;
+    int64_t aseq = -1;
+    int64_t k = 0;
+    for (int64_t t = tb; t < te; ++t, ++k) {
+      const int64_t rt = t / nct, ct = t - rt * nct;
+      bool ok = true;
+      if (rt != cur_rt) {
+        ++aseq;
+        const int ab = (int)(aseq & 1);
+        if (lane == 0) {
+          if (aseq >= 2) ok = tc::mbar_wait_or_abort(&bars->aempty[ab], (uint32_t)((aseq / 2 - 1) & 1), abort, kOzTimeoutNs);
+          if (ok) {
+            tc::mbar_arrive_expect_tx(&bars->afull[ab], kOzTileA);
+            tc::bulk_g2s(Abuf + ab * kOzTileA, ozA + rt * (int64_t)kOzTileA, kOzTileA, &bars->afull[ab]);
           }
         }
+        cur_rt = rt;
       }
-      tc::mma_commit(mbar);
+      const int s = (int)(k % kOzNS);
+      if (lane == 0 && ok && k >= kOzNS)
+        ok = tc::mbar_wait_or_abort(&bars->empty[s], (uint32_t)((k / kOzNS - 1) & 1), abort, kOzTimeoutNs);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) break;
+      uint8_t* stage = smem + 2 * kOzTileA + s * kOzStage;
+      if (lane == 0) {
+        // x in doubles (2 per complex entry), y in rows; both boxes are always full-size
+        const int x = (int)(ct * kOzN), y = (int)(rt * kOzM);
+        const bool second = x + 16 < 2 * n;         // the right box holds at least one column
+        tc::mbar_arrive_expect_tx(&bars->full[s], (uint32_t)((second ? kOzGTile : kOzBox) + kOzBBlock));
+        tc::tma_load_2d(stage, &tmapG, x, y, &bars->full[s]);
+        if (second) tc::tma_load_2d(stage + kOzBox, &tmapG, x + 16, y, &bars->full[s]);
+        tc::bulk_g2s(stage + kOzGTile, ozB + ct * (int64_t)kOzBBlock, kOzBBlock, &bars->full[s]);
+      }
+      __syncwarp();
     }
-    // prefetch this thread's G row segment while the MMAs run
-    const int64_t j0 = ct * (kOzN / 2);
-    double2 g[kOzN / 2];
-    const bool row_ok = i < n;
+  } else if (warp == kWarpMma) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_tf32(kOzM, kOzN);
+      int64_t cur_rt = -1;
+      int64_t aseq = -1;
+      int64_t k = 0;
+      int ab = 0;
+      for (int64_t t = tb; t < te; ++t, ++k) {
+        const int64_t rt = t / nct;
+        if (rt != cur_rt) {
+          if (cur_rt >= 0) tc::mma_commit(&bars->aempty[ab]);      // old A tile free once its MMAs end
+          ++aseq;
+          ab = (int)(aseq & 1);
+          if (!tc::mbar_wait_or_abort(&bars->afull[ab], (uint32_t)((aseq / 2) & 1), abort, kOzTimeoutNs)) break;
+          cur_rt = rt;
+        }
+        const int s = (int)(k % kOzNS);
+        const int b = (int)(k & 1);
+        if (!tc::mbar_wait_or_abort(&bars->full[s], (uint32_t)((k / kOzNS) & 1), abort, kOzTimeoutNs)) break;
+        if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[b], (uint32_t)((k / 2 - 1) & 1), abort, kOzTimeoutNs)) break;
+        tc::fence_after_sync();
+        const uint32_t sA = tc::smem_u32(Abuf + ab * kOzTileA);
+        const uint32_t sB = tc::smem_u32(smem + 2 * kOzTileA + s * kOzStage + kOzGTile);
+        bool first[kOzLv];
 #pragma unroll
-    for (int q = 0; q < kOzN / 2; ++q) {
-      const int64_t j = j0 + q;
-      g[q] = (row_ok && j < n) ? G[i * ldg + j] : make_double2(0.0, 0.0);
-    }
-    const bool ok = tc::mbar_wait_bounded(mbar, phase, kOzTimeoutNs);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    tc::fence_after_sync();
+        for (int L = 0; L < kOzLv; ++L) first[L] = true;
 #pragma unroll
-    for (int cg = 0; cg < kOzN / 8; ++cg) {
+        for (int a = 0; a < kOzS; ++a) {
+#pragma unroll
+          for (int bb = 0; bb < kOzS; ++bb) {
+            if (a + bb <= kOzLv - 1) {
+              const int L = a + bb;
+              tc::mma_tf32(tbase + (uint32_t)(b * 256 + L * kOzN), tc::smem_desc(sA + a * kOzSliceA, 128, 256),
+                           tc::smem_desc(sB + bb * kOzSliceB, 128, 256), idesc, first[L] ? 0u : 1u);
+              first[L] = false;
+            }
+          }
+        }
+        tc::mma_commit(&bars->tfull[b]);
+        tc::mma_commit(&bars->empty[s]);
+      }
+    }
+    __syncwarp();
+  } else if (warp < kEpiWarps) {
+    // ------------------------------------------------------------------ epilogue
+    const int q = warp & 3, h = warp >> 2;     // TMEM lane quarter, column quarter
+    const int r = q * 32 + lane;               // tile row
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    int64_t cur_rt = -1;
+    int Ei = 0;
+    int64_t k = 0;
+    for (int64_t t = tb; t < te; ++t, ++k) {
+      const int64_t rt = t / nct, ct = t - rt * nct;
+      if (rt != cur_rt) {
+        Ei = ozE[rt * kOzM + r];
+        cur_rt = rt;
+      }
+      const int s = (int)(k % kOzNS);
+      const int b = (int)(k & 1);
+      if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kOzTimeoutNs)) break;
+      if (!tc::mbar_wait_or_abort(&bars->full[s], (uint32_t)((k / kOzNS) & 1), abort, kOzTimeoutNs)) break;
+      tc::fence_after_sync();
       float acc[kOzLv][8];
 #pragma unroll
       for (int L = 0; L < kOzLv; ++L)
-        tc::tmem_ld8(tbase + lane_base + (uint32_t)(L * kOzN + cg * 8), acc[L]);
+        tc::tmem_ld8(tbase + lane_addr + (uint32_t)(b * 256 + L * kOzN + h * 8), acc[L]);
       tc::tmem_ld_wait();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
+      uint8_t* stage = smem + 2 * kOzTileA + s * kOzStage;
+      const int32_t* Fj = reinterpret_cast<const int32_t*>(stage + kOzGTile + kOzTileB);
+      // complex column jj of row r: box jj/8, 16-byte chunk (jj%8) XOR (r%8) (128B swizzle)
+      uint8_t* rowbase = stage + r * 128;
+      const int64_t i = rt * kOzM + r;
+      const int64_t j0 = ct * (kOzN / 2);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int qq = cg * 4 + q;
-        const int64_t j = j0 + qq;
-        if (!row_ok || j >= n) continue;
-        float lr[kOzLv], li[kOzLv];
+      for (int c = 0; c < kOzColsPerThread; ++c) {
+        const int jj = h * kOzColsPerThread + c;
+        if (i < n && j0 + jj < n) {
+          float lr[kOzLv], li[kOzLv];
 #pragma unroll
-        for (int L = 0; L < kOzLv; ++L) {
-          lr[L] = acc[L][2 * q];
-          li[L] = acc[L][2 * q + 1];
+          for (int L = 0; L < kOzLv; ++L) {
+            lr[L] = acc[L][2 * c];
+            li[L] = acc[L][2 * c + 1];
+          }
+          const int u = Ei + Fj[jj] - 59;
+          double2* gp = reinterpret_cast<double2*>(rowbase + (jj >> 3) * kOzBox + (((jj & 7) ^ (r & 7)) << 4));
+          const double2 g = *gp;
+          *gp = make_double2(g.x + oz_to_double(oz_combine(lr), u), g.y + oz_to_double(oz_combine(li), u));
         }
-        const int u = Ei + ozF[j] - 59;
-        const double dre = oz_to_double(oz_combine(lr), u);
-        const double dim = oz_to_double(oz_combine(li), u);
-        G[i * ldg + j] = make_double2(g[qq].x + dre, g[qq].y + dim);
       }
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(&bars->ebar[s]);
     }
-    tc::fence_before_sync();
-    __syncthreads();
   }
-  if (failed) {
-    if (t == 0) atomicExch(status, GF_ETIMEOUT);
-    // wait (bounded) for the MMAs of the failed tile before giving the TMEM back
-    tc::mbar_wait_bounded(mbar, phase ^ 1u, kOzTimeoutNs);
+  if (warp == kWarpStore) {
+    // ------------------------------------------------------------------ storer
+    int64_t k = 0;
+    for (int64_t t = tb; t < te; ++t, ++k) {
+      const int64_t rt = t / nct, ct = t - rt * nct;
+      const int s = (int)(k % kOzNS);
+      bool ok = true;
+      if (lane == 0) ok = tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)((k / kOzNS) & 1), abort, kOzTimeoutNs);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) break;
+      uint8_t* stage = smem + 2 * kOzTileA + s * kOzStage;
+      if (lane == 0) {
+        const int x = (int)(ct * kOzN), y = (int)(rt * kOzM);
+        tc::tma_store_2d(&tmapG, x, y, stage);
+        if (x + 16 < 2 * n) tc::tma_store_2d(&tmapG, x + 16, y, stage + kOzBox);
+      }
+      tc::bulk_commit();
+      tc::bulk_wait_read0();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars->empty[s]);
+    }
+    tc::bulk_wait0();
   }
-  tc::fence_after_sync();
+  tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, kOzTmemCols);
+  if (tid == 0 && bars->abort) atomicExch(status, GF_ETIMEOUT);
+  tc::fence_after_sync();
+  if (warp == kWarpMma) tc::tmem_dealloc(tbase, kOzTmemColsV2);
 }
 
 OzLayout oz_layout(int64_t n) {
@@ -306,15 +428,46 @@ OzLayout oz_layout(int64_t n) {
   o.ncol_tiles = (2 * n + kOzN - 1) / kOzN;
   o.bytesA = (size_t)o.nrow_tiles * kOzTileA;
   o.bytesE = (size_t)o.nrow_tiles * kOzM * 4;
-  o.bytesB = (size_t)o.ncol_tiles * kOzTileB;
-  o.bytesF = (size_t)o.ncol_tiles * (kOzN / 2) * 4;
+  o.bytesB = (size_t)o.ncol_tiles * kOzBBlockG;
+  o.bytesF = 0;
   return o;
 }
 
-void launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0,
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// G as a 2-D tensor of doubles: 2n columns (re, im interleaved) by n rows, row stride 16 ldg
+// bytes; boxes of 16 doubles (128 B) x 128 rows with 128-byte swizzle.
+static bool make_tmap_G(CUtensorMap* m, double2* G, int64_t ldg, int64_t n) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)(2 * n), (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)(16 * ldg)};
+  cuuint32_t box[2] = {16, (cuuint32_t)kOzM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)G, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0,
                               const cplx* S, const UpdCtl* ctl, uint8_t* ozA, int32_t* ozE,
                               uint8_t* ozB, int32_t* ozF, int32_t* status, int32_t* prof_p,
                               int sm_count, cudaStream_t st) {
+  (void)ozF;
+  CUtensorMap tmap;
+  if (!make_tmap_G(&tmap, G, ldg, n)) return false;
   const OzLayout o = oz_layout(n);
   {
     int64_t rows = o.nrow_tiles * kOzM;
@@ -322,18 +475,14 @@ void launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, cons
     k_oz_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, pmax, n, rows, ctl, ozA, ozE);
     int64_t cols = o.ncol_tiles * (kOzN / 2);
     b = (cols + 127) / 128;
-    k_oz_prep_cols<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(S, n, cols, ctl, ozB, ozF);
+    k_oz_prep_cols<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(S, n, cols, ctl, ozB);
   }
-  cudaFuncSetAttribute(k_rank_update_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
-  // about 4 waves of 2 CTAs per SM
-  int64_t target = (int64_t)sm_count * 2 * 4;
-  int64_t chunks = (target + o.nrow_tiles - 1) / o.nrow_tiles;
-  if (chunks < 1) chunks = 1;
-  if (chunks > o.ncol_tiles) chunks = o.ncol_tiles;
-  if (chunks > 65535) chunks = 65535;
-  dim3 grid((unsigned)o.nrow_tiles, (unsigned)chunks);
-  k_rank_update_ozaki<<<grid, kOzThreads, kOzSmem, st>>>(G, ldg, n, o.ncol_tiles, ozA, ozE, ozB, ozF,
-                                                         ctl, status, prof_p);
+  cudaFuncSetAttribute(k_rank_update_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmemV2);
+  const int64_t tiles = o.nrow_tiles * o.ncol_tiles;
+  const int grid = (int)(tiles < sm_count ? tiles : sm_count);
+  k_rank_update_ozaki<<<grid, kOzThreadsV2, kOzSmemV2, st>>>(tmap, G, ldg, n, o.nrow_tiles, o.ncol_tiles, ozA,
+                                                            ozE, ozB, ctl, status, prof_p);
+  return true;
 }
 
 }  // namespace gf
