@@ -222,7 +222,9 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restri
                     int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int p = ctl->skip ? 0 : ctl->nv;
+#ifndef GF_EXPERIMENT_NO_PROFP
   if (prof_p && blockIdx.x == 0 && threadIdx.x == 0 && p >= 1 && p <= 4) *prof_p = p;
+#endif
   if (p < 1 || p > 4) return;
 
   OzBars* bars = reinterpret_cast<OzBars*>(smem + kOzBarOff);
@@ -477,7 +479,17 @@ bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, cons
     b = (cols + 127) / 128;
     k_oz_prep_cols<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(S, n, cols, ctl, ozB);
   }
-  cudaFuncSetAttribute(k_rank_update_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmemV2);
+  {  // once per device
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+      cudaFuncSetAttribute(k_rank_update_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmemV2);
+      if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+  }
   const int64_t tiles = o.nrow_tiles * o.ncol_tiles;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
   k_rank_update_ozaki<<<grid, kOzThreadsV2, kOzSmemV2, st>>>(tmap, G, ldg, n, o.nrow_tiles, o.ncol_tiles, ozA,
