@@ -122,6 +122,15 @@ size_t gf_workspace_size(const gf_geom* geom, int32_t nlam, int32_t dtype,
 gf_status gf_fill_g0(gf_handle* h, const gf_problem* prob, int32_t dtype,
                      void* ws, size_t ws_bytes, void* stream);
 
+/* gf_fill_g0 without a workspace, for callers that cannot allocate device memory (a host
+ * application that owns all device allocations, or a loop that must not call cudaMalloc).
+ * The paper has no counterpart.  The Hankel table lives in a fixed 4 MiB array inside the
+ * library (held on every GPU that loads it until exit), so N = nx*ny <= 131072 (GF_EINVAL
+ * otherwise).  All calls share that array: calls overlapping on the GPU race and must be
+ * ordered by the caller.  The first call on a device looks up the array's address; make it
+ * before any stream capture.  Writes the same G, E and bands as gf_fill_g0. */
+gf_status gf_fill_g0_static(gf_handle* h, const gf_problem* prob, int32_t dtype, void* stream);
+
 /* Re-extract the bands of one wavelength from its G (used after external edits of G). */
 gf_status gf_extract_bands(gf_handle* h, const gf_problem* prob, int32_t dtype, void* stream);
 

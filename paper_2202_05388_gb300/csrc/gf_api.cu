@@ -122,6 +122,13 @@ static gf_status check_lams(gf_handle* h, const gf_problem* probs, int32_t nlam,
 
 namespace gf {
 
+// Host helpers shared with other translation units that add entry points.
+gf_status api_check_problem(gf_handle* h, const gf_problem* p, int dtype) { return check_problem(h, p, dtype, true); }
+gf_status api_bind_device(gf_handle* h) { return bind_device(h); }
+gf_status api_cuda_check(gf_handle* h, const char* where) { return cuda_check(h, where); }
+gf_status api_fail_msg(gf_handle* h, gf_status s, const char* msg) { return fail(h, s, "%s", msg); }
+int api_device(const gf_handle* h) { return h->device; }
+
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& spec) {

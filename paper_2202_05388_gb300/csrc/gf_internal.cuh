@@ -95,6 +95,13 @@ OzLayout oz_layout(int64_t n);
 
 WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& spec);
 
+// host helpers of gf_api.cu for entry points defined in other translation units
+gf_status api_check_problem(gf_handle* h, const gf_problem* p, int dtype);
+gf_status api_bind_device(gf_handle* h);
+gf_status api_cuda_check(gf_handle* h, const char* where);
+gf_status api_fail_msg(gf_handle* h, gf_status s, const char* msg);
+int api_device(const gf_handle* h);
+
 // ----------------------------------------------------------------------------- kernels
 void launch_fill_table(const gf_geom& g, cplx* table, cudaStream_t st);
 void launch_fill_expand(const gf_geom& g, int dtype, void* G, int64_t ldg, const cplx* table,

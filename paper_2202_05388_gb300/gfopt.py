@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
                                             C.POINTER(gf_cand_spec), P, P, P, P, C.c_size_t, P]),
             "gf_profile_begin": (C.c_int32, [P, C.c_int32]),
             "gf_set_update_algo": (C.c_int32, [P, C.c_int32]),
+            "gf_fill_g0_static": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, P]),
             "gf_profile_end": (C.c_int32, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         }
@@ -166,6 +167,10 @@ class Handle:
     def gf_fill_g0(self, prob: gf_problem, dtype, ws, ws_bytes, stream=None):
         self._check(self.lib.gf_fill_g0(self.h, C.byref(prob), int(dtype), _ptr(ws), int(ws_bytes),
                                         _stream(stream)))
+
+    def gf_fill_g0_static(self, prob: gf_problem, dtype, stream=None):
+        """gf_fill_g0 with its table in the library's fixed device array (no workspace)."""
+        self._check(self.lib.gf_fill_g0_static(self.h, C.byref(prob), int(dtype), _stream(stream)))
 
     def gf_extract_bands(self, prob: gf_problem, dtype, stream=None):
         self._check(self.lib.gf_extract_bands(self.h, C.byref(prob), int(dtype), _stream(stream)))
