@@ -50,7 +50,9 @@ def parse():
 
 
 def workload(name):
-    return {"brush_192": W.brush_192, "plain_32": W.plain_32, "brush_64": W.brush_64}[name]()
+    return {"brush_192": W.brush_192, "plain_32": W.plain_32, "brush_64": W.brush_64,
+            "brush_128_topk": W.brush_128_topk,
+            "brush_320_topk": W.brush_320_topk, "multilambda_512x64": W.multi_lambda_512x64}[name]()
 
 
 # ------------------------------------------------------------------------------ clocks
@@ -114,6 +116,18 @@ def measured_peaks():
             d = json.load(fh)
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def tf32_peak_tflops():
+    """Dense TF32 tensor peak: the measured BF16 burst peak x the nominal TF32/BF16 ratio
+    (1.1 / 2.25 PFLOP/s dense)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    ratio = 1.1 / 2.25
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get("bf16_tflops", 1900.0) * ratio, "measured bf16 burst x nominal tf32/bf16 (0.489)"
+    return 1900.0 * ratio, "fallback bf16 x nominal tf32/bf16 (0.489)"
 
 
 # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit count x max clock)
@@ -263,7 +277,7 @@ def run_native(args):
     # bookkeeping ops) is loaded before timing -- lazy module loading costs seconds
     for _ in range(args.warmup):
         opt.step()
-        accepted += (opt.status == B.GF_OK).to(torch.int64)
+        accepted += opt.applied.to(torch.int64)
     accepted.zero_()
     torch.cuda.synchronize()
     if world > 1:
@@ -280,7 +294,7 @@ def run_native(args):
     e0.record(stream)
     for _ in range(args.steps):
         opt.step()
-        accepted += (opt.status == B.GF_OK).to(torch.int64)
+        accepted += opt.applied.to(torch.int64)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -337,17 +351,17 @@ def run_native(args):
     e2e = None
     if not args.no_e2e:
         host_state = torch.zeros(g.N, dtype=torch.uint8).pin_memory()
-        host_out = torch.empty(2 * max(1, wl.spec.k) + 2, dtype=torch.float64).pin_memory()
+        host_out = torch.empty(2 * max(1, wl.spec.k) + 3, dtype=torch.float64).pin_memory()
         opt2 = opt
         k = max(1, wl.spec.k)
 
         def e2e_step():
             opt2.step()
             packed = torch.cat([opt2.idx[:k].to(torch.float64), opt2.val[:k],
-                                opt2.status.to(torch.float64), opt2.fom])
+                                opt2.status.to(torch.float64), opt2.fom, opt2.applied.to(torch.float64)])
             host_out.copy_(packed, non_blocking=True)
             torch.cuda.current_stream().synchronize()
-            return int(host_out[2 * k].item() == B.GF_OK)
+            return int(host_out[2 * k + 2].item())
 
         opt2.state.copy_(host_state, non_blocking=True)
         opt2.fill()
@@ -377,11 +391,18 @@ def run_native(args):
     flops_per_launch = kern_flops / max(kern_launches, 1)
     achieved_gbs = bytes_per_launch / (kern_avg_ms * 1e-3) / 1e9
     achieved_tfl = flops_per_launch / (kern_avg_ms * 1e-3) / 1e12
-    roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
-            "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind,
-            "kernel": ("k_rank_update_ozaki (tcgen05 digit products, TMA tiles) + operand prep"
-                       if wl.dtype == "c128" else "G update (complex64)"),
-            "fp64_pipe_note": "the same update on native DFMA is FP64-pipe bound; see dfma_update"}
+    if wl.dtype == "c128":
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
+                "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "k_rank_update_ozaki (tcgen05 digit products, TMA tiles) + operand prep",
+                "fp64_pipe_note": "the same update on native DFMA is FP64-pipe bound; see dfma_update"}
+    else:
+        tf32_peak, tf32_kind = tf32_peak_tflops()
+        roof = {"bound": "tensor", "achieved": achieved_tfl, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": achieved_tfl / tf32_peak, "traffic": None, "peak_kind": tf32_kind,
+                "kernel": "k_rank_update_c64_tc (tcgen05 split-TF32, 3 products) + D A^-1 + S GEMM + operand prep",
+                "flops_note": "algorithmic 8 p n^2 per update; the split-TF32 form executes 3x that on the tensor pipe",
+                "hbm_achieved_gbs": achieved_gbs, "hbm_frac": achieved_gbs / peak_hbm, "hbm_peak_gbs": peak_hbm}
     roof["algorithmic_bytes_per_launch"] = bytes_per_launch
     roof["kernel_ms_avg"] = kern_avg_ms
     roof["kernel_share_of_step"] = kern_ms / ms
@@ -392,7 +413,8 @@ def run_native(args):
             "data": "synthetic",
             "config": {"workload": wl.name, "nx": g.nx, "ny": g.ny, "n": g.N + 1,
                        "candidates": opt.ncand, "G_GB": opt.G[0].numel() * opt.G[0].element_size() / 1e9,
-                       "storage": wl.dtype, "l2": "inputs larger than L2 (G is 21.7 GB per replica)",
+                       "storage": wl.dtype, "k": wl.spec.k, "nlam": nlam,
+                       "l2": "inputs larger than L2 (G is %.1f GB per replica)" % (opt.G[0].numel() * opt.G[0].element_size() / 1e9 * nlam),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "candidate_evals_per_s": opt.ncand * args.steps * world / (t_max / 1e3),
             "g_update_GBps": achieved_gbs,

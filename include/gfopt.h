@@ -157,12 +157,13 @@ gf_status gf_select_topk(gf_handle* h, const gf_geom* geom, const gf_cand_spec* 
  * y = A^{-1} E_V (Eqs. 4, 9); flip state at V, re-extract bands and write the new
  * FOM (sum over wavelengths of |E_N|^2) to *fom_out (device double).  With more than one
  * candidate, the union is applied only if its joint dFOM is positive; otherwise idx[0]
- * alone (the best one) is applied.  No-op when *status != GF_OK on entry; sets
+ * alone (the best one) is applied.  *applied (device int32, may be NULL) receives the number
+ * of candidates applied (0 when nothing changed).  No-op when *status != GF_OK on entry; sets
  * *status = GF_ESINGULAR (and changes nothing) when A is singular. */
 gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, int32_t dtype,
                           uint8_t* state, const gf_cand_spec* spec, const int32_t* idx,
-                          int32_t* status, double* fom_out, void* ws, size_t ws_bytes,
-                          void* stream);
+                          int32_t* status, double* fom_out, int32_t* applied, void* ws,
+                          size_t ws_bytes, void* stream);
 
 /* Arithmetic of the complex128 G update (Eq. 10).  GF_UPDATE_TC (default): exact digit
  * products on the tensor cores with an integer recombination (FP64-accurate to ~2^-50 of

@@ -132,7 +132,6 @@ int api_device(const gf_handle* h) { return h->device; }
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& spec) {
-  (void)dtype;
   WsLayout L;
   const int64_t N = (int64_t)g.nx * g.ny;
   L.n = N + 1;
@@ -157,6 +156,10 @@ WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& sp
   L.ozE = o; o = up256(o + oz.bytesE);
   L.ozB = o; o = up256(o + oz.bytesB);
   L.ozF = o; o = up256(o + oz.bytesF);
+  const C64Layout c6 = c64_layout(L.n, L.pmax);
+  L.c64M = o; o = up256(o + c6.bytesM);
+  L.c64A = o; o = up256(o + (dtype == GF_C64 ? c6.bytesA : 0));
+  L.c64B = o; o = up256(o + (dtype == GF_C64 ? c6.bytesB : 0));
   L.total = o;
   // the fill's Toeplitz table reuses the start of the workspace
   L.table = 0;
@@ -299,7 +302,7 @@ gf_status gf_select_topk(gf_handle* h, const gf_geom* geom, const gf_cand_spec* 
 
 gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, int32_t dtype, uint8_t* state,
                           const gf_cand_spec* spec, const int32_t* idx, int32_t* status, double* fom_out,
-                          void* ws, size_t ws_bytes, void* stream) {
+                          int32_t* applied, void* ws, size_t ws_bytes, void* stream) {
   if (!h) return GF_EINVAL;
   gf_status s = check_lams(h, probs, nlam, dtype);
   if (s) return s;
@@ -325,7 +328,7 @@ gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, i
     a.lam[l].bands = reinterpret_cast<gf::cplx*>(probs[l].bands);
   }
   cudaStream_t st = (cudaStream_t)stream;
-  gf::launch_update(a, L, reinterpret_cast<char*>(ws), state, *spec, idx, status, fom_out, st, &h->timer);
+  gf::launch_update(a, L, reinterpret_cast<char*>(ws), state, *spec, idx, status, fom_out, applied, st, &h->timer);
   for (int l = 0; l < nlam; ++l)
     gf::launch_bands(probs[l].geom, dtype, probs[l].G, probs[l].ldg, reinterpret_cast<gf::cplx*>(probs[l].bands), st);
   return cuda_check(h, "gf_apply_update launch");

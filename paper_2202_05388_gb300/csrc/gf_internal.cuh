@@ -82,6 +82,7 @@ struct WsLayout {
   size_t C0, S, panel_s;      // per wavelength, C0 (n x pmax), S (pmax x n), stride panel_s
   size_t sel;                 // selection scratch
   size_t ozA, ozE, ozB, ozF;  // tensor-core update: digit slices and scale exponents (wavelength-shared)
+  size_t c64M, c64A, c64B;    // complex64 tensor-core update: D A^{-1}, split-TF32 operand blocks
   size_t table;               // fill: Toeplitz table + monitor vector
   size_t total;
 };
@@ -92,6 +93,14 @@ struct OzLayout {
   size_t bytesA, bytesE, bytesB, bytesF;
 };
 OzLayout oz_layout(int64_t n);
+
+// Operand blocks of the complex64 tensor-core update (K = 2P real, P = p rounded up to 16).
+struct C64Layout {
+  int64_t P, K, nkc, nrt, nct;
+  size_t bytesA, bytesB, bytesM;
+};
+C64Layout c64_layout(int64_t n, int pmax);
+constexpr int kC64MaxP = 128;        // the complex64 tensor-core path takes p <= 128
 
 WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& spec);
 
@@ -165,8 +174,12 @@ bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, cons
                               uint8_t* ozB, int32_t* ozF, int32_t* status, int32_t* prof_p,
                               int sm_count, cudaStream_t st);
 
+bool c64_tc_make_map(float2* G, int64_t ldg, int64_t n, void* map128);
+void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64_t n, const WsLayout& L, char* ws,
+                               int lam, int32_t* status, int32_t* prof_p, int sm_count, cudaStream_t st);
+
 void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state,
                    const gf_cand_spec& spec, const int32_t* idx, int32_t* status, double* fom_out,
-                   cudaStream_t st, KernelTimer* timer);
+                   int32_t* applied, cudaStream_t st, KernelTimer* timer);
 
 }  // namespace gf

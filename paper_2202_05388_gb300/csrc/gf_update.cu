@@ -221,7 +221,7 @@ __global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __
 
 // ----------------------------------------------------------------------------- panels
 // Column j: R[:, j] = A^{-1} G[V, j] (Eq. 14) and S[:, j] = D R[:, j]; row j: C0[j, :] = G[j, V].
-__global__ void k_panels(UpdArgs a, WsLayout L, char* ws) {
+__global__ void k_panels(UpdArgs a, WsLayout L, char* ws, int want_S) {
   const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
   if (ctl->skip) return;
   const int p = ctl->nv;
@@ -237,6 +237,7 @@ __global__ void k_panels(UpdArgs a, WsLayout L, char* ws) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
       for (int u = 0; u < p; ++u) C0[j * L.pmax + u] = ldG(U.G, a.dtype, U.ldg, j, V[u]);
+      if (!want_S) continue;
       if (p <= kMaxPixelsPerCand) {
         cplx x[kMaxPixelsPerCand];
 #pragma unroll
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_rank_update_c64_ref(float2* __r
 
 // ----------------------------------------------------------------------------- field, state, FOM
 __global__ void k_finish(UpdArgs a, WsLayout L, char* ws, uint8_t* __restrict__ state,
-                         double* __restrict__ fom_out) {
+                         double* __restrict__ fom_out, int32_t* __restrict__ applied) {
   const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
   const int64_t n = L.n;
   const int64_t N = n - 1;
@@ -396,7 +397,10 @@ __global__ void k_finish(UpdArgs a, WsLayout L, char* ws, uint8_t* __restrict__ 
       if (p > 0) a.lam[l].E[i] = e;
       f += abs2(e);
     }
-    if (i == N) *fom_out = f;
+    if (i == N) {
+      *fom_out = f;
+      if (applied) *applied = skip ? 0 : ctl->ncand;
+    }
   }
   if (blockIdx.x == 0) {
     for (int t = threadIdx.x; t < p; t += blockDim.x) state[V[t]] ^= 1;
@@ -405,7 +409,7 @@ __global__ void k_finish(UpdArgs a, WsLayout L, char* ws, uint8_t* __restrict__ 
 
 void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state,
                    const gf_cand_spec& spec, const int32_t* idx, int32_t* status, double* fom_out,
-                   cudaStream_t st, KernelTimer* timer) {
+                   int32_t* applied, cudaStream_t st, KernelTimer* timer) {
   CapArgs ca;
   ca.u = a;
   ca.kind = spec.kind;
@@ -414,9 +418,16 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   ca.pmax = L.pmax;
   k_capacitance<<<1, 256, 0, st>>>(ca, L, ws, state, idx, status);
   const int64_t n = L.n;
+  // complex64 on the tensor cores: S is formed from an explicit D A^{-1} by an FP32 GEMM, so
+  // the panels kernel only gathers C0
+  struct Map128 { alignas(64) unsigned char b[128]; };
+  Map128 maps[kMaxLam];
+  bool c64tc = a.dtype == GF_C64 && a.algo == GF_UPDATE_TC && L.pmax <= kC64MaxP;
+  for (int l = 0; c64tc && l < a.nlam; ++l)
+    c64tc = c64_tc_make_map(reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, maps[l].b);
   {
     int64_t b = (n + 255) / 256;
-    k_panels<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(a, L, ws);
+    k_panels<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(a, L, ws, c64tc ? 0 : 1);
   }
   const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
   dim3 grid((unsigned)((n + kUpdThreads - 1) / kUpdThreads),
@@ -444,6 +455,9 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
       }
       if (a.algo != GF_UPDATE_TC || L.pmax > 4 || only_above == 0)
         k_rank_update_f64<<<grid, kUpdThreads, 0, st>>>(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl, only_above, prof_p);
+    } else if (c64tc) {
+      launch_rank_update_c64_tc(maps[l].b, reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, L, ws, l, status,
+                                prof_p, a.sm_count, st);
     } else {
       k_rank_update_c64_ref<<<grid, kUpdThreads, 0, st>>>(reinterpret_cast<float2*>(a.lam[l].G),
                                                           a.lam[l].ldg, n, L.pmax, C0, S, ctl, prof_p);
@@ -457,7 +471,7 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   }
   {
     int64_t b = (n + 255) / 256;
-    k_finish<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(a, L, ws, state, fom_out);
+    k_finish<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(a, L, ws, state, fom_out, applied);
   }
 }
 

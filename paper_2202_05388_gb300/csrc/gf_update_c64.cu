@@ -1,0 +1,484 @@
+// Mixed-precision rank-k p update of a complex64 G (the Woodbury form of Eqs. 10 and 14 for a
+// set V of up to 4k pixels accepted together):
+//
+//   G <- G + C0 S,   C0 = G[:, V],   S = D A^{-1} G[V, :],   A = I - G_VV D.
+//
+// The p x p capacitance matrix A is factorised in FP64 (k_capacitance); its inverse is formed
+// here by p parallel FP64 column solves and scaled by D.  S is an FP32 GEMM of that p x p
+// matrix with the p rows G[V, :], written directly as split-TF32 operand tiles.  The n x n
+// update runs on the tensor cores as one real GEMM in the 4M form (K = 2P, P = p rounded up
+// to 16) with three TF32 products per K-step (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM),
+// which keeps about 21 bits of each product.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "gf_internal.cuh"
+#include "gf_tc.cuh"
+
+namespace gf {
+
+constexpr int kC64M = 128;                 // rows per tile
+constexpr int kC64N = 128;                 // real columns per tile (64 complex)
+constexpr int kC64KC = 16;                 // real K per operand chunk
+constexpr int kC64Half = kC64M * kC64KC * 4;   // one hi or lo chunk of a 128-row operand: 8 KB
+constexpr int kC64Block = 2 * kC64Half;        // hi + lo: 16 KB (A and B blocks alike)
+constexpr int kC64NSO = 3;                 // operand stages (A block + B block each)
+constexpr int kC64NSG = 2;                 // G tile stages
+constexpr int kC64Box = kC64M * 128;       // TMA box: 128 rows x 128 B (16 complex64)
+constexpr int kC64GTile = 4 * kC64Box;     // 64 KB
+constexpr int kC64OpStage = 2 * kC64Block; // 32 KB
+constexpr int kC64BarOff = kC64NSO * kC64OpStage + kC64NSG * kC64GTile;   // 229376
+constexpr int kC64Smem = kC64BarOff + 256;
+constexpr int kC64EpiWarps = 16;
+constexpr int kC64Threads = 32 * (kC64EpiWarps + 4);   // + G producer, MMA, storer, operand producer
+constexpr int kC64TmemCols = 256;          // two accumulators of kC64N columns
+constexpr uint64_t kC64TimeoutNs = 2000000000ull;
+constexpr int kC64Group = 8;               // tile raster: groups of 8 row tiles (L2 reuse of operands)
+
+// element (r, k) of a 128 x 16 K-major, no-swizzle chunk: 8x16-byte core matrices, K stride
+// 128 B, row-group stride 512 B
+__host__ __device__ __forceinline__ int c64_off(int r, int k) {
+  return (r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);   // exactly representable in TF32
+  lo = x - hi;                                               // exact in FP32
+}
+
+// P = p rounded up to 16, so that each of the four u-quarters of k_c64_s_gemm is a multiple
+// of 4 and every K chunk holds whole groups of four.
+int64_t c64_padP(int p) { return (int64_t)((p + 15) / 16) * 16; }
+
+C64Layout c64_layout(int64_t n, int pmax) {
+  C64Layout o;
+  o.P = c64_padP(pmax);
+  o.K = 2 * o.P;
+  o.nkc = o.K / kC64KC;
+  o.nrt = (n + kC64M - 1) / kC64M;
+  o.nct = (2 * n + kC64N - 1) / kC64N;
+  o.bytesA = (size_t)o.nrt * o.nkc * kC64Block;
+  o.bytesB = (size_t)o.nct * o.nkc * kC64Block;
+  o.bytesM = (size_t)pmax * pmax * 8;
+  return o;
+}
+
+// ---- D A^{-1} (p x p, FP32) from the FP64 LU: one CTA per column --------------------------
+__global__ void k_c64_inverse(WsLayout L, char* ws, int lam, float2* __restrict__ Mout) {
+  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
+  if (ctl->skip) return;
+  const int p = ctl->nv;
+  const int c = blockIdx.x;
+  if (c >= p) return;
+  const cplx* A = reinterpret_cast<const cplx*>(ws + L.lu + lam * L.lu_s);
+  const int32_t* piv = reinterpret_cast<const int32_t*>(ws + L.piv + lam * L.piv_s);
+  const double* dchi = reinterpret_cast<const double*>(ws + L.dchi);
+  __shared__ cplx x[256];
+  const int t = threadIdx.x;
+  for (int r = t; r < p; r += blockDim.x) x[r] = mk(r == c ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  if (t == 0) {   // row interchanges in order
+    for (int q = 0; q < p; ++q) {
+      int r = piv[q];
+      if (r != q) { cplx tt = x[q]; x[q] = x[r]; x[r] = tt; }
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < p; ++q) {            // unit lower
+    const cplx xq = x[q];
+    for (int r = q + 1 + t; r < p; r += blockDim.x) x[r] = x[r] - A[r * p + q] * xq;
+    __syncthreads();
+  }
+  for (int q = p - 1; q >= 0; --q) {       // upper
+    if (t == 0) x[q] = cdiv(x[q], A[q * p + q]);
+    __syncthreads();
+    const cplx xq = x[q];
+    for (int r = t; r < q; r += blockDim.x) x[r] = x[r] - A[r * p + q] * xq;
+    __syncthreads();
+  }
+  // column c of A^{-1}; row u scaled by d_chi[u]
+  for (int u = t; u < p; u += blockDim.x)
+    Mout[u * p + c] = make_float2((float)(dchi[u] * x[u].re), (float)(dchi[u] * x[u].im));
+}
+
+// ---- S = (D A^{-1}) G[V, :] in FP32, written as split-TF32 B operand blocks ----------------
+// One CTA per 64 complex columns (one 128-real-column tile); thread (j, quarter of u range).
+__global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G, int64_t ldg, int64_t n,
+                                                    const float2* __restrict__ Mdai, const int32_t* __restrict__ V,
+                                                    const UpdCtl* __restrict__ ctl, int64_t P, int nkc,
+                                                    uint8_t* __restrict__ Bops) {
+  if (ctl->skip) return;
+  const int p = ctl->nv;
+  __shared__ float2 Ms[128 * 16];            // M[u][v0 .. v0+16)
+  const int t = threadIdx.x;
+  const int jl = t & 63, q = t >> 6;         // local complex column, u quarter
+  const int64_t ct = blockIdx.x;
+  const int64_t j = ct * 64 + jl;
+  const int uq = (int)(P / 4);               // u values per thread (P <= 128 -> <= 32)
+  float2 acc[32];
+#pragma unroll
+  for (int a = 0; a < 32; ++a) acc[a] = make_float2(0.f, 0.f);
+  for (int v0 = 0; v0 < p; v0 += 16) {
+    __syncthreads();
+    for (int e = t; e < 128 * 16; e += 256) {
+      int u = e >> 4, v = v0 + (e & 15);
+      Ms[e] = (u < p && v < p) ? Mdai[u * p + v] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int vv = 0; vv < 16 && v0 + vv < p; ++vv) {
+      const float2 r = j < n ? G[(int64_t)V[v0 + vv] * ldg + j] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a < 32; ++a) {
+        if (a < uq) {
+          const float2 m = Ms[(q * uq + a) * 16 + vv];
+          acc[a].x = fmaf(m.x, r.x, fmaf(-m.y, r.y, acc[a].x));
+          acc[a].y = fmaf(m.x, r.y, fmaf(m.y, r.x, acc[a].y));
+        }
+      }
+    }
+  }
+  // columns 2j (re) and 2j+1 (im) of B':  k < P: (Re S, Im S);  k >= P: (-Im S, Re S)
+  uint8_t* tile = Bops + ct * (int64_t)nkc * kC64Block;
+  const int c_re = 2 * jl, c_im = 2 * jl + 1;
+#pragma unroll
+  for (int a4 = 0; a4 < 32; a4 += 4) {
+    if (a4 >= uq) break;
+    const int u0 = q * uq + a4;               // 4 consecutive u (uq = P/4 is a multiple of 4)
+    float re[4], im[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      re[e] = acc[a4 + e].x;
+      im[e] = acc[a4 + e].y;
+    }
+    // u0 .. u0+3 lie in one 4-aligned group when uq is a multiple of 4
+    float hr[4], lr[4], hi_[4], li[4], hn[4], ln[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      tf32_split(re[e], hr[e], lr[e]);
+      tf32_split(im[e], hi_[e], li[e]);
+      tf32_split(-im[e], hn[e], ln[e]);
+    }
+    const int kA = u0, kB = (int)P + u0;     // K positions of the two halves
+    const int kcA = kA / kC64KC, kcB = kB / kC64KC;
+    uint8_t* blkA = tile + kcA * kC64Block;
+    uint8_t* blkB = tile + kcB * kC64Block;
+    const int oRa = c64_off(c_re, kA % kC64KC), oIa = c64_off(c_im, kA % kC64KC);
+    const int oRb = c64_off(c_re, kB % kC64KC), oIb = c64_off(c_im, kB % kC64KC);
+    *reinterpret_cast<float4*>(blkA + oRa) = make_float4(hr[0], hr[1], hr[2], hr[3]);
+    *reinterpret_cast<float4*>(blkA + kC64Half + oRa) = make_float4(lr[0], lr[1], lr[2], lr[3]);
+    *reinterpret_cast<float4*>(blkA + oIa) = make_float4(hi_[0], hi_[1], hi_[2], hi_[3]);
+    *reinterpret_cast<float4*>(blkA + kC64Half + oIa) = make_float4(li[0], li[1], li[2], li[3]);
+    *reinterpret_cast<float4*>(blkB + oRb) = make_float4(hn[0], hn[1], hn[2], hn[3]);
+    *reinterpret_cast<float4*>(blkB + kC64Half + oRb) = make_float4(ln[0], ln[1], ln[2], ln[3]);
+    *reinterpret_cast<float4*>(blkB + oIb) = make_float4(hr[0], hr[1], hr[2], hr[3]);
+    *reinterpret_cast<float4*>(blkB + kC64Half + oIb) = make_float4(lr[0], lr[1], lr[2], lr[3]);
+  }
+}
+
+// ---- A operand blocks from C0 (n x pmax FP64): row i -> [Re C0[i, :P), Im C0[i, :P)] ------
+__global__ void k_c64_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n, int64_t nrows_pad,
+                                const UpdCtl* __restrict__ ctl, int64_t P, int nkc, uint8_t* __restrict__ Aops) {
+  if (ctl->skip) return;
+  const int p = ctl->nv;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows_pad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint8_t* tile = Aops + (i / kC64M) * (int64_t)nkc * kC64Block;
+    const int r = (int)(i % kC64M);
+    for (int u0 = 0; u0 < P; u0 += 4) {
+      float re[4], im[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int u = u0 + e;
+        const cplx c = (i < n && u < p) ? C0[i * pmax + u] : mk(0.0, 0.0);
+        re[e] = (float)c.re;
+        im[e] = (float)c.im;
+      }
+      float hr[4], lr[4], hi_[4], li[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        tf32_split(re[e], hr[e], lr[e]);
+        tf32_split(im[e], hi_[e], li[e]);
+      }
+      const int kA = u0, kB = (int)P + u0;
+      uint8_t* blkA = tile + (kA / kC64KC) * kC64Block;
+      uint8_t* blkB = tile + (kB / kC64KC) * kC64Block;
+      const int oa = c64_off(r, kA % kC64KC), ob = c64_off(r, kB % kC64KC);
+      *reinterpret_cast<float4*>(blkA + oa) = make_float4(hr[0], hr[1], hr[2], hr[3]);
+      *reinterpret_cast<float4*>(blkA + kC64Half + oa) = make_float4(lr[0], lr[1], lr[2], lr[3]);
+      *reinterpret_cast<float4*>(blkB + ob) = make_float4(hi_[0], hi_[1], hi_[2], hi_[3]);
+      *reinterpret_cast<float4*>(blkB + kC64Half + ob) = make_float4(li[0], li[1], li[2], li[3]);
+    }
+  }
+}
+
+// ---- the tensor-core update ------------------------------------------------------------------
+// Persistent, warp-specialised; tiles (128 rows x 64 complex columns) in a grouped raster order,
+// tile t handled by CTA t mod gridDim (so the CTAs work on neighbouring tiles and share the
+// operand blocks through L2).
+//   warps 0..15  epilogue: TMEM accumulator + G tile (shared memory) -> G tile
+//   warp 16      G producer (TMA, 4 boxes per tile)     warp 17  MMA issuer
+//   warp 18      storer (TMA stores)                     warp 19  operand producer (bulk copies)
+struct C64Bars {
+  uint64_t ofull[kC64NSO], oempty[kC64NSO];
+  uint64_t gfull[kC64NSG], gempty[kC64NSG], ebar[kC64NSG];
+  uint64_t tfull[2], tempty[2];
+  uint32_t tslot;
+  int abort;
+};
+
+__device__ __forceinline__ void c64_tile_coords(int64_t t, int64_t nrt, int64_t nct, int64_t& rt, int64_t& ct) {
+  const int64_t per_group = (int64_t)kC64Group * nct;
+  const int64_t g = t / per_group;
+  const int64_t rem = t - g * per_group;
+  const int64_t rows_in_group = (nrt - g * kC64Group) < kC64Group ? (nrt - g * kC64Group) : kC64Group;
+  rt = g * kC64Group + rem % rows_in_group;
+  ct = rem / rows_in_group;
+}
+
+__global__ void __launch_bounds__(kC64Threads, 1)
+k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_t nrt, int64_t nct, int nkc,
+                     const uint8_t* __restrict__ Aops, const uint8_t* __restrict__ Bops,
+                     const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int p = ctl->skip ? 0 : ctl->nv;
+  if (prof_p && blockIdx.x == 0 && threadIdx.x == 0 && p > 0) *prof_p = p;
+  if (p <= 0) return;
+  C64Bars* bars = reinterpret_cast<C64Bars*>(smem + kC64BarOff);
+  uint8_t* ops = smem;                                        // kC64NSO x (A block, B block)
+  uint8_t* gts = smem + kC64NSO * kC64OpStage;                // kC64NSG x G tile
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  volatile int* abort = &bars->abort;
+  constexpr int kWarpGProd = kC64EpiWarps, kWarpMma = kC64EpiWarps + 1, kWarpStore = kC64EpiWarps + 2,
+                kWarpOProd = kC64EpiWarps + 3;
+
+  if (warp == kWarpMma) {
+    tc::tmem_alloc(&bars->tslot, kC64TmemCols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int q = 0; q < kC64NSO; ++q) {
+      tc::mbar_init(&bars->ofull[q], 1);
+      tc::mbar_init(&bars->oempty[q], 1);
+    }
+    for (int q = 0; q < kC64NSG; ++q) {
+      tc::mbar_init(&bars->gfull[q], 1);
+      tc::mbar_init(&bars->gempty[q], 1);
+      tc::mbar_init(&bars->ebar[q], 32 * kC64EpiWarps);
+    }
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&bars->tfull[q], 1);
+      tc::mbar_init(&bars->tempty[q], kC64EpiWarps);
+    }
+    bars->abort = 0;
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = bars->tslot;
+  const int64_t T = nrt * nct;
+
+  if (warp == kWarpGProd) {
+    if (lane == 0) {
+      int64_t k = 0;
+      for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++k) {
+        int64_t rt, ct;
+        c64_tile_coords(t, nrt, nct, rt, ct);
+        const int s = (int)(k % kC64NSG);
+        if (k >= kC64NSG && !tc::mbar_wait_or_abort(&bars->gempty[s], (uint32_t)((k / kC64NSG - 1) & 1), abort, kC64TimeoutNs)) break;
+        const int x0 = (int)(ct * kC64N), y = (int)(rt * kC64M);     // x in floats
+        int nbox = 0;
+        for (int b = 0; b < 4; ++b) nbox += (x0 + 32 * b < 2 * n) ? 1 : 0;
+        tc::mbar_arrive_expect_tx(&bars->gfull[s], (uint32_t)(nbox * kC64Box));
+        uint8_t* gt = gts + s * kC64GTile;
+        for (int b = 0; b < nbox; ++b) tc::tma_load_2d(gt + b * kC64Box, &tmapG, x0 + 32 * b, y, &bars->gfull[s]);
+      }
+    }
+    __syncwarp();
+  } else if (warp == kWarpOProd) {
+    if (lane == 0) {
+      int64_t c = 0;
+      for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        int64_t rt, ct;
+        c64_tile_coords(t, nrt, nct, rt, ct);
+        bool ok = true;
+        for (int kc = 0; kc < nkc; ++kc, ++c) {
+          const int s = (int)(c % kC64NSO);
+          if (c >= kC64NSO && !tc::mbar_wait_or_abort(&bars->oempty[s], (uint32_t)((c / kC64NSO - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          uint8_t* st = ops + s * kC64OpStage;
+          tc::mbar_arrive_expect_tx(&bars->ofull[s], (uint32_t)kC64OpStage);
+          tc::bulk_g2s(st, Aops + (rt * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->ofull[s]);
+          tc::bulk_g2s(st + kC64Block, Bops + (ct * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->ofull[s]);
+        }
+        if (!ok) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp == kWarpMma) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_tf32(kC64M, kC64N);
+      int64_t k = 0, c = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < T && ok; t += gridDim.x, ++k) {
+        const int b = (int)(k & 1);
+        if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[b], (uint32_t)((k / 2 - 1) & 1), abort, kC64TimeoutNs)) break;
+        tc::fence_after_sync();
+        const uint32_t d = tbase + (uint32_t)(b * kC64N);
+        for (int kc = 0; kc < nkc; ++kc, ++c) {
+          const int s = (int)(c % kC64NSO);
+          if (!tc::mbar_wait_or_abort(&bars->ofull[s], (uint32_t)((c / kC64NSO) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          tc::fence_after_sync();
+          const uint32_t sA = tc::smem_u32(ops + s * kC64OpStage);
+          const uint32_t sB = sA + kC64Block;
+#pragma unroll
+          for (int ks = 0; ks < kC64KC / 8; ++ks) {
+            const uint32_t off = ks * 256;     // two K core matrices per K = 8 step
+            const uint64_t ah = tc::smem_desc(sA + off, 128, 512), al = tc::smem_desc(sA + kC64Half + off, 128, 512);
+            const uint64_t bh = tc::smem_desc(sB + off, 128, 512), bl = tc::smem_desc(sB + kC64Half + off, 128, 512);
+            tc::mma_tf32(d, ah, bh, idesc, (kc == 0 && ks == 0) ? 0u : 1u);
+            tc::mma_tf32(d, ah, bl, idesc, 1u);
+            tc::mma_tf32(d, al, bh, idesc, 1u);
+          }
+          tc::mma_commit(&bars->oempty[s]);
+        }
+        if (ok) tc::mma_commit(&bars->tfull[b]);
+      }
+    }
+    __syncwarp();
+  } else if (warp < kC64EpiWarps) {
+    const int q = warp & 3, h = warp >> 2;     // TMEM lane quarter, column quarter (32 real columns)
+    const int r = q * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    int64_t k = 0;
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++k) {
+      const int b = (int)(k & 1);
+      const int s = (int)(k % kC64NSG);
+      if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kC64TimeoutNs)) break;
+      if (!tc::mbar_wait_or_abort(&bars->gfull[s], (uint32_t)((k / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
+      tc::fence_after_sync();
+      float acc[32];
+      {
+        float a0[16], a1[16];
+        tc::tmem_ld16(tbase + lane_addr + (uint32_t)(b * kC64N + h * 32), a0);
+        tc::tmem_ld16(tbase + lane_addr + (uint32_t)(b * kC64N + h * 32 + 16), a1);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          acc[e] = a0[e];
+          acc[16 + e] = a1[e];
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
+      // box h holds real columns 32h .. 32h+31 of the tile = 8 chunks of 16 B (128B swizzle)
+      uint8_t* row = gts + s * kC64GTile + h * kC64Box + r * 128;
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch) {
+        float4* gp = reinterpret_cast<float4*>(row + ((ch ^ (r & 7)) << 4));
+        float4 g = *gp;
+        g.x += acc[4 * ch + 0];
+        g.y += acc[4 * ch + 1];
+        g.z += acc[4 * ch + 2];
+        g.w += acc[4 * ch + 3];
+        *gp = g;
+      }
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(&bars->ebar[s]);
+    }
+  }
+  if (warp == kWarpStore) {
+    if (lane == 0) {
+      int64_t k = 0;
+      for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++k) {
+        int64_t rt, ct;
+        c64_tile_coords(t, nrt, nct, rt, ct);
+        const int s = (int)(k % kC64NSG);
+        if (!tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)((k / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
+        const int x0 = (int)(ct * kC64N), y = (int)(rt * kC64M);
+        uint8_t* gt = gts + s * kC64GTile;
+        for (int b = 0; b < 4; ++b)
+          if (x0 + 32 * b < 2 * n) tc::tma_store_2d(&tmapG, x0 + 32 * b, y, gt + b * kC64Box);
+        tc::bulk_commit();
+        tc::bulk_wait_read0();
+        tc::mbar_arrive(&bars->gempty[s]);
+      }
+      tc::bulk_wait0();
+    }
+    __syncwarp();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid == 0 && bars->abort) atomicExch(status, GF_ETIMEOUT);
+  tc::fence_after_sync();
+  if (warp == kWarpMma) tc::tmem_dealloc(tbase, kC64TmemCols);
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 c64_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// complex64 G as a 2-D tensor of floats: 2n columns by n rows, row stride 8 ldg bytes; boxes of
+// 32 floats (128 B) x 128 rows, 128-byte swizzle.
+static bool make_tmap_G64(CUtensorMap* m, float2* G, int64_t ldg, int64_t n) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = c64_encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)(2 * n), (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)(8 * ldg)};
+  cuuint32_t box[2] = {32, (cuuint32_t)kC64M};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)G, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool c64_tc_make_map(float2* G, int64_t ldg, int64_t n, void* map128) {
+  return make_tmap_G64(reinterpret_cast<CUtensorMap*>(map128), G, ldg, n);
+}
+
+void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64_t n, const WsLayout& L, char* ws,
+                               int lam, int32_t* status, int32_t* prof_p, int sm_count, cudaStream_t st) {
+  const CUtensorMap& tmap = *reinterpret_cast<const CUtensorMap*>(map128);
+  const C64Layout o = c64_layout(n, L.pmax);
+  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
+  float2* Mdai = reinterpret_cast<float2*>(ws + L.c64M);
+  uint8_t* Aops = reinterpret_cast<uint8_t*>(ws + L.c64A);
+  uint8_t* Bops = reinterpret_cast<uint8_t*>(ws + L.c64B);
+  const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + lam * L.panel_s);
+  k_c64_inverse<<<L.pmax, 128, 0, st>>>(L, ws, lam, Mdai);
+  k_c64_s_gemm<<<(unsigned)o.nct, 256, 0, st>>>(G, ldg, n, Mdai, reinterpret_cast<const int32_t*>(ws + L.V), ctl, o.P,
+                                                 (int)o.nkc, Bops);
+  {
+    int64_t rows = o.nrt * kC64M;
+    int64_t b = (rows + 127) / 128;
+    k_c64_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, L.pmax, n, rows, ctl, o.P, (int)o.nkc, Aops);
+  }
+  {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+      cudaFuncSetAttribute(k_rank_update_c64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
+      if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+  }
+  const int64_t tiles = o.nrt * o.nct;
+  const int grid = (int)(tiles < sm_count ? tiles : sm_count);
+  k_rank_update_c64_tc<<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.nct, (int)o.nkc, Aops, Bops, ctl,
+                                                            status, prof_p);
+}
+
+}  // namespace gf

@@ -85,7 +85,7 @@ def load(path: str = LIB_PATH):
             "gf_select_topk": (C.c_int32, [P, C.POINTER(gf_geom), C.POINTER(gf_cand_spec), P,
                                            C.c_int64, P, P, P, P, C.c_size_t, P]),
             "gf_apply_update": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, C.c_int32, P,
-                                            C.POINTER(gf_cand_spec), P, P, P, P, C.c_size_t, P]),
+                                            C.POINTER(gf_cand_spec), P, P, P, P, P, C.c_size_t, P]),
             "gf_profile_begin": (C.c_int32, [P, C.c_int32]),
             "gf_set_update_algo": (C.c_int32, [P, C.c_int32]),
             "gf_fill_g0_static": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, P]),
@@ -188,12 +188,12 @@ class Handle:
                                             int(ws_bytes), _stream(stream)))
 
     def gf_apply_update(self, probs, dtype, state, spec, idx, status, fom_out, ws, ws_bytes,
-                        stream=None):
+                        stream=None, applied=None):
         arr = (gf_problem * len(probs))(*probs)
         s = spec_struct(spec)
         self._check(self.lib.gf_apply_update(self.h, arr, len(probs), int(dtype), _ptr(state),
                                              C.byref(s), _ptr(idx), _ptr(status), _ptr(fom_out),
-                                             _ptr(ws), int(ws_bytes), _stream(stream)))
+                                             _ptr(applied), _ptr(ws), int(ws_bytes), _stream(stream)))
 
     def gf_set_update_algo(self, algo: int):
         self._check(self.lib.gf_set_update_algo(self.h, int(algo)))

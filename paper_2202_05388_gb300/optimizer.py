@@ -53,6 +53,7 @@ class GreedyOptimizer:
         self.val = torch.empty(k, dtype=torch.float64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.fom = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.applied = torch.zeros(1, dtype=torch.int32, device=dev)
         self.ws_bytes = self.h.gf_workspace_size(g, nlam, self.dtype, spec)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.probs = [B.problem_struct(gg, self.G[l], self.ldg, self.E[l], self.bands[l])
@@ -77,7 +78,7 @@ class GreedyOptimizer:
 
     def update(self):
         self.h.gf_apply_update(self.probs, self.dtype, self.state, self.spec, self.idx, self.status,
-                               self.fom, self.ws, self.ws_bytes, self._st())
+                               self.fom, self.ws, self.ws_bytes, self._st(), applied=self.applied)
 
     def step(self):
         self.evaluate()
@@ -95,7 +96,7 @@ class GreedyOptimizer:
         self.idx[:k].copy_(idx.to(self.device))
         self.status.zero_()
         self.h.gf_apply_update(self.probs, self.dtype, self.state, spec, self.idx, self.status,
-                               self.fom, self.ws, self.ws_bytes, self._st())
+                               self.fom, self.ws, self.ws_bytes, self._st(), applied=self.applied)
 
     # ---- host readback
     def read_step(self) -> StepResult:

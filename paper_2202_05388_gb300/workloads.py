@@ -111,13 +111,25 @@ def brush_64() -> Workload:
 
 def brush_320_topk() -> Workload:
     """320x320 pixels, complex64 G (about 84 GB), top-32 brushes with a 3-pixel
-    exclusion radius accepted per step as one rank-128 update, 1500 steps."""
+    exclusion radius accepted per step as one rank-128 update, 1500 steps.  The focus is 5
+    lambda past the far edge (NA 0.85): 5 lambda beyond the centre would lie inside this
+    16-lambda-tall region."""
     nx = ny = 320
     dx = 0.05
-    mx, my = _centre_line_monitor(nx, ny, dx, beyond_centre=5.0)
+    mx, my = _centre_line_monitor(nx, ny, dx, beyond_edge=5.0)
     g = Geometry(nx, ny, dx, 1.0, mx, my)
     return Workload("brush_320x320_top32_c64", (g,),
                     CandidateSpec(KIND_BRUSH2, DIR_FILL | DIR_CLEAR, 32, 3), 1500, "c64")
+
+
+def brush_128_topk() -> Workload:
+    """128x128 member of the top-32 complex64 family (G = 2.1 GB), for profiling."""
+    nx = ny = 128
+    dx = 0.05
+    mx, my = _centre_line_monitor(nx, ny, dx, beyond_edge=5.0)
+    g = Geometry(nx, ny, dx, 1.0, mx, my)
+    return Workload("brush_128x128_top32_c64", (g,),
+                    CandidateSpec(KIND_BRUSH2, DIR_FILL | DIR_CLEAR, 32, 3), 200, "c64")
 
 
 def multi_lambda_512x64() -> Workload:

@@ -1,0 +1,98 @@
+"""Mixed precision (complex64 G, rank-k p Woodbury update on the tensor cores with split TF32,
+FP64 capacitance solve, E and FOM) against the FP64 oracle, run lock-step from the oracle's
+choices as the error statement for the precision pattern, and against the complex64 update
+done in FP64 arithmetic."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import gf_oracle as O
+from paper_2202_05388_gb300 import build as BLD
+from paper_2202_05388_gb300 import gfopt as B
+from paper_2202_05388_gb300 import workloads as W
+from paper_2202_05388_gb300.optimizer import GreedyOptimizer
+
+from gpu_parity import gpu_E, gpu_G, reach_state, rel_err
+
+# complex64 storage rounds every entry to 2^-24 relative; the split-TF32 products keep ~21 bits
+C64_TOL_G = 2e-5
+C64_TOL_E = 2e-5
+C64_TOL_DFOM = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BLD.build()
+
+
+def _force(opt, ids, k):
+    fixed = torch.full((k,), -1, dtype=torch.int32)
+    fixed[:len(ids)] = torch.tensor(ids, dtype=torch.int32)
+    opt.idx.copy_(fixed.to(opt.idx.device))
+    opt.status.zero_()
+
+
+@pytest.mark.parametrize("nx,ny,k,seed,steps", [(20, 18, 4, 51, 4), (33, 29, 16, 52, 3), (12, 10, 1, 53, 6)])
+def test_c64_lockstep_error_vs_fp64_oracle(nx, ny, k, seed, steps):
+    wl = W.small(nx, ny, kind=W.KIND_BRUSH2, dir_mask=3, k=k, excl_radius=3, steps=steps, dtype="c64")
+    g = wl.geoms[0]
+    orc = O.OracleProblem(wl.geoms, wl.spec)
+    opt = GreedyOptimizer(wl.geoms, wl.spec, dtype="c64")
+    opt.fill()
+    reach_state(opt, orc, W.random_state(g.N, seed=seed, fill=0.3))
+    torch.cuda.synchronize()
+    assert rel_err(gpu_G(opt), orc.Gs[0]) <= C64_TOL_G
+    done = 0
+    for t in range(steps):
+        opt.evaluate()
+        d_orc = orc.evaluate()
+        d_gpu = opt.dfom.cpu().numpy()
+        fin = np.isfinite(d_orc)
+        assert np.array_equal(fin, np.isfinite(d_gpu))
+        scale = max(1.0, float(np.max(np.abs(d_orc[fin]))))
+        assert np.max(np.abs(d_gpu[fin] - d_orc[fin])) <= C64_TOL_DFOM * scale
+        ids = orc.choose(d_orc)
+        if not ids:
+            break
+        _force(opt, ids, max(1, k))
+        opt.update()
+        applied = orc.accept(ids)
+        torch.cuda.synchronize()
+        assert int(opt.status.cpu()[0]) == B.GF_OK
+        eG = rel_err(gpu_G(opt), orc.Gs[0])
+        eE = rel_err(gpu_E(opt), orc.Es[0])
+        assert eG <= C64_TOL_G, (t, eG)
+        assert eE <= C64_TOL_E, (t, eE)
+        assert abs(float(opt.fom.cpu()[0]) - orc.fom()) <= C64_TOL_E * orc.fom()
+        assert np.array_equal(opt.state.cpu().numpy(), orc.state), "joint/fallback decision differs"
+        done += 1
+    assert done >= 1
+
+
+def test_c64_tensor_core_update_matches_fp64_arithmetic_update():
+    wl = W.small(40, 30, kind=W.KIND_BRUSH2, dir_mask=3, k=8, excl_radius=3, dtype="c64")
+    g = wl.geoms[0]
+    a = GreedyOptimizer(wl.geoms, wl.spec, dtype="c64")
+    b = GreedyOptimizer(wl.geoms, wl.spec, dtype="c64")
+    b.h.gf_set_update_algo(B.GF_UPDATE_DFMA)          # complex64 storage, FP64 arithmetic
+    a.fill()
+    b.fill()
+    single = W.CandidateSpec(W.KIND_SINGLE, 3, 1)
+    for j in np.flatnonzero(W.random_state(g.N, seed=61, fill=0.3))[:60]:
+        a.force([int(j)], single)
+        b.force([int(j)], single)
+    for t in range(3):
+        a.evaluate()
+        a.select()
+        b.idx.copy_(a.idx)
+        b.status.copy_(a.status)
+        a.update()
+        b.update()
+        torch.cuda.synchronize()
+        assert rel_err(gpu_G(a), gpu_G(b)) <= 5e-6, t
+        assert rel_err(gpu_E(a), gpu_E(b)) <= 5e-6, t
