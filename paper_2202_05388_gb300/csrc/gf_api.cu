@@ -141,6 +141,7 @@ WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& sp
   L.ctl = o; o = up256(o + sizeof(UpdCtl));
   L.V = o; o = up256(o + sizeof(int32_t) * L.pmax);
   L.dchi = o; o = up256(o + sizeof(double) * L.pmax);
+  L.sel = o; o = up256(o + topk_scratch_bytes());   // selection scratch: offset independent of nlam, dtype
   L.lu_s = up256(sizeof(cplx) * (size_t)L.pmax * L.pmax);
   L.piv_s = up256(sizeof(int32_t) * L.pmax);
   L.yd_s = up256(sizeof(cplx) * L.pmax);
@@ -150,7 +151,6 @@ WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& sp
   L.panel_s = up256(sizeof(cplx) * (size_t)L.n * L.pmax);
   L.C0 = o; o += L.panel_s * nlam;
   L.S = o; o += L.panel_s * nlam;
-  L.sel = o; o = up256(o + 4096);
   const OzLayout oz = oz_layout(L.n);
   L.ozA = o; o = up256(o + oz.bytesA);
   L.ozE = o; o = up256(o + oz.bytesE);
@@ -160,6 +160,8 @@ WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& sp
   L.c64M = o; o = up256(o + c6.bytesM);
   L.c64A = o; o = up256(o + (dtype == GF_C64 ? c6.bytesA : 0));
   L.c64B = o; o = up256(o + (dtype == GF_C64 ? c6.bytesB : 0));
+  L.c64E = o; o = up256(o + (dtype == GF_C64 ? c6.bytesE : 0));
+  L.c64F = o; o = up256(o + (dtype == GF_C64 ? c6.bytesF : 0));
   L.total = o;
   // the fill's Toeplitz table reuses the start of the workspace
   L.table = 0;
@@ -294,9 +296,14 @@ gf_status gf_select_topk(gf_handle* h, const gf_geom* geom, const gf_cand_spec* 
     return fail(h, GF_EINVAL, "ncand %lld does not match the candidate family (%lld)", (long long)ncand,
                 (long long)gf_num_candidates(geom, spec));
   if (!dfom || !idx || !val || !status) return fail(h, GF_EINVAL, "dfom, idx, val and status must be non-NULL");
-  (void)ws_bytes;
   if ((s = bind_device(h))) return s;
-  gf::launch_select(*geom, *spec, dfom, ncand, idx, val, status, ws, (cudaStream_t)stream);
+  // the pooled top-k uses the workspace's selection area when a workspace is given
+  void* sel = nullptr;
+  if (ws && spec->k > 1) {
+    const gf::WsLayout L = gf::ws_layout(*geom, 1, GF_C128, *spec);
+    if (((uintptr_t)ws & 255u) == 0 && ws_bytes >= L.sel + gf::topk_scratch_bytes()) sel = (char*)ws + L.sel;
+  }
+  gf::launch_select(*geom, *spec, dfom, ncand, idx, val, status, sel, (cudaStream_t)stream);
   return cuda_check(h, "gf_select_topk launch");
 }
 

@@ -82,7 +82,8 @@ struct WsLayout {
   size_t C0, S, panel_s;      // per wavelength, C0 (n x pmax), S (pmax x n), stride panel_s
   size_t sel;                 // selection scratch
   size_t ozA, ozE, ozB, ozF;  // tensor-core update: digit slices and scale exponents (wavelength-shared)
-  size_t c64M, c64A, c64B;    // complex64 tensor-core update: D A^{-1}, split-TF32 operand blocks
+  size_t c64M, c64A, c64B;    // complex64 tensor-core update: D A^{-1}, split-FP16 operand blocks
+  size_t c64E, c64F;          //   and their row / column scale exponents
   size_t table;               // fill: Toeplitz table + monitor vector
   size_t total;
 };
@@ -97,7 +98,7 @@ OzLayout oz_layout(int64_t n);
 // Operand blocks of the complex64 tensor-core update (K = 2P real, P = p rounded up to 16).
 struct C64Layout {
   int64_t P, K, nkc, nrt, nct;
-  size_t bytesA, bytesB, bytesM;
+  size_t bytesA, bytesB, bytesM, bytesE, bytesF;
 };
 C64Layout c64_layout(int64_t n, int pmax);
 constexpr int kC64MaxP = 128;        // the complex64 tensor-core path takes p <= 128
@@ -135,6 +136,7 @@ struct EvalArgs {
 void launch_eval(const EvalArgs& a, const uint8_t* state, const gf_cand_spec& spec, double* dfom,
                  cudaStream_t st);
 
+size_t topk_scratch_bytes();
 void launch_select(const gf_geom& g, const gf_cand_spec& spec, const double* dfom, int64_t ncand,
                    int32_t* idx, double* val, int32_t* status, void* ws, cudaStream_t st);
 

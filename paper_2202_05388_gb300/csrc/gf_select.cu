@@ -129,14 +129,117 @@ __global__ void __launch_bounds__(kSelThreads) k_select_topk(const double* __res
   }
 }
 
+// ---- multi-CTA top-k with exclusion: k passes; in pass t every CTA finds its best improving
+// candidate that conflicts with none of the t already taken, and the last CTA to finish (atomic
+// ticket after a memory fence -- no CTA waits for another) reduces the per-CTA results and
+// appends the winner.  Exactly the sorted-scan result.
+struct TopkScratch {
+  int32_t counter;      // CTAs finished in the current pass
+  int32_t ntaken;
+  int32_t done;         // no improving, non-conflicting candidate is left
+  int32_t pad;
+  int32_t ax[256], ay[256];
+};
+constexpr int kTopkBlocks = 148;
+constexpr int kTopkThreads = 256;
+
+__global__ void __launch_bounds__(kTopkThreads) k_topk_pass(const double* __restrict__ dfom, int64_t ncand,
+                                                           int kind, int nx, int ny, int excl, int pass,
+                                                           TopkScratch* sc, double* part_v, int64_t* part_i,
+                                                           int32_t* idx, double* val) {
+  if (sc->done) return;
+  __shared__ int tax[256], tay[256];
+  __shared__ bool s_last;
+  const int nt = pass;
+  for (int q = threadIdx.x; q < nt; q += blockDim.x) { tax[q] = sc->ax[q]; tay[q] = sc->ay[q]; }
+  __syncthreads();
+  const int64_t P = (int64_t)(nx - 1) * (ny - 1);
+  double bv = -INFINITY;
+  int64_t bid = INT64_MAX;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncand; c += (int64_t)gridDim.x * blockDim.x) {
+    const double v = dfom[c];
+    if (!(v > 0.0) || !better(v, c, bv, bid)) continue;
+    int ax, ay;
+    cand_anchor(c, kind, nx, P, ax, ay);
+    bool clash = false;
+    for (int q = 0; q < nt && !clash; ++q) clash = max(abs(ax - tax[q]), abs(ay - tay[q])) <= excl;
+    if (!clash) { bv = v; bid = c; }
+  }
+  block_best(bv, bid);
+  if (threadIdx.x == 0) {
+    part_v[blockIdx.x] = bv;
+    part_i[blockIdx.x] = bid;
+    __threadfence();
+    const int ticket = atomicAdd(&sc->counter, 1);
+    s_last = ticket == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double v = -INFINITY;
+  int64_t id = INT64_MAX;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double pv = ((volatile double*)part_v)[b];
+    const int64_t pi = ((volatile int64_t*)part_i)[b];
+    if (better(pv, pi, v, id)) { v = pv; id = pi; }
+  }
+  block_best(v, id);
+  if (threadIdx.x == 0) {
+    if (v > 0.0) {
+      int ax, ay;
+      cand_anchor(id, kind, nx, P, ax, ay);
+      sc->ax[nt] = ax;
+      sc->ay[nt] = ay;
+      idx[nt] = (int32_t)id;
+      val[nt] = v;
+      sc->ntaken = nt + 1;
+    } else {
+      sc->done = 1;
+    }
+    sc->counter = 0;
+  }
+}
+
+__global__ void k_topk_begin(TopkScratch* sc) {
+  sc->counter = 0;
+  sc->ntaken = 0;
+  sc->done = 0;
+}
+
+__global__ void k_topk_end(const TopkScratch* sc, int k, int32_t* idx, double* val, int32_t* status) {
+  const int nt = sc->ntaken;
+  for (int t = nt + threadIdx.x; t < k; t += blockDim.x) {
+    idx[t] = -1;
+    val[t] = -INFINITY;
+  }
+  if (threadIdx.x == 0) *status = nt > 0 ? GF_OK : GF_ENOIMPROVE;
+}
+
+size_t topk_scratch_bytes() {
+  return sizeof(TopkScratch) + kTopkBlocks * (sizeof(double) + sizeof(int64_t)) + 64;
+}
+
 void launch_select(const gf_geom& g, const gf_cand_spec& spec, const double* dfom, int64_t ncand,
                    int32_t* idx, double* val, int32_t* status, void* ws, cudaStream_t st) {
-  (void)ws;
-  if (spec.k <= 1)
+  if (spec.k <= 1) {
     k_select_best<<<1, kSelThreads, 0, st>>>(dfom, ncand, spec.tie_rel, idx, val, status);
-  else
-    k_select_topk<<<1, kSelThreads, 0, st>>>(dfom, ncand, spec.kind, g.nx, g.ny, spec.k,
-                                             spec.excl_radius, idx, val, status);
+    return;
+  }
+  if (ws == nullptr) {
+    k_select_topk<<<1, kSelThreads, 0, st>>>(dfom, ncand, spec.kind, g.nx, g.ny, spec.k, spec.excl_radius, idx, val,
+                                             status);
+    return;
+  }
+  TopkScratch* sc = reinterpret_cast<TopkScratch*>(ws);
+  double* part_v = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + ((sizeof(TopkScratch) + 63) & ~size_t(63)));
+  int64_t* part_i = reinterpret_cast<int64_t*>(part_v + kTopkBlocks);
+  int64_t blocks = (ncand + kTopkThreads - 1) / kTopkThreads;
+  if (blocks > kTopkBlocks) blocks = kTopkBlocks;
+  k_topk_begin<<<1, 1, 0, st>>>(sc);
+  for (int t = 0; t < spec.k; ++t)
+    k_topk_pass<<<(unsigned)blocks, kTopkThreads, 0, st>>>(dfom, ncand, spec.kind, g.nx, g.ny, spec.excl_radius, t, sc,
+                                                           part_v, part_i, idx, val);
+  k_topk_end<<<1, 256, 0, st>>>(sc, spec.k, idx, val, status);
 }
 
 }  // namespace gf

@@ -130,19 +130,36 @@ __global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __
       __syncthreads();
       const double thresh = kSingularRel * s_red[0];
       __syncthreads();
-      // LU with partial pivoting (row-major, in place; L below the diagonal, unit diagonal)
+      // LU with partial pivoting (row-major, in place; L below the diagonal, unit diagonal).
+      // Pivot: block-wide search for the largest modulus, lowest row on ties; multipliers per
+      // row; trailing update with a warp per row and lanes along the (coalesced) columns.
       __shared__ int s_piv;
       __shared__ int s_bad;
+      __shared__ double s_bv[32];
+      __shared__ int s_br[32];
+      __shared__ cplx s_f[1024];
       if (tid == 0) s_bad = 0;
+      const int nw = (int)(blockDim.x >> 5), lane = tid & 31, wid = tid >> 5;
       for (int c = 0; c < p; ++c) {
+        double bv = -1.0;
+        int br = 0x7fffffff;
+        for (int rr = c + tid; rr < p; rr += blockDim.x) {
+          const double m = cabs1(A[rr * p + c]);
+          if (m > bv) { bv = m; br = rr; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+          const int orr = __shfl_down_sync(0xffffffffu, br, o);
+          if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+        }
+        if (lane == 0) { s_bv[wid] = bv; s_br[wid] = br; }
+        __syncthreads();
         if (tid == 0) {
-          int r = c;
-          double best = cabs1(A[c * p + c]);
-          for (int rr = c + 1; rr < p; ++rr) {
-            double m = cabs1(A[rr * p + c]);
-            if (m > best) { best = m; r = rr; }
-          }
-          if (!(best >= thresh) || !(best > 0.0)) s_bad = 1;
+          double b = s_bv[0];
+          int r = s_br[0];
+          for (int w = 1; w < nw; ++w)
+            if (s_bv[w] > b || (s_bv[w] == b && s_br[w] < r)) { b = s_bv[w]; r = s_br[w]; }
+          if (!(b >= thresh) || !(b > 0.0)) s_bad = 1;
           s_piv = r;
           piv[c] = r;
         }
@@ -159,11 +176,17 @@ __global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __
         }
         __syncthreads();
         const cplx pv = A[c * p + c];
+        const cplx yc = y[c];
         for (int rr = c + 1 + tid; rr < p; rr += blockDim.x) {
-          cplx f = cdiv(A[rr * p + c], pv);
-          for (int v = c + 1; v < p; ++v) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
+          const cplx f = cdiv(A[rr * p + c], pv);
+          s_f[rr] = f;
           A[rr * p + c] = f;
-          y[rr] = y[rr] - f * y[c];
+          y[rr] = y[rr] - f * yc;
+        }
+        __syncthreads();
+        for (int rr = c + 1 + wid; rr < p; rr += nw) {
+          const cplx f = s_f[rr];
+          for (int v = c + 1 + lane; v < p; v += 32) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
         }
         __syncthreads();
       }

@@ -5,11 +5,15 @@
 //
 // The p x p capacitance matrix A is factorised in FP64 (k_capacitance); its inverse is formed
 // here by p parallel FP64 column solves and scaled by D.  S is an FP32 GEMM of that p x p
-// matrix with the p rows G[V, :], written directly as split-TF32 operand tiles.  The n x n
-// update runs on the tensor cores as one real GEMM in the 4M form (K = 2P, P = p rounded up
-// to 16) with three TF32 products per K-step (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM),
-// which keeps about 21 bits of each product.
+// matrix with the p rows G[V, :].  The n x n update runs on the tensor cores as one real GEMM
+// in the 4M form (K = 2P, P = p rounded up to 16).  Each row of A' (each column of B') is
+// scaled by a power of two 2^E_i (2^F_j) into (-1, 1) and split into two FP16 halves,
+// x = hi + 2^-11 lo; three products per K-step (hi*hi into one FP32 TMEM accumulator, hi*lo +
+// lo*hi into a second) keep about 22 bits of each product, and the epilogue forms
+// 2^(E_i + F_j) (D1 + 2^-11 D2).  FP16 halves cost 2 bytes per value (half of split TF32)
+// and run at twice the TF32 tensor rate.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <mutex>
@@ -21,8 +25,8 @@ namespace gf {
 
 constexpr int kC64M = 128;                 // rows per tile
 constexpr int kC64N = 128;                 // real columns per tile (64 complex)
-constexpr int kC64KC = 16;                 // real K per operand chunk
-constexpr int kC64Half = kC64M * kC64KC * 4;   // one hi or lo chunk of a 128-row operand: 8 KB
+constexpr int kC64KC = 32;                 // real K per operand chunk
+constexpr int kC64Half = kC64M * kC64KC * 2;   // one FP16 hi or lo chunk of a 128-row operand: 8 KB
 constexpr int kC64Block = 2 * kC64Half;        // hi + lo: 16 KB (A and B blocks alike)
 constexpr int kC64NSO = 3;                 // operand stages (A block + B block each)
 constexpr int kC64NSG = 2;                 // G tile stages
@@ -33,19 +37,31 @@ constexpr int kC64BarOff = kC64NSO * kC64OpStage + kC64NSG * kC64GTile;   // 229
 constexpr int kC64Smem = kC64BarOff + 256;
 constexpr int kC64EpiWarps = 16;
 constexpr int kC64Threads = 32 * (kC64EpiWarps + 4);   // + G producer, MMA, storer, operand producer
-constexpr int kC64TmemCols = 256;          // two accumulators of kC64N columns
+constexpr int kC64TmemCols = 512;          // two buffers x (D1, D2) of kC64N columns
 constexpr uint64_t kC64TimeoutNs = 2000000000ull;
 constexpr int kC64Group = 8;               // tile raster: groups of 8 row tiles (L2 reuse of operands)
 
-// element (r, k) of a 128 x 16 K-major, no-swizzle chunk: 8x16-byte core matrices, K stride
-// 128 B, row-group stride 512 B
+// byte offset of element (r, k) of a 128 x 32 FP16 K-major, no-swizzle chunk: 8 rows x 16 B
+// core matrices, K stride 128 B, row-group stride 512 B
 __host__ __device__ __forceinline__ int c64_off(int r, int k) {
-  return (r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+  return (r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
-  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);   // exactly representable in TF32
-  lo = x - hi;                                               // exact in FP32
+// x in (-1, 1) -> hi + 2^-11 lo with FP16 hi, lo
+__device__ __forceinline__ void f16_split(float x, __half& hi, __half& lo) {
+  hi = __float2half_rn(x);
+  const float r = x - __half2float(hi);          // exact in FP32
+  lo = __float2half_rn(r * 2048.0f);
+}
+
+__device__ __forceinline__ int scale_exp(float m) { return m > 0.f ? ilogbf(m) + 1 : 0; }
+
+__device__ __forceinline__ void st4h(uint8_t* p, __half a, __half b, __half c, __half d) {
+  __half2 x = __halves2half2(a, b), y = __halves2half2(c, d);
+  uint2 v;
+  v.x = *reinterpret_cast<uint32_t*>(&x);
+  v.y = *reinterpret_cast<uint32_t*>(&y);
+  *reinterpret_cast<uint2*>(p) = v;
 }
 
 // P = p rounded up to 16, so that each of the four u-quarters of k_c64_s_gemm is a multiple
@@ -62,6 +78,8 @@ C64Layout c64_layout(int64_t n, int pmax) {
   o.bytesA = (size_t)o.nrt * o.nkc * kC64Block;
   o.bytesB = (size_t)o.nct * o.nkc * kC64Block;
   o.bytesM = (size_t)pmax * pmax * 8;
+  o.bytesE = (size_t)o.nrt * kC64M * 4;
+  o.bytesF = (size_t)o.nct * (kC64N / 2) * 4;
   return o;
 }
 
@@ -103,20 +121,21 @@ __global__ void k_c64_inverse(WsLayout L, char* ws, int lam, float2* __restrict_
     Mout[u * p + c] = make_float2((float)(dchi[u] * x[u].re), (float)(dchi[u] * x[u].im));
 }
 
-// ---- S = (D A^{-1}) G[V, :] in FP32, written as split-TF32 B operand blocks ----------------
+// ---- S = (D A^{-1}) G[V, :] in FP32, written as scaled split-FP16 B operand blocks ----------
 // One CTA per 64 complex columns (one 128-real-column tile); thread (j, quarter of u range).
 __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G, int64_t ldg, int64_t n,
                                                     const float2* __restrict__ Mdai, const int32_t* __restrict__ V,
                                                     const UpdCtl* __restrict__ ctl, int64_t P, int nkc,
-                                                    uint8_t* __restrict__ Bops) {
+                                                    uint8_t* __restrict__ Bops, int32_t* __restrict__ Fcol) {
   if (ctl->skip) return;
   const int p = ctl->nv;
   __shared__ float2 Ms[128 * 16];            // M[u][v0 .. v0+16)
+  __shared__ float smax[4][64];
   const int t = threadIdx.x;
   const int jl = t & 63, q = t >> 6;         // local complex column, u quarter
   const int64_t ct = blockIdx.x;
   const int64_t j = ct * 64 + jl;
-  const int uq = (int)(P / 4);               // u values per thread (P <= 128 -> <= 32)
+  const int uq = (int)(P / 4);               // u values per thread (multiple of 4, <= 32)
   float2 acc[32];
 #pragma unroll
   for (int a = 0; a < 32; ++a) acc[a] = make_float2(0.f, 0.f);
@@ -139,76 +158,82 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G
       }
     }
   }
+  // per-column scale 2^F_j over all u (the four quarters of column j)
+  float m = 0.f;
+#pragma unroll
+  for (int a = 0; a < 32; ++a)
+    if (a < uq) m = fmaxf(m, fmaxf(fabsf(acc[a].x), fabsf(acc[a].y)));
+  smax[q][jl] = m;
+  __syncthreads();
+  const float mm = fmaxf(fmaxf(smax[0][jl], smax[1][jl]), fmaxf(smax[2][jl], smax[3][jl]));
+  const int F = scale_exp(mm);
+  if (q == 0) Fcol[j] = F;
+  const float sc = ldexpf(1.0f, -F);
   // columns 2j (re) and 2j+1 (im) of B':  k < P: (Re S, Im S);  k >= P: (-Im S, Re S)
   uint8_t* tile = Bops + ct * (int64_t)nkc * kC64Block;
   const int c_re = 2 * jl, c_im = 2 * jl + 1;
 #pragma unroll
   for (int a4 = 0; a4 < 32; a4 += 4) {
     if (a4 >= uq) break;
-    const int u0 = q * uq + a4;               // 4 consecutive u (uq = P/4 is a multiple of 4)
-    float re[4], im[4];
+    const int u0 = q * uq + a4;               // 4 consecutive u in one 8-aligned half of a core row
+    __half rh[4], rl[4], ih[4], il[4], nh[4], nl[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      re[e] = acc[a4 + e].x;
-      im[e] = acc[a4 + e].y;
+      f16_split(acc[a4 + e].x * sc, rh[e], rl[e]);
+      f16_split(acc[a4 + e].y * sc, ih[e], il[e]);
+      f16_split(-acc[a4 + e].y * sc, nh[e], nl[e]);
     }
-    // u0 .. u0+3 lie in one 4-aligned group when uq is a multiple of 4
-    float hr[4], lr[4], hi_[4], li[4], hn[4], ln[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      tf32_split(re[e], hr[e], lr[e]);
-      tf32_split(im[e], hi_[e], li[e]);
-      tf32_split(-im[e], hn[e], ln[e]);
-    }
-    const int kA = u0, kB = (int)P + u0;     // K positions of the two halves
-    const int kcA = kA / kC64KC, kcB = kB / kC64KC;
-    uint8_t* blkA = tile + kcA * kC64Block;
-    uint8_t* blkB = tile + kcB * kC64Block;
+    const int kA = u0, kB = (int)P + u0;
+    uint8_t* blkA = tile + (kA / kC64KC) * kC64Block;
+    uint8_t* blkB = tile + (kB / kC64KC) * kC64Block;
     const int oRa = c64_off(c_re, kA % kC64KC), oIa = c64_off(c_im, kA % kC64KC);
     const int oRb = c64_off(c_re, kB % kC64KC), oIb = c64_off(c_im, kB % kC64KC);
-    *reinterpret_cast<float4*>(blkA + oRa) = make_float4(hr[0], hr[1], hr[2], hr[3]);
-    *reinterpret_cast<float4*>(blkA + kC64Half + oRa) = make_float4(lr[0], lr[1], lr[2], lr[3]);
-    *reinterpret_cast<float4*>(blkA + oIa) = make_float4(hi_[0], hi_[1], hi_[2], hi_[3]);
-    *reinterpret_cast<float4*>(blkA + kC64Half + oIa) = make_float4(li[0], li[1], li[2], li[3]);
-    *reinterpret_cast<float4*>(blkB + oRb) = make_float4(hn[0], hn[1], hn[2], hn[3]);
-    *reinterpret_cast<float4*>(blkB + kC64Half + oRb) = make_float4(ln[0], ln[1], ln[2], ln[3]);
-    *reinterpret_cast<float4*>(blkB + oIb) = make_float4(hr[0], hr[1], hr[2], hr[3]);
-    *reinterpret_cast<float4*>(blkB + kC64Half + oIb) = make_float4(lr[0], lr[1], lr[2], lr[3]);
+    st4h(blkA + oRa, rh[0], rh[1], rh[2], rh[3]);
+    st4h(blkA + kC64Half + oRa, rl[0], rl[1], rl[2], rl[3]);
+    st4h(blkA + oIa, ih[0], ih[1], ih[2], ih[3]);
+    st4h(blkA + kC64Half + oIa, il[0], il[1], il[2], il[3]);
+    st4h(blkB + oRb, nh[0], nh[1], nh[2], nh[3]);
+    st4h(blkB + kC64Half + oRb, nl[0], nl[1], nl[2], nl[3]);
+    st4h(blkB + oIb, rh[0], rh[1], rh[2], rh[3]);
+    st4h(blkB + kC64Half + oIb, rl[0], rl[1], rl[2], rl[3]);
   }
 }
 
-// ---- A operand blocks from C0 (n x pmax FP64): row i -> [Re C0[i, :P), Im C0[i, :P)] ------
+// ---- A operand blocks from C0 (n x pmax FP64): row i -> [Re C0[i, :P), Im C0[i, :P)], scaled
+// by 2^-E_i and split into FP16 halves
 __global__ void k_c64_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n, int64_t nrows_pad,
-                                const UpdCtl* __restrict__ ctl, int64_t P, int nkc, uint8_t* __restrict__ Aops) {
+                                const UpdCtl* __restrict__ ctl, int64_t P, int nkc, uint8_t* __restrict__ Aops,
+                                int32_t* __restrict__ Erow) {
   if (ctl->skip) return;
   const int p = ctl->nv;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows_pad;
        i += (int64_t)gridDim.x * blockDim.x) {
     uint8_t* tile = Aops + (i / kC64M) * (int64_t)nkc * kC64Block;
     const int r = (int)(i % kC64M);
+    double m = 0.0;
+    for (int u = 0; u < p && i < n; ++u) {
+      const cplx c = C0[i * pmax + u];
+      m = fmax(m, fmax(fabs(c.re), fabs(c.im)));
+    }
+    const int E = m > 0.0 ? ilogb(m) + 1 : 0;
+    Erow[i] = E;
     for (int u0 = 0; u0 < P; u0 += 4) {
-      float re[4], im[4];
+      __half rh[4], rl[4], ih[4], il[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int u = u0 + e;
         const cplx c = (i < n && u < p) ? C0[i * pmax + u] : mk(0.0, 0.0);
-        re[e] = (float)c.re;
-        im[e] = (float)c.im;
-      }
-      float hr[4], lr[4], hi_[4], li[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        tf32_split(re[e], hr[e], lr[e]);
-        tf32_split(im[e], hi_[e], li[e]);
+        f16_split((float)ldexp(c.re, -E), rh[e], rl[e]);
+        f16_split((float)ldexp(c.im, -E), ih[e], il[e]);
       }
       const int kA = u0, kB = (int)P + u0;
       uint8_t* blkA = tile + (kA / kC64KC) * kC64Block;
       uint8_t* blkB = tile + (kB / kC64KC) * kC64Block;
       const int oa = c64_off(r, kA % kC64KC), ob = c64_off(r, kB % kC64KC);
-      *reinterpret_cast<float4*>(blkA + oa) = make_float4(hr[0], hr[1], hr[2], hr[3]);
-      *reinterpret_cast<float4*>(blkA + kC64Half + oa) = make_float4(lr[0], lr[1], lr[2], lr[3]);
-      *reinterpret_cast<float4*>(blkB + ob) = make_float4(hi_[0], hi_[1], hi_[2], hi_[3]);
-      *reinterpret_cast<float4*>(blkB + kC64Half + ob) = make_float4(li[0], li[1], li[2], li[3]);
+      st4h(blkA + oa, rh[0], rh[1], rh[2], rh[3]);
+      st4h(blkA + kC64Half + oa, rl[0], rl[1], rl[2], rl[3]);
+      st4h(blkB + ob, ih[0], ih[1], ih[2], ih[3]);
+      st4h(blkB + kC64Half + ob, il[0], il[1], il[2], il[3]);
     }
   }
 }
@@ -240,6 +265,7 @@ __device__ __forceinline__ void c64_tile_coords(int64_t t, int64_t nrt, int64_t 
 __global__ void __launch_bounds__(kC64Threads, 1)
 k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_t nrt, int64_t nct, int nkc,
                      const uint8_t* __restrict__ Aops, const uint8_t* __restrict__ Bops,
+                     const int32_t* __restrict__ Erow, const int32_t* __restrict__ Fcol,
                      const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int p = ctl->skip ? 0 : ctl->nv;
@@ -318,14 +344,14 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
     __syncwarp();
   } else if (warp == kWarpMma) {
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_tf32(kC64M, kC64N);
+      const uint32_t idesc = tc::idesc_f16(kC64M, kC64N);
       int64_t k = 0, c = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < T && ok; t += gridDim.x, ++k) {
         const int b = (int)(k & 1);
         if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[b], (uint32_t)((k / 2 - 1) & 1), abort, kC64TimeoutNs)) break;
         tc::fence_after_sync();
-        const uint32_t d = tbase + (uint32_t)(b * kC64N);
+        const uint32_t d1 = tbase + (uint32_t)(b * 2 * kC64N), d2 = d1 + kC64N;
         for (int kc = 0; kc < nkc; ++kc, ++c) {
           const int s = (int)(c % kC64NSO);
           if (!tc::mbar_wait_or_abort(&bars->ofull[s], (uint32_t)((c / kC64NSO) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
@@ -333,13 +359,14 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
           const uint32_t sA = tc::smem_u32(ops + s * kC64OpStage);
           const uint32_t sB = sA + kC64Block;
 #pragma unroll
-          for (int ks = 0; ks < kC64KC / 8; ++ks) {
-            const uint32_t off = ks * 256;     // two K core matrices per K = 8 step
+          for (int ks = 0; ks < kC64KC / 16; ++ks) {
+            const uint32_t off = ks * 256;     // K = 16 FP16 per step = two core matrices
             const uint64_t ah = tc::smem_desc(sA + off, 128, 512), al = tc::smem_desc(sA + kC64Half + off, 128, 512);
             const uint64_t bh = tc::smem_desc(sB + off, 128, 512), bl = tc::smem_desc(sB + kC64Half + off, 128, 512);
-            tc::mma_tf32(d, ah, bh, idesc, (kc == 0 && ks == 0) ? 0u : 1u);
-            tc::mma_tf32(d, ah, bl, idesc, 1u);
-            tc::mma_tf32(d, al, bh, idesc, 1u);
+            const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+            tc::mma_f16(d1, ah, bh, idesc, first);
+            tc::mma_f16(d2, ah, bl, idesc, first);
+            tc::mma_f16(d2, al, bh, idesc, 1u);
           }
           tc::mma_commit(&bars->oempty[s]);
         }
@@ -353,36 +380,48 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
     int64_t k = 0;
     for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++k) {
+      int64_t rt, ct;
+      c64_tile_coords(t, nrt, nct, rt, ct);
       const int b = (int)(k & 1);
       const int s = (int)(k % kC64NSG);
+      const int Ei = Erow[rt * kC64M + r];
       if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kC64TimeoutNs)) break;
       if (!tc::mbar_wait_or_abort(&bars->gfull[s], (uint32_t)((k / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
       tc::fence_after_sync();
-      float acc[32];
+      float acc1[32], acc2[32];
       {
-        float a0[16], a1[16];
-        tc::tmem_ld16(tbase + lane_addr + (uint32_t)(b * kC64N + h * 32), a0);
-        tc::tmem_ld16(tbase + lane_addr + (uint32_t)(b * kC64N + h * 32 + 16), a1);
+        float a0[16], a1[16], a2[16], a3[16];
+        const uint32_t base = tbase + lane_addr + (uint32_t)(b * 2 * kC64N + h * 32);
+        tc::tmem_ld16(base, a0);
+        tc::tmem_ld16(base + 16, a1);
+        tc::tmem_ld16(base + kC64N, a2);
+        tc::tmem_ld16(base + kC64N + 16, a3);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          acc[e] = a0[e];
-          acc[16 + e] = a1[e];
+          acc1[e] = a0[e];
+          acc1[16 + e] = a1[e];
+          acc2[e] = a2[e];
+          acc2[16 + e] = a3[e];
         }
       }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
-      // box h holds real columns 32h .. 32h+31 of the tile = 8 chunks of 16 B (128B swizzle)
+      // box h holds real columns 32h .. 32h+31 of the tile = 8 chunks of 16 B (128B swizzle);
+      // chunk ch holds complex columns 2ch, 2ch+1 of this quarter
+      const int32_t* Fq = Fcol + ct * (kC64N / 2) + h * 16;
       uint8_t* row = gts + s * kC64GTile + h * kC64Box + r * 128;
 #pragma unroll
       for (int ch = 0; ch < 8; ++ch) {
+        const float s0 = __int_as_float((Ei + Fq[2 * ch] + 127) << 23);
+        const float s1 = __int_as_float((Ei + Fq[2 * ch + 1] + 127) << 23);
         float4* gp = reinterpret_cast<float4*>(row + ((ch ^ (r & 7)) << 4));
         float4 g = *gp;
-        g.x += acc[4 * ch + 0];
-        g.y += acc[4 * ch + 1];
-        g.z += acc[4 * ch + 2];
-        g.w += acc[4 * ch + 3];
+        g.x += s0 * fmaf(acc2[4 * ch + 0], 0.00048828125f, acc1[4 * ch + 0]);
+        g.y += s0 * fmaf(acc2[4 * ch + 1], 0.00048828125f, acc1[4 * ch + 1]);
+        g.z += s1 * fmaf(acc2[4 * ch + 2], 0.00048828125f, acc1[4 * ch + 2]);
+        g.w += s1 * fmaf(acc2[4 * ch + 3], 0.00048828125f, acc1[4 * ch + 3]);
         *gp = g;
       }
       tc::fence_proxy_async_smem();
@@ -457,12 +496,15 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
   uint8_t* Bops = reinterpret_cast<uint8_t*>(ws + L.c64B);
   const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + lam * L.panel_s);
   k_c64_inverse<<<L.pmax, 128, 0, st>>>(L, ws, lam, Mdai);
+  int32_t* Erow = reinterpret_cast<int32_t*>(ws + L.c64E);
+  int32_t* Fcol = reinterpret_cast<int32_t*>(ws + L.c64F);
   k_c64_s_gemm<<<(unsigned)o.nct, 256, 0, st>>>(G, ldg, n, Mdai, reinterpret_cast<const int32_t*>(ws + L.V), ctl, o.P,
-                                                 (int)o.nkc, Bops);
+                                                 (int)o.nkc, Bops, Fcol);
   {
     int64_t rows = o.nrt * kC64M;
     int64_t b = (rows + 127) / 128;
-    k_c64_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, L.pmax, n, rows, ctl, o.P, (int)o.nkc, Aops);
+    k_c64_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, L.pmax, n, rows, ctl, o.P, (int)o.nkc, Aops,
+                                                                 Erow);
   }
   {
     static std::mutex mu;
@@ -477,8 +519,8 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
   }
   const int64_t tiles = o.nrt * o.nct;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  k_rank_update_c64_tc<<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.nct, (int)o.nkc, Aops, Bops, ctl,
-                                                            status, prof_p);
+  k_rank_update_c64_tc<<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.nct, (int)o.nkc, Aops, Bops, Erow, Fcol,
+                                                            ctl, status, prof_p);
 }
 
 }  // namespace gf

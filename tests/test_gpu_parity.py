@@ -210,3 +210,34 @@ def test_tensor_core_update_matches_dfma_update(nx, ny):
         assert e <= 1e-14, (t, e)
         assert rel_err(gpu_E(a), gpu_E(b)) <= 1e-14
     assert int(a.status.cpu()[0]) in (B.GF_OK, B.GF_ENOIMPROVE)
+
+
+@pytest.mark.parametrize("nx,ny,k,seed", [(60, 50, 8, 71), (90, 70, 32, 72), (40, 30, 16, 73)])
+def test_pooled_topk_selection_matches_oracle(nx, ny, k, seed):
+    """Top-k with exclusion on random dFOM arrays (pooled path and its exact fallback) against
+    the oracle's sorted scan."""
+    g = W.small(nx, ny, kind=W.KIND_BRUSH2).geoms[0]
+    spec = W.CandidateSpec(W.KIND_BRUSH2, 3, k=k, excl_radius=3)
+    h = B.Handle(0)
+    nc = h.gf_num_candidates(g, spec)
+    rng = np.random.default_rng(seed)
+    ws_bytes = h.gf_workspace_size(g, 1, B.GF_C128, spec)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    for trial in range(4):
+        d = rng.normal(size=nc)
+        if trial == 1:
+            d = -np.abs(d)                                  # nothing improves
+        if trial == 2:
+            d = np.round(d, 1)                              # many exact ties
+        if trial == 3:
+            d[rng.random(nc) < 0.97] = -np.inf              # sparse improving set
+        dt = torch.tensor(d, dtype=torch.float64, device="cuda")
+        idx = torch.full((k,), -7, dtype=torch.int32, device="cuda")
+        val = torch.empty(k, dtype=torch.float64, device="cuda")
+        st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        h.gf_select_topk(g, spec, dt, nc, idx, val, st, ws, ws_bytes)
+        torch.cuda.synchronize()
+        ref = O.select_topk(g, spec, d)
+        got = [int(x) for x in idx.cpu().numpy() if x >= 0]
+        assert got == ref, (trial, got[:5], ref[:5])
+        assert int(st.cpu()[0]) == (B.GF_OK if ref else B.GF_ENOIMPROVE)
