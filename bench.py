@@ -381,6 +381,16 @@ def run_native(args):
                "note": "timed: H2D of the design state, gf_fill_g0, then K x (step + D2H of "
                        "the step result) through GreedyOptimizer"}
 
+    # ---- drift refresh (every few hundred steps in a run; timed once here, outside the step)
+    refresh = None
+    if not args.no_breakdown:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rr = opt.refresh(nsample=8)
+        refresh = {"ms": 1e3 * (time.perf_counter() - t0), "ls_residual": rr[0][0][0],
+                   "column_drift_max": max(rr[0][0][1:]) if len(rr[0][0]) > 1 else None,
+                   "gmres_iters": rr[0][1], "columns": 8}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -427,6 +437,8 @@ def run_native(args):
         line["step_breakdown_ms"] = breakdown
     if dfma is not None:
         line["dfma_update"] = dfma
+    if refresh is not None:
+        line["refresh"] = refresh
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget)
     print(json.dumps(line), flush=True)

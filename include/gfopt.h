@@ -165,6 +165,22 @@ gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, i
                           int32_t* status, double* fom_out, int32_t* applied, void* ws,
                           size_t ws_bytes, void* stream);
 
+/* Drift refresh of one wavelength (checks against the discrete Eqs. 3 and 2; run every few
+ * hundred steps).  resid_out (host, 1 + nsample doubles):
+ *   resid_out[0]   = ||E - E_inc - G0 X E||_2 / ||E||_2 (Lippmann-Schwinger residual, with G0 X E
+ *                    computed by FFT convolution of the Toeplitz pixel block, FP64);
+ *   resid_out[1+s] = ||G[:, cols[s]] - g||_2 / ||g||_2 where (I - G0 X) g = G0[:, cols[s]] is
+ *                    solved by restarted GMRES(restart) from the stored column to relative
+ *                    residual tol (at most max_iter iterations; iters_out[s] = iterations, may
+ *                    be NULL).
+ * cols: host array of nsample indices in [0, n).  Blocking: returns after synchronising
+ * `stream`.  ws: at least gf_refresh_workspace_size() bytes.  nx, ny <= 4096. */
+size_t gf_refresh_workspace_size(const gf_geom* geom, int32_t restart);
+gf_status gf_refresh(gf_handle* h, const gf_problem* prob, int32_t dtype, const uint8_t* state,
+                     int32_t nsample, const int32_t* cols, int32_t restart, int32_t max_iter,
+                     double tol, double* resid_out, int32_t* iters_out, void* ws, size_t ws_bytes,
+                     void* stream);
+
 /* Arithmetic of the complex128 G update (Eq. 10).  GF_UPDATE_TC (default): exact digit
  * products on the tensor cores with an integer recombination (FP64-accurate to ~2^-50 of
  * |C0||S|; used for p <= 4, larger p falls back to DFMA).  GF_UPDATE_DFMA: native FP64 FMA.

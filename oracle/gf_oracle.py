@@ -313,6 +313,22 @@ def brute_force(g: Geometry, state: np.ndarray) -> Tuple[np.ndarray, np.ndarray]
     return np.linalg.solve(M, G0), np.linalg.solve(M, incident_field(g))
 
 
+# --------------------------------------------------------------------------- drift checks
+def ls_residual(g: Geometry, state: np.ndarray, E: np.ndarray) -> float:
+    """Relative Lippmann-Schwinger residual of a field (discrete Eq. 3):
+    ||E - E_inc - G0 X E||_2 / ||E||_2 with the dense background matrix."""
+    G0 = g0_matrix(g)
+    x = np.zeros(g.N + 1)
+    x[:g.N] = np.asarray(state, dtype=np.float64) * contrast(g)
+    r = E - incident_field(g) - G0 @ (x * E)
+    return float(np.linalg.norm(r) / np.linalg.norm(E))
+
+
+def exact_columns(g: Geometry, state: np.ndarray, cols) -> np.ndarray:
+    """Columns of G = (I - G0 X)^{-1} G0 (discrete Eq. 2) for the given design."""
+    return brute_force(g, np.asarray(state))[0][:, list(cols)]
+
+
 # --------------------------------------------------------------------------- driver
 class OracleProblem:
     """One design problem (one G and E per wavelength) advanced by greedy steps."""

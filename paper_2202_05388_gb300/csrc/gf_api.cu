@@ -341,6 +341,36 @@ gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, i
   return cuda_check(h, "gf_apply_update launch");
 }
 
+size_t gf_refresh_workspace_size(const gf_geom* g, int32_t restart) {
+  if (!g || g->nx < 1 || g->ny < 1 || g->nx > 4096 || g->ny > 4096 || restart < 1 || restart > 200) return 0;
+  return gf::refresh_workspace_size(*g, restart);
+}
+
+gf_status gf_refresh(gf_handle* h, const gf_problem* prob, int32_t dtype, const uint8_t* state, int32_t nsample,
+                     const int32_t* cols, int32_t restart, int32_t max_iter, double tol, double* resid_out,
+                     int32_t* iters_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!h) return GF_EINVAL;
+  gf_status s = check_problem(h, prob, dtype, false);
+  if (s) return s;
+  if (prob->geom.nx > 4096 || prob->geom.ny > 4096) return fail(h, GF_EINVAL, "gf_refresh supports nx, ny <= 4096");
+  if (!state || !resid_out) return fail(h, GF_EINVAL, "state and resid_out must be non-NULL");
+  if (nsample < 0 || (nsample > 0 && !cols)) return fail(h, GF_EINVAL, "nsample must be >= 0 with a cols array");
+  if (restart < 1 || restart > 200) return fail(h, GF_EINVAL, "restart must be in [1, 200]");
+  if (max_iter < 1) return fail(h, GF_EINVAL, "max_iter must be >= 1");
+  if (!(tol > 0.0) || !isfinite(tol)) return fail(h, GF_EINVAL, "tol must be positive");
+  const int64_t n = (int64_t)prob->geom.nx * prob->geom.ny + 1;
+  for (int q = 0; q < nsample; ++q)
+    if (cols[q] < 0 || cols[q] >= n) return fail(h, GF_EINVAL, "column %d out of range", cols[q]);
+  const size_t need = gf::refresh_workspace_size(prob->geom, restart);
+  if (!ws || ((uintptr_t)ws & 255u)) return fail(h, GF_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < need) return fail(h, GF_ENOMEM, "workspace has %zu bytes, refresh needs %zu", ws_bytes, need);
+  if ((s = bind_device(h))) return s;
+  s = gf::refresh(*prob, dtype, state, nsample, cols, restart, max_iter, tol, resid_out, iters_out,
+                  reinterpret_cast<char*>(ws), (cudaStream_t)stream);
+  if (s) return cuda_check(h, "gf_refresh");
+  return GF_OK;
+}
+
 gf_status gf_set_update_algo(gf_handle* h, int32_t algo) {
   if (!h) return GF_EINVAL;
   if (algo != GF_UPDATE_TC && algo != GF_UPDATE_DFMA) return fail(h, GF_EINVAL, "unknown update algorithm %d", algo);

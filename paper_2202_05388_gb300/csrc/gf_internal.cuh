@@ -180,6 +180,10 @@ bool c64_tc_make_map(float2* G, int64_t ldg, int64_t n, void* map128);
 void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64_t n, const WsLayout& L, char* ws,
                                int lam, int32_t* status, int32_t* prof_p, int sm_count, cudaStream_t st);
 
+size_t refresh_workspace_size(const gf_geom& g, int restart);
+gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int nsample, const int32_t* cols,
+                  int restart, int max_iter, double tol, double* resid, int32_t* iters, char* ws, cudaStream_t st);
+
 void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state,
                    const gf_cand_spec& spec, const int32_t* idx, int32_t* status, double* fom_out,
                    int32_t* applied, cudaStream_t st, KernelTimer* timer);

@@ -1,0 +1,416 @@
+// Drift refresh: checks of the accumulated state against the discrete Lippmann-Schwinger and
+// Dyson equations (Eqs. 3 and 2), which the step-by-step updates satisfy only up to rounding.
+//
+//   resid[0]     = ||E - E_inc - G0 X E||_2 / ||E||_2                      (Eq. 3 residual)
+//   resid[1 + s] = ||G[:, c_s] - g_s||_2 / ||g_s||_2,  (I - G0 X) g_s = G0[:, c_s]   (Eq. 2)
+//
+// g_s is found by restarted GMRES started from the stored column.  The background G0 depends
+// on pixel offsets only, so G0 X v restricted to the pixels is a 2-D convolution: it is
+// computed by circulant embedding on an Ly x Lx power-of-two grid (Lx >= 2 nx - 1,
+// Ly >= 2 ny - 1) with radix-2 FFTs in FP64; the monitor row of G0 X v is a dot product.
+// X is zero at the monitor, so the monitor column of G0 never enters.
+#include <math.h>
+
+#include <vector>
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+static int64_t pow2_at_least(int64_t v) {
+  int64_t L = 1;
+  while (L < v) L <<= 1;
+  return L;
+}
+
+struct RefLayout {
+  int64_t Lx, Ly, n, N;
+  int m;
+  size_t table, khat, grid, V, w, x, b, r, dots, total;
+};
+
+static size_t up256r(size_t x) { return (x + 255) & ~(size_t)255; }
+
+RefLayout ref_layout(const gf_geom& g, int restart) {
+  RefLayout L;
+  L.N = (int64_t)g.nx * g.ny;
+  L.n = L.N + 1;
+  L.Lx = pow2_at_least(2 * (int64_t)g.nx - 1);
+  L.Ly = pow2_at_least(2 * (int64_t)g.ny - 1);
+  L.m = restart;
+  const size_t c = sizeof(cplx);
+  size_t o = 0;
+  L.table = o; o = up256r(o + c * (size_t)(2 * L.N));
+  L.khat = o; o = up256r(o + c * (size_t)(L.Lx * L.Ly));
+  L.grid = o; o = up256r(o + c * (size_t)(L.Lx * L.Ly));
+  L.V = o; o = up256r(o + c * (size_t)L.n * (L.m + 1));
+  L.w = o; o = up256r(o + c * (size_t)L.n);
+  L.x = o; o = up256r(o + c * (size_t)L.n);
+  L.b = o; o = up256r(o + c * (size_t)L.n);
+  L.r = o; o = up256r(o + c * (size_t)L.n);
+  L.dots = o; o = up256r(o + c * (size_t)(L.m + 2));
+  L.total = o;
+  return L;
+}
+
+// ---- FFT: one CTA per line, radix-2 decimation in time in shared memory ----------------------
+__global__ void k_fft_lines(cplx* __restrict__ data, int L, int logL, int64_t stride, int64_t line_stride,
+                            double sign) {
+  extern __shared__ cplx sh[];
+  cplx* base = data + blockIdx.x * line_stride;
+  for (int e = threadIdx.x; e < L; e += blockDim.x) {
+    const int rev = (int)(__brev((unsigned)e) >> (32 - logL));
+    sh[rev] = base[(int64_t)e * stride];
+  }
+  __syncthreads();
+  for (int s = 1; s <= logL; ++s) {
+    const int half = 1 << (s - 1);
+    for (int t = threadIdx.x; t < L / 2; t += blockDim.x) {
+      const int kk = t & (half - 1);
+      const int i = ((t >> (s - 1)) << s) + kk;
+      const int j = i + half;
+      double sn, cs;
+      sincospi(sign * (double)kk / (double)half, &sn, &cs);
+      const cplx wv = mk(cs, sn);
+      const cplx tv = wv * sh[j];
+      sh[j] = sh[i] - tv;
+      sh[i] = sh[i] + tv;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < L; e += blockDim.x) base[(int64_t)e * stride] = sh[e];
+}
+
+static void fft2(cplx* grid, int64_t Lx, int64_t Ly, double sign, cudaStream_t st) {
+  int lx = 0, ly = 0;
+  while ((1LL << lx) < Lx) ++lx;
+  while ((1LL << ly) < Ly) ++ly;
+  if (Lx > 1) {
+    int th = (int)(Lx / 2 < 512 ? Lx / 2 : 512);
+    k_fft_lines<<<(unsigned)Ly, th, sizeof(cplx) * Lx, st>>>(grid, (int)Lx, lx, 1, Lx, sign);
+  }
+  if (Ly > 1) {
+    int th = (int)(Ly / 2 < 512 ? Ly / 2 : 512);
+    k_fft_lines<<<(unsigned)Lx, th, sizeof(cplx) * Ly, st>>>(grid, (int)Ly, ly, Lx, 1, sign);
+  }
+}
+
+// ---- circulant embedding of the G0 pixel kernel ---------------------------------------------
+__global__ void k_embed(const cplx* __restrict__ table, int nx, int ny, int64_t Lx, int64_t Ly, cplx* __restrict__ K) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < Lx * Ly; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = e / Lx, x = e - y * Lx;
+    const int64_t dy = y < ny ? y : (y > Ly - ny ? Ly - y : -1);
+    const int64_t dx = x < nx ? x : (x > Lx - nx ? Lx - x : -1);
+    K[e] = (dy >= 0 && dx >= 0) ? table[dy * nx + dx] : mk(0.0, 0.0);
+  }
+}
+
+__global__ void k_mul(cplx* __restrict__ a, const cplx* __restrict__ b, int64_t cnt, double scale) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x)
+    a[e] = scale * (a[e] * b[e]);
+}
+
+// grid <- chi v on the pixels (zero padded)
+__global__ void k_scatter(const cplx* __restrict__ v, const uint8_t* __restrict__ state, double chi, int nx, int ny,
+                          int64_t Lx, int64_t Ly, cplx* __restrict__ grid) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < Lx * Ly; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = e / Lx, x = e - y * Lx;
+    cplx u = mk(0.0, 0.0);
+    if (x < nx && y < ny) {
+      const int64_t j = y * nx + x;
+      if (state[j]) u = chi * v[j];
+    }
+    grid[e] = u;
+  }
+}
+
+// out = alpha * v + beta * (G0 X v), with the pixel part from the convolution grid and the
+// monitor part as the dot product of the monitor row with X v (one block does the dot)
+__global__ void k_gather_combine(const cplx* __restrict__ v, const cplx* __restrict__ grid, const cplx* __restrict__ mon,
+                                 const uint8_t* __restrict__ state, double chi, int nx, int ny, int64_t Lx,
+                                 double alpha, double beta, cplx* __restrict__ out) {
+  const int64_t N = (int64_t)nx * ny;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = i / nx, x = i - y * nx;
+    out[i] = alpha * v[i] + beta * grid[y * Lx + x];
+  }
+  if (blockIdx.x == 0) {
+    __shared__ double sr[32], si[32];
+    double ar = 0.0, ai = 0.0;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+      if (state[j]) {
+        const cplx t = mon[j] * (chi * v[j]);
+        ar += t.re;
+        ai += t.im;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ar += __shfl_down_sync(0xffffffffu, ar, o);
+      ai += __shfl_down_sync(0xffffffffu, ai, o);
+    }
+    if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = ar; si[threadIdx.x >> 5] = ai; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tr = 0.0, ti = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tr += sr[w]; ti += si[w]; }
+      out[N] = alpha * v[N] + beta * mk(tr, ti);
+    }
+  }
+}
+
+// ---- vectors ----------------------------------------------------------------------------------
+__device__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[32], sb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { sa[threadIdx.x >> 5] = a; sb[threadIdx.x >> 5] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { ta += sa[w]; tb += sb[w]; }
+    a = ta;
+    b = tb;
+  }
+}
+
+// h[q] = <V_q, w> = sum conj(V_q) w for q < nvec (one block per vector)
+__global__ void k_dots(const cplx* __restrict__ V, int64_t n, int nvec, const cplx* __restrict__ w, cplx* __restrict__ h) {
+  const int q = blockIdx.x;
+  if (q >= nvec) return;
+  const cplx* vq = V + (int64_t)q * n;
+  double ar = 0.0, ai = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const cplx a = vq[i], b = w[i];
+    ar += a.re * b.re + a.im * b.im;
+    ai += a.re * b.im - a.im * b.re;
+  }
+  block_sum2(ar, ai);
+  if (threadIdx.x == 0) h[q] = mk(ar, ai);
+}
+
+// w -= sum_q h[q] V_q
+__global__ void k_sub_combo(cplx* __restrict__ w, const cplx* __restrict__ V, int64_t n, int nvec,
+                            const cplx* __restrict__ h) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cplx acc = w[i];
+    for (int q = 0; q < nvec; ++q) acc = acc - h[q] * V[(int64_t)q * n + i];
+    w[i] = acc;
+  }
+}
+
+// out[0] = ||a||^2 (single block)
+__global__ void k_norm2(const cplx* __restrict__ a, int64_t n, double* out) {
+  double s = 0.0, z = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += abs2(a[i]);
+  block_sum2(s, z);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// y = a * x   (a real)
+__global__ void k_scale(cplx* __restrict__ y, const cplx* __restrict__ x, int64_t n, double a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// y = x - z
+__global__ void k_diff(cplx* __restrict__ y, const cplx* __restrict__ x, const cplx* __restrict__ z, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] - z[i];
+}
+
+// x += sum_q c[q] V_q  (c on the device)
+__global__ void k_add_combo(cplx* __restrict__ x, const cplx* __restrict__ V, int64_t n, int nvec,
+                            const cplx* __restrict__ c) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cplx acc = x[i];
+    for (int q = 0; q < nvec; ++q) acc = acc + c[q] * V[(int64_t)q * n + i];
+    x[i] = acc;
+  }
+}
+
+// E_inc at the n points
+__global__ void k_einc(int nx, int ny, double dx, double k, double my, cplx* __restrict__ out) {
+  const int64_t N = (int64_t)nx * ny;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= N; j += (int64_t)gridDim.x * blockDim.x) {
+    const double y = j < N ? ((double)(j / nx) + 0.5) * dx : my;
+    double s, c;
+    sincos(k * y, &s, &c);
+    out[j] = mk(c, s);
+  }
+}
+
+// b = G0[:, c] from the table (column c of the background matrix), x = stored G[:, c]
+__global__ void k_column_rhs(const cplx* __restrict__ table, int nx, int ny, int64_t c, const void* G, int dtype,
+                             int64_t ldg, cplx* __restrict__ b, cplx* __restrict__ x) {
+  const int64_t N = (int64_t)nx * ny;
+  const cplx* mon = table + N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= N; i += (int64_t)gridDim.x * blockDim.x) {
+    cplx v;
+    if (c == N) {
+      v = i < N ? mon[i] : mk(0.0, 0.0);
+    } else if (i == N) {
+      v = mon[c];
+    } else {
+      const int64_t iy = i / nx, ix = i - iy * nx, cy = c / nx, cx = c - cy * nx;
+      const int64_t ay = iy > cy ? iy - cy : cy - iy, ax = ix > cx ? ix - cx : cx - ix;
+      v = table[ay * nx + ax];
+    }
+    b[i] = v;
+    x[i] = ldG(G, dtype, ldg, i, c);
+  }
+}
+
+struct RefCtx {
+  const gf_geom* g;
+  RefLayout L;
+  char* ws;
+  const uint8_t* state;
+  double chi;
+  cudaStream_t st;
+  int blocks;
+};
+
+static cplx* P(const RefCtx& c, size_t off) { return reinterpret_cast<cplx*>(c.ws + off); }
+
+// out = v - G0 X v  (alpha = 1, beta = -1) or out = G0 X v (alpha = 0, beta = 1)
+static void apply(const RefCtx& c, const cplx* v, cplx* out, double alpha, double beta) {
+  const RefLayout& L = c.L;
+  cplx* grid = P(c, L.grid);
+  k_scatter<<<c.blocks, 256, 0, c.st>>>(v, c.state, c.chi, c.g->nx, c.g->ny, L.Lx, L.Ly, grid);
+  fft2(grid, L.Lx, L.Ly, -1.0, c.st);
+  k_mul<<<c.blocks, 256, 0, c.st>>>(grid, P(c, L.khat), L.Lx * L.Ly, 1.0 / (double)(L.Lx * L.Ly));
+  fft2(grid, L.Lx, L.Ly, +1.0, c.st);
+  k_gather_combine<<<c.blocks, 256, 0, c.st>>>(v, grid, P(c, L.table) + L.N, c.state, c.chi, c.g->nx, c.g->ny, L.Lx,
+                                               alpha, beta, out);
+}
+
+static double norm2_host(const RefCtx& c, const cplx* a) {
+  double* d = reinterpret_cast<double*>(P(c, c.L.dots));
+  k_norm2<<<1, 1024, 0, c.st>>>(a, c.L.n, d);
+  double h = 0.0;
+  cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, c.st);
+  cudaStreamSynchronize(c.st);
+  return sqrt(h);
+}
+
+// GMRES(m) on (I - G0 X) x = b from the initial x.  Returns iterations used.
+static int gmres(const RefCtx& c, int max_iter, double tol) {
+  const RefLayout& L = c.L;
+  const int64_t n = L.n;
+  cplx *V = P(c, L.V), *w = P(c, L.w), *x = P(c, L.x), *b = P(c, L.b), *r = P(c, L.r);
+  cplx* hd = P(c, L.dots);
+  const double bnorm = norm2_host(c, b);
+  if (!(bnorm > 0.0)) return 0;
+  const int m = L.m;
+  std::vector<cplx> H((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1), hcol(m + 2);
+  int it = 0;
+  while (it < max_iter) {
+    apply(c, x, w, 1.0, -1.0);                        // w = A x
+    k_diff<<<c.blocks, 256, 0, c.st>>>(r, b, w, n);    // r = b - A x
+    const double beta = norm2_host(c, r);
+    if (!(beta > tol * bnorm)) break;
+    k_scale<<<c.blocks, 256, 0, c.st>>>(V, r, n, 1.0 / beta);
+    for (auto& z : gvec) z = mk(0.0, 0.0);
+    gvec[0] = mk(beta, 0.0);
+    int k = 0;
+    bool converged = false;
+    for (; k < m && it < max_iter; ++k, ++it) {
+      apply(c, V + (int64_t)k * n, w, 1.0, -1.0);     // w = A v_k
+      // classical Gram-Schmidt, twice
+      std::vector<cplx> hsum(k + 1, mk(0.0, 0.0));
+      for (int pass = 0; pass < 2; ++pass) {
+        k_dots<<<k + 1, 256, 0, c.st>>>(V, n, k + 1, w, hd);
+        k_sub_combo<<<c.blocks, 256, 0, c.st>>>(w, V, n, k + 1, hd);
+        cudaMemcpyAsync(hcol.data(), hd, sizeof(cplx) * (k + 1), cudaMemcpyDeviceToHost, c.st);
+        cudaStreamSynchronize(c.st);
+        for (int q = 0; q <= k; ++q) hsum[q] = hsum[q] + hcol[q];
+      }
+      const double hn = norm2_host(c, w);
+      for (int q = 0; q <= k; ++q) H[(size_t)q * m + k] = hsum[q];
+      H[(size_t)(k + 1) * m + k] = mk(hn, 0.0);
+      if (hn > 0.0) k_scale<<<c.blocks, 256, 0, c.st>>>(V + (int64_t)(k + 1) * n, w, n, 1.0 / hn);
+      // apply the previous Givens rotations, then a new one zeroing H[k+1][k]
+      for (int q = 0; q < k; ++q) {
+        const cplx a = H[(size_t)q * m + k], bq = H[(size_t)(q + 1) * m + k];
+        const cplx cq = cs[q], sq = sn[q];
+        H[(size_t)q * m + k] = cq * a + sq * bq;
+        H[(size_t)(q + 1) * m + k] = mk(-sq.re, sq.im) * a + mk(cq.re, -cq.im) * bq;   // -conj(s) a + conj(c) b
+      }
+      {
+        const cplx a = H[(size_t)k * m + k], bb = H[(size_t)(k + 1) * m + k];
+        const double den = sqrt(abs2(a) + abs2(bb));
+        cplx ck, sk;
+        if (den == 0.0) { ck = mk(1.0, 0.0); sk = mk(0.0, 0.0); }
+        else { ck = mk(a.re / den, -a.im / den); sk = mk(bb.re / den, -bb.im / den); }   // conj(a)/den, conj(b)/den
+        cs[k] = ck;
+        sn[k] = sk;
+        H[(size_t)k * m + k] = ck * a + sk * bb;
+        H[(size_t)(k + 1) * m + k] = mk(0.0, 0.0);
+        const cplx gk = gvec[k];
+        gvec[k] = ck * gk;
+        gvec[k + 1] = mk(-sk.re, sk.im) * gk;
+      }
+      if (!(cabs1(gvec[k + 1]) > tol * bnorm) || hn == 0.0) { ++k; ++it; converged = true; break; }
+    }
+    // back substitution H y = g (k x k upper triangular), x += V y
+    std::vector<cplx> y(k);
+    for (int q = k - 1; q >= 0; --q) {
+      cplx acc = gvec[q];
+      for (int v = q + 1; v < k; ++v) acc = acc - H[(size_t)q * m + v] * y[v];
+      y[q] = cdiv(acc, H[(size_t)q * m + q]);
+    }
+    if (k > 0) {
+      cudaMemcpyAsync(hd, y.data(), sizeof(cplx) * k, cudaMemcpyHostToDevice, c.st);
+      k_add_combo<<<c.blocks, 256, 0, c.st>>>(x, V, n, k, hd);
+    }
+    if (converged) break;
+  }
+  cudaStreamSynchronize(c.st);
+  return it;
+}
+
+size_t refresh_workspace_size(const gf_geom& g, int restart) { return ref_layout(g, restart).total; }
+
+gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int nsample, const int32_t* cols,
+                  int restart, int max_iter, double tol, double* resid, int32_t* iters, char* ws, cudaStream_t st) {
+  const gf_geom& g = prob.geom;
+  RefCtx c;
+  c.g = &g;
+  c.L = ref_layout(g, restart);
+  c.ws = ws;
+  c.state = state;
+  c.chi = g.eps_mat - g.eps_bg;
+  c.st = st;
+  c.blocks = 152 * 4;
+  const RefLayout& L = c.L;
+  cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(cplx) * 8192));
+  launch_fill_table(g, P(c, L.table), st);
+  k_embed<<<c.blocks, 256, 0, st>>>(P(c, L.table), g.nx, g.ny, L.Lx, L.Ly, P(c, L.khat));
+  fft2(P(c, L.khat), L.Lx, L.Ly, -1.0, st);
+  // Eq. 3 residual of E: r = E - E_inc - G0 X E
+  const cplx* E = reinterpret_cast<const cplx*>(prob.E);
+  const double k0 = 2.0 * M_PI / g.wavelength;
+  k_einc<<<c.blocks, 256, 0, st>>>(g.nx, g.ny, g.dx, k0, g.mon_y, P(c, L.b));
+  apply(c, E, P(c, L.w), 0.0, 1.0);                               // w = G0 X E
+  k_diff<<<c.blocks, 256, 0, st>>>(P(c, L.r), E, P(c, L.b), L.n);   // r = E - E_inc
+  k_diff<<<c.blocks, 256, 0, st>>>(P(c, L.r), P(c, L.r), P(c, L.w), L.n);
+  resid[0] = norm2_host(c, P(c, L.r)) / norm2_host(c, E);
+  for (int s = 0; s < nsample; ++s) {
+    k_column_rhs<<<c.blocks, 256, 0, st>>>(P(c, L.table), g.nx, g.ny, cols[s], prob.G, dtype, prob.ldg, P(c, L.b),
+                                           P(c, L.x));
+    const int its = gmres(c, max_iter, tol);     // x: stored column -> refined solution
+    if (iters) iters[s] = its;
+    k_column_rhs<<<c.blocks, 256, 0, st>>>(P(c, L.table), g.nx, g.ny, cols[s], prob.G, dtype, prob.ldg, P(c, L.b),
+                                           P(c, L.w));                 // w = stored column again
+    k_diff<<<c.blocks, 256, 0, st>>>(P(c, L.r), P(c, L.w), P(c, L.x), L.n);
+    resid[1 + s] = norm2_host(c, P(c, L.r)) / norm2_host(c, P(c, L.x));
+  }
+  cudaStreamSynchronize(st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GF_OK : GF_ECUDA;
+}
+
+}  // namespace gf

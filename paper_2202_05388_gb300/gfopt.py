@@ -29,7 +29,7 @@ STATUS_NAMES = {GF_OK: "GF_OK", GF_EINVAL: "GF_EINVAL", GF_ECUDA: "GF_ECUDA",
 EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_version",
            "gf_num_candidates", "gf_workspace_size", "gf_fill_g0", "gf_extract_bands",
            "gf_eval_candidates", "gf_select_topk", "gf_apply_update", "gf_profile_begin",
-           "gf_profile_end", "gf_set_update_algo"]
+           "gf_profile_end", "gf_set_update_algo", "gf_refresh", "gf_refresh_workspace_size"]
 
 
 class GfError(RuntimeError):
@@ -89,6 +89,10 @@ def load(path: str = LIB_PATH):
             "gf_profile_begin": (C.c_int32, [P, C.c_int32]),
             "gf_set_update_algo": (C.c_int32, [P, C.c_int32]),
             "gf_fill_g0_static": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, P]),
+            "gf_refresh_workspace_size": (C.c_size_t, [C.POINTER(gf_geom), C.c_int32]),
+            "gf_refresh": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, P, C.c_int32,
+                                       C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_double,
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int32), P, C.c_size_t, P]),
             "gf_profile_end": (C.c_int32, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         }
@@ -197,6 +201,22 @@ class Handle:
 
     def gf_set_update_algo(self, algo: int):
         self._check(self.lib.gf_set_update_algo(self.h, int(algo)))
+
+    def gf_refresh_workspace_size(self, geom, restart: int) -> int:
+        g = geom_struct(geom)
+        return int(self.lib.gf_refresh_workspace_size(C.byref(g), int(restart)))
+
+    def gf_refresh(self, prob: gf_problem, dtype, state, cols, restart, max_iter, tol, ws, ws_bytes,
+                   stream=None):
+        """Returns (resid list of 1 + len(cols), GMRES iterations per column)."""
+        ns = len(cols)
+        ca = (C.c_int32 * max(ns, 1))(*cols)
+        res = (C.c_double * (ns + 1))()
+        its = (C.c_int32 * max(ns, 1))()
+        self._check(self.lib.gf_refresh(self.h, C.byref(prob), int(dtype), _ptr(state), ns, ca, int(restart),
+                                        int(max_iter), float(tol), res, its, _ptr(ws), int(ws_bytes),
+                                        _stream(stream)))
+        return list(res), list(its)[:ns]
 
     def gf_profile_begin(self, max_records: int):
         self._check(self.lib.gf_profile_begin(self.h, int(max_records)))

@@ -98,6 +98,23 @@ class GreedyOptimizer:
         self.h.gf_apply_update(self.probs, self.dtype, self.state, spec, self.idx, self.status,
                                self.fom, self.ws, self.ws_bytes, self._st(), applied=self.applied)
 
+    def refresh(self, cols: Optional[Sequence[int]] = None, nsample: int = 8, restart: int = 30,
+                max_iter: int = 300, tol: float = 1e-12, seed: int = 0):
+        """Drift check of every wavelength: Lippmann-Schwinger residual of E and GMRES re-solves
+        of sampled columns of G (blocking).  Returns a list (per wavelength) of
+        (residuals, iterations)."""
+        if cols is None:
+            rng = np.random.default_rng(seed)
+            cols = sorted(set(int(c) for c in rng.integers(0, self.n, nsample)))
+        need = self.h.gf_refresh_workspace_size(self.geoms[0], restart)
+        if getattr(self, "_rws", None) is None or self._rws.numel() < need:
+            self._rws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        out = []
+        for p in self.probs:
+            out.append(self.h.gf_refresh(p, self.dtype, self.state, list(cols), restart, max_iter, tol,
+                                         self._rws, self._rws.numel(), self._st()))
+        return out
+
     # ---- host readback
     def read_step(self) -> StepResult:
         k = max(1, self.spec.k)

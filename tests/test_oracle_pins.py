@@ -349,3 +349,35 @@ def test_pins_catch_wrong_dfom_index(monkeypatch):
     c = O.candidate(g, wl.spec, state, 7)
     ref = _brute_dfom(g, state, c[0], None)
     assert abs(d_bad[7] - ref) > 1e-6 * max(1, abs(ref))
+
+
+def test_ls_residual_vanishes_for_exact_field_and_measures_a_perturbation():
+    wl = W.small(7, 6)
+    g = wl.geoms[0]
+    state = W.random_state(g.N, seed=9, fill=0.4)
+    _, E = O.brute_force(g, state)
+    assert O.ls_residual(g, state, E) < 1e-14
+    # perturb one pixel's field by delta: residual = ||delta e_j - G0 X delta e_j|| / ||E||
+    j = int(np.flatnonzero(state)[0])
+    delta = 1e-6
+    E2 = E.copy()
+    E2[j] += delta
+    G0 = O.g0_matrix(g)
+    x = np.zeros(g.n)
+    x[:g.N] = state * (g.eps_mat - g.eps_bg)
+    e = np.zeros(g.n, dtype=complex)
+    e[j] = delta
+    expect = np.linalg.norm(e - G0 @ (x * e)) / np.linalg.norm(E2)
+    assert abs(O.ls_residual(g, state, E2) - expect) < 1e-12
+
+
+def test_exact_columns_solve_the_dyson_system():
+    g = W.small(5, 5).geoms[0]
+    state = W.random_state(g.N, seed=10, fill=0.4)
+    cols = [0, 7, g.N]
+    C = O.exact_columns(g, state, cols)
+    G0 = O.g0_matrix(g)
+    x = np.zeros(g.n)
+    x[:g.N] = state * (g.eps_mat - g.eps_bg)
+    lhs = C - G0 @ (x[:, None] * C)
+    assert np.max(np.abs(lhs - G0[:, cols])) < 1e-13
