@@ -99,10 +99,12 @@ class GreedyOptimizer:
                                self.fom, self.ws, self.ws_bytes, self._st(), applied=self.applied)
 
     def refresh(self, cols: Optional[Sequence[int]] = None, nsample: int = 8, restart: int = 30,
-                max_iter: int = 300, tol: float = 1e-12, seed: int = 0):
+                max_iter: int = 300, tol: Optional[float] = None, seed: int = 0):
         """Drift check of every wavelength: Lippmann-Schwinger residual of E and GMRES re-solves
         of sampled columns of G (blocking).  Returns a list (per wavelength) of
         (residuals, iterations)."""
+        if tol is None:                      # well below the storage precision of G
+            tol = 1e-12 if self.dtype == B.GF_C128 else 1e-8
         if cols is None:
             rng = np.random.default_rng(seed)
             cols = sorted(set(int(c) for c in rng.integers(0, self.n, nsample)))
