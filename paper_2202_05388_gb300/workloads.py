@@ -122,6 +122,14 @@ def brush_320_topk() -> Workload:
                     CandidateSpec(KIND_BRUSH2, DIR_FILL | DIR_CLEAR, 32, 3), 1500, "c64")
 
 
+def brush_320_c128() -> Workload:
+    """The 320x320 geometry of brush_320_topk with the plain FP64 form: complex128 G
+    (168 GB), one brush (rank 4) per step -- the comparison point for the mixed form."""
+    w = brush_320_topk()
+    return Workload("brush_320x320_p4_c128", w.geoms, CandidateSpec(KIND_BRUSH2, DIR_FILL | DIR_CLEAR, 1),
+                    w.steps, "c128")
+
+
 def brush_128_topk() -> Workload:
     """128x128 member of the top-32 complex64 family (G = 2.1 GB), for profiling."""
     nx = ny = 128
