@@ -52,6 +52,7 @@ def parse():
 def workload(name):
     return {"brush_192": W.brush_192, "plain_32": W.plain_32, "brush_64": W.brush_64,
             "brush_128_topk": W.brush_128_topk, "brush_320_c128": W.brush_320_c128,
+            "brush_320_c64_rank4": W.brush_320_c64_rank4,
             "brush_320_topk": W.brush_320_topk, "multilambda_512x64": W.multi_lambda_512x64}[name]()
 
 
@@ -247,9 +248,28 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------ native
+def sched_json(s):
+    if s.fused:
+        return {"fused": True, "groups": max(1, s.nstreams), "update_ctas": s.update_ctas or "default"}
+    return {"fused": False, "streams": s.nstreams, "order": s.order}
+
+
+def launches_per_step(s, nprob, dtype):
+    """Library kernels per batched step: fused = one launch per stage and per group of 64
+    problems (eval, select, capacitance, panels, [digit prep], update, finish, bands); stream
+    branches = the single-problem sequence per problem (eval, select, capacitance, panels,
+    [2 digit preps], update, finish, bands)."""
+    if s.fused:
+        groups = max(1, s.nstreams)
+        per_group = -(-nprob // groups)
+        return groups * ((per_group + 63) // 64) * (8 if dtype == "c128" else 7)
+    return nprob * (9 if dtype == "c128" else 7)
+
+
 def run_batch(args):
     """48 independent single-pixel problems (seeded sizes) advanced together: autotuned
-    fork-join schedule, K steps captured in one CUDA graph and replayed in the timed region."""
+    schedule (fused batch launches or fork-join stream branches), K steps captured in one CUDA
+    graph and replayed in the timed region."""
     import torch
     from paper_2202_05388_gb300 import build as BLD
     from paper_2202_05388_gb300.batch import BatchOptimizer
@@ -285,11 +305,12 @@ def run_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if dtype == "c128" else "f32",
             "data": "synthetic",
             "config": {"workload": f"batch48_single_pixel_{dtype}", "problems": len(wls), "sum_G_GB": sumG / 1e9,
-                       "storage": dtype, "schedule": {"streams": best.nstreams, "order": best.order},
-                       "autotune_ms_per_step": [[t[0].nstreams, t[0].order, t[1]] for t in bo.timings],
+                       "storage": dtype, "schedule": sched_json(best),
+                       "autotune_ms_per_step": [[sched_json(t[0]), t[1]] for t in bo.timings],
                        "graph": f"{args.steps} steps of all problems in one CUDA graph",
                        "l2": "inputs larger than L2 (sum of G %.1f GB)" % (sumG / 1e9)},
             "accepted_flips": flips,
+            "gpu_launches": launches_per_step(best, len(wls), dtype) * args.steps,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s", "frac": gbs / peak_hbm,
                          "traffic": None, "peak_kind": peak_kind,
                          "note": "whole step (all kernels of all problems): algorithmic G bytes / step time"},
@@ -455,6 +476,10 @@ def run_native(args):
                 "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind,
                 "kernel": "k_rank_update_ozaki (tcgen05 digit products, TMA tiles) + operand prep",
                 "fp64_pipe_note": "the same update on native DFMA is FP64-pipe bound; see dfma_update"}
+    elif wl.spec.k * (4 if wl.spec.kind == 1 else 1) <= 4:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
+                "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "k_rank_update_c64_fp32 (rank <= 4, FP32 FMA stream on the CUDA cores)"}
     else:
         f16_peak, f16_kind = f16_peak_tflops()
         roof = {"bound": "tensor", "achieved": achieved_tfl, "peak": f16_peak, "unit": "TFLOP/s",
@@ -465,7 +490,15 @@ def run_native(args):
     roof["algorithmic_bytes_per_launch"] = bytes_per_launch
     roof["kernel_ms_avg"] = kern_avg_ms
     roof["kernel_share_of_step"] = kern_ms / ms
-    per_step_launches = 4 + 2 * nlam + 1          # eval, select, capacitance, panels, finish + per-wavelength update and bands
+    # library kernels per step: eval, select (k = 1: one; top-k: begin + k passes + end),
+    # capacitance, panels, finish, then per wavelength the update's launches and the bands
+    pmax = wl.spec.k * (4 if wl.spec.kind == 1 else 1)
+    sel = 1 if wl.spec.k <= 1 else wl.spec.k + 2
+    if wl.dtype == "c128":
+        upd = 3 if pmax <= 4 else 1                # digit prep rows + cols + tensor-core update, or DFMA
+    else:
+        upd = 1 if pmax <= 4 else 4                # FP32 stream, or inverse + S GEMM + prep + tensor-core update
+    per_step_launches = 4 + sel + nlam * (upd + 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.dtype == "c128" else "f32",

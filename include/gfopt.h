@@ -181,14 +181,56 @@ gf_status gf_refresh(gf_handle* h, const gf_problem* prob, int32_t dtype, const 
                      double tol, double* resid_out, int32_t* iters_out, void* ws, size_t ws_bytes,
                      void* stream);
 
-/* Arithmetic of the complex128 G update (Eq. 10).  GF_UPDATE_TC (default): exact digit
- * products on the tensor cores with an integer recombination (FP64-accurate to ~2^-50 of
- * |C0||S|; used for p <= 4, larger p falls back to DFMA).  GF_UPDATE_DFMA: native FP64 FMA.
- * Both match the FP64 oracle within 1e-10; they differ only in speed on GB300 (whose FP64
- * pipe is 1/64 of its FP32 rate).  Applies to later gf_apply_update calls on h. */
+/* Arithmetic of the G update (Eq. 10).  GF_UPDATE_TC (default), the fast form per case:
+ *   complex128, p <= 4: exact digit products on the tensor cores with an integer
+ *     recombination (FP64-accurate to ~2^-50 of |C0||S|); larger p: native FP64 FMA;
+ *   complex64, p <= 4: FP32 FMA on the CUDA cores (a pure HBM stream);
+ *   complex64, 4 < p <= 128: the Woodbury form S = D A^-1 G[V,:] and a scaled split-FP16
+ *     tensor-core GEMM with FP32 accumulation.
+ * GF_UPDATE_DFMA: native FP64 FMA for every case (complex64 storage rounded once per entry).
+ * The complex128 forms match the FP64 oracle within 1e-10; they differ only in speed on GB300
+ * (whose FP64 pipe is 1/64 of its FP32 rate).  Applies to later gf_apply_update calls on h. */
 #define GF_UPDATE_TC   0
 #define GF_UPDATE_DFMA 1
 gf_status gf_set_update_algo(gf_handle* h, int32_t algo);
+
+/* Batches: many independent problems advanced together (the problems of a design study, e.g.
+ * sweeps over sizes, wavelengths and focal distances; the paper parallelises one problem's
+ * partitions instead, Sec. III).  Each item is one single-wavelength problem with its own
+ * design state, step buffers and workspace -- the arguments of the single-problem calls.  One
+ * gf_batch_step runs a whole greedy step (dFOM of every candidate, greedy selection, capacitance
+ * solve, panels, G and E update, band extraction) for every item with one launch per stage: the
+ * G update is one persistent launch over the tiles of all items that accepted a flip.  The
+ * step only enqueues kernels (no host synchronisation, no copies), so it can be captured in a
+ * CUDA graph.  Limits: k = 1 (rank <= 4), 1 to 64 items, shared dtype and candidate spec.
+ * The items' buffers must stay valid until gf_batch_destroy. */
+typedef struct gf_batch_item {
+  gf_problem prob;      /* one wavelength: geometry, G (n x ldg), E (n), bands (9 N) */
+  uint8_t* state;       /* N bytes, 0 = eps_bg, 1 = eps_mat */
+  double* dfom;         /* gf_num_candidates(&prob.geom, spec) doubles */
+  int32_t* idx;         /* 1: chosen candidate id (-1: none) */
+  double* val;          /* 1: its dFOM */
+  int32_t* status;      /* 1: device status word of this item */
+  double* fom_out;      /* 1: FOM after the step */
+  int32_t* applied;     /* 1: candidates applied by the step; may be NULL */
+  void* ws;             /* gf_workspace_size(&prob.geom, 1, dtype, spec) bytes, 256-byte aligned */
+  size_t ws_bytes;
+} gf_batch_item;
+typedef struct gf_batch gf_batch;
+/* Device bytes of the item table of a batch of nitems. */
+size_t gf_batch_table_size(int32_t nitems);
+/* Validate every item like the single-problem calls, write the item table to `table` (device,
+ * 256-byte aligned, gf_batch_table_size bytes, owned by the caller) and build the launch
+ * parameters (one TMA descriptor per complex128 G).  Blocking (synchronises `stream`). */
+gf_status gf_batch_create(gf_handle* h, int32_t nitems, const gf_batch_item* items, int32_t dtype,
+                          const gf_cand_spec* spec, void* table, size_t table_bytes, void* stream,
+                          gf_batch** out);
+/* Enqueue one greedy step of every item on `stream` (capturable). */
+gf_status gf_batch_step(gf_batch* b, void* stream);
+/* Launch shape of the persistent G update: update_ctas CTAs (0: one per SM for complex128,
+ * three per SM for complex64).  Used by the autotuner; results do not depend on it. */
+gf_status gf_batch_set_schedule(gf_batch* b, int32_t update_ctas);
+void gf_batch_destroy(gf_batch* b);
 
 /* Kernel timing (no counterpart in the paper; it backs the per-step timers of the bench).
  * gf_profile_begin arms up to max_records CUDA-event pairs that the library records on the

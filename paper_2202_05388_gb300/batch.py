@@ -1,11 +1,18 @@
 """Many independent design problems advanced together (the batched pattern of the greedy
-step): every problem runs its own evaluate / select / update sequence as one branch of a
-fork-join over CUDA streams, and a whole run of steps is captured once into a CUDA graph and
-replayed, so the per-kernel launch cost of the small problems disappears and the problems'
-kernels overlap on the GPU.  An autotuner picks the number of concurrent branches and their
-order by timing graph replays.
+step).  Two schedules run the same kernels' arithmetic:
 
-Nothing here computes: the steps are the libgfopt kernels driven through GreedyOptimizer.
+  * fused: the library's batch entry points -- one launch per stage of the step for all
+    problems (64 per launch), the G update being one persistent launch over the tiles of
+    every problem that accepted a flip;
+  * streams: every problem runs its own evaluate / select / update sequence as one branch of
+    a fork-join over CUDA streams.
+
+Either way a run of steps is captured once into a CUDA graph and replayed, so launch cost
+disappears, and an autotuner picks the schedule (fused with a given number of update CTAs,
+or streams with a branch count and order) by timing graph replays.
+
+Nothing here computes: the steps are libgfopt kernels (through the gf_batch_* calls or
+GreedyOptimizer).
 """
 from __future__ import annotations
 
@@ -22,8 +29,11 @@ from .workloads import Workload
 
 @dataclass
 class Schedule:
-    nstreams: int          # concurrent branches (problems are dealt round-robin onto them)
-    order: str             # "given" or "largest_first"
+    nstreams: int          # streams: concurrent branches (problems are dealt round-robin onto them)
+    order: str             # streams: "given" or "largest_first"
+    fused: bool = False    # True: the library's batch entry points; nstreams >= 2 then splits the
+                           # problems into that many size-balanced groups on their own streams
+    update_ctas: int = 0   # fused: CTAs of the persistent G update (0: the library's default)
 
 
 class BatchOptimizer:
@@ -34,11 +44,59 @@ class BatchOptimizer:
         self.opts = [GreedyOptimizer(w.geoms, w.spec, dtype=dtype, device=device, handle=self.h)
                      for w in self.workloads]
         self.sizes = [o.n for o in self.opts]
-        self.schedule = Schedule(min(8, len(self.opts)), "largest_first")
+        self.schedule = Schedule(0, "given", fused=True)
         self._streams: List[torch.cuda.Stream] = []
         self._graph: Optional[torch.cuda.CUDAGraph] = None
         self._graph_steps = 0
         self.applied = torch.zeros(len(self.opts), dtype=torch.int64, device=self.device)
+        self._batches = None
+        self._batch_groups = 0
+        self.fusable = all(o.spec.k == 1 and len(o.geoms) == 1 for o in self.opts)
+        if not self.fusable:
+            self.schedule = Schedule(min(8, len(self.opts)), "largest_first")
+
+    # ---- the library's batch objects (created on first fused use, per group count)
+    def _ensure_batches(self):
+        groups = max(1, self.schedule.nstreams)
+        if self._batches is not None and self._batch_groups == groups:
+            return
+        self.close()
+        self._applied_step = torch.zeros(len(self.opts), dtype=torch.int32, device=self.device)
+        by_size = sorted(range(len(self.opts)), key=lambda i: -self.sizes[i])
+        self._batches = []          # list (per group) of gf_batch handles
+        self._tables = []
+        self._batch_groups = groups
+        st = torch.cuda.current_stream(self.device)
+        for g in range(groups):
+            members = sorted(by_size[g::groups])
+            handles = []
+            for c0 in range(0, len(members), B.BATCH_MAX):
+                items = []
+                for i in members[c0:c0 + B.BATCH_MAX]:
+                    o = self.opts[i]
+                    items.append(B.gf_batch_item(o.probs[0], o.state.data_ptr(), o.dfom.data_ptr(),
+                                                 o.idx.data_ptr(), o.val.data_ptr(), o.status.data_ptr(),
+                                                 o.fom.data_ptr(), self._applied_step[i:i + 1].data_ptr(),
+                                                 o.ws.data_ptr(), o.ws_bytes))
+                tb = self.h.gf_batch_table_size(len(items))
+                table = torch.empty(tb, dtype=torch.uint8, device=self.device)
+                self._tables.append(table)
+                handles.append(self.h.gf_batch_create(items, self.opts[0].dtype, self.opts[0].spec, table, tb, st))
+            if handles:
+                self._batches.append(handles)
+
+    def close(self):
+        if self._batches:
+            for handles in self._batches:
+                for b in handles:
+                    self.h.gf_batch_destroy(b)
+        self._batches = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
     # ---- set-up
     def fill(self):
@@ -52,12 +110,34 @@ class BatchOptimizer:
             idx.sort(key=lambda i: -self.sizes[i])
         return idx
 
-    def _ensure_streams(self):
-        while len(self._streams) < self.schedule.nstreams:
+    def _ensure_streams(self, count=None):
+        while len(self._streams) < (self.schedule.nstreams if count is None else count):
             self._streams.append(torch.cuda.Stream(self.device))
 
-    # ---- one step of every problem, enqueued as a fork-join on the current stream
+    # ---- one step of every problem, enqueued on the current stream
     def enqueue_step(self):
+        if self.schedule.fused:
+            self._ensure_batches()
+            main = torch.cuda.current_stream(self.device)
+            if len(self._batches) == 1:
+                for b in self._batches[0]:
+                    self.h.gf_batch_set_schedule(b, self.schedule.update_ctas)
+                    self.h.gf_batch_step(b, main)
+            else:
+                self._ensure_streams(len(self._batches))
+                start = torch.cuda.Event()
+                start.record(main)
+                for g, handles in enumerate(self._batches):
+                    st = self._streams[g]
+                    st.wait_event(start)
+                    for b in handles:
+                        self.h.gf_batch_set_schedule(b, self.schedule.update_ctas)
+                        self.h.gf_batch_step(b, st)
+                    done = torch.cuda.Event()
+                    done.record(st)
+                    main.wait_event(done)
+            self.applied += self._applied_step
+            return
         self._ensure_streams()
         main = torch.cuda.current_stream(self.device)
         start = torch.cuda.Event()
@@ -102,8 +182,15 @@ class BatchOptimizer:
         problems (the trials are part of the optimisation run)."""
         if candidates is None:
             n = len(self.opts)
-            counts = sorted({c for c in (1, 4, 8, 16, n) if c <= n})
+            counts = sorted({c for c in (1, 8, 16, n) if c <= n})
             candidates = [Schedule(c, o) for c, o in itertools.product(counts, ("given", "largest_first"))]
+            if self.fusable:
+                sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+                if self.opts[0].dtype == B.GF_C128:     # one update CTA fits an SM
+                    fused = [(1, sms), (2, sms // 2), (2, sms), (4, sms // 4)]
+                else:
+                    fused = [(1, 3 * sms), (1, 6 * sms), (2, 3 * sms), (4, 3 * sms)]
+                candidates = [Schedule(g, "given", True, c) for g, c in fused] + candidates
         best, best_ms = None, float("inf")
         self.timings = []
         for sch in candidates:

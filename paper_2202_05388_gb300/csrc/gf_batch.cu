@@ -1,0 +1,165 @@
+// Host side of the batch entry points: many independent single-wavelength problems advanced
+// by one launch per stage of the greedy step (Fig. 1: evaluate every candidate, select,
+// update).  The item table lives in caller-owned device memory; the complex128 update's TMA
+// descriptors live in a host parameter block that every step passes to the persistent
+// tensor-core launch.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "gf_internal.cuh"
+
+struct gf_batch {
+  gf_handle* h;
+  int nitems;
+  int dtype;
+  gf_cand_spec spec;
+  gf::BatchItem* table;            // device
+  std::vector<gf::BatchItem> host; // host copy
+  void* oz_params;                 // complex128: parameter block of the persistent update
+  int64_t widest_n, widest_N, widest_units;
+  int update_ctas;
+};
+
+static gf_status bfail(gf_handle* h, gf_status s, const char* fmt, int a = 0, long long b = 0, long long c = 0) {
+  char msg[256];
+  snprintf(msg, sizeof msg, fmt, a, b, c);
+  return gf::api_fail_msg(h, s, msg);
+}
+
+extern "C" {
+
+size_t gf_batch_table_size(int32_t nitems) {
+  if (nitems < 1 || nitems > gf::kBatchMax) return 0;
+  return ((size_t)nitems * sizeof(gf::BatchItem) + 255) & ~(size_t)255;
+}
+
+gf_status gf_batch_create(gf_handle* h, int32_t nitems, const gf_batch_item* items, int32_t dtype,
+                          const gf_cand_spec* spec, void* table, size_t table_bytes, void* stream,
+                          gf_batch** out) {
+  if (!h) return GF_EINVAL;
+  if (!out) return bfail(h, GF_EINVAL, "output pointer is NULL");
+  *out = nullptr;
+  if (nitems < 1 || nitems > gf::kBatchMax) return bfail(h, GF_EINVAL, "nitems must be in [1, %d]", gf::kBatchMax);
+  if (!items) return bfail(h, GF_EINVAL, "items array is NULL");
+  if (dtype != GF_C128 && dtype != GF_C64) return bfail(h, GF_EINVAL, "unknown dtype %d", dtype);
+  if (!spec) return bfail(h, GF_EINVAL, "candidate spec is NULL");
+  if (spec->k != 1) return bfail(h, GF_EINVAL, "batches take k = 1 (got %d)", spec->k);
+  if (!table || ((uintptr_t)table & 255u)) return bfail(h, GF_EINVAL, "table must be non-NULL and 256-byte aligned");
+  if (table_bytes < gf_batch_table_size(nitems))
+    return bfail(h, GF_ENOMEM, "table has %d bytes too few", (int)(gf_batch_table_size(nitems) - table_bytes));
+  gf_batch* b = new (std::nothrow) gf_batch;
+  if (!b) return bfail(h, GF_ENOMEM, "out of host memory");
+  b->h = h;
+  b->nitems = nitems;
+  b->dtype = dtype;
+  b->spec = *spec;
+  b->table = reinterpret_cast<gf::BatchItem*>(table);
+  b->oz_params = nullptr;
+  b->widest_n = b->widest_N = b->widest_units = 0;
+  b->update_ctas = 0;
+  b->host.resize(nitems);
+  for (int i = 0; i < nitems; ++i) {
+    const gf_batch_item& it = items[i];
+    gf_status s = gf::api_check_problem(h, &it.prob, dtype);
+    if (!s) s = gf::api_check_spec(h, &it.prob.geom, spec);
+    if (s) { delete b; return s; }
+    if (!it.state || !it.dfom || !it.idx || !it.val || !it.status || !it.fom_out) {
+      delete b;
+      return bfail(h, GF_EINVAL, "item %d: state, dfom, idx, val, status and fom_out must be non-NULL", i);
+    }
+    const gf::WsLayout L = gf::ws_layout(it.prob.geom, 1, dtype, *spec);
+    if (!it.ws || ((uintptr_t)it.ws & 255u)) {
+      delete b;
+      return bfail(h, GF_EINVAL, "item %d: workspace must be non-NULL and 256-byte aligned", i);
+    }
+    if (it.ws_bytes < L.total) {
+      delete b;
+      return bfail(h, GF_ENOMEM, "item %d: workspace has %lld bytes, needs %lld", i, (long long)it.ws_bytes,
+                   (long long)L.total);
+    }
+    gf::BatchItem& d = b->host[i];
+    d.G = it.prob.G;
+    d.ldg = it.prob.ldg;
+    d.E = reinterpret_cast<gf::cplx*>(it.prob.E);
+    d.bands = reinterpret_cast<gf::cplx*>(it.prob.bands);
+    d.nx = it.prob.geom.nx;
+    d.ny = it.prob.geom.ny;
+    d.chi = it.prob.geom.eps_mat - it.prob.geom.eps_bg;
+    d.ws = reinterpret_cast<char*>(it.ws);
+    d.L = L;
+    d.state = it.state;
+    d.dfom = it.dfom;
+    d.ncand = gf_num_candidates(&it.prob.geom, spec);
+    d.idx = it.idx;
+    d.val = it.val;
+    d.status = it.status;
+    d.fom = it.fom_out;
+    d.applied = it.applied;
+    const int64_t N = (int64_t)d.nx * d.ny;
+    const int64_t units = spec->kind == GF_KIND_SINGLE ? N : (int64_t)(d.nx - 1) * (d.ny - 1);
+    if (N + 1 > b->widest_n) b->widest_n = N + 1;
+    if (N > b->widest_N) b->widest_N = N;
+    if (units > b->widest_units) b->widest_units = units;
+  }
+  gf_status s = gf::api_bind_device(h);
+  if (s) { delete b; return s; }
+  if (dtype == GF_C128) {
+    b->oz_params = ::operator new(gf::ozaki_batch_params_bytes(), std::align_val_t(64), std::nothrow);
+    if (!b->oz_params) { delete b; return bfail(h, GF_ENOMEM, "out of host memory"); }
+    if (!gf::ozaki_batch_params(b->oz_params, b->host.data(), nitems)) {
+      ::operator delete(b->oz_params, std::align_val_t(64));
+      delete b;
+      return bfail(h, GF_ECUDA, "cannot encode the TMA descriptors of the batch (driver entry point missing)");
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaMemcpyAsync(table, b->host.data(), sizeof(gf::BatchItem) * (size_t)nitems, cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);
+  s = gf::api_cuda_check(h, "gf_batch_create upload");
+  if (s) {
+    gf_batch_destroy(b);
+    return s;
+  }
+  *out = b;
+  return GF_OK;
+}
+
+gf_status gf_batch_set_schedule(gf_batch* b, int32_t update_ctas) {
+  if (!b) return GF_EINVAL;
+  if (update_ctas < 0 || update_ctas > 65535) return bfail(b->h, GF_EINVAL, "update_ctas must be in [0, 65535]");
+  b->update_ctas = update_ctas;
+  return GF_OK;
+}
+
+gf_status gf_batch_step(gf_batch* b, void* stream) {
+  if (!b) return GF_EINVAL;
+  gf_status s = gf::api_bind_device(b->h);
+  if (s) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = b->nitems;
+  const int sms = gf::api_sm_count(b->h);
+  gf::launch_eval_batch(b->table, n, b->dtype, b->spec, b->widest_units, st);
+  gf::launch_select_batch(b->table, n, b->spec.tie_rel, st);
+  gf::launch_capacitance_batch(b->table, n, b->dtype, b->spec, st);
+  gf::launch_panels_batch(b->table, n, b->dtype, b->widest_n, st);
+  if (b->dtype == GF_C128) {
+    gf::launch_oz_prep_batch(b->table, n, b->widest_n, st);
+    gf::launch_rank_update_ozaki_batch(b->oz_params, b->update_ctas > 0 ? b->update_ctas : sms, st);
+  } else {
+    gf::launch_rank_update_c64_fp32_batch(b->table, n, b->update_ctas > 0 ? b->update_ctas : 3 * sms, st);
+  }
+  gf::launch_finish_batch(b->table, n, b->dtype, b->widest_n, st);
+  gf::launch_bands_batch(b->table, n, b->dtype, b->widest_N, st);
+  return gf::api_cuda_check(b->h, "gf_batch_step launch");
+}
+
+void gf_batch_destroy(gf_batch* b) {
+  if (!b) return;
+  if (b->oz_params) ::operator delete(b->oz_params, std::align_val_t(64));
+  delete b;
+}
+
+}  // extern "C"

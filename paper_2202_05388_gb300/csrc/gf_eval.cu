@@ -66,8 +66,8 @@ __device__ __forceinline__ bool solve_small(cplx (&A)[P][P], cplx (&b)[P], const
 }
 
 // Single-pixel candidates: id = j.  p = 1, so Eq. 9 is y = E_j / (1 - G_jj d_chi).
-__global__ void k_eval_single(EvalArgs a, const uint8_t* __restrict__ state, int dir_mask,
-                              double* __restrict__ dfom) {
+__device__ __forceinline__ void eval_single_body(const EvalArgs& a, const uint8_t* __restrict__ state,
+                                                 int dir_mask, double* __restrict__ dfom) {
   const int64_t N = (int64_t)a.nx * a.ny;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
        j += (int64_t)gridDim.x * blockDim.x) {
@@ -96,8 +96,8 @@ __global__ void k_eval_single(EvalArgs a, const uint8_t* __restrict__ state, int
 // 2x2 brush candidates: id = dir*P + a, anchor a = iy*(nx-1) + ix; pixels
 // q0 = (ix,iy), q1 = (ix+1,iy), q2 = (ix,iy+1), q3 = (ix+1,iy+1).  One thread evaluates both
 // directions of its anchor.
-__global__ void __launch_bounds__(128) k_eval_brush(EvalArgs a, const uint8_t* __restrict__ state,
-                                                    int dir_mask, double* __restrict__ dfom) {
+__device__ __forceinline__ void eval_brush_body(const EvalArgs& a, const uint8_t* __restrict__ state,
+                                                int dir_mask, double* __restrict__ dfom) {
   const int nx = a.nx;
   const int64_t N = (int64_t)nx * a.ny;
   const int64_t P = (int64_t)(nx - 1) * (a.ny - 1);
@@ -160,6 +160,66 @@ __global__ void __launch_bounds__(128) k_eval_brush(EvalArgs a, const uint8_t* _
     dfom[an] = valid[0] ? total[0] : -INFINITY;
     dfom[P + an] = valid[1] ? total[1] : -INFINITY;
   }
+}
+
+__global__ void k_eval_single(EvalArgs a, const uint8_t* __restrict__ state, int dir_mask,
+                              double* __restrict__ dfom) {
+  eval_single_body(a, state, dir_mask, dfom);
+}
+
+__global__ void __launch_bounds__(128) k_eval_brush(EvalArgs a, const uint8_t* __restrict__ state,
+                                                    int dir_mask, double* __restrict__ dfom) {
+  eval_brush_body(a, state, dir_mask, dfom);
+}
+
+// Batched forms: blockIdx.y selects the problem of the device table; the x dimension strides
+// over that problem's pixels or anchors exactly as in the single-problem kernels.
+__device__ __forceinline__ void batch_eval_args(const BatchItem* items, int dtype, EvalArgs& sa,
+                                                const uint8_t*& s_state, double*& s_dfom) {
+  if (threadIdx.x == 0) {
+    const BatchItem& it = items[blockIdx.y];
+    sa.nlam = 1;
+    sa.dtype = dtype;
+    sa.nx = it.nx;
+    sa.ny = it.ny;
+    sa.chi = it.chi;
+    sa.lam[0].G = it.G;
+    sa.lam[0].ldg = it.ldg;
+    sa.lam[0].E = it.E;
+    sa.lam[0].bands = it.bands;
+    s_state = it.state;
+    s_dfom = it.dfom;
+  }
+  __syncthreads();
+}
+
+__global__ void k_eval_single_batch(const BatchItem* __restrict__ items, int dtype, int dir_mask) {
+  __shared__ EvalArgs sa;
+  __shared__ const uint8_t* s_state;
+  __shared__ double* s_dfom;
+  batch_eval_args(items, dtype, sa, s_state, s_dfom);
+  eval_single_body(sa, s_state, dir_mask, s_dfom);
+}
+
+__global__ void __launch_bounds__(128) k_eval_brush_batch(const BatchItem* __restrict__ items, int dtype,
+                                                          int dir_mask) {
+  __shared__ EvalArgs sa;
+  __shared__ const uint8_t* s_state;
+  __shared__ double* s_dfom;
+  batch_eval_args(items, dtype, sa, s_state, s_dfom);
+  eval_brush_body(sa, s_state, dir_mask, s_dfom);
+}
+
+void launch_eval_batch(const BatchItem* items, int nprob, int dtype, const gf_cand_spec& spec, int64_t widest,
+                       cudaStream_t st) {
+  const int threads = spec.kind == GF_KIND_SINGLE ? 256 : 128;
+  int64_t b = (widest + threads - 1) / threads;       // widest: pixels (single) or anchors (brush)
+  if (b > 1216) b = 1216;
+  dim3 grid((unsigned)(b < 1 ? 1 : b), (unsigned)nprob);
+  if (spec.kind == GF_KIND_SINGLE)
+    k_eval_single_batch<<<grid, threads, 0, st>>>(items, dtype, spec.dir_mask);
+  else
+    k_eval_brush_batch<<<grid, threads, 0, st>>>(items, dtype, spec.dir_mask);
 }
 
 void launch_eval(const EvalArgs& a, const uint8_t* state, const gf_cand_spec& spec, double* dfom,

@@ -107,8 +107,8 @@ __global__ void k_fill_field(int nx, int ny, double dx, double k, double my, cpl
   }
 }
 
-__global__ void k_bands(int nx, int ny, int dtype, const void* __restrict__ G, int64_t ldg,
-                        cplx* __restrict__ bands) {
+__device__ __forceinline__ void bands_body(int nx, int ny, int dtype, const void* __restrict__ G, int64_t ldg,
+                                           cplx* __restrict__ bands) {
   const int64_t N = (int64_t)nx * ny;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < GF_NBANDS * N;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -122,6 +122,23 @@ __global__ void k_bands(int nx, int ny, int dtype, const void* __restrict__ G, i
     if (jx >= 0 && jx < nx && jy >= 0 && jy < ny) v = ldG(G, dtype, ldg, i, (int64_t)jy * nx + jx);
     bands[t] = v;
   }
+}
+
+__global__ void k_bands(int nx, int ny, int dtype, const void* __restrict__ G, int64_t ldg,
+                        cplx* __restrict__ bands) {
+  bands_body(nx, ny, dtype, G, ldg, bands);
+}
+
+// Batched band extraction: blockIdx.y selects the problem of the device table.
+__global__ void k_bands_batch(const BatchItem* __restrict__ items, int dtype) {
+  const BatchItem& it = items[blockIdx.y];
+  bands_body(it.nx, it.ny, dtype, it.G, it.ldg, it.bands);
+}
+
+void launch_bands_batch(const BatchItem* items, int nprob, int dtype, int64_t widest, cudaStream_t st) {
+  int64_t b = (GF_NBANDS * widest + 255) / 256;      // widest: pixels of the largest problem
+  if (b > 1216) b = 1216;
+  k_bands_batch<<<dim3((unsigned)(b < 1 ? 1 : b), (unsigned)nprob), 256, 0, st>>>(items, dtype);
 }
 
 static int grid_for(int64_t work, int threads) {

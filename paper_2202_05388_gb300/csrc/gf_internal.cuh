@@ -111,6 +111,8 @@ gf_status api_bind_device(gf_handle* h);
 gf_status api_cuda_check(gf_handle* h, const char* where);
 gf_status api_fail_msg(gf_handle* h, gf_status s, const char* msg);
 int api_device(const gf_handle* h);
+int api_sm_count(const gf_handle* h);
+gf_status api_check_spec(gf_handle* h, const gf_geom* g, const gf_cand_spec* s);
 
 // ----------------------------------------------------------------------------- kernels
 void launch_fill_table(const gf_geom& g, cplx* table, cudaStream_t st);
@@ -187,5 +189,64 @@ gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int n
 void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state,
                    const gf_cand_spec& spec, const int32_t* idx, int32_t* status, double* fom_out,
                    int32_t* applied, cudaStream_t st, KernelTimer* timer);
+
+// ----------------------------------------------------------------------------- batches
+// One problem of a batch (single wavelength, rank <= 4 steps), as the batched kernels read it
+// from the device table: blockIdx.y of a batched launch selects the problem.
+constexpr int kBatchMax = 64;        // problems per batched launch
+struct BatchItem {
+  void* G;
+  int64_t ldg;
+  cplx* E;
+  cplx* bands;
+  int32_t nx, ny;
+  double chi;
+  char* ws;
+  WsLayout L;
+  uint8_t* state;
+  double* dfom;
+  int64_t ncand;
+  int32_t* idx;
+  double* val;
+  int32_t* status;
+  double* fom;
+  int32_t* applied;
+};
+__device__ __forceinline__ void batch_upd_args(const BatchItem& it, int dtype, UpdArgs& a) {
+  a.nlam = 1;
+  a.dtype = dtype;
+  a.nx = it.nx;
+  a.ny = it.ny;
+  a.chi = it.chi;
+  a.pmax = it.L.pmax;
+  a.algo = GF_UPDATE_TC;
+  a.sm_count = 0;
+  a.lam[0].G = it.G;
+  a.lam[0].ldg = it.ldg;
+  a.lam[0].E = it.E;
+  a.lam[0].bands = it.bands;
+}
+// each launcher covers problems [0, nprob) of the device table; `widest` is the largest
+// per-problem extent of the launch's x dimension (pixels, candidates or rows)
+void launch_eval_batch(const BatchItem* items, int nprob, int dtype, const gf_cand_spec& spec, int64_t widest,
+                       cudaStream_t st);
+void launch_select_batch(const BatchItem* items, int nprob, double tie_rel, cudaStream_t st);
+void launch_capacitance_batch(const BatchItem* items, int nprob, int dtype, const gf_cand_spec& spec,
+                              cudaStream_t st);
+void launch_panels_batch(const BatchItem* items, int nprob, int dtype, int64_t widest, cudaStream_t st);
+void launch_finish_batch(const BatchItem* items, int nprob, int dtype, int64_t widest, cudaStream_t st);
+void launch_bands_batch(const BatchItem* items, int nprob, int dtype, int64_t widest, cudaStream_t st);
+// complex64 rank <= 4 update in FP32 on the CUDA cores (HBM-bound streaming)
+void launch_rank_update_c64_fp32_batch(const BatchItem* items, int nprob, int ctas, cudaStream_t st);
+void launch_rank_update_c64_fp32(float2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0, const cplx* S,
+                                 const UpdCtl* ctl, int32_t* prof_p, int ctas, cudaStream_t st);
+constexpr int kC64Fp32MaxP = 4;
+// complex128 rank <= 4 update on the tensor cores for a whole batch: the operand preparation
+// of every problem, then one persistent launch over all problems' tiles.  The parameter block
+// (tensor maps and descriptors) is built once per batch by ozaki_batch_params.
+size_t ozaki_batch_params_bytes();
+bool ozaki_batch_params(void* out, const BatchItem* host_items, int nprob);
+void launch_oz_prep_batch(const BatchItem* items, int nprob, int64_t widest, cudaStream_t st);
+void launch_rank_update_ozaki_batch(const void* params, int ctas, cudaStream_t st);
 
 }  // namespace gf

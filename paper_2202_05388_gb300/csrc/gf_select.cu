@@ -57,9 +57,8 @@ __device__ __forceinline__ void cand_anchor(int64_t c, int kind, int nx, int64_t
 }
 
 // Greedy policy: m = max dfom; lowest id with dfom >= m - tie_rel |m|.
-__global__ void __launch_bounds__(kSelThreads) k_select_best(const double* __restrict__ dfom, int64_t ncand,
-                                                             double tie_rel, int32_t* idx, double* val,
-                                                             int32_t* status) {
+__device__ __forceinline__ void select_best_body(const double* __restrict__ dfom, int64_t ncand, double tie_rel,
+                                                 int32_t* idx, double* val, int32_t* status) {
   double bv = -INFINITY;
   int64_t bid = INT64_MAX;
   for (int64_t c = threadIdx.x; c < ncand; c += blockDim.x) {
@@ -84,6 +83,23 @@ __global__ void __launch_bounds__(kSelThreads) k_select_best(const double* __res
     val[0] = dfom[first];
     *status = GF_OK;
   }
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_select_best(const double* __restrict__ dfom, int64_t ncand,
+                                                             double tie_rel, int32_t* idx, double* val,
+                                                             int32_t* status) {
+  select_best_body(dfom, ncand, tie_rel, idx, val, status);
+}
+
+// Batched greedy selection: one CTA per problem of the device table.
+__global__ void __launch_bounds__(kSelThreads) k_select_best_batch(const BatchItem* __restrict__ items,
+                                                                   double tie_rel) {
+  const BatchItem& it = items[blockIdx.x];
+  select_best_body(it.dfom, it.ncand, tie_rel, it.idx, it.val, it.status);
+}
+
+void launch_select_batch(const BatchItem* items, int nprob, double tie_rel, cudaStream_t st) {
+  k_select_best_batch<<<nprob, kSelThreads, 0, st>>>(items, tie_rel);
 }
 
 // Top-k with exclusion: repeatedly take the best (dfom, id) candidate that is positive and

@@ -52,8 +52,9 @@ __device__ int cand_pixels(int64_t c, int kind, int dir_mask, int nx, int ny, do
 }
 
 // Single CTA.  The p x p matrices live in the workspace (p can reach 4k).
-__global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __restrict__ state,
-                              const int32_t* __restrict__ idx, int32_t* status) {
+__device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayout& L, char* ws,
+                                                 const uint8_t* __restrict__ state,
+                                                 const int32_t* __restrict__ idx, int32_t* status) {
   UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
   int32_t* V = reinterpret_cast<int32_t*>(ws + L.V);
   double* dchi = reinterpret_cast<double*>(ws + L.dchi);
@@ -242,9 +243,14 @@ __global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __
   }
 }
 
+__global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __restrict__ state,
+                              const int32_t* __restrict__ idx, int32_t* status) {
+  capacitance_body(a, L, ws, state, idx, status);
+}
+
 // ----------------------------------------------------------------------------- panels
 // Column j: R[:, j] = A^{-1} G[V, j] (Eq. 14) and S[:, j] = D R[:, j]; row j: C0[j, :] = G[j, V].
-__global__ void k_panels(UpdArgs a, WsLayout L, char* ws, int want_S) {
+__device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L, char* ws, int want_S) {
   const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
   if (ctl->skip) return;
   const int p = ctl->nv;
@@ -325,6 +331,8 @@ __global__ void k_panels(UpdArgs a, WsLayout L, char* ws, int want_S) {
   }
 }
 
+__global__ void k_panels(UpdArgs a, WsLayout L, char* ws, int want_S) { panels_body(a, L, ws, want_S); }
+
 // ----------------------------------------------------------------------------- rank-p (FP64)
 constexpr int kUpdThreads = 256;
 constexpr int kUpdRows = 16;
@@ -400,9 +408,130 @@ __global__ void __launch_bounds__(kUpdThreads) k_rank_update_c64_ref(float2* __r
   }
 }
 
+// complex64 storage, rank p <= 4, FP32 arithmetic on the CUDA cores: the update is a pure
+// HBM stream (4p FP32 FMA per 16 bytes moved), so no tensor-core form is needed.  A tile is
+// 32 rows x 512 complex columns; each thread owns two adjacent columns (one 16-byte vector per
+// row) and keeps their S entries in registers; the tile's C0 rows are staged in shared memory.
+// G is touched once per step, so its loads and stores carry the streaming (evict-first) hint
+// and leave L2 to the panels.  Three CTAs fit an SM; launches use a multiple of that.
+constexpr int kF32Threads = 256;
+constexpr int kF32Rows = 32;
+constexpr int kF32Cols = 2 * kF32Threads;
+
+__device__ __forceinline__ void c64_fp32_tile(float2* __restrict__ G, int64_t ldg, int64_t n, int pmax, int p,
+                                              const cplx* __restrict__ C0, const cplx* __restrict__ S,
+                                              int64_t rt, int64_t ct, float2 (*sC)[kC64Fp32MaxP]) {
+  const int64_t i0 = rt * kF32Rows;
+  const int64_t j = ct * kF32Cols + 2 * threadIdx.x;
+  __syncthreads();                                   // previous tile done with sC
+  for (int t = threadIdx.x; t < kF32Rows * kC64Fp32MaxP; t += kF32Threads) {
+    const int r = t / kC64Fp32MaxP, u = t % kC64Fp32MaxP;
+    const int64_t i = i0 + r;
+    cplx c = (i < n && u < p) ? C0[i * pmax + u] : mk(0.0, 0.0);
+    sC[r][u] = make_float2((float)c.re, (float)c.im);
+  }
+  __syncthreads();
+  if (j >= n) return;
+  const bool two = j + 1 < n;
+  float2 s0[kC64Fp32MaxP], s1[kC64Fp32MaxP];
+#pragma unroll
+  for (int u = 0; u < kC64Fp32MaxP; ++u) {
+    cplx a = u < p ? S[(int64_t)u * n + j] : mk(0.0, 0.0);
+    cplx b = (u < p && two) ? S[(int64_t)u * n + j + 1] : mk(0.0, 0.0);
+    s0[u] = make_float2((float)a.re, (float)a.im);
+    s1[u] = make_float2((float)b.re, (float)b.im);
+  }
+  const int rows = (int)(n - i0 < kF32Rows ? n - i0 : kF32Rows);
+  constexpr int U = 8;
+  for (int r0 = 0; r0 < rows; r0 += U) {
+    float4 g[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q)
+      if (r0 + q < rows) g[q] = __ldcs(reinterpret_cast<const float4*>(G + (i0 + r0 + q) * ldg + j));
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (r0 + q < rows) {
+        float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+#pragma unroll
+        for (int u = 0; u < kC64Fp32MaxP; ++u) {
+          const float2 c = sC[r0 + q][u];
+          ar = fmaf(c.x, s0[u].x, fmaf(-c.y, s0[u].y, ar));
+          ai = fmaf(c.x, s0[u].y, fmaf(c.y, s0[u].x, ai));
+          br = fmaf(c.x, s1[u].x, fmaf(-c.y, s1[u].y, br));
+          bi = fmaf(c.x, s1[u].y, fmaf(c.y, s1[u].x, bi));
+        }
+        float4 v = g[q];
+        v.x += ar;
+        v.y += ai;
+        if (two) {
+          v.z += br;
+          v.w += bi;
+        }
+        __stcs(reinterpret_cast<float4*>(G + (i0 + r0 + q) * ldg + j), v);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kF32Threads, 3) k_rank_update_c64_fp32(float2* __restrict__ G, int64_t ldg, int64_t n,
+                                                                      int pmax, const cplx* __restrict__ C0,
+                                                                      const cplx* __restrict__ S,
+                                                                      const UpdCtl* __restrict__ ctl,
+                                                                      int32_t* __restrict__ prof_p) {
+  __shared__ float2 sC[kF32Rows][kC64Fp32MaxP];
+  const int p = ctl->skip ? 0 : ctl->nv;
+  if (prof_p && blockIdx.x == 0 && threadIdx.x == 0) *prof_p = p;
+  if (p < 1 || p > kC64Fp32MaxP) return;
+  const int64_t nrt = (n + kF32Rows - 1) / kF32Rows, nct = (n + kF32Cols - 1) / kF32Cols;
+  for (int64_t t = blockIdx.x; t < nrt * nct; t += gridDim.x)
+    c64_fp32_tile(G, ldg, n, pmax, p, C0, S, t / nct, t % nct, sC);
+}
+
+// Batched: the tiles of every problem that applies an update, interleaved over the CTAs.
+__global__ void __launch_bounds__(kF32Threads, 3) k_rank_update_c64_fp32_batch(const BatchItem* __restrict__ items,
+                                                                            int nprob) {
+  __shared__ float2 sC[kF32Rows][kC64Fp32MaxP];
+  __shared__ int64_t s_begin[kBatchMax + 1];
+  __shared__ int s_p[kBatchMax];
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int b = 0; b < nprob; ++b) {
+      s_begin[b] = acc;
+      const UpdCtl* c = reinterpret_cast<const UpdCtl*>(items[b].ws + items[b].L.ctl);
+      const int p = c->skip ? 0 : c->nv;
+      s_p[b] = p;
+      const int64_t n = items[b].L.n;
+      if (p >= 1 && p <= kC64Fp32MaxP) acc += ((n + kF32Rows - 1) / kF32Rows) * ((n + kF32Cols - 1) / kF32Cols);
+    }
+    s_begin[nprob] = acc;
+  }
+  __syncthreads();
+  const int64_t T = s_begin[nprob];
+  int b = 0;
+  for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+    while (t >= s_begin[b + 1]) ++b;
+    const BatchItem& it = items[b];
+    const int64_t n = it.L.n;
+    const int64_t nct = (n + kF32Cols - 1) / kF32Cols;
+    const int64_t u = t - s_begin[b];
+    c64_fp32_tile(reinterpret_cast<float2*>(it.G), it.ldg, n, it.L.pmax, s_p[b],
+                  reinterpret_cast<const cplx*>(it.ws + it.L.C0), reinterpret_cast<const cplx*>(it.ws + it.L.S),
+                  u / nct, u % nct, sC);
+  }
+}
+
+void launch_rank_update_c64_fp32(float2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0, const cplx* S,
+                                 const UpdCtl* ctl, int32_t* prof_p, int ctas, cudaStream_t st) {
+  k_rank_update_c64_fp32<<<ctas, kF32Threads, 0, st>>>(G, ldg, n, pmax, C0, S, ctl, prof_p);
+}
+
+void launch_rank_update_c64_fp32_batch(const BatchItem* items, int nprob, int ctas, cudaStream_t st) {
+  k_rank_update_c64_fp32_batch<<<ctas, kF32Threads, 0, st>>>(items, nprob);
+}
+
 // ----------------------------------------------------------------------------- field, state, FOM
-__global__ void k_finish(UpdArgs a, WsLayout L, char* ws, uint8_t* __restrict__ state,
-                         double* __restrict__ fom_out, int32_t* __restrict__ applied) {
+__device__ __forceinline__ void finish_body(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* __restrict__ state,
+                                            double* __restrict__ fom_out, int32_t* __restrict__ applied) {
   const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
   const int64_t n = L.n;
   const int64_t N = n - 1;
@@ -430,6 +559,73 @@ __global__ void k_finish(UpdArgs a, WsLayout L, char* ws, uint8_t* __restrict__ 
   }
 }
 
+__global__ void k_finish(UpdArgs a, WsLayout L, char* ws, uint8_t* __restrict__ state,
+                         double* __restrict__ fom_out, int32_t* __restrict__ applied) {
+  finish_body(a, L, ws, state, fom_out, applied);
+}
+
+// ----------------------------------------------------------------------------- batched steps
+// blockIdx.y (x for the single-CTA capacitance) selects the problem; the argument blocks are
+// rebuilt in shared memory from the device table and the single-problem bodies run unchanged.
+__device__ __forceinline__ void batch_shared_args(const BatchItem* items, int b, int dtype, UpdArgs& sa,
+                                                  WsLayout& sL) {
+  if (threadIdx.x == 0) {
+    batch_upd_args(items[b], dtype, sa);
+    sL = items[b].L;
+  }
+  __syncthreads();
+}
+
+__global__ void k_capacitance_batch(const BatchItem* __restrict__ items, int dtype, int kind, int dir_mask) {
+  __shared__ CapArgs sa;
+  __shared__ WsLayout sL;
+  if (threadIdx.x == 0) {
+    batch_upd_args(items[blockIdx.x], dtype, sa.u);
+    sa.kind = kind;
+    sa.dir_mask = dir_mask;
+    sa.k = 1;
+    sa.pmax = items[blockIdx.x].L.pmax;
+    sL = items[blockIdx.x].L;
+  }
+  __syncthreads();
+  const BatchItem& it = items[blockIdx.x];
+  capacitance_body(sa, sL, it.ws, it.state, it.idx, it.status);
+}
+
+__global__ void k_panels_batch(const BatchItem* __restrict__ items, int dtype) {
+  __shared__ UpdArgs sa;
+  __shared__ WsLayout sL;
+  batch_shared_args(items, blockIdx.y, dtype, sa, sL);
+  panels_body(sa, sL, items[blockIdx.y].ws, 1);
+}
+
+__global__ void k_finish_batch(const BatchItem* __restrict__ items, int dtype) {
+  __shared__ UpdArgs sa;
+  __shared__ WsLayout sL;
+  batch_shared_args(items, blockIdx.y, dtype, sa, sL);
+  const BatchItem& it = items[blockIdx.y];
+  finish_body(sa, sL, it.ws, it.state, it.fom, it.applied);
+}
+
+static dim3 batch_grid(int64_t widest, int nprob) {
+  int64_t b = (widest + 255) / 256;
+  if (b > 1216) b = 1216;
+  return dim3((unsigned)(b < 1 ? 1 : b), (unsigned)nprob);
+}
+
+void launch_capacitance_batch(const BatchItem* items, int nprob, int dtype, const gf_cand_spec& spec,
+                              cudaStream_t st) {
+  k_capacitance_batch<<<nprob, 256, 0, st>>>(items, dtype, spec.kind, spec.dir_mask);
+}
+
+void launch_panels_batch(const BatchItem* items, int nprob, int dtype, int64_t widest, cudaStream_t st) {
+  k_panels_batch<<<batch_grid(widest, nprob), 256, 0, st>>>(items, dtype);
+}
+
+void launch_finish_batch(const BatchItem* items, int nprob, int dtype, int64_t widest, cudaStream_t st) {
+  k_finish_batch<<<batch_grid(widest, nprob), 256, 0, st>>>(items, dtype);
+}
+
 void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state,
                    const gf_cand_spec& spec, const int32_t* idx, int32_t* status, double* fom_out,
                    int32_t* applied, cudaStream_t st, KernelTimer* timer) {
@@ -445,7 +641,9 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   // the panels kernel only gathers C0
   struct Map128 { alignas(64) unsigned char b[128]; };
   Map128 maps[kMaxLam];
-  bool c64tc = a.dtype == GF_C64 && a.algo == GF_UPDATE_TC && L.pmax <= kC64MaxP;
+  // rank <= 4 complex64: an FP32 stream on the CUDA cores (HBM-bound); larger ranks: tensor cores
+  const bool c64f32 = a.dtype == GF_C64 && a.algo == GF_UPDATE_TC && L.pmax <= kC64Fp32MaxP;
+  bool c64tc = a.dtype == GF_C64 && a.algo == GF_UPDATE_TC && !c64f32 && L.pmax <= kC64MaxP;
   for (int l = 0; c64tc && l < a.nlam; ++l)
     c64tc = c64_tc_make_map(reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, maps[l].b);
   {
@@ -478,6 +676,9 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
       }
       if (a.algo != GF_UPDATE_TC || L.pmax > 4 || only_above == 0)
         k_rank_update_f64<<<grid, kUpdThreads, 0, st>>>(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl, only_above, prof_p);
+    } else if (c64f32) {
+      launch_rank_update_c64_fp32(reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, L.pmax, C0, S, ctl, prof_p,
+                                  a.sm_count * 3, st);
     } else if (c64tc) {
       launch_rank_update_c64_tc(maps[l].b, reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, L, ws, l, status,
                                 prof_p, a.sm_count, st);

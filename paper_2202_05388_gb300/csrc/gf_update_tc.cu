@@ -27,6 +27,7 @@
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <new>
 
 #include "gf_internal.cuh"
 #include "gf_tc.cuh"
@@ -44,6 +45,7 @@ constexpr int kOzSliceB = kOzN * kOzK * 4;      // bytes of one digit slice of a
 constexpr int kOzTileA = kOzS * kOzSliceA;      // 24 KB
 constexpr int kOzTileB = kOzS * kOzSliceB;      // 6 KB
 constexpr uint64_t kOzTimeoutNs = 2000000000ull;
+constexpr int kOzMaxBatch = kBatchMax;
 constexpr int kOzBBlockG = kOzTileB + 64;       // B digit slices + 16 column exponents (global block)
 
 // byte offset of element (r, k) inside one K-major, no-swizzle digit slice (8x16-byte core
@@ -70,9 +72,9 @@ __device__ __forceinline__ int oz_exponent(double m) {
 }
 
 // ---- operand preparation (once per step, O(n p) work) --------------------------------------
-__global__ void k_oz_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n, int64_t nrows_pad,
-                               const UpdCtl* __restrict__ ctl, uint8_t* __restrict__ ozA,
-                               int32_t* __restrict__ ozE) {
+__device__ __forceinline__ void oz_prep_rows_body(const cplx* __restrict__ C0, int pmax, int64_t n,
+                                                  int64_t nrows_pad, const UpdCtl* __restrict__ ctl,
+                                                  uint8_t* __restrict__ ozA, int32_t* __restrict__ ozE) {
   if (ctl->skip || ctl->nv > 4) return;
   const int p = ctl->nv;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows_pad;
@@ -104,8 +106,8 @@ __global__ void k_oz_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n,
   }
 }
 
-__global__ void k_oz_prep_cols(const cplx* __restrict__ S, int64_t n, int64_t ncols_pad,
-                               const UpdCtl* __restrict__ ctl, uint8_t* __restrict__ ozB) {
+__device__ __forceinline__ void oz_prep_cols_body(const cplx* __restrict__ S, int64_t n, int64_t ncols_pad,
+                                                  const UpdCtl* __restrict__ ctl, uint8_t* __restrict__ ozB) {
   if (ctl->skip || ctl->nv > 4) return;
   const int p = ctl->nv;
   // one thread per complex column j; writes real columns 2j and 2j+1
@@ -141,6 +143,31 @@ __global__ void k_oz_prep_cols(const cplx* __restrict__ S, int64_t n, int64_t nc
       *reinterpret_cast<float4*>(sl + oz_off(c + 1, 4)) = make_float4(dr[0][a], dr[1][a], dr[2][a], dr[3][a]);
     }
   }
+}
+
+__global__ void k_oz_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n, int64_t nrows_pad,
+                               const UpdCtl* __restrict__ ctl, uint8_t* __restrict__ ozA,
+                               int32_t* __restrict__ ozE) {
+  oz_prep_rows_body(C0, pmax, n, nrows_pad, ctl, ozA, ozE);
+}
+
+__global__ void k_oz_prep_cols(const cplx* __restrict__ S, int64_t n, int64_t ncols_pad,
+                               const UpdCtl* __restrict__ ctl, uint8_t* __restrict__ ozB) {
+  oz_prep_cols_body(S, n, ncols_pad, ctl, ozB);
+}
+
+// Batched preparation: blockIdx.y selects the problem; rows and columns of its digit blocks
+// come from the panels in its own workspace.
+__global__ void k_oz_prep_batch(const BatchItem* __restrict__ items) {
+  const BatchItem& it = items[blockIdx.y];
+  const int64_t n = it.L.n;
+  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(it.ws + it.L.ctl);
+  const int64_t rows = ((n + kOzM - 1) / kOzM) * kOzM;
+  const int64_t cols = ((2 * n + kOzN - 1) / kOzN) * (kOzN / 2);
+  oz_prep_rows_body(reinterpret_cast<const cplx*>(it.ws + it.L.C0), it.L.pmax, n, rows, ctl,
+                    reinterpret_cast<uint8_t*>(it.ws + it.L.ozA), reinterpret_cast<int32_t*>(it.ws + it.L.ozE));
+  oz_prep_cols_body(reinterpret_cast<const cplx*>(it.ws + it.L.S), n, cols, ctl,
+                    reinterpret_cast<uint8_t*>(it.ws + it.L.ozB));
 }
 
 // ---- epilogue arithmetic --------------------------------------------------------------------
@@ -214,19 +241,86 @@ struct OzBars {
   int abort;
 };
 
-__global__ void __launch_bounds__(kOzThreadsV2, 1)
-k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restrict__ G, int64_t ldg,
-                    int64_t n, int64_t nrt, int64_t nct,
-                    const uint8_t* __restrict__ ozA, const int32_t* __restrict__ ozE,
-                    const uint8_t* __restrict__ ozB, const UpdCtl* __restrict__ ctl,
-                    int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  const int p = ctl->skip ? 0 : ctl->nv;
-#ifndef GF_EXPERIMENT_NO_PROFP
-  if (prof_p && blockIdx.x == 0 && threadIdx.x == 0 && p >= 1 && p <= 4) *prof_p = p;
-#endif
-  if (p < 1 || p > 4) return;
+// Where the tiles come from.  A source enumerates the work as tiles t in [0, total) in raster
+// order and maps each to (problem b, row tile rt, column tile ct); row tiles of one problem
+// are consecutive so that the A digit tile is reused along the row.
+struct OzProb {
+  int64_t n, nrt, nct;
+  const uint8_t* ozA;
+  const int32_t* ozE;
+  const uint8_t* ozB;
+};
 
+// A role walks its contiguous tile range with a cursor: one division at the start, then
+// increments (the epilogue is issue-bound, so no per-tile 64-bit division or search).
+struct OzCursor {
+  int b;
+  int64_t rt, ct;
+};
+
+struct OzSingleSrc {
+  const CUtensorMap* map;
+  OzProb pr;
+  __device__ int64_t total() const { return pr.nrt * pr.nct; }
+  __device__ void first(int64_t t, OzCursor& c) const {
+    c.b = 0;
+    c.rt = t / pr.nct;
+    c.ct = t - c.rt * pr.nct;
+  }
+  __device__ void next(OzCursor& c) const {
+    if (++c.ct == pr.nct) {
+      c.ct = 0;
+      ++c.rt;
+    }
+  }
+  __device__ const OzProb& prob(int) const { return pr; }
+  __device__ const CUtensorMap* tmap(int) const { return map; }
+};
+
+// Many independent problems in one launch: the tensor maps and descriptors travel in the
+// kernel parameters; the tile prefix over the problems that apply an update this step is
+// built in shared memory at kernel start (problems that skip contribute no tiles).
+struct OzBatchParams {
+  CUtensorMap maps[kOzMaxBatch];
+  OzProb probs[kOzMaxBatch];
+  const UpdCtl* ctl[kOzMaxBatch];
+  int32_t* status[kOzMaxBatch];
+  int nprob;
+};
+
+struct OzBatchSrc {
+  const OzBatchParams* P;
+  const int64_t* begin;     // shared memory, nprob + 1 entries
+  __device__ int64_t total() const { return begin[P->nprob]; }
+  __device__ void first(int64_t t, OzCursor& c) const {
+    int lo = 0, hi = P->nprob - 1;       // last b with begin[b] <= t: a problem with tiles
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (begin[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    c.b = lo;
+    const int64_t u = t - begin[lo];
+    c.rt = u / P->probs[lo].nct;
+    c.ct = u - c.rt * P->probs[lo].nct;
+  }
+  __device__ void next(OzCursor& c) const {
+    if (++c.ct < P->probs[c.b].nct) return;
+    c.ct = 0;
+    if (++c.rt < P->probs[c.b].nrt) return;
+    c.rt = 0;
+    do {
+      ++c.b;
+    } while (c.b < P->nprob && begin[c.b + 1] == begin[c.b]);     // skip problems without tiles
+  }
+  __device__ const OzProb& prob(int b) const { return P->probs[b]; }
+  __device__ const CUtensorMap* tmap(int b) const { return &P->maps[b]; }
+};
+
+__device__ __forceinline__ int64_t oz_key(int b, int64_t rt) { return ((int64_t)b << 40) | rt; }
+
+// Returns true (in every thread) when a wait timed out and the tile loop was abandoned.
+template <class Src>
+__device__ __forceinline__ bool ozaki_body(const Src& src, uint8_t* smem) {
   OzBars* bars = reinterpret_cast<OzBars*>(smem + kOzBarOff);
   uint8_t* Abuf = smem;                                       // 2 x kOzTileA
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -256,29 +350,33 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restri
   tc::fence_after_sync();
   const uint32_t tbase = bars->tslot;
 
-  const int64_t T = nrt * nct;
+  const int64_t T = src.total();
   const int64_t tb = T * blockIdx.x / gridDim.x;
   const int64_t te = T * (blockIdx.x + 1) / gridDim.x;
 
   if (warp == kWarpProd) {
     // ------------------------------------------------------------------ producer
-    int64_t cur_rt = -1;
+    int64_t cur = -1;
     int64_t aseq = -1;
     int64_t k = 0;
-    for (int64_t t = tb; t < te; ++t, ++k) {
-      const int64_t rt = t / nct, ct = t - rt * nct;
+    OzCursor cs;
+    if (tb < te) src.first(tb, cs);
+    for (int64_t t = tb; t < te; ++t, ++k, src.next(cs)) {
+      const int b = cs.b;
+      const int64_t rt = cs.rt, ct = cs.ct;
+      const OzProb& pr = src.prob(b);
       bool ok = true;
-      if (rt != cur_rt) {
+      if (oz_key(b, rt) != cur) {
         ++aseq;
         const int ab = (int)(aseq & 1);
         if (lane == 0) {
           if (aseq >= 2) ok = tc::mbar_wait_or_abort(&bars->aempty[ab], (uint32_t)((aseq / 2 - 1) & 1), abort, kOzTimeoutNs);
           if (ok) {
             tc::mbar_arrive_expect_tx(&bars->afull[ab], kOzTileA);
-            tc::bulk_g2s(Abuf + ab * kOzTileA, ozA + rt * (int64_t)kOzTileA, kOzTileA, &bars->afull[ab]);
+            tc::bulk_g2s(Abuf + ab * kOzTileA, pr.ozA + rt * (int64_t)kOzTileA, kOzTileA, &bars->afull[ab]);
           }
         }
-        cur_rt = rt;
+        cur = oz_key(b, rt);
       }
       const int s = (int)(k % kOzNS);
       if (lane == 0 && ok && k >= kOzNS)
@@ -289,11 +387,12 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restri
       if (lane == 0) {
         // x in doubles (2 per complex entry), y in rows; both boxes are always full-size
         const int x = (int)(ct * kOzN), y = (int)(rt * kOzM);
-        const bool second = x + 16 < 2 * n;         // the right box holds at least one column
+        const bool second = x + 16 < 2 * pr.n;      // the right box holds at least one column
+        const CUtensorMap* map = src.tmap(b);
         tc::mbar_arrive_expect_tx(&bars->full[s], (uint32_t)((second ? kOzGTile : kOzBox) + kOzBBlock));
-        tc::tma_load_2d(stage, &tmapG, x, y, &bars->full[s]);
-        if (second) tc::tma_load_2d(stage + kOzBox, &tmapG, x + 16, y, &bars->full[s]);
-        tc::bulk_g2s(stage + kOzGTile, ozB + ct * (int64_t)kOzBBlock, kOzBBlock, &bars->full[s]);
+        tc::tma_load_2d(stage, map, x, y, &bars->full[s]);
+        if (second) tc::tma_load_2d(stage + kOzBox, map, x + 16, y, &bars->full[s]);
+        tc::bulk_g2s(stage + kOzGTile, pr.ozB + ct * (int64_t)kOzBBlock, kOzBBlock, &bars->full[s]);
       }
       __syncwarp();
     }
@@ -301,23 +400,26 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restri
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_tf32(kOzM, kOzN);
-      int64_t cur_rt = -1;
+      int64_t cur = -1;
       int64_t aseq = -1;
       int64_t k = 0;
       int ab = 0;
-      for (int64_t t = tb; t < te; ++t, ++k) {
-        const int64_t rt = t / nct;
-        if (rt != cur_rt) {
-          if (cur_rt >= 0) tc::mma_commit(&bars->aempty[ab]);      // old A tile free once its MMAs end
+      OzCursor cs;
+      if (tb < te) src.first(tb, cs);
+      for (int64_t t = tb; t < te; ++t, ++k, src.next(cs)) {
+        const int b = cs.b;
+        const int64_t rt = cs.rt;
+        if (oz_key(b, rt) != cur) {
+          if (cur >= 0) tc::mma_commit(&bars->aempty[ab]);         // old A tile free once its MMAs end
           ++aseq;
           ab = (int)(aseq & 1);
           if (!tc::mbar_wait_or_abort(&bars->afull[ab], (uint32_t)((aseq / 2) & 1), abort, kOzTimeoutNs)) break;
-          cur_rt = rt;
+          cur = oz_key(b, rt);
         }
         const int s = (int)(k % kOzNS);
-        const int b = (int)(k & 1);
+        const int bf = (int)(k & 1);
         if (!tc::mbar_wait_or_abort(&bars->full[s], (uint32_t)((k / kOzNS) & 1), abort, kOzTimeoutNs)) break;
-        if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[b], (uint32_t)((k / 2 - 1) & 1), abort, kOzTimeoutNs)) break;
+        if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[bf], (uint32_t)((k / 2 - 1) & 1), abort, kOzTimeoutNs)) break;
         tc::fence_after_sync();
         const uint32_t sA = tc::smem_u32(Abuf + ab * kOzTileA);
         const uint32_t sB = tc::smem_u32(smem + 2 * kOzTileA + s * kOzStage + kOzGTile);
@@ -330,13 +432,13 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restri
           for (int bb = 0; bb < kOzS; ++bb) {
             if (a + bb <= kOzLv - 1) {
               const int L = a + bb;
-              tc::mma_tf32(tbase + (uint32_t)(b * 256 + L * kOzN), tc::smem_desc(sA + a * kOzSliceA, 128, 256),
+              tc::mma_tf32(tbase + (uint32_t)(bf * 256 + L * kOzN), tc::smem_desc(sA + a * kOzSliceA, 128, 256),
                            tc::smem_desc(sB + bb * kOzSliceB, 128, 256), idesc, first[L] ? 0u : 1u);
               first[L] = false;
             }
           }
         }
-        tc::mma_commit(&bars->tfull[b]);
+        tc::mma_commit(&bars->tfull[bf]);
         tc::mma_commit(&bars->empty[s]);
       }
     }
@@ -346,28 +448,32 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restri
     const int q = warp & 3, h = warp >> 2;     // TMEM lane quarter, column quarter
     const int r = q * 32 + lane;               // tile row
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-    int64_t cur_rt = -1;
+    int64_t cur = -1;
     int Ei = 0;
     int64_t k = 0;
-    for (int64_t t = tb; t < te; ++t, ++k) {
-      const int64_t rt = t / nct, ct = t - rt * nct;
-      if (rt != cur_rt) {
-        Ei = ozE[rt * kOzM + r];
-        cur_rt = rt;
+    OzCursor cs;
+    if (tb < te) src.first(tb, cs);
+    for (int64_t t = tb; t < te; ++t, ++k, src.next(cs)) {
+      const int b = cs.b;
+      const int64_t rt = cs.rt, ct = cs.ct;
+      const OzProb& pr = src.prob(b);
+      if (oz_key(b, rt) != cur) {
+        Ei = pr.ozE[rt * kOzM + r];
+        cur = oz_key(b, rt);
       }
       const int s = (int)(k % kOzNS);
-      const int b = (int)(k & 1);
-      if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kOzTimeoutNs)) break;
+      const int bf = (int)(k & 1);
+      if (!tc::mbar_wait_or_abort(&bars->tfull[bf], (uint32_t)((k / 2) & 1), abort, kOzTimeoutNs)) break;
       if (!tc::mbar_wait_or_abort(&bars->full[s], (uint32_t)((k / kOzNS) & 1), abort, kOzTimeoutNs)) break;
       tc::fence_after_sync();
       float acc[kOzLv][8];
 #pragma unroll
       for (int L = 0; L < kOzLv; ++L)
-        tc::tmem_ld8(tbase + lane_addr + (uint32_t)(b * 256 + L * kOzN + h * 8), acc[L]);
+        tc::tmem_ld8(tbase + lane_addr + (uint32_t)(bf * 256 + L * kOzN + h * 8), acc[L]);
       tc::tmem_ld_wait();
       tc::fence_before_sync();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
+      if (lane == 0) tc::mbar_arrive(&bars->tempty[bf]);
       uint8_t* stage = smem + 2 * kOzTileA + s * kOzStage;
       const int32_t* Fj = reinterpret_cast<const int32_t*>(stage + kOzGTile + kOzTileB);
       // complex column jj of row r: box jj/8, 16-byte chunk (jj%8) XOR (r%8) (128B swizzle)
@@ -377,7 +483,7 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restri
 #pragma unroll
       for (int c = 0; c < kOzColsPerThread; ++c) {
         const int jj = h * kOzColsPerThread + c;
-        if (i < n && j0 + jj < n) {
+        if (i < pr.n && j0 + jj < pr.n) {
           float lr[kOzLv], li[kOzLv];
 #pragma unroll
           for (int L = 0; L < kOzLv; ++L) {
@@ -397,8 +503,11 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restri
   if (warp == kWarpStore) {
     // ------------------------------------------------------------------ storer
     int64_t k = 0;
-    for (int64_t t = tb; t < te; ++t, ++k) {
-      const int64_t rt = t / nct, ct = t - rt * nct;
+    OzCursor cs;
+    if (tb < te) src.first(tb, cs);
+    for (int64_t t = tb; t < te; ++t, ++k, src.next(cs)) {
+      const int b = cs.b;
+      const int64_t rt = cs.rt, ct = cs.ct;
       const int s = (int)(k % kOzNS);
       bool ok = true;
       if (lane == 0) ok = tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)((k / kOzNS) & 1), abort, kOzTimeoutNs);
@@ -407,8 +516,9 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restri
       uint8_t* stage = smem + 2 * kOzTileA + s * kOzStage;
       if (lane == 0) {
         const int x = (int)(ct * kOzN), y = (int)(rt * kOzM);
-        tc::tma_store_2d(&tmapG, x, y, stage);
-        if (x + 16 < 2 * n) tc::tma_store_2d(&tmapG, x + 16, y, stage + kOzBox);
+        const CUtensorMap* map = src.tmap(b);
+        tc::tma_store_2d(map, x, y, stage);
+        if (x + 16 < 2 * src.prob(b).n) tc::tma_store_2d(map, x + 16, y, stage + kOzBox);
       }
       tc::bulk_commit();
       tc::bulk_wait_read0();
@@ -419,9 +529,55 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, double2* __restri
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (tid == 0 && bars->abort) atomicExch(status, GF_ETIMEOUT);
+  const bool aborted = bars->abort != 0;
   tc::fence_after_sync();
   if (warp == kWarpMma) tc::tmem_dealloc(tbase, kOzTmemColsV2);
+  return aborted;
+}
+
+__global__ void __launch_bounds__(kOzThreadsV2, 1)
+k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_t nrt, int64_t nct,
+                    const uint8_t* __restrict__ ozA, const int32_t* __restrict__ ozE,
+                    const uint8_t* __restrict__ ozB, const UpdCtl* __restrict__ ctl,
+                    int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int p = ctl->skip ? 0 : ctl->nv;
+#ifndef GF_EXPERIMENT_NO_PROFP
+  if (prof_p && blockIdx.x == 0 && threadIdx.x == 0 && p >= 1 && p <= 4) *prof_p = p;
+#endif
+  if (p < 1 || p > 4) return;
+  OzSingleSrc src;
+  src.map = &tmapG;
+  src.pr = OzProb{n, nrt, nct, ozA, ozE, ozB};
+  if (ozaki_body(src, smem) && threadIdx.x == 0) atomicExch(status, GF_ETIMEOUT);
+}
+
+// Batched form: the tiles of every problem that applies a rank-1..4 update this step, one
+// persistent launch.  On a timeout every problem's status word receives GF_ETIMEOUT.  The tile
+// prefix lives behind the barriers in dynamic shared memory (no static shared memory, so the
+// 1024-byte alignment of the swizzled stages holds).
+constexpr int kOzSmemBatch = kOzSmemV2 + 8 * (kOzMaxBatch + 1);
+__global__ void __launch_bounds__(kOzThreadsV2, 1)
+k_rank_update_ozaki_batch(const __grid_constant__ OzBatchParams P) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  int64_t* s_begin = reinterpret_cast<int64_t*>(smem + kOzSmemV2);
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int b = 0; b < P.nprob; ++b) {
+      s_begin[b] = acc;
+      const UpdCtl* c = P.ctl[b];
+      const int p = c->skip ? 0 : c->nv;
+      if (p >= 1 && p <= 4) acc += P.probs[b].nrt * P.probs[b].nct;
+    }
+    s_begin[P.nprob] = acc;
+  }
+  __syncthreads();
+  if (s_begin[P.nprob] == 0) return;
+  OzBatchSrc src;
+  src.P = &P;
+  src.begin = s_begin;
+  if (ozaki_body(src, smem) && threadIdx.x == 0)
+    for (int b = 0; b < P.nprob; ++b) atomicExch(P.status[b], GF_ETIMEOUT);
 }
 
 OzLayout oz_layout(int64_t n) {
@@ -492,9 +648,51 @@ bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, cons
   }
   const int64_t tiles = o.nrow_tiles * o.ncol_tiles;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  k_rank_update_ozaki<<<grid, kOzThreadsV2, kOzSmemV2, st>>>(tmap, G, ldg, n, o.nrow_tiles, o.ncol_tiles, ozA,
-                                                            ozE, ozB, ctl, status, prof_p);
+  k_rank_update_ozaki<<<grid, kOzThreadsV2, kOzSmemV2, st>>>(tmap, n, o.nrow_tiles, o.ncol_tiles, ozA, ozE, ozB,
+                                                            ctl, status, prof_p);
   return true;
+}
+
+size_t ozaki_batch_params_bytes() { return sizeof(OzBatchParams); }
+
+// Host: the parameter block of the batched update (one tensor map and descriptor per problem,
+// pointing at the problem's G and at the digit buffers in its workspace).
+bool ozaki_batch_params(void* out, const BatchItem* it, int nprob) {
+  if (nprob < 1 || nprob > kOzMaxBatch) return false;
+  OzBatchParams* P = new (out) OzBatchParams();
+  P->nprob = nprob;
+  for (int b = 0; b < nprob; ++b) {
+    const int64_t n = it[b].L.n;
+    if (!make_tmap_G(&P->maps[b], reinterpret_cast<double2*>(it[b].G), it[b].ldg, n)) return false;
+    const OzLayout o = oz_layout(n);
+    P->probs[b] = OzProb{n, o.nrow_tiles, o.ncol_tiles, reinterpret_cast<const uint8_t*>(it[b].ws + it[b].L.ozA),
+                         reinterpret_cast<const int32_t*>(it[b].ws + it[b].L.ozE),
+                         reinterpret_cast<const uint8_t*>(it[b].ws + it[b].L.ozB)};
+    P->ctl[b] = reinterpret_cast<const UpdCtl*>(it[b].ws + it[b].L.ctl);
+    P->status[b] = it[b].status;
+  }
+  return true;
+}
+
+void launch_oz_prep_batch(const BatchItem* items, int nprob, int64_t widest, cudaStream_t st) {
+  int64_t b = (widest + 127) / 128;           // widest: rows (= complex columns) of the largest G
+  if (b > 608) b = 608;
+  k_oz_prep_batch<<<dim3((unsigned)(b < 1 ? 1 : b), (unsigned)nprob), 128, 0, st>>>(items);
+}
+
+void launch_rank_update_ozaki_batch(const void* params, int ctas, cudaStream_t st) {
+  {  // once per device
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+      cudaFuncSetAttribute(k_rank_update_ozaki_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmemBatch);
+      if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+  }
+  k_rank_update_ozaki_batch<<<ctas, kOzThreadsV2, kOzSmemBatch, st>>>(*reinterpret_cast<const OzBatchParams*>(params));
 }
 
 }  // namespace gf

@@ -21,6 +21,7 @@ GF_KIND_SINGLE, GF_KIND_BRUSH2 = 0, 1
 GF_DIR_FILL, GF_DIR_CLEAR = 1, 2
 GF_NBANDS = 9
 GF_UPDATE_TC, GF_UPDATE_DFMA = 0, 1
+BATCH_MAX = 64             # items per gf_batch
 
 STATUS_NAMES = {GF_OK: "GF_OK", GF_EINVAL: "GF_EINVAL", GF_ECUDA: "GF_ECUDA",
                 GF_ESINGULAR: "GF_ESINGULAR", GF_ENOIMPROVE: "GF_ENOIMPROVE",
@@ -29,7 +30,9 @@ STATUS_NAMES = {GF_OK: "GF_OK", GF_EINVAL: "GF_EINVAL", GF_ECUDA: "GF_ECUDA",
 EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_version",
            "gf_num_candidates", "gf_workspace_size", "gf_fill_g0", "gf_extract_bands",
            "gf_eval_candidates", "gf_select_topk", "gf_apply_update", "gf_profile_begin",
-           "gf_profile_end", "gf_set_update_algo", "gf_refresh", "gf_refresh_workspace_size"]
+           "gf_profile_end", "gf_set_update_algo", "gf_refresh", "gf_refresh_workspace_size",
+           "gf_fill_g0_static", "gf_batch_table_size", "gf_batch_create", "gf_batch_step",
+           "gf_batch_set_schedule", "gf_batch_destroy"]
 
 
 class GfError(RuntimeError):
@@ -52,6 +55,12 @@ class gf_problem(C.Structure):
 class gf_cand_spec(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dir_mask", C.c_int32), ("k", C.c_int32),
                 ("excl_radius", C.c_int32), ("tie_rel", C.c_double)]
+
+
+class gf_batch_item(C.Structure):
+    _fields_ = [("prob", gf_problem), ("state", C.c_void_p), ("dfom", C.c_void_p), ("idx", C.c_void_p),
+                ("val", C.c_void_p), ("status", C.c_void_p), ("fom_out", C.c_void_p),
+                ("applied", C.c_void_p), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
 
 
 _lib = None
@@ -95,6 +104,12 @@ def load(path: str = LIB_PATH):
                                        C.POINTER(C.c_double), C.POINTER(C.c_int32), P, C.c_size_t, P]),
             "gf_profile_end": (C.c_int32, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+            "gf_batch_table_size": (C.c_size_t, [C.c_int32]),
+            "gf_batch_create": (C.c_int32, [P, C.c_int32, C.POINTER(gf_batch_item), C.c_int32,
+                                            C.POINTER(gf_cand_spec), P, C.c_size_t, P, C.POINTER(P)]),
+            "gf_batch_step": (C.c_int32, [P, P]),
+            "gf_batch_set_schedule": (C.c_int32, [P, C.c_int32]),
+            "gf_batch_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -217,6 +232,28 @@ class Handle:
                                         int(max_iter), float(tol), res, its, _ptr(ws), int(ws_bytes),
                                         _stream(stream)))
         return list(res), list(its)[:ns]
+
+    # ---- batches
+    def gf_batch_table_size(self, nitems: int) -> int:
+        return int(self.lib.gf_batch_table_size(int(nitems)))
+
+    def gf_batch_create(self, items, dtype, spec, table, table_bytes, stream=None):
+        """items: list of gf_batch_item.  Returns the gf_batch pointer (a c_void_p)."""
+        arr = (gf_batch_item * len(items))(*items)
+        s = spec_struct(spec)
+        out = C.c_void_p()
+        self._check(self.lib.gf_batch_create(self.h, len(items), arr, int(dtype), C.byref(s), _ptr(table),
+                                             int(table_bytes), _stream(stream), C.byref(out)))
+        return out
+
+    def gf_batch_step(self, batch, stream=None):
+        self._check(self.lib.gf_batch_step(batch, _stream(stream)))
+
+    def gf_batch_set_schedule(self, batch, update_ctas: int):
+        self._check(self.lib.gf_batch_set_schedule(batch, int(update_ctas)))
+
+    def gf_batch_destroy(self, batch):
+        self.lib.gf_batch_destroy(batch)
 
     def gf_profile_begin(self, max_records: int):
         self._check(self.lib.gf_profile_begin(self.h, int(max_records)))

@@ -130,6 +130,14 @@ def brush_320_c128() -> Workload:
                     w.steps, "c128")
 
 
+def brush_320_c64_rank4() -> Workload:
+    """The 320x320 geometry with complex64 G and one brush (rank 4) per step: the rank-4
+    baseline form of the mixed-precision family."""
+    w = brush_320_topk()
+    return Workload("brush_320x320_p4_c64", w.geoms, CandidateSpec(KIND_BRUSH2, DIR_FILL | DIR_CLEAR, 1),
+                    w.steps, "c64")
+
+
 def brush_128_topk() -> Workload:
     """128x128 member of the top-32 complex64 family (G = 2.1 GB), for profiling."""
     nx = ny = 128

@@ -70,3 +70,14 @@ def test_create_without_gpu_reports_cuda_error(lib):
     st = lib.gf_create(C.byref(h), 0)
     assert st == B.GF_ECUDA
     assert len(lib.gf_last_error(None)) > 0
+
+
+def test_batch_host_checks(lib):
+    assert lib.gf_batch_table_size(0) == 0
+    assert lib.gf_batch_table_size(B.BATCH_MAX + 1) == 0
+    one = lib.gf_batch_table_size(1)
+    assert one > 0 and one % 256 == 0
+    assert lib.gf_batch_table_size(B.BATCH_MAX) >= B.BATCH_MAX * one // 256 * 0 + one
+    assert lib.gf_batch_step(None, None) == B.GF_EINVAL
+    assert lib.gf_batch_set_schedule(None, 0) == B.GF_EINVAL
+    lib.gf_batch_destroy(None)

@@ -1,6 +1,7 @@
-"""Batched problems through CUDA-graph replay: every problem of a small seeded batch follows
-exactly the trajectory it follows when stepped alone (same flips, same G, E and FOM), and
-both match the FP64 oracle."""
+"""Batched problems through CUDA-graph replay, with the fused schedule (the library's batch
+entry points: one launch per stage for all problems) and the stream-branch schedules: every
+problem of a small seeded batch follows exactly the trajectory it follows when stepped alone
+(same flips, same G, E and FOM), and the complex128 runs match the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -25,19 +26,55 @@ def built():
     BLD.build()
 
 
-def _small_batch():
-    # the batched family (single-pixel toggles, seeded sides / lambda/dx / focus), scaled down
+def _small_batch(count=6, sides=(8, 10, 12, 14), kind=W.KIND_SINGLE, ratios=(16, 20, 24), dtype="c128",
+                 seed=5):
+    # the batched family (seeded sides / lambda/dx / focus), scaled down
     out = []
-    rng = np.random.default_rng(5)
-    for b in range(6):
-        side = int(rng.choice([8, 10, 12, 14]))
-        ratio = int(rng.choice([16, 20, 24]))
-        out.append(W.small(side, side, kind=W.KIND_SINGLE, dir_mask=3, ratio=ratio,
-                           beyond_edge=float(rng.uniform(2.0, 6.0)), steps=4))
+    rng = np.random.default_rng(seed)
+    for b in range(count):
+        side = int(rng.choice(list(sides)))
+        ratio = int(rng.choice(list(ratios)))
+        out.append(W.small(side, side, kind=kind, dir_mask=3, ratio=ratio,
+                           beyond_edge=float(rng.uniform(2.0, 6.0)), steps=4, dtype=dtype))
     return out
 
 
-@pytest.mark.parametrize("sch", [Schedule(1, "given"), Schedule(3, "largest_first"), Schedule(6, "given")])
+def _pattern(opt, seed):
+    """Seeded patterned start (forced single-pixel toggles)."""
+    single = W.CandidateSpec(W.KIND_SINGLE, 3, 1)
+    for j in np.flatnonzero(W.random_state(opt.N, seed=seed, fill=0.3)):
+        opt.force([int(j)], single)
+
+
+def _check_against_single_runs(wls, bo, total, dtype, oracle, patterned=False, start=None):
+    improved = 0
+    for b, (wl, opt) in enumerate(zip(wls, bo.opts)):
+        ref = GreedyOptimizer(wl.geoms, wl.spec, dtype=dtype)
+        ref.fill()
+        if patterned:
+            _pattern(ref, 100 + b)
+        orc = O.OracleProblem(wl.geoms, wl.spec) if oracle else None
+        for _ in range(total):
+            ref.step()
+            if orc is not None:
+                orc.step()
+        torch.cuda.synchronize()
+        assert torch.equal(opt.state, ref.state)
+        assert int(opt.status.cpu()[0]) == int(ref.status.cpu()[0])
+        assert rel_err(opt.G[0][:, :opt.n].cpu().numpy(), ref.G[0][:, :ref.n].cpu().numpy()) <= 1e-14
+        assert rel_err(opt.E[0].cpu().numpy(), ref.E[0].cpu().numpy()) <= 1e-14
+        assert rel_err(opt.bands[0].cpu().numpy(), ref.bands[0].cpu().numpy()) <= 1e-14
+        assert float(opt.fom.cpu()[0]) == float(ref.fom.cpu()[0])
+        improved += int(not torch.equal(ref.state, start[b])) if patterned else int(ref.state.sum().item() > 0)
+        if orc is not None:
+            assert np.array_equal(opt.state.cpu().numpy(), orc.state)
+            assert rel_err(opt.G[0][:, :opt.n].cpu().numpy(), orc.Gs[0]) <= 1e-10
+            assert abs(float(opt.fom.cpu()[0]) - orc.fom()) <= 1e-10 * orc.fom()
+    assert improved > 0, "no problem of the batch accepted a flip"
+
+
+@pytest.mark.parametrize("sch", [Schedule(0, "given", True), Schedule(0, "given", True, 5), Schedule(3, "given", True),
+                                 Schedule(1, "given"), Schedule(3, "largest_first"), Schedule(6, "given")])
 def test_graph_batch_matches_single_problem_runs_and_oracle(sch):
     wls = _small_batch()
     bo = BatchOptimizer(wls)
@@ -47,20 +84,33 @@ def test_graph_batch_matches_single_problem_runs_and_oracle(sch):
     bo.capture(steps)           # one warm-up step runs during capture set-up
     bo.replay()
     torch.cuda.synchronize()
-    total = steps + 1
-    for wl, opt in zip(wls, bo.opts):
-        ref = GreedyOptimizer(wl.geoms, wl.spec)
-        ref.fill()
-        orc = O.OracleProblem(wl.geoms, wl.spec)
-        for _ in range(total):
-            ref.step()
-            orc.step()
-        torch.cuda.synchronize()
-        assert torch.equal(opt.state, ref.state)
-        assert rel_err(opt.G[0][:, :opt.n].cpu().numpy(), ref.G[0][:, :ref.n].cpu().numpy()) <= 1e-14
-        assert np.array_equal(opt.state.cpu().numpy(), orc.state)
-        assert rel_err(opt.G[0][:, :opt.n].cpu().numpy(), orc.Gs[0]) <= 1e-10
-        assert abs(float(opt.fom.cpu()[0]) - orc.fom()) <= 1e-10 * orc.fom()
+    _check_against_single_runs(wls, bo, steps + 1, "c128", oracle=True)
+
+
+@pytest.mark.parametrize("dtype,kind,count", [("c64", W.KIND_SINGLE, 6), ("c128", W.KIND_BRUSH2, 5),
+                                              ("c64", W.KIND_BRUSH2, 5), ("c128", W.KIND_SINGLE, 70)])
+def test_fused_batch_kinds_dtypes_and_groups(dtype, kind, count):
+    """Complex64 items (FP32 update), brush candidates and more items than one launch takes
+    (two groups) behave exactly like the single-problem calls."""
+    if kind == W.KIND_BRUSH2:
+        wls = _small_batch(count, sides=(10, 12, 14), kind=kind, ratios=(20,), dtype=dtype, seed=7)
+    elif count > B.BATCH_MAX:
+        wls = _small_batch(count, sides=(4, 5, 6), dtype=dtype, seed=8)
+    else:
+        wls = _small_batch(count, dtype=dtype)
+    bo = BatchOptimizer(wls, dtype=dtype)
+    assert bo.schedule.fused
+    bo.fill()
+    patterned = kind == W.KIND_BRUSH2        # brushes rarely improve a vacuum start
+    if patterned:
+        for b, opt in enumerate(bo.opts):
+            _pattern(opt, 100 + b)
+    start = [o.state.clone() for o in bo.opts]
+    bo.capture(2)
+    bo.replay()
+    torch.cuda.synchronize()
+    _check_against_single_runs(wls, bo, 3, dtype, oracle=False, patterned=patterned, start=start)
+    assert bo.total_applied() > 0
 
 
 def test_autotune_picks_a_timed_schedule():

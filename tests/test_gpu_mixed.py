@@ -1,4 +1,4 @@
-"""Mixed precision (complex64 G, rank-k p Woodbury update on the tensor cores with split TF32,
+"""Mixed precision (complex64 G, rank-k p Woodbury update on the tensor cores with split FP16 (kind::f16),
 FP64 capacitance solve, E and FOM) against the FP64 oracle, run lock-step from the oracle's
 choices as the error statement for the precision pattern, and against the complex64 update
 done in FP64 arithmetic."""
@@ -96,3 +96,47 @@ def test_c64_tensor_core_update_matches_fp64_arithmetic_update():
         torch.cuda.synchronize()
         assert rel_err(gpu_G(a), gpu_G(b)) <= 5e-6, t
         assert rel_err(gpu_E(a), gpu_E(b)) <= 5e-6, t
+
+
+@pytest.mark.parametrize("nx,beyond,seed", [(24, 2.0, 71), (24, 2.0, 73), (32, 3.0, 71)])
+def test_c64_free_running_final_fom_vs_fp64(nx, beyond, seed):
+    """From the same patterned start, the oracle, the FP64 path and the mixed form each run
+    greedily on their own choices (top-8 brushes, rank <= 32) until no improving move is left:
+    the FP64 path ends at the oracle's FOM, the mixed form within 1e-4 relative of it."""
+    wl = W.small(nx, nx, kind=W.KIND_BRUSH2, dir_mask=3, k=8, excl_radius=3, beyond_edge=beyond)
+    g = wl.geoms[0]
+    start = W.random_state(g.N, seed=seed, fill=0.3)
+    orc = O.OracleProblem(wl.geoms, wl.spec)
+    fp64 = GreedyOptimizer(wl.geoms, wl.spec, dtype="c128")
+    mixed = GreedyOptimizer(wl.geoms, wl.spec, dtype="c64")
+    single = W.CandidateSpec(W.KIND_SINGLE, 3, 1)
+    for opt in (fp64, mixed):
+        opt.fill()
+        for j in np.flatnonzero(start):
+            opt.force([int(j)], single)
+    for j in np.flatnonzero(start):
+        V, d = O.candidate(g, single, orc.state, int(j))
+        Gn, En, ok = O.apply_update(orc.Gs[0], orc.Es[0], V, d)
+        assert ok
+        orc.Gs, orc.Es = [Gn], [En]
+        orc.state[V] ^= 1
+    steps_orc = 0
+    while True:
+        ids = orc.choose(orc.evaluate())
+        if not ids:
+            break
+        orc.accept(ids)
+        steps_orc += 1
+    f_orc = orc.fom()
+    finals = []
+    for opt in (fp64, mixed):
+        res = opt.run(500)
+        assert res[-1].status == B.GF_ENOIMPROVE, "did not reach a design without improving moves"
+        foms = [r.fom for r in res]
+        assert all(b >= a * (1 - 1e-12) for a, b in zip(foms, foms[1:])), "FOM decreased"
+        finals.append((len(res) - 1, foms[-1]))
+    (s64, f64), (s32, f32) = finals
+    print(f"final FOM: oracle {f_orc:.10g} ({steps_orc} steps), FP64 path {f64:.10g} ({s64}), "
+          f"mixed {f32:.10g} ({s32}), mixed rel diff {abs(f32 - f_orc) / f_orc:.2e}")
+    assert s64 == steps_orc and abs(f64 - f_orc) <= 1e-10 * f_orc
+    assert abs(f32 - f_orc) <= 1e-4 * f_orc
