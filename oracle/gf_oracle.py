@@ -28,6 +28,9 @@ What it computes (Wang et al., arXiv:2202.05388), restated for the 2-D scalar E_
 * Top-k variant: candidates ordered by (-dFOM, id), taken greedily while they do not
   conflict (Chebyshev anchor distance <= excl_radius) with a taken one; the union is
   applied as one joint update when its joint dFOM is positive, else only the best one.
+* epsilon-greedy policy (Sec. V): with probability 1 - epsilon the greedy choice, with
+  probability epsilon a uniformly random one of the (up to) four best improving
+  candidates ranked by (-dFOM, id).  The two uniform numbers of a step are inputs.
 * Brute force (discrete Eqs. 2-3): G = (I - G0 X)^{-1} G0 and E = (I - G0 X)^{-1} E_inc.
 
 Everything is complex128 / float64 with numpy and scipy.special.hankel1 as the only
@@ -279,6 +282,26 @@ def select_topk(g: Geometry, spec: CandidateSpec, dfom: np.ndarray) -> List[int]
     return taken
 
 
+EXPLORE_TOP = 4      # Sec. V: exploration draws among the top four FOM-increasing actions
+
+
+def select_egreedy(dfom: np.ndarray, tie_rel: float, epsilon: float, u_explore: float,
+                   u_pick: float) -> Optional[int]:
+    """epsilon-greedy policy (Sec. V).  Exploit (u_explore >= epsilon): the greedy choice of
+    select_best.  Explore (u_explore < epsilon): rank floor(u_pick * m) of the m <= 4 best
+    improving candidates in (-dFOM, id) order (rank 0 is the best).  None when no candidate
+    increases the FOM.  u_explore, u_pick are uniform numbers in [0, 1)."""
+    best = select_best(dfom, tie_rel)
+    if best is None:
+        return None
+    if not u_explore < epsilon:
+        return best
+    order = np.lexsort((np.arange(dfom.size), -dfom))
+    top = [int(c) for c in order[:EXPLORE_TOP] if dfom[c] > 0.0]
+    r = int(u_pick * len(top))
+    return top[min(r, len(top) - 1)]
+
+
 # --------------------------------------------------------------------------- update
 def update_rows(G_rows: np.ndarray, C_rows: np.ndarray, dchi: np.ndarray, R: np.ndarray) -> np.ndarray:
     """Eq. 10 for a block of rows r: G_new[r, :] = G_old[r, :] + G_old[r, V] D R, where
@@ -352,6 +375,10 @@ class OracleProblem:
 
     def evaluate(self) -> np.ndarray:
         return evaluate_all(self.geoms, self.spec, self.state, self.Gs, self.Es)
+
+    def choose_egreedy(self, dfom: np.ndarray, epsilon: float, u_explore: float, u_pick: float) -> List[int]:
+        c = select_egreedy(dfom, self.spec.tie_rel, epsilon, u_explore, u_pick)
+        return [] if c is None else [c]
 
     def choose(self, dfom: np.ndarray) -> List[int]:
         if self.spec.k <= 1:

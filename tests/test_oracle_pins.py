@@ -381,3 +381,56 @@ def test_exact_columns_solve_the_dyson_system():
     x[:g.N] = state * (g.eps_mat - g.eps_bg)
     lhs = C - G0 @ (x[:, None] * C)
     assert np.max(np.abs(lhs - G0[:, cols])) < 1e-13
+
+
+# --------------------------------------------------------------------------- epsilon-greedy (Sec. V)
+def _ranked_improving(d):
+    """Independent ranking: Python's tuple sort of (-dFOM, id) over the improving entries."""
+    return [c for _, c in sorted((-float(v), c) for c, v in enumerate(d) if v > 0.0)]
+
+
+def test_egreedy_exploit_branch_is_the_greedy_policy():
+    rng = np.random.default_rng(41)
+    for _ in range(100):
+        d = rng.normal(size=40)
+        d[rng.integers(0, 40, 3)] = d.max()          # exact ties at the maximum
+        for u1 in (0.0, 0.3, 0.99):
+            assert O.select_egreedy(d, 1e-12, 0.0, u1, rng.random()) == O.select_best(d, 1e-12)
+        assert O.select_egreedy(d, 1e-12, 0.25, 0.25, rng.random()) == O.select_best(d, 1e-12)
+
+
+def test_egreedy_explore_branch_picks_uniformly_among_the_top_four():
+    rng = np.random.default_rng(42)
+    for _ in range(100):
+        d = np.round(rng.normal(size=30), 1)          # many exact ties below the top
+        ranked = _ranked_improving(d)
+        m = min(4, len(ranked))
+        if m == 0:
+            assert O.select_egreedy(d, 1e-12, 1.0, 0.0, 0.5) is None
+            continue
+        for r in range(m):
+            for frac in (0.0, 0.5, 0.999):
+                u2 = (r + frac) / m
+                assert O.select_egreedy(d, 1e-12, 1.0, 0.0, u2) == ranked[r]
+
+
+def test_egreedy_with_fewer_than_four_improving_and_none():
+    d = np.array([-1.0, 0.5, -2.0, 0.25, 0.0, -0.1])
+    assert [O.select_egreedy(d, 1e-12, 1.0, 0.1, u) for u in (0.0, 0.49, 0.5, 0.99)] == [1, 1, 3, 3]
+    assert O.select_egreedy(-np.abs(d) - 1.0, 1e-12, 1.0, 0.0, 0.3) is None
+
+
+def test_egreedy_choice_frequencies_match_the_closed_form():
+    """On a midpoint grid of (u_explore, u_pick) the share of each rank is exactly
+    (1 - eps) [r = 0] + eps / 4 (eps = 0.3, 40 x 40 grid, four improving candidates)."""
+    d = np.array([0.9, 0.1, 0.4, -0.3, 0.7, 0.2, -1.0])
+    ranked = _ranked_improving(d)[:4]                 # ids 0, 4, 2, 5
+    grid = (np.arange(40) + 0.5) / 40
+    counts = {c: 0 for c in ranked}
+    for u1 in grid:
+        for u2 in grid:
+            counts[O.select_egreedy(d, 1e-12, 0.3, float(u1), float(u2))] += 1
+    total = 40 * 40
+    assert counts[ranked[0]] == round(total * (0.7 + 0.3 / 4))
+    for c in ranked[1:]:
+        assert counts[c] == round(total * 0.3 / 4)
