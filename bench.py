@@ -529,12 +529,45 @@ def run_native(args):
     return 0
 
 
+def run_egreedy(args):
+    """Sec. V exploration study on the 21x21 metalens analogue: the greedy trajectory and
+    20 seeded epsilon-greedy trajectories for each of epsilon = 0.1, 0.2, 0.3, every one run to
+    termination.  Reported: accepted flips per second over the whole study (host-timed; each
+    step reads its status back) and the final-FOM statistics per epsilon."""
+    import torch
+    from paper_2202_05388_gb300 import build as BLD
+    from paper_2202_05388_gb300.egreedy import egreedy_study
+
+    torch.cuda.set_device(0)
+    BLD.build()
+    egreedy_study(epsilons=(0.0, 0.1), trajectories=1, seed=99, max_steps=4000)     # warm-up (kernel loading)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    res = egreedy_study(epsilons=(0.0, 0.1, 0.2, 0.3), trajectories=20, seed=0, max_steps=4000)
+    dt = time.perf_counter() - t0
+    clk = clocks.stop()
+    flips = sum(r["steps_mean"] * r["trajectories"] for r in res.values())
+    line = {"metric": METRIC + " [epsilon-greedy study]", "value": flips / dt, "unit": UNIT, "n_gpus": 1,
+            "steps": int(flips), "warmup": 1, "ms_per_step": 1e3 * dt / max(flips, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "egreedy_21x21_single_c128", "trajectories_per_epsilon": 20,
+                       "note": "every step synchronises to read its status (run-to-termination loop)"},
+            "study": {str(e): {k: v for k, v in r.items() if k != "finals"} for e, r in res.items()},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload.startswith("batch_48"):
         return run_batch(args)
+    if args.workload == "egreedy_21x21":
+        return run_egreedy(args)
     return run_native(args)
 
 

@@ -151,6 +151,17 @@ gf_status gf_select_topk(gf_handle* h, const gf_geom* geom, const gf_cand_spec* 
                          const double* dfom, int64_t ncand, int32_t* idx, double* val,
                          int32_t* status, void* ws, size_t ws_bytes, void* stream);
 
+/* epsilon-greedy policy (Sec. V): with probability 1 - epsilon the greedy choice of
+ * gf_select_topk (k = 1), with probability epsilon a uniformly random one of the (up to) four
+ * best improving candidates ranked by (-dFOM, id).  The randomness is an input: u (device, 2
+ * doubles in [0, 1)) -- explore when u[0] < epsilon, then take rank floor(u[1] m) of the m <= 4
+ * ranked candidates (rank 0 is the best).  Outputs and statuses as gf_select_topk with k = 1.
+ * spec->k must be 1; ws is required (gf_workspace_size bytes, 256-byte aligned). */
+gf_status gf_select_egreedy(gf_handle* h, const gf_geom* geom, const gf_cand_spec* spec,
+                            const double* dfom, int64_t ncand, double epsilon, const double* u,
+                            int32_t* idx, double* val, int32_t* status, void* ws, size_t ws_bytes,
+                            void* stream);
+
 /* Apply the candidates idx[0..k) (device; -1 ends the list) to every wavelength:
  * snapshot rows G[V,:] and columns G[:,V], solve A R = G[V,:] with A = I - G_VV D (Eq. 14,
  * FP64, partial pivoting), then G <- G + G[:,V] D R (Eq. 10) and E <- E + G[:,V] D y with

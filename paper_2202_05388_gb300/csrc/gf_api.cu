@@ -309,6 +309,29 @@ gf_status gf_select_topk(gf_handle* h, const gf_geom* geom, const gf_cand_spec* 
   return cuda_check(h, "gf_select_topk launch");
 }
 
+gf_status gf_select_egreedy(gf_handle* h, const gf_geom* geom, const gf_cand_spec* spec, const double* dfom,
+                            int64_t ncand, double epsilon, const double* u, int32_t* idx, double* val,
+                            int32_t* status, void* ws, size_t ws_bytes, void* stream) {
+  if (!h) return GF_EINVAL;
+  gf_status s = check_geom(h, geom);
+  if (s) return s;
+  if ((s = check_spec(h, geom, spec))) return s;
+  if (spec->k != 1) return fail(h, GF_EINVAL, "the epsilon-greedy policy chooses one candidate (k = 1, got %d)", spec->k);
+  if (ncand != gf_num_candidates(geom, spec))
+    return fail(h, GF_EINVAL, "ncand %lld does not match the candidate family (%lld)", (long long)ncand,
+                (long long)gf_num_candidates(geom, spec));
+  if (!(epsilon >= 0.0 && epsilon <= 1.0)) return fail(h, GF_EINVAL, "epsilon must lie in [0, 1]");
+  if (!dfom || !u || !idx || !val || !status) return fail(h, GF_EINVAL, "dfom, u, idx, val and status must be non-NULL");
+  const gf::WsLayout L = gf::ws_layout(*geom, 1, GF_C128, *spec);
+  if (!ws || ((uintptr_t)ws & 255u)) return fail(h, GF_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < L.sel + gf::topk_scratch_bytes())
+    return fail(h, GF_ENOMEM, "workspace has %zu bytes, selection needs %zu", ws_bytes, L.sel + gf::topk_scratch_bytes());
+  if ((s = bind_device(h))) return s;
+  gf::launch_select_egreedy(*geom, *spec, dfom, ncand, epsilon, u, idx, val, status, (char*)ws + L.sel,
+                            (cudaStream_t)stream);
+  return cuda_check(h, "gf_select_egreedy launch");
+}
+
 gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, int32_t dtype, uint8_t* state,
                           const gf_cand_spec* spec, const int32_t* idx, int32_t* status, double* fom_out,
                           int32_t* applied, void* ws, size_t ws_bytes, void* stream) {

@@ -141,6 +141,9 @@ void launch_eval(const EvalArgs& a, const uint8_t* state, const gf_cand_spec& sp
 size_t topk_scratch_bytes();
 void launch_select(const gf_geom& g, const gf_cand_spec& spec, const double* dfom, int64_t ncand,
                    int32_t* idx, double* val, int32_t* status, void* ws, cudaStream_t st);
+void launch_select_egreedy(const gf_geom& g, const gf_cand_spec& spec, const double* dfom, int64_t ncand,
+                           double epsilon, const double* u, int32_t* idx, double* val, int32_t* status, void* ws,
+                           cudaStream_t st);
 
 struct UpdLam {
   void* G;

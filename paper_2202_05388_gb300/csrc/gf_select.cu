@@ -146,9 +146,10 @@ __global__ void __launch_bounds__(kSelThreads) k_select_topk(const double* __res
 }
 
 // ---- multi-CTA top-k with exclusion: k passes; in pass t every CTA finds its best improving
-// candidate that conflicts with none of the t already taken, and the last CTA to finish (atomic
-// ticket after a memory fence -- no CTA waits for another) reduces the per-CTA results and
-// appends the winner.  Exactly the sorted-scan result.
+// candidate that conflicts with none of the t already taken (with excl < 0 a candidate only
+// conflicts with itself), and the last CTA to finish (atomic ticket after a memory fence -- no
+// CTA waits for another) reduces the per-CTA results and appends the winner.  Exactly the
+// sorted-scan result.
 struct TopkScratch {
   int32_t counter;      // CTAs finished in the current pass
   int32_t ntaken;
@@ -175,10 +176,15 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk_pass(const double* __rest
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncand; c += (int64_t)gridDim.x * blockDim.x) {
     const double v = dfom[c];
     if (!(v > 0.0) || !better(v, c, bv, bid)) continue;
-    int ax, ay;
-    cand_anchor(c, kind, nx, P, ax, ay);
     bool clash = false;
-    for (int q = 0; q < nt && !clash; ++q) clash = max(abs(ax - tax[q]), abs(ay - tay[q])) <= excl;
+    if (excl < 0) {
+      // no exclusion zone: only the candidates already taken are skipped (tax holds their ids)
+      for (int q = 0; q < nt && !clash; ++q) clash = c == (int64_t)tax[q];
+    } else {
+      int ax, ay;
+      cand_anchor(c, kind, nx, P, ax, ay);
+      for (int q = 0; q < nt && !clash; ++q) clash = max(abs(ax - tax[q]), abs(ay - tay[q])) <= excl;
+    }
     if (!clash) { bv = v; bid = c; }
   }
   block_best(bv, bid);
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk_pass(const double* __rest
     if (v > 0.0) {
       int ax, ay;
       cand_anchor(id, kind, nx, P, ax, ay);
-      sc->ax[nt] = ax;
+      sc->ax[nt] = excl < 0 ? (int32_t)id : ax;
       sc->ay[nt] = ay;
       idx[nt] = (int32_t)id;
       val[nt] = v;
@@ -231,8 +237,51 @@ __global__ void k_topk_end(const TopkScratch* sc, int k, int32_t* idx, double* v
   if (threadIdx.x == 0) *status = nt > 0 ? GF_OK : GF_ENOIMPROVE;
 }
 
-size_t topk_scratch_bytes() {
-  return sizeof(TopkScratch) + kTopkBlocks * (sizeof(double) + sizeof(int64_t)) + 64;
+// scratch: TopkScratch | per-CTA partials | the explore list of the epsilon-greedy policy
+static size_t topk_part_off() { return (sizeof(TopkScratch) + 63) & ~size_t(63); }
+static size_t explore_off() { return topk_part_off() + kTopkBlocks * (sizeof(double) + sizeof(int64_t)); }
+constexpr int kExploreTop = 4;      // Sec. V: exploration draws among the four best improving actions
+
+size_t topk_scratch_bytes() { return explore_off() + kExploreTop * (sizeof(double) + sizeof(int32_t)) + 64; }
+
+static void launch_topk_passes(const gf_geom& g, int kind, int k, int excl, const double* dfom, int64_t ncand,
+                               int32_t* idx, double* val, void* ws, cudaStream_t st) {
+  TopkScratch* sc = reinterpret_cast<TopkScratch*>(ws);
+  double* part_v = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + topk_part_off());
+  int64_t* part_i = reinterpret_cast<int64_t*>(part_v + kTopkBlocks);
+  int64_t blocks = (ncand + kTopkThreads - 1) / kTopkThreads;
+  if (blocks > kTopkBlocks) blocks = kTopkBlocks;
+  k_topk_begin<<<1, 1, 0, st>>>(sc);
+  for (int t = 0; t < k; ++t)
+    k_topk_pass<<<(unsigned)blocks, kTopkThreads, 0, st>>>(dfom, ncand, kind, g.nx, g.ny, excl, t, sc, part_v,
+                                                           part_i, idx, val);
+}
+
+// epsilon-greedy (Sec. V): the greedy choice is already in idx[0] / val[0] / status; when
+// u[0] < epsilon it is replaced by rank floor(u[1] m) of the m <= 4 best improving candidates
+// in (-dFOM, id) order.  u: two uniform numbers in [0, 1) drawn by the caller.
+__global__ void k_egreedy_pick(const TopkScratch* __restrict__ sc, const int32_t* __restrict__ top_i,
+                               const double* __restrict__ top_v, double epsilon, const double* __restrict__ u,
+                               int32_t* idx, double* val, const int32_t* __restrict__ status) {
+  if (threadIdx.x != 0 || *status != GF_OK) return;
+  const int m = sc->ntaken < kExploreTop ? sc->ntaken : kExploreTop;
+  if (m < 1 || !(u[0] < epsilon)) return;
+  int r = (int)(u[1] * (double)m);
+  if (r > m - 1) r = m - 1;
+  if (r < 0) r = 0;
+  idx[0] = top_i[r];
+  val[0] = top_v[r];
+}
+
+void launch_select_egreedy(const gf_geom& g, const gf_cand_spec& spec, const double* dfom, int64_t ncand,
+                           double epsilon, const double* u, int32_t* idx, double* val, int32_t* status, void* ws,
+                           cudaStream_t st) {
+  k_select_best<<<1, kSelThreads, 0, st>>>(dfom, ncand, spec.tie_rel, idx, val, status);
+  int32_t* top_i = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ws) + explore_off());
+  double* top_v = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + explore_off() + 64);
+  launch_topk_passes(g, spec.kind, kExploreTop, -1, dfom, ncand, top_i, top_v, ws, st);   // no exclusion
+  k_egreedy_pick<<<1, 32, 0, st>>>(reinterpret_cast<const TopkScratch*>(ws), top_i, top_v, epsilon, u, idx, val,
+                                   status);
 }
 
 void launch_select(const gf_geom& g, const gf_cand_spec& spec, const double* dfom, int64_t ncand,
@@ -246,16 +295,8 @@ void launch_select(const gf_geom& g, const gf_cand_spec& spec, const double* dfo
                                              status);
     return;
   }
-  TopkScratch* sc = reinterpret_cast<TopkScratch*>(ws);
-  double* part_v = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + ((sizeof(TopkScratch) + 63) & ~size_t(63)));
-  int64_t* part_i = reinterpret_cast<int64_t*>(part_v + kTopkBlocks);
-  int64_t blocks = (ncand + kTopkThreads - 1) / kTopkThreads;
-  if (blocks > kTopkBlocks) blocks = kTopkBlocks;
-  k_topk_begin<<<1, 1, 0, st>>>(sc);
-  for (int t = 0; t < spec.k; ++t)
-    k_topk_pass<<<(unsigned)blocks, kTopkThreads, 0, st>>>(dfom, ncand, spec.kind, g.nx, g.ny, spec.excl_radius, t, sc,
-                                                           part_v, part_i, idx, val);
-  k_topk_end<<<1, 256, 0, st>>>(sc, spec.k, idx, val, status);
+  launch_topk_passes(g, spec.kind, spec.k, spec.excl_radius, dfom, ncand, idx, val, ws, st);
+  k_topk_end<<<1, 256, 0, st>>>(reinterpret_cast<const TopkScratch*>(ws), spec.k, idx, val, status);
 }
 
 }  // namespace gf

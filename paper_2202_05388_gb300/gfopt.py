@@ -32,7 +32,7 @@ EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_v
            "gf_eval_candidates", "gf_select_topk", "gf_apply_update", "gf_profile_begin",
            "gf_profile_end", "gf_set_update_algo", "gf_refresh", "gf_refresh_workspace_size",
            "gf_fill_g0_static", "gf_batch_table_size", "gf_batch_create", "gf_batch_step",
-           "gf_batch_set_schedule", "gf_batch_destroy"]
+           "gf_batch_set_schedule", "gf_batch_destroy", "gf_select_egreedy"]
 
 
 class GfError(RuntimeError):
@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
                                        C.POINTER(C.c_double), C.POINTER(C.c_int32), P, C.c_size_t, P]),
             "gf_profile_end": (C.c_int32, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+            "gf_select_egreedy": (C.c_int32, [P, C.POINTER(gf_geom), C.POINTER(gf_cand_spec), P, C.c_int64,
+                                              C.c_double, P, P, P, P, P, C.c_size_t, P]),
             "gf_batch_table_size": (C.c_size_t, [C.c_int32]),
             "gf_batch_create": (C.c_int32, [P, C.c_int32, C.POINTER(gf_batch_item), C.c_int32,
                                             C.POINTER(gf_cand_spec), P, C.c_size_t, P, C.POINTER(P)]),
@@ -205,6 +207,12 @@ class Handle:
         self._check(self.lib.gf_select_topk(self.h, C.byref(g), C.byref(s), _ptr(dfom), int(ncand),
                                             _ptr(idx), _ptr(val), _ptr(status), _ptr(ws),
                                             int(ws_bytes), _stream(stream)))
+
+    def gf_select_egreedy(self, geom, spec, dfom, ncand, epsilon, u, idx, val, status, ws, ws_bytes, stream=None):
+        g, s = geom_struct(geom), spec_struct(spec)
+        self._check(self.lib.gf_select_egreedy(self.h, C.byref(g), C.byref(s), _ptr(dfom), int(ncand), float(epsilon),
+                                               _ptr(u), _ptr(idx), _ptr(val), _ptr(status), _ptr(ws), int(ws_bytes),
+                                               _stream(stream)))
 
     def gf_apply_update(self, probs, dtype, state, spec, idx, status, fom_out, ws, ws_bytes,
                         stream=None, applied=None):

@@ -58,6 +58,16 @@ class GreedyOptimizer:
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.probs = [B.problem_struct(gg, self.G[l], self.ldg, self.E[l], self.bands[l])
                       for l, gg in enumerate(self.geoms)]
+        self.epsilon = None          # None: greedy policy; else the epsilon-greedy policy
+
+    def set_egreedy(self, epsilon: float, seed: int, horizon: int = 4096):
+        """epsilon-greedy policy (Sec. V).  The two uniform numbers of every step are drawn
+        up front on the host (numpy PCG64, seeded) and kept on the device; step t reads row
+        t (``uniforms`` holds them for replays and checks)."""
+        self.epsilon = float(epsilon)
+        self.uniforms = np.random.default_rng(seed).random((horizon, 2))
+        self._u = torch.tensor(self.uniforms, dtype=torch.float64, device=self.device)
+        self._t = 0
 
     # ---- stages (asynchronous on the current stream)
     def _st(self):
@@ -73,6 +83,14 @@ class GreedyOptimizer:
         self.h.gf_eval_candidates(self.probs, self.dtype, self.state, self.spec, self.dfom, self._st())
 
     def select(self):
+        if self.epsilon is not None:
+            if self._t >= self._u.shape[0]:
+                raise IndexError("epsilon-greedy horizon exhausted; call set_egreedy with a larger horizon")
+            self.h.gf_select_egreedy(self.geoms[0], self.spec, self.dfom, self.ncand, self.epsilon,
+                                     self._u[self._t], self.idx, self.val, self.status, self.ws, self.ws_bytes,
+                                     self._st())
+            self._t += 1
+            return
         self.h.gf_select_topk(self.geoms[0], self.spec, self.dfom, self.ncand, self.idx, self.val,
                               self.status, self.ws, self.ws_bytes, self._st())
 
