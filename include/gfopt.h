@@ -205,6 +205,47 @@ gf_status gf_refresh(gf_handle* h, const gf_problem* prob, int32_t dtype, const 
 #define GF_UPDATE_DFMA 1
 gf_status gf_set_update_algo(gf_handle* h, int32_t algo);
 
+/* Deferred (low-rank) form, single wavelength, one candidate per step (k = 1), FP64.
+ * Eq. 10 applied step after step gives G_t = G0 + sum_s C_s D_s R_s (C_s = G_s[:, V_s],
+ * R_s = A_s^-1 G_s[V_s, :], Eq. 14); with G = G^T (reciprocity) every term is C_s M_s C_s^T with
+ * M_s = D_s A_s^-1.  This form keeps G0 implicit (its offset table, in ws) and stores only the
+ * columns C_s (n x K, K = pixels flipped so far) and the blocks M_s, plus the entries candidate
+ * evaluation reads: the bands, the monitor row G[N, :] and E.  Memory O(n K) instead of
+ * O(n^2); a step costs O(n K p).  Steps: gf_lowrank_eval, gf_select_topk (or
+ * gf_select_egreedy), gf_lowrank_update.  Fields (device, 16-byte aligned, caller-owned):
+ *   E (n complex128), bands (9 N complex128, layout of gf_problem.bands), monrow (n
+ *   complex128), U (n x max_cols complex128, column-major: column k at U + k n).
+ * ws (gf_lowrank_workspace_size bytes, 256-byte aligned) must be the same buffer for
+ * gf_lowrank_init and every later call on the problem: it holds the G0 table, the blocks and
+ * the term bookkeeping.  When K would exceed max_cols, the update sets *status = GF_ENOMEM and
+ * changes nothing. */
+typedef struct gf_lowrank {
+  gf_geom geom;
+  void* E;
+  void* bands;
+  void* monrow;
+  void* U;
+  int32_t max_cols;
+} gf_lowrank;
+size_t gf_lowrank_workspace_size(const gf_geom* geom, int32_t max_cols);
+/* Vacuum start: G0 table, bands, monitor row, E = E_inc, no terms. */
+gf_status gf_lowrank_init(gf_handle* h, const gf_lowrank* lr, void* ws, size_t ws_bytes, void* stream);
+/* dFOM of every candidate (as gf_eval_candidates). */
+gf_status gf_lowrank_eval(gf_handle* h, const gf_lowrank* lr, const uint8_t* state, const gf_cand_spec* spec,
+                          double* dfom, void* stream);
+/* Apply idx[0] (as gf_apply_update with k = 1): new columns G[:, V], capacitance solve,
+ * append the term, update bands, monitor row, E, state and *fom_out. */
+gf_status gf_lowrank_update(gf_handle* h, const gf_lowrank* lr, uint8_t* state, const gf_cand_spec* spec,
+                            const int32_t* idx, int32_t* status, double* fom_out, int32_t* applied,
+                            void* ws, size_t ws_bytes, void* stream);
+/* Terms and columns stored so far (blocking: synchronises stream). */
+gf_status gf_lowrank_count(gf_handle* h, const gf_lowrank* lr, void* ws, size_t ws_bytes, int32_t* nterms,
+                           int32_t* ncols, void* stream);
+/* Dense complex128 G (n x ldg) = G0 + sum_s C_s M_s C_s^T, for checks or a switch to the dense
+ * form; O(n^2 K) work. */
+gf_status gf_lowrank_materialize(gf_handle* h, const gf_lowrank* lr, void* G, int64_t ldg, void* ws,
+                                 size_t ws_bytes, void* stream);
+
 /* Batches: many independent problems advanced together (the problems of a design study, e.g.
  * sweeps over sizes, wavelengths and focal distances; the paper parallelises one problem's
  * partitions instead, Sec. III).  Each item is one single-wavelength problem with its own
@@ -245,7 +286,8 @@ void gf_batch_destroy(gf_batch* b);
 
 /* Kernel timing (no counterpart in the paper; it backs the per-step timers of the bench).
  * gf_profile_begin arms up to max_records CUDA-event pairs that the library records on the
- * launching stream around every launch of the G-update kernel.  gf_profile_end waits for the
+ * launching stream around every launch of the G-update kernel (in the deferred form: of the
+ * column product, whose flops are counted as 8 K p n).  gf_profile_end waits for the
  * last recorded event, returns the summed kernel time in ms, the number of timed launches and
  * the algorithmic bytes (read + write of every G entry) and flops of those launches, and
  * disarms.  Launches beyond max_records are not timed.  Not for use inside graph capture. */

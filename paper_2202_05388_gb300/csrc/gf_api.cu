@@ -129,6 +129,7 @@ gf_status api_cuda_check(gf_handle* h, const char* where) { return cuda_check(h,
 gf_status api_fail_msg(gf_handle* h, gf_status s, const char* msg) { return fail(h, s, "%s", msg); }
 int api_device(const gf_handle* h) { return h->device; }
 int api_sm_count(const gf_handle* h) { return h->sm_count; }
+KernelTimer* api_timer(gf_handle* h) { return &h->timer; }
 gf_status api_check_spec(gf_handle* h, const gf_geom* g, const gf_cand_spec* s) { return check_spec(h, g, s); }
 
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -165,6 +165,12 @@ void launch_fill_expand(const gf_geom& g, int dtype, void* G, int64_t ldg, const
   k_fill_field<<<grid_for(N + 1, 256), 256, 0, st>>>(g.nx, g.ny, g.dx, k, g.mon_y, E);
 }
 
+void launch_fill_field(const gf_geom& g, cplx* E, cudaStream_t st) {
+  const int64_t N = (int64_t)g.nx * g.ny;
+  const double k = 2.0 * M_PI / g.wavelength;
+  k_fill_field<<<grid_for(N + 1, 256), 256, 0, st>>>(g.nx, g.ny, g.dx, k, g.mon_y, E);
+}
+
 void launch_bands(const gf_geom& g, int dtype, const void* G, int64_t ldg, cplx* bands,
                   cudaStream_t st) {
   const int64_t N = (int64_t)g.nx * g.ny;

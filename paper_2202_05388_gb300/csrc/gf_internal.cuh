@@ -63,6 +63,37 @@ __host__ __device__ __forceinline__ void band_offset(int b, int& ddx, int& ddy) 
   ddy = ty[b];
 }
 
+// Pixels and contrast changes of candidate c given the current state (same rule as the
+// candidate kernels).  Appends to V/dchi; returns the number appended.
+__device__ __forceinline__ int cand_pixels(int64_t c, int kind, int dir_mask, int nx, int ny, double chi,
+                           const uint8_t* state, int32_t* V, double* dchi) {
+  const int64_t N = (int64_t)nx * ny;
+  if (kind == GF_KIND_SINGLE) {
+    if (c < 0 || c >= N) return 0;
+    uint8_t s = state[c];
+    if (s == 0 && (dir_mask & GF_DIR_FILL)) { V[0] = (int32_t)c; dchi[0] = chi; return 1; }
+    if (s != 0 && (dir_mask & GF_DIR_CLEAR)) { V[0] = (int32_t)c; dchi[0] = -chi; return 1; }
+    return 0;
+  }
+  const int64_t P = (int64_t)(nx - 1) * (ny - 1);
+  if (c < 0 || c >= 2 * P) return 0;
+  const int dir = (int)(c / P);
+  const int64_t a = c - dir * P;
+  if (!(dir_mask & (dir == 0 ? GF_DIR_FILL : GF_DIR_CLEAR))) return 0;
+  const int ay = (int)(a / (nx - 1)), ax = (int)(a - (int64_t)ay * (nx - 1));
+  const int64_t j0 = (int64_t)ay * nx + ax;
+  const int64_t q[4] = {j0, j0 + 1, j0 + nx, j0 + nx + 1};
+  int m = 0;
+  for (int u = 0; u < 4; ++u) {
+    if (state[q[u]] == (dir == 0 ? 0 : 1)) {
+      V[m] = (int32_t)q[u];
+      dchi[m] = dir == 0 ? chi : -chi;
+      ++m;
+    }
+  }
+  return m;
+}
+
 // ----------------------------------------------------------------------------- workspace
 // Per-step control block written by the capacitance kernel, read by the panel/update kernels.
 struct UpdCtl {
@@ -120,6 +151,7 @@ void launch_fill_expand(const gf_geom& g, int dtype, void* G, int64_t ldg, const
                         cplx* E, cudaStream_t st);
 void launch_bands(const gf_geom& g, int dtype, const void* G, int64_t ldg, cplx* bands,
                   cudaStream_t st);
+void launch_fill_field(const gf_geom& g, cplx* E, cudaStream_t st);
 
 struct EvalLam {     // one wavelength as seen by the candidate kernels
   const void* G;
@@ -175,6 +207,8 @@ struct KernelTimer {
   int* bytes_per_entry = nullptr;
   void release();
 };
+
+KernelTimer* api_timer(gf_handle* h);
 
 bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0,
                               const cplx* S, const UpdCtl* ctl, uint8_t* ozA, int32_t* ozE,

@@ -1,0 +1,491 @@
+// Deferred (low-rank) form of the greedy step: G is never materialised.
+//
+// Eq. 10 applied step after step gives G_t = G0 + sum_s C_s D_s R_s with C_s = G_s[:, V_s] and
+// R_s = A_s^{-1} G_s[V_s, :] (Eq. 14).  G is symmetric (reciprocity of the scalar Green's
+// function; the update preserves it), so G_s[V_s, :] = C_s^T and every term is
+// C_s M_s C_s^T with the p_s x p_s block M_s = D_s A_s^{-1}.  The state of a problem is then
+//   * G0 implicitly: its table of values by pixel offset plus the monitor column (gf_fill_g0's
+//     table, kept in the workspace);
+//   * the stored columns C_s (n x sum p_s, column-major) and blocks M_s;
+//   * the data candidate evaluation reads, kept explicit: the nine bands (G_VV blocks of
+//     Eq. 8), the monitor row G[N, :] and the field E.
+// A step computes the p new columns G[:, V] = G0[:, V] + sum_s C_s (M_s C_s[V, :]^T) (an n x K
+// by K x p product, K = columns stored), solves the p x p capacitance system (Eqs. 8-9, 14),
+// appends the term and updates bands, monitor row and E by O(n p) work (Eqs. 10 and 4
+// restricted to those entries).  Memory is O(n K) instead of O(n^2).
+#include <math.h>
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+constexpr int kLrP = 4;            // pixels per candidate at most (2x2 brush)
+
+struct LrCount {
+  int32_t nterms, ncols;
+};
+
+// Per-step scratch written by the pixel / capacitance kernels.
+struct LrStep {
+  int32_t skip, p, col0, pad;
+  int32_t V[kLrP];
+  double dchi[kLrP];
+  cplx dy[kLrP];          // D y, y = A^{-1} E_V
+  cplx M[kLrP * kLrP];    // D A^{-1}, row-major p x p (stride kLrP)
+};
+
+// workspace layout: G0 table (2N) | M blocks | term first column | term width | column -> term |
+// counters | step | w (K x kLrP)
+struct LrLayout {
+  size_t table, coef, tcol, tp, colterm, count, step, w, total;
+};
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static LrLayout lr_layout(const gf_geom& g, int max_cols) {
+  const int64_t N = (int64_t)g.nx * g.ny;
+  LrLayout L;
+  size_t o = 0;
+  L.table = o; o = up256(o + sizeof(cplx) * (size_t)(2 * N));
+  L.coef = o; o = up256(o + sizeof(cplx) * kLrP * kLrP * (size_t)max_cols);
+  L.tcol = o; o = up256(o + sizeof(int32_t) * (size_t)max_cols);
+  L.tp = o; o = up256(o + sizeof(int32_t) * (size_t)max_cols);
+  L.colterm = o; o = up256(o + sizeof(int32_t) * (size_t)max_cols);
+  L.count = o; o = up256(o + sizeof(LrCount));
+  L.step = o; o = up256(o + sizeof(LrStep));
+  L.w = o; o = up256(o + sizeof(cplx) * kLrP * (size_t)max_cols);
+  L.total = o;
+  return L;
+}
+
+struct LrArgs {
+  int nx, ny;
+  int64_t N, n;
+  double chi;
+  int max_cols;
+  cplx* E;
+  cplx* bands;
+  cplx* mon;
+  cplx* U;
+  const cplx* table;
+  cplx* coef;
+  int32_t* tcol;
+  int32_t* tp;
+  int32_t* colterm;
+  LrCount* count;
+  LrStep* step;
+  cplx* w;
+};
+
+// G0[i, j] of a pixel column j (i may be the monitor N)
+__device__ __forceinline__ cplx g0_entry(const LrArgs& a, int64_t i, int64_t j) {
+  if (i == a.N) return a.table[a.N + j];
+  const int iy = (int)(i / a.nx), ix = (int)(i - (int64_t)iy * a.nx);
+  const int jy = (int)(j / a.nx), jx = (int)(j - (int64_t)jy * a.nx);
+  const int dy = iy > jy ? iy - jy : jy - iy, dx = ix > jx ? ix - jx : jx - ix;
+  return a.table[(int64_t)dy * a.nx + dx];
+}
+
+// ---- initial state: bands, monitor row and field of the vacuum background; no terms
+__global__ void k_lr_init(LrArgs a) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < GF_NBANDS * a.N;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / a.N);
+    const int64_t i = t - (int64_t)b * a.N;
+    const int iy = (int)(i / a.nx), ix = (int)(i % a.nx);
+    int ddx, ddy;
+    band_offset(b, ddx, ddy);
+    const int jx = ix + ddx, jy = iy + ddy;
+    cplx v = mk(0.0, 0.0);
+    if (jx >= 0 && jx < a.nx && jy >= 0 && jy < a.ny) v = a.table[(int64_t)(ddy < 0 ? -ddy : ddy) * a.nx + (ddx < 0 ? -ddx : ddx)];
+    a.bands[t] = v;
+  }
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.n; j += (int64_t)gridDim.x * blockDim.x)
+    a.mon[j] = j < a.N ? a.table[a.N + j] : mk(0.0, 0.0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.count->nterms = 0;
+    a.count->ncols = 0;
+  }
+}
+
+// ---- the chosen candidate's pixels (device status and capacity checks)
+__global__ void k_lr_pixels(LrArgs a, int kind, int dir_mask, const uint8_t* __restrict__ state,
+                            const int32_t* __restrict__ idx, int32_t* status) {
+  if (threadIdx.x != 0) return;
+  LrStep* s = a.step;
+  s->skip = 1;
+  s->p = 0;
+  if (*status != GF_OK || idx[0] < 0) return;
+  const int p = cand_pixels(idx[0], kind, dir_mask, a.nx, a.ny, a.chi, state, s->V, s->dchi);
+  if (p == 0) return;
+  const LrCount c = *a.count;
+  if (c.ncols + p > a.max_cols || c.nterms + 1 > a.max_cols) {
+    *status = GF_ENOMEM;        // term storage full: materialise (gf_lowrank_materialize) and restart
+    return;
+  }
+  s->p = p;
+  s->col0 = c.ncols;
+  s->skip = 0;
+}
+
+// ---- w[k][u] = (M_s C_s[v_u, :]^T)_a for stored column k = first column of term s + a
+__global__ void k_lr_w(LrArgs a) {
+  const LrStep* s = a.step;
+  if (s->skip) return;
+  const int p = s->p;
+  const int K = s->col0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t info = a.colterm[k];
+    const int term = info >> 2, row = info & 3;
+    const int c0 = a.tcol[term], pt = a.tp[term];
+    const cplx* M = a.coef + (int64_t)term * kLrP * kLrP;
+    for (int u = 0; u < kLrP; ++u) {
+      cplx acc = mk(0.0, 0.0);
+      if (u < p)
+        for (int b = 0; b < pt; ++b) acc = cfma(M[row * kLrP + b], a.U[(int64_t)(c0 + b) * a.n + s->V[u]], acc);
+      a.w[k * kLrP + u] = acc;
+    }
+  }
+}
+
+// ---- the p new columns: C[:, u] = G0[:, v_u] + sum_k U[:, k] w[k][u], appended to U
+constexpr int kLrThreads = 256;
+constexpr int kLrChunk = 256;      // stored columns per shared-memory chunk of w
+__global__ void __launch_bounds__(kLrThreads) k_lr_columns(LrArgs a, int32_t* __restrict__ prof) {
+  const LrStep* s = a.step;
+  if (prof && blockIdx.x == 0 && threadIdx.x == 0) *prof = s->skip ? 0 : s->col0 * s->p;
+  if (s->skip) return;
+  __shared__ cplx sw[kLrChunk * kLrP];
+  const int p = s->p;
+  const int K = s->col0;
+  int V[kLrP];
+#pragma unroll
+  for (int u = 0; u < kLrP; ++u) V[u] = s->V[u];
+  for (int64_t i0 = (int64_t)blockIdx.x * kLrThreads; i0 < a.n; i0 += (int64_t)gridDim.x * kLrThreads) {
+    const int64_t i = i0 + threadIdx.x;
+    cplx acc[kLrP];
+#pragma unroll
+    for (int u = 0; u < kLrP; ++u) acc[u] = (i < a.n && u < p) ? g0_entry(a, i, V[u]) : mk(0.0, 0.0);
+    for (int k0 = 0; k0 < K; k0 += kLrChunk) {
+      const int kc = K - k0 < kLrChunk ? K - k0 : kLrChunk;
+      __syncthreads();
+      for (int t = threadIdx.x; t < kc * kLrP; t += kLrThreads) sw[t] = a.w[(int64_t)k0 * kLrP + t];
+      __syncthreads();
+      if (i < a.n) {
+        for (int k = 0; k < kc; ++k) {
+          const cplx uk = a.U[(int64_t)(k0 + k) * a.n + i];
+#pragma unroll
+          for (int u = 0; u < kLrP; ++u)
+            if (u < p) acc[u] = cfma(uk, sw[k * kLrP + u], acc[u]);
+        }
+      }
+    }
+    if (i < a.n) {
+#pragma unroll
+      for (int u = 0; u < kLrP; ++u)
+        if (u < p) a.U[(int64_t)(K + u) * a.n + i] = acc[u];
+    }
+  }
+}
+
+// ---- capacitance: A = I - G_VV D from the new columns, y = A^{-1} E_V, M = D A^{-1} (one thread;
+// p <= 4, Gaussian elimination with partial pivoting as in the candidate kernels)
+__global__ void k_lr_capacitance(LrArgs a, int32_t* status) {
+  if (threadIdx.x != 0) return;
+  LrStep* s = a.step;
+  if (s->skip) return;
+  const int p = s->p;
+  const int K = s->col0;
+  cplx A[kLrP][kLrP], X[kLrP][kLrP + 1];
+  double norm = 0.0;
+  for (int r = 0; r < p; ++r) {
+    double rs = 0.0;
+    for (int c = 0; c < p; ++c) {
+      const cplx g = a.U[(int64_t)(K + c) * a.n + s->V[r]];      // G[v_r, v_c]
+      A[r][c] = mk(r == c ? 1.0 : 0.0, 0.0) - s->dchi[c] * g;
+      rs += cabs1(A[r][c]);
+    }
+    norm = fmax(norm, rs);
+  }
+  // right-hand sides: the identity (for A^{-1}) and E_V (for y)
+  for (int r = 0; r < p; ++r) {
+    for (int c = 0; c < p; ++c) X[r][c] = mk(r == c ? 1.0 : 0.0, 0.0);
+    X[r][p] = a.E[s->V[r]];
+  }
+  const double thresh = kSingularRel * norm;
+  for (int c = 0; c < p; ++c) {
+    int piv = c;
+    double best = cabs1(A[c][c]);
+    for (int r = c + 1; r < p; ++r)
+      if (cabs1(A[r][c]) > best) { best = cabs1(A[r][c]); piv = r; }
+    if (!(best >= thresh) || !(best > 0.0)) {
+      *status = GF_ESINGULAR;
+      s->skip = 1;
+      return;
+    }
+    if (piv != c) {
+      for (int v = 0; v < p; ++v) { cplx t = A[c][v]; A[c][v] = A[piv][v]; A[piv][v] = t; }
+      for (int v = 0; v <= p; ++v) { cplx t = X[c][v]; X[c][v] = X[piv][v]; X[piv][v] = t; }
+    }
+    for (int r = c + 1; r < p; ++r) {
+      const cplx f = cdiv(A[r][c], A[c][c]);
+      for (int v = c; v < p; ++v) A[r][v] = A[r][v] - f * A[c][v];
+      for (int v = 0; v <= p; ++v) X[r][v] = X[r][v] - f * X[c][v];
+    }
+  }
+  for (int c = p - 1; c >= 0; --c)
+    for (int v = 0; v <= p; ++v) {
+      cplx acc = X[c][v];
+      for (int q = c + 1; q < p; ++q) acc = acc - A[c][q] * X[q][v];
+      X[c][v] = cdiv(acc, A[c][c]);
+    }
+  const int term = a.count->nterms;
+  cplx* M = a.coef + (int64_t)term * kLrP * kLrP;
+  for (int r = 0; r < kLrP; ++r)
+    for (int c = 0; c < kLrP; ++c) {
+      const cplx m = (r < p && c < p) ? s->dchi[r] * X[r][c] : mk(0.0, 0.0);
+      M[r * kLrP + c] = m;
+      s->M[r * kLrP + c] = m;
+    }
+  for (int r = 0; r < p; ++r) s->dy[r] = s->dchi[r] * X[r][p];
+  a.tcol[term] = K;
+  a.tp[term] = p;
+  for (int u = 0; u < p; ++u) a.colterm[K + u] = (term << 2) | u;
+  a.count->nterms = term + 1;
+  a.count->ncols = K + p;
+}
+
+// ---- Eq. 10 on the explicit entries (bands, monitor row) and Eq. 4 on E; state, FOM
+__global__ void k_lr_apply(LrArgs a, uint8_t* __restrict__ state, double* __restrict__ fom_out,
+                           int32_t* __restrict__ applied) {
+  const LrStep* s = a.step;
+  const bool skip = s->skip != 0;
+  const int p = skip ? 0 : s->p;
+  const int K = s->col0;
+  const cplx* C = a.U + (int64_t)K * a.n;        // the new columns, C[u * n + i]
+  cplx M[kLrP * kLrP];
+#pragma unroll
+  for (int t = 0; t < kLrP * kLrP; ++t) M[t] = skip ? mk(0.0, 0.0) : s->M[t];
+  // q_N = C[N, :] M (row vector) for the monitor row
+  cplx qN[kLrP];
+#pragma unroll
+  for (int c = 0; c < kLrP; ++c) {
+    qN[c] = mk(0.0, 0.0);
+    for (int r = 0; r < p; ++r) qN[c] = cfma(C[(int64_t)r * a.n + a.N], M[r * kLrP + c], qN[c]);
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (p > 0) {
+      cplx ri[kLrP], qi[kLrP];
+#pragma unroll
+      for (int u = 0; u < kLrP; ++u) ri[u] = u < p ? C[(int64_t)u * a.n + i] : mk(0.0, 0.0);
+#pragma unroll
+      for (int c = 0; c < kLrP; ++c) {
+        qi[c] = mk(0.0, 0.0);
+#pragma unroll
+        for (int r = 0; r < kLrP; ++r) qi[c] = cfma(ri[r], M[r * kLrP + c], qi[c]);
+      }
+      cplx e = a.E[i];
+      for (int u = 0; u < p; ++u) e = cfma(ri[u], s->dy[u], e);
+      a.E[i] = e;
+      cplx dm = mk(0.0, 0.0);
+      for (int c = 0; c < p; ++c) dm = cfma(qN[c], ri[c], dm);
+      a.mon[i] = a.mon[i] + dm;
+      if (i < a.N) {
+        const int iy = (int)(i / a.nx), ix = (int)(i % a.nx);
+        for (int b = 0; b < GF_NBANDS; ++b) {
+          int ddx, ddy;
+          band_offset(b, ddx, ddy);
+          const int jx = ix + ddx, jy = iy + ddy;
+          if (jx < 0 || jx >= a.nx || jy < 0 || jy >= a.ny) continue;
+          const int64_t j = (int64_t)jy * a.nx + jx;
+          cplx d = mk(0.0, 0.0);
+          for (int c = 0; c < p; ++c) d = cfma(qi[c], C[(int64_t)c * a.n + j], d);
+          a.bands[(int64_t)b * a.N + i] = a.bands[(int64_t)b * a.N + i] + d;
+        }
+      }
+    }
+    if (i == a.N) {
+      *fom_out = abs2(a.E[a.N]);
+      if (applied) *applied = p > 0 ? 1 : 0;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < p) state[s->V[threadIdx.x]] ^= 1;
+}
+
+// ---- dense G = G0 + sum_s C_s M_s C_s^T (checks and flushes; O(n^2 K))
+__global__ void k_lr_materialize(LrArgs a, double2* __restrict__ G, int64_t ldg) {
+  const int K = a.count->ncols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.n * a.n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / a.n, j = t - i * a.n;
+    cplx v;
+    if (i == a.N && j == a.N) v = mk(0.0, 0.0);
+    else if (j == a.N) v = g0_entry(a, j, i);
+    else v = g0_entry(a, i, j);
+    for (int k = 0; k < K; ++k) {
+      const int32_t info = a.colterm[k];
+      const int term = info >> 2, row = info & 3;
+      const int c0 = a.tcol[term], pt = a.tp[term];
+      cplx mj = mk(0.0, 0.0);
+      for (int b = 0; b < pt; ++b) mj = cfma(a.coef[(int64_t)term * kLrP * kLrP + row * kLrP + b], a.U[(int64_t)(c0 + b) * a.n + j], mj);
+      v = cfma(a.U[(int64_t)k * a.n + i], mj, v);
+    }
+    G[i * ldg + j] = make_double2(v.re, v.im);
+  }
+}
+
+static LrArgs lr_args(const gf_lowrank& lr, char* ws) {
+  const LrLayout L = lr_layout(lr.geom, lr.max_cols);
+  LrArgs a;
+  a.nx = lr.geom.nx;
+  a.ny = lr.geom.ny;
+  a.N = (int64_t)a.nx * a.ny;
+  a.n = a.N + 1;
+  a.chi = lr.geom.eps_mat - lr.geom.eps_bg;
+  a.max_cols = lr.max_cols;
+  a.E = reinterpret_cast<cplx*>(lr.E);
+  a.bands = reinterpret_cast<cplx*>(lr.bands);
+  a.mon = reinterpret_cast<cplx*>(lr.monrow);
+  a.U = reinterpret_cast<cplx*>(lr.U);
+  a.table = reinterpret_cast<const cplx*>(ws + L.table);
+  a.coef = reinterpret_cast<cplx*>(ws + L.coef);
+  a.tcol = reinterpret_cast<int32_t*>(ws + L.tcol);
+  a.tp = reinterpret_cast<int32_t*>(ws + L.tp);
+  a.colterm = reinterpret_cast<int32_t*>(ws + L.colterm);
+  a.count = reinterpret_cast<LrCount*>(ws + L.count);
+  a.step = reinterpret_cast<LrStep*>(ws + L.step);
+  a.w = reinterpret_cast<cplx*>(ws + L.w);
+  return a;
+}
+
+static int grid_of(int64_t work, int threads, int cap) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace gf
+
+// ----------------------------------------------------------------------------- C ABI
+static gf_status lr_check(gf_handle* h, const gf_lowrank* lr, void* ws, size_t ws_bytes) {
+  if (!lr) return gf::api_fail_msg(h, GF_EINVAL, "low-rank problem is NULL");
+  gf_problem probe;
+  probe.geom = lr->geom;
+  probe.G = lr->monrow;          // shape checks only: the monitor row stands in for G
+  const int64_t n = (int64_t)lr->geom.nx * lr->geom.ny + 1;
+  probe.ldg = n + (n & 1);
+  probe.E = lr->E;
+  probe.bands = lr->bands;
+  gf_status s = gf::api_check_problem(h, &probe, GF_C128);
+  if (s) return s;
+  if (!lr->U || ((uintptr_t)lr->U & 15u)) return gf::api_fail_msg(h, GF_EINVAL, "U must be non-NULL and 16-byte aligned");
+  if (lr->max_cols < 4 || lr->max_cols > (1 << 24)) return gf::api_fail_msg(h, GF_EINVAL, "max_cols must lie in [4, 2^24]");
+  if (!ws || ((uintptr_t)ws & 255u)) return gf::api_fail_msg(h, GF_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < gf::lr_layout(lr->geom, lr->max_cols).total) return gf::api_fail_msg(h, GF_ENOMEM, "workspace too small");
+  return gf::api_bind_device(h);
+}
+
+extern "C" {
+
+size_t gf_lowrank_workspace_size(const gf_geom* geom, int32_t max_cols) {
+  if (!geom || geom->nx < 1 || geom->ny < 1 || max_cols < 4 || max_cols > (1 << 24)) return 0;
+  return gf::lr_layout(*geom, max_cols).total;
+}
+
+gf_status gf_lowrank_init(gf_handle* h, const gf_lowrank* lr, void* ws, size_t ws_bytes, void* stream) {
+  if (!h) return GF_EINVAL;
+  gf_status s = lr_check(h, lr, ws, ws_bytes);
+  if (s) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  gf::LrArgs a = gf::lr_args(*lr, reinterpret_cast<char*>(ws));
+  gf::launch_fill_table(lr->geom, const_cast<gf::cplx*>(a.table), st);
+  gf::launch_fill_field(lr->geom, a.E, st);
+  gf::k_lr_init<<<gf::grid_of(GF_NBANDS * a.N, 256, 4864), 256, 0, st>>>(a);
+  return gf::api_cuda_check(h, "gf_lowrank_init launch");
+}
+
+gf_status gf_lowrank_eval(gf_handle* h, const gf_lowrank* lr, const uint8_t* state, const gf_cand_spec* spec,
+                          double* dfom, void* stream) {
+  if (!h) return GF_EINVAL;
+  if (!lr) return gf::api_fail_msg(h, GF_EINVAL, "low-rank problem is NULL");
+  if (!state || !dfom || !spec) return gf::api_fail_msg(h, GF_EINVAL, "state, spec and dfom must be non-NULL");
+  gf_status s = gf::api_check_spec(h, &lr->geom, spec);
+  if (s) return s;
+  if ((s = gf::api_bind_device(h))) return s;
+  // the candidate kernels read bands, E and the monitor row G[N, j]: a one-row "G" with
+  // leading dimension 0 makes G[N * 0 + j] the monitor row
+  gf::EvalArgs a;
+  a.nlam = 1;
+  a.dtype = GF_C128;
+  a.nx = lr->geom.nx;
+  a.ny = lr->geom.ny;
+  a.chi = lr->geom.eps_mat - lr->geom.eps_bg;
+  a.lam[0].G = lr->monrow;
+  a.lam[0].ldg = 0;
+  a.lam[0].E = reinterpret_cast<const gf::cplx*>(lr->E);
+  a.lam[0].bands = reinterpret_cast<const gf::cplx*>(lr->bands);
+  gf::launch_eval(a, state, *spec, dfom, (cudaStream_t)stream);
+  return gf::api_cuda_check(h, "gf_lowrank_eval launch");
+}
+
+gf_status gf_lowrank_update(gf_handle* h, const gf_lowrank* lr, uint8_t* state, const gf_cand_spec* spec,
+                            const int32_t* idx, int32_t* status, double* fom_out, int32_t* applied, void* ws,
+                            size_t ws_bytes, void* stream) {
+  if (!h) return GF_EINVAL;
+  gf_status s = lr_check(h, lr, ws, ws_bytes);
+  if (s) return s;
+  if (!spec) return gf::api_fail_msg(h, GF_EINVAL, "candidate spec is NULL");
+  if ((s = gf::api_check_spec(h, &lr->geom, spec))) return s;
+  if (spec->k != 1) return gf::api_fail_msg(h, GF_EINVAL, "the deferred form applies one candidate per step (k = 1)");
+  if (!state || !idx || !status || !fom_out) return gf::api_fail_msg(h, GF_EINVAL, "state, idx, status and fom_out must be non-NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  gf::LrArgs a = gf::lr_args(*lr, reinterpret_cast<char*>(ws));
+  gf::k_lr_pixels<<<1, 32, 0, st>>>(a, spec->kind, spec->dir_mask, state, idx, status);
+  gf::k_lr_w<<<gf::grid_of(lr->max_cols, 256, 1216), 256, 0, st>>>(a);
+  // timed like the dense G update when profiling is armed: the record's rank is K p (columns
+  // read x columns written), so the recorded flops 8 (K p) n are the product's
+  gf::KernelTimer* tm = gf::api_timer(h);
+  const bool rec = tm->on && tm->used < tm->max;
+  if (rec) {
+    tm->p_host[tm->used] = 0;
+    cudaEventRecord(tm->ev0[tm->used], st);
+  }
+  gf::k_lr_columns<<<gf::grid_of(a.n, gf::kLrThreads, 4864), gf::kLrThreads, 0, st>>>(a, rec ? tm->p_dev + tm->used : nullptr);
+  if (rec) {
+    cudaEventRecord(tm->ev1[tm->used], st);
+    tm->n2[tm->used] = (double)a.n;
+    tm->bytes_per_entry[tm->used] = 0;
+    tm->used++;
+  }
+  gf::k_lr_capacitance<<<1, 32, 0, st>>>(a, status);
+  gf::k_lr_apply<<<gf::grid_of(a.n, 256, 4864), 256, 0, st>>>(a, state, fom_out, applied);
+  return gf::api_cuda_check(h, "gf_lowrank_update launch");
+}
+
+gf_status gf_lowrank_count(gf_handle* h, const gf_lowrank* lr, void* ws, size_t ws_bytes, int32_t* nterms,
+                           int32_t* ncols, void* stream) {
+  if (!h) return GF_EINVAL;
+  gf_status s = lr_check(h, lr, ws, ws_bytes);
+  if (s) return s;
+  gf::LrArgs a = gf::lr_args(*lr, reinterpret_cast<char*>(ws));
+  gf::LrCount c{0, 0};
+  cudaMemcpyAsync(&c, a.count, sizeof c, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  cudaStreamSynchronize((cudaStream_t)stream);
+  if (nterms) *nterms = c.nterms;
+  if (ncols) *ncols = c.ncols;
+  return gf::api_cuda_check(h, "gf_lowrank_count");
+}
+
+gf_status gf_lowrank_materialize(gf_handle* h, const gf_lowrank* lr, void* G, int64_t ldg, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  if (!h) return GF_EINVAL;
+  gf_status s = lr_check(h, lr, ws, ws_bytes);
+  if (s) return s;
+  const int64_t n = (int64_t)lr->geom.nx * lr->geom.ny + 1;
+  if (!G || ((uintptr_t)G & 15u) || ldg < n) return gf::api_fail_msg(h, GF_EINVAL, "G must be 16-byte aligned with ldg >= n");
+  gf::LrArgs a = gf::lr_args(*lr, reinterpret_cast<char*>(ws));
+  gf::k_lr_materialize<<<gf::grid_of(n * n, 256, 4864), 256, 0, (cudaStream_t)stream>>>(a, reinterpret_cast<double2*>(G), ldg);
+  return gf::api_cuda_check(h, "gf_lowrank_materialize launch");
+}
+
+}  // extern "C"

@@ -20,37 +20,6 @@ struct CapArgs {
   int pmax;
 };
 
-// Pixels and contrast changes of candidate c given the current state (same rule as the
-// candidate kernels).  Appends to V/dchi; returns the number appended.
-__device__ int cand_pixels(int64_t c, int kind, int dir_mask, int nx, int ny, double chi,
-                           const uint8_t* state, int32_t* V, double* dchi) {
-  const int64_t N = (int64_t)nx * ny;
-  if (kind == GF_KIND_SINGLE) {
-    if (c < 0 || c >= N) return 0;
-    uint8_t s = state[c];
-    if (s == 0 && (dir_mask & GF_DIR_FILL)) { V[0] = (int32_t)c; dchi[0] = chi; return 1; }
-    if (s != 0 && (dir_mask & GF_DIR_CLEAR)) { V[0] = (int32_t)c; dchi[0] = -chi; return 1; }
-    return 0;
-  }
-  const int64_t P = (int64_t)(nx - 1) * (ny - 1);
-  if (c < 0 || c >= 2 * P) return 0;
-  const int dir = (int)(c / P);
-  const int64_t a = c - dir * P;
-  if (!(dir_mask & (dir == 0 ? GF_DIR_FILL : GF_DIR_CLEAR))) return 0;
-  const int ay = (int)(a / (nx - 1)), ax = (int)(a - (int64_t)ay * (nx - 1));
-  const int64_t j0 = (int64_t)ay * nx + ax;
-  const int64_t q[4] = {j0, j0 + 1, j0 + nx, j0 + nx + 1};
-  int m = 0;
-  for (int u = 0; u < 4; ++u) {
-    if (state[q[u]] == (dir == 0 ? 0 : 1)) {
-      V[m] = (int32_t)q[u];
-      dchi[m] = dir == 0 ? chi : -chi;
-      ++m;
-    }
-  }
-  return m;
-}
-
 // Single CTA.  The p x p matrices live in the workspace (p can reach 4k).
 __device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayout& L, char* ws,
                                                  const uint8_t* __restrict__ state,

@@ -32,7 +32,9 @@ EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_v
            "gf_eval_candidates", "gf_select_topk", "gf_apply_update", "gf_profile_begin",
            "gf_profile_end", "gf_set_update_algo", "gf_refresh", "gf_refresh_workspace_size",
            "gf_fill_g0_static", "gf_batch_table_size", "gf_batch_create", "gf_batch_step",
-           "gf_batch_set_schedule", "gf_batch_destroy", "gf_select_egreedy"]
+           "gf_batch_set_schedule", "gf_batch_destroy", "gf_select_egreedy", "gf_lowrank_workspace_size",
+           "gf_lowrank_init", "gf_lowrank_eval", "gf_lowrank_update", "gf_lowrank_count",
+           "gf_lowrank_materialize"]
 
 
 class GfError(RuntimeError):
@@ -55,6 +57,11 @@ class gf_problem(C.Structure):
 class gf_cand_spec(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dir_mask", C.c_int32), ("k", C.c_int32),
                 ("excl_radius", C.c_int32), ("tie_rel", C.c_double)]
+
+
+class gf_lowrank(C.Structure):
+    _fields_ = [("geom", gf_geom), ("E", C.c_void_p), ("bands", C.c_void_p), ("monrow", C.c_void_p),
+                ("U", C.c_void_p), ("max_cols", C.c_int32)]
 
 
 class gf_batch_item(C.Structure):
@@ -106,6 +113,14 @@ def load(path: str = LIB_PATH):
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "gf_select_egreedy": (C.c_int32, [P, C.POINTER(gf_geom), C.POINTER(gf_cand_spec), P, C.c_int64,
                                               C.c_double, P, P, P, P, P, C.c_size_t, P]),
+            "gf_lowrank_workspace_size": (C.c_size_t, [C.POINTER(gf_geom), C.c_int32]),
+            "gf_lowrank_init": (C.c_int32, [P, C.POINTER(gf_lowrank), P, C.c_size_t, P]),
+            "gf_lowrank_eval": (C.c_int32, [P, C.POINTER(gf_lowrank), P, C.POINTER(gf_cand_spec), P, P]),
+            "gf_lowrank_update": (C.c_int32, [P, C.POINTER(gf_lowrank), P, C.POINTER(gf_cand_spec), P, P, P, P, P,
+                                              C.c_size_t, P]),
+            "gf_lowrank_count": (C.c_int32, [P, C.POINTER(gf_lowrank), P, C.c_size_t, C.POINTER(C.c_int32),
+                                             C.POINTER(C.c_int32), P]),
+            "gf_lowrank_materialize": (C.c_int32, [P, C.POINTER(gf_lowrank), P, C.c_int64, P, C.c_size_t, P]),
             "gf_batch_table_size": (C.c_size_t, [C.c_int32]),
             "gf_batch_create": (C.c_int32, [P, C.c_int32, C.POINTER(gf_batch_item), C.c_int32,
                                             C.POINTER(gf_cand_spec), P, C.c_size_t, P, C.POINTER(P)]),
@@ -240,6 +255,36 @@ class Handle:
                                         int(max_iter), float(tol), res, its, _ptr(ws), int(ws_bytes),
                                         _stream(stream)))
         return list(res), list(its)[:ns]
+
+    # ---- deferred (low-rank) form
+    def gf_lowrank_workspace_size(self, geom, max_cols: int) -> int:
+        g = geom_struct(geom)
+        return int(self.lib.gf_lowrank_workspace_size(C.byref(g), int(max_cols)))
+
+    def gf_lowrank_init(self, lr: gf_lowrank, ws, ws_bytes, stream=None):
+        self._check(self.lib.gf_lowrank_init(self.h, C.byref(lr), _ptr(ws), int(ws_bytes), _stream(stream)))
+
+    def gf_lowrank_eval(self, lr: gf_lowrank, state, spec, dfom, stream=None):
+        s = spec_struct(spec)
+        self._check(self.lib.gf_lowrank_eval(self.h, C.byref(lr), _ptr(state), C.byref(s), _ptr(dfom),
+                                             _stream(stream)))
+
+    def gf_lowrank_update(self, lr: gf_lowrank, state, spec, idx, status, fom_out, ws, ws_bytes, stream=None,
+                          applied=None):
+        s = spec_struct(spec)
+        self._check(self.lib.gf_lowrank_update(self.h, C.byref(lr), _ptr(state), C.byref(s), _ptr(idx),
+                                               _ptr(status), _ptr(fom_out), _ptr(applied), _ptr(ws), int(ws_bytes),
+                                               _stream(stream)))
+
+    def gf_lowrank_count(self, lr: gf_lowrank, ws, ws_bytes, stream=None):
+        nt, nc = C.c_int32(), C.c_int32()
+        self._check(self.lib.gf_lowrank_count(self.h, C.byref(lr), _ptr(ws), int(ws_bytes), C.byref(nt), C.byref(nc),
+                                              _stream(stream)))
+        return nt.value, nc.value
+
+    def gf_lowrank_materialize(self, lr: gf_lowrank, G, ldg, ws, ws_bytes, stream=None):
+        self._check(self.lib.gf_lowrank_materialize(self.h, C.byref(lr), _ptr(G), int(ldg), _ptr(ws), int(ws_bytes),
+                                                    _stream(stream)))
 
     # ---- batches
     def gf_batch_table_size(self, nitems: int) -> int:
