@@ -654,10 +654,13 @@ def run_full(args, deferred: bool):
 
     opt, start = make()
     start()
-    for _ in range(max(3, args.warmup)):
-        opt.step()
-    torch.cuda.synchronize()
     accepted = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for _ in range(max(3, args.warmup)):          # the exact loop body, so every kernel is loaded
+        opt.step()
+        accepted += opt.applied.to(torch.int64)
+    int(opt.status.cpu()[0])
+    accepted.zero_()
+    torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
     time.sleep(0.3)
@@ -665,11 +668,15 @@ def run_full(args, deferred: bool):
     e0.record()
     start()
     steps = 0
+    marks = []
     while steps < max_steps:
         for _ in range(32):
             opt.step()
             accepted += opt.applied.to(torch.int64)
         steps += 32
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record()
+        marks.append(ev)
         if int(opt.status.cpu()[0]) != B.GF_OK:
             break
     e1.record()
@@ -680,7 +687,9 @@ def run_full(args, deferred: bool):
     fom = float(opt.fom.cpu()[0])
     peak_hbm, peak_kind = measured_peaks()
     n = g.N + 1
+    chunk_ms = [e0.elapsed_time(marks[0])] + [marks[i - 1].elapsed_time(marks[i]) for i in range(1, len(marks))]
     cfg = {"workload": ("deferred" if deferred else "dense") + "_brush_192x192_p4_to_termination", "n": n,
+           "ms_per_32_steps": [round(x, 2) for x in chunk_ms],
            "flips_to_termination": flips, "final_fom": fom,
            "steps_enqueued": steps, "status_readback_every": 32,
            "memory_GB": (opt.U.numel() * 16 if deferred else opt.G[0].numel() * 16) / 1e9,
