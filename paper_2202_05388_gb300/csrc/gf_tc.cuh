@@ -169,6 +169,32 @@ __device__ __forceinline__ void tma_store_2d(const void* tmap, int x, int y, con
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
                :: "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(src_smem)) : "memory");
 }
+// L2 cache policies for the copies below: data streamed once (evict first) and small operand
+// blocks that many CTAs re-read during the kernel (evict last).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bulk_g2s_hint(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* mbar,
+                                              uint64_t policy) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+               :: "r"(smem_u32(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_u32(mbar)), "l"(policy) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d_hint(void* dst_smem, const void* tmap, int x, int y, uint64_t* mbar,
+                                                 uint64_t policy) {
+  asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;"
+               :: "r"(smem_u32(dst_smem)), "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(mbar)), "l"(policy) : "memory");
+}
+__device__ __forceinline__ void tma_store_2d_hint(const void* tmap, int x, int y, const void* src_smem, uint64_t policy) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;"
+               :: "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(src_smem)), "l"(policy) : "memory");
+}
 __device__ __forceinline__ void tma_prefetch_desc(const void* tmap) {
   asm volatile("prefetch.tensormap [%0];" :: "l"(tmap) : "memory");
 }

@@ -325,6 +325,7 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
     __syncwarp();
   } else if (warp == kWarpOProd) {
     if (lane == 0) {
+      const uint64_t pol_ops = tc::policy_evict_last();    // operand blocks: re-read by many tiles
       int64_t c = 0;
       for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
         int64_t rt, ct;
@@ -335,8 +336,9 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
           if (c >= kC64NSO && !tc::mbar_wait_or_abort(&bars->oempty[s], (uint32_t)((c / kC64NSO - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
           uint8_t* st = ops + s * kC64OpStage;
           tc::mbar_arrive_expect_tx(&bars->ofull[s], (uint32_t)kC64OpStage);
-          tc::bulk_g2s(st, Aops + (rt * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->ofull[s]);
-          tc::bulk_g2s(st + kC64Block, Bops + (ct * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->ofull[s]);
+          tc::bulk_g2s_hint(st, Aops + (rt * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->ofull[s], pol_ops);
+          tc::bulk_g2s_hint(st + kC64Block, Bops + (ct * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->ofull[s],
+                            pol_ops);
         }
         if (!ok) break;
       }

@@ -356,6 +356,9 @@ __device__ __forceinline__ bool ozaki_body(const Src& src, uint8_t* smem) {
 
   if (warp == kWarpProd) {
     // ------------------------------------------------------------------ producer
+    // the digit blocks are re-read by every row tile: evict last, so that the G stream does
+    // not push them out of L2
+    const uint64_t pol_ops = tc::policy_evict_last();
     int64_t cur = -1;
     int64_t aseq = -1;
     int64_t k = 0;
@@ -373,7 +376,8 @@ __device__ __forceinline__ bool ozaki_body(const Src& src, uint8_t* smem) {
           if (aseq >= 2) ok = tc::mbar_wait_or_abort(&bars->aempty[ab], (uint32_t)((aseq / 2 - 1) & 1), abort, kOzTimeoutNs);
           if (ok) {
             tc::mbar_arrive_expect_tx(&bars->afull[ab], kOzTileA);
-            tc::bulk_g2s(Abuf + ab * kOzTileA, pr.ozA + rt * (int64_t)kOzTileA, kOzTileA, &bars->afull[ab]);
+            tc::bulk_g2s_hint(Abuf + ab * kOzTileA, pr.ozA + rt * (int64_t)kOzTileA, kOzTileA, &bars->afull[ab],
+                              pol_ops);
           }
         }
         cur = oz_key(b, rt);
@@ -392,7 +396,7 @@ __device__ __forceinline__ bool ozaki_body(const Src& src, uint8_t* smem) {
         tc::mbar_arrive_expect_tx(&bars->full[s], (uint32_t)((second ? kOzGTile : kOzBox) + kOzBBlock));
         tc::tma_load_2d(stage, map, x, y, &bars->full[s]);
         if (second) tc::tma_load_2d(stage + kOzBox, map, x + 16, y, &bars->full[s]);
-        tc::bulk_g2s(stage + kOzGTile, pr.ozB + ct * (int64_t)kOzBBlock, kOzBBlock, &bars->full[s]);
+        tc::bulk_g2s_hint(stage + kOzGTile, pr.ozB + ct * (int64_t)kOzBBlock, kOzBBlock, &bars->full[s], pol_ops);
       }
       __syncwarp();
     }

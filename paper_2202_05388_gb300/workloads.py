@@ -138,6 +138,15 @@ def brush_320_c64_rank4() -> Workload:
                     w.steps, "c64")
 
 
+def brush_96_c64_rank4() -> Workload:
+    """96x96 member of the complex64 rank-4 family (G = 680 MB, larger than L2), for profiling."""
+    nx = ny = 96
+    dx = 0.05
+    mx, my = _centre_line_monitor(nx, ny, dx, beyond_edge=5.0)
+    g = Geometry(nx, ny, dx, 1.0, mx, my)
+    return Workload("brush_96x96_p4_c64", (g,), CandidateSpec(KIND_BRUSH2, DIR_FILL | DIR_CLEAR, 1), 200, "c64")
+
+
 def brush_128_topk() -> Workload:
     """128x128 member of the top-32 complex64 family (G = 2.1 GB), for profiling."""
     nx = ny = 128
