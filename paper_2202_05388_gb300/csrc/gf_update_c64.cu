@@ -262,15 +262,26 @@ __device__ __forceinline__ void c64_tile_coords(int64_t t, int64_t nrt, int64_t 
   ct = rem / rows_in_group;
 }
 
+// Operand sharing in a thread-block cluster of CR x CC CTAs (1x1, 2x1 or 2x2): the cluster
+// works on a CR x CC block of tiles at a time.  CTAs in the same tile row need the same A
+// blocks and CTAs in the same tile column the same B blocks, so each loads one half (hi or
+// lo) of its row's A block and one half of its column's B block and multicasts each half to
+// the partner that shares it: per CTA and K chunk, operand traffic falls from two blocks (A and
+// B) to 1.5 for a 2x1 cluster and to one for a 2x2 cluster.  A stage is free only
+// when every CTA that writes into it is done with its own copy: the MMA warp commits to the
+// "empty" barrier of itself and of its A and B partners, and that barrier counts one arrival
+// per CTA in the mask.  At ragged edges the CTAs without a real tile work on a phantom tile
+// (operands of tile 0, no G load, update or store) so that the cluster stays in step.
+template <int CR, int CC>
 __global__ void __launch_bounds__(kC64Threads, 1)
-k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_t nrt, int64_t nct, int nkc,
-                     const uint8_t* __restrict__ Aops, const uint8_t* __restrict__ Bops,
-                     const int32_t* __restrict__ Erow, const int32_t* __restrict__ Fcol,
-                     const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
+k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_t nrt, int64_t nct, int nkc,
+                       const uint8_t* __restrict__ Aops, const uint8_t* __restrict__ Bops,
+                       const int32_t* __restrict__ Erow, const int32_t* __restrict__ Fcol,
+                       const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int p = ctl->skip ? 0 : ctl->nv;
   if (prof_p && blockIdx.x == 0 && threadIdx.x == 0 && p > 0) *prof_p = p;
-  if (p <= 0) return;
+  if (p <= 0) return;                            // uniform over the grid (both CTAs of a cluster)
   C64Bars* bars = reinterpret_cast<C64Bars*>(smem + kC64BarOff);
   uint8_t* ops = smem;                                        // kC64NSO x (A block, B block)
   uint8_t* gts = smem + kC64NSO * kC64OpStage;                // kC64NSG x G tile
@@ -278,6 +289,16 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
   volatile int* abort = &bars->abort;
   constexpr int kWarpGProd = kC64EpiWarps, kWarpMma = kC64EpiWarps + 1, kWarpStore = kC64EpiWarps + 2,
                 kWarpOProd = kC64EpiWarps + 3;
+  constexpr int CS = CR * CC;
+  const int crank = CS > 1 ? (int)tc::cluster_ctarank() : 0;
+  const int rr = crank / CC, cc = crank % CC;     // position in the cluster's tile block
+  const int64_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
+  const int64_t nrt_c = (nrt + CR - 1) / CR, nct_c = (nct + CC - 1) / CC;
+  const uint16_t me = (uint16_t)(1u << crank);
+  const uint16_t mask_a = CC == 2 ? (uint16_t)(me | (1u << (crank ^ 1))) : me;    // CTAs sharing my A
+  const uint16_t mask_b = CR == 2 ? (uint16_t)(me | (1u << (crank ^ CC))) : me;   // CTAs sharing my B
+  const uint16_t mask_e = (uint16_t)(mask_a | mask_b);
+  const int nempty = __popc(mask_e);
 
   if (warp == kWarpMma) {
     tc::tmem_alloc(&bars->tslot, kC64TmemCols);
@@ -286,7 +307,7 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
   if (tid == 0) {
     for (int q = 0; q < kC64NSO; ++q) {
       tc::mbar_init(&bars->ofull[q], 1);
-      tc::mbar_init(&bars->oempty[q], 1);
+      tc::mbar_init(&bars->oempty[q], (uint32_t)nempty);
     }
     for (int q = 0; q < kC64NSG; ++q) {
       tc::mbar_init(&bars->gfull[q], 1);
@@ -302,18 +323,24 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (CS > 1) tc::cluster_sync();                // the partners' barriers exist before any multicast
   tc::fence_after_sync();
   const uint32_t tbase = bars->tslot;
-  const int64_t T = nrt * nct;
+  const int64_t T = nrt_c * nct_c;
 
   if (warp == kWarpGProd) {
     if (lane == 0) {
       int64_t k = 0;
-      for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++k) {
-        int64_t rt, ct;
-        c64_tile_coords(t, nrt, nct, rt, ct);
+      for (int64_t t = cid; t < T; t += ncl, ++k) {
+        int64_t rg, cg;
+        c64_tile_coords(t, nrt_c, nct_c, rg, cg);
+        const int64_t rt = rg * CR + rr, ct = cg * CC + cc;
         const int s = (int)(k % kC64NSG);
         if (k >= kC64NSG && !tc::mbar_wait_or_abort(&bars->gempty[s], (uint32_t)((k / kC64NSG - 1) & 1), abort, kC64TimeoutNs)) break;
+        if (rt >= nrt || ct >= nct) {            // phantom tile: nothing to load
+          tc::mbar_arrive(&bars->gfull[s]);
+          continue;
+        }
         const int x0 = (int)(ct * kC64N), y = (int)(rt * kC64M);     // x in floats
         int nbox = 0;
         for (int b = 0; b < 4; ++b) nbox += (x0 + 32 * b < 2 * n) ? 1 : 0;
@@ -327,20 +354,39 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
     if (lane == 0) {
       const uint64_t pol_ops = tc::policy_evict_last();    // operand blocks: re-read by many tiles
       int64_t c = 0;
-      for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
-        int64_t rt, ct;
-        c64_tile_coords(t, nrt, nct, rt, ct);
+      for (int64_t t = cid; t < T; t += ncl) {
+        int64_t rg, cg;
+        c64_tile_coords(t, nrt_c, nct_c, rg, cg);
+        int64_t rt = rg * CR + rr, ct = cg * CC + cc;
+        if (rt >= nrt) rt = 0;                   // phantom tile: any valid operands
+        if (ct >= nct) ct = 0;
         bool ok = true;
         for (int kc = 0; kc < nkc; ++kc, ++c) {
           const int s = (int)(c % kC64NSO);
           if (c >= kC64NSO && !tc::mbar_wait_or_abort(&bars->oempty[s], (uint32_t)((c / kC64NSO - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
           uint8_t* st = ops + s * kC64OpStage;
           tc::mbar_arrive_expect_tx(&bars->ofull[s], (uint32_t)kC64OpStage);
-          tc::bulk_g2s_hint(st, Aops + (rt * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->ofull[s], pol_ops);
-          tc::bulk_g2s_hint(st + kC64Block, Bops + (ct * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->ofull[s],
-                            pol_ops);
+          const uint8_t* asrc = Aops + (rt * nkc + kc) * (int64_t)kC64Block;
+          const uint8_t* bsrc = Bops + (ct * nkc + kc) * (int64_t)kC64Block;
+          if (CC == 2)      // my half of the A block, to me and my row partner
+            tc::bulk_g2s_mc_hint(st + cc * kC64Half, asrc + cc * kC64Half, kC64Half, &bars->ofull[s], mask_a, pol_ops);
+          else
+            tc::bulk_g2s_hint(st, asrc, kC64Block, &bars->ofull[s], pol_ops);
+          if (CR == 2)      // my half of the B block, to me and my column partner
+            tc::bulk_g2s_mc_hint(st + kC64Block + rr * kC64Half, bsrc + rr * kC64Half, kC64Half, &bars->ofull[s],
+                                 mask_b, pol_ops);
+          else
+            tc::bulk_g2s_hint(st + kC64Block, bsrc, kC64Block, &bars->ofull[s], pol_ops);
         }
         if (!ok) break;
+      }
+      if (CS > 1) {
+        // drain: copies into this CTA (own and the peer's halves) of the last stages may still
+        // be in flight if the loop was abandoned; wait (bounded) until they landed
+        for (int64_t q = c - kC64NSO; q < c; ++q) {
+          if (q < 0) continue;
+          tc::mbar_wait_bounded(&bars->ofull[q % kC64NSO], (uint32_t)((q / kC64NSO) & 1), 100000000ull);
+        }
       }
     }
     __syncwarp();
@@ -349,7 +395,7 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
       const uint32_t idesc = tc::idesc_f16(kC64M, kC64N);
       int64_t k = 0, c = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < T && ok; t += gridDim.x, ++k) {
+      for (int64_t t = cid; t < T && ok; t += ncl, ++k) {
         const int b = (int)(k & 1);
         if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[b], (uint32_t)((k / 2 - 1) & 1), abort, kC64TimeoutNs)) break;
         tc::fence_after_sync();
@@ -370,9 +416,18 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
             tc::mma_f16(d2, ah, bl, idesc, first);
             tc::mma_f16(d2, al, bh, idesc, 1u);
           }
-          tc::mma_commit(&bars->oempty[s]);
+          if (CS > 1) tc::mma_commit_mc(&bars->oempty[s], mask_e);
+          else tc::mma_commit(&bars->oempty[s]);
         }
         if (ok) tc::mma_commit(&bars->tfull[b]);
+      }
+      if (CS > 1) {
+        // this CTA's last commits (to both CTAs' empty barriers) fire when its MMAs complete:
+        // wait (bounded) for them locally before the cluster may retire
+        for (int64_t q = c - kC64NSO; q < c; ++q) {
+          if (q < 0) continue;
+          tc::mbar_wait_bounded(&bars->oempty[q % kC64NSO], (uint32_t)((q / kC64NSO) & 1), 100000000ull);
+        }
       }
     }
     __syncwarp();
@@ -381,12 +436,14 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
     const int r = q * 32 + lane;
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
     int64_t k = 0;
-    for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++k) {
-      int64_t rt, ct;
-      c64_tile_coords(t, nrt, nct, rt, ct);
+    for (int64_t t = cid; t < T; t += ncl, ++k) {
+      int64_t rg, cg;
+      c64_tile_coords(t, nrt_c, nct_c, rg, cg);
+      const int64_t rt = rg * CR + rr, ct = cg * CC + cc;
+      const bool real = rt < nrt && ct < nct;
       const int b = (int)(k & 1);
       const int s = (int)(k % kC64NSG);
-      const int Ei = Erow[rt * kC64M + r];
+      const int Ei = real ? Erow[rt * kC64M + r] : 0;
       if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kC64TimeoutNs)) break;
       if (!tc::mbar_wait_or_abort(&bars->gfull[s], (uint32_t)((k / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
       tc::fence_after_sync();
@@ -410,21 +467,23 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
-      // box h holds real columns 32h .. 32h+31 of the tile = 8 chunks of 16 B (128B swizzle);
-      // chunk ch holds complex columns 2ch, 2ch+1 of this quarter
-      const int32_t* Fq = Fcol + ct * (kC64N / 2) + h * 16;
-      uint8_t* row = gts + s * kC64GTile + h * kC64Box + r * 128;
+      if (real) {
+        // box h holds real columns 32h .. 32h+31 of the tile = 8 chunks of 16 B (128B swizzle);
+        // chunk ch holds complex columns 2ch, 2ch+1 of this quarter
+        const int32_t* Fq = Fcol + ct * (kC64N / 2) + h * 16;
+        uint8_t* row = gts + s * kC64GTile + h * kC64Box + r * 128;
 #pragma unroll
-      for (int ch = 0; ch < 8; ++ch) {
-        const float s0 = __int_as_float((Ei + Fq[2 * ch] + 127) << 23);
-        const float s1 = __int_as_float((Ei + Fq[2 * ch + 1] + 127) << 23);
-        float4* gp = reinterpret_cast<float4*>(row + ((ch ^ (r & 7)) << 4));
-        float4 g = *gp;
-        g.x += s0 * fmaf(acc2[4 * ch + 0], 0.00048828125f, acc1[4 * ch + 0]);
-        g.y += s0 * fmaf(acc2[4 * ch + 1], 0.00048828125f, acc1[4 * ch + 1]);
-        g.z += s1 * fmaf(acc2[4 * ch + 2], 0.00048828125f, acc1[4 * ch + 2]);
-        g.w += s1 * fmaf(acc2[4 * ch + 3], 0.00048828125f, acc1[4 * ch + 3]);
-        *gp = g;
+        for (int ch = 0; ch < 8; ++ch) {
+          const float s0 = __int_as_float((Ei + Fq[2 * ch] + 127) << 23);
+          const float s1 = __int_as_float((Ei + Fq[2 * ch + 1] + 127) << 23);
+          float4* gp = reinterpret_cast<float4*>(row + ((ch ^ (r & 7)) << 4));
+          float4 g = *gp;
+          g.x += s0 * fmaf(acc2[4 * ch + 0], 0.00048828125f, acc1[4 * ch + 0]);
+          g.y += s0 * fmaf(acc2[4 * ch + 1], 0.00048828125f, acc1[4 * ch + 1]);
+          g.z += s1 * fmaf(acc2[4 * ch + 2], 0.00048828125f, acc1[4 * ch + 2]);
+          g.w += s1 * fmaf(acc2[4 * ch + 3], 0.00048828125f, acc1[4 * ch + 3]);
+          *gp = g;
+        }
       }
       tc::fence_proxy_async_smem();
       tc::mbar_arrive(&bars->ebar[s]);
@@ -433,15 +492,18 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
   if (warp == kWarpStore) {
     if (lane == 0) {
       int64_t k = 0;
-      for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++k) {
-        int64_t rt, ct;
-        c64_tile_coords(t, nrt, nct, rt, ct);
+      for (int64_t t = cid; t < T; t += ncl, ++k) {
+        int64_t rg, cg;
+        c64_tile_coords(t, nrt_c, nct_c, rg, cg);
+        const int64_t rt = rg * CR + rr, ct = cg * CC + cc;
         const int s = (int)(k % kC64NSG);
         if (!tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)((k / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
-        const int x0 = (int)(ct * kC64N), y = (int)(rt * kC64M);
-        uint8_t* gt = gts + s * kC64GTile;
-        for (int b = 0; b < 4; ++b)
-          if (x0 + 32 * b < 2 * n) tc::tma_store_2d(&tmapG, x0 + 32 * b, y, gt + b * kC64Box);
+        if (rt < nrt && ct < nct) {
+          const int x0 = (int)(ct * kC64N), y = (int)(rt * kC64M);
+          uint8_t* gt = gts + s * kC64GTile;
+          for (int b = 0; b < 4; ++b)
+            if (x0 + 32 * b < 2 * n) tc::tma_store_2d(&tmapG, x0 + 32 * b, y, gt + b * kC64Box);
+        }
         tc::bulk_commit();
         tc::bulk_wait_read0();
         tc::mbar_arrive(&bars->gempty[s]);
@@ -452,6 +514,7 @@ k_rank_update_c64_tc(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
   }
   tc::fence_before_sync();
   __syncthreads();
+  if (CS > 1) tc::cluster_sync();                // no CTA retires while a partner may still signal it
   if (tid == 0 && bars->abort) atomicExch(status, GF_ETIMEOUT);
   tc::fence_after_sync();
   if (warp == kWarpMma) tc::tmem_dealloc(tbase, kC64TmemCols);
@@ -508,21 +571,84 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
     k_c64_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, L.pmax, n, rows, ctl, o.P, (int)o.nkc, Aops,
                                                                  Erow);
   }
-  {
-    static std::mutex mu;
-    static bool done[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> lk(mu);
-    if (dev < 0 || dev >= 64 || !done[dev]) {
-      cudaFuncSetAttribute(k_rank_update_c64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
-      if (dev >= 0 && dev < 64) done[dev] = true;
+  // once per device: shared-memory opt-in of every form and the number of 4- and 2-CTA clusters
+  // that can be resident at once (0: that form is unavailable)
+  static std::mutex mu;
+  static bool done[64] = {};
+  static int clusters4[64] = {}, clusters2[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto max_active = [&](auto kernel, int size) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(size * sm_count));
+    cfg.blockDim = dim3(kC64Threads);
+    cfg.dynamicSmemBytes = kC64Smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int m = 0;
+    if (cudaOccupancyMaxActiveClusters(&m, kernel, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      m = 0;
     }
+    return m;
+  };
+  int c4 = 0, c2 = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const bool cache = dev >= 0 && dev < 64;
+    if (!cache || !done[dev]) {
+      cudaFuncSetAttribute(k_rank_update_c64_tc_t<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
+      cudaFuncSetAttribute(k_rank_update_c64_tc_t<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
+      cudaFuncSetAttribute(k_rank_update_c64_tc_t<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
+      c4 = max_active(k_rank_update_c64_tc_t<2, 2>, 4);
+      c2 = max_active(k_rank_update_c64_tc_t<2, 1>, 2);
+      if (cache) {
+        clusters4[dev] = c4;
+        clusters2[dev] = c2;
+        done[dev] = true;
+      }
+    } else {
+      c4 = clusters4[dev];
+      c2 = clusters2[dev];
+    }
+  }
+  auto launch_cluster = [&](auto kernel, int size, int64_t blocks, int max_cl) {
+    const int ncl = (int)(blocks < max_cl ? blocks : max_cl);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(size * ncl));
+    cfg.blockDim = dim3(kC64Threads);
+    cfg.dynamicSmemBytes = kC64Smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, tmap, n, o.nrt, o.nct, (int)o.nkc, (const uint8_t*)Aops, (const uint8_t*)Bops,
+                       (const int32_t*)Erow, (const int32_t*)Fcol, ctl, status, prof_p);
+  };
+  // the 2x2 form only where it keeps as many SMs busy as the 2x1 form (the GPCs' SM counts
+  // decide how many clusters of each size fit) and has a tile block for every cluster
+  const int64_t blocks4 = ((o.nrt + 1) / 2) * ((o.nct + 1) / 2), blocks2 = ((o.nrt + 1) / 2) * o.nct;
+  if (c4 >= 1 && 4 * c4 >= 2 * c2 && blocks4 >= c4) {
+    launch_cluster(k_rank_update_c64_tc_t<2, 2>, 4, blocks4, c4);
+    return;
+  }
+  if (c2 >= 1 && blocks2 >= 1) {
+    launch_cluster(k_rank_update_c64_tc_t<2, 1>, 2, blocks2, c2);
+    return;
   }
   const int64_t tiles = o.nrt * o.nct;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  k_rank_update_c64_tc<<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.nct, (int)o.nkc, Aops, Bops, Erow, Fcol,
-                                                            ctl, status, prof_p);
+  k_rank_update_c64_tc_t<1, 1><<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.nct, (int)o.nkc, Aops, Bops,
+                                                                    Erow, Fcol, ctl, status, prof_p);
 }
 
 }  // namespace gf
