@@ -29,9 +29,9 @@ constexpr int kC64KC = 32;                 // real K per operand chunk
 constexpr int kC64Half = kC64M * kC64KC * 2;   // one FP16 hi or lo chunk of a 128-row operand: 8 KB
 constexpr int kC64Block = 2 * kC64Half;        // hi + lo: 16 KB (A and B blocks alike)
 constexpr int kC64NSO = 3;                 // operand stages (A block + B block each)
-constexpr int kC64NSG = 2;                 // G tile stages
+constexpr int kC64NSG = 4;                 // G half-tile stages (a tile's two 64-column halves)
 constexpr int kC64Box = kC64M * 128;       // TMA box: 128 rows x 128 B (16 complex64)
-constexpr int kC64GTile = 4 * kC64Box;     // 64 KB
+constexpr int kC64GTile = 2 * kC64Box;     // one half tile: 32 KB
 constexpr int kC64OpStage = 2 * kC64Block; // 32 KB
 constexpr int kC64BarOff = kC64NSO * kC64OpStage + kC64NSG * kC64GTile;   // 229376
 constexpr int kC64Smem = kC64BarOff + 256;
@@ -243,7 +243,7 @@ __global__ void k_c64_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n
 // tile t handled by CTA t mod gridDim (so the CTAs work on neighbouring tiles and share the
 // operand blocks through L2).
 //   warps 0..15  epilogue: TMEM accumulator + G tile (shared memory) -> G tile
-//   warp 16      G producer (TMA, 4 boxes per tile)     warp 17  MMA issuer
+//   warp 16      G producer (TMA, 2 boxes per half tile) warp 17  MMA issuer
 //   warp 18      storer (TMA stores)                     warp 19  operand producer (bulk copies)
 struct C64Bars {
   uint64_t ofull[kC64NSO], oempty[kC64NSO];
@@ -312,7 +312,7 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
     for (int q = 0; q < kC64NSG; ++q) {
       tc::mbar_init(&bars->gfull[q], 1);
       tc::mbar_init(&bars->gempty[q], 1);
-      tc::mbar_init(&bars->ebar[q], 32 * kC64EpiWarps);
+      tc::mbar_init(&bars->ebar[q], 32 * kC64EpiWarps / 2);   // the epilogue warps of that half
     }
     for (int q = 0; q < 2; ++q) {
       tc::mbar_init(&bars->tfull[q], 1);
@@ -335,18 +335,24 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
         int64_t rg, cg;
         c64_tile_coords(t, nrt_c, nct_c, rg, cg);
         const int64_t rt = rg * CR + rr, ct = cg * CC + cc;
-        const int s = (int)(k % kC64NSG);
-        if (k >= kC64NSG && !tc::mbar_wait_or_abort(&bars->gempty[s], (uint32_t)((k / kC64NSG - 1) & 1), abort, kC64TimeoutNs)) break;
-        if (rt >= nrt || ct >= nct) {            // phantom tile: nothing to load
-          tc::mbar_arrive(&bars->gfull[s]);
-          continue;
+        bool ok = true;
+        for (int hh = 0; hh < 2; ++hh) {         // the tile's two halves go to their own stages
+          const int64_t u = 2 * k + hh;
+          const int s = (int)(u % kC64NSG);
+          if (u >= kC64NSG && !tc::mbar_wait_or_abort(&bars->gempty[s], (uint32_t)((u / kC64NSG - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          const int x0 = (int)(ct * kC64N) + 64 * hh, y = (int)(rt * kC64M);     // x in floats
+          int nbox = 0;
+          if (rt < nrt && ct < nct)              // phantom tile: nothing to load
+            for (int b = 0; b < 2; ++b) nbox += (x0 + 32 * b < 2 * n) ? 1 : 0;
+          if (nbox == 0) {
+            tc::mbar_arrive(&bars->gfull[s]);
+            continue;
+          }
+          tc::mbar_arrive_expect_tx(&bars->gfull[s], (uint32_t)(nbox * kC64Box));
+          uint8_t* gt = gts + s * kC64GTile;
+          for (int b = 0; b < nbox; ++b) tc::tma_load_2d(gt + b * kC64Box, &tmapG, x0 + 32 * b, y, &bars->gfull[s]);
         }
-        const int x0 = (int)(ct * kC64N), y = (int)(rt * kC64M);     // x in floats
-        int nbox = 0;
-        for (int b = 0; b < 4; ++b) nbox += (x0 + 32 * b < 2 * n) ? 1 : 0;
-        tc::mbar_arrive_expect_tx(&bars->gfull[s], (uint32_t)(nbox * kC64Box));
-        uint8_t* gt = gts + s * kC64GTile;
-        for (int b = 0; b < nbox; ++b) tc::tma_load_2d(gt + b * kC64Box, &tmapG, x0 + 32 * b, y, &bars->gfull[s]);
+        if (!ok) break;
       }
     }
     __syncwarp();
@@ -442,10 +448,11 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
       const int64_t rt = rg * CR + rr, ct = cg * CC + cc;
       const bool real = rt < nrt && ct < nct;
       const int b = (int)(k & 1);
-      const int s = (int)(k % kC64NSG);
+      const int64_t u = 2 * k + (h >> 1);      // this warp's half of the tile
+      const int s = (int)(u % kC64NSG);
       const int Ei = real ? Erow[rt * kC64M + r] : 0;
       if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kC64TimeoutNs)) break;
-      if (!tc::mbar_wait_or_abort(&bars->gfull[s], (uint32_t)((k / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
+      if (!tc::mbar_wait_or_abort(&bars->gfull[s], (uint32_t)((u / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
       tc::fence_after_sync();
       float acc1[32], acc2[32];
       {
@@ -471,7 +478,7 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
         // box h holds real columns 32h .. 32h+31 of the tile = 8 chunks of 16 B (128B swizzle);
         // chunk ch holds complex columns 2ch, 2ch+1 of this quarter
         const int32_t* Fq = Fcol + ct * (kC64N / 2) + h * 16;
-        uint8_t* row = gts + s * kC64GTile + h * kC64Box + r * 128;
+        uint8_t* row = gts + s * kC64GTile + (h & 1) * kC64Box + r * 128;
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
           const float s0 = __int_as_float((Ei + Fq[2 * ch] + 127) << 23);
@@ -496,17 +503,22 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
         int64_t rg, cg;
         c64_tile_coords(t, nrt_c, nct_c, rg, cg);
         const int64_t rt = rg * CR + rr, ct = cg * CC + cc;
-        const int s = (int)(k % kC64NSG);
-        if (!tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)((k / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
-        if (rt < nrt && ct < nct) {
-          const int x0 = (int)(ct * kC64N), y = (int)(rt * kC64M);
-          uint8_t* gt = gts + s * kC64GTile;
-          for (int b = 0; b < 4; ++b)
-            if (x0 + 32 * b < 2 * n) tc::tma_store_2d(&tmapG, x0 + 32 * b, y, gt + b * kC64Box);
+        bool ok = true;
+        for (int hh = 0; hh < 2; ++hh) {
+          const int64_t u = 2 * k + hh;
+          const int s = (int)(u % kC64NSG);
+          if (!tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)((u / kC64NSG) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          if (rt < nrt && ct < nct) {
+            const int x0 = (int)(ct * kC64N) + 64 * hh, y = (int)(rt * kC64M);
+            uint8_t* gt = gts + s * kC64GTile;
+            for (int b = 0; b < 2; ++b)
+              if (x0 + 32 * b < 2 * n) tc::tma_store_2d(&tmapG, x0 + 32 * b, y, gt + b * kC64Box);
+          }
+          tc::bulk_commit();
+          tc::bulk_wait_read0();
+          tc::mbar_arrive(&bars->gempty[s]);
         }
-        tc::bulk_commit();
-        tc::bulk_wait_read0();
-        tc::mbar_arrive(&bars->gempty[s]);
+        if (!ok) break;
       }
       tc::bulk_wait0();
     }
