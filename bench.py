@@ -110,6 +110,30 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one update launch, from a
+# single-pass ncu capture of the full-size workload, valid only for the kernel source it was
+# taken on (SHA-256 over the files below); otherwise the line reports null.
+TRAFFIC_SOURCES = ("paper_2202_05388_gb300/csrc/gf_update_tc.cu", "paper_2202_05388_gb300/csrc/gf_tc.cuh")
+TRAFFIC = {
+    "brush_192x192_p4_c128": {"sha256": "f2811ae0be0fd617654bb80bf7337bbb1d796642412f3a13e236c266fb746205",
+                              "bytes": 21.79e9 + 21.69e9,
+                              "profile": "profiles/rank_update_tc_brush192_launches.md"},
+}
+
+
+def measured_traffic(workload_name):
+    import hashlib
+    rec = TRAFFIC.get(workload_name)
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes"] if h.hexdigest() == rec["sha256"] else None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -472,8 +496,11 @@ def run_native(args):
     achieved_gbs = bytes_per_launch / (kern_avg_ms * 1e-3) / 1e9
     achieved_tfl = flops_per_launch / (kern_avg_ms * 1e-3) / 1e12
     if wl.dtype == "c128":
+        tr = measured_traffic(wl.name)
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
-                "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind,
+                "frac": achieved_gbs / peak_hbm, "traffic": tr, "peak_kind": peak_kind,
+                "traffic_note": "bytes per launch, ncu single-pass capture of this workload on this kernel source"
+                                if tr is not None else "no capture for this workload / kernel source",
                 "kernel": "k_rank_update_ozaki (tcgen05 digit products, TMA tiles) + operand prep",
                 "fp64_pipe_note": "the same update on native DFMA is FP64-pipe bound; see dfma_update"}
     elif wl.spec.k * (4 if wl.spec.kind == 1 else 1) <= 4:
