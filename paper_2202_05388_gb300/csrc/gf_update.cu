@@ -20,6 +20,129 @@ struct CapArgs {
   int pmax;
 };
 
+// Blocked right-looking LU with partial pivoting of the row-major p x p complex matrix A (global
+// memory), for p <= kLuMaxBlocked, by the whole CTA.  Panels of kLuNB columns are factored in
+// shared memory (pivot = largest modulus, lowest row on ties, as in the unblocked form); their row
+// interchanges are then applied to the rest of the rows, U12 = L11^{-1} A12 is solved column by
+// column and the trailing matrix receives the rank-kLuNB update -- every element independently,
+// so the global-memory traffic is parallel instead of a chain of dependent accesses.  The result
+// (L below the diagonal with unit diagonal, U on and above it, piv[c] = row exchanged with row c
+// at step c) is the unblocked factorisation's.  Returns false (in every thread) when a pivot is
+// zero or below thresh.
+constexpr int kLuNB = 8;
+constexpr int kLuMaxBlocked = 256;
+
+// sP: shared memory for kLuMaxBlocked x kLuNB entries (the panel, row-major [row][j])
+__device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ piv, double thresh, cplx* sP) {
+  __shared__ int s_pv[kLuNB];
+  __shared__ int s_bad2, s_pr;
+  __shared__ double s_bv2[32];
+  __shared__ int s_br2[32];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  if (tid == 0) s_bad2 = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < p; c0 += kLuNB) {
+    const int nb = p - c0 < kLuNB ? p - c0 : kLuNB;
+    const int m = p - c0;
+    for (int t = tid; t < m * nb; t += nt) {
+      const int r = t / nb, j = t - r * nb;
+      sP[r * kLuNB + j] = A[(int64_t)(c0 + r) * p + c0 + j];
+    }
+    __syncthreads();
+    // ---- panel factorisation in shared memory
+    for (int j = 0; j < nb; ++j) {
+      double bv = -1.0;
+      int br = 0x7fffffff;
+      for (int r = j + tid; r < m; r += nt) {
+        const double v = cabs1(sP[r * kLuNB + j]);
+        if (v > bv) { bv = v; br = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int orr = __shfl_down_sync(0xffffffffu, br, o);
+        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+      }
+      if (lane == 0) { s_bv2[wid] = bv; s_br2[wid] = br; }
+      __syncthreads();
+      if (tid == 0) {
+        double b = s_bv2[0];
+        int r = s_br2[0];
+        for (int w = 1; w < nw; ++w)
+          if (s_bv2[w] > b || (s_bv2[w] == b && s_br2[w] < r)) { b = s_bv2[w]; r = s_br2[w]; }
+        if (!(b >= thresh) || !(b > 0.0)) s_bad2 = 1;
+        s_pr = r;
+        s_pv[j] = c0 + r;
+        piv[c0 + j] = c0 + r;
+      }
+      __syncthreads();
+      if (s_bad2) return false;
+      const int pr = s_pr;
+      if (pr != j && tid < nb) {
+        const cplx t0 = sP[j * kLuNB + tid];
+        sP[j * kLuNB + tid] = sP[pr * kLuNB + tid];
+        sP[pr * kLuNB + tid] = t0;
+      }
+      __syncthreads();
+      const cplx pv = sP[j * kLuNB + j];
+      for (int r = j + 1 + tid; r < m; r += nt) {
+        const cplx f = cdiv(sP[r * kLuNB + j], pv);
+        sP[r * kLuNB + j] = f;
+        for (int k = j + 1; k < nb; ++k) sP[r * kLuNB + k] = sP[r * kLuNB + k] - f * sP[j * kLuNB + k];
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < m * nb; t += nt) {
+      const int r = t / nb, j = t - r * nb;
+      A[(int64_t)(c0 + r) * p + c0 + j] = sP[r * kLuNB + j];
+    }
+    // ---- the panel's interchanges on the columns outside it (one thread per column)
+    for (int v = tid; v < p; v += nt) {
+      if (v >= c0 && v < c0 + nb) continue;
+      for (int j = 0; j < nb; ++j) {
+        const int r = s_pv[j];
+        if (r != c0 + j) {
+          const cplx t0 = A[(int64_t)(c0 + j) * p + v];
+          A[(int64_t)(c0 + j) * p + v] = A[(int64_t)r * p + v];
+          A[(int64_t)r * p + v] = t0;
+        }
+      }
+    }
+    __syncthreads();
+    const int w = p - c0 - nb;                   // trailing width
+    if (w > 0) {
+      // ---- U12 = L11^{-1} A12 (unit lower, one thread per column)
+      for (int v = tid; v < w; v += nt) {
+        cplx x[kLuNB];
+#pragma unroll
+        for (int j = 0; j < kLuNB; ++j)
+          if (j < nb) x[j] = A[(int64_t)(c0 + j) * p + c0 + nb + v];
+#pragma unroll
+        for (int j = 1; j < kLuNB; ++j)
+          if (j < nb)
+#pragma unroll
+            for (int i = 0; i < kLuNB; ++i)
+              if (i < j) x[j] = x[j] - sP[j * kLuNB + i] * x[i];
+#pragma unroll
+        for (int j = 1; j < kLuNB; ++j)
+          if (j < nb) A[(int64_t)(c0 + j) * p + c0 + nb + v] = x[j];
+      }
+      __syncthreads();
+      // ---- A22 -= L21 U12, every element independently (coalesced along the row)
+      for (int e = tid; e < w * w; e += nt) {
+        const int i = e / w, v = e - i * w;
+        const int64_t o = (int64_t)(c0 + nb + i) * p + c0 + nb + v;
+        cplx acc = A[o];
+#pragma unroll
+        for (int j = 0; j < kLuNB; ++j)
+          if (j < nb) acc = acc - sP[(nb + i) * kLuNB + j] * A[(int64_t)(c0 + j) * p + c0 + nb + v];
+        A[o] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 // Single CTA.  The p x p matrices live in the workspace (p can reach 4k).
 __device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayout& L, char* ws,
                                                  const uint8_t* __restrict__ state,
@@ -101,74 +224,92 @@ __device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayou
       const double thresh = kSingularRel * s_red[0];
       __syncthreads();
       // LU with partial pivoting (row-major, in place; L below the diagonal, unit diagonal).
-      // Pivot: block-wide search for the largest modulus, lowest row on ties; multipliers per
-      // row; trailing update with a warp per row and lanes along the (coalesced) columns.
       __shared__ int s_piv;
       __shared__ int s_bad;
       __shared__ double s_bv[32];
       __shared__ int s_br[32];
-      __shared__ cplx s_f[1024];
+      __shared__ cplx s_f[kLuMaxBlocked * kLuNB];   // blocked: the panel; unblocked: multipliers
       if (tid == 0) s_bad = 0;
       const int nw = (int)(blockDim.x >> 5), lane = tid & 31, wid = tid >> 5;
-      for (int c = 0; c < p; ++c) {
-        double bv = -1.0;
-        int br = 0x7fffffff;
-        for (int rr = c + tid; rr < p; rr += blockDim.x) {
-          const double m = cabs1(A[rr * p + c]);
-          if (m > bv) { bv = m; br = rr; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-          const int orr = __shfl_down_sync(0xffffffffu, br, o);
-          if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-        }
-        if (lane == 0) { s_bv[wid] = bv; s_br[wid] = br; }
-        __syncthreads();
-        if (tid == 0) {
-          double b = s_bv[0];
-          int r = s_br[0];
-          for (int w = 1; w < nw; ++w)
-            if (s_bv[w] > b || (s_bv[w] == b && s_br[w] < r)) { b = s_bv[w]; r = s_br[w]; }
-          if (!(b >= thresh) || !(b > 0.0)) s_bad = 1;
-          s_piv = r;
-          piv[c] = r;
-        }
-        __syncthreads();
-        const int r = s_piv;
-        if (s_bad) break;
-        if (r != c) {
-          for (int v = tid; v < p; v += blockDim.x) {
-            cplx t0 = A[c * p + v];
-            A[c * p + v] = A[r * p + v];
-            A[r * p + v] = t0;
+      if (p <= kLuMaxBlocked) {
+        if (!lu_blocked(A, p, piv, thresh, s_f)) { singular = true; break; }
+        // y = P E_V, then the unit-lower solve (column-oriented: one synchronisation per column)
+        if (tid == 0)
+          for (int c = 0; c < p; ++c) {
+            const int r = piv[c];
+            if (r != c) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
           }
-          if (tid == 0) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
+        __syncthreads();
+        for (int c = 0; c < p; ++c) {
+          const cplx yc = y[c];
+          for (int r = c + 1 + tid; r < p; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
+          __syncthreads();
+        }
+      } else {
+        // unblocked form for very large joint sets (p > 256): pivot search across the block,
+        // multipliers per row, trailing update with a warp per row and lanes along the columns
+        for (int c = 0; c < p; ++c) {
+          double bv = -1.0;
+          int br = 0x7fffffff;
+          for (int rr = c + tid; rr < p; rr += blockDim.x) {
+            const double m = cabs1(A[rr * p + c]);
+            if (m > bv) { bv = m; br = rr; }
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+            const int orr = __shfl_down_sync(0xffffffffu, br, o);
+            if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+          }
+          if (lane == 0) { s_bv[wid] = bv; s_br[wid] = br; }
+          __syncthreads();
+          if (tid == 0) {
+            double b = s_bv[0];
+            int r = s_br[0];
+            for (int w = 1; w < nw; ++w)
+              if (s_bv[w] > b || (s_bv[w] == b && s_br[w] < r)) { b = s_bv[w]; r = s_br[w]; }
+            if (!(b >= thresh) || !(b > 0.0)) s_bad = 1;
+            s_piv = r;
+            piv[c] = r;
+          }
+          __syncthreads();
+          const int r = s_piv;
+          if (s_bad) break;
+          if (r != c) {
+            for (int v = tid; v < p; v += blockDim.x) {
+              cplx t0 = A[c * p + v];
+              A[c * p + v] = A[r * p + v];
+              A[r * p + v] = t0;
+            }
+            if (tid == 0) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
+          }
+          __syncthreads();
+          const cplx pv = A[c * p + c];
+          const cplx yc = y[c];
+          for (int rr = c + 1 + tid; rr < p; rr += blockDim.x) {
+            const cplx f = cdiv(A[rr * p + c], pv);
+            s_f[rr] = f;
+            A[rr * p + c] = f;
+            y[rr] = y[rr] - f * yc;
+          }
+          __syncthreads();
+          for (int rr = c + 1 + wid; rr < p; rr += nw) {
+            const cplx f = s_f[rr];
+            for (int v = c + 1 + lane; v < p; v += 32) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
+          }
+          __syncthreads();
         }
         __syncthreads();
-        const cplx pv = A[c * p + c];
+        if (s_bad) { singular = true; break; }
+      }
+      // upper solve for y (column-oriented: one synchronisation per column)
+      for (int c = p - 1; c >= 0; --c) {
+        if (tid == 0) y[c] = cdiv(y[c], A[c * p + c]);
+        __syncthreads();
         const cplx yc = y[c];
-        for (int rr = c + 1 + tid; rr < p; rr += blockDim.x) {
-          const cplx f = cdiv(A[rr * p + c], pv);
-          s_f[rr] = f;
-          A[rr * p + c] = f;
-          y[rr] = y[rr] - f * yc;
-        }
-        __syncthreads();
-        for (int rr = c + 1 + wid; rr < p; rr += nw) {
-          const cplx f = s_f[rr];
-          for (int v = c + 1 + lane; v < p; v += 32) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
-        }
+        for (int r = tid; r < c; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
         __syncthreads();
       }
-      __syncthreads();
-      if (s_bad) { singular = true; break; }
-      // back substitution for y (serial; p is small)
       if (tid == 0) {
-        for (int c = p - 1; c >= 0; --c) {
-          cplx acc = y[c];
-          for (int v = c + 1; v < p; ++v) acc = acc - A[c * p + v] * y[v];
-          y[c] = cdiv(acc, A[c * p + c]);
-        }
         cplx EN = U.E[N];
         cplx dE = mk(0.0, 0.0);
         for (int u = 0; u < p; ++u) dE = dE + dchi[u] * (ldG(U.G, a.u.dtype, U.ldg, N, V[u]) * y[u]);
