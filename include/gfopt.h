@@ -267,6 +267,15 @@ typedef struct gf_batch_item {
   int32_t* applied;     /* 1: candidates applied by the step; may be NULL */
   void* ws;             /* gf_workspace_size(&prob.geom, 1, dtype, spec) bytes, 256-byte aligned */
   size_t ws_bytes;
+  /* policy: epsilon = 0 greedy; epsilon in (0, 1] the epsilon-greedy policy of
+   * gf_select_egreedy, reading the pair uniforms[2 t], uniforms[2 t + 1] at step t = *step (device
+   * counter, incremented by every batch step, so graph replays draw new numbers); a step with
+   * t >= horizon sets the item's status to GF_ENOMEM.  uniforms and step may be NULL when
+   * epsilon = 0. */
+  double epsilon;
+  const double* uniforms;
+  int32_t* step;
+  int32_t horizon;
 } gf_batch_item;
 typedef struct gf_batch gf_batch;
 /* Device bytes of the item table of a batch of nitems. */

@@ -37,12 +37,22 @@ class Schedule:
 
 
 class BatchOptimizer:
-    def __init__(self, workloads: Sequence[Workload], dtype: str = "c128", device: int = 0):
+    def __init__(self, workloads: Sequence[Workload], dtype: str = "c128", device: int = 0,
+                 policies: Optional[Sequence[Optional[tuple]]] = None, horizon: int = 4096):
+        """policies: per problem None (greedy) or (epsilon, seed) for the epsilon-greedy policy;
+        epsilon-greedy batches run on the fused schedule only (its device step counters keep
+        drawing new uniforms across graph replays)."""
         self.device = torch.device("cuda", device)
         self.h = B.Handle(device)
         self.workloads = list(workloads)
         self.opts = [GreedyOptimizer(w.geoms, w.spec, dtype=dtype, device=device, handle=self.h)
                      for w in self.workloads]
+        self.policies = list(policies) if policies is not None else [None] * len(self.opts)
+        for o, pol in zip(self.opts, self.policies):
+            if pol is not None and pol[0] > 0:
+                o.set_egreedy(pol[0], seed=pol[1], horizon=horizon)
+        self._policy_steps = torch.zeros(len(self.opts), dtype=torch.int32, device=self.device)
+        self.exploring = any(o.epsilon is not None for o in self.opts)
         self.sizes = [o.n for o in self.opts]
         self.schedule = Schedule(0, "given", fused=True)
         self._streams: List[torch.cuda.Stream] = []
@@ -52,6 +62,8 @@ class BatchOptimizer:
         self._batches = None
         self._batch_groups = 0
         self.fusable = all(o.spec.k == 1 and len(o.geoms) == 1 for o in self.opts)
+        if not self.fusable and self.exploring:
+            raise ValueError("epsilon-greedy batches need k = 1 and one wavelength per problem")
         if not self.fusable:
             self.schedule = Schedule(min(8, len(self.opts)), "largest_first")
 
@@ -74,10 +86,14 @@ class BatchOptimizer:
                 items = []
                 for i in members[c0:c0 + B.BATCH_MAX]:
                     o = self.opts[i]
+                    eps = o.epsilon if o.epsilon is not None else 0.0
                     items.append(B.gf_batch_item(o.probs[0], o.state.data_ptr(), o.dfom.data_ptr(),
                                                  o.idx.data_ptr(), o.val.data_ptr(), o.status.data_ptr(),
                                                  o.fom.data_ptr(), self._applied_step[i:i + 1].data_ptr(),
-                                                 o.ws.data_ptr(), o.ws_bytes))
+                                                 o.ws.data_ptr(), o.ws_bytes, eps,
+                                                 o._u.data_ptr() if eps > 0 else None,
+                                                 self._policy_steps[i:i + 1].data_ptr() if eps > 0 else None,
+                                                 int(o._u.shape[0]) if eps > 0 else 0))
                 tb = self.h.gf_batch_table_size(len(items))
                 table = torch.empty(tb, dtype=torch.uint8, device=self.device)
                 self._tables.append(table)
@@ -102,6 +118,8 @@ class BatchOptimizer:
     def fill(self):
         for o in self.opts:
             o.fill()
+        self._policy_steps.zero_()
+        self.applied.zero_()
         torch.cuda.synchronize(self.device)
 
     def _order(self) -> List[int]:
@@ -116,6 +134,8 @@ class BatchOptimizer:
 
     # ---- one step of every problem, enqueued on the current stream
     def enqueue_step(self):
+        if self.exploring and not self.schedule.fused:
+            raise ValueError("epsilon-greedy batches run on the fused schedule")
         if self.schedule.fused:
             self._ensure_batches()
             main = torch.cuda.current_stream(self.device)
@@ -184,6 +204,8 @@ class BatchOptimizer:
             n = len(self.opts)
             counts = sorted({c for c in (1, 8, 16, n) if c <= n})
             candidates = [Schedule(c, o) for c, o in itertools.product(counts, ("given", "largest_first"))]
+            if self.exploring:
+                candidates = []
             if self.fusable:
                 sms = torch.cuda.get_device_properties(self.device).multi_processor_count
                 if self.opts[0].dtype == B.GF_C128:     # one update CTA fits an SM

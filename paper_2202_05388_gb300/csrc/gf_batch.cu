@@ -80,6 +80,14 @@ gf_status gf_batch_create(gf_handle* h, int32_t nitems, const gf_batch_item* ite
       return bfail(h, GF_ENOMEM, "item %d: workspace has %lld bytes, needs %lld", i, (long long)it.ws_bytes,
                    (long long)L.total);
     }
+    if (!(it.epsilon >= 0.0 && it.epsilon <= 1.0)) {
+      delete b;
+      return bfail(h, GF_EINVAL, "item %d: epsilon must lie in [0, 1]", i);
+    }
+    if (it.epsilon > 0.0 && (!it.uniforms || !it.step || it.horizon < 1)) {
+      delete b;
+      return bfail(h, GF_EINVAL, "item %d: the epsilon-greedy policy needs uniforms, a step counter and horizon >= 1", i);
+    }
     gf::BatchItem& d = b->host[i];
     d.G = it.prob.G;
     d.ldg = it.prob.ldg;
@@ -98,6 +106,10 @@ gf_status gf_batch_create(gf_handle* h, int32_t nitems, const gf_batch_item* ite
     d.status = it.status;
     d.fom = it.fom_out;
     d.applied = it.applied;
+    d.epsilon = it.epsilon;
+    d.uniforms = it.uniforms;
+    d.step = it.step;
+    d.horizon = it.horizon;
     const int64_t N = (int64_t)d.nx * d.ny;
     const int64_t units = spec->kind == GF_KIND_SINGLE ? N : (int64_t)(d.nx - 1) * (d.ny - 1);
     if (N + 1 > b->widest_n) b->widest_n = N + 1;

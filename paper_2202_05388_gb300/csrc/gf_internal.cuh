@@ -248,6 +248,10 @@ struct BatchItem {
   int32_t* status;
   double* fom;
   int32_t* applied;
+  double epsilon;              // 0: greedy; else epsilon-greedy with the uniforms below
+  const double* uniforms;      // 2 per step
+  int32_t* step;               // device step counter
+  int32_t horizon;
 };
 __device__ __forceinline__ void batch_upd_args(const BatchItem& it, int dtype, UpdArgs& a) {
   a.nlam = 1;

@@ -91,11 +91,55 @@ __global__ void __launch_bounds__(kSelThreads) k_select_best(const double* __res
   select_best_body(dfom, ncand, tie_rel, idx, val, status);
 }
 
-// Batched greedy selection: one CTA per problem of the device table.
+// Batched selection: one CTA per problem of the device table; greedy, or epsilon-greedy (Sec. V)
+// with the problem's own uniform stream: the explore list (the four best improving candidates
+// in (-dFOM, id) order) comes from four block-wide passes that skip the ids already taken.
 __global__ void __launch_bounds__(kSelThreads) k_select_best_batch(const BatchItem* __restrict__ items,
                                                                    double tie_rel) {
   const BatchItem& it = items[blockIdx.x];
   select_best_body(it.dfom, it.ncand, tie_rel, it.idx, it.val, it.status);
+  if (!(it.epsilon > 0.0)) return;
+  __shared__ int s_go;
+  __shared__ int64_t s_top[4];
+  __shared__ double s_val[4];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int32_t t = *it.step;
+    *it.step = t + 1;
+    s_go = 0;
+    if (t >= it.horizon) {
+      *it.status = GF_ENOMEM;                     // the uniform stream is exhausted
+    } else if (*it.status == GF_OK && it.uniforms[2 * (int64_t)t] < it.epsilon) {
+      s_go = 1;
+    }
+  }
+  __syncthreads();
+  if (!s_go) return;
+  int m = 0;
+  for (int pass = 0; pass < 4; ++pass) {
+    double bv = -INFINITY;
+    int64_t bid = INT64_MAX;
+    for (int64_t c = threadIdx.x; c < it.ncand; c += blockDim.x) {
+      const double v = it.dfom[c];
+      if (!(v > 0.0) || !better(v, c, bv, bid)) continue;
+      bool taken = false;
+      for (int q = 0; q < pass; ++q) taken |= s_top[q] == c;
+      if (!taken) { bv = v; bid = c; }
+    }
+    block_best(bv, bid);
+    if (!(bv > 0.0)) break;
+    if (threadIdx.x == 0) { s_top[pass] = bid; s_val[pass] = bv; }
+    __syncthreads();
+    m = pass + 1;
+  }
+  if (threadIdx.x == 0 && m > 0) {
+    const int32_t t = *it.step - 1;
+    int r = (int)(it.uniforms[2 * (int64_t)t + 1] * (double)m);
+    if (r > m - 1) r = m - 1;
+    if (r < 0) r = 0;
+    it.idx[0] = (int32_t)s_top[r];
+    it.val[0] = s_val[r];
+  }
 }
 
 void launch_select_batch(const BatchItem* items, int nprob, double tie_rel, cudaStream_t st) {

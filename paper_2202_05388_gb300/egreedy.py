@@ -11,7 +11,10 @@ from typing import Dict, List, Sequence
 
 import numpy as np
 
+import torch
+
 from . import gfopt as B
+from .batch import BatchOptimizer
 from .optimizer import GreedyOptimizer
 from .workloads import CandidateSpec, Geometry, KIND_SINGLE, DIR_FILL, DIR_CLEAR, Workload
 
@@ -53,7 +56,7 @@ def egreedy_study(epsilons: Sequence[float] = (0.0, 0.1, 0.2, 0.3), trajectories
             opt.fill()
             fom0 = float(opt.fom.cpu()[0])
             if eps > 0:
-                opt.set_egreedy(eps, seed=seed * 1000003 + e_i * 1009 + t, horizon=max_steps + 1)
+                opt.set_egreedy(eps, seed=_seed(seed, e_i, t), horizon=max_steps + 1)
             trace = run_to_termination(opt, max_steps)
             finals.append((trace[-1] if trace else fom0) / fom0)
             steps.append(len(trace))
@@ -61,4 +64,44 @@ def egreedy_study(epsilons: Sequence[float] = (0.0, 0.1, 0.2, 0.3), trajectories
         out[eps] = {"trajectories": len(finals), "final_fom_mean": float(f.mean()), "final_fom_std": float(f.std()),
                     "final_fom_max": float(f.max()), "final_fom_min": float(f.min()),
                     "steps_mean": float(np.mean(steps)), "finals": finals}
+    return out
+
+
+def _seed(seed: int, e_i: int, t: int) -> int:
+    return seed * 1000003 + e_i * 1009 + t
+
+
+def egreedy_study_batched(epsilons: Sequence[float] = (0.0, 0.1, 0.2, 0.3), trajectories: int = 20,
+                          seed: int = 0, max_steps: int = 4000, device: int = 0, chunk: int = 32) -> Dict[float, dict]:
+    """The same study with every trajectory a problem of one fused batch (one launch per stage
+    of the step for all of them, chunk steps per CUDA graph), run until every trajectory has no
+    improving action left.  Same seeds as egreedy_study, so the same trajectories."""
+    wl = metalens_21()
+    pols, owner = [], []
+    for e_i, eps in enumerate(epsilons):
+        for t in range(trajectories if eps > 0 else 1):
+            pols.append((eps, _seed(seed, e_i, t)) if eps > 0 else None)
+            owner.append(eps)
+    bo = BatchOptimizer([wl] * len(pols), dtype=wl.dtype, device=device, policies=pols, horizon=max_steps + 2 * chunk)
+    bo.fill()
+    fom0 = float(bo.opts[0].fom.cpu()[0])
+    bo.capture(chunk)                       # one step runs before the capture
+    steps = 1
+    while steps < max_steps:
+        bo.replay()
+        steps += chunk
+        status = torch.stack([o.status for o in bo.opts]).cpu().numpy().ravel()
+        if (status != B.GF_OK).all():
+            break
+    applied = bo.applied.cpu().numpy()
+    foms = [float(o.fom.cpu()[0]) / fom0 for o in bo.opts]
+    out = {}
+    for eps in epsilons:
+        sel = [i for i, e in enumerate(owner) if e == eps]
+        f = np.array([foms[i] for i in sel])
+        out[eps] = {"trajectories": len(sel), "final_fom_mean": float(f.mean()), "final_fom_std": float(f.std()),
+                    "final_fom_max": float(f.max()), "final_fom_min": float(f.min()),
+                    "steps_mean": float(np.mean([applied[i] for i in sel])), "finals": [foms[i] for i in sel]}
+    out["_steps_enqueued"] = steps
+    bo.close()
     return out

@@ -67,7 +67,8 @@ class gf_lowrank(C.Structure):
 class gf_batch_item(C.Structure):
     _fields_ = [("prob", gf_problem), ("state", C.c_void_p), ("dfom", C.c_void_p), ("idx", C.c_void_p),
                 ("val", C.c_void_p), ("status", C.c_void_p), ("fom_out", C.c_void_p),
-                ("applied", C.c_void_p), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
+                ("applied", C.c_void_p), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t),
+                ("epsilon", C.c_double), ("uniforms", C.c_void_p), ("step", C.c_void_p), ("horizon", C.c_int32)]
 
 
 _lib = None

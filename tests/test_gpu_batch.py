@@ -120,3 +120,32 @@ def test_autotune_picks_a_timed_schedule():
     best = bo.autotune(candidates=[Schedule(1, "given"), Schedule(6, "largest_first")], steps=1, reps=1)
     assert best in [t[0] for t in bo.timings]
     assert min(t[1] for t in bo.timings) == [t[1] for t in bo.timings if t[0] == best][0]
+
+
+def test_batch_create_validates_every_item():
+    wls = _small_batch(3)
+    bo = BatchOptimizer(wls)
+    h = bo.h
+    o = bo.opts[0]
+    item = B.gf_batch_item(o.probs[0], o.state.data_ptr(), o.dfom.data_ptr(), o.idx.data_ptr(), o.val.data_ptr(),
+                           o.status.data_ptr(), o.fom.data_ptr(), 0, o.ws.data_ptr(), o.ws_bytes)
+    tb = h.gf_batch_table_size(1)
+    table = torch.empty(tb, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.GfError, match="k = 1"):
+        h.gf_batch_create([item], o.dtype, W.CandidateSpec(W.KIND_SINGLE, 3, 2), table, tb)
+    with pytest.raises(B.GfError) as e:
+        h.gf_batch_create([item], o.dtype, o.spec, table, tb - 256)
+    assert e.value.status == B.GF_ENOMEM
+    short = B.gf_batch_item(o.probs[0], o.state.data_ptr(), o.dfom.data_ptr(), o.idx.data_ptr(), o.val.data_ptr(),
+                            o.status.data_ptr(), o.fom.data_ptr(), 0, o.ws.data_ptr(), 1024)
+    with pytest.raises(B.GfError) as e:
+        h.gf_batch_create([short], o.dtype, o.spec, table, tb)
+    assert e.value.status == B.GF_ENOMEM
+    null_state = B.gf_batch_item(o.probs[0], None, o.dfom.data_ptr(), o.idx.data_ptr(), o.val.data_ptr(),
+                                 o.status.data_ptr(), o.fom.data_ptr(), 0, o.ws.data_ptr(), o.ws_bytes)
+    with pytest.raises(B.GfError, match="non-NULL"):
+        h.gf_batch_create([null_state], o.dtype, o.spec, table, tb)
+    b = h.gf_batch_create([item], o.dtype, o.spec, table, tb)
+    with pytest.raises(B.GfError):
+        h.gf_batch_set_schedule(b, -1)
+    h.gf_batch_destroy(b)

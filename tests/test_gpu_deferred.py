@@ -122,3 +122,27 @@ def test_deferred_full_store_reports_enomem():
     assert len(res) == 5 and res[-1].status == B.GF_ENOMEM
     assert opt.count() == (4, 4)
     assert int(opt.state.sum().item()) == 4
+
+
+def test_deferred_validation():
+    wl = W.small(10, 8, kind=W.KIND_SINGLE, dir_mask=3)
+    g = wl.geoms[0]
+    opt = DeferredOptimizer(g, wl.spec, max_cols=8)
+    with pytest.raises(B.GfError) as e:
+        opt.h.gf_lowrank_init(opt.lr, opt.ws, 256)
+    assert e.value.status == B.GF_ENOMEM
+    bad = B.gf_lowrank(B.geom_struct(g), opt.E.data_ptr(), opt.bands.data_ptr(), opt.monrow.data_ptr(),
+                       opt.U.data_ptr() + 8, 8)
+    with pytest.raises(B.GfError, match="aligned"):
+        opt.h.gf_lowrank_init(bad, opt.ws, opt.ws_bytes)
+    few = B.gf_lowrank(B.geom_struct(g), opt.E.data_ptr(), opt.bands.data_ptr(), opt.monrow.data_ptr(),
+                       opt.U.data_ptr(), 2)
+    with pytest.raises(B.GfError, match="max_cols"):
+        opt.h.gf_lowrank_init(few, opt.ws, opt.ws_bytes)
+    opt.init()
+    with pytest.raises(B.GfError, match="k = 1"):
+        opt.h.gf_lowrank_update(opt.lr, opt.state, W.CandidateSpec(W.KIND_SINGLE, 3, 4), opt.idx, opt.status,
+                                opt.fom, opt.ws, opt.ws_bytes)
+    with pytest.raises(B.GfError) as e:
+        DeferredOptimizer(g, W.CandidateSpec(W.KIND_SINGLE, 3, 2), max_cols=8)
+    assert e.value.status == B.GF_EINVAL
