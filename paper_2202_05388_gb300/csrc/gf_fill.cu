@@ -96,6 +96,55 @@ __global__ void k_fill_expand(int nx, int ny, int64_t ldg, const cplx* __restric
   }
 }
 
+// Pixel-row-pair blocks: for image rows (iy, jy) the nx x nx sub-block G[iy*nx + ix, jy*nx + jx]
+// equals table row |iy - jy| at offset |ix - jx| (G0 depends on the offset only).  One CTA stages
+// that table row in shared memory (in the storage precision) and writes the sub-block row by
+// row with coalesced stores, so the table is read nx times less often than per entry and the
+// fill is bound by the stores.  The monitor row and column and the padding columns follow in
+// k_fill_edges.  Used for nx <= kFillMaxNx.
+constexpr int kFillMaxNx = 2048;
+
+template <typename T>
+__device__ __forceinline__ T to_store(cplx v);
+template <>
+__device__ __forceinline__ double2 to_store<double2>(cplx v) { return make_double2(v.re, v.im); }
+template <>
+__device__ __forceinline__ float2 to_store<float2>(cplx v) { return make_float2((float)v.re, (float)v.im); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fill_blocks(int nx, int ny, int64_t ldg, const cplx* __restrict__ table,
+                                                     T* __restrict__ G) {
+  extern __shared__ __align__(16) unsigned char fill_smem[];
+  T* trow = reinterpret_cast<T*>(fill_smem);
+  const int64_t pairs = (int64_t)ny * ny;
+  for (int64_t q = blockIdx.x; q < pairs; q += gridDim.x) {
+    const int iy = (int)(q / ny), jy = (int)(q - (int64_t)iy * ny);
+    const int ay = iy > jy ? iy - jy : jy - iy;
+    __syncthreads();                               // previous pair done with trow
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) trow[x] = to_store<T>(table[(int64_t)ay * nx + x]);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int ix = warp; ix < nx; ix += nwarp) {          // a warp per row, lanes along it
+      T* row = G + ((int64_t)iy * nx + ix) * ldg + (int64_t)jy * nx;
+      for (int jx = lane; jx < nx; jx += 32) row[jx] = trow[ix > jx ? ix - jx : jx - ix];
+    }
+  }
+}
+
+// monitor column (rows 0..N-1), monitor row (G_NN = 0) and padding columns (zero)
+template <typename T>
+__global__ void k_fill_edges(int nx, int ny, int64_t ldg, const cplx* __restrict__ table, T* __restrict__ G) {
+  const int64_t N = (int64_t)nx * ny;
+  const cplx* mon = table + N;
+  const int64_t pad = ldg - N;                     // columns N .. ldg-1 of every row
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N * pad; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / pad, c = t - i * pad;
+    G[i * ldg + N + c] = to_store<T>(c == 0 ? mon[i] : mk(0.0, 0.0));
+  }
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ldg; j += (int64_t)gridDim.x * blockDim.x)
+    G[N * ldg + j] = to_store<T>(j < N ? mon[j] : mk(0.0, 0.0));
+}
+
 __global__ void k_fill_field(int nx, int ny, double dx, double k, double my, cplx* __restrict__ E) {
   const int64_t N = (int64_t)nx * ny;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= N;
@@ -158,10 +207,24 @@ void launch_fill_expand(const gf_geom& g, int dtype, void* G, int64_t ldg, const
   const int64_t N = (int64_t)g.nx * g.ny;
   const double k = 2.0 * M_PI / g.wavelength;
   int blocks = (int)(N + 1 < 152 * 16 ? N + 1 : 152 * 16);
-  if (dtype == GF_C128)
+  if (g.nx <= kFillMaxNx) {
+    const int64_t pairs = (int64_t)g.ny * g.ny;
+    const int fb = (int)(pairs < 152 * 8 ? pairs : 152 * 8);
+    const int eb = grid_for(N + 1, 256);
+    if (dtype == GF_C128) {
+      k_fill_blocks<double2><<<fb, 256, (size_t)g.nx * sizeof(double2), st>>>(g.nx, g.ny, ldg, table,
+                                                                              reinterpret_cast<double2*>(G));
+      k_fill_edges<double2><<<eb, 256, 0, st>>>(g.nx, g.ny, ldg, table, reinterpret_cast<double2*>(G));
+    } else {
+      k_fill_blocks<float2><<<fb, 256, (size_t)g.nx * sizeof(float2), st>>>(g.nx, g.ny, ldg, table,
+                                                                            reinterpret_cast<float2*>(G));
+      k_fill_edges<float2><<<eb, 256, 0, st>>>(g.nx, g.ny, ldg, table, reinterpret_cast<float2*>(G));
+    }
+  } else if (dtype == GF_C128) {
     k_fill_expand<double2><<<blocks, 256, 0, st>>>(g.nx, g.ny, ldg, table, G);
-  else
+  } else {
     k_fill_expand<float2><<<blocks, 256, 0, st>>>(g.nx, g.ny, ldg, table, G);
+  }
   k_fill_field<<<grid_for(N + 1, 256), 256, 0, st>>>(g.nx, g.ny, g.dx, k, g.mon_y, E);
 }
 
