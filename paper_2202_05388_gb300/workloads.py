@@ -22,6 +22,7 @@ import numpy as np
 
 KIND_SINGLE = 0     # one pixel per candidate, id = j
 KIND_BRUSH2 = 1     # 2x2 brush per candidate, id = dir*P + iy*(nx-1) + ix
+KIND_PILLAR = 2     # 3-D: 2x2 lateral block through all nz layers, id as for KIND_BRUSH2
 DIR_FILL = 1        # eps_bg -> eps_mat
 DIR_CLEAR = 2       # eps_mat -> eps_bg
 
@@ -47,6 +48,32 @@ class Geometry:
 
 
 @dataclass(frozen=True)
+class Geometry3D:
+    """3-D slab of nx*ny*nz cubic voxels of side dx (Sec. IV's metalens: a slab in the xy plane,
+    thickness along z); plane wave polarised along x travelling +z; one monitor point.
+    Voxel j = (iz*ny + iy)*nx + ix, centre ((ix+1/2)dx, (iy+1/2)dx, (iz+1/2)dx); the monitor is
+    point N; unknown u = 3*point + component (x, y, z)."""
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    wavelength: float
+    mon_x: float
+    mon_y: float
+    mon_z: float
+    eps_bg: float = 1.0
+    eps_mat: float = 12.0
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def n(self) -> int:
+        return 3 * (self.N + 1)
+
+
+@dataclass(frozen=True)
 class CandidateSpec:
     kind: int = KIND_SINGLE
     dir_mask: int = DIR_FILL
@@ -54,7 +81,7 @@ class CandidateSpec:
     excl_radius: int = 3       # Chebyshev distance between anchors that counts as a conflict
     tie_rel: float = 1e-12     # relative window of the lowest-index tie rule
 
-    def ncand(self, g: Geometry) -> int:
+    def ncand(self, g) -> int:
         if self.kind == KIND_SINGLE:
             return g.N
         return 2 * (g.nx - 1) * (g.ny - 1)
@@ -204,3 +231,26 @@ def random_state(N: int, seed: int, fill: float = 0.3) -> np.ndarray:
     """Seeded random binary design (uint8), for tests that start from a patterned design."""
     rng = np.random.default_rng(seed)
     return (rng.random(N) < fill).astype(np.uint8)
+
+
+def metalens_3d(nx: int = 120, ny: int = 120, nz: int = 4, na: float = 0.7, eps_mat: float = 12.0,
+                dtype: str = "c64") -> Workload:
+    """Sec. IV's metalens: nx x ny x nz voxels of lambda/20 (75 nm at lambda = 1.5 um: a
+    9 um x 9 um x 300 nm silicon slab for 120 x 120 x 4), x-polarised plane wave at normal
+    incidence, focus on the axis past the slab at the distance giving numerical aperture `na`
+    (4.5 um = 3 lambda for NA 0.7), pillar (2x2 x nz) flips in both directions."""
+    dx = 0.05
+    half = nx * dx / 2.0
+    import math
+    f = half / math.tan(math.asin(na))
+    g = Geometry3D(nx, ny, nz, dx, 1.0, half, ny * dx / 2.0, nz * dx + f, eps_mat=eps_mat)
+    return Workload(f"metalens3d_{nx}x{ny}x{nz}_pillar_{dtype}", (g,),
+                    CandidateSpec(KIND_PILLAR, DIR_FILL | DIR_CLEAR, 1), 750, dtype)
+
+
+def small_3d(nx: int, ny: int, nz: int, focus: float = 1.0, eps_mat: float = 12.0, k: int = 1,
+             dtype: str = "c128") -> Workload:
+    """A small 3-D slab of the same family, for parity tests."""
+    dx = 0.05
+    g = Geometry3D(nx, ny, nz, dx, 1.0, nx * dx / 2.0, ny * dx / 2.0, nz * dx + focus, eps_mat=eps_mat)
+    return Workload(f"small3d_{nx}x{ny}x{nz}", (g,), CandidateSpec(KIND_PILLAR, DIR_FILL | DIR_CLEAR, k), 10, dtype)
