@@ -57,6 +57,7 @@ typedef int32_t gf_status;
 
 #define GF_KIND_SINGLE 0   /* candidate id = pixel j */
 #define GF_KIND_BRUSH2 1   /* candidate id = dir*P + iy*(nx-1) + ix, P = (nx-1)(ny-1) */
+#define GF_KIND_PILLAR 2   /* 3-D: 2x2 lateral block through all layers; ids as GF_KIND_BRUSH2 */
 #define GF_DIR_FILL  1     /* eps_bg -> eps_mat allowed */
 #define GF_DIR_CLEAR 2     /* eps_mat -> eps_bg allowed */
 
@@ -245,6 +246,45 @@ gf_status gf_lowrank_count(gf_handle* h, const gf_lowrank* lr, void* ws, size_t 
  * form; O(n^2 K) work. */
 gf_status gf_lowrank_materialize(gf_handle* h, const gf_lowrank* lr, void* G, int64_t ldg, void* ws,
                                  size_t ws_bytes, void* stream);
+
+/* 3-D form (the paper's own setting, Sec. II with 3x3 dyadic blocks; Sec. IV's metalens).
+ * A slab of nx*ny*nz cubic voxels of side dx, voxel j = (iz*ny + iy)*nx + ix with centre
+ * ((ix+1/2)dx, (iy+1/2)dx, (iz+1/2)dx); one monitor point (mon_x, mon_y, mon_z) outside the
+ * slab.  Unknowns u = 3*point + component (x, y, z), the monitor last: n = 3 (N + 1).
+ *   G_ij (3x3 block) = k^2 dV G0(r_i - r_j), G0(R) = (I + grad grad / k^2) e^{ikR} / (4 pi R);
+ *   G_jj = [(2/3)((1 - i k a) e^{ika} - 1) - 1/3] I, a = (3 dV / (4 pi))^(1/3) (principal volume
+ *   over the equal-volume sphere with the depolarisation I/3); the monitor's own block is 0;
+ *   E_inc = x^ e^{ikz} (x-polarised, travelling +z); FOM = |E(r_m)|^2 over the three components.
+ * Candidates: GF_KIND_PILLAR (2x2 lateral blocks through all layers, p = 12 nz unknowns, ids as
+ * for 2-D brushes, both directions per dir_mask).  Restrictions: 1 <= nz <= 8, one wavelength,
+ * complex128 or complex64 G (n x ldg, ldg even >= n); a flip changes all three components.
+ * The steps mirror the 2-D calls: gf3_fill_g0, gf3_eval_candidates, gf3_select_topk,
+ * gf3_apply_update (the update kernels are the 2-D ones on the 3n unknowns). */
+typedef struct gf_geom3d {
+  int32_t nx, ny, nz, pad;
+  double dx;
+  double wavelength;
+  double eps_bg, eps_mat;
+  double mon_x, mon_y, mon_z;
+} gf_geom3d;
+typedef struct gf_problem3d {
+  gf_geom3d geom;
+  void* G;
+  int64_t ldg;
+  void* E;       /* n complex128 */
+} gf_problem3d;
+int64_t gf3_num_unknowns(const gf_geom3d* geom);
+int64_t gf3_num_candidates(const gf_geom3d* geom);
+size_t gf3_workspace_size(const gf_geom3d* geom, int32_t dtype, const gf_cand_spec* spec);
+gf_status gf3_fill_g0(gf_handle* h, const gf_problem3d* prob, int32_t dtype, void* ws, size_t ws_bytes, void* stream);
+gf_status gf3_eval_candidates(gf_handle* h, const gf_problem3d* prob, int32_t dtype, const uint8_t* state,
+                              const gf_cand_spec* spec, double* dfom, void* stream);
+gf_status gf3_select_topk(gf_handle* h, const gf_geom3d* geom, const gf_cand_spec* spec, const double* dfom,
+                          int64_t ncand, int32_t* idx, double* val, int32_t* status, void* ws, size_t ws_bytes,
+                          void* stream);
+gf_status gf3_apply_update(gf_handle* h, const gf_problem3d* prob, int32_t dtype, uint8_t* state,
+                           const gf_cand_spec* spec, const int32_t* idx, int32_t* status, double* fom_out,
+                           int32_t* applied, void* ws, size_t ws_bytes, void* stream);
 
 /* Batches: many independent problems advanced together (the problems of a design study, e.g.
  * sweeps over sizes, wavelengths and focal distances; the paper parallelises one problem's

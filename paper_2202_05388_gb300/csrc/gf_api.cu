@@ -129,17 +129,23 @@ gf_status api_cuda_check(gf_handle* h, const char* where) { return cuda_check(h,
 gf_status api_fail_msg(gf_handle* h, gf_status s, const char* msg) { return fail(h, s, "%s", msg); }
 int api_device(const gf_handle* h) { return h->device; }
 int api_sm_count(const gf_handle* h) { return h->sm_count; }
+int api_update_algo(const gf_handle* h) { return h->update_algo; }
 KernelTimer* api_timer(gf_handle* h) { return &h->timer; }
 gf_status api_check_spec(gf_handle* h, const gf_geom* g, const gf_cand_spec* s) { return check_spec(h, g, s); }
 
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& spec) {
-  WsLayout L;
   const int64_t N = (int64_t)g.nx * g.ny;
-  L.n = N + 1;
   const int per = spec.kind == GF_KIND_SINGLE ? 1 : kMaxPixelsPerCand;
-  L.pmax = per * (spec.k < 1 ? 1 : spec.k);
+  return ws_layout_n(N + 1, 2 * N, per * (spec.k < 1 ? 1 : spec.k), nlam, dtype);
+}
+
+// n unknowns, a fill table of `table_entries` complex values, pmax unknowns per step
+WsLayout ws_layout_n(int64_t n, int64_t table_entries, int pmax, int nlam, int dtype) {
+  WsLayout L;
+  L.n = n;
+  L.pmax = pmax;
   size_t o = 0;
   L.ctl = o; o = up256(o + sizeof(UpdCtl));
   L.V = o; o = up256(o + sizeof(int32_t) * L.pmax);
@@ -168,7 +174,7 @@ WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& sp
   L.total = o;
   // the fill's Toeplitz table reuses the start of the workspace
   L.table = 0;
-  size_t tab = up256(sizeof(cplx) * (size_t)(2 * N));
+  size_t tab = up256(sizeof(cplx) * (size_t)table_entries);
   if (tab > L.total) L.total = tab;
   return L;
 }
@@ -354,6 +360,10 @@ gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, i
   a.pmax = L.pmax;
   a.algo = h->update_algo;
   a.sm_count = h->sm_count;
+  a.nz = 0;
+  a.ncomp = 1;
+  a.mrow = L.n - 1;
+  a.mcount = 1;
   for (int l = 0; l < nlam; ++l) {
     a.lam[l].G = probs[l].G;
     a.lam[l].ldg = probs[l].ldg;

@@ -63,10 +63,12 @@ __host__ __device__ __forceinline__ void band_offset(int b, int& ddx, int& ddy) 
   ddy = ty[b];
 }
 
-// Pixels and contrast changes of candidate c given the current state (same rule as the
-// candidate kernels).  Appends to V/dchi; returns the number appended.
+// Unknowns and contrast changes of candidate c given the current state (same rule as the
+// candidate kernels).  Appends to V/dchi; returns the number appended.  2-D (nz = 0): single
+// pixels and 2x2 brushes, one unknown per pixel.  3-D (nz >= 1, kind GF_KIND_PILLAR): the 2x2
+// lateral block through all nz layers, three unknowns (x, y, z) per flipped voxel, voxel-major.
 __device__ __forceinline__ int cand_pixels(int64_t c, int kind, int dir_mask, int nx, int ny, double chi,
-                           const uint8_t* state, int32_t* V, double* dchi) {
+                                           const uint8_t* state, int32_t* V, double* dchi, int nz = 0) {
   const int64_t N = (int64_t)nx * ny;
   if (kind == GF_KIND_SINGLE) {
     if (c < 0 || c >= N) return 0;
@@ -81,13 +83,29 @@ __device__ __forceinline__ int cand_pixels(int64_t c, int kind, int dir_mask, in
   const int64_t a = c - dir * P;
   if (!(dir_mask & (dir == 0 ? GF_DIR_FILL : GF_DIR_CLEAR))) return 0;
   const int ay = (int)(a / (nx - 1)), ax = (int)(a - (int64_t)ay * (nx - 1));
+  const uint8_t target = dir == 0 ? 0 : 1;
+  const double d = dir == 0 ? chi : -chi;
+  int m = 0;
+  if (kind == GF_KIND_PILLAR) {
+    for (int iz = 0; iz < nz; ++iz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const int64_t j = ((int64_t)iz * ny + ay + dy) * nx + ax + dx;
+          if (state[j] != target) continue;
+          for (int comp = 0; comp < 3; ++comp) {
+            V[m] = (int32_t)(3 * j + comp);
+            dchi[m] = d;
+            ++m;
+          }
+        }
+    return m;
+  }
   const int64_t j0 = (int64_t)ay * nx + ax;
   const int64_t q[4] = {j0, j0 + 1, j0 + nx, j0 + nx + 1};
-  int m = 0;
   for (int u = 0; u < 4; ++u) {
-    if (state[q[u]] == (dir == 0 ? 0 : 1)) {
+    if (state[q[u]] == target) {
       V[m] = (int32_t)q[u];
-      dchi[m] = dir == 0 ? chi : -chi;
+      dchi[m] = d;
       ++m;
     }
   }
@@ -135,6 +153,7 @@ C64Layout c64_layout(int64_t n, int pmax);
 constexpr int kC64MaxP = 128;        // the complex64 tensor-core path takes p <= 128
 
 WsLayout ws_layout(const gf_geom& g, int nlam, int dtype, const gf_cand_spec& spec);
+WsLayout ws_layout_n(int64_t n, int64_t table_entries, int pmax, int nlam, int dtype);
 
 // host helpers of gf_api.cu for entry points defined in other translation units
 gf_status api_check_problem(gf_handle* h, const gf_problem* p, int dtype);
@@ -143,6 +162,7 @@ gf_status api_cuda_check(gf_handle* h, const char* where);
 gf_status api_fail_msg(gf_handle* h, gf_status s, const char* msg);
 int api_device(const gf_handle* h);
 int api_sm_count(const gf_handle* h);
+int api_update_algo(const gf_handle* h);
 gf_status api_check_spec(gf_handle* h, const gf_geom* g, const gf_cand_spec* s);
 
 // ----------------------------------------------------------------------------- kernels
@@ -191,6 +211,10 @@ struct UpdArgs {
   int pmax;
   int algo;            // GF_UPDATE_TC or GF_UPDATE_DFMA
   int sm_count;
+  int nz;              // 0: 2-D scalar problem; >= 1: 3-D dyadic problem with nz layers
+  int ncomp;           // unknowns per point (1 or 3)
+  int64_t mrow;        // first monitor unknown
+  int mcount;          // monitor unknowns (1 or 3); FOM = sum of their |E|^2
   UpdLam lam[kMaxLam];
 };
 // CUDA-event timer of the G-update kernel launches (armed by gf_profile_begin).  Each record
@@ -262,6 +286,10 @@ __device__ __forceinline__ void batch_upd_args(const BatchItem& it, int dtype, U
   a.pmax = it.L.pmax;
   a.algo = GF_UPDATE_TC;
   a.sm_count = 0;
+  a.nz = 0;
+  a.ncomp = 1;
+  a.mrow = it.L.n - 1;
+  a.mcount = 1;
   a.lam[0].G = it.G;
   a.lam[0].ldg = it.ldg;
   a.lam[0].E = it.E;

@@ -166,7 +166,7 @@ __device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayou
       for (int c = 0; c < a.k; ++c) {
         int32_t id = idx[c];
         if (id < 0) break;
-        int m = cand_pixels(id, a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V + nv, dchi + nv);
+        int m = cand_pixels(id, a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V + nv, dchi + nv, a.u.nz);
         if (m == 0) continue;
         nv += m;
         ++nc;
@@ -310,11 +310,16 @@ __device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayou
         __syncthreads();
       }
       if (tid == 0) {
-        cplx EN = U.E[N];
-        cplx dE = mk(0.0, 0.0);
-        for (int u = 0; u < p; ++u) dE = dE + dchi[u] * (ldG(U.G, a.u.dtype, U.ldg, N, V[u]) * y[u]);
-        cplx Em = EN + dE;
-        s_red[0] = abs2(Em) - abs2(EN);
+        double df = 0.0;
+        for (int mc = 0; mc < a.u.mcount; ++mc) {          // the monitor's unknowns (Eq. 1)
+          const int64_t m = a.u.mrow + mc;
+          cplx EN = U.E[m];
+          cplx dE = mk(0.0, 0.0);
+          for (int u = 0; u < p; ++u) dE = dE + dchi[u] * (ldG(U.G, a.u.dtype, U.ldg, m, V[u]) * y[u]);
+          cplx Em = EN + dE;
+          df += abs2(Em) - abs2(EN);
+        }
+        s_red[0] = df;
         // store D y for the field update
         for (int u = 0; u < p; ++u) y[u] = dchi[u] * y[u];
       }
@@ -336,7 +341,7 @@ __device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayou
       // the joint set does not improve the FOM: apply the best candidate alone
       __syncthreads();
       if (tid == 0) {
-        int m = cand_pixels(idx[0], a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V, dchi);
+        int m = cand_pixels(idx[0], a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V, dchi, a.u.nz);
         s_nv = m;
         s_ncand = 1;
       }
@@ -648,24 +653,32 @@ __device__ __forceinline__ void finish_body(const UpdArgs& a, const WsLayout& L,
   const bool skip = ctl->skip != 0;
   const int p = skip ? 0 : ctl->nv;
   const int32_t* V = reinterpret_cast<const int32_t*>(ws + L.V);
+  (void)N;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    // the first monitor unknown's thread also updates the others, so that it can sum the FOM
+    if (i > a.mrow && i < a.mrow + a.mcount) continue;
+    const int reps = i == a.mrow ? a.mcount : 1;
     double f = 0.0;
-    for (int l = 0; l < a.nlam; ++l) {
-      const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + l * L.panel_s);
-      const cplx* yd = reinterpret_cast<const cplx*>(ws + L.yd + l * L.yd_s);
-      cplx e = a.lam[l].E[i];
-      for (int u = 0; u < p; ++u) e = cfma(C0[i * L.pmax + u], yd[u], e);
-      if (p > 0) a.lam[l].E[i] = e;
-      f += abs2(e);
+    for (int q = 0; q < reps; ++q) {
+      const int64_t ii = i + q;
+      for (int l = 0; l < a.nlam; ++l) {
+        const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + l * L.panel_s);
+        const cplx* yd = reinterpret_cast<const cplx*>(ws + L.yd + l * L.yd_s);
+        cplx e = a.lam[l].E[ii];
+        for (int u = 0; u < p; ++u) e = cfma(C0[ii * L.pmax + u], yd[u], e);
+        if (p > 0) a.lam[l].E[ii] = e;
+        f += abs2(e);
+      }
     }
-    if (i == N) {
+    if (i == a.mrow) {
       *fom_out = f;
       if (applied) *applied = skip ? 0 : ctl->ncand;
     }
   }
-  if (blockIdx.x == 0) {
-    for (int t = threadIdx.x; t < p; t += blockDim.x) state[V[t]] ^= 1;
+  if (blockIdx.x == 0) {   // one flip per point (the unknowns of a point are consecutive in V)
+    for (int t = threadIdx.x; t < p; t += blockDim.x)
+      if (V[t] % a.ncomp == 0) state[V[t] / a.ncomp] ^= 1;
   }
 }
 

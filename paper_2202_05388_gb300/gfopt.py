@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libgfopt.so")
 
 GF_OK, GF_EINVAL, GF_ECUDA, GF_ESINGULAR, GF_ENOIMPROVE, GF_ETIMEOUT, GF_ENOMEM = range(7)
 GF_C128, GF_C64 = 0, 1
-GF_KIND_SINGLE, GF_KIND_BRUSH2 = 0, 1
+GF_KIND_SINGLE, GF_KIND_BRUSH2, GF_KIND_PILLAR = 0, 1, 2
 GF_DIR_FILL, GF_DIR_CLEAR = 1, 2
 GF_NBANDS = 9
 GF_UPDATE_TC, GF_UPDATE_DFMA = 0, 1
@@ -34,7 +34,8 @@ EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_v
            "gf_fill_g0_static", "gf_batch_table_size", "gf_batch_create", "gf_batch_step",
            "gf_batch_set_schedule", "gf_batch_destroy", "gf_select_egreedy", "gf_lowrank_workspace_size",
            "gf_lowrank_init", "gf_lowrank_eval", "gf_lowrank_update", "gf_lowrank_count",
-           "gf_lowrank_materialize"]
+           "gf_lowrank_materialize", "gf3_num_unknowns", "gf3_num_candidates", "gf3_workspace_size",
+           "gf3_fill_g0", "gf3_eval_candidates", "gf3_select_topk", "gf3_apply_update"]
 
 
 class GfError(RuntimeError):
@@ -57,6 +58,16 @@ class gf_problem(C.Structure):
 class gf_cand_spec(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dir_mask", C.c_int32), ("k", C.c_int32),
                 ("excl_radius", C.c_int32), ("tie_rel", C.c_double)]
+
+
+class gf_geom3d(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("pad", C.c_int32), ("dx", C.c_double),
+                ("wavelength", C.c_double), ("eps_bg", C.c_double), ("eps_mat", C.c_double),
+                ("mon_x", C.c_double), ("mon_y", C.c_double), ("mon_z", C.c_double)]
+
+
+class gf_problem3d(C.Structure):
+    _fields_ = [("geom", gf_geom3d), ("G", C.c_void_p), ("ldg", C.c_int64), ("E", C.c_void_p)]
 
 
 class gf_lowrank(C.Structure):
@@ -114,6 +125,15 @@ def load(path: str = LIB_PATH):
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "gf_select_egreedy": (C.c_int32, [P, C.POINTER(gf_geom), C.POINTER(gf_cand_spec), P, C.c_int64,
                                               C.c_double, P, P, P, P, P, C.c_size_t, P]),
+            "gf3_num_unknowns": (C.c_int64, [C.POINTER(gf_geom3d)]),
+            "gf3_num_candidates": (C.c_int64, [C.POINTER(gf_geom3d)]),
+            "gf3_workspace_size": (C.c_size_t, [C.POINTER(gf_geom3d), C.c_int32, C.POINTER(gf_cand_spec)]),
+            "gf3_fill_g0": (C.c_int32, [P, C.POINTER(gf_problem3d), C.c_int32, P, C.c_size_t, P]),
+            "gf3_eval_candidates": (C.c_int32, [P, C.POINTER(gf_problem3d), C.c_int32, P, C.POINTER(gf_cand_spec), P, P]),
+            "gf3_select_topk": (C.c_int32, [P, C.POINTER(gf_geom3d), C.POINTER(gf_cand_spec), P, C.c_int64, P, P, P, P,
+                                            C.c_size_t, P]),
+            "gf3_apply_update": (C.c_int32, [P, C.POINTER(gf_problem3d), C.c_int32, P, C.POINTER(gf_cand_spec), P, P, P,
+                                             P, P, C.c_size_t, P]),
             "gf_lowrank_workspace_size": (C.c_size_t, [C.POINTER(gf_geom), C.c_int32]),
             "gf_lowrank_init": (C.c_int32, [P, C.POINTER(gf_lowrank), P, C.c_size_t, P]),
             "gf_lowrank_eval": (C.c_int32, [P, C.POINTER(gf_lowrank), P, C.POINTER(gf_cand_spec), P, P]),
@@ -160,6 +180,15 @@ def geom_struct(g) -> gf_geom:
 
 def spec_struct(s) -> gf_cand_spec:
     return gf_cand_spec(int(s.kind), int(s.dir_mask), int(s.k), int(s.excl_radius), float(s.tie_rel))
+
+
+def geom3d_struct(g) -> gf_geom3d:
+    return gf_geom3d(int(g.nx), int(g.ny), int(g.nz), 0, float(g.dx), float(g.wavelength), float(g.eps_bg),
+                     float(g.eps_mat), float(g.mon_x), float(g.mon_y), float(g.mon_z))
+
+
+def problem3d_struct(g, G, ldg, E) -> gf_problem3d:
+    return gf_problem3d(geom3d_struct(g), _ptr(G), int(ldg), _ptr(E))
 
 
 def problem_struct(g, G, ldg, E, bands) -> gf_problem:
@@ -256,6 +285,39 @@ class Handle:
                                         int(max_iter), float(tol), res, its, _ptr(ws), int(ws_bytes),
                                         _stream(stream)))
         return list(res), list(its)[:ns]
+
+    # ---- 3-D form
+    def gf3_num_unknowns(self, geom) -> int:
+        g = geom3d_struct(geom)
+        return int(self.lib.gf3_num_unknowns(C.byref(g)))
+
+    def gf3_num_candidates(self, geom) -> int:
+        g = geom3d_struct(geom)
+        return int(self.lib.gf3_num_candidates(C.byref(g)))
+
+    def gf3_workspace_size(self, geom, dtype, spec) -> int:
+        g, s = geom3d_struct(geom), spec_struct(spec)
+        return int(self.lib.gf3_workspace_size(C.byref(g), int(dtype), C.byref(s)))
+
+    def gf3_fill_g0(self, prob: gf_problem3d, dtype, ws, ws_bytes, stream=None):
+        self._check(self.lib.gf3_fill_g0(self.h, C.byref(prob), int(dtype), _ptr(ws), int(ws_bytes), _stream(stream)))
+
+    def gf3_eval_candidates(self, prob: gf_problem3d, dtype, state, spec, dfom, stream=None):
+        s = spec_struct(spec)
+        self._check(self.lib.gf3_eval_candidates(self.h, C.byref(prob), int(dtype), _ptr(state), C.byref(s), _ptr(dfom),
+                                                 _stream(stream)))
+
+    def gf3_select_topk(self, geom, spec, dfom, ncand, idx, val, status, ws, ws_bytes, stream=None):
+        g, s = geom3d_struct(geom), spec_struct(spec)
+        self._check(self.lib.gf3_select_topk(self.h, C.byref(g), C.byref(s), _ptr(dfom), int(ncand), _ptr(idx),
+                                             _ptr(val), _ptr(status), _ptr(ws), int(ws_bytes), _stream(stream)))
+
+    def gf3_apply_update(self, prob: gf_problem3d, dtype, state, spec, idx, status, fom_out, ws, ws_bytes,
+                         stream=None, applied=None):
+        s = spec_struct(spec)
+        self._check(self.lib.gf3_apply_update(self.h, C.byref(prob), int(dtype), _ptr(state), C.byref(s), _ptr(idx),
+                                              _ptr(status), _ptr(fom_out), _ptr(applied), _ptr(ws), int(ws_bytes),
+                                              _stream(stream)))
 
     # ---- deferred (low-rank) form
     def gf_lowrank_workspace_size(self, geom, max_cols: int) -> int:

@@ -156,3 +156,68 @@ class GreedyOptimizer:
 
     def state_host(self) -> np.ndarray:
         return self.state.cpu().numpy()
+
+
+class GreedyOptimizer3D:
+    """One 3-D problem (dyadic G over the 3 (N + 1) unknowns, pillar candidates) driven
+    through the gf3_* calls; the same stages and read-back as GreedyOptimizer."""
+
+    def __init__(self, geom, spec: CandidateSpec, dtype: str = "c64", device: int = 0,
+                 handle: Optional[B.Handle] = None):
+        if not torch.cuda.is_available():
+            raise B.GfError(B.GF_ECUDA, "GreedyOptimizer3D needs a CUDA device (no CPU fallback)")
+        self.geom = geom
+        self.spec = spec
+        self.dtype = B.GF_C128 if dtype == "c128" else B.GF_C64
+        self.device = torch.device("cuda", device)
+        self.h = handle or B.Handle(device)
+        self.N = geom.nx * geom.ny * geom.nz
+        self.n = self.h.gf3_num_unknowns(geom)
+        self.ldg = self.n + (self.n & 1)
+        tdt = torch.complex128 if self.dtype == B.GF_C128 else torch.complex64
+        dev = self.device
+        self.G = torch.empty((self.n, self.ldg), dtype=tdt, device=dev)
+        self.E = torch.empty(self.n, dtype=torch.complex128, device=dev)
+        self.state = torch.zeros(self.N, dtype=torch.uint8, device=dev)
+        self.ncand = self.h.gf3_num_candidates(geom)
+        self.dfom = torch.empty(self.ncand, dtype=torch.float64, device=dev)
+        k = max(1, spec.k)
+        self.idx = torch.full((k,), -1, dtype=torch.int32, device=dev)
+        self.val = torch.empty(k, dtype=torch.float64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.fom = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.applied = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.ws_bytes = self.h.gf3_workspace_size(geom, self.dtype, spec)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.prob = B.problem3d_struct(geom, self.G, self.ldg, self.E)
+
+    def _st(self):
+        return torch.cuda.current_stream(self.device)
+
+    def fill(self):
+        self.h.gf3_fill_g0(self.prob, self.dtype, self.ws, self.ws_bytes, self._st())
+        self.state.zero_()
+        self.fom.copy_((self.E[-3:].abs() ** 2).sum().reshape(1))
+
+    def evaluate(self):
+        self.h.gf3_eval_candidates(self.prob, self.dtype, self.state, self.spec, self.dfom, self._st())
+
+    def select(self):
+        self.h.gf3_select_topk(self.geom, self.spec, self.dfom, self.ncand, self.idx, self.val, self.status, self.ws,
+                               self.ws_bytes, self._st())
+
+    def update(self):
+        self.h.gf3_apply_update(self.prob, self.dtype, self.state, self.spec, self.idx, self.status, self.fom,
+                                self.ws, self.ws_bytes, self._st(), applied=self.applied)
+
+    def step(self):
+        self.evaluate()
+        self.select()
+        self.update()
+
+    def read_step(self) -> StepResult:
+        k = max(1, self.spec.k)
+        packed = torch.cat([self.idx[:k].to(torch.float64), self.val[:k],
+                            self.status.to(torch.float64), self.fom]).cpu().numpy()
+        ids = [int(x) for x in packed[:k] if x >= 0]
+        return StepResult(ids, [float(x) for x in packed[k:k + len(ids)]], int(packed[2 * k]), float(packed[2 * k + 1]))

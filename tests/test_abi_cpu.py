@@ -22,7 +22,7 @@ def lib():
 def _declared():
     txt = open(os.path.join(ROOT, "include", "gfopt.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(gf_[a-z0-9_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(gf3?_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_every_declared_symbol_is_exported(lib):
