@@ -837,7 +837,8 @@ def run_metalens3d_full(args):
 
     torch.cuda.set_device(0)
     BLD.build()
-    wl = W.metalens_3d()
+    wl = (W.metalens_3d_aligned(fill_only="fill" in args.workload) if "aligned" in args.workload
+          else W.metalens_3d())
     g = wl.geoms[0]
     opt = GreedyOptimizer3D(g, wl.spec, dtype="c64")
     accepted = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -897,7 +898,7 @@ def main():
         return run_deferred(args)
     if args.workload == "metalens3d":
         return run_metalens3d(args)
-    if args.workload == "metalens3d_run":
+    if args.workload in ("metalens3d_run", "metalens3d_aligned_run", "metalens3d_aligned_fill_run"):
         return run_metalens3d_full(args)
     if args.workload in ("deferred_192_run", "brush_192_run"):
         return run_full(args, deferred=args.workload.startswith("deferred"))

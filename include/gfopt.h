@@ -88,13 +88,17 @@ typedef struct gf_problem {
 
 /* Candidate family (Sec. II-A "shapes and sizes for region V"; Sec. IV 2x2 brushes).
  * k > 1 accepts up to k non-conflicting candidates per step (conflict: Chebyshev distance of
- * anchors <= excl_radius).  Ties: lowest id among dFOM >= max - tie_rel*|max|. */
+ * anchors <= excl_radius).  Ties: lowest id among dFOM >= max - tie_rel*|max|.
+ * aligned != 0 (brushes and pillars): only anchors with even ix and iy are candidates -- the
+ * aligned, non-overlapping 2x2 partitions of Sec. IV; the others evaluate to -inf. */
 typedef struct gf_cand_spec {
   int32_t kind;
   int32_t dir_mask;
   int32_t k;
   int32_t excl_radius;
   double tie_rel;
+  int32_t aligned;
+  int32_t pad;
 } gf_cand_spec;
 
 typedef struct gf_handle gf_handle;

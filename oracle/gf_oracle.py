@@ -133,6 +133,8 @@ def candidate(g: Geometry, spec: CandidateSpec, state: np.ndarray, cid: int
     if not spec.dir_mask & (DIR_FILL if direction == 0 else DIR_CLEAR):
         return None
     ax, ay = a % (g.nx - 1), a // (g.nx - 1)
+    if getattr(spec, "aligned", False) and (ax % 2 or ay % 2):
+        return None                                  # Sec. IV: aligned 2x2 partitions only
     j0 = ay * g.nx + ax
     brush = [j0, j0 + 1, j0 + g.nx, j0 + g.nx + 1]
     want_from = 0 if direction == 0 else 1          # only pixels that actually change

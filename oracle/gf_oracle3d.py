@@ -111,6 +111,8 @@ def candidate(g: Geometry3D, spec: CandidateSpec, state: np.ndarray, cid: int) -
     if not (spec.dir_mask & (DIR_FILL if d == 0 else DIR_CLEAR)):
         return np.zeros(0, dtype=np.int64), np.zeros(0)
     ay, ax = divmod(a, g.nx - 1)
+    if getattr(spec, "aligned", False) and (ax % 2 or ay % 2):
+        return np.zeros(0, dtype=np.int64), np.zeros(0)      # Sec. IV: aligned partitions only
     target = 0 if d == 0 else 1
     vox = []
     for iz in range(g.nz):

@@ -211,7 +211,8 @@ __device__ __forceinline__ cplx block_sum(cplx v, cplx* sc) {
 }
 
 __global__ void __launch_bounds__(kEv3Threads) k_eval_pillar(Ev3Args a, const uint8_t* __restrict__ state,
-                                                             int dir_mask, int64_t ncand, double* __restrict__ dfom) {
+                                                             int dir_mask, int aligned, int64_t ncand,
+                                                             double* __restrict__ dfom) {
   extern __shared__ __align__(16) unsigned char ev3_smem[];
   cplx* A = reinterpret_cast<cplx*>(ev3_smem);                   // p x p, row-major
   __shared__ cplx y[kEv3MaxP];
@@ -226,7 +227,10 @@ __global__ void __launch_bounds__(kEv3Threads) k_eval_pillar(Ev3Args a, const ui
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int64_t c = blockIdx.x; c < ncand; c += gridDim.x) {
     if (tid == 0) {
-      s_p = cand_pixels(c, GF_KIND_PILLAR, dir_mask, g.nx, g.ny, g.chi, state, V, D, g.nz);
+      const int64_t an = c % ((int64_t)(g.nx - 1) * (g.ny - 1));
+      const int ay = (int)(an / (g.nx - 1)), ax = (int)(an - (int64_t)ay * (g.nx - 1));
+      s_p = (aligned && ((ax | ay) & 1)) ? 0
+                                         : cand_pixels(c, GF_KIND_PILLAR, dir_mask, g.nx, g.ny, g.chi, state, V, D, g.nz);
       s_bad = 0;
     }
     __syncthreads();
@@ -432,7 +436,8 @@ gf_status gf3_eval_candidates(gf_handle* h, const gf_problem3d* prob, int32_t dt
   }
   const int64_t ncand = gf3_num_candidates(&prob->geom);
   const int grid = (int)(ncand < (int64_t)gf::api_sm_count(h) * 8 ? ncand : (int64_t)gf::api_sm_count(h) * 8);
-  gf::k_eval_pillar<<<grid, gf::kEv3Threads, smem, (cudaStream_t)stream>>>(a, state, spec->dir_mask, ncand, dfom);
+  gf::k_eval_pillar<<<grid, gf::kEv3Threads, smem, (cudaStream_t)stream>>>(a, state, spec->dir_mask, spec->aligned,
+                                                                           ncand, dfom);
   return gf::api_cuda_check(h, "gf3_eval_candidates launch");
 }
 

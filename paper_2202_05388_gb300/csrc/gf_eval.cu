@@ -10,6 +10,8 @@
 
 namespace gf {
 
+constexpr int kEvalAligned = 4;    // dir_mask bit set by the launchers: only even anchors
+
 // Solve A y = b for a 4x4 complex system by Gaussian elimination with partial pivoting.
 // Rows u with active[u] == false are identity rows with b[u] = 0, which reproduces the
 // elimination of the reduced system over the active pixels (same pivots, same arithmetic on
@@ -119,7 +121,8 @@ __device__ __forceinline__ void eval_brush_body(const EvalArgs& a, const uint8_t
       bool any = false;
 #pragma unroll
       for (int u = 0; u < 4; ++u) any |= (s[u] == (dir == 0 ? 0 : 1));
-      valid[dir] = any && (dir_mask & (dir == 0 ? GF_DIR_FILL : GF_DIR_CLEAR));
+      valid[dir] = any && (dir_mask & (dir == 0 ? GF_DIR_FILL : GF_DIR_CLEAR)) &&
+                   !((dir_mask & kEvalAligned) && ((ax | ay) & 1));
     }
     for (int l = 0; l < a.nlam; ++l) {
       const EvalLam& L = a.lam[l];
@@ -219,7 +222,7 @@ void launch_eval_batch(const BatchItem* items, int nprob, int dtype, const gf_ca
   if (spec.kind == GF_KIND_SINGLE)
     k_eval_single_batch<<<grid, threads, 0, st>>>(items, dtype, spec.dir_mask);
   else
-    k_eval_brush_batch<<<grid, threads, 0, st>>>(items, dtype, spec.dir_mask);
+    k_eval_brush_batch<<<grid, threads, 0, st>>>(items, dtype, spec.dir_mask | (spec.aligned ? kEvalAligned : 0));
 }
 
 void launch_eval(const EvalArgs& a, const uint8_t* state, const gf_cand_spec& spec, double* dfom,
@@ -231,7 +234,8 @@ void launch_eval(const EvalArgs& a, const uint8_t* state, const gf_cand_spec& sp
   } else {
     const int64_t P = (int64_t)(a.nx - 1) * (a.ny - 1);
     int64_t b = (P + 127) / 128;
-    k_eval_brush<<<(int)(b < 9728 ? b : 9728), 128, 0, st>>>(a, state, spec.dir_mask, dfom);
+    k_eval_brush<<<(int)(b < 9728 ? b : 9728), 128, 0, st>>>(a, state, spec.dir_mask | (spec.aligned ? kEvalAligned : 0),
+                                                             dfom);
   }
 }
 

@@ -57,7 +57,7 @@ class gf_problem(C.Structure):
 
 class gf_cand_spec(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dir_mask", C.c_int32), ("k", C.c_int32),
-                ("excl_radius", C.c_int32), ("tie_rel", C.c_double)]
+                ("excl_radius", C.c_int32), ("tie_rel", C.c_double), ("aligned", C.c_int32), ("pad", C.c_int32)]
 
 
 class gf_geom3d(C.Structure):
@@ -179,7 +179,8 @@ def geom_struct(g) -> gf_geom:
 
 
 def spec_struct(s) -> gf_cand_spec:
-    return gf_cand_spec(int(s.kind), int(s.dir_mask), int(s.k), int(s.excl_radius), float(s.tie_rel))
+    return gf_cand_spec(int(s.kind), int(s.dir_mask), int(s.k), int(s.excl_radius), float(s.tie_rel),
+                        int(getattr(s, "aligned", False)), 0)
 
 
 def geom3d_struct(g) -> gf_geom3d:

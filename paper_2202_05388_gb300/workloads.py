@@ -80,6 +80,7 @@ class CandidateSpec:
     k: int = 1                 # flips accepted per step (top-k with exclusion when k > 1)
     excl_radius: int = 3       # Chebyshev distance between anchors that counts as a conflict
     tie_rel: float = 1e-12     # relative window of the lowest-index tie rule
+    aligned: bool = False      # brushes / pillars: only even anchors (Sec. IV's aligned 2x2 partitions)
 
     def ncand(self, g) -> int:
         if self.kind == KIND_SINGLE:
@@ -246,6 +247,16 @@ def metalens_3d(nx: int = 120, ny: int = 120, nz: int = 4, na: float = 0.7, eps_
     g = Geometry3D(nx, ny, nz, dx, 1.0, half, ny * dx / 2.0, nz * dx + f, eps_mat=eps_mat)
     return Workload(f"metalens3d_{nx}x{ny}x{nz}_pillar_{dtype}", (g,),
                     CandidateSpec(KIND_PILLAR, DIR_FILL | DIR_CLEAR, 1), 750, dtype)
+
+
+def metalens_3d_aligned(fill_only: bool = False) -> Workload:
+    """metalens_3d with the paper's candidate set: the 60 x 60 aligned 2x2 partitions (and, with
+    fill_only, blocks of silicon added to the vacuum slab only)."""
+    w = metalens_3d()
+    tag = "aligned_fill_pillar" if fill_only else "aligned_pillar"
+    return Workload(w.name.replace("pillar", tag), w.geoms,
+                    CandidateSpec(KIND_PILLAR, DIR_FILL if fill_only else DIR_FILL | DIR_CLEAR, 1, aligned=True),
+                    w.steps, w.dtype)
 
 
 def small_3d(nx: int, ny: int, nz: int, focus: float = 1.0, eps_mat: float = 12.0, k: int = 1,

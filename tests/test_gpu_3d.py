@@ -102,3 +102,27 @@ def test_3d_validation():
                               W.CandidateSpec(W.KIND_BRUSH2, 3, 1), torch.empty(12, dtype=torch.float64, device="cuda"))
     with pytest.raises(B.GfError, match="ldg"):
         h.gf3_fill_g0(B.problem3d_struct(g, G, n - 1, E), B.GF_C128, ws, ws.numel())
+
+
+def test_aligned_pillars_match_oracle():
+    wl = W.small_3d(6, 5, 2)
+    g = wl.geoms[0]
+    spec = W.CandidateSpec(W.KIND_PILLAR, 3, 1, aligned=True)
+    opt = GreedyOptimizer3D(g, spec, dtype="c128")
+    opt.fill()
+    orc = O3.OracleProblem3D(g, spec)
+    for t in range(3):
+        opt.evaluate()
+        d_orc = orc.evaluate()
+        d_gpu = opt.dfom.cpu().numpy()
+        fin = np.isfinite(d_orc)
+        assert np.array_equal(fin, np.isfinite(d_gpu))
+        assert np.max(np.abs(d_gpu[fin] - d_orc[fin])) <= TOL * max(1.0, np.max(np.abs(d_orc[fin])))
+        ids = orc.choose(d_orc)
+        if not ids:
+            break
+        opt.select()
+        orc.accept(ids)
+        opt.update()
+        torch.cuda.synchronize()
+        assert np.array_equal(opt.state.cpu().numpy(), orc.state)

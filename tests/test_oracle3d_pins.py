@@ -154,3 +154,13 @@ def test_pins_catch_a_dropped_rr_term(monkeypatch):
     with pytest.raises(AssertionError):
         test_dyadic_matches_mpmath_hessian_of_the_scalar_green_function()
     monkeypatch.setattr(O3, "dyadic", orig)
+
+
+def test_aligned_candidates_are_the_even_partitions():
+    g = _geom(5, 5, 2)
+    spec = W.CandidateSpec(W.KIND_PILLAR, 3, 1, aligned=True)
+    state = np.zeros(g.N, dtype=np.uint8)
+    valid = [c for c in range(O3.num_candidates(g, spec)) if O3.candidate(g, spec, state, c)[0].size]
+    P = (g.nx - 1) * (g.ny - 1)
+    want = [c for c in range(P) if (c % (g.nx - 1)) % 2 == 0 and (c // (g.nx - 1)) % 2 == 0]   # fill only (vacuum)
+    assert valid == want
