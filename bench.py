@@ -751,7 +751,7 @@ def run_metalens3d(args):
 
     torch.cuda.set_device(0)
     BLD.build()
-    wl = W.metalens_3d()
+    wl = W.metalens_3d(nx=32, ny=32) if args.workload == "metalens3d_32" else W.metalens_3d()
     g = wl.geoms[0]
     opt = GreedyOptimizer3D(g, wl.spec, dtype="c64")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -896,7 +896,7 @@ def main():
         return run_egreedy(args)
     if args.workload == "deferred_192":
         return run_deferred(args)
-    if args.workload == "metalens3d":
+    if args.workload in ("metalens3d", "metalens3d_32"):
         return run_metalens3d(args)
     if args.workload in ("metalens3d_run", "metalens3d_aligned_run", "metalens3d_aligned_fill_run"):
         return run_metalens3d_full(args)
