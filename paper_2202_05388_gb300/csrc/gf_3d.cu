@@ -67,21 +67,63 @@ __device__ __forceinline__ cplx self_block(const Geo3& g) {
 
 // table over lattice offsets (|dx|, |dy|, |dz|): entry 2 t = fA, 2 t + 1 = fB / dx^2-scaled so that
 // the block is fA I + fB' d d^T with integer offsets d
-__global__ void k_fill3_table(Geo3 g, cplx* __restrict__ table) {
+__global__ void k_fill3_table(Geo3 g, cplx* __restrict__ table, float4* __restrict__ table32) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.N; t += (int64_t)gridDim.x * blockDim.x) {
     const int dz = (int)(t / ((int64_t)g.nx * g.ny));
     const int64_t r = t - (int64_t)dz * g.nx * g.ny;
     const int dy = (int)(r / g.nx), dxi = (int)(r - (int64_t)dy * g.nx);
-    if (t == 0) {
-      table[0] = self_block(g);
-      table[1] = mk(0.0, 0.0);
-      continue;
-    }
-    const double d2 = (double)dxi * dxi + (double)dy * dy + (double)dz * dz;
     cplx fA, fB;
-    dyadic_parts(g, g.dx * sqrt(d2), fA, fB);
+    if (t == 0) {
+      fA = self_block(g);
+      fB = mk(0.0, 0.0);
+    } else {
+      const double d2 = (double)dxi * dxi + (double)dy * dy + (double)dz * dz;
+      dyadic_parts(g, g.dx * sqrt(d2), fA, fB);
+      fB = (g.dx * g.dx) * fB;                                      // times integer d_a d_b
+    }
     table[2 * t] = fA;
-    table[2 * t + 1] = (g.dx * g.dx) * fB;                          // times integer d_a d_b
+    table[2 * t + 1] = fB;
+    table32[t] = make_float4((float)fA.re, (float)fA.im, (float)fB.re, (float)fB.im);
+  }
+}
+
+// complex64 storage: the same assembly in FP32 from the FP32 copy of the table (the stored
+// value is FP32 anyway; the FP64 form of this loop is bound by the FP64 pipe)
+__global__ void __launch_bounds__(256) k_fill3_expand_f32(Geo3 g, int64_t ldg, const float4* __restrict__ table32,
+                                                          float2* __restrict__ G) {
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+  for (int64_t u = blockIdx.x; u < 3 * g.N; u += gridDim.x) {
+    const int64_t i = u / 3;
+    const int a = (int)(u - 3 * i);
+    const int iz = (int)(i / nxy);
+    const int64_t ri = i - iz * nxy;
+    const int iy = (int)(ri / g.nx), ix = (int)(ri - (int64_t)iy * g.nx);
+    float2* row = G + u * ldg;
+    int64_t j = threadIdx.x;
+    int jz = (int)(j / nxy);
+    int64_t rj = j - jz * nxy;
+    int jy = (int)(rj / g.nx), jx = (int)(rj - (int64_t)jy * g.nx);
+    for (; j < g.N; j += blockDim.x) {
+      const int d[3] = {ix - jx, iy - jy, iz - jz};
+      const int ax = d[0] < 0 ? -d[0] : d[0], ay = d[1] < 0 ? -d[1] : d[1], az = d[2] < 0 ? -d[2] : d[2];
+      const float4 tv = table32[((int64_t)az * g.ny + ay) * g.nx + ax];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float w = (float)(d[a] * d[b]);
+        float2 v = make_float2(tv.z * w, tv.w * w);
+        if (a == b) {
+          v.x += tv.x;
+          v.y += tv.y;
+        }
+        row[3 * j + b] = v;
+      }
+      jx += blockDim.x;
+      while (jx >= g.nx) {
+        jx -= g.nx;
+        if (++jy >= g.ny) { jy = 0; ++jz; }
+      }
+    }
+    for (int64_t c = g.n + threadIdx.x; c < ldg; c += blockDim.x) row[c] = make_float2(0.f, 0.f);
   }
 }
 
@@ -358,7 +400,7 @@ static gf_status check3_problem(gf_handle* h, const gf_problem3d* p, int dtype) 
 
 static WsLayout ws3(const gf_geom3d& g, int dtype, const gf_cand_spec& spec) {
   const int64_t N = (int64_t)g.nx * g.ny * g.nz;
-  return ws_layout_n(3 * (N + 1), 2 * N, 12 * g.nz * (spec.k < 1 ? 1 : spec.k), 1, dtype);
+  return ws_layout_n(3 * (N + 1), 3 * N, 12 * g.nz * (spec.k < 1 ? 1 : spec.k), 1, dtype);
 }
 
 }  // namespace gf
@@ -387,19 +429,20 @@ gf_status gf3_fill_g0(gf_handle* h, const gf_problem3d* prob, int32_t dtype, voi
   if (s) return s;
   const gf::Geo3 g = gf::geo3(prob->geom);
   if (!ws || ((uintptr_t)ws & 255u)) return gf::api_fail_msg(h, GF_EINVAL, "workspace must be non-NULL and 256-byte aligned");
-  if (ws_bytes < sizeof(gf::cplx) * (size_t)(2 * g.N)) return gf::api_fail_msg(h, GF_ENOMEM, "workspace too small for the fill table");
+  if (ws_bytes < sizeof(gf::cplx) * (size_t)(3 * g.N)) return gf::api_fail_msg(h, GF_ENOMEM, "workspace too small for the fill table");
   if ((s = gf::api_bind_device(h))) return s;
   cudaStream_t st = (cudaStream_t)stream;
   gf::cplx* table = reinterpret_cast<gf::cplx*>(ws);
+  float4* table32 = reinterpret_cast<float4*>(table + 2 * g.N);
   int64_t b = (g.N + 255) / 256;
-  gf::k_fill3_table<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(g, table);
+  gf::k_fill3_table<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(g, table, table32);
   const int rows = (int)(3 * g.N < 152 * 16 ? 3 * g.N : 152 * 16);
   if (dtype == GF_C128) {
     gf::k_fill3_expand<double2><<<rows, 256, 0, st>>>(g, prob->ldg, table, reinterpret_cast<double2*>(prob->G));
     gf::k_fill3_monitor<double2><<<(int)(b < 4864 ? b + 1 : 4864), 256, 0, st>>>(g, prob->ldg, reinterpret_cast<double2*>(prob->G),
                                                                                  reinterpret_cast<gf::cplx*>(prob->E));
   } else {
-    gf::k_fill3_expand<float2><<<rows, 256, 0, st>>>(g, prob->ldg, table, reinterpret_cast<float2*>(prob->G));
+    gf::k_fill3_expand_f32<<<rows, 256, 0, st>>>(g, prob->ldg, table32, reinterpret_cast<float2*>(prob->G));
     gf::k_fill3_monitor<float2><<<(int)(b < 4864 ? b + 1 : 4864), 256, 0, st>>>(g, prob->ldg, reinterpret_cast<float2*>(prob->G),
                                                                                 reinterpret_cast<gf::cplx*>(prob->E));
   }
