@@ -337,6 +337,12 @@ gf_status gf_batch_step(gf_batch* b, void* stream);
 gf_status gf_batch_set_schedule(gf_batch* b, int32_t update_ctas);
 void gf_batch_destroy(gf_batch* b);
 
+/* Diagnostic of the bounded waits (no counterpart in the paper): one CTA waits on a barrier that
+ * nothing signals, with the abortable bounded wait of the tensor-core kernels, for timeout_ns
+ * (1 us .. 2 s), then writes GF_ETIMEOUT to *status (device int32) -- the status a stalled
+ * update reports -- without faulting the GPU; later calls on the context work as usual. */
+gf_status gf_selftest_timeout(gf_handle* h, int64_t timeout_ns, int32_t* status, void* stream);
+
 /* Kernel timing (no counterpart in the paper; it backs the per-step timers of the bench).
  * gf_profile_begin arms up to max_records CUDA-event pairs that the library records on the
  * launching stream around every launch of the G-update kernel (in the deferred form: of the

@@ -35,7 +35,7 @@ EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_v
            "gf_batch_set_schedule", "gf_batch_destroy", "gf_select_egreedy", "gf_lowrank_workspace_size",
            "gf_lowrank_init", "gf_lowrank_eval", "gf_lowrank_update", "gf_lowrank_count",
            "gf_lowrank_materialize", "gf3_num_unknowns", "gf3_num_candidates", "gf3_workspace_size",
-           "gf3_fill_g0", "gf3_eval_candidates", "gf3_select_topk", "gf3_apply_update"]
+           "gf3_fill_g0", "gf3_eval_candidates", "gf3_select_topk", "gf3_apply_update", "gf_selftest_timeout"]
 
 
 class GfError(RuntimeError):
@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "gf_select_egreedy": (C.c_int32, [P, C.POINTER(gf_geom), C.POINTER(gf_cand_spec), P, C.c_int64,
                                               C.c_double, P, P, P, P, P, C.c_size_t, P]),
+            "gf_selftest_timeout": (C.c_int32, [P, C.c_int64, P, P]),
             "gf3_num_unknowns": (C.c_int64, [C.POINTER(gf_geom3d)]),
             "gf3_num_candidates": (C.c_int64, [C.POINTER(gf_geom3d)]),
             "gf3_workspace_size": (C.c_size_t, [C.POINTER(gf_geom3d), C.c_int32, C.POINTER(gf_cand_spec)]),
@@ -286,6 +287,9 @@ class Handle:
                                         int(max_iter), float(tol), res, its, _ptr(ws), int(ws_bytes),
                                         _stream(stream)))
         return list(res), list(its)[:ns]
+
+    def gf_selftest_timeout(self, timeout_ns: int, status, stream=None):
+        self._check(self.lib.gf_selftest_timeout(self.h, int(timeout_ns), _ptr(status), _stream(stream)))
 
     # ---- 3-D form
     def gf3_num_unknowns(self, geom) -> int:

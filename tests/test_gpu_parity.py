@@ -241,3 +241,22 @@ def test_pooled_topk_selection_matches_oracle(nx, ny, k, seed):
         got = [int(x) for x in idx.cpu().numpy() if x >= 0]
         assert got == ref, (trial, got[:5], ref[:5])
         assert int(st.cpu()[0]) == (B.GF_OK if ref else B.GF_ENOIMPROVE)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A wait that nothing satisfies gives up after its limit and reports GF_ETIMEOUT through the
+    device status word (no fault); the next greedy step on the same context is unaffected."""
+    import time
+    wl = W.plain_32()
+    opt = GreedyOptimizer(wl.geoms, wl.spec)
+    opt.fill()
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    opt.h.gf_selftest_timeout(50_000_000, st)            # 50 ms
+    torch.cuda.synchronize()
+    assert int(st.cpu()[0]) == B.GF_ETIMEOUT
+    assert time.perf_counter() - t0 >= 0.045
+    r = opt.run(3)
+    assert r[0].status == B.GF_OK and len(r[0].ids) == 1
+    with pytest.raises(B.GfError):
+        opt.h.gf_selftest_timeout(10, st)
