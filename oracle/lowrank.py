@@ -122,12 +122,25 @@ class LowRankProblem:
             Ds.append(d)
         return np.concatenate(Vs), np.concatenate(Ds)
 
-    def accept(self, ids: Sequence[int], spec: CandidateSpec = None) -> List[int]:
+    def joint_dfom(self, ids: Sequence[int], spec: CandidateSpec = None) -> float:
+        """dFOM of applying the candidates together (this wavelength's share); -inf if A is
+        singular."""
+        V, d = self.flip_set(list(ids), spec)
+        GVV = self.entries(V[:, None], V[None, :])
+        A = np.eye(len(V)) - GVV * d[None, :]
+        y, ok = O.gauss_pp(A, self.E[V])
+        if not ok:
+            return -np.inf
+        dE = np.sum(self.entries(np.full(len(V), self.N), V) * d * y)
+        return abs(self.E[self.N] + dE) ** 2 - abs(self.E[self.N]) ** 2
+
+    def accept(self, ids: Sequence[int], spec: CandidateSpec = None, joint_check: bool = True) -> List[int]:
         """Apply candidates; with `spec` given they are applied as that family's candidates
-        (used to reach a patterned design by single-pixel toggles)."""
+        (used to reach a patterned design by single-pixel toggles).  joint_check=False applies
+        the set as given (the caller took the joint decision, e.g. summed over wavelengths)."""
         ids = list(ids)
         V, d = self.flip_set(ids, spec)
-        if len(ids) > 1:
+        if len(ids) > 1 and joint_check:
             GVV = self.entries(V[:, None], V[None, :])
             A = np.eye(len(V)) - GVV * d[None, :]
             y, ok = O.gauss_pp(A, self.E[V])
