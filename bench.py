@@ -115,7 +115,7 @@ class ClockSampler:
 # taken on (SHA-256 over the files below); otherwise the line reports null.
 TRAFFIC_SOURCES = ("paper_2202_05388_gb300/csrc/gf_update_tc.cu", "paper_2202_05388_gb300/csrc/gf_tc.cuh")
 TRAFFIC = {
-    "brush_192x192_p4_c128": {"sha256": "f2811ae0be0fd617654bb80bf7337bbb1d796642412f3a13e236c266fb746205",
+    "brush_192x192_p4_c128": {"sha256": "7db4f095d08bf6265dec088813df9ac40098300829d41afd685f7c2b83e7f6ca",
                               "bytes": 21.79e9 + 21.69e9,
                               "profile": "profiles/rank_update_tc_brush192_launches.md"},
 }

@@ -546,9 +546,7 @@ k_rank_update_ozaki(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_
                     int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int p = ctl->skip ? 0 : ctl->nv;
-#ifndef GF_EXPERIMENT_NO_PROFP
   if (prof_p && blockIdx.x == 0 && threadIdx.x == 0 && p >= 1 && p <= 4) *prof_p = p;
-#endif
   if (p < 1 || p > 4) return;
   OzSingleSrc src;
   src.map = &tmapG;
