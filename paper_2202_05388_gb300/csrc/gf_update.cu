@@ -110,7 +110,9 @@ __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ pi
     __syncthreads();
     const int w = p - c0 - nb;                   // trailing width
     if (w > 0) {
-      // ---- U12 = L11^{-1} A12 (unit lower, one thread per column)
+      // ---- U12 = L11^{-1} A12 (unit lower, one thread per column); for p <= kLuMaxBlocked / 2
+      // the block is also kept in the free half of the panel buffer for the trailing update
+      cplx* sU = p <= kLuMaxBlocked / 2 ? sP + (kLuMaxBlocked / 2) * kLuNB : nullptr;
       for (int v = tid; v < w; v += nt) {
         cplx x[kLuNB];
 #pragma unroll
@@ -125,6 +127,10 @@ __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ pi
 #pragma unroll
         for (int j = 1; j < kLuNB; ++j)
           if (j < nb) A[(int64_t)(c0 + j) * p + c0 + nb + v] = x[j];
+        if (sU)
+#pragma unroll
+          for (int j = 0; j < kLuNB; ++j)
+            if (j < nb) sU[j * w + v] = x[j];
       }
       __syncthreads();
       // ---- A22 -= L21 U12, every element independently (coalesced along the row)
@@ -134,7 +140,8 @@ __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ pi
         cplx acc = A[o];
 #pragma unroll
         for (int j = 0; j < kLuNB; ++j)
-          if (j < nb) acc = acc - sP[(nb + i) * kLuNB + j] * A[(int64_t)(c0 + j) * p + c0 + nb + v];
+          if (j < nb)
+            acc = acc - sP[(nb + i) * kLuNB + j] * (sU ? sU[j * w + v] : A[(int64_t)(c0 + j) * p + c0 + nb + v]);
         A[o] = acc;
       }
     }
@@ -309,20 +316,29 @@ __device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayou
         for (int r = tid; r < c; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
         __syncthreads();
       }
-      if (tid == 0) {
-        double df = 0.0;
-        for (int mc = 0; mc < a.u.mcount; ++mc) {          // the monitor's unknowns (Eq. 1)
-          const int64_t m = a.u.mrow + mc;
-          cplx EN = U.E[m];
-          cplx dE = mk(0.0, 0.0);
-          for (int u = 0; u < p; ++u) dE = dE + dchi[u] * (ldG(U.G, a.u.dtype, U.ldg, m, V[u]) * y[u]);
-          cplx Em = EN + dE;
-          df += abs2(Em) - abs2(EN);
+      // Eq. 4 at the monitor's unknowns (Eq. 1): the gathers of the monitor row are spread over
+      // the block and reduced
+      double df = 0.0;
+      for (int mc = 0; mc < a.u.mcount; ++mc) {
+        const int64_t m = a.u.mrow + mc;
+        cplx part = mk(0.0, 0.0);
+        for (int u = tid; u < p; u += blockDim.x) part = part + dchi[u] * (ldG(U.G, a.u.dtype, U.ldg, m, V[u]) * y[u]);
+        for (int o = 16; o > 0; o >>= 1) {
+          part.re += __shfl_down_sync(0xffffffffu, part.re, o);
+          part.im += __shfl_down_sync(0xffffffffu, part.im, o);
         }
-        s_red[0] = df;
-        // store D y for the field update
-        for (int u = 0; u < p; ++u) y[u] = dchi[u] * y[u];
+        if (lane == 0) { s_bv[wid] = part.re; s_red[wid] = part.im; }
+        __syncthreads();
+        if (tid == 0) {
+          cplx dE = mk(0.0, 0.0);
+          for (int w = 0; w < nw; ++w) dE = dE + mk(s_bv[w], s_red[w]);
+          const cplx EN = U.E[m];
+          df += abs2(EN + dE) - abs2(EN);
+        }
+        __syncthreads();
       }
+      if (tid == 0) s_red[0] = df;
+      for (int u = tid; u < p; u += blockDim.x) y[u] = dchi[u] * y[u];      // D y for the field update
       __syncthreads();
       total += s_red[0];
       __syncthreads();

@@ -146,8 +146,14 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G
       Ms[e] = (u < p && v < p) ? Mdai[u * p + v] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    for (int vv = 0; vv < 16 && v0 + vv < p; ++vv) {
-      const float2 r = j < n ? G[(int64_t)V[v0 + vv] * ldg + j] : make_float2(0.f, 0.f);
+    // the chunk's 16 entries of this column first (independent loads in flight), then the FMAs
+    float2 rv[16];
+#pragma unroll
+    for (int vv = 0; vv < 16; ++vv)
+      rv[vv] = (j < n && v0 + vv < p) ? G[(int64_t)V[v0 + vv] * ldg + j] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int vv = 0; vv < 16; ++vv) {
+      const float2 r = rv[vv];
 #pragma unroll
       for (int a = 0; a < 32; ++a) {
         if (a < uq) {
