@@ -66,7 +66,7 @@ __device__ __forceinline__ void st4h(uint8_t* p, __half a, __half b, __half c, _
 
 // P = p rounded up to 16, so that each of the four u-quarters of k_c64_s_gemm is a multiple
 // of 4 and every K chunk holds whole groups of four.
-int64_t c64_padP(int p) { return (int64_t)((p + 15) / 16) * 16; }
+__host__ __device__ int64_t c64_padP(int p) { return (int64_t)((p + 15) / 16) * 16; }
 
 C64Layout c64_layout(int64_t n, int pmax) {
   C64Layout o;
@@ -125,17 +125,18 @@ __global__ void k_c64_inverse(WsLayout L, char* ws, int lam, float2* __restrict_
 // One CTA per 64 complex columns (one 128-real-column tile); thread (j, quarter of u range).
 __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G, int64_t ldg, int64_t n,
                                                     const float2* __restrict__ Mdai, const int32_t* __restrict__ V,
-                                                    const UpdCtl* __restrict__ ctl, int64_t P, int nkc,
+                                                    const UpdCtl* __restrict__ ctl, int nkc,
                                                     uint8_t* __restrict__ Bops, int32_t* __restrict__ Fcol) {
   if (ctl->skip) return;
   const int p = ctl->nv;
+  const int P = (int)c64_padP(p);            // this step's P: the blocks beyond K = 2P are not read
   __shared__ float2 Ms[128 * 16];            // M[u][v0 .. v0+16)
   __shared__ float smax[4][64];
   const int t = threadIdx.x;
   const int jl = t & 63, q = t >> 6;         // local complex column, u quarter
   const int64_t ct = blockIdx.x;
   const int64_t j = ct * 64 + jl;
-  const int uq = (int)(P / 4);               // u values per thread (multiple of 4, <= 32)
+  const int uq = P / 4;                      // u values per thread (multiple of 4, <= 32)
   float2 acc[32];
 #pragma unroll
   for (int a = 0; a < 32; ++a) acc[a] = make_float2(0.f, 0.f);
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G
       f16_split(acc[a4 + e].y * sc, ih[e], il[e]);
       f16_split(-acc[a4 + e].y * sc, nh[e], nl[e]);
     }
-    const int kA = u0, kB = (int)P + u0;
+    const int kA = u0, kB = P + u0;
     uint8_t* blkA = tile + (kA / kC64KC) * kC64Block;
     uint8_t* blkB = tile + (kB / kC64KC) * kC64Block;
     const int oRa = c64_off(c_re, kA % kC64KC), oIa = c64_off(c_im, kA % kC64KC);
@@ -208,10 +209,11 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G
 // ---- A operand blocks from C0 (n x pmax FP64): row i -> [Re C0[i, :P), Im C0[i, :P)], scaled
 // by 2^-E_i and split into FP16 halves
 __global__ void k_c64_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n, int64_t nrows_pad,
-                                const UpdCtl* __restrict__ ctl, int64_t P, int nkc, uint8_t* __restrict__ Aops,
+                                const UpdCtl* __restrict__ ctl, int nkc, uint8_t* __restrict__ Aops,
                                 int32_t* __restrict__ Erow) {
   if (ctl->skip) return;
   const int p = ctl->nv;
+  const int P = (int)c64_padP(p);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows_pad;
        i += (int64_t)gridDim.x * blockDim.x) {
     uint8_t* tile = Aops + (i / kC64M) * (int64_t)nkc * kC64Block;
@@ -232,7 +234,7 @@ __global__ void k_c64_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n
         f16_split((float)ldexp(c.re, -E), rh[e], rl[e]);
         f16_split((float)ldexp(c.im, -E), ih[e], il[e]);
       }
-      const int kA = u0, kB = (int)P + u0;
+      const int kA = u0, kB = P + u0;
       uint8_t* blkA = tile + (kA / kC64KC) * kC64Block;
       uint8_t* blkB = tile + (kB / kC64KC) * kC64Block;
       const int oa = c64_off(r, kA % kC64KC), ob = c64_off(r, kB % kC64KC);
@@ -283,11 +285,14 @@ __global__ void __launch_bounds__(kC64Threads, 1)
 k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_t nrt, int64_t nct, int nkc,
                        const uint8_t* __restrict__ Aops, const uint8_t* __restrict__ Bops,
                        const int32_t* __restrict__ Erow, const int32_t* __restrict__ Fcol,
-                       const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
+                       const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status, int32_t* __restrict__ prof_p,
+                       int nkr_min) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int p = ctl->skip ? 0 : ctl->nv;
-  if (prof_p && blockIdx.x == 0 && threadIdx.x == 0 && p > 0) *prof_p = p;
-  if (p <= 0) return;                            // uniform over the grid (both CTAs of a cluster)
+  const int nkr = (int)(c64_padP(p) / 16);       // K chunks of this step (K = 2P); nkc is the block stride
+  // uniform over the grid (both CTAs of a cluster); nkr <= nkr_min: the resident-A form took it
+  if (p <= 0 || nkr <= nkr_min) return;
+  if (prof_p && blockIdx.x == 0 && threadIdx.x == 0) *prof_p = p;
   C64Bars* bars = reinterpret_cast<C64Bars*>(smem + kC64BarOff);
   uint8_t* ops = smem;                                        // kC64NSO x (A block, B block)
   uint8_t* gts = smem + kC64NSO * kC64OpStage;                // kC64NSG x G tile
@@ -373,7 +378,7 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
         if (rt >= nrt) rt = 0;                   // phantom tile: any valid operands
         if (ct >= nct) ct = 0;
         bool ok = true;
-        for (int kc = 0; kc < nkc; ++kc, ++c) {
+        for (int kc = 0; kc < nkr; ++kc, ++c) {
           const int s = (int)(c % kC64NSO);
           if (c >= kC64NSO && !tc::mbar_wait_or_abort(&bars->oempty[s], (uint32_t)((c / kC64NSO - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
           uint8_t* st = ops + s * kC64OpStage;
@@ -412,7 +417,7 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
         if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[b], (uint32_t)((k / 2 - 1) & 1), abort, kC64TimeoutNs)) break;
         tc::fence_after_sync();
         const uint32_t d1 = tbase + (uint32_t)(b * 2 * kC64N), d2 = d1 + kC64N;
-        for (int kc = 0; kc < nkc; ++kc, ++c) {
+        for (int kc = 0; kc < nkr; ++kc, ++c) {
           const int s = (int)(c % kC64NSO);
           if (!tc::mbar_wait_or_abort(&bars->ofull[s], (uint32_t)((c / kC64NSO) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
           tc::fence_after_sync();
@@ -456,7 +461,14 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
       const int b = (int)(k & 1);
       const int64_t u = 2 * k + (h >> 1);      // this warp's half of the tile
       const int s = (int)(u % kC64NSG);
+      // the scale exponents first: their loads overlap the waits below
       const int Ei = real ? Erow[rt * kC64M + r] : 0;
+      int Fr[16];
+      {
+        const int32_t* Fq = Fcol + (real ? ct : 0) * (kC64N / 2) + h * 16;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) Fr[e] = Fq[e];
+      }
       if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kC64TimeoutNs)) break;
       if (!tc::mbar_wait_or_abort(&bars->gfull[s], (uint32_t)((u / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
       tc::fence_after_sync();
@@ -483,12 +495,11 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
       if (real) {
         // box h holds real columns 32h .. 32h+31 of the tile = 8 chunks of 16 B (128B swizzle);
         // chunk ch holds complex columns 2ch, 2ch+1 of this quarter
-        const int32_t* Fq = Fcol + ct * (kC64N / 2) + h * 16;
         uint8_t* row = gts + s * kC64GTile + (h & 1) * kC64Box + r * 128;
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
-          const float s0 = __int_as_float((Ei + Fq[2 * ch] + 127) << 23);
-          const float s1 = __int_as_float((Ei + Fq[2 * ch + 1] + 127) << 23);
+          const float s0 = __int_as_float((Ei + Fr[2 * ch] + 127) << 23);
+          const float s1 = __int_as_float((Ei + Fr[2 * ch + 1] + 127) << 23);
           float4* gp = reinterpret_cast<float4*>(row + ((ch ^ (r & 7)) << 4));
           float4 g = *gp;
           g.x += s0 * fmaf(acc2[4 * ch + 0], 0.00048828125f, acc1[4 * ch + 0]);
@@ -538,6 +549,320 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
   if (warp == kWarpMma) tc::tmem_dealloc(tbase, kC64TmemCols);
 }
 
+// ---- resident-A form: joint rank p <= 64 (K <= 128 real) ------------------------------------
+// Each CTA owns one row tile at a time and sweeps a run of its column tiles.  The row tile's A
+// blocks (nkr x 16 KB, at most 64 KB) are loaded once per run and stay in shared memory, so per
+// tile only the B blocks (nkr x 16 KB, a ring of 16 KB stages) and the G tile move: half the
+// operand bytes of the streaming form above.  Runs: the row tiles are taken in groups of
+// gridDim.x; in a full group CTA b takes row tile b of the group across every column tile, all
+// CTAs stepping through the columns together (each B block is read from L2 by every CTA at
+// about the same time); in the last group of R < gridDim.x row tiles each row is split into
+// gridDim.x / R column segments.  Before it retires, every role waits (bounded) for the copies
+// and MMAs it issued, so a CTA that gave up on a wait leaves nothing in flight.
+constexpr int kRaMaxK = 4;                                   // A chunks that fit next to the ring
+constexpr int kRaOps = kC64NSO * kC64OpStage;                // 96 KB: A blocks + B ring
+constexpr int kRaMaxB = kRaOps / kC64Block - 1;              // B stages when nkr = 1
+constexpr uint64_t kRaDrainNs = 100000000ull;
+
+struct C64RaBars {
+  uint64_t bfull[kRaMaxB], bempty[kRaMaxB];
+  uint64_t afull, aempty;
+  uint64_t gfull[kC64NSG], gempty[kC64NSG], ebar[kC64NSG];
+  uint64_t tfull[2], tempty[2];
+  uint64_t drain;
+  uint32_t tslot;
+  int abort;
+};
+static_assert(sizeof(C64RaBars) <= kC64Smem - kC64BarOff, "barrier block");
+
+struct RaCursor {
+  int64_t g, rt, c, cbeg, cend;
+  int64_t lnext, lend;                          // rest of a contiguous range in its group
+};
+// Runs of CTA b of G.  A group of R row tiles (R = G except in the last group) is split into s =
+// G / R column segments per row tile when that keeps every CTA busy, or at least 3/4 of them where
+// the B blocks of all column tiles would not stay in L2 (more than 512 column tiles); otherwise
+// each CTA takes an equal contiguous range of the group's tiles in row-major order, a run per row
+// tile it touches (the CTAs then read B blocks of different columns at any one time).
+__device__ __forceinline__ bool ra_piece(RaCursor& k, int64_t nct, int64_t G) {
+  k.rt = k.g * G + k.lnext / nct;
+  k.c = k.cbeg = k.lnext % nct;
+  k.cend = (k.cbeg + (k.lend - k.lnext)) < nct ? (k.cbeg + (k.lend - k.lnext)) : nct;
+  k.lnext += k.cend - k.cbeg;
+  return true;
+}
+__device__ __forceinline__ bool ra_run(RaCursor& k, int64_t nrt, int64_t nct, int64_t G, int64_t b) {
+  for (; k.g * G < nrt; ++k.g) {
+    const int64_t R = (nrt - k.g * G) < G ? (nrt - k.g * G) : G;
+    const int64_t s = G / R;                  // column segments per row tile
+    if (R * s == G || (nct > 512 && 4 * R * s >= 3 * G)) {
+      if (b >= R * s) continue;
+      const int64_t seg = b / R;
+      const int64_t c0 = seg * nct / s, c1 = (seg + 1) * nct / s;
+      if (c1 <= c0) continue;
+      k.rt = k.g * G + b % R;
+      k.c = k.cbeg = c0;
+      k.cend = c1;
+      k.lnext = k.lend = 0;
+      return true;
+    }
+    const int64_t l0 = b * R * nct / G, l1 = (b + 1) * R * nct / G;
+    if (l1 <= l0) continue;
+    k.lnext = l0;
+    k.lend = l1;
+    return ra_piece(k, nct, G);
+  }
+  return false;
+}
+__device__ __forceinline__ bool ra_first(RaCursor& k, int64_t nrt, int64_t nct, int64_t G, int64_t b) {
+  k.g = 0;
+  return ra_run(k, nrt, nct, G, b);
+}
+__device__ __forceinline__ bool ra_next(RaCursor& k, int64_t nrt, int64_t nct, int64_t G, int64_t b) {
+  if (++k.c < k.cend) return true;
+  if (k.lnext < k.lend) return ra_piece(k, nct, G);
+  ++k.g;
+  return ra_run(k, nrt, nct, G, b);
+}
+
+__global__ void __launch_bounds__(kC64Threads, 1)
+k_rank_update_c64_ra(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_t nrt, int64_t nct, int nkc,
+                     const uint8_t* __restrict__ Aops, const uint8_t* __restrict__ Bops,
+                     const int32_t* __restrict__ Erow, const int32_t* __restrict__ Fcol,
+                     const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int p = ctl->skip ? 0 : ctl->nv;
+  const int nkr = (int)(c64_padP(p) / 16);       // K chunks of this step
+  if (p <= 0 || nkr > kRaMaxK) return;           // uniform over the grid; larger K: streaming form
+  if (prof_p && blockIdx.x == 0 && threadIdx.x == 0) *prof_p = p;
+  C64RaBars* bars = reinterpret_cast<C64RaBars*>(smem + kC64BarOff);
+  uint8_t* As = smem;                            // nkr A blocks of the current row tile
+  uint8_t* Bs = smem + nkr * kC64Block;          // B ring
+  const int nsb = kRaOps / kC64Block - nkr;      // 2 .. kRaMaxB stages
+  uint8_t* gts = smem + kRaOps;                  // kC64NSG G half tiles
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  volatile int* abort = &bars->abort;
+  constexpr int kWarpGProd = kC64EpiWarps, kWarpMma = kC64EpiWarps + 1, kWarpStore = kC64EpiWarps + 2,
+                kWarpOProd = kC64EpiWarps + 3;
+  const int64_t G = gridDim.x, me = blockIdx.x;
+
+  if (warp == kWarpMma) {
+    tc::tmem_alloc(&bars->tslot, kC64TmemCols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int q = 0; q < nsb; ++q) {
+      tc::mbar_init(&bars->bfull[q], 1);
+      tc::mbar_init(&bars->bempty[q], 1);
+    }
+    tc::mbar_init(&bars->afull, 1);
+    tc::mbar_init(&bars->aempty, 1);
+    for (int q = 0; q < kC64NSG; ++q) {
+      tc::mbar_init(&bars->gfull[q], 1);
+      tc::mbar_init(&bars->gempty[q], 1);
+      tc::mbar_init(&bars->ebar[q], 32 * kC64EpiWarps / 2);   // the epilogue warps of that half
+    }
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&bars->tfull[q], 1);
+      tc::mbar_init(&bars->tempty[q], kC64EpiWarps);
+    }
+    tc::mbar_init(&bars->drain, 1);
+    bars->abort = 0;
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = bars->tslot;
+
+  if (warp == kWarpGProd) {
+    if (lane == 0) {
+      int64_t k = 0, issued = 0;                 // tiles begun, half-tile uses issued
+      bool ok = true;
+      RaCursor cur;
+      for (bool more = ra_first(cur, nrt, nct, G, me); more && ok; more = ra_next(cur, nrt, nct, G, me), ++k) {
+        for (int hh = 0; hh < 2; ++hh) {
+          const int64_t u = 2 * k + hh;
+          const int s = (int)(u % kC64NSG);
+          if (u >= kC64NSG && !tc::mbar_wait_or_abort(&bars->gempty[s], (uint32_t)((u / kC64NSG - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          const int x0 = (int)(cur.c * kC64N) + 64 * hh, y = (int)(cur.rt * kC64M);     // x in floats
+          int nbox = 0;
+          for (int bx = 0; bx < 2; ++bx) nbox += (x0 + 32 * bx < 2 * n) ? 1 : 0;
+          if (nbox == 0) tc::mbar_arrive(&bars->gfull[s]);
+          else {
+            tc::mbar_arrive_expect_tx(&bars->gfull[s], (uint32_t)(nbox * kC64Box));
+            uint8_t* gt = gts + s * kC64GTile;
+            for (int bx = 0; bx < nbox; ++bx) tc::tma_load_2d(gt + bx * kC64Box, &tmapG, x0 + 32 * bx, y, &bars->gfull[s]);
+          }
+          issued = u + 1;
+        }
+      }
+      // every load issued has landed before the CTA may retire
+      for (int64_t q = issued - kC64NSG; q < issued; ++q)
+        if (q >= 0) tc::mbar_wait_bounded(&bars->gfull[q % kC64NSG], (uint32_t)((q / kC64NSG) & 1), kRaDrainNs);
+    }
+    __syncwarp();
+  } else if (warp == kWarpOProd) {
+    if (lane == 0) {
+      const uint64_t pol_ops = tc::policy_evict_last();    // B blocks: read by every row tile
+      int64_t c = 0, na = 0;                     // B chunks issued, A loads issued
+      bool ok = true;
+      RaCursor cur;
+      for (bool more = ra_first(cur, nrt, nct, G, me); more && ok; more = ra_next(cur, nrt, nct, G, me)) {
+        if (cur.c == cur.cbeg) {                 // a new run: its row tile's A blocks
+          if (na >= 1 && !tc::mbar_wait_or_abort(&bars->aempty, (uint32_t)((na - 1) & 1), abort, kC64TimeoutNs)) break;
+          tc::mbar_arrive_expect_tx(&bars->afull, (uint32_t)(nkr * kC64Block));
+          for (int kc = 0; kc < nkr; ++kc)
+            tc::bulk_g2s(As + kc * kC64Block, Aops + (cur.rt * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->afull);
+          ++na;
+        }
+        for (int kc = 0; kc < nkr; ++kc, ++c) {
+          const int s = (int)(c % nsb);
+          if (c >= nsb && !tc::mbar_wait_or_abort(&bars->bempty[s], (uint32_t)((c / nsb - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          tc::mbar_arrive_expect_tx(&bars->bfull[s], (uint32_t)kC64Block);
+          tc::bulk_g2s_hint(Bs + s * kC64Block, Bops + (cur.c * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->bfull[s],
+                            pol_ops);
+        }
+      }
+      // every copy issued has landed before the CTA may retire
+      if (na >= 1) tc::mbar_wait_bounded(&bars->afull, (uint32_t)((na - 1) & 1), kRaDrainNs);
+      for (int64_t q = c - nsb; q < c; ++q)
+        if (q >= 0) tc::mbar_wait_bounded(&bars->bfull[q % nsb], (uint32_t)((q / nsb) & 1), kRaDrainNs);
+    }
+    __syncwarp();
+  } else if (warp == kWarpMma) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_f16(kC64M, kC64N);
+      int64_t k = 0, c = 0, na = 0;
+      bool ok = true;
+      RaCursor cur;
+      for (bool more = ra_first(cur, nrt, nct, G, me); more && ok; more = ra_next(cur, nrt, nct, G, me), ++k) {
+        if (cur.c == cur.cbeg) {
+          if (!tc::mbar_wait_or_abort(&bars->afull, (uint32_t)(na & 1), abort, kC64TimeoutNs)) break;
+          ++na;
+        }
+        const int b = (int)(k & 1);
+        if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[b], (uint32_t)((k / 2 - 1) & 1), abort, kC64TimeoutNs)) break;
+        tc::fence_after_sync();
+        const uint32_t d1 = tbase + (uint32_t)(b * 2 * kC64N), d2 = d1 + kC64N;
+        for (int kc = 0; kc < nkr; ++kc, ++c) {
+          const int s = (int)(c % nsb);
+          if (!tc::mbar_wait_or_abort(&bars->bfull[s], (uint32_t)((c / nsb) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          tc::fence_after_sync();
+          const uint32_t sA = tc::smem_u32(As + kc * kC64Block);
+          const uint32_t sB = tc::smem_u32(Bs + s * kC64Block);
+#pragma unroll
+          for (int ks = 0; ks < kC64KC / 16; ++ks) {
+            const uint32_t off = ks * 256;     // K = 16 FP16 per step = two core matrices
+            const uint64_t ah = tc::smem_desc(sA + off, 128, 512), al = tc::smem_desc(sA + kC64Half + off, 128, 512);
+            const uint64_t bh = tc::smem_desc(sB + off, 128, 512), bl = tc::smem_desc(sB + kC64Half + off, 128, 512);
+            const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
+            tc::mma_f16(d1, ah, bh, idesc, first);
+            tc::mma_f16(d2, ah, bl, idesc, first);
+            tc::mma_f16(d2, al, bh, idesc, 1u);
+          }
+          tc::mma_commit(&bars->bempty[s]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&bars->tfull[b]);
+        if (cur.c == cur.cend - 1) tc::mma_commit(&bars->aempty);    // last tile of the run
+      }
+      // every MMA issued has completed before the CTA may release TMEM and retire
+      tc::mma_commit(&bars->drain);
+      tc::mbar_wait_bounded(&bars->drain, 0u, kRaDrainNs);
+    }
+    __syncwarp();
+  } else if (warp < kC64EpiWarps) {
+    const int q = warp & 3, h = warp >> 2;     // TMEM lane quarter, column quarter (32 real columns)
+    const int r = q * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    int64_t k = 0;
+    RaCursor cur;
+    for (bool more = ra_first(cur, nrt, nct, G, me); more; more = ra_next(cur, nrt, nct, G, me), ++k) {
+      const int64_t rt = cur.rt, ct = cur.c;
+      const int b = (int)(k & 1);
+      const int64_t u = 2 * k + (h >> 1);      // this warp's half of the tile
+      const int s = (int)(u % kC64NSG);
+      // the scale exponents first: their loads overlap the waits below
+      const int Ei = Erow[rt * kC64M + r];
+      int Fr[16];
+      {
+        const int32_t* Fq = Fcol + ct * (kC64N / 2) + h * 16;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) Fr[e] = Fq[e];
+      }
+      if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kC64TimeoutNs)) break;
+      if (!tc::mbar_wait_or_abort(&bars->gfull[s], (uint32_t)((u / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
+      tc::fence_after_sync();
+      float acc1[32], acc2[32];
+      {
+        float a0[16], a1[16], a2[16], a3[16];
+        const uint32_t base = tbase + lane_addr + (uint32_t)(b * 2 * kC64N + h * 32);
+        tc::tmem_ld16(base, a0);
+        tc::tmem_ld16(base + 16, a1);
+        tc::tmem_ld16(base + kC64N, a2);
+        tc::tmem_ld16(base + kC64N + 16, a3);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          acc1[e] = a0[e];
+          acc1[16 + e] = a1[e];
+          acc2[e] = a2[e];
+          acc2[16 + e] = a3[e];
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
+      // box h holds real columns 32h .. 32h+31 of the tile = 8 chunks of 16 B (128B swizzle);
+      // chunk ch holds complex columns 2ch, 2ch+1 of this quarter
+      uint8_t* row = gts + s * kC64GTile + (h & 1) * kC64Box + r * 128;
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch) {
+        const float s0 = __int_as_float((Ei + Fr[2 * ch] + 127) << 23);
+        const float s1 = __int_as_float((Ei + Fr[2 * ch + 1] + 127) << 23);
+        float4* gp = reinterpret_cast<float4*>(row + ((ch ^ (r & 7)) << 4));
+        float4 g = *gp;
+        g.x += s0 * fmaf(acc2[4 * ch + 0], 0.00048828125f, acc1[4 * ch + 0]);
+        g.y += s0 * fmaf(acc2[4 * ch + 1], 0.00048828125f, acc1[4 * ch + 1]);
+        g.z += s1 * fmaf(acc2[4 * ch + 2], 0.00048828125f, acc1[4 * ch + 2]);
+        g.w += s1 * fmaf(acc2[4 * ch + 3], 0.00048828125f, acc1[4 * ch + 3]);
+        *gp = g;
+      }
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(&bars->ebar[s]);
+    }
+  }
+  if (warp == kWarpStore) {
+    if (lane == 0) {
+      int64_t k = 0;
+      bool ok = true;
+      RaCursor cur;
+      for (bool more = ra_first(cur, nrt, nct, G, me); more && ok; more = ra_next(cur, nrt, nct, G, me), ++k) {
+        for (int hh = 0; hh < 2; ++hh) {
+          const int64_t u = 2 * k + hh;
+          const int s = (int)(u % kC64NSG);
+          if (!tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)((u / kC64NSG) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          const int x0 = (int)(cur.c * kC64N) + 64 * hh, y = (int)(cur.rt * kC64M);
+          uint8_t* gt = gts + s * kC64GTile;
+          for (int bx = 0; bx < 2; ++bx)
+            if (x0 + 32 * bx < 2 * n) tc::tma_store_2d(&tmapG, x0 + 32 * bx, y, gt + bx * kC64Box);
+          tc::bulk_commit();
+          tc::bulk_wait_read0();
+          tc::mbar_arrive(&bars->gempty[s]);
+        }
+      }
+      tc::bulk_wait0();
+    }
+    __syncwarp();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid == 0 && bars->abort) atomicExch(status, GF_ETIMEOUT);
+  tc::fence_after_sync();
+  if (warp == kWarpMma) tc::tmem_dealloc(tbase, kC64TmemCols);
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 c64_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -581,12 +906,12 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
   k_c64_inverse<<<L.pmax, 128, 0, st>>>(L, ws, lam, Mdai);
   int32_t* Erow = reinterpret_cast<int32_t*>(ws + L.c64E);
   int32_t* Fcol = reinterpret_cast<int32_t*>(ws + L.c64F);
-  k_c64_s_gemm<<<(unsigned)o.nct, 256, 0, st>>>(G, ldg, n, Mdai, reinterpret_cast<const int32_t*>(ws + L.V), ctl, o.P,
+  k_c64_s_gemm<<<(unsigned)o.nct, 256, 0, st>>>(G, ldg, n, Mdai, reinterpret_cast<const int32_t*>(ws + L.V), ctl,
                                                  (int)o.nkc, Bops, Fcol);
   {
     int64_t rows = o.nrt * kC64M;
     int64_t b = (rows + 127) / 128;
-    k_c64_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, L.pmax, n, rows, ctl, o.P, (int)o.nkc, Aops,
+    k_c64_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, L.pmax, n, rows, ctl, (int)o.nkc, Aops,
                                                                  Erow);
   }
   // once per device: shared-memory opt-in of every form and the number of 4- and 2-CTA clusters
@@ -620,6 +945,7 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
     std::lock_guard<std::mutex> lk(mu);
     const bool cache = dev >= 0 && dev < 64;
     if (!cache || !done[dev]) {
+      cudaFuncSetAttribute(k_rank_update_c64_ra, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
       cudaFuncSetAttribute(k_rank_update_c64_tc_t<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
       cudaFuncSetAttribute(k_rank_update_c64_tc_t<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
       cudaFuncSetAttribute(k_rank_update_c64_tc_t<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
@@ -634,6 +960,15 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
       c4 = clusters4[dev];
       c2 = clusters2[dev];
     }
+  }
+  // joint rank p <= 64 (decided on the device): the resident-A form; larger p: a streaming form,
+  // launched only where the workspace allows p > 64 (each returns at once when the other applies)
+  {
+    const int64_t tiles = o.nrt * o.nct;
+    const int grid = (int)(tiles < sm_count ? tiles : sm_count);
+    k_rank_update_c64_ra<<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.nct, (int)o.nkc, Aops, Bops, Erow,
+                                                               Fcol, ctl, status, prof_p);
+    if (o.nkc <= kRaMaxK) return;
   }
   auto launch_cluster = [&](auto kernel, int size, int64_t blocks, int max_cl) {
     const int ncl = (int)(blocks < max_cl ? blocks : max_cl);
@@ -650,7 +985,7 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, kernel, tmap, n, o.nrt, o.nct, (int)o.nkc, (const uint8_t*)Aops, (const uint8_t*)Bops,
-                       (const int32_t*)Erow, (const int32_t*)Fcol, ctl, status, prof_p);
+                       (const int32_t*)Erow, (const int32_t*)Fcol, ctl, status, prof_p, kRaMaxK);
   };
   // the 2x2 form only where it keeps as many SMs busy as the 2x1 form (the GPCs' SM counts
   // decide how many clusters of each size fit) and has a tile block for every cluster
@@ -666,7 +1001,7 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
   const int64_t tiles = o.nrt * o.nct;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
   k_rank_update_c64_tc_t<1, 1><<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.nct, (int)o.nkc, Aops, Bops,
-                                                                    Erow, Fcol, ctl, status, prof_p);
+                                                                    Erow, Fcol, ctl, status, prof_p, kRaMaxK);
 }
 
 }  // namespace gf

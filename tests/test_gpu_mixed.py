@@ -37,7 +37,10 @@ def _force(opt, ids, k):
     opt.status.zero_()
 
 
-@pytest.mark.parametrize("nx,ny,k,seed,steps", [(20, 18, 4, 51, 4), (33, 29, 16, 52, 3), (12, 10, 1, 53, 6)])
+# joint ranks: k = 4 and 16 stay within p <= 64 (the resident-A update); k = 32 accepts 32
+# brushes per step here (p up to 128: the streaming update)
+@pytest.mark.parametrize("nx,ny,k,seed,steps", [(20, 18, 4, 51, 4), (33, 29, 16, 52, 3), (12, 10, 1, 53, 6),
+                                                (40, 36, 32, 55, 2)])
 def test_c64_lockstep_error_vs_fp64_oracle(nx, ny, k, seed, steps):
     wl = W.small(nx, ny, kind=W.KIND_BRUSH2, dir_mask=3, k=k, excl_radius=3, steps=steps, dtype="c64")
     g = wl.geoms[0]
