@@ -531,12 +531,16 @@ def run_native(args):
                 "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind,
                 "kernel": "k_rank_update_c64_fp32 (rank <= 4, FP32 FMA stream on the CUDA cores)"}
     else:
+        # 8 p flops per 16 bytes of G at p <= 128: far below the tensor pipe's flops per HBM byte
         f16_peak, f16_kind = f16_peak_tflops()
-        roof = {"bound": "tensor", "achieved": achieved_tfl, "peak": f16_peak, "unit": "TFLOP/s",
-                "frac": achieved_tfl / f16_peak, "traffic": None, "peak_kind": f16_kind,
-                "kernel": "k_rank_update_c64_tc (tcgen05 kind::f16, scaled split-FP16, 3 products) + D A^-1 + S GEMM + operand prep",
-                "flops_note": "algorithmic 8 p n^2 per update (p rounded up to 16 executes); the split form runs 3 products",
-                "hbm_achieved_gbs": achieved_gbs, "hbm_frac": achieved_gbs / peak_hbm, "hbm_peak_gbs": peak_hbm}
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
+                "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "k_rank_update_c64_ra (p <= 64: resident A blocks) / k_rank_update_c64_tc_t (p > 64: "
+                          "streaming, 2-CTA clusters); tcgen05 kind::f16, scaled split-FP16, 3 products; "
+                          "+ D A^-1 + S GEMM + operand prep",
+                "tensor_achieved_tflops": achieved_tfl, "tensor_peak_tflops": f16_peak, "tensor_peak_kind": f16_kind,
+                "tensor_frac": achieved_tfl / f16_peak,
+                "flops_note": "algorithmic 8 p n^2 per update (p rounded up to 16 executes); the split form runs 3 products"}
     roof["algorithmic_bytes_per_launch"] = bytes_per_launch
     roof["kernel_ms_avg"] = kern_avg_ms
     roof["kernel_share_of_step"] = kern_ms / ms
@@ -547,7 +551,9 @@ def run_native(args):
     if wl.dtype == "c128":
         upd = 3 if pmax <= 4 else 1                # digit prep rows + cols + tensor-core update, or DFMA
     else:
-        upd = 1 if pmax <= 4 else 4                # FP32 stream, or inverse + S GEMM + prep + tensor-core update
+        # FP32 stream, or inverse + S GEMM + prep + the resident-A update (+ the streaming update
+        # where the workspace allows p > 64; it returns at once when p <= 64)
+        upd = 1 if pmax <= 4 else (4 if pmax <= 64 else 5)
     per_step_launches = 4 + sel + nlam * (upd + 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -842,7 +848,7 @@ def run_metalens3d(args):
             "candidate_evals_per_s": opt.ncand * args.steps / (ms / 1e3),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s", "frac": gbs / peak_hbm,
                          "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "k_rank_update_c64_tc_t (rank 3p, split-FP16 tensor cores, 2-CTA clusters)",
+                         "kernel": "k_rank_update_c64_ra (rank 3p, split-FP16 tensor cores, resident A blocks)",
                          "kernel_ms_avg": kavg, "algorithmic_bytes_per_launch": bpl,
                          "tflops_achieved": kern_flops / max(kern_n, 1) / (kavg * 1e-3) / 1e12 if kavg > 0 else 0.0},
             "gpu_launches": 9 * args.steps, "clocks": clk}

@@ -205,7 +205,10 @@ gf_status gf_refresh(gf_handle* h, const gf_problem* prob, int32_t dtype, const 
  *     tensor-core GEMM with FP32 accumulation.
  * GF_UPDATE_DFMA: native FP64 FMA for every case (complex64 storage rounded once per entry).
  * The complex128 forms match the FP64 oracle within 1e-10; they differ only in speed on GB300
- * (whose FP64 pipe is 1/64 of its FP32 rate).  Applies to later gf_apply_update calls on h. */
+ * (whose FP64 pipe is 1/64 of its FP32 rate).  Applies to later gf_apply_update calls on h.
+ * For complex64 G the setting also selects the arithmetic of gf3_eval_candidates: GF_UPDATE_TC
+ * factorises each pillar's system in FP32 and refines the solution once with an FP64 residual
+ * (the accuracy of an FP64 solve of the stored system); GF_UPDATE_DFMA factorises in FP64. */
 #define GF_UPDATE_TC   0
 #define GF_UPDATE_DFMA 1
 gf_status gf_set_update_algo(gf_handle* h, int32_t algo);

@@ -359,6 +359,232 @@ __global__ void __launch_bounds__(kEv3Threads) k_eval_pillar(Ev3Args a, const ui
   }
 }
 
+// ---- dFOM of every pillar for complex64 G --------------------------------------------------
+// The stored G is FP32, so the p x p system of Eqs. 6-9 is factorised in FP32 (LU with partial
+// pivoting, largest modulus, lowest row on ties) and the solution is refined once with the
+// residual b - A y formed in FP64 from the stored entries (classical iterative refinement):
+// y then has the accuracy of an FP64 solve of the same system, at the FP32 rate for the O(p^3)
+// part.  Eq. 4 at the monitor in FP64.  Singular: a pivot below kSingularRel of the largest row
+// sum, or a refinement correction above 2^-10 of the solution (the FP32 factors do not resolve
+// the system: condition number around 10^4 or more).  Shared memory: the factors, row stride
+// p + 1 (column walks free of bank conflicts).
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 crecipf(float2 b) {
+  const float s = 1.0f / fmaf(b.x, b.x, b.y * b.y);
+  return make_float2(b.x * s, -b.y * s);
+}
+
+// w <- U^{-1} L^{-1} P w for the factors in A (row stride lda, unit lower L below the
+// diagonal, row interchanges piv); one warp, row-oriented dot products
+__device__ __forceinline__ void lu32_solve_warp(const float2* A, int lda, const int* piv, int p, float2* w) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int c = 0; c < p; ++c) {
+      const int r = piv[c];
+      if (r != c) { const float2 t = w[c]; w[c] = w[r]; w[r] = t; }
+    }
+  __syncwarp();
+  for (int r = 1; r < p; ++r) {
+    float sx = 0.f, sy = 0.f;
+    for (int q = lane; q < r; q += 32) {
+      const float2 t = cmulf(A[r * lda + q], w[q]);
+      sx += t.x;
+      sy += t.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) w[r] = make_float2(w[r].x - sx, w[r].y - sy);
+    __syncwarp();
+  }
+  for (int r = p - 1; r >= 0; --r) {
+    float sx = 0.f, sy = 0.f;
+    for (int q = r + 1 + lane; q < p; q += 32) {
+      const float2 t = cmulf(A[r * lda + q], w[q]);
+      sx += t.x;
+      sy += t.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) w[r] = cmulf(make_float2(w[r].x - sx, w[r].y - sy), crecipf(A[r * lda + r]));
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(kEv3Threads) k_eval_pillar_f32(Ev3Args a, const uint8_t* __restrict__ state,
+                                                                 int dir_mask, int aligned, int64_t ncand,
+                                                                 double* __restrict__ dfom) {
+  extern __shared__ __align__(16) unsigned char ev3_smem[];
+  float2* A = reinterpret_cast<float2*>(ev3_smem);              // p x p, row stride p + 1
+  __shared__ cplx b[kEv3MaxP], y[kEv3MaxP], rv[kEv3MaxP];
+  __shared__ float2 w[kEv3MaxP];
+  __shared__ int32_t V[kEv3MaxP];
+  __shared__ int piv[kEv3MaxP];
+  __shared__ double D[kEv3MaxP];
+  __shared__ int s_p;
+  __shared__ double s_v[kEv3Threads / 32];
+  __shared__ int s_i[kEv3Threads / 32];
+  __shared__ cplx s_c[kEv3Threads / 32];
+  __shared__ int s_bad;
+  const Geo3& g = a.g;
+  const float2* G = reinterpret_cast<const float2*>(a.G);
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int64_t c = blockIdx.x; c < ncand; c += gridDim.x) {
+    if (tid == 0) {
+      const int64_t an = c % ((int64_t)(g.nx - 1) * (g.ny - 1));
+      const int ay = (int)(an / (g.nx - 1)), ax = (int)(an - (int64_t)ay * (g.nx - 1));
+      s_p = (aligned && ((ax | ay) & 1)) ? 0
+                                         : cand_pixels(c, GF_KIND_PILLAR, dir_mask, g.nx, g.ny, g.chi, state, V, D, g.nz);
+      s_bad = 0;
+    }
+    __syncthreads();
+    const int p = s_p, lda = p + 1;
+    if (p == 0) {
+      if (tid == 0) dfom[c] = -INFINITY;
+      __syncthreads();
+      continue;
+    }
+    // A = I - G_VV D: each entry in FP64 from the stored FP32 value, then rounded to FP32
+    for (int r = warp; r < p; r += nw) {
+      const float2* Grow = G + (int64_t)V[r] * a.ldg;
+      for (int q = lane; q < p; q += 32) {
+        const float2 gv = Grow[V[q]];
+        A[r * lda + q] = make_float2((float)((r == q ? 1.0 : 0.0) - D[q] * (double)gv.x), (float)(-D[q] * (double)gv.y));
+      }
+    }
+    for (int t = tid; t < p; t += nt) b[t] = a.E[V[t]];
+    __syncthreads();
+    double rs = 0.0;
+    for (int r = tid; r < p; r += nt) {
+      float s = 0.f;
+      for (int q = 0; q < p; ++q) {
+        const float2 e = A[r * lda + q];
+        s += sqrtf(fmaf(e.x, e.x, e.y * e.y));
+      }
+      rs = fmax(rs, (double)s);
+    }
+    int dummy = 0;
+    block_argmax(rs, dummy, s_v, s_i);
+    const double thresh = kSingularRel * rs;
+    for (int cc = 0; cc < p; ++cc) {
+      double bv = -1.0;
+      int br = 0x7fffffff;
+      for (int r = cc + tid; r < p; r += nt) {
+        const float2 e = A[r * lda + cc];
+        const double m = (double)sqrtf(fmaf(e.x, e.x, e.y * e.y));
+        if (m > bv) { bv = m; br = r; }
+      }
+      block_argmax(bv, br, s_v, s_i);
+      if (!(bv >= thresh) || !(bv > 0.0)) {
+        if (tid == 0) s_bad = 1;
+        break;
+      }
+      if (tid == 0) piv[cc] = br;
+      if (br != cc)
+        for (int q = tid; q < p; q += nt) {
+          const float2 t0 = A[cc * lda + q];
+          A[cc * lda + q] = A[br * lda + q];
+          A[br * lda + q] = t0;
+        }
+      __syncthreads();
+      const float2 rp = crecipf(A[cc * lda + cc]);
+      for (int r = cc + 1 + tid; r < p; r += nt) A[r * lda + cc] = cmulf(A[r * lda + cc], rp);
+      __syncthreads();
+      // trailing update: warps over rows, lanes over columns (the pivot row's entries in registers)
+      float2 u[kEv3MaxP / 32];
+#pragma unroll
+      for (int j = 0; j < kEv3MaxP / 32; ++j) {
+        const int q = cc + 1 + lane + 32 * j;
+        u[j] = q < p ? A[cc * lda + q] : make_float2(0.f, 0.f);
+      }
+      for (int r = cc + 1 + warp; r < p; r += nw) {
+        const float2 l = A[r * lda + cc];
+#pragma unroll
+        for (int j = 0; j < kEv3MaxP / 32; ++j) {
+          const int q = cc + 1 + lane + 32 * j;
+          if (q < p) {
+            float2 e = A[r * lda + q];
+            e.x = fmaf(-l.x, u[j].x, fmaf(l.y, u[j].y, e.x));
+            e.y = fmaf(-l.x, u[j].y, fmaf(-l.y, u[j].x, e.y));
+            A[r * lda + q] = e;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (s_bad) {
+      if (tid == 0) dfom[c] = -INFINITY;
+      __syncthreads();
+      continue;
+    }
+    // y0 = A^{-1} b with the FP32 factors
+    if (warp == 0) {
+      for (int t = lane; t < p; t += 32) w[t] = make_float2((float)b[t].re, (float)b[t].im);
+      __syncwarp();
+      lu32_solve_warp(A, lda, piv, p, w);
+      for (int t = lane; t < p; t += 32) y[t] = mk((double)w[t].x, (double)w[t].y);
+    }
+    __syncthreads();
+    // refinement: rv = b - A y in FP64 (A y = y - G_VV D y), then y += A^{-1} rv
+    for (int r = warp; r < p; r += nw) {
+      const float2* Grow = G + (int64_t)V[r] * a.ldg;
+      double sx = 0.0, sy = 0.0;
+      for (int q = lane; q < p; q += 32) {
+        const float2 gv = Grow[V[q]];
+        const double gx = D[q] * (double)gv.x, gy = D[q] * (double)gv.y;
+        sx = fma(gx, y[q].re, fma(-gy, y[q].im, sx));
+        sy = fma(gx, y[q].im, fma(gy, y[q].re, sy));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      }
+      if (lane == 0) rv[r] = mk(b[r].re - y[r].re + sx, b[r].im - y[r].im + sy);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int t = lane; t < p; t += 32) w[t] = make_float2((float)rv[t].re, (float)rv[t].im);
+      __syncwarp();
+      lu32_solve_warp(A, lda, piv, p, w);
+      double dmax = 0.0, ymax = 0.0;
+      for (int t = lane; t < p; t += 32) {
+        const cplx yn = mk(y[t].re + (double)w[t].x, y[t].im + (double)w[t].y);
+        y[t] = yn;
+        dmax = fmax(dmax, fmax(fabs((double)w[t].x), fabs((double)w[t].y)));
+        ymax = fmax(ymax, fmax(fabs(yn.re), fabs(yn.im)));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+      }
+      if (lane == 0 && !(dmax <= 0x1p-10 * ymax)) s_bad = 1;
+    }
+    __syncthreads();
+    if (s_bad) {
+      if (tid == 0) dfom[c] = -INFINITY;
+      __syncthreads();
+      continue;
+    }
+    double df = 0.0;
+    for (int mc = 0; mc < 3; ++mc) {                 // Eq. 4 at the monitor, |E|^2 over components
+      const int64_t m = 3 * g.N + mc;
+      cplx part = mk(0.0, 0.0);
+      for (int u = tid; u < p; u += nt) part = part + D[u] * (ldG(a.G, a.dtype, a.ldg, m, V[u]) * y[u]);
+      const cplx dE = block_sum(part, s_c);
+      const cplx Em = a.E[m];
+      df += abs2(Em + dE) - abs2(Em);
+    }
+    if (tid == 0) dfom[c] = df;
+    __syncthreads();
+  }
+}
+
 static gf_status check3(gf_handle* h, const gf_geom3d* g) {
   if (!g) return api_fail_msg(h, GF_EINVAL, "geometry is NULL");
   if (g->nx < 2 || g->ny < 2 || g->nz < 1 || g->nz > 8)
@@ -464,7 +690,8 @@ gf_status gf3_eval_candidates(gf_handle* h, const gf_problem3d* prob, int32_t dt
   a.ldg = prob->ldg;
   a.E = reinterpret_cast<const gf::cplx*>(prob->E);
   const int p = 12 * prob->geom.nz;
-  const size_t smem = sizeof(gf::cplx) * (size_t)p * p;
+  const bool f32 = dtype == GF_C64 && gf::api_update_algo(h) == GF_UPDATE_TC;
+  const size_t smem = f32 ? sizeof(float2) * (size_t)p * (p + 1) : sizeof(gf::cplx) * (size_t)p * p;
   {
     static std::mutex mu;
     static bool done[64] = {};
@@ -474,13 +701,27 @@ gf_status gf3_eval_candidates(gf_handle* h, const gf_problem3d* prob, int32_t dt
     if (dev < 0 || dev >= 64 || !done[dev]) {
       cudaFuncSetAttribute(gf::k_eval_pillar, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(gf::cplx) * gf::kEv3MaxP * gf::kEv3MaxP));
+      cudaFuncSetAttribute(gf::k_eval_pillar_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(float2) * gf::kEv3MaxP * (gf::kEv3MaxP + 1)));
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
   const int64_t ncand = gf3_num_candidates(&prob->geom);
-  const int grid = (int)(ncand < (int64_t)gf::api_sm_count(h) * 8 ? ncand : (int64_t)gf::api_sm_count(h) * 8);
-  gf::k_eval_pillar<<<grid, gf::kEv3Threads, smem, (cudaStream_t)stream>>>(a, state, spec->dir_mask, spec->aligned,
-                                                                           ncand, dfom);
+  int per_sm = 8;
+  if (f32 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::k_eval_pillar_f32, gf::kEv3Threads, smem) !=
+                  cudaSuccess ||
+              per_sm < 1)) {
+    cudaGetLastError();
+    per_sm = 4;
+  }
+  const int64_t cap = (int64_t)gf::api_sm_count(h) * per_sm;
+  const int grid = (int)(ncand < cap ? ncand : cap);
+  if (f32)
+    gf::k_eval_pillar_f32<<<grid, gf::kEv3Threads, smem, (cudaStream_t)stream>>>(a, state, spec->dir_mask,
+                                                                                 spec->aligned, ncand, dfom);
+  else
+    gf::k_eval_pillar<<<grid, gf::kEv3Threads, smem, (cudaStream_t)stream>>>(a, state, spec->dir_mask, spec->aligned,
+                                                                             ncand, dfom);
   return gf::api_cuda_check(h, "gf3_eval_candidates launch");
 }
 

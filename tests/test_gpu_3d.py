@@ -126,3 +126,32 @@ def test_aligned_pillars_match_oracle():
         opt.update()
         torch.cuda.synchronize()
         assert np.array_equal(opt.state.cpu().numpy(), orc.state)
+
+
+@pytest.mark.parametrize("nx,ny,nz,steps", [(24, 20, 4, 6), (17, 13, 2, 4)])
+def test_c64_eval_fp32_factors_refined_match_fp64_factors(nx, ny, nz, steps):
+    """Complex64 G: the pillar evaluation with FP32 factors and one FP64 refinement step
+    (GF_UPDATE_TC) against FP64 factors of the same stored system (GF_UPDATE_DFMA), on every
+    candidate after a few greedy steps: the refined solve reaches the FP64 solve of the stored
+    matrix (both read the same FP32 entries), well inside the storage rounding of G."""
+    wl = W.small_3d(nx, ny, nz, dtype="c64")
+    opt = GreedyOptimizer3D(wl.geoms[0], wl.spec, dtype="c64")
+    opt.fill()
+    for _ in range(steps):
+        opt.step()
+    torch.cuda.synchronize()
+    assert int(opt.status.cpu()[0]) == B.GF_OK
+    opt.evaluate()
+    d32 = opt.dfom.cpu().numpy().copy()
+    opt.h.gf_set_update_algo(B.GF_UPDATE_DFMA)
+    opt.evaluate()
+    d64 = opt.dfom.cpu().numpy().copy()
+    opt.h.gf_set_update_algo(B.GF_UPDATE_TC)
+    fin = np.isfinite(d64)
+    assert fin.sum() > 0.4 * fin.size
+    assert np.array_equal(fin, np.isfinite(d32))
+    scale = float(np.max(np.abs(d64[fin])))
+    err = float(np.max(np.abs(d32[fin] - d64[fin])))
+    print(f"max |dFOM(FP32 factors + refinement) - dFOM(FP64 factors)| = {err:.3e} (scale {scale:.3e})")
+    assert err <= 1e-9 * scale
+    assert int(np.argmax(np.where(fin, d32, -np.inf))) == int(np.argmax(np.where(fin, d64, -np.inf)))
