@@ -535,7 +535,7 @@ def run_native(args):
         f16_peak, f16_kind = f16_peak_tflops()
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
                 "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind,
-                "kernel": "k_rank_update_c64_ra (p <= 64: resident A blocks) / k_rank_update_c64_tc_t (p > 64: "
+                "kernel": "k_rank_update_c64_ra (p <= 48: resident A blocks) / k_rank_update_c64_tc_t (p > 48: "
                           "streaming, 2-CTA clusters); tcgen05 kind::f16, scaled split-FP16, 3 products; "
                           "+ D A^-1 + S GEMM + operand prep",
                 "tensor_achieved_tflops": achieved_tfl, "tensor_peak_tflops": f16_peak, "tensor_peak_kind": f16_kind,
@@ -552,8 +552,8 @@ def run_native(args):
         upd = 3 if pmax <= 4 else 1                # digit prep rows + cols + tensor-core update, or DFMA
     else:
         # FP32 stream, or inverse + S GEMM + prep + the resident-A update (+ the streaming update
-        # where the workspace allows p > 64; it returns at once when p <= 64)
-        upd = 1 if pmax <= 4 else (4 if pmax <= 64 else 5)
+        # where the workspace allows p > 48; it returns at once when p <= 48)
+        upd = 1 if pmax <= 4 else (4 if pmax <= 48 else 5)
     per_step_launches = 4 + sel + nlam * (upd + 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,

@@ -376,6 +376,26 @@ __device__ __forceinline__ float2 crecipf(float2 b) {
   return make_float2(b.x * s, -b.y * s);
 }
 
+// block-wide (max value, lowest index on ties) in FP32 (the pivot search of the FP32 factors)
+__device__ __forceinline__ void block_argmax_f(float& v, int& idx, float* sv, int* si) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_down_sync(0xffffffffu, v, o);
+    const int oi = __shfl_down_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if (lane == 0) { sv[w] = v; si[w] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < nw; ++q)
+      if (sv[q] > sv[0] || (sv[q] == sv[0] && si[q] < si[0])) { sv[0] = sv[q]; si[0] = si[q]; }
+  }
+  __syncthreads();
+  v = sv[0];
+  idx = si[0];
+  __syncthreads();
+}
+
 // w <- U^{-1} L^{-1} P w for the factors in A (row stride lda, unit lower L below the
 // diagonal, row interchanges piv); one warp, row-oriented dot products
 __device__ __forceinline__ void lu32_solve_warp(const float2* A, int lda, const int* piv, int p, float2* w) {
@@ -427,7 +447,7 @@ __global__ void __launch_bounds__(kEv3Threads) k_eval_pillar_f32(Ev3Args a, cons
   __shared__ int piv[kEv3MaxP];
   __shared__ double D[kEv3MaxP];
   __shared__ int s_p;
-  __shared__ double s_v[kEv3Threads / 32];
+  __shared__ float s_v[kEv3Threads / 32];
   __shared__ int s_i[kEv3Threads / 32];
   __shared__ cplx s_c[kEv3Threads / 32];
   __shared__ int s_bad;
@@ -449,38 +469,40 @@ __global__ void __launch_bounds__(kEv3Threads) k_eval_pillar_f32(Ev3Args a, cons
       __syncthreads();
       continue;
     }
-    // A = I - G_VV D: each entry in FP64 from the stored FP32 value, then rounded to FP32
+    // A = I - G_VV D in FP32 (only the factors use it; the refinement residual below forms
+    // its entries again in FP64)
     for (int r = warp; r < p; r += nw) {
       const float2* Grow = G + (int64_t)V[r] * a.ldg;
       for (int q = lane; q < p; q += 32) {
         const float2 gv = Grow[V[q]];
-        A[r * lda + q] = make_float2((float)((r == q ? 1.0 : 0.0) - D[q] * (double)gv.x), (float)(-D[q] * (double)gv.y));
+        const float dq = (float)D[q];
+        A[r * lda + q] = make_float2(fmaf(-dq, gv.x, r == q ? 1.f : 0.f), -dq * gv.y);
       }
     }
     for (int t = tid; t < p; t += nt) b[t] = a.E[V[t]];
     __syncthreads();
-    double rs = 0.0;
+    float rs = 0.f;
     for (int r = tid; r < p; r += nt) {
       float s = 0.f;
       for (int q = 0; q < p; ++q) {
         const float2 e = A[r * lda + q];
         s += sqrtf(fmaf(e.x, e.x, e.y * e.y));
       }
-      rs = fmax(rs, (double)s);
+      rs = fmaxf(rs, s);
     }
     int dummy = 0;
-    block_argmax(rs, dummy, s_v, s_i);
-    const double thresh = kSingularRel * rs;
+    block_argmax_f(rs, dummy, s_v, s_i);
+    const float thresh = (float)kSingularRel * rs;
     for (int cc = 0; cc < p; ++cc) {
-      double bv = -1.0;
+      float bv = -1.f;
       int br = 0x7fffffff;
       for (int r = cc + tid; r < p; r += nt) {
         const float2 e = A[r * lda + cc];
-        const double m = (double)sqrtf(fmaf(e.x, e.x, e.y * e.y));
+        const float m = sqrtf(fmaf(e.x, e.x, e.y * e.y));
         if (m > bv) { bv = m; br = r; }
       }
-      block_argmax(bv, br, s_v, s_i);
-      if (!(bv >= thresh) || !(bv > 0.0)) {
+      block_argmax_f(bv, br, s_v, s_i);
+      if (!(bv >= thresh) || !(bv > 0.f)) {
         if (tid == 0) s_bad = 1;
         break;
       }

@@ -549,9 +549,9 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
   if (warp == kWarpMma) tc::tmem_dealloc(tbase, kC64TmemCols);
 }
 
-// ---- resident-A form: joint rank p <= 64 (K <= 128 real) ------------------------------------
+// ---- resident-A form: joint rank p <= 48 (K <= 96 real) -------------------------------------
 // Each CTA owns one row tile at a time and sweeps a run of its column tiles.  The row tile's A
-// blocks (nkr x 16 KB, at most 64 KB) are loaded once per run and stay in shared memory, so per
+// blocks (nkr x 16 KB, at most 48 KB) are loaded once per run and stay in shared memory, so per
 // tile only the B blocks (nkr x 16 KB, a ring of 16 KB stages) and the G tile move: half the
 // operand bytes of the streaming form above.  Runs: the row tiles are taken in groups of
 // gridDim.x; in a full group CTA b takes row tile b of the group across every column tile, all
@@ -559,7 +559,9 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
 // about the same time); in the last group of R < gridDim.x row tiles each row is split into
 // gridDim.x / R column segments.  Before it retires, every role waits (bounded) for the copies
 // and MMAs it issued, so a CTA that gave up on a wait leaves nothing in flight.
-constexpr int kRaMaxK = 4;                                   // A chunks that fit next to the ring
+// A chunks kept resident: K <= 96 real (p <= 48).  At four chunks (64 KB of A) only two B stages
+// would fit beside the four G stages, too few to cover the L2 latency: p > 48 streams instead.
+constexpr int kRaMaxK = 3;
 constexpr int kRaOps = kC64NSO * kC64OpStage;                // 96 KB: A blocks + B ring
 constexpr int kRaMaxB = kRaOps / kC64Block - 1;              // B stages when nkr = 1
 constexpr uint64_t kRaDrainNs = 100000000ull;
@@ -961,8 +963,8 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
       c2 = clusters2[dev];
     }
   }
-  // joint rank p <= 64 (decided on the device): the resident-A form; larger p: a streaming form,
-  // launched only where the workspace allows p > 64 (each returns at once when the other applies)
+  // joint rank p <= 48 (decided on the device): the resident-A form; larger p: a streaming form,
+  // launched only where the workspace allows p > 48 (each returns at once when the other applies)
   {
     const int64_t tiles = o.nrt * o.nct;
     const int grid = (int)(tiles < sm_count ? tiles : sm_count);

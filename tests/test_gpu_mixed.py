@@ -37,8 +37,8 @@ def _force(opt, ids, k):
     opt.status.zero_()
 
 
-# joint ranks: k = 4 and 16 stay within p <= 64 (the resident-A update); k = 32 accepts 32
-# brushes per step here (p up to 128: the streaming update)
+# joint ranks: k = 4 stays within p <= 16 (the resident-A update), k = 16 reaches p = 64 and k = 32
+# accepts 32 brushes per step here (p up to 128): both forms of the update run
 @pytest.mark.parametrize("nx,ny,k,seed,steps", [(20, 18, 4, 51, 4), (33, 29, 16, 52, 3), (12, 10, 1, 53, 6),
                                                 (40, 36, 32, 55, 2)])
 def test_c64_lockstep_error_vs_fp64_oracle(nx, ny, k, seed, steps):
