@@ -184,3 +184,42 @@ def test_batch_48_full_size_sampled_problems():
         assert rel_err(opt.E[0].cpu().numpy(), lazy.E) <= TOL, i
         assert abs(float(opt.fom.cpu()[0]) - lazy.fom()) <= TOL * lazy.fom()
         _sampled_G(opt, [lazy], rng, TOL)
+
+
+def test_resident_a_update_groups_and_segments_lockstep():
+    """215x215 brushes, top-8 (joint rank <= 32: every update in the resident-A form), complex64
+    G = 17 GB, three lock-step steps against the deferred FP64 oracle.  n = 46226 gives 362 row
+    tiles: two full groups of 152 (each CTA one row tile across all 723 column tiles, the CTAs in
+    step) and a last group of 58 row tiles cut into two column segments each -- every tile
+    schedule of the kernel at a size the oracle still samples quickly."""
+    g = W.small(215, 215, kind=W.KIND_BRUSH2, dir_mask=3, k=8, excl_radius=3, dtype="c64").geoms[0]
+    spec = W.CandidateSpec(W.KIND_BRUSH2, 3, 8, 3)
+    assert g.N + 1 == 46226
+    lazy = LowRankProblem(g, spec)
+    opt = GreedyOptimizer((g,), spec, dtype="c64")
+    opt.fill()
+    rng = np.random.default_rng(4215)
+    for t in range(3):
+        opt.evaluate()
+        d_orc = lazy.evaluate()
+        d_gpu = opt.dfom.cpu().numpy()
+        fin = np.isfinite(d_orc)
+        assert np.array_equal(fin, np.isfinite(d_gpu))
+        scale = max(1.0, float(np.max(np.abs(d_orc[fin]))))
+        assert np.max(np.abs(d_gpu[fin] - d_orc[fin])) <= C64_DFOM * scale, t
+        ids = lazy.choose(d_orc)
+        assert ids
+        _force(opt, ids, spec.k)
+        opt.update()
+        lazy.accept(ids)
+        torch.cuda.synchronize()
+        assert int(opt.status.cpu()[0]) == B.GF_OK
+        assert np.array_equal(opt.state.cpu().numpy(), lazy.state), t
+        assert rel_err(opt.E[0].cpu().numpy(), lazy.E) <= C64_TOL, t
+        assert abs(float(opt.fom.cpu()[0]) - lazy.fom()) <= C64_TOL * lazy.fom()
+        _sampled_G(opt, [lazy], rng, C64_TOL)
+        # whole rows in each part of the schedule: full groups, and the segmented last group
+        rows = np.array([5, 128 * 151 + 3, 128 * 200 + 77, 128 * 310 + 1, g.N])
+        Gr = opt.G[0][torch.as_tensor(rows, device="cuda"), :g.N + 1].cpu().numpy().astype(np.complex128)
+        Gl = lazy.rows(rows)
+        assert np.max(np.abs(Gr - Gl)) <= C64_TOL * float(np.max(np.abs(Gl))), t
