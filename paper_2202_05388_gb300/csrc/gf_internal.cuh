@@ -114,12 +114,15 @@ __device__ __forceinline__ int cand_pixels(int64_t c, int kind, int dir_mask, in
 
 // ----------------------------------------------------------------------------- workspace
 // Per-step control block written by the capacitance kernel, read by the panel/update kernels.
+constexpr int kMaxLamCtl = 8;  // wavelengths per problem (kMaxLam)
 struct UpdCtl {
   int32_t skip;       // 1: nothing is applied this step
   int32_t nv;         // number of flipped pixels (0 < nv <= pmax)
   int32_t ncand;      // number of candidates applied
   int32_t pad;
   double joint_dfom;  // dFOM of the applied set (FP64)
+  double lam_df[kMaxLamCtl];     // per-wavelength dFOM of the joint set (parallel capacitance solve)
+  int32_t lam_bad[kMaxLamCtl];   // per-wavelength singular flag (parallel capacitance solve)
 };
 
 struct WsLayout {
@@ -180,6 +183,7 @@ struct EvalLam {     // one wavelength as seen by the candidate kernels
   const cplx* bands;
 };
 constexpr int kMaxLam = 8;
+static_assert(kMaxLam == kMaxLamCtl, "control block sized for every wavelength");
 struct EvalArgs {
   int nlam;
   int dtype;

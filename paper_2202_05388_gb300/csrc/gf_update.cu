@@ -9,6 +9,8 @@
 //   k_finish      : E <- E + C0 (D y) (Eq. 4), state flip, FOM = sum |E_N|^2.
 #include <math.h>
 
+#include <mutex>
+
 #include "gf_internal.cuh"
 
 namespace gf {
@@ -31,14 +33,14 @@ struct CapArgs {
 // zero or below thresh.
 constexpr int kLuNB = 8;
 constexpr int kLuMaxBlocked = 256;
+constexpr int kCapSmemP = 64;          // capacitance systems up to this size in shared memory (64 KB)
 
 // sP: shared memory for kLuMaxBlocked x kLuNB entries (the panel, row-major [row][j])
 __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ piv, double thresh, cplx* sP) {
   __shared__ int s_pv[kLuNB];
   __shared__ int s_bad2, s_pr;
-  __shared__ double s_bv2[32];
-  __shared__ int s_br2[32];
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  __shared__ cplx s_inv;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_bad2 = 0;
   __syncthreads();
   for (int c0 = 0; c0 < p; c0 += kLuNB) {
@@ -49,30 +51,34 @@ __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ pi
       sP[r * kLuNB + j] = A[(int64_t)(c0 + r) * p + c0 + j];
     }
     __syncthreads();
-    // ---- panel factorisation in shared memory
+    // ---- panel factorisation in shared memory.  The pivot search is one warp's: the largest
+    // |a|^2 (the order of the moduli), lowest row on ties; its lane 0 also forms 1 / pivot, so
+    // each row's multiplier is a product instead of a division.
     for (int j = 0; j < nb; ++j) {
-      double bv = -1.0;
-      int br = 0x7fffffff;
-      for (int r = j + tid; r < m; r += nt) {
-        const double v = cabs1(sP[r * kLuNB + j]);
-        if (v > bv) { bv = v; br = r; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-        const int orr = __shfl_down_sync(0xffffffffu, br, o);
-        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-      }
-      if (lane == 0) { s_bv2[wid] = bv; s_br2[wid] = br; }
-      __syncthreads();
-      if (tid == 0) {
-        double b = s_bv2[0];
-        int r = s_br2[0];
-        for (int w = 1; w < nw; ++w)
-          if (s_bv2[w] > b || (s_bv2[w] == b && s_br2[w] < r)) { b = s_bv2[w]; r = s_br2[w]; }
-        if (!(b >= thresh) || !(b > 0.0)) s_bad2 = 1;
-        s_pr = r;
-        s_pv[j] = c0 + r;
-        piv[c0 + j] = c0 + r;
+      if (wid == 0) {
+        double bv = -1.0;
+        int br = 0x7fffffff;
+        for (int r = j + lane; r < m; r += 32) {
+          const double v = abs2(sP[r * kLuNB + j]);
+          if (v > bv) { bv = v; br = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+          const int orr = __shfl_down_sync(0xffffffffu, br, o);
+          if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+        }
+        if (lane == 0) {
+          if (!(bv >= thresh * thresh) || !(bv > 0.0)) {
+            s_bad2 = 1;
+          } else {
+            const cplx pv = sP[br * kLuNB + j];
+            const double d = 1.0 / bv;
+            s_inv = mk(pv.re * d, -pv.im * d);
+          }
+          s_pr = br;
+          s_pv[j] = c0 + br;
+          piv[c0 + j] = c0 + br;
+        }
       }
       __syncthreads();
       if (s_bad2) return false;
@@ -83,9 +89,9 @@ __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ pi
         sP[pr * kLuNB + tid] = t0;
       }
       __syncthreads();
-      const cplx pv = sP[j * kLuNB + j];
+      const cplx inv = s_inv;
       for (int r = j + 1 + tid; r < m; r += nt) {
-        const cplx f = cdiv(sP[r * kLuNB + j], pv);
+        const cplx f = sP[r * kLuNB + j] * inv;
         sP[r * kLuNB + j] = f;
         for (int k = j + 1; k < nb; ++k) sP[r * kLuNB + k] = sP[r * kLuNB + k] - f * sP[j * kLuNB + k];
       }
@@ -150,17 +156,182 @@ __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ pi
   return true;
 }
 
-// Single CTA.  The p x p matrices live in the workspace (p can reach 4k).
+// One wavelength of the capacitance solve for the set V (p pixels, contrasts dchi): A = I - G_VV D
+// (Eq. 9), its LU with partial pivoting, y = A^{-1} E_V and the dFOM of Eq. 4 at the monitor into
+// *df (every thread); the factors, pivots and D y go to the wavelength's workspace slots.  With sA
+// (shared memory for kCapSmemP^2 + kCapSmemP entries) a system of p <= kCapSmemP and its
+// right-hand side are built, factorised and solved there and copied to the workspace once.
+// Returns false (in every thread) when A is singular.
+__device__ bool cap_lam(const CapArgs& a, const WsLayout& L, char* ws, int l, int p, const int32_t* __restrict__ V,
+                        const double* __restrict__ dchi, cplx* sA, double* df_out) {
+  __shared__ double s_red[32];
+  const int tid = threadIdx.x;
+    const UpdLam& U = a.u.lam[l];
+    cplx* Aw = reinterpret_cast<cplx*>(ws + L.lu + l * L.lu_s);
+    const bool in_smem = sA && p <= kCapSmemP;
+    cplx* A = in_smem ? sA : Aw;
+    int32_t* piv = reinterpret_cast<int32_t*>(ws + L.piv + l * L.piv_s);
+    cplx* yw = reinterpret_cast<cplx*>(ws + L.yd + l * L.yd_s);
+    cplx* y = in_smem ? sA + kCapSmemP * kCapSmemP : yw;
+    // A = I - G_VV D, row-major p x p;  y = E_V
+    for (int t = tid; t < p * p; t += blockDim.x) {
+      int r = t / p, c = t % p;
+      cplx g = ldG(U.G, a.u.dtype, U.ldg, V[r], V[c]);
+      cplx e = mk(r == c ? 1.0 : 0.0, 0.0);
+      A[t] = e - dchi[c] * g;
+    }
+    for (int t = tid; t < p; t += blockDim.x) y[t] = U.E[V[t]];
+    __syncthreads();
+    // ||A||_inf
+    double rs = 0.0;
+    for (int r = tid; r < p; r += blockDim.x) {
+      double s = 0.0;
+      for (int c = 0; c < p; ++c) s += cabs1(A[r * p + c]);
+      rs = fmax(rs, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) rs = fmax(rs, __shfl_down_sync(0xffffffffu, rs, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = rs;
+    __syncthreads();
+    if (tid == 0) {
+      double m = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[w]);
+      s_red[0] = m;
+    }
+    __syncthreads();
+    const double thresh = kSingularRel * s_red[0];
+    __syncthreads();
+    // LU with partial pivoting (row-major, in place; L below the diagonal, unit diagonal).
+    __shared__ int s_piv;
+    __shared__ int s_bad;
+    __shared__ double s_bv[32];
+    __shared__ int s_br[32];
+    __shared__ cplx s_f[kLuMaxBlocked * kLuNB];   // blocked: the panel; unblocked: multipliers
+    if (tid == 0) s_bad = 0;
+    const int nw = (int)(blockDim.x >> 5), lane = tid & 31, wid = tid >> 5;
+    if (p <= kLuMaxBlocked) {
+      if (!lu_blocked(A, p, piv, thresh, s_f)) return false;
+      // y = P E_V, then the unit-lower solve (column-oriented: one synchronisation per column)
+      if (tid == 0)
+        for (int c = 0; c < p; ++c) {
+          const int r = piv[c];
+          if (r != c) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
+        }
+      __syncthreads();
+      for (int c = 0; c < p; ++c) {
+        const cplx yc = y[c];
+        for (int r = c + 1 + tid; r < p; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
+        __syncthreads();
+      }
+    } else {
+      // unblocked form for very large joint sets (p > 256): pivot search across the block,
+      // multipliers per row, trailing update with a warp per row and lanes along the columns
+      for (int c = 0; c < p; ++c) {
+        double bv = -1.0;
+        int br = 0x7fffffff;
+        for (int rr = c + tid; rr < p; rr += blockDim.x) {
+          const double m = cabs1(A[rr * p + c]);
+          if (m > bv) { bv = m; br = rr; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+          const int orr = __shfl_down_sync(0xffffffffu, br, o);
+          if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+        }
+        if (lane == 0) { s_bv[wid] = bv; s_br[wid] = br; }
+        __syncthreads();
+        if (tid == 0) {
+          double b = s_bv[0];
+          int r = s_br[0];
+          for (int w = 1; w < nw; ++w)
+            if (s_bv[w] > b || (s_bv[w] == b && s_br[w] < r)) { b = s_bv[w]; r = s_br[w]; }
+          if (!(b >= thresh) || !(b > 0.0)) s_bad = 1;
+          s_piv = r;
+          piv[c] = r;
+        }
+        __syncthreads();
+        const int r = s_piv;
+        if (s_bad) break;
+        if (r != c) {
+          for (int v = tid; v < p; v += blockDim.x) {
+            cplx t0 = A[c * p + v];
+            A[c * p + v] = A[r * p + v];
+            A[r * p + v] = t0;
+          }
+          if (tid == 0) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
+        }
+        __syncthreads();
+        const cplx pv = A[c * p + c];
+        const cplx yc = y[c];
+        for (int rr = c + 1 + tid; rr < p; rr += blockDim.x) {
+          const cplx f = cdiv(A[rr * p + c], pv);
+          s_f[rr] = f;
+          A[rr * p + c] = f;
+          y[rr] = y[rr] - f * yc;
+        }
+        __syncthreads();
+        for (int rr = c + 1 + wid; rr < p; rr += nw) {
+          const cplx f = s_f[rr];
+          for (int v = c + 1 + lane; v < p; v += 32) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
+        }
+        __syncthreads();
+      }
+      __syncthreads();
+      if (s_bad) return false;
+    }
+    // upper solve for y (column-oriented: one synchronisation per column)
+    for (int c = p - 1; c >= 0; --c) {
+      if (tid == 0) y[c] = cdiv(y[c], A[c * p + c]);
+      __syncthreads();
+      const cplx yc = y[c];
+      for (int r = tid; r < c; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
+      __syncthreads();
+    }
+    // Eq. 4 at the monitor's unknowns (Eq. 1): the gathers of the monitor row are spread over
+    // the block and reduced
+    double df = 0.0;
+    for (int mc = 0; mc < a.u.mcount; ++mc) {
+      const int64_t m = a.u.mrow + mc;
+      cplx part = mk(0.0, 0.0);
+      for (int u = tid; u < p; u += blockDim.x) part = part + dchi[u] * (ldG(U.G, a.u.dtype, U.ldg, m, V[u]) * y[u]);
+      for (int o = 16; o > 0; o >>= 1) {
+        part.re += __shfl_down_sync(0xffffffffu, part.re, o);
+        part.im += __shfl_down_sync(0xffffffffu, part.im, o);
+      }
+      if (lane == 0) { s_bv[wid] = part.re; s_red[wid] = part.im; }
+      __syncthreads();
+      if (tid == 0) {
+        cplx dE = mk(0.0, 0.0);
+        for (int w = 0; w < nw; ++w) dE = dE + mk(s_bv[w], s_red[w]);
+        const cplx EN = U.E[m];
+        df += abs2(EN + dE) - abs2(EN);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) s_red[0] = df;
+    for (int u = tid; u < p; u += blockDim.x) y[u] = dchi[u] * y[u];      // D y for the field update
+    if (in_smem) {                                 // the factors and D y for the later kernels
+      for (int t = tid; t < p * p; t += blockDim.x) Aw[t] = A[t];
+      for (int t = tid; t < p; t += blockDim.x) yw[t] = y[t];
+    }
+    __syncthreads();
+  *df_out = s_red[0];
+  __syncthreads();
+  return true;
+}
+
+// Single CTA: the set V of the accepted candidates, every wavelength's solve (cap_lam; with pre,
+// the first attempt's solves were done by k_capacitance_lam and are read from the control block),
+// the joint decision and the fallback to the best single candidate.  The p x p matrices live in
+// the workspace (p can reach 4k), or in sA for p <= kCapSmemP.
 __device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayout& L, char* ws,
                                                  const uint8_t* __restrict__ state,
-                                                 const int32_t* __restrict__ idx, int32_t* status) {
+                                                 const int32_t* __restrict__ idx, int32_t* status,
+                                                 cplx* sA = nullptr, bool pre = false) {
   UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
   int32_t* V = reinterpret_cast<int32_t*>(ws + L.V);
   double* dchi = reinterpret_cast<double*>(ws + L.dchi);
   __shared__ int s_nv, s_ncand, s_fail;
-  __shared__ double s_red[32];
   const int tid = threadIdx.x;
-  const int64_t N = (int64_t)a.u.nx * a.u.ny;
 
   if (tid == 0) {
     s_fail = 0;
@@ -199,149 +370,15 @@ __device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayou
     double total = 0.0;
     bool singular = false;
     for (int l = 0; l < a.u.nlam; ++l) {
-      const UpdLam& U = a.u.lam[l];
-      cplx* A = reinterpret_cast<cplx*>(ws + L.lu + l * L.lu_s);
-      int32_t* piv = reinterpret_cast<int32_t*>(ws + L.piv + l * L.piv_s);
-      cplx* y = reinterpret_cast<cplx*>(ws + L.yd + l * L.yd_s);
-      // A = I - G_VV D, row-major p x p;  y = E_V
-      for (int t = tid; t < p * p; t += blockDim.x) {
-        int r = t / p, c = t % p;
-        cplx g = ldG(U.G, a.u.dtype, U.ldg, V[r], V[c]);
-        cplx e = mk(r == c ? 1.0 : 0.0, 0.0);
-        A[t] = e - dchi[c] * g;
-      }
-      for (int t = tid; t < p; t += blockDim.x) y[t] = U.E[V[t]];
-      __syncthreads();
-      // ||A||_inf
-      double rs = 0.0;
-      for (int r = tid; r < p; r += blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < p; ++c) s += cabs1(A[r * p + c]);
-        rs = fmax(rs, s);
-      }
-      for (int o = 16; o > 0; o >>= 1) rs = fmax(rs, __shfl_down_sync(0xffffffffu, rs, o));
-      if ((tid & 31) == 0) s_red[tid >> 5] = rs;
-      __syncthreads();
-      if (tid == 0) {
-        double m = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[w]);
-        s_red[0] = m;
-      }
-      __syncthreads();
-      const double thresh = kSingularRel * s_red[0];
-      __syncthreads();
-      // LU with partial pivoting (row-major, in place; L below the diagonal, unit diagonal).
-      __shared__ int s_piv;
-      __shared__ int s_bad;
-      __shared__ double s_bv[32];
-      __shared__ int s_br[32];
-      __shared__ cplx s_f[kLuMaxBlocked * kLuNB];   // blocked: the panel; unblocked: multipliers
-      if (tid == 0) s_bad = 0;
-      const int nw = (int)(blockDim.x >> 5), lane = tid & 31, wid = tid >> 5;
-      if (p <= kLuMaxBlocked) {
-        if (!lu_blocked(A, p, piv, thresh, s_f)) { singular = true; break; }
-        // y = P E_V, then the unit-lower solve (column-oriented: one synchronisation per column)
-        if (tid == 0)
-          for (int c = 0; c < p; ++c) {
-            const int r = piv[c];
-            if (r != c) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
-          }
-        __syncthreads();
-        for (int c = 0; c < p; ++c) {
-          const cplx yc = y[c];
-          for (int r = c + 1 + tid; r < p; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
-          __syncthreads();
-        }
-      } else {
-        // unblocked form for very large joint sets (p > 256): pivot search across the block,
-        // multipliers per row, trailing update with a warp per row and lanes along the columns
-        for (int c = 0; c < p; ++c) {
-          double bv = -1.0;
-          int br = 0x7fffffff;
-          for (int rr = c + tid; rr < p; rr += blockDim.x) {
-            const double m = cabs1(A[rr * p + c]);
-            if (m > bv) { bv = m; br = rr; }
-          }
-          for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-            const int orr = __shfl_down_sync(0xffffffffu, br, o);
-            if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-          }
-          if (lane == 0) { s_bv[wid] = bv; s_br[wid] = br; }
-          __syncthreads();
-          if (tid == 0) {
-            double b = s_bv[0];
-            int r = s_br[0];
-            for (int w = 1; w < nw; ++w)
-              if (s_bv[w] > b || (s_bv[w] == b && s_br[w] < r)) { b = s_bv[w]; r = s_br[w]; }
-            if (!(b >= thresh) || !(b > 0.0)) s_bad = 1;
-            s_piv = r;
-            piv[c] = r;
-          }
-          __syncthreads();
-          const int r = s_piv;
-          if (s_bad) break;
-          if (r != c) {
-            for (int v = tid; v < p; v += blockDim.x) {
-              cplx t0 = A[c * p + v];
-              A[c * p + v] = A[r * p + v];
-              A[r * p + v] = t0;
-            }
-            if (tid == 0) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
-          }
-          __syncthreads();
-          const cplx pv = A[c * p + c];
-          const cplx yc = y[c];
-          for (int rr = c + 1 + tid; rr < p; rr += blockDim.x) {
-            const cplx f = cdiv(A[rr * p + c], pv);
-            s_f[rr] = f;
-            A[rr * p + c] = f;
-            y[rr] = y[rr] - f * yc;
-          }
-          __syncthreads();
-          for (int rr = c + 1 + wid; rr < p; rr += nw) {
-            const cplx f = s_f[rr];
-            for (int v = c + 1 + lane; v < p; v += 32) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
-          }
-          __syncthreads();
-        }
-        __syncthreads();
-        if (s_bad) { singular = true; break; }
-      }
-      // upper solve for y (column-oriented: one synchronisation per column)
-      for (int c = p - 1; c >= 0; --c) {
-        if (tid == 0) y[c] = cdiv(y[c], A[c * p + c]);
-        __syncthreads();
-        const cplx yc = y[c];
-        for (int r = tid; r < c; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
-        __syncthreads();
-      }
-      // Eq. 4 at the monitor's unknowns (Eq. 1): the gathers of the monitor row are spread over
-      // the block and reduced
       double df = 0.0;
-      for (int mc = 0; mc < a.u.mcount; ++mc) {
-        const int64_t m = a.u.mrow + mc;
-        cplx part = mk(0.0, 0.0);
-        for (int u = tid; u < p; u += blockDim.x) part = part + dchi[u] * (ldG(U.G, a.u.dtype, U.ldg, m, V[u]) * y[u]);
-        for (int o = 16; o > 0; o >>= 1) {
-          part.re += __shfl_down_sync(0xffffffffu, part.re, o);
-          part.im += __shfl_down_sync(0xffffffffu, part.im, o);
-        }
-        if (lane == 0) { s_bv[wid] = part.re; s_red[wid] = part.im; }
-        __syncthreads();
-        if (tid == 0) {
-          cplx dE = mk(0.0, 0.0);
-          for (int w = 0; w < nw; ++w) dE = dE + mk(s_bv[w], s_red[w]);
-          const cplx EN = U.E[m];
-          df += abs2(EN + dE) - abs2(EN);
-        }
-        __syncthreads();
+      if (pre && attempt == 0) {                     // the per-wavelength kernel solved it
+        df = ctl->lam_df[l];
+        if (ctl->lam_bad[l]) { singular = true; break; }
+      } else if (!cap_lam(a, L, ws, l, p, V, dchi, sA, &df)) {
+        singular = true;
+        break;
       }
-      if (tid == 0) s_red[0] = df;
-      for (int u = tid; u < p; u += blockDim.x) y[u] = dchi[u] * y[u];      // D y for the field update
-      __syncthreads();
-      total += s_red[0];
-      __syncthreads();
+      total += df;
     }
     if (singular) {
       if (tid == 0) {
@@ -375,8 +412,42 @@ __device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayou
 }
 
 __global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __restrict__ state,
-                              const int32_t* __restrict__ idx, int32_t* status) {
-  capacitance_body(a, L, ws, state, idx, status);
+                              const int32_t* __restrict__ idx, int32_t* status, int pre) {
+  extern __shared__ __align__(16) unsigned char cap_smem[];
+  capacitance_body(a, L, ws, state, idx, status, L.pmax <= kCapSmemP ? reinterpret_cast<cplx*>(cap_smem) : nullptr,
+                   pre != 0);
+}
+
+// The first attempt's per-wavelength solves of a multi-wavelength step in parallel, one CTA per
+// wavelength (p <= kCapSmemP; each CTA forms the set V again in its shared memory from the same
+// ids): each writes its factors, pivots and D y to its workspace slots and its dFOM and singular
+// flag to the control block; k_capacitance (pre) reads them, decides and runs any fallback.
+__global__ void k_capacitance_lam(CapArgs a, WsLayout L, char* ws, const uint8_t* __restrict__ state,
+                                  const int32_t* __restrict__ idx, const int32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char cap_smem[];
+  __shared__ int32_t sV[kCapSmemP];
+  __shared__ double sD[kCapSmemP];
+  __shared__ int s_nv;
+  UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
+  const int l = blockIdx.x;
+  if (threadIdx.x == 0) {
+    int nv = 0;
+    if (*status == GF_OK)
+      for (int c = 0; c < a.k; ++c) {
+        const int32_t id = idx[c];
+        if (id < 0) break;
+        nv += cand_pixels(id, a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, sV + nv, sD + nv, a.u.nz);
+      }
+    s_nv = nv;
+  }
+  __syncthreads();
+  const int p = s_nv;
+  double df = 0.0;
+  const bool ok = p > 0 ? cap_lam(a, L, ws, l, p, sV, sD, reinterpret_cast<cplx*>(cap_smem), &df) : true;
+  if (threadIdx.x == 0) {
+    ctl->lam_df[l] = df;
+    ctl->lam_bad[l] = ok ? 0 : 1;
+  }
 }
 
 // ----------------------------------------------------------------------------- panels
@@ -774,7 +845,26 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   ca.dir_mask = spec.dir_mask;
   ca.k = spec.k < 1 ? 1 : spec.k;
   ca.pmax = L.pmax;
-  k_capacitance<<<1, 256, 0, st>>>(ca, L, ws, state, idx, status);
+  const size_t cap_smem = L.pmax <= kCapSmemP ? sizeof(cplx) * ((size_t)kCapSmemP * kCapSmemP + kCapSmemP) : 0;
+  {
+    // once per device: the opt-in above the default (48 KB less the static shared memory)
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+      cudaFuncSetAttribute(k_capacitance, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(cplx) * (kCapSmemP * kCapSmemP + kCapSmemP)));
+      cudaFuncSetAttribute(k_capacitance_lam, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(cplx) * (kCapSmemP * kCapSmemP + kCapSmemP)));
+      if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+  }
+  // several wavelengths: their joint solves run side by side, one CTA each
+  const int pre = a.nlam > 1 && L.pmax <= kCapSmemP ? 1 : 0;
+  if (pre) k_capacitance_lam<<<a.nlam, 256, cap_smem, st>>>(ca, L, ws, state, idx, status);
+  k_capacitance<<<1, 256, cap_smem, st>>>(ca, L, ws, state, idx, status, pre);
   const int64_t n = L.n;
   // complex64 on the tensor cores: S is formed from an explicit D A^{-1} by an FP32 GEMM, so
   // the panels kernel only gathers C0
