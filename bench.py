@@ -554,7 +554,8 @@ def run_native(args):
         # FP32 stream, or inverse + S GEMM + prep + the resident-A update (+ the streaming update
         # where the workspace allows p > 48; it returns at once when p <= 48)
         upd = 1 if pmax <= 4 else (4 if pmax <= 48 else 5)
-    per_step_launches = 4 + sel + nlam * (upd + 1)
+    # + the per-wavelength capacitance kernel when several wavelengths share a step (p_max <= 64)
+    per_step_launches = 4 + sel + nlam * (upd + 1) + (1 if nlam > 1 and pmax <= 64 else 0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.dtype == "c128" else "f32",
