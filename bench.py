@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--graph", action="store_true",
                     help="capture the K timed steps in one CUDA graph and time its replay")
+    ap.add_argument("--update-algo", choices=["tc", "dfma", "tensor"], default="tc",
+                    help="arithmetic of the G update (gf_set_update_algo): the fastest form per case "
+                         "(default), FP64 FMA, or the tensor-core forms at every size")
     return ap.parse_args()
 
 
@@ -366,6 +369,8 @@ def run_native(args):
     wl = workload(args.workload)
     g = wl.geoms[0]
     opt = GreedyOptimizer(wl.geoms, wl.spec, dtype=wl.dtype, device=dev)
+    if args.update_algo != "tc":
+        opt.h.gf_set_update_algo(B.GF_UPDATE_DFMA if args.update_algo == "dfma" else B.GF_UPDATE_TENSOR)
     opt.fill()
     torch.cuda.synchronize()
     accepted = torch.zeros(1, dtype=torch.int64, device=f"cuda:{dev}")
@@ -518,7 +523,18 @@ def run_native(args):
     flops_per_launch = kern_flops / max(kern_launches, 1)
     achieved_gbs = bytes_per_launch / (kern_avg_ms * 1e-3) / 1e9
     achieved_tfl = flops_per_launch / (kern_avg_ms * 1e-3) / 1e12
-    if wl.dtype == "c128":
+    pmax_upd = wl.spec.k * (4 if wl.spec.kind == 1 else 1)
+    n_upd = g.N + 1
+    oz = wl.dtype == "c128" and pmax_upd <= 4 and (
+        args.update_algo == "tensor" or (args.update_algo == "tc" and n_upd * n_upd * pmax_upd > 2.5e6))
+    if wl.dtype == "c128" and not oz:
+        # the FP64 FMA kernel: the library's choice for L2-resident problems (n^2 p_max <= 2.5e6)
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
+                "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "k_rank_update_f64 (FP64 FMA)",
+                "note": "G is L2-resident at this size: the launch is latency-bound, not HBM-bound"
+                        if n_upd * n_upd * 16 < 64e6 else "FP64-pipe bound"}
+    elif wl.dtype == "c128":
         tr = measured_traffic(wl.name)
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
                 "frac": achieved_gbs / peak_hbm, "traffic": tr, "peak_kind": peak_kind,
@@ -549,7 +565,7 @@ def run_native(args):
     pmax = wl.spec.k * (4 if wl.spec.kind == 1 else 1)
     sel = 1 if wl.spec.k <= 1 else wl.spec.k + 2
     if wl.dtype == "c128":
-        upd = 3 if pmax <= 4 else 1                # digit prep rows + cols + tensor-core update, or DFMA
+        upd = 3 if oz else 1                       # digit prep rows + cols + tensor-core update, or DFMA
     else:
         # FP32 stream, or inverse + S GEMM + prep + the resident-A update (+ the streaming update
         # where the workspace allows p > 48; it returns at once when p <= 48)
@@ -565,7 +581,8 @@ def run_native(args):
                        "storage": wl.dtype, "k": wl.spec.k, "nlam": nlam,
                        "l2": "inputs larger than L2 (G is %.1f GB per replica)" % (opt.G[0].numel() * opt.G[0].element_size() / 1e9 * nlam),
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "timed_as": "one CUDA-graph replay of the K steps" if args.graph else "K eager steps"},
+                       "timed_as": "one CUDA-graph replay of the K steps" if args.graph else "K eager steps",
+                       "update_algo": args.update_algo},
             "candidate_evals_per_s": opt.ncand * args.steps * world / (t_max / 1e3),
             "g_update_GBps": achieved_gbs,
             "accepted_flips": flips_total,

@@ -199,18 +199,22 @@ gf_status gf_refresh(gf_handle* h, const gf_problem* prob, int32_t dtype, const 
 
 /* Arithmetic of the G update (Eq. 10).  GF_UPDATE_TC (default), the fast form per case:
  *   complex128, p <= 4: exact digit products on the tensor cores with an integer
- *     recombination (FP64-accurate to ~2^-50 of |C0||S|); larger p: native FP64 FMA;
+ *     recombination (FP64-accurate to ~2^-50 of |C0||S|), except on problems with
+ *     n^2 p_max <= 2.5e6 (L2-resident; the persistent tensor-core pipeline's fixed cost
+ *     dominates there), which take native FP64 FMA; larger p: native FP64 FMA;
  *   complex64, p <= 4: FP32 FMA on the CUDA cores (a pure HBM stream);
  *   complex64, 4 < p <= 128: the Woodbury form S = D A^-1 G[V,:] and a scaled split-FP16
  *     tensor-core GEMM with FP32 accumulation.
  * GF_UPDATE_DFMA: native FP64 FMA for every case (complex64 storage rounded once per entry).
+ * GF_UPDATE_TENSOR: as GF_UPDATE_TC, but the tensor-core forms at every problem size.
  * The complex128 forms match the FP64 oracle within 1e-10; they differ only in speed on GB300
  * (whose FP64 pipe is 1/64 of its FP32 rate).  Applies to later gf_apply_update calls on h.
  * For complex64 G the setting also selects the arithmetic of gf3_eval_candidates: GF_UPDATE_TC
- * factorises each pillar's system in FP32 and refines the solution once with an FP64 residual
+ * and GF_UPDATE_TENSOR factorise each pillar's system in FP32 and refines the solution once with an FP64 residual
  * (the accuracy of an FP64 solve of the stored system); GF_UPDATE_DFMA factorises in FP64. */
-#define GF_UPDATE_TC   0
-#define GF_UPDATE_DFMA 1
+#define GF_UPDATE_TC     0
+#define GF_UPDATE_DFMA   1
+#define GF_UPDATE_TENSOR 2
 gf_status gf_set_update_algo(gf_handle* h, int32_t algo);
 
 /* Deferred (low-rank) form, single wavelength, one candidate per step (k = 1), FP64.

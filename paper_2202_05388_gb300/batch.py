@@ -44,6 +44,10 @@ class BatchOptimizer:
         drawing new uniforms across graph replays)."""
         self.device = torch.device("cuda", device)
         self.h = B.Handle(device)
+        # every schedule (fused launches or per-problem stream branches) updates G with the same
+        # arithmetic -- the tensor-core forms the fused launch uses at every size -- so that the
+        # autotuner's choice of schedule cannot change a single bit of the results
+        self.h.gf_set_update_algo(B.GF_UPDATE_TENSOR)
         self.workloads = list(workloads)
         self.opts = [GreedyOptimizer(w.geoms, w.spec, dtype=dtype, device=device, handle=self.h)
                      for w in self.workloads]

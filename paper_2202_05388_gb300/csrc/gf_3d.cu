@@ -712,7 +712,7 @@ gf_status gf3_eval_candidates(gf_handle* h, const gf_problem3d* prob, int32_t dt
   a.ldg = prob->ldg;
   a.E = reinterpret_cast<const gf::cplx*>(prob->E);
   const int p = 12 * prob->geom.nz;
-  const bool f32 = dtype == GF_C64 && gf::api_update_algo(h) == GF_UPDATE_TC;
+  const bool f32 = dtype == GF_C64 && gf::api_update_algo(h) != GF_UPDATE_DFMA;
   const size_t smem = f32 ? sizeof(float2) * (size_t)p * (p + 1) : sizeof(gf::cplx) * (size_t)p * p;
   {
     static std::mutex mu;

@@ -409,7 +409,8 @@ gf_status gf_refresh(gf_handle* h, const gf_problem* prob, int32_t dtype, const 
 
 gf_status gf_set_update_algo(gf_handle* h, int32_t algo) {
   if (!h) return GF_EINVAL;
-  if (algo != GF_UPDATE_TC && algo != GF_UPDATE_DFMA) return fail(h, GF_EINVAL, "unknown update algorithm %d", algo);
+  if (algo != GF_UPDATE_TC && algo != GF_UPDATE_DFMA && algo != GF_UPDATE_TENSOR)
+    return fail(h, GF_EINVAL, "unknown update algorithm %d", algo);
   h->update_algo = algo;
   return GF_OK;
 }

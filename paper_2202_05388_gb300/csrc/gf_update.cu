@@ -34,6 +34,7 @@ struct CapArgs {
 constexpr int kLuNB = 8;
 constexpr int kLuMaxBlocked = 256;
 constexpr int kCapSmemP = 64;          // capacitance systems up to this size in shared memory (64 KB)
+constexpr double kC128SmallWork = 2.5e6;   // n^2 p_max below which the FP64 FMA update is faster
 
 // sP: shared memory for kLuMaxBlocked x kLuNB entries (the panel, row-major [row][j])
 __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ piv, double thresh, cplx* sP) {
@@ -871,8 +872,14 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   struct Map128 { alignas(64) unsigned char b[128]; };
   Map128 maps[kMaxLam];
   // rank <= 4 complex64: an FP32 stream on the CUDA cores (HBM-bound); larger ranks: tensor cores
-  const bool c64f32 = a.dtype == GF_C64 && a.algo == GF_UPDATE_TC && L.pmax <= kC64Fp32MaxP;
-  bool c64tc = a.dtype == GF_C64 && a.algo == GF_UPDATE_TC && !c64f32 && L.pmax <= kC64MaxP;
+  const bool fast = a.algo != GF_UPDATE_DFMA;
+  const bool c64f32 = a.dtype == GF_C64 && fast && L.pmax <= kC64Fp32MaxP;
+  bool c64tc = a.dtype == GF_C64 && fast && !c64f32 && L.pmax <= kC64MaxP;
+  // complex128, p <= 4: the tensor-core digit products, except where the whole update is small
+  // enough (n^2 p_max <= kC128SmallWork, G resident in L2) that the FP64 FMA kernel finishes
+  // before the persistent tensor-core pipeline has filled (32x32 single pixel: 19 vs 44 us)
+  const bool oz = a.dtype == GF_C128 &&
+                  (a.algo == GF_UPDATE_TENSOR || (a.algo == GF_UPDATE_TC && (double)n * (double)n * L.pmax > kC128SmallWork));
   for (int l = 0; c64tc && l < a.nlam; ++l)
     c64tc = c64_tc_make_map(reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, maps[l].b);
   {
@@ -894,7 +901,7 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
     if (a.dtype == GF_C128) {
       double2* G = reinterpret_cast<double2*>(a.lam[l].G);
       int only_above = 0;
-      if (a.algo == GF_UPDATE_TC) {
+      if (oz) {
         // p <= 4 on the tensor cores; the DFMA kernel below takes p > 4
         // without a tensor map (driver too old) the DFMA kernel below takes every p
         if (launch_rank_update_ozaki(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl,
@@ -903,7 +910,7 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
                                      status, prof_p, a.sm_count, st))
           only_above = 4;
       }
-      if (a.algo != GF_UPDATE_TC || L.pmax > 4 || only_above == 0)
+      if (!oz || L.pmax > 4 || only_above == 0)
         k_rank_update_f64<<<grid, kUpdThreads, 0, st>>>(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl, only_above, prof_p);
     } else if (c64f32) {
       launch_rank_update_c64_fp32(reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, L.pmax, C0, S, ctl, prof_p,

@@ -7,7 +7,7 @@ trajectories and summarises their final FOM.
 from __future__ import annotations
 
 import math
-from typing import Dict, List, Sequence
+from typing import Optional, Dict, List, Sequence
 
 import numpy as np
 
@@ -44,15 +44,19 @@ def run_to_termination(opt: GreedyOptimizer, max_steps: int) -> List[float]:
 
 
 def egreedy_study(epsilons: Sequence[float] = (0.0, 0.1, 0.2, 0.3), trajectories: int = 20, seed: int = 0,
-                  max_steps: int = 4000, device: int = 0) -> Dict[float, dict]:
+                  max_steps: int = 4000, device: int = 0, update_algo: Optional[int] = None) -> Dict[float, dict]:
     """Final-FOM statistics per epsilon over seeded trajectories (epsilon = 0 is the greedy
-    policy; its trajectories are all the same)."""
+    policy; its trajectories are all the same).  update_algo: the G update's arithmetic
+    (gf_set_update_algo; the library default when None -- GF_UPDATE_TENSOR gives the fused
+    batch's arithmetic exactly)."""
     wl = metalens_21()
     out = {}
     for e_i, eps in enumerate(epsilons):
         finals, steps = [], []
         for t in range(trajectories if eps > 0 else 1):
             opt = GreedyOptimizer(wl.geoms, wl.spec, dtype=wl.dtype, device=device)
+            if update_algo is not None:
+                opt.h.gf_set_update_algo(update_algo)
             opt.fill()
             fom0 = float(opt.fom.cpu()[0])
             if eps > 0:

@@ -20,7 +20,7 @@ GF_C128, GF_C64 = 0, 1
 GF_KIND_SINGLE, GF_KIND_BRUSH2, GF_KIND_PILLAR = 0, 1, 2
 GF_DIR_FILL, GF_DIR_CLEAR = 1, 2
 GF_NBANDS = 9
-GF_UPDATE_TC, GF_UPDATE_DFMA = 0, 1
+GF_UPDATE_TC, GF_UPDATE_DFMA, GF_UPDATE_TENSOR = 0, 1, 2
 BATCH_MAX = 64             # items per gf_batch
 
 STATUS_NAMES = {GF_OK: "GF_OK", GF_EINVAL: "GF_EINVAL", GF_ECUDA: "GF_ECUDA",

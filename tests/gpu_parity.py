@@ -69,10 +69,13 @@ def near_tie(d, chosen):
     return others.size > 0 and np.max(others) >= m - GAP * abs(m)
 
 
-def run_parity(wl, steps, state=None, check_every=1, dtype="c128", compare_every_G=True):
-    """Advance the GPU path and the oracle side by side; returns (n_steps, n_lockstep)."""
+def run_parity(wl, steps, state=None, check_every=1, dtype="c128", compare_every_G=True, algo=None):
+    """Advance the GPU path and the oracle side by side; returns (n_steps, n_lockstep).
+    algo: the update arithmetic (gf_set_update_algo), the library default when None."""
     orc = O.OracleProblem(wl.geoms, wl.spec)
     opt = GreedyOptimizer(wl.geoms, wl.spec, dtype=dtype)
+    if algo is not None:
+        opt.h.gf_set_update_algo(algo)
     opt.fill()
     torch.cuda.synchronize()
     compare_state(opt, orc, tag="fill")

@@ -47,9 +47,12 @@ def _pattern(opt, seed):
 
 
 def _check_against_single_runs(wls, bo, total, dtype, oracle, patterned=False, start=None):
+    """Each problem of the batch against its own single-problem run with the batch's update
+    arithmetic (the tensor-core forms at every size, GF_UPDATE_TENSOR, on every schedule)."""
     improved = 0
     for b, (wl, opt) in enumerate(zip(wls, bo.opts)):
         ref = GreedyOptimizer(wl.geoms, wl.spec, dtype=dtype)
+        ref.h.gf_set_update_algo(B.GF_UPDATE_TENSOR)
         ref.fill()
         if patterned:
             _pattern(ref, 100 + b)

@@ -76,21 +76,24 @@ def test_eval_candidates_matches_oracle(kind, dir_mask, seed):
     compare_dfom(opt.dfom.cpu().numpy(), orc.evaluate())
 
 
-def test_plain_32x32_single_fill_100_steps():
+@pytest.mark.parametrize("algo", [B.GF_UPDATE_TC, B.GF_UPDATE_TENSOR])
+def test_plain_32x32_single_fill_100_steps(algo):
     """The 32x32 single-pixel workload in full: up to 100 greedy steps (the greedy run stops
     early when no fill improves the FOM; both sides must stop at the same step), G/E/FOM
-    compared every 10 steps."""
+    compared every 10 steps; with the default arithmetic (FP64 FMA at this size) and with the
+    tensor-core update forced."""
     wl = W.plain_32()
-    done, lock = run_parity(wl, wl.steps, check_every=10)
+    done, lock = run_parity(wl, wl.steps, check_every=10, algo=algo)
     assert done >= 50
     assert lock <= 10
 
 
+@pytest.mark.parametrize("algo", [B.GF_UPDATE_TC, B.GF_UPDATE_TENSOR])
 @pytest.mark.parametrize("nx,ny,seed,steps", [(12, 10, 21, 12), (9, 14, 22, 10)])
-def test_brush_trajectory(nx, ny, seed, steps):
+def test_brush_trajectory(nx, ny, seed, steps, algo):
     wl = W.small(nx, ny, kind=W.KIND_BRUSH2, dir_mask=3, steps=steps)
     state = W.random_state(nx * ny, seed=seed, fill=0.3)
-    done, lock = run_parity(wl, steps, state=state)
+    done, lock = run_parity(wl, steps, state=state, algo=algo)
     assert done >= 3
 
 
@@ -189,6 +192,7 @@ def test_tensor_core_update_matches_dfma_update(nx, ny):
     state = W.random_state(nx * ny, seed=31, fill=0.3)
     a = GreedyOptimizer(wl.geoms, wl.spec)
     b = GreedyOptimizer(wl.geoms, wl.spec)
+    a.h.gf_set_update_algo(B.GF_UPDATE_TENSOR)        # the tensor-core form at any size
     b.h.gf_set_update_algo(B.GF_UPDATE_DFMA)
     a.fill()
     b.fill()
