@@ -26,7 +26,7 @@ static int64_t pow2_at_least(int64_t v) {
 struct RefLayout {
   int64_t Lx, Ly, n, N;
   int m;
-  size_t table, khat, grid, V, w, x, b, r, dots, total;
+  size_t table, khat, grid, V, w, x, b, r, dots, twx, twy, total;
 };
 
 static size_t up256r(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -49,29 +49,44 @@ RefLayout ref_layout(const gf_geom& g, int restart) {
   L.b = o; o = up256r(o + c * (size_t)L.n);
   L.r = o; o = up256r(o + c * (size_t)L.n);
   L.dots = o; o = up256r(o + c * (size_t)(L.m + 2));
+  L.twx = o; o = up256r(o + c * (size_t)(L.Lx / 2 + 1));
+  L.twy = o; o = up256r(o + c * (size_t)(L.Ly / 2 + 1));
   L.total = o;
   return L;
 }
 
 // ---- FFT: one CTA per line, radix-2 decimation in time in shared memory ----------------------
+// Twiddles from a table tw[t] = exp(-2 pi i t / L), t < L / 2, made once per refresh (computing
+// them per butterfly cost an FP64 sincospi each: 21 million per GMRES iteration at L = 1024);
+// the stage with butterflies of span 2h uses tw[kk L / (2 h)], conjugated for sign = +1.
+__global__ void k_twiddles(cplx* __restrict__ tw, int L) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L / 2; t += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(-(double)t / (double)(L / 2), &sn, &cs);
+    tw[t] = mk(cs, sn);
+  }
+}
+
 __global__ void k_fft_lines(cplx* __restrict__ data, int L, int logL, int64_t stride, int64_t line_stride,
-                            double sign) {
+                            double sign, const cplx* __restrict__ tw) {
   extern __shared__ cplx sh[];
+  cplx* stw = sh + L;                                  // the twiddle table, L / 2 entries
   cplx* base = data + blockIdx.x * line_stride;
   for (int e = threadIdx.x; e < L; e += blockDim.x) {
     const int rev = (int)(__brev((unsigned)e) >> (32 - logL));
     sh[rev] = base[(int64_t)e * stride];
   }
+  for (int t = threadIdx.x; t < L / 2; t += blockDim.x) stw[t] = tw[t];
   __syncthreads();
   for (int s = 1; s <= logL; ++s) {
     const int half = 1 << (s - 1);
+    const int step = L >> s;                           // L / (2 half)
     for (int t = threadIdx.x; t < L / 2; t += blockDim.x) {
       const int kk = t & (half - 1);
       const int i = ((t >> (s - 1)) << s) + kk;
       const int j = i + half;
-      double sn, cs;
-      sincospi(sign * (double)kk / (double)half, &sn, &cs);
-      const cplx wv = mk(cs, sn);
+      cplx wv = stw[kk * step];
+      if (sign > 0.0) wv.im = -wv.im;
       const cplx tv = wv * sh[j];
       sh[j] = sh[i] - tv;
       sh[i] = sh[i] + tv;
@@ -81,17 +96,17 @@ __global__ void k_fft_lines(cplx* __restrict__ data, int L, int logL, int64_t st
   for (int e = threadIdx.x; e < L; e += blockDim.x) base[(int64_t)e * stride] = sh[e];
 }
 
-static void fft2(cplx* grid, int64_t Lx, int64_t Ly, double sign, cudaStream_t st) {
+static void fft2(cplx* grid, int64_t Lx, int64_t Ly, double sign, const cplx* twx, const cplx* twy, cudaStream_t st) {
   int lx = 0, ly = 0;
   while ((1LL << lx) < Lx) ++lx;
   while ((1LL << ly) < Ly) ++ly;
   if (Lx > 1) {
     int th = (int)(Lx / 2 < 512 ? Lx / 2 : 512);
-    k_fft_lines<<<(unsigned)Ly, th, sizeof(cplx) * Lx, st>>>(grid, (int)Lx, lx, 1, Lx, sign);
+    k_fft_lines<<<(unsigned)Ly, th, sizeof(cplx) * (Lx + Lx / 2), st>>>(grid, (int)Lx, lx, 1, Lx, sign, twx);
   }
   if (Ly > 1) {
     int th = (int)(Ly / 2 < 512 ? Ly / 2 : 512);
-    k_fft_lines<<<(unsigned)Lx, th, sizeof(cplx) * Ly, st>>>(grid, (int)Ly, ly, Lx, 1, sign);
+    k_fft_lines<<<(unsigned)Lx, th, sizeof(cplx) * (Ly + Ly / 2), st>>>(grid, (int)Ly, ly, Lx, 1, sign, twy);
   }
 }
 
@@ -280,9 +295,9 @@ static void apply(const RefCtx& c, const cplx* v, cplx* out, double alpha, doubl
   const RefLayout& L = c.L;
   cplx* grid = P(c, L.grid);
   k_scatter<<<c.blocks, 256, 0, c.st>>>(v, c.state, c.chi, c.g->nx, c.g->ny, L.Lx, L.Ly, grid);
-  fft2(grid, L.Lx, L.Ly, -1.0, c.st);
+  fft2(grid, L.Lx, L.Ly, -1.0, P(c, L.twx), P(c, L.twy), c.st);
   k_mul<<<c.blocks, 256, 0, c.st>>>(grid, P(c, L.khat), L.Lx * L.Ly, 1.0 / (double)(L.Lx * L.Ly));
-  fft2(grid, L.Lx, L.Ly, +1.0, c.st);
+  fft2(grid, L.Lx, L.Ly, +1.0, P(c, L.twx), P(c, L.twy), c.st);
   k_gather_combine<<<c.blocks, 256, 0, c.st>>>(v, grid, P(c, L.table) + L.N, c.state, c.chi, c.g->nx, c.g->ny, L.Lx,
                                                alpha, beta, out);
 }
@@ -386,10 +401,12 @@ gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int n
   c.st = st;
   c.blocks = 152 * 4;
   const RefLayout& L = c.L;
-  cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(cplx) * 8192));
+  cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(cplx) * (8192 + 4096)));
+  if (L.Lx > 1) k_twiddles<<<(unsigned)((L.Lx / 2 + 255) / 256), 256, 0, st>>>(P(c, L.twx), (int)L.Lx);
+  if (L.Ly > 1) k_twiddles<<<(unsigned)((L.Ly / 2 + 255) / 256), 256, 0, st>>>(P(c, L.twy), (int)L.Ly);
   launch_fill_table(g, P(c, L.table), st);
   k_embed<<<c.blocks, 256, 0, st>>>(P(c, L.table), g.nx, g.ny, L.Lx, L.Ly, P(c, L.khat));
-  fft2(P(c, L.khat), L.Lx, L.Ly, -1.0, st);
+  fft2(P(c, L.khat), L.Lx, L.Ly, -1.0, P(c, L.twx), P(c, L.twy), st);
   // Eq. 3 residual of E: r = E - E_inc - G0 X E
   const cplx* E = reinterpret_cast<const cplx*>(prob.E);
   const double k0 = 2.0 * M_PI / g.wavelength;
