@@ -26,8 +26,14 @@ static int64_t pow2_at_least(int64_t v) {
 struct RefLayout {
   int64_t Lx, Ly, n, N;
   int m;
-  size_t table, khat, grid, V, w, x, b, r, dots, twx, twy, total;
+  size_t table, khat, grid, V, w, x, b, r, dots, twx, twy, part, total;
 };
+
+// Reductions over the n unknowns run on the whole GPU in two stages: kRefParts slices (or the
+// CTAs of a grid-stride kernel) write partial sums, one warp per result adds them in a fixed
+// order -- deterministic, unlike atomics.
+constexpr int kRefParts = 128;
+constexpr int kRefBlocks = 152 * 4;          // CTAs of the grid-stride vector kernels
 
 static size_t up256r(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -51,6 +57,9 @@ RefLayout ref_layout(const gf_geom& g, int restart) {
   L.dots = o; o = up256r(o + c * (size_t)(L.m + 2));
   L.twx = o; o = up256r(o + c * (size_t)(L.Lx / 2 + 1));
   L.twy = o; o = up256r(o + c * (size_t)(L.Ly / 2 + 1));
+  const size_t nparts = (size_t)(L.m + 1) * kRefParts > (size_t)kRefBlocks ? (size_t)(L.m + 1) * kRefParts
+                                                                              : (size_t)kRefBlocks;
+  L.part = o; o = up256r(o + c * nparts);
   L.total = o;
   return L;
 }
@@ -139,38 +148,56 @@ __global__ void k_scatter(const cplx* __restrict__ v, const uint8_t* __restrict_
   }
 }
 
-// out = alpha * v + beta * (G0 X v), with the pixel part from the convolution grid and the
-// monitor part as the dot product of the monitor row with X v (one block does the dot)
+// out = alpha * v + beta * (G0 X v) on the pixels from the convolution grid; the monitor entry is
+// the dot product of the monitor row with X v, whose per-CTA partial sums go to part[blockIdx.x]
+// (k_mon_finish adds them)
 __global__ void k_gather_combine(const cplx* __restrict__ v, const cplx* __restrict__ grid, const cplx* __restrict__ mon,
                                  const uint8_t* __restrict__ state, double chi, int nx, int ny, int64_t Lx,
-                                 double alpha, double beta, cplx* __restrict__ out) {
+                                 double alpha, double beta, cplx* __restrict__ out, cplx* __restrict__ part) {
+  __shared__ double sr[32], si[32];
   const int64_t N = (int64_t)nx * ny;
+  double ar = 0.0, ai = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t y = i / nx, x = i - y * nx;
     out[i] = alpha * v[i] + beta * grid[y * Lx + x];
-  }
-  if (blockIdx.x == 0) {
-    __shared__ double sr[32], si[32];
-    double ar = 0.0, ai = 0.0;
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-      if (state[j]) {
-        const cplx t = mon[j] * (chi * v[j]);
-        ar += t.re;
-        ai += t.im;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      ar += __shfl_down_sync(0xffffffffu, ar, o);
-      ai += __shfl_down_sync(0xffffffffu, ai, o);
-    }
-    if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = ar; si[threadIdx.x >> 5] = ai; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tr = 0.0, ti = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tr += sr[w]; ti += si[w]; }
-      out[N] = alpha * v[N] + beta * mk(tr, ti);
+    if (state[i]) {
+      const cplx t = mon[i] * (chi * v[i]);
+      ar += t.re;
+      ai += t.im;
     }
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    ar += __shfl_down_sync(0xffffffffu, ar, o);
+    ai += __shfl_down_sync(0xffffffffu, ai, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = ar; si[threadIdx.x >> 5] = ai; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, ti = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tr += sr[w]; ti += si[w]; }
+    part[blockIdx.x] = mk(tr, ti);
+  }
+}
+
+// one warp: s = the nparts partial sums in a fixed order
+__device__ __forceinline__ cplx warp_sum_parts(const cplx* __restrict__ part, int nparts) {
+  const int lane = threadIdx.x & 31;
+  double ar = 0.0, ai = 0.0;
+  for (int p = lane; p < nparts; p += 32) {
+    ar += part[p].re;
+    ai += part[p].im;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ar += __shfl_down_sync(0xffffffffu, ar, o);
+    ai += __shfl_down_sync(0xffffffffu, ai, o);
+  }
+  return mk(ar, ai);
+}
+
+__global__ void k_mon_finish(const cplx* __restrict__ part, int nparts, const cplx* __restrict__ v, int64_t N,
+                             double alpha, double beta, cplx* __restrict__ out) {
+  const cplx s = warp_sum_parts(part, nparts);
+  if (threadIdx.x == 0) out[N] = alpha * v[N] + beta * s;
 }
 
 // ---- vectors ----------------------------------------------------------------------------------
@@ -191,19 +218,25 @@ __device__ void block_sum2(double& a, double& b) {
   }
 }
 
-// h[q] = <V_q, w> = sum conj(V_q) w for q < nvec (one block per vector)
-__global__ void k_dots(const cplx* __restrict__ V, int64_t n, int nvec, const cplx* __restrict__ w, cplx* __restrict__ h) {
-  const int q = blockIdx.x;
-  if (q >= nvec) return;
+// part[q][p] = sum over slice p of conj(V_q) w  (grid kRefParts x nvec)
+__global__ void k_dots_part(const cplx* __restrict__ V, int64_t n, const cplx* __restrict__ w, cplx* __restrict__ part) {
+  const int q = blockIdx.y, p = blockIdx.x;
+  const int64_t lo = n * p / kRefParts, hi = n * (p + 1) / kRefParts;
   const cplx* vq = V + (int64_t)q * n;
   double ar = 0.0, ai = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const cplx a = vq[i], b = w[i];
     ar += a.re * b.re + a.im * b.im;
     ai += a.re * b.im - a.im * b.re;
   }
   block_sum2(ar, ai);
-  if (threadIdx.x == 0) h[q] = mk(ar, ai);
+  if (threadIdx.x == 0) part[q * kRefParts + p] = mk(ar, ai);
+}
+
+// h[q] = sum of part[q][*] (one warp per vector)
+__global__ void k_parts_sum(const cplx* __restrict__ part, cplx* __restrict__ h) {
+  const cplx s = warp_sum_parts(part + (int64_t)blockIdx.x * kRefParts, kRefParts);
+  if (threadIdx.x == 0) h[blockIdx.x] = s;
 }
 
 // w -= sum_q h[q] V_q
@@ -216,12 +249,20 @@ __global__ void k_sub_combo(cplx* __restrict__ w, const cplx* __restrict__ V, in
   }
 }
 
-// out[0] = ||a||^2 (single block)
-__global__ void k_norm2(const cplx* __restrict__ a, int64_t n, double* out) {
+// part[p] = ||a restricted to slice p||^2 (as the real part; grid kRefParts)
+__global__ void k_norm2_part(const cplx* __restrict__ a, int64_t n, cplx* __restrict__ part) {
+  const int p = blockIdx.x;
+  const int64_t lo = n * p / kRefParts, hi = n * (p + 1) / kRefParts;
   double s = 0.0, z = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += abs2(a[i]);
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += abs2(a[i]);
   block_sum2(s, z);
-  if (threadIdx.x == 0) *out = s;
+  if (threadIdx.x == 0) part[p] = mk(s, 0.0);
+}
+
+// out[0] = the sum of the kRefParts partial squares
+__global__ void k_norm2_finish(const cplx* __restrict__ part, double* __restrict__ out) {
+  const cplx s = warp_sum_parts(part, kRefParts);
+  if (threadIdx.x == 0) *out = s.re;
 }
 
 // y = a * x   (a real)
@@ -298,13 +339,15 @@ static void apply(const RefCtx& c, const cplx* v, cplx* out, double alpha, doubl
   fft2(grid, L.Lx, L.Ly, -1.0, P(c, L.twx), P(c, L.twy), c.st);
   k_mul<<<c.blocks, 256, 0, c.st>>>(grid, P(c, L.khat), L.Lx * L.Ly, 1.0 / (double)(L.Lx * L.Ly));
   fft2(grid, L.Lx, L.Ly, +1.0, P(c, L.twx), P(c, L.twy), c.st);
-  k_gather_combine<<<c.blocks, 256, 0, c.st>>>(v, grid, P(c, L.table) + L.N, c.state, c.chi, c.g->nx, c.g->ny, L.Lx,
-                                               alpha, beta, out);
+  k_gather_combine<<<kRefBlocks, 256, 0, c.st>>>(v, grid, P(c, L.table) + L.N, c.state, c.chi, c.g->nx, c.g->ny, L.Lx,
+                                                alpha, beta, out, P(c, L.part));
+  k_mon_finish<<<1, 32, 0, c.st>>>(P(c, L.part), kRefBlocks, v, L.N, alpha, beta, out);
 }
 
 static double norm2_host(const RefCtx& c, const cplx* a) {
   double* d = reinterpret_cast<double*>(P(c, c.L.dots));
-  k_norm2<<<1, 1024, 0, c.st>>>(a, c.L.n, d);
+  k_norm2_part<<<kRefParts, 256, 0, c.st>>>(a, c.L.n, P(c, c.L.part));
+  k_norm2_finish<<<1, 32, 0, c.st>>>(P(c, c.L.part), d);
   double h = 0.0;
   cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, c.st);
   cudaStreamSynchronize(c.st);
@@ -337,7 +380,8 @@ static int gmres(const RefCtx& c, int max_iter, double tol) {
       // classical Gram-Schmidt, twice
       std::vector<cplx> hsum(k + 1, mk(0.0, 0.0));
       for (int pass = 0; pass < 2; ++pass) {
-        k_dots<<<k + 1, 256, 0, c.st>>>(V, n, k + 1, w, hd);
+        k_dots_part<<<dim3(kRefParts, (unsigned)(k + 1)), 256, 0, c.st>>>(V, n, w, P(c, L.part));
+        k_parts_sum<<<k + 1, 32, 0, c.st>>>(P(c, L.part), hd);
         k_sub_combo<<<c.blocks, 256, 0, c.st>>>(w, V, n, k + 1, hd);
         cudaMemcpyAsync(hcol.data(), hd, sizeof(cplx) * (k + 1), cudaMemcpyDeviceToHost, c.st);
         cudaStreamSynchronize(c.st);
@@ -399,7 +443,7 @@ gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int n
   c.state = state;
   c.chi = g.eps_mat - g.eps_bg;
   c.st = st;
-  c.blocks = 152 * 4;
+  c.blocks = kRefBlocks;
   const RefLayout& L = c.L;
   cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(cplx) * (8192 + 4096)));
   if (L.Lx > 1) k_twiddles<<<(unsigned)((L.Lx / 2 + 255) / 256), 256, 0, st>>>(P(c, L.twx), (int)L.Lx);
