@@ -81,3 +81,40 @@ def test_batch_host_checks(lib):
     assert lib.gf_batch_step(None, None) == B.GF_EINVAL
     assert lib.gf_batch_set_schedule(None, 0) == B.GF_EINVAL
     lib.gf_batch_destroy(None)
+
+
+def test_workspace_sizes_cover_the_tensor_core_operand_blocks(lib):
+    """The complex64 tensor-core update's split-FP16 operand blocks (A: one per 128-row tile, B:
+    one per 64-column tile, 16 KB per 32-deep K chunk, K = 2 P with P = p_max rounded to 16) fit
+    in the workspace, for the 2-D top-k workload and the 3-D lens; the refresh workspace holds
+    the GMRES basis and the partial sums of its reductions."""
+    def blocks(n, pmax):
+        P = (pmax + 15) // 16 * 16
+        nkc = 2 * P // 32
+        nrt, nct = (n + 127) // 128, (2 * n + 127) // 128
+        return (nrt + nct) * nkc * 16384
+    wl = W.brush_320_topk()
+    g, s = wl.geoms[0], wl.spec
+    ws = lib.gf_workspace_size(C.byref(B.geom_struct(g)), 1, B.GF_C64, C.byref(B.spec_struct(s)))
+    assert ws >= blocks(g.N + 1, 4 * s.k) and ws % 256 == 0
+    k1 = W.CandidateSpec(s.kind, s.dir_mask, 1, s.excl_radius)
+    assert lib.gf_workspace_size(C.byref(B.geom_struct(g)), 1, B.GF_C64, C.byref(B.spec_struct(k1))) < ws
+    ml = W.metalens_3d()
+    g3 = B.geom3d_struct(ml.geoms[0])
+    n3 = lib.gf3_num_unknowns(C.byref(g3))
+    assert n3 == 3 * (120 * 120 * 4 + 1)
+    ws3 = lib.gf3_workspace_size(C.byref(g3), B.GF_C64, C.byref(B.spec_struct(ml.spec)))
+    assert ws3 >= blocks(n3, 12 * 4) and ws3 % 256 == 0
+    gr = B.geom_struct(g)
+    rw = lib.gf_refresh_workspace_size(C.byref(gr), 30)
+    assert rw >= 16 * (g.N + 1) * 31 + 16 * 31 * 128
+    assert lib.gf_refresh_workspace_size(C.byref(gr), 0) == 0
+    assert lib.gf_refresh_workspace_size(C.byref(gr), 201) == 0
+
+
+def test_update_algo_settings(lib):
+    assert (B.GF_UPDATE_TC, B.GF_UPDATE_DFMA, B.GF_UPDATE_TENSOR) == (0, 1, 2)
+    hdr = open(os.path.join(ROOT, "include", "gfopt.h")).read()
+    for name, v in (("GF_UPDATE_TC", 0), ("GF_UPDATE_DFMA", 1), ("GF_UPDATE_TENSOR", 2)):
+        assert re.search(r"#define\s+%s\s+%d\b" % (name, v), hdr), name
+    assert lib.gf_set_update_algo(None, B.GF_UPDATE_TENSOR) == B.GF_EINVAL
