@@ -248,6 +248,18 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_replicas(ms: float, flips: int, device) -> tuple:
+    """Across the ranks of the initialised process group: the slowest rank's time and the
+    flips of all ranks (every rank runs its own replica; no data path crosses ranks)."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ff = torch.tensor([flips], dtype=torch.int64, device=device)
+    dist.all_reduce(ff)
+    return float(tt.item()), int(ff.item())
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -426,13 +438,7 @@ def run_native(args):
     t_max = ms
     flips_total = flips
     if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        ff = torch.tensor([flips], device=f"cuda:{dev}", dtype=torch.int64)
-        dist.all_reduce(ff)
-        flips_total = int(ff.item())
+        t_max, flips_total = reduce_replicas(ms, flips, f"cuda:{dev}")
     value = flips_total / (t_max / 1e3)
 
     # ---- per-stage breakdown (CUDA events around each ABI call; not part of the timed region)
