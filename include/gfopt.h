@@ -132,9 +132,17 @@ gf_status gf_fill_g0(gf_handle* h, const gf_problem* prob, int32_t dtype,
  * The paper has no counterpart.  The Hankel table lives in a fixed 4 MiB array inside the
  * library (held on every GPU that loads it until exit), so N = nx*ny <= 131072 (GF_EINVAL
  * otherwise).  All calls share that array: calls overlapping on the GPU race and must be
- * ordered by the caller.  The first call on a device looks up the array's address; make it
- * before any stream capture.  Writes the same G, E and bands as gf_fill_g0. */
+ * ordered by the caller.  Every call looks up the array's address on the handle's device;
+ * the first call on a device also loads the library's device code there, so make that first
+ * call before any stream capture.  Writes the same G, E and bands as gf_fill_g0. */
 gf_status gf_fill_g0_static(gf_handle* h, const gf_problem* prob, int32_t dtype, void* stream);
+
+/* Figure of merit of the current fields (Eq. 1): *fom_out (device double) = sum over the nlam
+ * wavelengths of |E(r_m)|^2 = |E[N]|^2.  gf_apply_update writes the FOM after every step;
+ * this call gives it for a state no step has produced yet, e.g. right after gf_fill_g0.
+ * probs as for gf_eval_candidates (only E is read). */
+gf_status gf_fom(gf_handle* h, const gf_problem* probs, int32_t nlam, int32_t dtype, double* fom_out,
+                 void* stream);
 
 /* Re-extract the bands of one wavelength from its G (used after external edits of G). */
 gf_status gf_extract_bands(gf_handle* h, const gf_problem* prob, int32_t dtype, void* stream);
@@ -242,6 +250,8 @@ typedef struct gf_lowrank {
 size_t gf_lowrank_workspace_size(const gf_geom* geom, int32_t max_cols);
 /* Vacuum start: G0 table, bands, monitor row, E = E_inc, no terms. */
 gf_status gf_lowrank_init(gf_handle* h, const gf_lowrank* lr, void* ws, size_t ws_bytes, void* stream);
+/* Eq. 1 for the low-rank state: *fom_out (device double) = |E[N]|^2 (only lr->E is read). */
+gf_status gf_lowrank_fom(gf_handle* h, const gf_lowrank* lr, double* fom_out, void* stream);
 /* dFOM of every candidate (as gf_eval_candidates). */
 gf_status gf_lowrank_eval(gf_handle* h, const gf_lowrank* lr, const uint8_t* state, const gf_cand_spec* spec,
                           double* dfom, void* stream);
@@ -288,6 +298,8 @@ int64_t gf3_num_unknowns(const gf_geom3d* geom);
 int64_t gf3_num_candidates(const gf_geom3d* geom);
 size_t gf3_workspace_size(const gf_geom3d* geom, int32_t dtype, const gf_cand_spec* spec);
 gf_status gf3_fill_g0(gf_handle* h, const gf_problem3d* prob, int32_t dtype, void* ws, size_t ws_bytes, void* stream);
+/* Eq. 1 in 3-D: *fom_out (device double) = sum over the three components of |E(r_m)|^2. */
+gf_status gf3_fom(gf_handle* h, const gf_problem3d* prob, int32_t dtype, double* fom_out, void* stream);
 gf_status gf3_eval_candidates(gf_handle* h, const gf_problem3d* prob, int32_t dtype, const uint8_t* state,
                               const gf_cand_spec* spec, double* dfom, void* stream);
 gf_status gf3_select_topk(gf_handle* h, const gf_geom3d* geom, const gf_cand_spec* spec, const double* dfom,

@@ -697,6 +697,21 @@ gf_status gf3_fill_g0(gf_handle* h, const gf_problem3d* prob, int32_t dtype, voi
   return gf::api_cuda_check(h, "gf3_fill_g0 launch");
 }
 
+gf_status gf3_fom(gf_handle* h, const gf_problem3d* prob, int32_t dtype, double* fom_out, void* stream) {
+  if (!h) return GF_EINVAL;
+  gf_status s = gf::check3_problem(h, prob, dtype);
+  if (s) return s;
+  if (!fom_out) return gf::api_fail_msg(h, GF_EINVAL, "fom_out must be non-NULL");
+  if ((s = gf::api_bind_device(h))) return s;
+  gf::FomArgs a;
+  a.nlam = 1;
+  a.ncomp = 3;
+  a.mrow = 3 * (int64_t)prob->geom.nx * prob->geom.ny * prob->geom.nz;
+  a.E[0] = reinterpret_cast<const gf::cplx*>(prob->E);
+  gf::launch_fom(a, fom_out, (cudaStream_t)stream);
+  return gf::api_cuda_check(h, "gf3_fom launch");
+}
+
 gf_status gf3_eval_candidates(gf_handle* h, const gf_problem3d* prob, int32_t dtype, const uint8_t* state,
                               const gf_cand_spec* spec, double* dfom, void* stream) {
   if (!h) return GF_EINVAL;

@@ -260,6 +260,21 @@ gf_status gf_fill_g0(gf_handle* h, const gf_problem* prob, int32_t dtype, void* 
   return cuda_check(h, "gf_fill_g0 launch");
 }
 
+gf_status gf_fom(gf_handle* h, const gf_problem* probs, int32_t nlam, int32_t dtype, double* fom_out, void* stream) {
+  if (!h) return GF_EINVAL;
+  gf_status s = check_lams(h, probs, nlam, dtype);
+  if (s) return s;
+  if (!fom_out) return fail(h, GF_EINVAL, "fom_out must be non-NULL");
+  if ((s = bind_device(h))) return s;
+  gf::FomArgs a;
+  a.nlam = nlam;
+  a.ncomp = 1;
+  a.mrow = (int64_t)probs[0].geom.nx * probs[0].geom.ny;
+  for (int l = 0; l < nlam; ++l) a.E[l] = reinterpret_cast<const gf::cplx*>(probs[l].E);
+  gf::launch_fom(a, fom_out, (cudaStream_t)stream);
+  return cuda_check(h, "gf_fom launch");
+}
+
 gf_status gf_extract_bands(gf_handle* h, const gf_problem* prob, int32_t dtype, void* stream) {
   if (!h) return GF_EINVAL;
   gf_status s = check_problem(h, prob, dtype, true);

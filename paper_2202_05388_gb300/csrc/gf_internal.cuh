@@ -224,6 +224,16 @@ struct UpdArgs {
 // CUDA-event timer of the G-update kernel launches (armed by gf_profile_begin).  Each record
 // holds an event pair and the rank p that the launch applied (written by the kernel into
 // mapped host memory, since p is only known on the device).
+// Eq. 1 at the monitor: FOM = sum over components q < ncomp and wavelengths l < nlam of
+// |E_l[mrow + q]|^2, written to *out (device).
+struct FomArgs {
+  const cplx* E[kMaxLam];
+  int nlam;
+  int ncomp;
+  int64_t mrow;
+};
+void launch_fom(const FomArgs& a, double* out, cudaStream_t st);
+
 struct KernelTimer {
   bool on = false;
   int max = 0, used = 0;

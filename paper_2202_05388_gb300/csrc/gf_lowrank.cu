@@ -404,6 +404,23 @@ gf_status gf_lowrank_init(gf_handle* h, const gf_lowrank* lr, void* ws, size_t w
   return gf::api_cuda_check(h, "gf_lowrank_init launch");
 }
 
+gf_status gf_lowrank_fom(gf_handle* h, const gf_lowrank* lr, double* fom_out, void* stream) {
+  if (!h) return GF_EINVAL;
+  if (!lr) return gf::api_fail_msg(h, GF_EINVAL, "low-rank problem is NULL");
+  if (!lr->E || ((uintptr_t)lr->E & 15u)) return gf::api_fail_msg(h, GF_EINVAL, "E must be non-NULL and 16-byte aligned");
+  if (lr->geom.nx < 1 || lr->geom.ny < 1) return gf::api_fail_msg(h, GF_EINVAL, "nx, ny must be >= 1");
+  if (!fom_out) return gf::api_fail_msg(h, GF_EINVAL, "fom_out must be non-NULL");
+  gf_status s = gf::api_bind_device(h);
+  if (s) return s;
+  gf::FomArgs a;
+  a.nlam = 1;
+  a.ncomp = 1;
+  a.mrow = (int64_t)lr->geom.nx * lr->geom.ny;
+  a.E[0] = reinterpret_cast<const gf::cplx*>(lr->E);
+  gf::launch_fom(a, fom_out, (cudaStream_t)stream);
+  return gf::api_cuda_check(h, "gf_lowrank_fom launch");
+}
+
 gf_status gf_lowrank_eval(gf_handle* h, const gf_lowrank* lr, const uint8_t* state, const gf_cand_spec* spec,
                           double* dfom, void* stream) {
   if (!h) return GF_EINVAL;

@@ -16,11 +16,12 @@
 //     call writes every table entry it reads, so nothing has to start at zero;
 //   * calls that overlap on the GPU (for example on two streams) race on the array and must
 //     be ordered by the caller;
-//   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (once per device, with that device current); make that first call
-//     before any stream capture.
-#include <mutex>
-
+//   * every call looks up the array's device address with cudaGetSymbolAddress, with the
+//     handle's device current, and checks the result; the first call on a device also loads
+//     the library's device code there, so make that first call before any stream capture.
+//     Looking the address up per call (a host-side table lookup once the code is loaded) keeps
+//     it right after the device's context has been torn down and created again, where a
+//     cached address would point into memory that no longer belongs to the array.
 #include "gf_internal.cuh"
 
 namespace gf {
@@ -29,20 +30,11 @@ constexpr int64_t kStaticTableEntries = int64_t(1) << 18;
 
 static __device__ __align__(256) cplx g_static_table[kStaticTableEntries];
 
-// Device address of g_static_table on the current device (looked up once per device).
-static cplx* static_table_address(int device, cudaError_t* err) {
-  static std::mutex mu;
-  static cplx* addr[64] = {};
-  std::lock_guard<std::mutex> lk(mu);
-  if (device >= 0 && device < 64 && addr[device]) {
-    *err = cudaSuccess;
-    return addr[device];
-  }
+// Device address of g_static_table on the current device.
+static cplx* static_table_address(cudaError_t* err) {
   void* p = nullptr;
   *err = cudaGetSymbolAddress(&p, g_static_table);
-  if (*err != cudaSuccess) return nullptr;
-  if (device >= 0 && device < 64) addr[device] = reinterpret_cast<cplx*>(p);
-  return reinterpret_cast<cplx*>(p);
+  return *err == cudaSuccess ? reinterpret_cast<cplx*>(p) : nullptr;
 }
 
 }  // namespace gf
@@ -58,7 +50,7 @@ extern "C" gf_status gf_fill_g0_static(gf_handle* h, const gf_problem* prob, int
                             "holds 2N entries); use gf_fill_g0 with a workspace for larger grids");
   if ((s = gf::api_bind_device(h))) return s;
   cudaError_t e;
-  gf::cplx* table = gf::static_table_address(gf::api_device(h), &e);
+  gf::cplx* table = gf::static_table_address(&e);
   if (!table) {
     cudaGetLastError();
     return gf::api_fail_msg(h, GF_ECUDA, cudaGetErrorString(e));

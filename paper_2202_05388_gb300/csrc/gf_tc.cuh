@@ -195,31 +195,6 @@ __device__ __forceinline__ void tma_store_2d_hint(const void* tmap, int x, int y
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;"
                :: "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(src_smem)), "l"(policy) : "memory");
 }
-// ---- thread-block clusters: rank, cluster-wide barrier, multicast bulk copy and commit
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// every thread of every CTA of the cluster (convergent warps)
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// the same bytes land at the same shared-memory offset of every CTA in cta_mask, each
-// completing `bytes` on its own mbarrier at the offset of mbar
-__device__ __forceinline__ void bulk_g2s_mc_hint(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* mbar,
-                                                 uint16_t cta_mask, uint64_t policy) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster.L2::cache_hint [%0], [%1], %2, [%3], %4, %5;"
-               :: "r"(smem_u32(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_u32(mbar)), "h"(cta_mask), "l"(policy)
-               : "memory");
-}
-// arrive (once) on the mbarrier at the offset of mbar in every CTA of cta_mask when all
-// tcgen05.mma issued so far by this thread completed
-__device__ __forceinline__ void mma_commit_mc(uint64_t* mbar, uint16_t cta_mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-               :: "r"(smem_u32(mbar)), "h"(cta_mask) : "memory");
-}
-
 __device__ __forceinline__ void tma_prefetch_desc(const void* tmap) {
   asm volatile("prefetch.tensormap [%0];" :: "l"(tmap) : "memory");
 }

@@ -271,17 +271,9 @@ __device__ __forceinline__ void c64_tile_coords(int64_t t, int64_t nrt, int64_t 
   ct = rem / rows_in_group;
 }
 
-// Operand sharing in a thread-block cluster of CR x CC CTAs (1x1, 2x1 or 2x2): the cluster
-// works on a CR x CC block of tiles at a time.  CTAs in the same tile row need the same A
-// blocks and CTAs in the same tile column the same B blocks, so each loads one half (hi or
-// lo) of its row's A block and one half of its column's B block and multicasts each half to
-// the partner that shares it: per CTA and K chunk, operand traffic falls from two blocks (A and
-// B) to 1.5 for a 2x1 cluster and to one for a 2x2 cluster.  A stage is free only
-// when every CTA that writes into it is done with its own copy: the MMA warp commits to the
-// "empty" barrier of itself and of its A and B partners, and that barrier counts one arrival
-// per CTA in the mask.  At ragged edges the CTAs without a real tile work on a phantom tile
-// (operands of tile 0, no G load, update or store) so that the cluster stays in step.
-template <int CR, int CC>
+// One CTA per SM walks its tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; per tile and K
+// chunk it brings in the A block of its row tile and the B block of its column tile with plain
+// bulk copies into its own shared memory.
 __global__ void __launch_bounds__(kC64Threads, 1)
 k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_t nrt, int64_t nct, int nkc,
                        const uint8_t* __restrict__ Aops, const uint8_t* __restrict__ Bops,
@@ -301,16 +293,7 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
   volatile int* abort = &bars->abort;
   constexpr int kWarpGProd = kC64EpiWarps, kWarpMma = kC64EpiWarps + 1, kWarpStore = kC64EpiWarps + 2,
                 kWarpOProd = kC64EpiWarps + 3;
-  constexpr int CS = CR * CC;
-  const int crank = CS > 1 ? (int)tc::cluster_ctarank() : 0;
-  const int rr = crank / CC, cc = crank % CC;     // position in the cluster's tile block
-  const int64_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
-  const int64_t nrt_c = (nrt + CR - 1) / CR, nct_c = (nct + CC - 1) / CC;
-  const uint16_t me = (uint16_t)(1u << crank);
-  const uint16_t mask_a = CC == 2 ? (uint16_t)(me | (1u << (crank ^ 1))) : me;    // CTAs sharing my A
-  const uint16_t mask_b = CR == 2 ? (uint16_t)(me | (1u << (crank ^ CC))) : me;   // CTAs sharing my B
-  const uint16_t mask_e = (uint16_t)(mask_a | mask_b);
-  const int nempty = __popc(mask_e);
+  const int64_t cid = blockIdx.x, ncl = gridDim.x;
 
   if (warp == kWarpMma) {
     tc::tmem_alloc(&bars->tslot, kC64TmemCols);
@@ -319,7 +302,7 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
   if (tid == 0) {
     for (int q = 0; q < kC64NSO; ++q) {
       tc::mbar_init(&bars->ofull[q], 1);
-      tc::mbar_init(&bars->oempty[q], (uint32_t)nempty);
+      tc::mbar_init(&bars->oempty[q], 1);
     }
     for (int q = 0; q < kC64NSG; ++q) {
       tc::mbar_init(&bars->gfull[q], 1);
@@ -335,18 +318,16 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (CS > 1) tc::cluster_sync();                // the partners' barriers exist before any multicast
   tc::fence_after_sync();
   const uint32_t tbase = bars->tslot;
-  const int64_t T = nrt_c * nct_c;
+  const int64_t T = nrt * nct;
 
   if (warp == kWarpGProd) {
     if (lane == 0) {
       int64_t k = 0;
       for (int64_t t = cid; t < T; t += ncl, ++k) {
-        int64_t rg, cg;
-        c64_tile_coords(t, nrt_c, nct_c, rg, cg);
-        const int64_t rt = rg * CR + rr, ct = cg * CC + cc;
+        int64_t rt, ct;
+        c64_tile_coords(t, nrt, nct, rt, ct);
         bool ok = true;
         for (int hh = 0; hh < 2; ++hh) {         // the tile's two halves go to their own stages
           const int64_t u = 2 * k + hh;
@@ -373,11 +354,8 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
       const uint64_t pol_ops = tc::policy_evict_last();    // operand blocks: re-read by many tiles
       int64_t c = 0;
       for (int64_t t = cid; t < T; t += ncl) {
-        int64_t rg, cg;
-        c64_tile_coords(t, nrt_c, nct_c, rg, cg);
-        int64_t rt = rg * CR + rr, ct = cg * CC + cc;
-        if (rt >= nrt) rt = 0;                   // phantom tile: any valid operands
-        if (ct >= nct) ct = 0;
+        int64_t rt, ct;
+        c64_tile_coords(t, nrt, nct, rt, ct);
         bool ok = true;
         for (int kc = 0; kc < nkr; ++kc, ++c) {
           const int s = (int)(c % kC64NSO);
@@ -386,25 +364,15 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
           tc::mbar_arrive_expect_tx(&bars->ofull[s], (uint32_t)kC64OpStage);
           const uint8_t* asrc = Aops + (rt * nkc + kc) * (int64_t)kC64Block;
           const uint8_t* bsrc = Bops + (ct * nkc + kc) * (int64_t)kC64Block;
-          if (CC == 2)      // my half of the A block, to me and my row partner
-            tc::bulk_g2s_mc_hint(st + cc * kC64Half, asrc + cc * kC64Half, kC64Half, &bars->ofull[s], mask_a, pol_ops);
-          else
-            tc::bulk_g2s_hint(st, asrc, kC64Block, &bars->ofull[s], pol_ops);
-          if (CR == 2)      // my half of the B block, to me and my column partner
-            tc::bulk_g2s_mc_hint(st + kC64Block + rr * kC64Half, bsrc + rr * kC64Half, kC64Half, &bars->ofull[s],
-                                 mask_b, pol_ops);
-          else
-            tc::bulk_g2s_hint(st + kC64Block, bsrc, kC64Block, &bars->ofull[s], pol_ops);
+          tc::bulk_g2s_hint(st, asrc, kC64Block, &bars->ofull[s], pol_ops);
+          tc::bulk_g2s_hint(st + kC64Block, bsrc, kC64Block, &bars->ofull[s], pol_ops);
         }
         if (!ok) break;
       }
-      if (CS > 1) {
-        // drain: copies into this CTA (own and the peer's halves) of the last stages may still
-        // be in flight if the loop was abandoned; wait (bounded) until they landed
-        for (int64_t q = c - kC64NSO; q < c; ++q) {
-          if (q < 0) continue;
-          tc::mbar_wait_bounded(&bars->ofull[q % kC64NSO], (uint32_t)((q / kC64NSO) & 1), 100000000ull);
-        }
+      // every copy issued has landed before the CTA may retire
+      for (int64_t q = c - kC64NSO; q < c; ++q) {
+        if (q < 0) continue;
+        tc::mbar_wait_bounded(&bars->ofull[q % kC64NSO], (uint32_t)((q / kC64NSO) & 1), 100000000ull);
       }
     }
     __syncwarp();
@@ -434,18 +402,14 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
             tc::mma_f16(d2, ah, bl, idesc, first);
             tc::mma_f16(d2, al, bh, idesc, 1u);
           }
-          if (CS > 1) tc::mma_commit_mc(&bars->oempty[s], mask_e);
-          else tc::mma_commit(&bars->oempty[s]);
+          tc::mma_commit(&bars->oempty[s]);
         }
         if (ok) tc::mma_commit(&bars->tfull[b]);
       }
-      if (CS > 1) {
-        // this CTA's last commits (to both CTAs' empty barriers) fire when its MMAs complete:
-        // wait (bounded) for them locally before the cluster may retire
-        for (int64_t q = c - kC64NSO; q < c; ++q) {
-          if (q < 0) continue;
-          tc::mbar_wait_bounded(&bars->oempty[q % kC64NSO], (uint32_t)((q / kC64NSO) & 1), 100000000ull);
-        }
+      // every MMA issued has completed before the CTA may release TMEM and retire
+      for (int64_t q = c - kC64NSO; q < c; ++q) {
+        if (q < 0) continue;
+        tc::mbar_wait_bounded(&bars->oempty[q % kC64NSO], (uint32_t)((q / kC64NSO) & 1), 100000000ull);
       }
     }
     __syncwarp();
@@ -455,9 +419,8 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
     int64_t k = 0;
     for (int64_t t = cid; t < T; t += ncl, ++k) {
-      int64_t rg, cg;
-      c64_tile_coords(t, nrt_c, nct_c, rg, cg);
-      const int64_t rt = rg * CR + rr, ct = cg * CC + cc;
+      int64_t rt, ct;
+      c64_tile_coords(t, nrt, nct, rt, ct);
       const bool real = rt < nrt && ct < nct;
       const int b = (int)(k & 1);
       const int64_t u = 2 * k + (h >> 1);      // this warp's half of the tile
@@ -518,15 +481,14 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
     if (lane == 0) {
       int64_t k = 0;
       for (int64_t t = cid; t < T; t += ncl, ++k) {
-        int64_t rg, cg;
-        c64_tile_coords(t, nrt_c, nct_c, rg, cg);
-        const int64_t rt = rg * CR + rr, ct = cg * CC + cc;
+        int64_t rt, ct;
+        c64_tile_coords(t, nrt, nct, rt, ct);
         bool ok = true;
         for (int hh = 0; hh < 2; ++hh) {
           const int64_t u = 2 * k + hh;
           const int s = (int)(u % kC64NSG);
           if (!tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)((u / kC64NSG) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
-          if (rt < nrt && ct < nct) {
+          {
             const int x0 = (int)(ct * kC64N) + 64 * hh, y = (int)(rt * kC64M);
             uint8_t* gt = gts + s * kC64GTile;
             for (int b = 0; b < 2; ++b)
@@ -544,7 +506,6 @@ k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (CS > 1) tc::cluster_sync();                // no CTA retires while a partner may still signal it
   if (tid == 0 && bars->abort) atomicExch(status, GF_ETIMEOUT);
   tc::fence_after_sync();
   if (warp == kWarpMma) tc::tmem_dealloc(tbase, kC64TmemCols);
@@ -867,51 +828,17 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
     k_c64_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, L.pmax, n, rows, ctl, (int)o.nkc, Aops,
                                                                  Erow);
   }
-  // once per device: shared-memory opt-in of every form and the number of 4- and 2-CTA clusters
-  // that can be resident at once (0: that form is unavailable)
+  // once per device: shared-memory opt-in of both forms
   static std::mutex mu;
   static bool done[64] = {};
-  static int clusters4[64] = {}, clusters2[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  auto max_active = [&](auto kernel, int size) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)size;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)(size * sm_count));
-    cfg.blockDim = dim3(kC64Threads);
-    cfg.dynamicSmemBytes = kC64Smem;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int m = 0;
-    if (cudaOccupancyMaxActiveClusters(&m, kernel, &cfg) != cudaSuccess) {
-      cudaGetLastError();
-      m = 0;
-    }
-    return m;
-  };
-  int c4 = 0, c2 = 0;
   {
     std::lock_guard<std::mutex> lk(mu);
-    const bool cache = dev >= 0 && dev < 64;
-    if (!cache || !done[dev]) {
+    if (dev < 0 || dev >= 64 || !done[dev]) {
       cudaFuncSetAttribute(k_rank_update_c64_ra, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
-      cudaFuncSetAttribute(k_rank_update_c64_tc_t<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
-      cudaFuncSetAttribute(k_rank_update_c64_tc_t<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
-      cudaFuncSetAttribute(k_rank_update_c64_tc_t<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
-      c4 = max_active(k_rank_update_c64_tc_t<2, 2>, 4);
-      c2 = max_active(k_rank_update_c64_tc_t<2, 1>, 2);
-      if (cache) {
-        clusters4[dev] = c4;
-        clusters2[dev] = c2;
-        done[dev] = true;
-      }
-    } else {
-      c4 = clusters4[dev];
-      c2 = clusters2[dev];
+      cudaFuncSetAttribute(k_rank_update_c64_tc_t, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
+      if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
   // joint rank p <= 48 (decided on the device): the resident-A form; larger p: a streaming form,
@@ -923,37 +850,9 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
                                                                Fcol, ctl, status, prof_p);
     if (o.nkc <= kRaMaxK) return;
   }
-  auto launch_cluster = [&](auto kernel, int size, int64_t blocks, int max_cl) {
-    const int ncl = (int)(blocks < max_cl ? blocks : max_cl);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)size;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)(size * ncl));
-    cfg.blockDim = dim3(kC64Threads);
-    cfg.dynamicSmemBytes = kC64Smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, tmap, n, o.nrt, o.nct, (int)o.nkc, (const uint8_t*)Aops, (const uint8_t*)Bops,
-                       (const int32_t*)Erow, (const int32_t*)Fcol, ctl, status, prof_p, kRaMaxK);
-  };
-  // the 2x2 form only where it keeps as many SMs busy as the 2x1 form (the GPCs' SM counts
-  // decide how many clusters of each size fit) and has a tile block for every cluster
-  const int64_t blocks4 = ((o.nrt + 1) / 2) * ((o.nct + 1) / 2), blocks2 = ((o.nrt + 1) / 2) * o.nct;
-  if (c4 >= 1 && 4 * c4 >= 2 * c2 && blocks4 >= c4) {
-    launch_cluster(k_rank_update_c64_tc_t<2, 2>, 4, blocks4, c4);
-    return;
-  }
-  if (c2 >= 1 && blocks2 >= 1) {
-    launch_cluster(k_rank_update_c64_tc_t<2, 1>, 2, blocks2, c2);
-    return;
-  }
   const int64_t tiles = o.nrt * o.nct;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  k_rank_update_c64_tc_t<1, 1><<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.nct, (int)o.nkc, Aops, Bops,
+  k_rank_update_c64_tc_t<<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.nct, (int)o.nkc, Aops, Bops,
                                                                     Erow, Fcol, ctl, status, prof_p, kRaMaxK);
 }
 

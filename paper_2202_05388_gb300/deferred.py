@@ -54,7 +54,7 @@ class DeferredOptimizer:
     def init(self):
         self.h.gf_lowrank_init(self.lr, self.ws, self.ws_bytes, self._st())
         self.state.zero_()
-        self.fom.copy_((self.E[-1].abs() ** 2).reshape(1))
+        self.h.gf_lowrank_fom(self.lr, self.fom, self._st())
 
     def evaluate(self):
         self.h.gf_lowrank_eval(self.lr, self.state, self.spec, self.dfom, self._st())

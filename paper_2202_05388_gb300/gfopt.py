@@ -35,7 +35,8 @@ EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_v
            "gf_batch_set_schedule", "gf_batch_destroy", "gf_select_egreedy", "gf_lowrank_workspace_size",
            "gf_lowrank_init", "gf_lowrank_eval", "gf_lowrank_update", "gf_lowrank_count",
            "gf_lowrank_materialize", "gf3_num_unknowns", "gf3_num_candidates", "gf3_workspace_size",
-           "gf3_fill_g0", "gf3_eval_candidates", "gf3_select_topk", "gf3_apply_update", "gf_selftest_timeout"]
+           "gf3_fill_g0", "gf3_eval_candidates", "gf3_select_topk", "gf3_apply_update", "gf_selftest_timeout",
+           "gf_fom", "gf3_fom", "gf_lowrank_fom"]
 
 
 class GfError(RuntimeError):
@@ -108,6 +109,9 @@ def load(path: str = LIB_PATH):
                                                C.POINTER(gf_cand_spec)]),
             "gf_fill_g0": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, P, C.c_size_t, P]),
             "gf_extract_bands": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, P]),
+            "gf_fom": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, C.c_int32, P, P]),
+            "gf3_fom": (C.c_int32, [P, C.POINTER(gf_problem3d), C.c_int32, P, P]),
+            "gf_lowrank_fom": (C.c_int32, [P, C.POINTER(gf_lowrank), P, P]),
             "gf_eval_candidates": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, C.c_int32, P,
                                                C.POINTER(gf_cand_spec), P, P]),
             "gf_select_topk": (C.c_int32, [P, C.POINTER(gf_geom), C.POINTER(gf_cand_spec), P,
@@ -243,6 +247,10 @@ class Handle:
     def gf_extract_bands(self, prob: gf_problem, dtype, stream=None):
         self._check(self.lib.gf_extract_bands(self.h, C.byref(prob), int(dtype), _stream(stream)))
 
+    def gf_fom(self, probs, dtype, fom_out, stream=None):
+        arr = (gf_problem * len(probs))(*probs)
+        self._check(self.lib.gf_fom(self.h, arr, len(probs), int(dtype), _ptr(fom_out), _stream(stream)))
+
     def gf_eval_candidates(self, probs, dtype, state, spec, dfom, stream=None):
         arr = (gf_problem * len(probs))(*probs)
         s = spec_struct(spec)
@@ -307,6 +315,9 @@ class Handle:
     def gf3_fill_g0(self, prob: gf_problem3d, dtype, ws, ws_bytes, stream=None):
         self._check(self.lib.gf3_fill_g0(self.h, C.byref(prob), int(dtype), _ptr(ws), int(ws_bytes), _stream(stream)))
 
+    def gf3_fom(self, prob: gf_problem3d, dtype, fom_out, stream=None):
+        self._check(self.lib.gf3_fom(self.h, C.byref(prob), int(dtype), _ptr(fom_out), _stream(stream)))
+
     def gf3_eval_candidates(self, prob: gf_problem3d, dtype, state, spec, dfom, stream=None):
         s = spec_struct(spec)
         self._check(self.lib.gf3_eval_candidates(self.h, C.byref(prob), int(dtype), _ptr(state), C.byref(s), _ptr(dfom),
@@ -331,6 +342,9 @@ class Handle:
 
     def gf_lowrank_init(self, lr: gf_lowrank, ws, ws_bytes, stream=None):
         self._check(self.lib.gf_lowrank_init(self.h, C.byref(lr), _ptr(ws), int(ws_bytes), _stream(stream)))
+
+    def gf_lowrank_fom(self, lr: gf_lowrank, fom_out, stream=None):
+        self._check(self.lib.gf_lowrank_fom(self.h, C.byref(lr), _ptr(fom_out), _stream(stream)))
 
     def gf_lowrank_eval(self, lr: gf_lowrank, state, spec, dfom, stream=None):
         s = spec_struct(spec)

@@ -77,7 +77,7 @@ class GreedyOptimizer:
         for p in self.probs:
             self.h.gf_fill_g0(p, self.dtype, self.ws, self.ws_bytes, self._st())
         self.state.zero_()
-        self.fom.copy_(sum((E[-1].abs() ** 2) for E in self.E).reshape(1))
+        self.h.gf_fom(self.probs, self.dtype, self.fom, self._st())
 
     def evaluate(self):
         self.h.gf_eval_candidates(self.probs, self.dtype, self.state, self.spec, self.dfom, self._st())
@@ -197,7 +197,7 @@ class GreedyOptimizer3D:
     def fill(self):
         self.h.gf3_fill_g0(self.prob, self.dtype, self.ws, self.ws_bytes, self._st())
         self.state.zero_()
-        self.fom.copy_((self.E[-3:].abs() ** 2).sum().reshape(1))
+        self.h.gf3_fom(self.prob, self.dtype, self.fom, self._st())
 
     def evaluate(self):
         self.h.gf3_eval_candidates(self.prob, self.dtype, self.state, self.spec, self.dfom, self._st())

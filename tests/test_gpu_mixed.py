@@ -17,7 +17,7 @@ from paper_2202_05388_gb300.optimizer import GreedyOptimizer
 
 from gpu_parity import gpu_E, gpu_G, reach_state, rel_err
 
-# complex64 storage rounds every entry to 2^-24 relative; the split-TF32 products keep ~21 bits
+# complex64 storage rounds every entry to 2^-24 relative; the split-FP16 products keep ~22 bits
 C64_TOL_G = 2e-5
 C64_TOL_E = 2e-5
 C64_TOL_DFOM = 1e-4

@@ -1,6 +1,7 @@
 """gf_fill_g0_static -- the fill for callers that cannot allocate a workspace -- checked
-through the C ABI against gf_fill_g0 on two calls in a row (different grid sizes, so the
-shared table is reused with other contents), plus its size limit.  Kept in a file that is
+through the C ABI against gf_fill_g0 on consecutive calls (different grid sizes, so the
+shared table is reused with other contents; narrow grids take the blocked fill, grids wider than
+2048 pixels the row expansion), plus its size limit.  Kept in a file that is
 collected last."""
 import ctypes as C
 
@@ -36,7 +37,10 @@ def test_static_fill_matches_workspace_fill_on_consecutive_calls():
     lib = B.load()
     h = B.Handle(0)
     stream = torch.cuda.current_stream()
-    for nx, ny, dtype in [(41, 29, B.GF_C128), (23, 17, B.GF_C128), (30, 20, B.GF_C64)]:
+    # the last two grids are wider than the blocked fill handles (nx > 2048), so the static
+    # table is read by the row-expansion kernel as well
+    for nx, ny, dtype in [(41, 29, B.GF_C128), (23, 17, B.GF_C128), (30, 20, B.GF_C64),
+                          (2100, 1, B.GF_C128), (2100, 1, B.GF_C64)]:
         g = W.small(nx, ny).geoms[0]
         Gr, Er, br, pr = _buffers(g, dtype)
         Gs, Es, bs, ps = _buffers(g, dtype)
