@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--graph", action="store_true",
                     help="capture the K timed steps in one CUDA graph and time its replay")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision vs FP64 comparison on the 320x320 geometry")
+    ap.add_argument("--mixed-err-steps", type=int, default=3,
+                    help="lock-step steps of the mixed form's error statement against the FP64 path")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--update-algo", choices=["tc", "dfma", "tensor"], default="tc",
                     help="arithmetic of the G update (gf_set_update_algo): the fastest form per case "
                          "(default), FP64 FMA, or the tensor-core forms at every size")
@@ -234,10 +239,32 @@ def blas_threads():
         return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
-def cpu_baseline(wl, budget_s):
+SINGLE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def oracle_sample_single_thread(wl_name, budget_s):
+    """The same bounded oracle sample in a child process whose BLAS runs one thread (the
+    thread count of numpy's BLAS is fixed when it loads, so it takes a fresh process)."""
+    env = dict(os.environ)
+    for k in SINGLE_THREAD_ENV:
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", f"{wl_name}:{budget_s}"],
+                       env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(wl, budget_s, wl_name="brush_192"):
     step, desc, parts = oracle_step_sample(wl, budget_s)
-    return {"value": 1.0 / step, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-            "sample": desc, "seconds_per_step": step, "parts_s": parts}
+    out = {"value": 1.0 / step, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+           "sample": desc, "seconds_per_step": step, "parts_s": parts}
+    one = oracle_sample_single_thread(wl_name, max(2.0, budget_s / 2))
+    if one is not None:
+        out["single_thread"] = {"value": 1.0 / one["seconds_per_step"], "unit": UNIT, "cores": 1,
+                                "seconds_per_step": one["seconds_per_step"], "parts_s": one["parts_s"],
+                                "note": "same sample, BLAS limited to one thread in a child process"}
+    return out
 
 
 # ------------------------------------------------------------------------------ dist
@@ -358,6 +385,102 @@ def run_batch(args):
             "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def mixed_comparison(K, err_steps, dev):
+    """The mixed-precision form against the plain FP64 form on one geometry (320x320 pixels,
+    dx = lambda/20, focus 5 lambda past the far edge), both timed over steps 1..K from the vacuum
+    start (fill excluded): complex64 G with the top-32 rank-k p Woodbury update, and complex128 G
+    with one brush (rank 4) per step.  Then the error statement: the complex64 form and the
+    library's complex128 path run lock-step on the complex64 form's own choices for err_steps
+    steps from vacuum (the complex128 path applies the same ids; it matches the FP64 oracle
+    within 1e-10 in the parity tests), comparing E, the FOM and 4096 sampled G entries after
+    every step.  Each G is freed before the next one is allocated, except the two of the
+    lock-step run (84 + 168 GB)."""
+    import gc
+    import torch
+    from paper_2202_05388_gb300.optimizer import GreedyOptimizer
+
+    peak_hbm, peak_kind = measured_peaks()
+
+    def free():
+        gc.collect()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+    def timed(wl):
+        opt = GreedyOptimizer(wl.geoms, wl.spec, dtype=wl.dtype, device=dev)
+        opt.fill()
+        acc = torch.zeros(1, dtype=torch.int64, device=f"cuda:{dev}")
+        torch.cuda.synchronize()
+        opt.h.gf_profile_begin(K + 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            opt.step()
+            acc += opt.applied.to(torch.int64)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms, kn, kb, _ = opt.h.gf_profile_end()
+        flips = int(acc.item())
+        gbs = (kb / kn) / (kms / kn * 1e-3) / 1e9 if kn else 0.0
+        return opt, {"flips_per_s": flips / (ms / 1e3), "ms_per_step": ms / K, "accepted_flips": flips,
+                     "update_ms_avg": kms / max(kn, 1), "update_GBps": gbs, "update_frac": gbs / peak_hbm,
+                     "update_launches": kn}
+
+    wl64, wl128 = W.brush_320_topk(), W.brush_320_c128()
+    # load every kernel of the complex64 top-k path first (both update forms) on a small member
+    warm = GreedyOptimizer(W.brush_128_topk().geoms, W.brush_128_topk().spec, dtype="c64", device=dev)
+    warm.fill()
+    for _ in range(3):
+        warm.step()
+    del warm
+    free()
+    o128, r128 = timed(wl128)
+    del o128
+    free()
+    o64, r64 = timed(wl64)
+    # error statement: lock-step from vacuum against the complex128 path on the same choices
+    o64.fill()
+    ref = GreedyOptimizer(wl64.geoms, wl64.spec, dtype="c128", device=dev)
+    ref.fill()
+    n = wl64.geoms[0].N + 1
+    rng = np.random.default_rng(5)
+    ri = torch.tensor(rng.integers(0, n, 4096), device=f"cuda:{dev}")
+    ci = torch.tensor(rng.integers(0, n, 4096), device=f"cuda:{dev}")
+    per_step = []
+    t0 = time.perf_counter()
+    for t in range(err_steps):
+        o64.step()
+        ref.idx.copy_(o64.idx)
+        ref.status.copy_(o64.status)
+        ref.update()
+        torch.cuda.synchronize()
+        g64 = o64.G[0][ri, ci].to(torch.complex128)
+        g128 = ref.G[0][ri, ci]
+        eG = float((g64 - g128).abs().max() / g128.abs().max())
+        eE = float((o64.E[0] - ref.E[0]).abs().max() / ref.E[0].abs().max())
+        f64, f128 = float(o64.fom.cpu()[0]), float(ref.fom.cpu()[0])
+        same = bool(torch.equal(o64.state, ref.state))
+        per_step.append({"step": t + 1, "applied": int(o64.applied.cpu()[0]), "G_sampled_rel": eG, "E_rel": eE,
+                         "FOM_rel": abs(f64 - f128) / f128, "same_decision": same})
+    err_s = time.perf_counter() - t0
+    del o64, ref
+    free()
+    return {"workload": wl64.name, "fp64_workload": wl128.name, "window": f"steps 1..{K} from the vacuum start "
+            "(fill excluded), K CUDA-event-timed eager steps", "mixed": r64, "fp64": r128,
+            "flips_ratio_mixed_over_fp64": r64["flips_per_s"] / r128["flips_per_s"],
+            "peak_kind": peak_kind,
+            "error_vs_fp64": {"steps": err_steps, "per_step": per_step,
+                              "G_sampled_rel_max": max(x["G_sampled_rel"] for x in per_step),
+                              "E_rel_max": max(x["E_rel"] for x in per_step),
+                              "FOM_rel_max": max(x["FOM_rel"] for x in per_step),
+                              "reference": "the library's complex128 path applying the complex64 form's choices "
+                                           "(within 1e-10 of the FP64 oracle in the parity tests)",
+                              "metric": "max-norm relative: max |x64 - x128| / max |x128| over 4096 seeded G "
+                                        "entries, all of E; |FOM64 - FOM128| / FOM128",
+                              "seconds": err_s}}
 
 
 def run_native(args):
@@ -519,6 +642,14 @@ def run_native(args):
                    "column_drift_max": max(rr[0][0][1:]) if len(rr[0][0]) > 1 else None,
                    "gmres_iters": rr[0][1], "columns": 8}
 
+    ncand_main, G_GB_main = opt.ncand, opt.G[0].numel() * opt.G[0].element_size() / 1e9
+    mixed = None
+    if rank == 0 and world == 1 and args.workload == "brush_192" and not args.no_mixed:
+        # the dense 192x192 problem is freed first: the comparison needs up to 252 GB of HBM
+        opt2 = None
+        del opt
+        mixed = mixed_comparison(args.steps, args.mixed_err_steps, dev)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -557,8 +688,8 @@ def run_native(args):
         f16_peak, f16_kind = f16_peak_tflops()
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
                 "frac": achieved_gbs / peak_hbm, "traffic": None, "peak_kind": peak_kind,
-                "kernel": "k_rank_update_c64_ra (p <= 48: resident A blocks) / k_rank_update_c64_tc_t (p > 48: "
-                          "streaming, 2-CTA clusters); tcgen05 kind::f16, scaled split-FP16, 3 products; "
+                "kernel": "k_rank_update_c64_ra (p <= 48: resident A blocks) / k_rank_update_c64_wide (p > 48: "
+                          "streaming 128 x 256 tiles); tcgen05 kind::f16, scaled split-FP16, 3 products; "
                           "+ D A^-1 + S GEMM + operand prep",
                 "tensor_achieved_tflops": achieved_tfl, "tensor_peak_tflops": f16_peak, "tensor_peak_kind": f16_kind,
                 "tensor_frac": achieved_tfl / f16_peak,
@@ -583,13 +714,13 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.dtype == "c128" else "f32",
             "data": "synthetic",
             "config": {"workload": wl.name, "nx": g.nx, "ny": g.ny, "n": g.N + 1,
-                       "candidates": opt.ncand, "G_GB": opt.G[0].numel() * opt.G[0].element_size() / 1e9,
+                       "candidates": ncand_main, "G_GB": G_GB_main,
                        "storage": wl.dtype, "k": wl.spec.k, "nlam": nlam,
-                       "l2": "inputs larger than L2 (G is %.1f GB per replica)" % (opt.G[0].numel() * opt.G[0].element_size() / 1e9 * nlam),
+                       "l2": "inputs larger than L2 (G is %.1f GB per replica)" % (G_GB_main * nlam),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "timed_as": "one CUDA-graph replay of the K steps" if args.graph else "K eager steps",
                        "update_algo": args.update_algo},
-            "candidate_evals_per_s": opt.ncand * args.steps * world / (t_max / 1e3),
+            "candidate_evals_per_s": ncand_main * args.steps * world / (t_max / 1e3),
             "g_update_GBps": achieved_gbs,
             "accepted_flips": flips_total,
             "roofline": roof,
@@ -603,7 +734,7 @@ def run_native(args):
     if refresh is not None:
         line["refresh"] = refresh
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget, args.workload)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -942,6 +1073,11 @@ def run_metalens3d_full(args):
 
 def main():
     args = parse()
+    if args.oracle_sample:
+        name, budget = args.oracle_sample.split(":")
+        step, desc, parts = oracle_step_sample(workload(name), float(budget))
+        print(json.dumps({"seconds_per_step": step, "parts_s": parts, "sample": desc}), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.workload.startswith("batch_48"):

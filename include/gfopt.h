@@ -196,14 +196,36 @@ gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, i
  *   resid_out[1+s] = ||G[:, cols[s]] - g||_2 / ||g||_2 where (I - G0 X) g = G0[:, cols[s]] is
  *                    solved by restarted GMRES(restart) from the stored column to relative
  *                    residual tol (at most max_iter iterations; iters_out[s] = iterations, may
- *                    be NULL).
+ *                    be NULL).  A stored column that already meets tol takes no iteration and
+ *                    reads 0 here; its backward error is in colres_out.
+ *   colres_out[s]  (host, nsample doubles, may be NULL) = ||G0[:, c] - (I - G0 X) G[:, c]||_2 /
+ *                    ||G0[:, c]||_2 for c = cols[s], the stored column's own Eq. 2 residual
+ *                    (its forward error is at most the condition number of I - G0 X times it).
  * cols: host array of nsample indices in [0, n).  Blocking: returns after synchronising
  * `stream`.  ws: at least gf_refresh_workspace_size() bytes.  nx, ny <= 4096. */
 size_t gf_refresh_workspace_size(const gf_geom* geom, int32_t restart);
 gf_status gf_refresh(gf_handle* h, const gf_problem* prob, int32_t dtype, const uint8_t* state,
                      int32_t nsample, const int32_t* cols, int32_t restart, int32_t max_iter,
-                     double tol, double* resid_out, int32_t* iters_out, void* ws, size_t ws_bytes,
-                     void* stream);
+                     double tol, double* resid_out, int32_t* iters_out, double* colres_out, void* ws,
+                     size_t ws_bytes, void* stream);
+
+/* Field repair of one wavelength (the discrete Eq. 3, (I - G0 X) E = E_inc).  Computes
+ * rho = ||E_inc - (I - G0 X) E||_2 / ||E_inc||_2 with the FFT matvec of gf_refresh; when
+ * rho > e_tol, re-solves the system by restarted GMRES(restart) from the stored E to relative
+ * residual tol (at most max_iter iterations) and replaces E by the solution if its residual is
+ * smaller.  G is not read or changed.  The FOM of the new field is not written: call gf_fom.
+ * report (host): e_residual = rho on entry, e_residual_after = the residual of E on return,
+ * e_iters = GMRES iterations (0 when E was kept), e_replaced = 1 when E was replaced.
+ * Blocking (synchronises `stream`); ws as for gf_refresh; nx, ny <= 4096. */
+typedef struct gf_refresh_report {
+  double e_residual;
+  double e_residual_after;
+  int32_t e_iters;
+  int32_t e_replaced;
+} gf_refresh_report;
+gf_status gf_refresh_field(gf_handle* h, const gf_problem* prob, int32_t dtype, const uint8_t* state,
+                           double e_tol, int32_t restart, int32_t max_iter, double tol,
+                           gf_refresh_report* report, void* ws, size_t ws_bytes, void* stream);
 
 /* Arithmetic of the G update (Eq. 10).  GF_UPDATE_TC (default), the fast form per case:
  *   complex128, p <= 4: exact digit products on the tensor cores with an integer

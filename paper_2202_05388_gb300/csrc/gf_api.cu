@@ -399,7 +399,7 @@ size_t gf_refresh_workspace_size(const gf_geom* g, int32_t restart) {
 
 gf_status gf_refresh(gf_handle* h, const gf_problem* prob, int32_t dtype, const uint8_t* state, int32_t nsample,
                      const int32_t* cols, int32_t restart, int32_t max_iter, double tol, double* resid_out,
-                     int32_t* iters_out, void* ws, size_t ws_bytes, void* stream) {
+                     int32_t* iters_out, double* colres_out, void* ws, size_t ws_bytes, void* stream) {
   if (!h) return GF_EINVAL;
   gf_status s = check_problem(h, prob, dtype, false);
   if (s) return s;
@@ -416,9 +416,31 @@ gf_status gf_refresh(gf_handle* h, const gf_problem* prob, int32_t dtype, const 
   if (!ws || ((uintptr_t)ws & 255u)) return fail(h, GF_EINVAL, "workspace must be non-NULL and 256-byte aligned");
   if (ws_bytes < need) return fail(h, GF_ENOMEM, "workspace has %zu bytes, refresh needs %zu", ws_bytes, need);
   if ((s = bind_device(h))) return s;
-  s = gf::refresh(*prob, dtype, state, nsample, cols, restart, max_iter, tol, resid_out, iters_out,
+  s = gf::refresh(*prob, dtype, state, nsample, cols, restart, max_iter, tol, resid_out, iters_out, colres_out,
                   reinterpret_cast<char*>(ws), (cudaStream_t)stream);
   if (s) return cuda_check(h, "gf_refresh");
+  return GF_OK;
+}
+
+gf_status gf_refresh_field(gf_handle* h, const gf_problem* prob, int32_t dtype, const uint8_t* state, double e_tol,
+                           int32_t restart, int32_t max_iter, double tol, gf_refresh_report* report, void* ws,
+                           size_t ws_bytes, void* stream) {
+  if (!h) return GF_EINVAL;
+  gf_status s = check_problem(h, prob, dtype, false);
+  if (s) return s;
+  if (prob->geom.nx > 4096 || prob->geom.ny > 4096) return fail(h, GF_EINVAL, "gf_refresh_field supports nx, ny <= 4096");
+  if (!state || !report) return fail(h, GF_EINVAL, "state and report must be non-NULL");
+  if (restart < 1 || restart > 200) return fail(h, GF_EINVAL, "restart must be in [1, 200]");
+  if (max_iter < 1) return fail(h, GF_EINVAL, "max_iter must be >= 1");
+  if (!(tol > 0.0) || !isfinite(tol)) return fail(h, GF_EINVAL, "tol must be positive");
+  if (!(e_tol >= 0.0) || !isfinite(e_tol)) return fail(h, GF_EINVAL, "e_tol must be >= 0");
+  const size_t need = gf::refresh_workspace_size(prob->geom, restart);
+  if (!ws || ((uintptr_t)ws & 255u)) return fail(h, GF_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < need) return fail(h, GF_ENOMEM, "workspace has %zu bytes, refresh needs %zu", ws_bytes, need);
+  if ((s = bind_device(h))) return s;
+  s = gf::refresh_field(*prob, state, e_tol, restart, max_iter, tol, report, reinterpret_cast<char*>(ws),
+                        (cudaStream_t)stream);
+  if (s) return cuda_check(h, "gf_refresh_field");
   return GF_OK;
 }
 

@@ -149,7 +149,7 @@ OzLayout oz_layout(int64_t n);
 
 // Operand blocks of the complex64 tensor-core update (K = 2P real, P = p rounded up to 16).
 struct C64Layout {
-  int64_t P, K, nkc, nrt, nct;
+  int64_t P, K, nkc, nrt, nct, ncp;
   size_t bytesA, bytesB, bytesM, bytesE, bytesF;
 };
 C64Layout c64_layout(int64_t n, int pmax);
@@ -259,7 +259,10 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
 
 size_t refresh_workspace_size(const gf_geom& g, int restart);
 gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int nsample, const int32_t* cols,
-                  int restart, int max_iter, double tol, double* resid, int32_t* iters, char* ws, cudaStream_t st);
+                  int restart, int max_iter, double tol, double* resid, int32_t* iters, double* colres, char* ws,
+                  cudaStream_t st);
+gf_status refresh_field(const gf_problem& prob, const uint8_t* state, double e_tol, int restart, int max_iter,
+                        double tol, gf_refresh_report* rep, char* ws, cudaStream_t st);
 
 void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state,
                    const gf_cand_spec& spec, const int32_t* idx, int32_t* status, double* fom_out,

@@ -433,10 +433,9 @@ static int gmres(const RefCtx& c, int max_iter, double tol) {
 
 size_t refresh_workspace_size(const gf_geom& g, int restart) { return ref_layout(g, restart).total; }
 
-gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int nsample, const int32_t* cols,
-                  int restart, int max_iter, double tol, double* resid, int32_t* iters, char* ws, cudaStream_t st) {
-  const gf_geom& g = prob.geom;
-  RefCtx c;
+// Twiddles, the background table and the FFT of the embedded Toeplitz kernel: the set-up every
+// G0 X v product of a refresh call needs.
+static void ref_setup(RefCtx& c, const gf_geom& g, const uint8_t* state, int restart, char* ws, cudaStream_t st) {
   c.g = &g;
   c.L = ref_layout(g, restart);
   c.ws = ws;
@@ -451,6 +450,23 @@ gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int n
   launch_fill_table(g, P(c, L.table), st);
   k_embed<<<c.blocks, 256, 0, st>>>(P(c, L.table), g.nx, g.ny, L.Lx, L.Ly, P(c, L.khat));
   fft2(P(c, L.khat), L.Lx, L.Ly, -1.0, P(c, L.twx), P(c, L.twy), st);
+}
+
+// ||b - (I - G0 X) x|| / ||b||, using w and r as scratch
+static double rel_residual(const RefCtx& c, const cplx* x, const cplx* b) {
+  const RefLayout& L = c.L;
+  apply(c, x, P(c, L.w), 1.0, -1.0);
+  k_diff<<<c.blocks, 256, 0, c.st>>>(P(c, L.r), b, P(c, L.w), L.n);
+  return norm2_host(c, P(c, L.r)) / norm2_host(c, b);
+}
+
+gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int nsample, const int32_t* cols,
+                  int restart, int max_iter, double tol, double* resid, int32_t* iters, double* colres, char* ws,
+                  cudaStream_t st) {
+  const gf_geom& g = prob.geom;
+  RefCtx c;
+  ref_setup(c, g, state, restart, ws, st);
+  const RefLayout& L = c.L;
   // Eq. 3 residual of E: r = E - E_inc - G0 X E
   const cplx* E = reinterpret_cast<const cplx*>(prob.E);
   const double k0 = 2.0 * M_PI / g.wavelength;
@@ -462,12 +478,43 @@ gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int n
   for (int s = 0; s < nsample; ++s) {
     k_column_rhs<<<c.blocks, 256, 0, st>>>(P(c, L.table), g.nx, g.ny, cols[s], prob.G, dtype, prob.ldg, P(c, L.b),
                                            P(c, L.x));
+    // backward error of the stored column (Eq. 2): ||G0[:, c] - (I - G0 X) G[:, c]|| / ||G0[:, c]||
+    if (colres) colres[s] = rel_residual(c, P(c, L.x), P(c, L.b));
     const int its = gmres(c, max_iter, tol);     // x: stored column -> refined solution
     if (iters) iters[s] = its;
     k_column_rhs<<<c.blocks, 256, 0, st>>>(P(c, L.table), g.nx, g.ny, cols[s], prob.G, dtype, prob.ldg, P(c, L.b),
                                            P(c, L.w));                 // w = stored column again
     k_diff<<<c.blocks, 256, 0, st>>>(P(c, L.r), P(c, L.w), P(c, L.x), L.n);
     resid[1 + s] = norm2_host(c, P(c, L.r)) / norm2_host(c, P(c, L.x));
+  }
+  cudaStreamSynchronize(st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GF_OK : GF_ECUDA;
+}
+
+gf_status refresh_field(const gf_problem& prob, const uint8_t* state, double e_tol, int restart, int max_iter,
+                        double tol, gf_refresh_report* rep, char* ws, cudaStream_t st) {
+  const gf_geom& g = prob.geom;
+  RefCtx c;
+  ref_setup(c, g, state, restart, ws, st);
+  const RefLayout& L = c.L;
+  cplx* E = reinterpret_cast<cplx*>(prob.E);
+  const double k0 = 2.0 * M_PI / g.wavelength;
+  k_einc<<<c.blocks, 256, 0, st>>>(g.nx, g.ny, g.dx, k0, g.mon_y, P(c, L.b));   // b = E_inc
+  const double r0 = rel_residual(c, E, P(c, L.b));               // ||E_inc - (I - G0 X) E|| / ||E_inc||
+  rep->e_residual = r0;
+  rep->e_residual_after = r0;
+  rep->e_iters = 0;
+  rep->e_replaced = 0;
+  if (r0 > e_tol) {
+    k_scale<<<c.blocks, 256, 0, st>>>(P(c, L.x), E, L.n, 1.0);    // x = E, the initial guess
+    rep->e_iters = gmres(c, max_iter, tol);
+    const double r1 = rel_residual(c, P(c, L.x), P(c, L.b));
+    if (r1 < r0) {
+      k_scale<<<c.blocks, 256, 0, st>>>(E, P(c, L.x), L.n, 1.0);
+      rep->e_residual_after = r1;
+      rep->e_replaced = 1;
+    }
   }
   cudaStreamSynchronize(st);
   cudaError_t e = cudaGetLastError();

@@ -7,11 +7,12 @@
 // here by p parallel FP64 column solves and scaled by D.  S is an FP32 GEMM of that p x p
 // matrix with the p rows G[V, :].  The n x n update runs on the tensor cores as one real GEMM
 // in the 4M form (K = 2P, P = p rounded up to 16).  Each row of A' (each column of B') is
-// scaled by a power of two 2^E_i (2^F_j) into (-1, 1) and split into two FP16 halves,
-// x = hi + 2^-11 lo; three products per K-step (hi*hi into one FP32 TMEM accumulator, hi*lo +
-// lo*hi into a second) keep about 22 bits of each product, and the epilogue forms
-// 2^(E_i + F_j) (D1 + 2^-11 D2).  FP16 halves cost 2 bytes per value (half of split TF32)
-// and run at twice the TF32 tensor rate.
+// scaled by a power of two into (-2^14, 2^14), x' = 2^(14 - E_i) x (2^(14 - F_j) x), and split
+// into two FP16 values, x' = hi + lo with hi = fp16(x') and lo = fp16(x' - hi).  Three products
+// per K step, hi*hi + hi*lo + lo*hi, accumulate into one FP32 TMEM accumulator (the dropped
+// lo*lo term and the rounding of lo are below 2^-22 of |x'|max |y'|max per product), and the
+// epilogue adds 2^(E_i + F_j - 28) times the accumulator to G.  FP16 values cost 2 bytes each
+// and run at the FP16 tensor rate.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
@@ -24,38 +25,51 @@
 
 namespace gf {
 
-constexpr int kC64M = 128;                 // rows per tile
-constexpr int kC64N = 128;                 // real columns per tile (64 complex)
-constexpr int kC64KC = 32;                 // real K per operand chunk
-constexpr int kC64Half = kC64M * kC64KC * 2;   // one FP16 hi or lo chunk of a 128-row operand: 8 KB
-constexpr int kC64Block = 2 * kC64Half;        // hi + lo: 16 KB (A and B blocks alike)
-constexpr int kC64NSO = 3;                 // operand stages (A block + B block each)
-constexpr int kC64NSG = 4;                 // G half-tile stages (a tile's two 64-column halves)
-constexpr int kC64Box = kC64M * 128;       // TMA box: 128 rows x 128 B (16 complex64)
-constexpr int kC64GTile = 2 * kC64Box;     // one half tile: 32 KB
-constexpr int kC64OpStage = 2 * kC64Block; // 32 KB
-constexpr int kC64BarOff = kC64NSO * kC64OpStage + kC64NSG * kC64GTile;   // 229376
-constexpr int kC64Smem = kC64BarOff + 256;
+constexpr int kC64M = 128;                     // rows per tile
+constexpr int kC64N = 128;                     // real columns per resident-A tile (64 complex)
+constexpr int kC64WN = 256;                    // real columns per streaming tile (128 complex)
+constexpr int kC64KC = 16;                     // K per operand chunk
+constexpr int kC64Half = kC64M * kC64KC * 2;   // hi (or lo) of a 128-row chunk: 4 KB
+constexpr int kC64Block = 2 * kC64Half;        // hi + lo of a 128-row chunk: 8 KB
+constexpr int kC64PairBlock = 2 * kC64Block;   // B chunk of a column-tile pair: 16 KB
+constexpr int kC64Box = kC64M * 128;           // TMA box: 128 rows x 128 B (16 complex64)
+constexpr int kC64GStage = 2 * kC64Box;        // one G stage (two boxes): 32 KB
+constexpr int kC64NSG = 4;                     // G stages
+constexpr int kC64Ops = 96 * 1024;             // operand area (both forms)
+constexpr int kC64BarOff = kC64Ops + kC64NSG * kC64GStage;   // 229376
+constexpr int kC64Smem = kC64BarOff + 512;
 constexpr int kC64EpiWarps = 16;
 constexpr int kC64Threads = 32 * (kC64EpiWarps + 4);   // + G producer, MMA, storer, operand producer
-constexpr int kC64TmemCols = 512;          // two buffers x (D1, D2) of kC64N columns
 constexpr uint64_t kC64TimeoutNs = 2000000000ull;
-constexpr int kC64Group = 8;               // tile raster: groups of 8 row tiles (L2 reuse of operands)
+constexpr uint64_t kC64DrainNs = 100000000ull;
+// streaming raster: groups of 32 row tiles.  The 152 CTAs work on neighbouring tiles of about
+// five column pairs; a group's A chunks (32 x 128 KB at K = 256) stay in L2 and every B chunk is
+// fetched from DRAM once per group.  Measured at 320x320, K = 256: 39.7 ms per update with
+// groups of 8 (B fetched 100 times per launch), 35.6 ms with 32, 43.8 ms with 64 and an L2 prefetch.
+constexpr int kC64Group = 32;
+constexpr int kC64Exp = 14;                    // scaled operands lie in (-2^14, 2^14)
+constexpr int kC64MinExp = -40;                // smallest scale exponent (keeps 2^(E+F-28) normal)
 
-// byte offset of element (r, k) of a 128 x 32 FP16 K-major, no-swizzle chunk: 8 rows x 16 B
-// core matrices, K stride 128 B, row-group stride 512 B
+// byte offset of element (r, k) in the hi (or lo) part of a 128-row x 16-deep FP16 chunk,
+// K-major without swizzle: 8-row x 16-byte core matrices, K neighbour at +128 B (LBO), next
+// 8-row group at +256 B (SBO); two 128-row parts placed back to back form one 256-row operand
+// with the same strides.
 __host__ __device__ __forceinline__ int c64_off(int r, int k) {
-  return (r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+  return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
+constexpr uint32_t kC64Lbo = 128, kC64Sbo = 256;
 
-// x in (-1, 1) -> hi + 2^-11 lo with FP16 hi, lo
+// x' in (-2^14, 2^14) -> hi + lo, both FP16 (x' - hi is exact in FP32)
 __device__ __forceinline__ void f16_split(float x, __half& hi, __half& lo) {
   hi = __float2half_rn(x);
-  const float r = x - __half2float(hi);          // exact in FP32
-  lo = __float2half_rn(r * 2048.0f);
+  lo = __float2half_rn(x - __half2float(hi));
 }
 
-__device__ __forceinline__ int scale_exp(float m) { return m > 0.f ? ilogbf(m) + 1 : 0; }
+// E with |x| < 2^E for every x of a row (column) whose largest magnitude is m
+__device__ __forceinline__ int scale_exp(float m) {
+  const int e = m > 0.f ? ilogbf(m) + 1 : 0;
+  return e < kC64MinExp ? kC64MinExp : e;
+}
 
 __device__ __forceinline__ void st4h(uint8_t* p, __half a, __half b, __half c, __half d) {
   __half2 x = __halves2half2(a, b), y = __halves2half2(c, d);
@@ -69,6 +83,10 @@ __device__ __forceinline__ void st4h(uint8_t* p, __half a, __half b, __half c, _
 // of 4 and every K chunk holds whole groups of four.
 __host__ __device__ int64_t c64_padP(int p) { return (int64_t)((p + 15) / 16) * 16; }
 
+// Operand blocks: A chunk of row tile rt at Aops + (rt nkc + kc) 8 KB = [hi | lo]; B chunk of
+// column-tile pair cp at Bops + (cp nkc + kc) 16 KB = [hi(2cp) | hi(2cp+1) | lo(2cp) | lo(2cp+1)],
+// so a 256-column streaming tile takes one 16 KB copy per chunk and a 128-column tile two 4 KB
+// copies.  Erow: one exponent per row (nrt 128); Fcol: one per complex column (ncp 128).
 C64Layout c64_layout(int64_t n, int pmax) {
   C64Layout o;
   o.P = c64_padP(pmax);
@@ -76,11 +94,12 @@ C64Layout c64_layout(int64_t n, int pmax) {
   o.nkc = o.K / kC64KC;
   o.nrt = (n + kC64M - 1) / kC64M;
   o.nct = (2 * n + kC64N - 1) / kC64N;
+  o.ncp = (o.nct + 1) / 2;
   o.bytesA = (size_t)o.nrt * o.nkc * kC64Block;
-  o.bytesB = (size_t)o.nct * o.nkc * kC64Block;
+  o.bytesB = (size_t)o.ncp * o.nkc * kC64PairBlock;
   o.bytesM = (size_t)pmax * pmax * 8;
   o.bytesE = (size_t)o.nrt * kC64M * 4;
-  o.bytesF = (size_t)o.nct * (kC64N / 2) * 4;
+  o.bytesF = (size_t)o.ncp * (kC64WN / 2) * 4;
   return o;
 }
 
@@ -123,7 +142,8 @@ __global__ void k_c64_inverse(WsLayout L, char* ws, int lam, float2* __restrict_
 }
 
 // ---- S = (D A^{-1}) G[V, :] in FP32, written as scaled split-FP16 B operand blocks ----------
-// One CTA per 64 complex columns (one 128-real-column tile); thread (j, quarter of u range).
+// One CTA per 64 complex columns (one 128-real-column tile, both tiles of the last pair are
+// written); thread (j, quarter of u range).
 __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G, int64_t ldg, int64_t n,
                                                     const float2* __restrict__ Mdai, const int32_t* __restrict__ V,
                                                     const UpdCtl* __restrict__ ctl, int nkc,
@@ -176,9 +196,9 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G
   const float mm = fmaxf(fmaxf(smax[0][jl], smax[1][jl]), fmaxf(smax[2][jl], smax[3][jl]));
   const int F = scale_exp(mm);
   if (q == 0) Fcol[j] = F;
-  const float sc = ldexpf(1.0f, -F);
+  const float sc = ldexpf(1.0f, kC64Exp - F);
   // columns 2j (re) and 2j+1 (im) of B':  k < P: (Re S, Im S);  k >= P: (-Im S, Re S)
-  uint8_t* tile = Bops + ct * (int64_t)nkc * kC64Block;
+  uint8_t* pair = Bops + (ct >> 1) * (int64_t)nkc * kC64PairBlock + (ct & 1) * kC64Half;
   const int c_re = 2 * jl, c_im = 2 * jl + 1;
 #pragma unroll
   for (int a4 = 0; a4 < 32; a4 += 4) {
@@ -192,23 +212,23 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G
       f16_split(-acc[a4 + e].y * sc, nh[e], nl[e]);
     }
     const int kA = u0, kB = P + u0;
-    uint8_t* blkA = tile + (kA / kC64KC) * kC64Block;
-    uint8_t* blkB = tile + (kB / kC64KC) * kC64Block;
+    uint8_t* blkA = pair + (kA / kC64KC) * kC64PairBlock;     // hi part; lo part at + kC64Block
+    uint8_t* blkB = pair + (kB / kC64KC) * kC64PairBlock;
     const int oRa = c64_off(c_re, kA % kC64KC), oIa = c64_off(c_im, kA % kC64KC);
     const int oRb = c64_off(c_re, kB % kC64KC), oIb = c64_off(c_im, kB % kC64KC);
     st4h(blkA + oRa, rh[0], rh[1], rh[2], rh[3]);
-    st4h(blkA + kC64Half + oRa, rl[0], rl[1], rl[2], rl[3]);
+    st4h(blkA + kC64Block + oRa, rl[0], rl[1], rl[2], rl[3]);
     st4h(blkA + oIa, ih[0], ih[1], ih[2], ih[3]);
-    st4h(blkA + kC64Half + oIa, il[0], il[1], il[2], il[3]);
+    st4h(blkA + kC64Block + oIa, il[0], il[1], il[2], il[3]);
     st4h(blkB + oRb, nh[0], nh[1], nh[2], nh[3]);
-    st4h(blkB + kC64Half + oRb, nl[0], nl[1], nl[2], nl[3]);
+    st4h(blkB + kC64Block + oRb, nl[0], nl[1], nl[2], nl[3]);
     st4h(blkB + oIb, rh[0], rh[1], rh[2], rh[3]);
-    st4h(blkB + kC64Half + oIb, rl[0], rl[1], rl[2], rl[3]);
+    st4h(blkB + kC64Block + oIb, rl[0], rl[1], rl[2], rl[3]);
   }
 }
 
 // ---- A operand blocks from C0 (n x pmax FP64): row i -> [Re C0[i, :P), Im C0[i, :P)], scaled
-// by 2^-E_i and split into FP16 halves
+// by 2^(14 - E_i) and split into FP16 hi + lo
 __global__ void k_c64_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n, int64_t nrows_pad,
                                 const UpdCtl* __restrict__ ctl, int nkc, uint8_t* __restrict__ Aops,
                                 int32_t* __restrict__ Erow) {
@@ -224,7 +244,8 @@ __global__ void k_c64_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n
       const cplx c = C0[i * pmax + u];
       m = fmax(m, fmax(fabs(c.re), fabs(c.im)));
     }
-    const int E = m > 0.0 ? ilogb(m) + 1 : 0;
+    int E = m > 0.0 ? ilogb(m) + 1 : 0;
+    if (E < kC64MinExp) E = kC64MinExp;
     Erow[i] = E;
     for (int u0 = 0; u0 < P; u0 += 4) {
       __half rh[4], rl[4], ih[4], il[4];
@@ -232,8 +253,8 @@ __global__ void k_c64_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n
       for (int e = 0; e < 4; ++e) {
         const int u = u0 + e;
         const cplx c = (i < n && u < p) ? C0[i * pmax + u] : mk(0.0, 0.0);
-        f16_split((float)ldexp(c.re, -E), rh[e], rl[e]);
-        f16_split((float)ldexp(c.im, -E), ih[e], il[e]);
+        f16_split((float)ldexp(c.re, kC64Exp - E), rh[e], rl[e]);
+        f16_split((float)ldexp(c.im, kC64Exp - E), ih[e], il[e]);
       }
       const int kA = u0, kB = P + u0;
       uint8_t* blkA = tile + (kA / kC64KC) * kC64Block;
@@ -247,286 +268,55 @@ __global__ void k_c64_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n
   }
 }
 
-// ---- the tensor-core update ------------------------------------------------------------------
-// Persistent, warp-specialised; tiles (128 rows x 64 complex columns) in a grouped raster order,
-// tile t handled by CTA t mod gridDim (so the CTAs work on neighbouring tiles and share the
-// operand blocks through L2).
-//   warps 0..15  epilogue: TMEM accumulator + G tile (shared memory) -> G tile
-//   warp 16      G producer (TMA, 2 boxes per half tile) warp 17  MMA issuer
-//   warp 18      storer (TMA stores)                     warp 19  operand producer (bulk copies)
-struct C64Bars {
-  uint64_t ofull[kC64NSO], oempty[kC64NSO];
-  uint64_t gfull[kC64NSG], gempty[kC64NSG], ebar[kC64NSG];
-  uint64_t tfull[2], tempty[2];
-  uint32_t tslot;
-  int abort;
-};
-
-__device__ __forceinline__ void c64_tile_coords(int64_t t, int64_t nrt, int64_t nct, int64_t& rt, int64_t& ct) {
-  const int64_t per_group = (int64_t)kC64Group * nct;
-  const int64_t g = t / per_group;
-  const int64_t rem = t - g * per_group;
-  const int64_t rows_in_group = (nrt - g * kC64Group) < kC64Group ? (nrt - g * kC64Group) : kC64Group;
-  rt = g * kC64Group + rem % rows_in_group;
-  ct = rem / rows_in_group;
+// 2^(E + F - 28) as an FP32 bit pattern (E, F >= -40 keep the biased exponent >= 19)
+__device__ __forceinline__ float c64_scale(int E, int F) {
+  return __int_as_float((E + F - 2 * kC64Exp + 127) << 23);
 }
 
-// One CTA per SM walks its tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; per tile and K
-// chunk it brings in the A block of its row tile and the B block of its column tile with plain
-// bulk copies into its own shared memory.
-__global__ void __launch_bounds__(kC64Threads, 1)
-k_rank_update_c64_tc_t(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_t nrt, int64_t nct, int nkc,
-                       const uint8_t* __restrict__ Aops, const uint8_t* __restrict__ Bops,
-                       const int32_t* __restrict__ Erow, const int32_t* __restrict__ Fcol,
-                       const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status, int32_t* __restrict__ prof_p,
-                       int nkr_min) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  const int p = ctl->skip ? 0 : ctl->nv;
-  const int nkr = (int)(c64_padP(p) / 16);       // K chunks of this step (K = 2P); nkc is the block stride
-  // uniform over the grid (both CTAs of a cluster); nkr <= nkr_min: the resident-A form took it
-  if (p <= 0 || nkr <= nkr_min) return;
-  if (prof_p && blockIdx.x == 0 && threadIdx.x == 0) *prof_p = p;
-  C64Bars* bars = reinterpret_cast<C64Bars*>(smem + kC64BarOff);
-  uint8_t* ops = smem;                                        // kC64NSO x (A block, B block)
-  uint8_t* gts = smem + kC64NSO * kC64OpStage;                // kC64NSG x G tile
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  volatile int* abort = &bars->abort;
-  constexpr int kWarpGProd = kC64EpiWarps, kWarpMma = kC64EpiWarps + 1, kWarpStore = kC64EpiWarps + 2,
-                kWarpOProd = kC64EpiWarps + 3;
-  const int64_t cid = blockIdx.x, ncl = gridDim.x;
-
-  if (warp == kWarpMma) {
-    tc::tmem_alloc(&bars->tslot, kC64TmemCols);
-    tc::tmem_relinquish();
-  }
-  if (tid == 0) {
-    for (int q = 0; q < kC64NSO; ++q) {
-      tc::mbar_init(&bars->ofull[q], 1);
-      tc::mbar_init(&bars->oempty[q], 1);
-    }
-    for (int q = 0; q < kC64NSG; ++q) {
-      tc::mbar_init(&bars->gfull[q], 1);
-      tc::mbar_init(&bars->gempty[q], 1);
-      tc::mbar_init(&bars->ebar[q], 32 * kC64EpiWarps / 2);   // the epilogue warps of that half
-    }
-    for (int q = 0; q < 2; ++q) {
-      tc::mbar_init(&bars->tfull[q], 1);
-      tc::mbar_init(&bars->tempty[q], kC64EpiWarps);
-    }
-    bars->abort = 0;
-    tc::fence_mbar_init();
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tbase = bars->tslot;
-  const int64_t T = nrt * nct;
-
-  if (warp == kWarpGProd) {
-    if (lane == 0) {
-      int64_t k = 0;
-      for (int64_t t = cid; t < T; t += ncl, ++k) {
-        int64_t rt, ct;
-        c64_tile_coords(t, nrt, nct, rt, ct);
-        bool ok = true;
-        for (int hh = 0; hh < 2; ++hh) {         // the tile's two halves go to their own stages
-          const int64_t u = 2 * k + hh;
-          const int s = (int)(u % kC64NSG);
-          if (u >= kC64NSG && !tc::mbar_wait_or_abort(&bars->gempty[s], (uint32_t)((u / kC64NSG - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
-          const int x0 = (int)(ct * kC64N) + 64 * hh, y = (int)(rt * kC64M);     // x in floats
-          int nbox = 0;
-          if (rt < nrt && ct < nct)              // phantom tile: nothing to load
-            for (int b = 0; b < 2; ++b) nbox += (x0 + 32 * b < 2 * n) ? 1 : 0;
-          if (nbox == 0) {
-            tc::mbar_arrive(&bars->gfull[s]);
-            continue;
-          }
-          tc::mbar_arrive_expect_tx(&bars->gfull[s], (uint32_t)(nbox * kC64Box));
-          uint8_t* gt = gts + s * kC64GTile;
-          for (int b = 0; b < nbox; ++b) tc::tma_load_2d(gt + b * kC64Box, &tmapG, x0 + 32 * b, y, &bars->gfull[s]);
-        }
-        if (!ok) break;
-      }
-    }
-    __syncwarp();
-  } else if (warp == kWarpOProd) {
-    if (lane == 0) {
-      const uint64_t pol_ops = tc::policy_evict_last();    // operand blocks: re-read by many tiles
-      int64_t c = 0;
-      for (int64_t t = cid; t < T; t += ncl) {
-        int64_t rt, ct;
-        c64_tile_coords(t, nrt, nct, rt, ct);
-        bool ok = true;
-        for (int kc = 0; kc < nkr; ++kc, ++c) {
-          const int s = (int)(c % kC64NSO);
-          if (c >= kC64NSO && !tc::mbar_wait_or_abort(&bars->oempty[s], (uint32_t)((c / kC64NSO - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
-          uint8_t* st = ops + s * kC64OpStage;
-          tc::mbar_arrive_expect_tx(&bars->ofull[s], (uint32_t)kC64OpStage);
-          const uint8_t* asrc = Aops + (rt * nkc + kc) * (int64_t)kC64Block;
-          const uint8_t* bsrc = Bops + (ct * nkc + kc) * (int64_t)kC64Block;
-          tc::bulk_g2s_hint(st, asrc, kC64Block, &bars->ofull[s], pol_ops);
-          tc::bulk_g2s_hint(st + kC64Block, bsrc, kC64Block, &bars->ofull[s], pol_ops);
-        }
-        if (!ok) break;
-      }
-      // every copy issued has landed before the CTA may retire
-      for (int64_t q = c - kC64NSO; q < c; ++q) {
-        if (q < 0) continue;
-        tc::mbar_wait_bounded(&bars->ofull[q % kC64NSO], (uint32_t)((q / kC64NSO) & 1), 100000000ull);
-      }
-    }
-    __syncwarp();
-  } else if (warp == kWarpMma) {
-    if (lane == 0) {
-      const uint32_t idesc = tc::idesc_f16(kC64M, kC64N);
-      int64_t k = 0, c = 0;
-      bool ok = true;
-      for (int64_t t = cid; t < T && ok; t += ncl, ++k) {
-        const int b = (int)(k & 1);
-        if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[b], (uint32_t)((k / 2 - 1) & 1), abort, kC64TimeoutNs)) break;
-        tc::fence_after_sync();
-        const uint32_t d1 = tbase + (uint32_t)(b * 2 * kC64N), d2 = d1 + kC64N;
-        for (int kc = 0; kc < nkr; ++kc, ++c) {
-          const int s = (int)(c % kC64NSO);
-          if (!tc::mbar_wait_or_abort(&bars->ofull[s], (uint32_t)((c / kC64NSO) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
-          tc::fence_after_sync();
-          const uint32_t sA = tc::smem_u32(ops + s * kC64OpStage);
-          const uint32_t sB = sA + kC64Block;
+// G += 2^(E + F_j - 28) acc over one 128-byte row of a 128B-swizzled TMA box (16 complex
+// columns: chunk ch holds complex columns 2ch, 2ch+1)
+__device__ __forceinline__ void c64_epilogue_row(uint8_t* row, int r, int Ei, const int (&Fr)[16], const float (&acc)[32]) {
 #pragma unroll
-          for (int ks = 0; ks < kC64KC / 16; ++ks) {
-            const uint32_t off = ks * 256;     // K = 16 FP16 per step = two core matrices
-            const uint64_t ah = tc::smem_desc(sA + off, 128, 512), al = tc::smem_desc(sA + kC64Half + off, 128, 512);
-            const uint64_t bh = tc::smem_desc(sB + off, 128, 512), bl = tc::smem_desc(sB + kC64Half + off, 128, 512);
-            const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
-            tc::mma_f16(d1, ah, bh, idesc, first);
-            tc::mma_f16(d2, ah, bl, idesc, first);
-            tc::mma_f16(d2, al, bh, idesc, 1u);
-          }
-          tc::mma_commit(&bars->oempty[s]);
-        }
-        if (ok) tc::mma_commit(&bars->tfull[b]);
-      }
-      // every MMA issued has completed before the CTA may release TMEM and retire
-      for (int64_t q = c - kC64NSO; q < c; ++q) {
-        if (q < 0) continue;
-        tc::mbar_wait_bounded(&bars->oempty[q % kC64NSO], (uint32_t)((q / kC64NSO) & 1), 100000000ull);
-      }
-    }
-    __syncwarp();
-  } else if (warp < kC64EpiWarps) {
-    const int q = warp & 3, h = warp >> 2;     // TMEM lane quarter, column quarter (32 real columns)
-    const int r = q * 32 + lane;
-    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-    int64_t k = 0;
-    for (int64_t t = cid; t < T; t += ncl, ++k) {
-      int64_t rt, ct;
-      c64_tile_coords(t, nrt, nct, rt, ct);
-      const bool real = rt < nrt && ct < nct;
-      const int b = (int)(k & 1);
-      const int64_t u = 2 * k + (h >> 1);      // this warp's half of the tile
-      const int s = (int)(u % kC64NSG);
-      // the scale exponents first: their loads overlap the waits below
-      const int Ei = real ? Erow[rt * kC64M + r] : 0;
-      int Fr[16];
-      {
-        const int32_t* Fq = Fcol + (real ? ct : 0) * (kC64N / 2) + h * 16;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) Fr[e] = Fq[e];
-      }
-      if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kC64TimeoutNs)) break;
-      if (!tc::mbar_wait_or_abort(&bars->gfull[s], (uint32_t)((u / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
-      tc::fence_after_sync();
-      float acc1[32], acc2[32];
-      {
-        float a0[16], a1[16], a2[16], a3[16];
-        const uint32_t base = tbase + lane_addr + (uint32_t)(b * 2 * kC64N + h * 32);
-        tc::tmem_ld16(base, a0);
-        tc::tmem_ld16(base + 16, a1);
-        tc::tmem_ld16(base + kC64N, a2);
-        tc::tmem_ld16(base + kC64N + 16, a3);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          acc1[e] = a0[e];
-          acc1[16 + e] = a1[e];
-          acc2[e] = a2[e];
-          acc2[16 + e] = a3[e];
-        }
-      }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
-      if (real) {
-        // box h holds real columns 32h .. 32h+31 of the tile = 8 chunks of 16 B (128B swizzle);
-        // chunk ch holds complex columns 2ch, 2ch+1 of this quarter
-        uint8_t* row = gts + s * kC64GTile + (h & 1) * kC64Box + r * 128;
-#pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
-          const float s0 = __int_as_float((Ei + Fr[2 * ch] + 127) << 23);
-          const float s1 = __int_as_float((Ei + Fr[2 * ch + 1] + 127) << 23);
-          float4* gp = reinterpret_cast<float4*>(row + ((ch ^ (r & 7)) << 4));
-          float4 g = *gp;
-          g.x += s0 * fmaf(acc2[4 * ch + 0], 0.00048828125f, acc1[4 * ch + 0]);
-          g.y += s0 * fmaf(acc2[4 * ch + 1], 0.00048828125f, acc1[4 * ch + 1]);
-          g.z += s1 * fmaf(acc2[4 * ch + 2], 0.00048828125f, acc1[4 * ch + 2]);
-          g.w += s1 * fmaf(acc2[4 * ch + 3], 0.00048828125f, acc1[4 * ch + 3]);
-          *gp = g;
-        }
-      }
-      tc::fence_proxy_async_smem();
-      tc::mbar_arrive(&bars->ebar[s]);
-    }
+  for (int ch = 0; ch < 8; ++ch) {
+    const float s0 = c64_scale(Ei, Fr[2 * ch]);
+    const float s1 = c64_scale(Ei, Fr[2 * ch + 1]);
+    float4* gp = reinterpret_cast<float4*>(row + ((ch ^ (r & 7)) << 4));
+    float4 g = *gp;
+    g.x = fmaf(s0, acc[4 * ch + 0], g.x);
+    g.y = fmaf(s0, acc[4 * ch + 1], g.y);
+    g.z = fmaf(s1, acc[4 * ch + 2], g.z);
+    g.w = fmaf(s1, acc[4 * ch + 3], g.w);
+    *gp = g;
   }
-  if (warp == kWarpStore) {
-    if (lane == 0) {
-      int64_t k = 0;
-      for (int64_t t = cid; t < T; t += ncl, ++k) {
-        int64_t rt, ct;
-        c64_tile_coords(t, nrt, nct, rt, ct);
-        bool ok = true;
-        for (int hh = 0; hh < 2; ++hh) {
-          const int64_t u = 2 * k + hh;
-          const int s = (int)(u % kC64NSG);
-          if (!tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)((u / kC64NSG) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
-          {
-            const int x0 = (int)(ct * kC64N) + 64 * hh, y = (int)(rt * kC64M);
-            uint8_t* gt = gts + s * kC64GTile;
-            for (int b = 0; b < 2; ++b)
-              if (x0 + 32 * b < 2 * n) tc::tma_store_2d(&tmapG, x0 + 32 * b, y, gt + b * kC64Box);
-          }
-          tc::bulk_commit();
-          tc::bulk_wait_read0();
-          tc::mbar_arrive(&bars->gempty[s]);
-        }
-        if (!ok) break;
-      }
-      tc::bulk_wait0();
-    }
-    __syncwarp();
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  if (tid == 0 && bars->abort) atomicExch(status, GF_ETIMEOUT);
-  tc::fence_after_sync();
-  if (warp == kWarpMma) tc::tmem_dealloc(tbase, kC64TmemCols);
 }
 
-// ---- resident-A form: joint rank p <= 48 (K <= 96 real) -------------------------------------
-// Each CTA owns one row tile at a time and sweeps a run of its column tiles.  The row tile's A
-// blocks (nkr x 16 KB, at most 48 KB) are loaded once per run and stay in shared memory, so per
-// tile only the B blocks (nkr x 16 KB, a ring of 16 KB stages) and the G tile move: half the
-// operand bytes of the streaming form above.  Runs: the row tiles are taken in groups of
-// gridDim.x; in a full group CTA b takes row tile b of the group across every column tile, all
-// CTAs stepping through the columns together (each B block is read from L2 by every CTA at
-// about the same time); in the last group of R < gridDim.x row tiles each row is split into
-// gridDim.x / R column segments.  Before it retires, every role waits (bounded) for the copies
-// and MMAs it issued, so a CTA that gave up on a wait leaves nothing in flight.
-// A chunks kept resident: K <= 96 real (p <= 48).  At four chunks (64 KB of A) only two B stages
-// would fit beside the four G stages, too few to cover the L2 latency: p > 48 streams instead.
-constexpr int kRaMaxK = 3;
-constexpr int kRaOps = kC64NSO * kC64OpStage;                // 96 KB: A blocks + B ring
-constexpr int kRaMaxB = kRaOps / kC64Block - 1;              // B stages when nkr = 1
-constexpr uint64_t kRaDrainNs = 100000000ull;
+__device__ __forceinline__ void c64_load_f16(const int32_t* __restrict__ Fq, int (&Fr)[16]) {
+  const int4* f4 = reinterpret_cast<const int4*>(Fq);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int4 v = f4[e];
+    Fr[4 * e] = v.x;
+    Fr[4 * e + 1] = v.y;
+    Fr[4 * e + 2] = v.z;
+    Fr[4 * e + 3] = v.w;
+  }
+}
+
+// ---- resident-A form: joint rank p <= 48 (K <= 96) ------------------------------------------
+// Each CTA owns one row tile at a time and sweeps a run of its column tiles (128 rows x 64
+// complex columns).  The row tile's A chunks (nkr x 8 KB, at most 48 KB) are loaded once per run
+// and stay in shared memory, so per tile only the B chunks (a ring of 8 KB stages) and the G
+// tile move.  Runs: the row tiles are taken in groups of gridDim.x; in a full group CTA b takes
+// row tile b of the group across every column tile, all CTAs stepping through the columns
+// together (each B chunk is read from L2 by every CTA at about the same time); in the last group
+// of R < gridDim.x row tiles each row is split into gridDim.x / R column segments.  Before it
+// retires, every role waits (bounded) for the copies and MMAs it issued, so a CTA that gave up on
+// a wait leaves nothing in flight.
+// A chunks kept resident: K <= 96 (p <= 48).  At eight chunks (64 KB of A) the B ring would be
+// too short to cover the L2 latency: p > 48 takes the streaming form below.
+constexpr int kRaMaxK = 6;
+constexpr int kRaMaxB = kC64Ops / kC64Block - 2;             // B stages when nkr = 2 (K = 32)
+constexpr int kRaTmemCols = 256;                             // two buffers x kC64N columns
 
 struct C64RaBars {
   uint64_t bfull[kRaMaxB], bempty[kRaMaxB];
@@ -546,14 +336,14 @@ k_rank_update_c64_ra(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
                      const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int p = ctl->skip ? 0 : ctl->nv;
-  const int nkr = (int)(c64_padP(p) / 16);       // K chunks of this step
+  const int nkr = (int)(c64_padP(p) / 8);        // K chunks of this step (K = 2P)
   if (p <= 0 || nkr > kRaMaxK) return;           // uniform over the grid; larger K: streaming form
   if (prof_p && blockIdx.x == 0 && threadIdx.x == 0) *prof_p = p;
   C64RaBars* bars = reinterpret_cast<C64RaBars*>(smem + kC64BarOff);
-  uint8_t* As = smem;                            // nkr A blocks of the current row tile
+  uint8_t* As = smem;                            // nkr A chunks of the current row tile
   uint8_t* Bs = smem + nkr * kC64Block;          // B ring
-  const int nsb = kRaOps / kC64Block - nkr;      // 2 .. kRaMaxB stages
-  uint8_t* gts = smem + kRaOps;                  // kC64NSG G half tiles
+  const int nsb = kC64Ops / kC64Block - nkr;     // 6 .. kRaMaxB stages
+  uint8_t* gts = smem + kC64Ops;                 // kC64NSG G half tiles
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   volatile int* abort = &bars->abort;
   constexpr int kWarpGProd = kC64EpiWarps, kWarpMma = kC64EpiWarps + 1, kWarpStore = kC64EpiWarps + 2,
@@ -561,7 +351,7 @@ k_rank_update_c64_ra(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
   const int64_t G = gridDim.x, me = blockIdx.x;
 
   if (warp == kWarpMma) {
-    tc::tmem_alloc(&bars->tslot, kC64TmemCols);
+    tc::tmem_alloc(&bars->tslot, kRaTmemCols);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
@@ -605,7 +395,7 @@ k_rank_update_c64_ra(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
           if (nbox == 0) tc::mbar_arrive(&bars->gfull[s]);
           else {
             tc::mbar_arrive_expect_tx(&bars->gfull[s], (uint32_t)(nbox * kC64Box));
-            uint8_t* gt = gts + s * kC64GTile;
+            uint8_t* gt = gts + s * kC64GStage;
             for (int bx = 0; bx < nbox; ++bx) tc::tma_load_2d(gt + bx * kC64Box, &tmapG, x0 + 32 * bx, y, &bars->gfull[s]);
           }
           issued = u + 1;
@@ -613,35 +403,39 @@ k_rank_update_c64_ra(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
       }
       // every load issued has landed before the CTA may retire
       for (int64_t q = issued - kC64NSG; q < issued; ++q)
-        if (q >= 0) tc::mbar_wait_bounded(&bars->gfull[q % kC64NSG], (uint32_t)((q / kC64NSG) & 1), kRaDrainNs);
+        if (q >= 0) tc::mbar_wait_bounded(&bars->gfull[q % kC64NSG], (uint32_t)((q / kC64NSG) & 1), kC64DrainNs);
     }
     __syncwarp();
   } else if (warp == kWarpOProd) {
     if (lane == 0) {
-      const uint64_t pol_ops = tc::policy_evict_last();    // B blocks: read by every row tile
+      const uint64_t pol_ops = tc::policy_evict_last();    // B chunks: read by every row tile
       int64_t c = 0, na = 0;                     // B chunks issued, A loads issued
       bool ok = true;
       RaCursor cur;
       for (bool more = ra_first(cur, nrt, nct, G, me); more && ok; more = ra_next(cur, nrt, nct, G, me)) {
-        if (cur.c == cur.cbeg) {                 // a new run: its row tile's A blocks
+        if (cur.c == cur.cbeg) {                 // a new run: its row tile's A chunks
           if (na >= 1 && !tc::mbar_wait_or_abort(&bars->aempty, (uint32_t)((na - 1) & 1), abort, kC64TimeoutNs)) break;
           tc::mbar_arrive_expect_tx(&bars->afull, (uint32_t)(nkr * kC64Block));
           for (int kc = 0; kc < nkr; ++kc)
             tc::bulk_g2s(As + kc * kC64Block, Aops + (cur.rt * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->afull);
           ++na;
         }
+        // the column tile's half of each pair block: hi at +half 4 KB, lo at +8 KB + half 4 KB
+        const uint8_t* bsrc = Bops + (cur.c >> 1) * (int64_t)nkc * kC64PairBlock + (cur.c & 1) * kC64Half;
+
         for (int kc = 0; kc < nkr; ++kc, ++c) {
           const int s = (int)(c % nsb);
           if (c >= nsb && !tc::mbar_wait_or_abort(&bars->bempty[s], (uint32_t)((c / nsb - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
           tc::mbar_arrive_expect_tx(&bars->bfull[s], (uint32_t)kC64Block);
-          tc::bulk_g2s_hint(Bs + s * kC64Block, Bops + (cur.c * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->bfull[s],
-                            pol_ops);
+          const uint8_t* src = bsrc + kc * (int64_t)kC64PairBlock;
+          tc::bulk_g2s_hint(Bs + s * kC64Block, src, kC64Half, &bars->bfull[s], pol_ops);
+          tc::bulk_g2s_hint(Bs + s * kC64Block + kC64Half, src + kC64Block, kC64Half, &bars->bfull[s], pol_ops);
         }
       }
       // every copy issued has landed before the CTA may retire
-      if (na >= 1) tc::mbar_wait_bounded(&bars->afull, (uint32_t)((na - 1) & 1), kRaDrainNs);
+      if (na >= 1) tc::mbar_wait_bounded(&bars->afull, (uint32_t)((na - 1) & 1), kC64DrainNs);
       for (int64_t q = c - nsb; q < c; ++q)
-        if (q >= 0) tc::mbar_wait_bounded(&bars->bfull[q % nsb], (uint32_t)((q / nsb) & 1), kRaDrainNs);
+        if (q >= 0) tc::mbar_wait_bounded(&bars->bfull[q % nsb], (uint32_t)((q / nsb) & 1), kC64DrainNs);
     }
     __syncwarp();
   } else if (warp == kWarpMma) {
@@ -658,23 +452,18 @@ k_rank_update_c64_ra(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
         const int b = (int)(k & 1);
         if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[b], (uint32_t)((k / 2 - 1) & 1), abort, kC64TimeoutNs)) break;
         tc::fence_after_sync();
-        const uint32_t d1 = tbase + (uint32_t)(b * 2 * kC64N), d2 = d1 + kC64N;
+        const uint32_t d = tbase + (uint32_t)(b * kC64N);
         for (int kc = 0; kc < nkr; ++kc, ++c) {
           const int s = (int)(c % nsb);
           if (!tc::mbar_wait_or_abort(&bars->bfull[s], (uint32_t)((c / nsb) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
           tc::fence_after_sync();
           const uint32_t sA = tc::smem_u32(As + kc * kC64Block);
           const uint32_t sB = tc::smem_u32(Bs + s * kC64Block);
-#pragma unroll
-          for (int ks = 0; ks < kC64KC / 16; ++ks) {
-            const uint32_t off = ks * 256;     // K = 16 FP16 per step = two core matrices
-            const uint64_t ah = tc::smem_desc(sA + off, 128, 512), al = tc::smem_desc(sA + kC64Half + off, 128, 512);
-            const uint64_t bh = tc::smem_desc(sB + off, 128, 512), bl = tc::smem_desc(sB + kC64Half + off, 128, 512);
-            const uint32_t first = (kc == 0 && ks == 0) ? 0u : 1u;
-            tc::mma_f16(d1, ah, bh, idesc, first);
-            tc::mma_f16(d2, ah, bl, idesc, first);
-            tc::mma_f16(d2, al, bh, idesc, 1u);
-          }
+          const uint64_t ah = tc::smem_desc(sA, kC64Lbo, kC64Sbo), al = tc::smem_desc(sA + kC64Half, kC64Lbo, kC64Sbo);
+          const uint64_t bh = tc::smem_desc(sB, kC64Lbo, kC64Sbo), bl = tc::smem_desc(sB + kC64Half, kC64Lbo, kC64Sbo);
+          tc::mma_f16(d, ah, bh, idesc, kc == 0 ? 0u : 1u);
+          tc::mma_f16(d, ah, bl, idesc, 1u);
+          tc::mma_f16(d, al, bh, idesc, 1u);
           tc::mma_commit(&bars->bempty[s]);
         }
         if (!ok) break;
@@ -683,7 +472,7 @@ k_rank_update_c64_ra(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
       }
       // every MMA issued has completed before the CTA may release TMEM and retire
       tc::mma_commit(&bars->drain);
-      tc::mbar_wait_bounded(&bars->drain, 0u, kRaDrainNs);
+      tc::mbar_wait_bounded(&bars->drain, 0u, kC64DrainNs);
     }
     __syncwarp();
   } else if (warp < kC64EpiWarps) {
@@ -700,49 +489,28 @@ k_rank_update_c64_ra(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
       // the scale exponents first: their loads overlap the waits below
       const int Ei = Erow[rt * kC64M + r];
       int Fr[16];
-      {
-        const int32_t* Fq = Fcol + ct * (kC64N / 2) + h * 16;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) Fr[e] = Fq[e];
-      }
+      c64_load_f16(Fcol + ct * (kC64N / 2) + h * 16, Fr);
       if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kC64TimeoutNs)) break;
       if (!tc::mbar_wait_or_abort(&bars->gfull[s], (uint32_t)((u / kC64NSG) & 1), abort, kC64TimeoutNs)) break;
       tc::fence_after_sync();
-      float acc1[32], acc2[32];
+      float acc[32];
       {
-        float a0[16], a1[16], a2[16], a3[16];
-        const uint32_t base = tbase + lane_addr + (uint32_t)(b * 2 * kC64N + h * 32);
+        float a0[16], a1[16];
+        const uint32_t base = tbase + lane_addr + (uint32_t)(b * kC64N + h * 32);
         tc::tmem_ld16(base, a0);
         tc::tmem_ld16(base + 16, a1);
-        tc::tmem_ld16(base + kC64N, a2);
-        tc::tmem_ld16(base + kC64N + 16, a3);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          acc1[e] = a0[e];
-          acc1[16 + e] = a1[e];
-          acc2[e] = a2[e];
-          acc2[16 + e] = a3[e];
+          acc[e] = a0[e];
+          acc[16 + e] = a1[e];
         }
       }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
-      // box h holds real columns 32h .. 32h+31 of the tile = 8 chunks of 16 B (128B swizzle);
-      // chunk ch holds complex columns 2ch, 2ch+1 of this quarter
-      uint8_t* row = gts + s * kC64GTile + (h & 1) * kC64Box + r * 128;
-#pragma unroll
-      for (int ch = 0; ch < 8; ++ch) {
-        const float s0 = __int_as_float((Ei + Fr[2 * ch] + 127) << 23);
-        const float s1 = __int_as_float((Ei + Fr[2 * ch + 1] + 127) << 23);
-        float4* gp = reinterpret_cast<float4*>(row + ((ch ^ (r & 7)) << 4));
-        float4 g = *gp;
-        g.x += s0 * fmaf(acc2[4 * ch + 0], 0.00048828125f, acc1[4 * ch + 0]);
-        g.y += s0 * fmaf(acc2[4 * ch + 1], 0.00048828125f, acc1[4 * ch + 1]);
-        g.z += s1 * fmaf(acc2[4 * ch + 2], 0.00048828125f, acc1[4 * ch + 2]);
-        g.w += s1 * fmaf(acc2[4 * ch + 3], 0.00048828125f, acc1[4 * ch + 3]);
-        *gp = g;
-      }
+      // box h & 1 of the half tile holds real columns 32h .. 32h+31 of the tile
+      c64_epilogue_row(gts + s * kC64GStage + (h & 1) * kC64Box + r * 128, r, Ei, Fr, acc);
       tc::fence_proxy_async_smem();
       tc::mbar_arrive(&bars->ebar[s]);
     }
@@ -758,7 +526,7 @@ k_rank_update_c64_ra(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
           const int s = (int)(u % kC64NSG);
           if (!tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)((u / kC64NSG) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
           const int x0 = (int)(cur.c * kC64N) + 64 * hh, y = (int)(cur.rt * kC64M);
-          uint8_t* gt = gts + s * kC64GTile;
+          uint8_t* gt = gts + s * kC64GStage;
           for (int bx = 0; bx < 2; ++bx)
             if (x0 + 32 * bx < 2 * n) tc::tma_store_2d(&tmapG, x0 + 32 * bx, y, gt + bx * kC64Box);
           tc::bulk_commit();
@@ -774,7 +542,236 @@ k_rank_update_c64_ra(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64
   __syncthreads();
   if (tid == 0 && bars->abort) atomicExch(status, GF_ETIMEOUT);
   tc::fence_after_sync();
-  if (warp == kWarpMma) tc::tmem_dealloc(tbase, kC64TmemCols);
+  if (warp == kWarpMma) tc::tmem_dealloc(tbase, kRaTmemCols);
+}
+
+// ---- streaming form: joint rank p > 48 (K up to 256) ----------------------------------------
+// Persistent, warp-specialised; tiles of 128 rows x 128 complex columns (256 real: one column-
+// tile pair of the operand blocks) in a grouped raster order, tile t handled by CTA t mod
+// gridDim (neighbouring CTAs share the operand chunks through L2).  Per 16-deep K chunk a CTA
+// brings in 8 KB of A and 16 KB of B (a 24 KB stage, four stages), so a 128 KB G tile costs
+// 3 operand bytes per G byte; the accumulator is one 128 x 256 FP32 block (256 TMEM columns,
+// double-buffered).  G moves as four 32 KB quarter tiles (two TMA boxes each), so a whole tile's
+// G is staged while the MMAs of the next tile run.
+//   warps 0..15  epilogue (lane quarter q = warp & 3, column quarter h = warp >> 2)
+//   warp 16      G producer    warp 17  MMA issuer    warp 18  storer    warp 19  operand producer
+// Before it retires, every role waits (bounded) for the copies and MMAs it issued.
+constexpr int kWsStage = kC64Block + kC64PairBlock;          // 24 KB
+constexpr int kWsNSO = kC64Ops / kWsStage;                   // 4 operand stages
+constexpr int kWsTmemCols = 512;                             // two buffers x kC64WN columns
+static_assert(kWsStage % 1024 == 0 && kWsNSO == 4, "operand stages");
+
+struct C64WBars {
+  uint64_t ofull[kWsNSO], oempty[kWsNSO];
+  uint64_t gfull[kC64NSG], gempty[kC64NSG], ebar[kC64NSG];
+  uint64_t tfull[2], tempty[2];
+  uint64_t drain;
+  uint32_t tslot;
+  int abort;
+};
+static_assert(sizeof(C64WBars) <= kC64Smem - kC64BarOff, "barrier block");
+
+__device__ __forceinline__ void c64_tile_coords(int64_t t, int64_t nrt, int64_t ncol, int64_t& rt, int64_t& ct) {
+  const int64_t per_group = (int64_t)kC64Group * ncol;
+  const int64_t g = t / per_group;
+  const int64_t rem = t - g * per_group;
+  const int64_t rows_in_group = (nrt - g * kC64Group) < kC64Group ? (nrt - g * kC64Group) : kC64Group;
+  rt = g * kC64Group + rem % rows_in_group;
+  ct = rem / rows_in_group;
+}
+
+__global__ void __launch_bounds__(kC64Threads, 1)
+k_rank_update_c64_wide(const __grid_constant__ CUtensorMap tmapG, int64_t n, int64_t nrt, int64_t ncp, int nkc,
+                       const uint8_t* __restrict__ Aops, const uint8_t* __restrict__ Bops,
+                       const int32_t* __restrict__ Erow, const int32_t* __restrict__ Fcol,
+                       const UpdCtl* __restrict__ ctl, int32_t* __restrict__ status, int32_t* __restrict__ prof_p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int p = ctl->skip ? 0 : ctl->nv;
+  const int nkr = (int)(c64_padP(p) / 8);        // K chunks of this step (K = 2P); nkc is the block stride
+  if (p <= 0 || nkr <= kRaMaxK) return;          // uniform over the grid; the resident-A form took it
+  if (prof_p && blockIdx.x == 0 && threadIdx.x == 0) *prof_p = p;
+  C64WBars* bars = reinterpret_cast<C64WBars*>(smem + kC64BarOff);
+  uint8_t* ops = smem;                           // kWsNSO x (A chunk, B pair chunk)
+  uint8_t* gts = smem + kC64Ops;                 // kC64NSG G quarter tiles
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  volatile int* abort = &bars->abort;
+  constexpr int kWarpGProd = kC64EpiWarps, kWarpMma = kC64EpiWarps + 1, kWarpStore = kC64EpiWarps + 2,
+                kWarpOProd = kC64EpiWarps + 3;
+  const int64_t cid = blockIdx.x, ncl = gridDim.x;
+  const int64_t T = nrt * ncp;
+
+  if (warp == kWarpMma) {
+    tc::tmem_alloc(&bars->tslot, kWsTmemCols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int q = 0; q < kWsNSO; ++q) {
+      tc::mbar_init(&bars->ofull[q], 1);
+      tc::mbar_init(&bars->oempty[q], 1);
+    }
+    for (int q = 0; q < kC64NSG; ++q) {
+      tc::mbar_init(&bars->gfull[q], 1);
+      tc::mbar_init(&bars->gempty[q], 1);
+      tc::mbar_init(&bars->ebar[q], 32 * kC64EpiWarps / 4);   // the four epilogue warps of that quarter
+    }
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&bars->tfull[q], 1);
+      tc::mbar_init(&bars->tempty[q], kC64EpiWarps);
+    }
+    tc::mbar_init(&bars->drain, 1);
+    bars->abort = 0;
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = bars->tslot;
+
+  if (warp == kWarpGProd) {
+    if (lane == 0) {
+      int64_t k = 0;                             // tiles begun (every tile uses all four stages once)
+      int64_t fills[kC64NSG] = {0, 0, 0, 0};     // loads issued into each stage
+      bool ok = true;
+      for (int64_t t = cid; t < T && ok; t += ncl, ++k) {
+        int64_t rt, cp;
+        c64_tile_coords(t, nrt, ncp, rt, cp);
+        for (int s = 0; s < kC64NSG; ++s) {      // quarter s of the tile goes to stage s
+          if (k >= 1 && !tc::mbar_wait_or_abort(&bars->gempty[s], (uint32_t)((k - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          const int x0 = (int)(cp * kC64WN) + 64 * s, y = (int)(rt * kC64M);      // x in floats
+          int nbox = 0;
+          for (int bx = 0; bx < 2; ++bx) nbox += (x0 + 32 * bx < 2 * n) ? 1 : 0;
+          if (nbox == 0) tc::mbar_arrive(&bars->gfull[s]);
+          else {
+            tc::mbar_arrive_expect_tx(&bars->gfull[s], (uint32_t)(nbox * kC64Box));
+            uint8_t* gt = gts + s * kC64GStage;
+            for (int bx = 0; bx < nbox; ++bx) tc::tma_load_2d(gt + bx * kC64Box, &tmapG, x0 + 32 * bx, y, &bars->gfull[s]);
+          }
+          ++fills[s];
+        }
+      }
+      // every load issued has landed before the CTA may retire
+      for (int s = 0; s < kC64NSG; ++s)
+        if (fills[s] >= 1) tc::mbar_wait_bounded(&bars->gfull[s], (uint32_t)((fills[s] - 1) & 1), kC64DrainNs);
+    }
+    __syncwarp();
+  } else if (warp == kWarpOProd) {
+    if (lane == 0) {
+      const uint64_t pol_ops = tc::policy_evict_last();    // operand chunks: re-read by many tiles
+      int64_t c = 0;
+      bool ok = true;
+      for (int64_t t = cid; t < T && ok; t += ncl) {
+        int64_t rt, cp;
+        c64_tile_coords(t, nrt, ncp, rt, cp);
+        for (int kc = 0; kc < nkr; ++kc, ++c) {
+          const int s = (int)(c % kWsNSO);
+          if (c >= kWsNSO && !tc::mbar_wait_or_abort(&bars->oempty[s], (uint32_t)((c / kWsNSO - 1) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          uint8_t* st = ops + s * kWsStage;
+          tc::mbar_arrive_expect_tx(&bars->ofull[s], (uint32_t)kWsStage);
+          tc::bulk_g2s_hint(st, Aops + (rt * nkc + kc) * (int64_t)kC64Block, kC64Block, &bars->ofull[s], pol_ops);
+          tc::bulk_g2s_hint(st + kC64Block, Bops + (cp * nkc + kc) * (int64_t)kC64PairBlock, kC64PairBlock,
+                            &bars->ofull[s], pol_ops);
+        }
+      }
+      // every copy issued has landed before the CTA may retire
+      for (int64_t q = c - kWsNSO; q < c; ++q)
+        if (q >= 0) tc::mbar_wait_bounded(&bars->ofull[q % kWsNSO], (uint32_t)((q / kWsNSO) & 1), kC64DrainNs);
+    }
+    __syncwarp();
+  } else if (warp == kWarpMma) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_f16(kC64M, kC64WN);
+      int64_t k = 0, c = 0;
+      bool ok = true;
+      for (int64_t t = cid; t < T && ok; t += ncl, ++k) {
+        const int b = (int)(k & 1);
+        if (k >= 2 && !tc::mbar_wait_or_abort(&bars->tempty[b], (uint32_t)((k / 2 - 1) & 1), abort, kC64TimeoutNs)) break;
+        tc::fence_after_sync();
+        const uint32_t d = tbase + (uint32_t)(b * kC64WN);
+        for (int kc = 0; kc < nkr; ++kc, ++c) {
+          const int s = (int)(c % kWsNSO);
+          if (!tc::mbar_wait_or_abort(&bars->ofull[s], (uint32_t)((c / kWsNSO) & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          tc::fence_after_sync();
+          const uint32_t sA = tc::smem_u32(ops + s * kWsStage);
+          const uint32_t sB = sA + kC64Block;    // 256 rows: hi at +0 (8 KB), lo at +8 KB
+          const uint64_t ah = tc::smem_desc(sA, kC64Lbo, kC64Sbo), al = tc::smem_desc(sA + kC64Half, kC64Lbo, kC64Sbo);
+          const uint64_t bh = tc::smem_desc(sB, kC64Lbo, kC64Sbo), bl = tc::smem_desc(sB + kC64Block, kC64Lbo, kC64Sbo);
+          tc::mma_f16(d, ah, bh, idesc, kc == 0 ? 0u : 1u);
+          tc::mma_f16(d, ah, bl, idesc, 1u);
+          tc::mma_f16(d, al, bh, idesc, 1u);
+          tc::mma_commit(&bars->oempty[s]);
+        }
+        if (ok) tc::mma_commit(&bars->tfull[b]);
+      }
+      // every MMA issued has completed before the CTA may release TMEM and retire
+      tc::mma_commit(&bars->drain);
+      tc::mbar_wait_bounded(&bars->drain, 0u, kC64DrainNs);
+    }
+    __syncwarp();
+  } else if (warp < kC64EpiWarps) {
+    const int q = warp & 3, h = warp >> 2;     // TMEM lane quarter, column quarter (32 complex columns)
+    const int r = q * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    int64_t k = 0;
+    for (int64_t t = cid; t < T; t += ncl, ++k) {
+      int64_t rt, cp;
+      c64_tile_coords(t, nrt, ncp, rt, cp);
+      const int b = (int)(k & 1);
+      const int Ei = Erow[rt * kC64M + r];
+      if (!tc::mbar_wait_or_abort(&bars->tfull[b], (uint32_t)((k / 2) & 1), abort, kC64TimeoutNs)) break;
+      if (!tc::mbar_wait_or_abort(&bars->gfull[h], (uint32_t)(k & 1), abort, kC64TimeoutNs)) break;
+      tc::fence_after_sync();
+      for (int bx = 0; bx < 2; ++bx) {         // box bx of quarter h: real columns 64h + 32bx .. +31
+        int Fr[16];
+        c64_load_f16(Fcol + cp * (kC64WN / 2) + h * 32 + bx * 16, Fr);
+        float acc[32];
+        {
+          float a0[16], a1[16];
+          const uint32_t base = tbase + lane_addr + (uint32_t)(b * kC64WN + h * 64 + bx * 32);
+          tc::tmem_ld16(base, a0);
+          tc::tmem_ld16(base + 16, a1);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            acc[e] = a0[e];
+            acc[16 + e] = a1[e];
+          }
+        }
+        c64_epilogue_row(gts + h * kC64GStage + bx * kC64Box + r * 128, r, Ei, Fr, acc);
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars->tempty[b]);
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(&bars->ebar[h]);
+    }
+  }
+  if (warp == kWarpStore) {
+    if (lane == 0) {
+      int64_t k = 0;
+      bool ok = true;
+      for (int64_t t = cid; t < T && ok; t += ncl, ++k) {
+        int64_t rt, cp;
+        c64_tile_coords(t, nrt, ncp, rt, cp);
+        for (int s = 0; s < kC64NSG; ++s) {
+          if (!tc::mbar_wait_or_abort(&bars->ebar[s], (uint32_t)(k & 1), abort, kC64TimeoutNs)) { ok = false; break; }
+          const int x0 = (int)(cp * kC64WN) + 64 * s, y = (int)(rt * kC64M);
+          uint8_t* gt = gts + s * kC64GStage;
+          for (int bx = 0; bx < 2; ++bx)
+            if (x0 + 32 * bx < 2 * n) tc::tma_store_2d(&tmapG, x0 + 32 * bx, y, gt + bx * kC64Box);
+          tc::bulk_commit();
+          tc::bulk_wait_read0();
+          tc::mbar_arrive(&bars->gempty[s]);
+        }
+      }
+      tc::bulk_wait0();
+    }
+    __syncwarp();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid == 0 && bars->abort) atomicExch(status, GF_ETIMEOUT);
+  tc::fence_after_sync();
+  if (warp == kWarpMma) tc::tmem_dealloc(tbase, kWsTmemCols);
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 c64_encode_fn() {
@@ -820,8 +817,8 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
   k_c64_inverse<<<L.pmax, 128, 0, st>>>(L, ws, lam, Mdai);
   int32_t* Erow = reinterpret_cast<int32_t*>(ws + L.c64E);
   int32_t* Fcol = reinterpret_cast<int32_t*>(ws + L.c64F);
-  k_c64_s_gemm<<<(unsigned)o.nct, 256, 0, st>>>(G, ldg, n, Mdai, reinterpret_cast<const int32_t*>(ws + L.V), ctl,
-                                                 (int)o.nkc, Bops, Fcol);
+  k_c64_s_gemm<<<(unsigned)(2 * o.ncp), 256, 0, st>>>(G, ldg, n, Mdai, reinterpret_cast<const int32_t*>(ws + L.V), ctl,
+                                                       (int)o.nkc, Bops, Fcol);
   {
     int64_t rows = o.nrt * kC64M;
     int64_t b = (rows + 127) / 128;
@@ -837,12 +834,13 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
     std::lock_guard<std::mutex> lk(mu);
     if (dev < 0 || dev >= 64 || !done[dev]) {
       cudaFuncSetAttribute(k_rank_update_c64_ra, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
-      cudaFuncSetAttribute(k_rank_update_c64_tc_t, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
+      cudaFuncSetAttribute(k_rank_update_c64_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
-  // joint rank p <= 48 (decided on the device): the resident-A form; larger p: a streaming form,
-  // launched only where the workspace allows p > 48 (each returns at once when the other applies)
+  // joint rank p <= 48 (decided on the device): the resident-A form; larger p: the streaming
+  // form, launched only where the workspace allows p > 48 (each returns at once when the other
+  // applies)
   {
     const int64_t tiles = o.nrt * o.nct;
     const int grid = (int)(tiles < sm_count ? tiles : sm_count);
@@ -850,10 +848,10 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
                                                                Fcol, ctl, status, prof_p);
     if (o.nkc <= kRaMaxK) return;
   }
-  const int64_t tiles = o.nrt * o.nct;
+  const int64_t tiles = o.nrt * o.ncp;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  k_rank_update_c64_tc_t<<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.nct, (int)o.nkc, Aops, Bops,
-                                                                    Erow, Fcol, ctl, status, prof_p, kRaMaxK);
+  k_rank_update_c64_wide<<<grid, kC64Threads, kC64Smem, st>>>(tmap, n, o.nrt, o.ncp, (int)o.nkc, Aops, Bops, Erow,
+                                                               Fcol, ctl, status, prof_p);
 }
 
 }  // namespace gf

@@ -36,7 +36,7 @@ EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_v
            "gf_lowrank_init", "gf_lowrank_eval", "gf_lowrank_update", "gf_lowrank_count",
            "gf_lowrank_materialize", "gf3_num_unknowns", "gf3_num_candidates", "gf3_workspace_size",
            "gf3_fill_g0", "gf3_eval_candidates", "gf3_select_topk", "gf3_apply_update", "gf_selftest_timeout",
-           "gf_fom", "gf3_fom", "gf_lowrank_fom"]
+           "gf_fom", "gf3_fom", "gf_lowrank_fom", "gf_refresh_field"]
 
 
 class GfError(RuntimeError):
@@ -74,6 +74,11 @@ class gf_problem3d(C.Structure):
 class gf_lowrank(C.Structure):
     _fields_ = [("geom", gf_geom), ("E", C.c_void_p), ("bands", C.c_void_p), ("monrow", C.c_void_p),
                 ("U", C.c_void_p), ("max_cols", C.c_int32)]
+
+
+class gf_refresh_report(C.Structure):
+    _fields_ = [("e_residual", C.c_double), ("e_residual_after", C.c_double), ("e_iters", C.c_int32),
+                ("e_replaced", C.c_int32)]
 
 
 class gf_batch_item(C.Structure):
@@ -124,7 +129,11 @@ def load(path: str = LIB_PATH):
             "gf_refresh_workspace_size": (C.c_size_t, [C.POINTER(gf_geom), C.c_int32]),
             "gf_refresh": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, P, C.c_int32,
                                        C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_double,
-                                       C.POINTER(C.c_double), C.POINTER(C.c_int32), P, C.c_size_t, P]),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_double), P,
+                                       C.c_size_t, P]),
+            "gf_refresh_field": (C.c_int32, [P, C.POINTER(gf_problem), C.c_int32, P, C.c_double, C.c_int32,
+                                             C.c_int32, C.c_double, C.POINTER(gf_refresh_report), P, C.c_size_t,
+                                             P]),
             "gf_profile_end": (C.c_int32, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                            C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "gf_select_egreedy": (C.c_int32, [P, C.POINTER(gf_geom), C.POINTER(gf_cand_spec), P, C.c_int64,
@@ -286,15 +295,26 @@ class Handle:
 
     def gf_refresh(self, prob: gf_problem, dtype, state, cols, restart, max_iter, tol, ws, ws_bytes,
                    stream=None):
-        """Returns (resid list of 1 + len(cols), GMRES iterations per column)."""
+        """Returns (resid list of 1 + len(cols), GMRES iterations per column, each stored
+        column's own Eq. 2 residual)."""
         ns = len(cols)
         ca = (C.c_int32 * max(ns, 1))(*cols)
         res = (C.c_double * (ns + 1))()
         its = (C.c_int32 * max(ns, 1))()
+        cres = (C.c_double * max(ns, 1))()
         self._check(self.lib.gf_refresh(self.h, C.byref(prob), int(dtype), _ptr(state), ns, ca, int(restart),
-                                        int(max_iter), float(tol), res, its, _ptr(ws), int(ws_bytes),
+                                        int(max_iter), float(tol), res, its, cres, _ptr(ws), int(ws_bytes),
                                         _stream(stream)))
-        return list(res), list(its)[:ns]
+        return list(res), list(its)[:ns], list(cres)[:ns]
+
+    def gf_refresh_field(self, prob: gf_problem, dtype, state, e_tol, restart, max_iter, tol, ws, ws_bytes,
+                         stream=None) -> dict:
+        rep = gf_refresh_report()
+        self._check(self.lib.gf_refresh_field(self.h, C.byref(prob), int(dtype), _ptr(state), float(e_tol),
+                                              int(restart), int(max_iter), float(tol), C.byref(rep), _ptr(ws),
+                                              int(ws_bytes), _stream(stream)))
+        return {"e_residual": rep.e_residual, "e_residual_after": rep.e_residual_after, "e_iters": rep.e_iters,
+                "e_replaced": bool(rep.e_replaced)}
 
     def gf_selftest_timeout(self, timeout_ns: int, status, stream=None):
         self._check(self.lib.gf_selftest_timeout(self.h, int(timeout_ns), _ptr(status), _stream(stream)))

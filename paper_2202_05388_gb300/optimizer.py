@@ -116,24 +116,43 @@ class GreedyOptimizer:
         self.h.gf_apply_update(self.probs, self.dtype, self.state, spec, self.idx, self.status,
                                self.fom, self.ws, self.ws_bytes, self._st(), applied=self.applied)
 
+    def _refresh_ws(self, restart: int):
+        need = self.h.gf_refresh_workspace_size(self.geoms[0], restart)
+        if getattr(self, "_rws", None) is None or self._rws.numel() < need:
+            self._rws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self._rws
+
     def refresh(self, cols: Optional[Sequence[int]] = None, nsample: int = 8, restart: int = 30,
                 max_iter: int = 300, tol: Optional[float] = None, seed: int = 0):
         """Drift check of every wavelength: Lippmann-Schwinger residual of E and GMRES re-solves
         of sampled columns of G (blocking).  Returns a list (per wavelength) of
-        (residuals, iterations)."""
+        (residuals, iterations, column residuals)."""
         if tol is None:                      # well below the storage precision of G
             tol = 1e-12 if self.dtype == B.GF_C128 else 1e-8
         if cols is None:
             rng = np.random.default_rng(seed)
             cols = sorted(set(int(c) for c in rng.integers(0, self.n, nsample)))
-        need = self.h.gf_refresh_workspace_size(self.geoms[0], restart)
-        if getattr(self, "_rws", None) is None or self._rws.numel() < need:
-            self._rws = torch.empty(need, dtype=torch.uint8, device=self.device)
-        out = []
-        for p in self.probs:
-            out.append(self.h.gf_refresh(p, self.dtype, self.state, list(cols), restart, max_iter, tol,
-                                         self._rws, self._rws.numel(), self._st()))
-        return out
+        ws = self._refresh_ws(restart)
+        return [self.h.gf_refresh(p, self.dtype, self.state, list(cols), restart, max_iter, tol, ws, ws.numel(),
+                                  self._st()) for p in self.probs]
+
+    # Field repair tolerances: the Eq. 3 residual a field may carry before it is re-solved (well
+    # above the rounding the FP64 field accumulates from the stored G: ~1e-15 per step for
+    # complex128, ~1e-7 per step for complex64 storage), and the GMRES target of the re-solve.
+    E_TOL = {B.GF_C128: 1e-9, B.GF_C64: 1e-5}
+    E_GMRES_TOL = 1e-13
+
+    def refresh_fields(self, e_tol: Optional[float] = None, restart: int = 30, max_iter: int = 600):
+        """Eq. 3 check of every wavelength's field; a field whose residual exceeds e_tol is
+        replaced by its GMRES solution (gf_refresh_field), and the FOM is rewritten from the
+        fields (gf_fom).  Blocking.  Returns one report per wavelength."""
+        e_tol = self.E_TOL[self.dtype] if e_tol is None else e_tol
+        ws = self._refresh_ws(restart)
+        reps = [self.h.gf_refresh_field(p, self.dtype, self.state, e_tol, restart, max_iter, self.E_GMRES_TOL, ws,
+                                        ws.numel(), self._st()) for p in self.probs]
+        if any(r["e_replaced"] for r in reps):
+            self.h.gf_fom(self.probs, self.dtype, self.fom, self._st())
+        return reps
 
     # ---- host readback
     def read_step(self) -> StepResult:
@@ -144,14 +163,25 @@ class GreedyOptimizer:
         return StepResult(ids, [float(x) for x in packed[k:k + len(ids)]], int(packed[2 * k]),
                           float(packed[2 * k + 1]))
 
-    def run(self, steps: int) -> List[StepResult]:
+    def run(self, steps: int, refresh_every: int = 0, e_tol: Optional[float] = None) -> List[StepResult]:
+        """Up to `steps` greedy steps, stopping at the first non-OK status.  With refresh_every
+        = R > 0, every R accepted steps the fields are checked and repaired (refresh_fields);
+        the reports go to self.refresh_log as (step, reports, seconds)."""
         out = []
-        for _ in range(steps):
+        self.refresh_log = []
+        for t in range(steps):
             self.step()
             r = self.read_step()
             out.append(r)
             if r.status != B.GF_OK:
                 break
+            if refresh_every and (t + 1) % refresh_every == 0:
+                import time
+                t0 = time.perf_counter()
+                reps = self.refresh_fields(e_tol)
+                self.refresh_log.append((t + 1, reps, time.perf_counter() - t0))
+                if any(rep["e_replaced"] for rep in reps):
+                    out[-1] = StepResult(r.ids, r.dfom, r.status, float(self.fom.cpu()[0]))
         return out
 
     def state_host(self) -> np.ndarray:

@@ -84,15 +84,16 @@ def test_batch_host_checks(lib):
 
 
 def test_workspace_sizes_cover_the_tensor_core_operand_blocks(lib):
-    """The complex64 tensor-core update's split-FP16 operand blocks (A: one per 128-row tile, B:
-    one per 64-column tile, 16 KB per 32-deep K chunk, K = 2 P with P = p_max rounded to 16) fit
-    in the workspace, for the 2-D top-k workload and the 3-D lens; the refresh workspace holds
-    the GMRES basis and the partial sums of its reductions."""
+    """The complex64 tensor-core update's split-FP16 operand blocks (A: 8 KB per 128-row tile and
+    16-deep K chunk; B: 16 KB per pair of 64-column tiles and K chunk, K = 2 P with P = p_max
+    rounded to 16) fit in the workspace, for the 2-D top-k workload and the 3-D lens; the refresh
+    workspace holds the GMRES basis and the partial sums of its reductions."""
     def blocks(n, pmax):
         P = (pmax + 15) // 16 * 16
-        nkc = 2 * P // 32
+        nkc = 2 * P // 16
         nrt, nct = (n + 127) // 128, (2 * n + 127) // 128
-        return (nrt + nct) * nkc * 16384
+        ncp = (nct + 1) // 2
+        return nrt * nkc * 8192 + ncp * nkc * 16384
     wl = W.brush_320_topk()
     g, s = wl.geoms[0], wl.spec
     ws = lib.gf_workspace_size(C.byref(B.geom_struct(g)), 1, B.GF_C64, C.byref(B.spec_struct(s)))

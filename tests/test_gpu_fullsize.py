@@ -89,7 +89,7 @@ def _sampled_G(opt, lazies, rng, tol, l_all=True):
 
 def test_brush_320_top32_c64_full_size_lockstep():
     """The 320x320 top-32 workload (n = 102401, complex64 G = 83.9 GB, rank-k p Woodbury on the
-    tensor cores in 2-CTA clusters) for three steps from the oracle's choices: every candidate's
+    tensor cores, streaming 128 x 256 tiles) for three steps from the oracle's choices: every candidate's
     dFOM, the applied set (joint decision), E, FOM and sampled G within the mixed-precision
     bounds of the FP64 oracle."""
     wl = W.brush_320_topk()
