@@ -331,6 +331,63 @@ gf_status gf3_apply_update(gf_handle* h, const gf_problem3d* prob, int32_t dtype
                            const gf_cand_spec* spec, const int32_t* idx, int32_t* status, double* fom_out,
                            int32_t* applied, void* ws, size_t ws_bytes, void* stream);
 
+/* Row-block shards of one problem (Sec. III: the rows of G split over partitions, a
+ * partition-local dFOM, a global combine, a broadcast of the chosen pixels' rows and each
+ * partition's update of its own rows), for G larger than one GPU's memory.  A shard holds the
+ * rows of G of pixel rows [y0, y1), 0 <= y0 < y1 <= ny; the shard with y1 = ny also holds the
+ * monitor row.  Global rows [r0, r1), r0 = y0 nx, r1 = y1 nx (+1 when y1 = ny), are stored as
+ * (r1 - r0) x ldg entries of the storage dtype at G (ldg even, >= n).
+ *   E (n complex128) and the design state (N bytes) are whole on every shard; the calls below
+ *   keep them identical on all shards when every shard makes the same calls with the same idx.
+ *   bands (GF_NBANDS N complex128, layout of gf_problem.bands) and mon (n complex128, mon[j] =
+ *   G[N, j] = G[j, N] by reciprocity) are valid for the pixels of rows [y0, min(y1 + 1, ny)): the
+ *   shard's own rows and the halo row y1, which the next shard supplies.
+ * A step on every shard: gf_shard_eval; elementwise maximum of the dfom arrays over the shards;
+ * gf_select_topk (the same choice everywhere); gf_shard_gather_rows; sum of the panels over the
+ * shards; gf_shard_apply_update; gf_shard_pack_halo, exchange, gf_shard_unpack_halo.  One
+ * wavelength; ws = gf_workspace_size(&geom, 1, dtype, spec) bytes, 256-byte aligned. */
+typedef struct gf_shard {
+  gf_geom geom;
+  int32_t y0, y1;
+  void* G;
+  int64_t ldg;
+  void* E;
+  void* bands;
+  void* mon;
+} gf_shard;
+/* Rows of G the shard holds (r1 - r0; 0 on bad arguments). */
+int64_t gf_shard_rows(const gf_shard* shard);
+/* Vacuum start: the shard's rows of G0, E = E_inc, and bands and mon of rows [y0, min(y1+1, ny)). */
+gf_status gf_shard_fill_g0(gf_handle* h, const gf_shard* shard, int32_t dtype, void* ws, size_t ws_bytes,
+                           void* stream);
+/* dFOM (as gf_eval_candidates) of the candidates anchored in the shard's pixel rows: brushes with
+ * anchor row iy in [y0, min(y1, ny - 1)), single pixels of rows [y0, y1).  Every other entry of
+ * dfom (gf_num_candidates doubles) is -inf, so the elementwise maximum over the shards is the
+ * dFOM array of the whole problem. */
+gf_status gf_shard_eval(gf_handle* h, const gf_shard* shard, int32_t dtype, const uint8_t* state,
+                        const gf_cand_spec* spec, double* dfom, void* stream);
+/* The shard's part of the broadcast of the update set's rows.  V = the union of the candidates
+ * idx[0..k) (-1 ends the list) in the order gf_apply_update forms it; panel (pmax x ldp entries of
+ * the storage dtype, pmax = 4k for brushes and k for single pixels, ldp even and >= n): row u =
+ * G[V[u], :] where the shard holds row V[u], zero elsewhere, so the sum of all shards' panels holds
+ * every row of V exactly once.  All zero when *status != GF_OK. */
+gf_status gf_shard_gather_rows(gf_handle* h, const gf_shard* shard, int32_t dtype, const uint8_t* state,
+                               const gf_cand_spec* spec, const int32_t* idx, const int32_t* status, void* panel,
+                               int64_t ldp, void* stream);
+/* gf_apply_update for one shard, with the rows G[V, :] from the summed panel: the capacitance solve
+ * (Eqs. 9, 14; G_VV and G[N, V] = G[V, N] from the panel), the update of the shard's rows (Eq. 10),
+ * of the whole E (Eq. 4, G[i, V] = G[V, i] from the panel) and of the state, *fom_out, *applied,
+ * and the bands and mon of the shard's own rows read back from its updated rows. */
+gf_status gf_shard_apply_update(gf_handle* h, const gf_shard* shard, int32_t dtype, uint8_t* state,
+                                const gf_cand_spec* spec, const int32_t* idx, const void* panel, int64_t ldp,
+                                int32_t* status, double* fom_out, int32_t* applied, void* ws, size_t ws_bytes,
+                                void* stream);
+/* Halo exchange: pack writes the bands and mon of pixel row y0 to out ((GF_NBANDS + 1) nx complex128:
+ * band 0 .. band 8, then mon); unpack writes the next shard's record as pixel row y1 (nothing when
+ * y1 = ny). */
+gf_status gf_shard_pack_halo(gf_handle* h, const gf_shard* shard, void* out, void* stream);
+gf_status gf_shard_unpack_halo(gf_handle* h, const gf_shard* shard, const void* in, void* stream);
+
 /* Batches: many independent problems advanced together (the problems of a design study, e.g.
  * sweeps over sizes, wavelengths and focal distances; the paper parallelises one problem's
  * partitions instead, Sec. III).  Each item is one single-wavelength problem with its own

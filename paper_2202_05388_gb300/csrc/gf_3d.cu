@@ -815,6 +815,9 @@ gf_status gf3_apply_update(gf_handle* h, const gf_problem3d* prob, int32_t dtype
   a.lam[0].ldg = prob->ldg;
   a.lam[0].E = reinterpret_cast<gf::cplx*>(prob->E);
   a.lam[0].bands = nullptr;
+  a.lam[0].vrows = nullptr;
+  a.lam[0].ldv = 0;
+  a.lam[0].rows = 3 * (g.N + 1);
   gf::launch_update(a, L, reinterpret_cast<char*>(ws), state, *spec, idx, status, fom_out, applied,
                     (cudaStream_t)stream, gf::api_timer(h));
   return gf::api_cuda_check(h, "gf3_apply_update launch");

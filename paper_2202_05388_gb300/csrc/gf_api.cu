@@ -299,6 +299,8 @@ gf_status gf_eval_candidates(gf_handle* h, const gf_problem* probs, int32_t nlam
   a.nx = probs[0].geom.nx;
   a.ny = probs[0].geom.ny;
   a.chi = probs[0].geom.eps_mat - probs[0].geom.eps_bg;
+  a.c_begin = 0;
+  a.c_end = -1;
   for (int l = 0; l < nlam; ++l) {
     a.lam[l].G = probs[l].G;
     a.lam[l].ldg = probs[l].ldg;
@@ -384,6 +386,9 @@ gf_status gf_apply_update(gf_handle* h, const gf_problem* probs, int32_t nlam, i
     a.lam[l].ldg = probs[l].ldg;
     a.lam[l].E = reinterpret_cast<gf::cplx*>(probs[l].E);
     a.lam[l].bands = reinterpret_cast<gf::cplx*>(probs[l].bands);
+    a.lam[l].vrows = nullptr;
+    a.lam[l].ldv = 0;
+    a.lam[l].rows = L.n;
   }
   cudaStream_t st = (cudaStream_t)stream;
   gf::launch_update(a, L, reinterpret_cast<char*>(ws), state, *spec, idx, status, fom_out, applied, st, &h->timer);

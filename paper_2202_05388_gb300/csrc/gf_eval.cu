@@ -71,7 +71,8 @@ __device__ __forceinline__ bool solve_small(cplx (&A)[P][P], cplx (&b)[P], const
 __device__ __forceinline__ void eval_single_body(const EvalArgs& a, const uint8_t* __restrict__ state,
                                                  int dir_mask, double* __restrict__ dfom) {
   const int64_t N = (int64_t)a.nx * a.ny;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+  const int64_t jend = a.c_end >= 0 && a.c_end < N ? a.c_end : N;
+  for (int64_t j = a.c_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < jend;
        j += (int64_t)gridDim.x * blockDim.x) {
     const uint8_t s = state[j];
     double d = 0.0;
@@ -106,7 +107,8 @@ __device__ __forceinline__ void eval_brush_body(const EvalArgs& a, const uint8_t
   // local pixel offsets and the band that holds G[q_u, q_v]
   const int px[4] = {0, 1, 0, 1}, py[4] = {0, 0, 1, 1};
   const int band_of[9] = {8, 6, 4, 2, 0, 1, 3, 5, 7};   // index (ddy+1)*3 + (ddx+1)
-  for (int64_t an = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; an < P;
+  const int64_t aend = a.c_end >= 0 && a.c_end < P ? a.c_end : P;
+  for (int64_t an = a.c_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; an < aend;
        an += (int64_t)gridDim.x * blockDim.x) {
     const int ay = (int)(an / (nx - 1)), ax = (int)(an - (int64_t)ay * (nx - 1));
     const int64_t j0 = (int64_t)ay * nx + ax;
@@ -186,6 +188,8 @@ __device__ __forceinline__ void batch_eval_args(const BatchItem* items, int dtyp
     sa.nx = it.nx;
     sa.ny = it.ny;
     sa.chi = it.chi;
+    sa.c_begin = 0;
+    sa.c_end = -1;
     sa.lam[0].G = it.G;
     sa.lam[0].ldg = it.ldg;
     sa.lam[0].E = it.E;

@@ -189,6 +189,7 @@ struct EvalArgs {
   int dtype;
   int nx, ny;
   double chi;           // eps_mat - eps_bg
+  int64_t c_begin, c_end;   // anchors (brushes) or pixels (single) evaluated: [c_begin, c_end); c_end < 0: all
   EvalLam lam[kMaxLam];
 };
 void launch_eval(const EvalArgs& a, const uint8_t* state, const gf_cand_spec& spec, double* dfom,
@@ -206,6 +207,13 @@ struct UpdLam {
   int64_t ldg;
   cplx* E;
   cplx* bands;
+  // Row-block form (a shard of G): G holds `rows` rows (== n for the whole matrix); when vrows is
+  // set, the rows G[V[u], :] of the update set come from it (row u, ldv entries apart, storage
+  // dtype) instead of from G, and G[i, V[u]] for the field update is read there as G[V[u], i]
+  // (reciprocity).
+  const void* vrows;
+  int64_t ldv;
+  int64_t rows;
 };
 struct UpdArgs {
   int nlam;
@@ -248,14 +256,15 @@ struct KernelTimer {
 
 KernelTimer* api_timer(gf_handle* h);
 
-bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0,
+bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int64_t rows, int pmax, const cplx* C0,
                               const cplx* S, const UpdCtl* ctl, uint8_t* ozA, int32_t* ozE,
                               uint8_t* ozB, int32_t* ozF, int32_t* status, int32_t* prof_p,
                               int sm_count, cudaStream_t st);
 
-bool c64_tc_make_map(float2* G, int64_t ldg, int64_t n, void* map128);
-void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64_t n, const WsLayout& L, char* ws,
-                               int lam, int32_t* status, int32_t* prof_p, int sm_count, cudaStream_t st);
+bool c64_tc_make_map(float2* G, int64_t ldg, int64_t n, int64_t rows, void* map128);
+void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64_t n, int64_t rows,
+                               const void* vrows, int64_t ldv, const WsLayout& L, char* ws, int lam,
+                               int32_t* status, int32_t* prof_p, int sm_count, cudaStream_t st);
 
 size_t refresh_workspace_size(const gf_geom& g, int restart);
 gf_status refresh(const gf_problem& prob, int dtype, const uint8_t* state, int nsample, const int32_t* cols,
@@ -311,6 +320,9 @@ __device__ __forceinline__ void batch_upd_args(const BatchItem& it, int dtype, U
   a.lam[0].ldg = it.ldg;
   a.lam[0].E = it.E;
   a.lam[0].bands = it.bands;
+  a.lam[0].vrows = nullptr;
+  a.lam[0].ldv = 0;
+  a.lam[0].rows = it.L.n;
 }
 // each launcher covers problems [0, nprob) of the device table; `widest` is the largest
 // per-problem extent of the launch's x dimension (pixels, candidates or rows)
@@ -324,7 +336,7 @@ void launch_finish_batch(const BatchItem* items, int nprob, int dtype, int64_t w
 void launch_bands_batch(const BatchItem* items, int nprob, int dtype, int64_t widest, cudaStream_t st);
 // complex64 rank <= 4 update in FP32 on the CUDA cores (HBM-bound streaming)
 void launch_rank_update_c64_fp32_batch(const BatchItem* items, int nprob, int ctas, cudaStream_t st);
-void launch_rank_update_c64_fp32(float2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0, const cplx* S,
+void launch_rank_update_c64_fp32(float2* G, int64_t ldg, int64_t n, int64_t rows, int pmax, const cplx* C0, const cplx* S,
                                  const UpdCtl* ctl, int32_t* prof_p, int ctas, cudaStream_t st);
 constexpr int kC64Fp32MaxP = 4;
 // complex128 rank <= 4 update on the tensor cores for a whole batch: the operand preparation

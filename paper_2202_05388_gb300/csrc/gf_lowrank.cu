@@ -437,6 +437,8 @@ gf_status gf_lowrank_eval(gf_handle* h, const gf_lowrank* lr, const uint8_t* sta
   a.nx = lr->geom.nx;
   a.ny = lr->geom.ny;
   a.chi = lr->geom.eps_mat - lr->geom.eps_bg;
+  a.c_begin = 0;
+  a.c_end = -1;
   a.lam[0].G = lr->monrow;
   a.lam[0].ldg = 0;
   a.lam[0].E = reinterpret_cast<const gf::cplx*>(lr->E);

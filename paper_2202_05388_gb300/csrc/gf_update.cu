@@ -177,7 +177,7 @@ __device__ bool cap_lam(const CapArgs& a, const WsLayout& L, char* ws, int l, in
     // A = I - G_VV D, row-major p x p;  y = E_V
     for (int t = tid; t < p * p; t += blockDim.x) {
       int r = t / p, c = t % p;
-      cplx g = ldG(U.G, a.u.dtype, U.ldg, V[r], V[c]);
+      cplx g = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, r, V[c]) : ldG(U.G, a.u.dtype, U.ldg, V[r], V[c]);
       cplx e = mk(r == c ? 1.0 : 0.0, 0.0);
       A[t] = e - dchi[c] * g;
     }
@@ -293,7 +293,11 @@ __device__ bool cap_lam(const CapArgs& a, const WsLayout& L, char* ws, int l, in
     for (int mc = 0; mc < a.u.mcount; ++mc) {
       const int64_t m = a.u.mrow + mc;
       cplx part = mk(0.0, 0.0);
-      for (int u = tid; u < p; u += blockDim.x) part = part + dchi[u] * (ldG(U.G, a.u.dtype, U.ldg, m, V[u]) * y[u]);
+      // G[m, V[u]]; from the row panel as G[V[u], m] (reciprocity)
+      for (int u = tid; u < p; u += blockDim.x) {
+        const cplx gm = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, u, m) : ldG(U.G, a.u.dtype, U.ldg, m, V[u]);
+        part = part + dchi[u] * (gm * y[u]);
+      }
       for (int o = 16; o > 0; o >>= 1) {
         part.re += __shfl_down_sync(0xffffffffu, part.re, o);
         part.im += __shfl_down_sync(0xffffffffu, part.im, o);
@@ -452,7 +456,8 @@ __global__ void k_capacitance_lam(CapArgs a, WsLayout L, char* ws, const uint8_t
 }
 
 // ----------------------------------------------------------------------------- panels
-// Column j: R[:, j] = A^{-1} G[V, j] (Eq. 14) and S[:, j] = D R[:, j]; row j: C0[j, :] = G[j, V].
+// Column j: R[:, j] = A^{-1} G[V, j] (Eq. 14) and S[:, j] = D R[:, j]; row j of the rows held:
+// C0[j, :] = G[j, V].
 __device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L, char* ws, int want_S) {
   const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
   if (ctl->skip) return;
@@ -466,15 +471,17 @@ __device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L,
     const int32_t* piv = reinterpret_cast<const int32_t*>(ws + L.piv + l * L.piv_s);
     cplx* C0 = reinterpret_cast<cplx*>(ws + L.C0 + l * L.panel_s);
     cplx* S = reinterpret_cast<cplx*>(ws + L.S + l * L.panel_s);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+    const int64_t jend = U.rows > n ? U.rows : n;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < jend;
          j += (int64_t)gridDim.x * blockDim.x) {
-      for (int u = 0; u < p; ++u) C0[j * L.pmax + u] = ldG(U.G, a.dtype, U.ldg, j, V[u]);
-      if (!want_S) continue;
+      if (j < U.rows)
+        for (int u = 0; u < p; ++u) C0[j * L.pmax + u] = ldG(U.G, a.dtype, U.ldg, j, V[u]);
+      if (!want_S || j >= n) continue;
       if (p <= kMaxPixelsPerCand) {
         cplx x[kMaxPixelsPerCand];
 #pragma unroll
         for (int u = 0; u < kMaxPixelsPerCand; ++u)
-          if (u < p) x[u] = ldG(U.G, a.dtype, U.ldg, V[u], j);
+          if (u < p) x[u] = U.vrows ? ldG(U.vrows, a.dtype, U.ldv, u, j) : ldG(U.G, a.dtype, U.ldg, V[u], j);
         // P A = L U with full-row interchanges: apply all interchanges in order first,
         // then the unit-lower solve, then the upper solve
 #pragma unroll
@@ -509,7 +516,8 @@ __device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L,
           if (u < p) S[(int64_t)u * n + j] = dchi[u] * x[u];
       } else {
         // general p: the column of R lives in S itself (row stride n)
-        for (int u = 0; u < p; ++u) S[(int64_t)u * n + j] = ldG(U.G, a.dtype, U.ldg, V[u], j);
+        for (int u = 0; u < p; ++u)
+          S[(int64_t)u * n + j] = U.vrows ? ldG(U.vrows, a.dtype, U.ldv, u, j) : ldG(U.G, a.dtype, U.ldg, V[u], j);
         for (int c = 0; c < p; ++c) {
           int r = piv[c];
           if (r != c) {
@@ -543,7 +551,7 @@ constexpr int kUpdRows = 16;
 // G[i, j] += sum_u C0[i, u] S[u, j] for one wavelength, complex128 storage, native DFMA.
 // P > 0: compile-time rank; P == 0: runtime rank p.
 template <int P>
-__device__ __forceinline__ void rank_update_f64_body(double2* __restrict__ G, int64_t ldg, int64_t n,
+__device__ __forceinline__ void rank_update_f64_body(double2* __restrict__ G, int64_t ldg, int64_t n, int64_t rows,
                                                      int pmax, int p, const cplx* __restrict__ C0,
                                                      const cplx* __restrict__ S, int64_t j) {
   cplx s[P > 0 ? P : 1];
@@ -551,8 +559,8 @@ __device__ __forceinline__ void rank_update_f64_body(double2* __restrict__ G, in
 #pragma unroll
     for (int u = 0; u < P; ++u) s[u] = S[(int64_t)u * n + j];
   }
-  for (int64_t i0 = (int64_t)blockIdx.y * kUpdRows; i0 < n; i0 += (int64_t)gridDim.y * kUpdRows) {
-    const int64_t iend = i0 + kUpdRows < n ? i0 + kUpdRows : n;
+  for (int64_t i0 = (int64_t)blockIdx.y * kUpdRows; i0 < rows; i0 += (int64_t)gridDim.y * kUpdRows) {
+    const int64_t iend = i0 + kUpdRows < rows ? i0 + kUpdRows : rows;
     for (int64_t i = i0; i < iend; ++i) {
       double2 g = G[i * ldg + j];
       cplx acc = mk(g.x, g.y);
@@ -568,7 +576,7 @@ __device__ __forceinline__ void rank_update_f64_body(double2* __restrict__ G, in
 }
 
 __global__ void __launch_bounds__(kUpdThreads) k_rank_update_f64(double2* __restrict__ G, int64_t ldg,
-                                                                 int64_t n, int pmax,
+                                                                 int64_t n, int64_t rows, int pmax,
                                                                  const cplx* __restrict__ C0,
                                                                  const cplx* __restrict__ S,
                                                                  const UpdCtl* __restrict__ ctl,
@@ -580,17 +588,17 @@ __global__ void __launch_bounds__(kUpdThreads) k_rank_update_f64(double2* __rest
   const int64_t j = blockIdx.x * (int64_t)kUpdThreads + threadIdx.x;
   if (j >= n) return;
   switch (p) {
-    case 1: rank_update_f64_body<1>(G, ldg, n, pmax, p, C0, S, j); break;
-    case 2: rank_update_f64_body<2>(G, ldg, n, pmax, p, C0, S, j); break;
-    case 3: rank_update_f64_body<3>(G, ldg, n, pmax, p, C0, S, j); break;
-    case 4: rank_update_f64_body<4>(G, ldg, n, pmax, p, C0, S, j); break;
-    default: rank_update_f64_body<0>(G, ldg, n, pmax, p, C0, S, j); break;
+    case 1: rank_update_f64_body<1>(G, ldg, n, rows, pmax, p, C0, S, j); break;
+    case 2: rank_update_f64_body<2>(G, ldg, n, rows, pmax, p, C0, S, j); break;
+    case 3: rank_update_f64_body<3>(G, ldg, n, rows, pmax, p, C0, S, j); break;
+    case 4: rank_update_f64_body<4>(G, ldg, n, rows, pmax, p, C0, S, j); break;
+    default: rank_update_f64_body<0>(G, ldg, n, rows, pmax, p, C0, S, j); break;
   }
 }
 
 // complex64 storage: same update, FP64 arithmetic on the FP64 panels, rounded once on store.
 __global__ void __launch_bounds__(kUpdThreads) k_rank_update_c64_ref(float2* __restrict__ G, int64_t ldg,
-                                                                     int64_t n, int pmax,
+                                                                     int64_t n, int64_t rows, int pmax,
                                                                      const cplx* __restrict__ C0,
                                                                      const cplx* __restrict__ S,
                                                                      const UpdCtl* __restrict__ ctl,
@@ -600,8 +608,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_rank_update_c64_ref(float2* __r
   if (p == 0) return;
   const int64_t j = blockIdx.x * (int64_t)kUpdThreads + threadIdx.x;
   if (j >= n) return;
-  for (int64_t i0 = (int64_t)blockIdx.y * kUpdRows; i0 < n; i0 += (int64_t)gridDim.y * kUpdRows) {
-    const int64_t iend = i0 + kUpdRows < n ? i0 + kUpdRows : n;
+  for (int64_t i0 = (int64_t)blockIdx.y * kUpdRows; i0 < rows; i0 += (int64_t)gridDim.y * kUpdRows) {
+    const int64_t iend = i0 + kUpdRows < rows ? i0 + kUpdRows : rows;
     for (int64_t i = i0; i < iend; ++i) {
       float2 g = G[i * ldg + j];
       cplx acc = mk(0.0, 0.0);
@@ -621,7 +629,7 @@ constexpr int kF32Threads = 256;
 constexpr int kF32Rows = 32;
 constexpr int kF32Cols = 2 * kF32Threads;
 
-__device__ __forceinline__ void c64_fp32_tile(float2* __restrict__ G, int64_t ldg, int64_t n, int pmax, int p,
+__device__ __forceinline__ void c64_fp32_tile(float2* __restrict__ G, int64_t ldg, int64_t n, int64_t m, int pmax, int p,
                                               const cplx* __restrict__ C0, const cplx* __restrict__ S,
                                               int64_t rt, int64_t ct, float2 (*sC)[kC64Fp32MaxP]) {
   const int64_t i0 = rt * kF32Rows;
@@ -630,7 +638,7 @@ __device__ __forceinline__ void c64_fp32_tile(float2* __restrict__ G, int64_t ld
   for (int t = threadIdx.x; t < kF32Rows * kC64Fp32MaxP; t += kF32Threads) {
     const int r = t / kC64Fp32MaxP, u = t % kC64Fp32MaxP;
     const int64_t i = i0 + r;
-    cplx c = (i < n && u < p) ? C0[i * pmax + u] : mk(0.0, 0.0);
+    cplx c = (i < m && u < p) ? C0[i * pmax + u] : mk(0.0, 0.0);
     sC[r][u] = make_float2((float)c.re, (float)c.im);
   }
   __syncthreads();
@@ -644,7 +652,7 @@ __device__ __forceinline__ void c64_fp32_tile(float2* __restrict__ G, int64_t ld
     s0[u] = make_float2((float)a.re, (float)a.im);
     s1[u] = make_float2((float)b.re, (float)b.im);
   }
-  const int rows = (int)(n - i0 < kF32Rows ? n - i0 : kF32Rows);
+  const int rows = (int)(m - i0 < kF32Rows ? m - i0 : kF32Rows);
   constexpr int U = 8;
   for (int r0 = 0; r0 < rows; r0 += U) {
     float4 g[U];
@@ -677,7 +685,7 @@ __device__ __forceinline__ void c64_fp32_tile(float2* __restrict__ G, int64_t ld
 }
 
 __global__ void __launch_bounds__(kF32Threads, 3) k_rank_update_c64_fp32(float2* __restrict__ G, int64_t ldg, int64_t n,
-                                                                      int pmax, const cplx* __restrict__ C0,
+                                                                      int64_t m, int pmax, const cplx* __restrict__ C0,
                                                                       const cplx* __restrict__ S,
                                                                       const UpdCtl* __restrict__ ctl,
                                                                       int32_t* __restrict__ prof_p) {
@@ -685,9 +693,9 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_rank_update_c64_fp32(float2*
   const int p = ctl->skip ? 0 : ctl->nv;
   if (prof_p && blockIdx.x == 0 && threadIdx.x == 0) *prof_p = p;
   if (p < 1 || p > kC64Fp32MaxP) return;
-  const int64_t nrt = (n + kF32Rows - 1) / kF32Rows, nct = (n + kF32Cols - 1) / kF32Cols;
+  const int64_t nrt = (m + kF32Rows - 1) / kF32Rows, nct = (n + kF32Cols - 1) / kF32Cols;
   for (int64_t t = blockIdx.x; t < nrt * nct; t += gridDim.x)
-    c64_fp32_tile(G, ldg, n, pmax, p, C0, S, t / nct, t % nct, sC);
+    c64_fp32_tile(G, ldg, n, m, pmax, p, C0, S, t / nct, t % nct, sC);
 }
 
 // Batched: the tiles of every problem that applies an update, interleaved over the CTAs.
@@ -717,15 +725,15 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_rank_update_c64_fp32_batch(c
     const int64_t n = it.L.n;
     const int64_t nct = (n + kF32Cols - 1) / kF32Cols;
     const int64_t u = t - s_begin[b];
-    c64_fp32_tile(reinterpret_cast<float2*>(it.G), it.ldg, n, it.L.pmax, s_p[b],
+    c64_fp32_tile(reinterpret_cast<float2*>(it.G), it.ldg, n, n, it.L.pmax, s_p[b],
                   reinterpret_cast<const cplx*>(it.ws + it.L.C0), reinterpret_cast<const cplx*>(it.ws + it.L.S),
                   u / nct, u % nct, sC);
   }
 }
 
-void launch_rank_update_c64_fp32(float2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0, const cplx* S,
+void launch_rank_update_c64_fp32(float2* G, int64_t ldg, int64_t n, int64_t rows, int pmax, const cplx* C0, const cplx* S,
                                  const UpdCtl* ctl, int32_t* prof_p, int ctas, cudaStream_t st) {
-  k_rank_update_c64_fp32<<<ctas, kF32Threads, 0, st>>>(G, ldg, n, pmax, C0, S, ctl, prof_p);
+  k_rank_update_c64_fp32<<<ctas, kF32Threads, 0, st>>>(G, ldg, n, rows, pmax, C0, S, ctl, prof_p);
 }
 
 void launch_rank_update_c64_fp32_batch(const BatchItem* items, int nprob, int ctas, cudaStream_t st) {
@@ -753,8 +761,12 @@ __device__ __forceinline__ void finish_body(const UpdArgs& a, const WsLayout& L,
       for (int l = 0; l < a.nlam; ++l) {
         const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + l * L.panel_s);
         const cplx* yd = reinterpret_cast<const cplx*>(ws + L.yd + l * L.yd_s);
-        cplx e = a.lam[l].E[ii];
-        for (int u = 0; u < p; ++u) e = cfma(C0[ii * L.pmax + u], yd[u], e);
+        const UpdLam& U = a.lam[l];
+        cplx e = U.E[ii];
+        if (U.vrows)        // G[ii, V[u]] read as G[V[u], ii] from the row panel (reciprocity)
+          for (int u = 0; u < p; ++u) e = cfma(ldG(U.vrows, a.dtype, U.ldv, u, ii), yd[u], e);
+        else
+          for (int u = 0; u < p; ++u) e = cfma(C0[ii * L.pmax + u], yd[u], e);
         if (p > 0) a.lam[l].E[ii] = e;
         f += abs2(e);
       }
@@ -867,6 +879,7 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   if (pre) k_capacitance_lam<<<a.nlam, 256, cap_smem, st>>>(ca, L, ws, state, idx, status);
   k_capacitance<<<1, 256, cap_smem, st>>>(ca, L, ws, state, idx, status, pre);
   const int64_t n = L.n;
+  const int64_t rows = a.lam[0].rows;       // rows of G held (n, or a shard's row block)
   // complex64 on the tensor cores: S is formed from an explicit D A^{-1} by an FP32 GEMM, so
   // the panels kernel only gathers C0
   struct Map128 { alignas(64) unsigned char b[128]; };
@@ -879,16 +892,17 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   // enough (n^2 p_max <= kC128SmallWork, G resident in L2) that the FP64 FMA kernel finishes
   // before the persistent tensor-core pipeline has filled (32x32 single pixel: 19 vs 44 us)
   const bool oz = a.dtype == GF_C128 &&
-                  (a.algo == GF_UPDATE_TENSOR || (a.algo == GF_UPDATE_TC && (double)n * (double)n * L.pmax > kC128SmallWork));
+                  (a.algo == GF_UPDATE_TENSOR || (a.algo == GF_UPDATE_TC && (double)rows * (double)n * L.pmax > kC128SmallWork));
   for (int l = 0; c64tc && l < a.nlam; ++l)
-    c64tc = c64_tc_make_map(reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, maps[l].b);
+    c64tc = c64_tc_make_map(reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, rows, maps[l].b);
   {
-    int64_t b = (n + 255) / 256;
+    const int64_t w = rows > n ? rows : n;
+    int64_t b = (w + 255) / 256;
     k_panels<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(a, L, ws, c64tc ? 0 : 1);
   }
   const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
   dim3 grid((unsigned)((n + kUpdThreads - 1) / kUpdThreads),
-            (unsigned)(((n + kUpdRows - 1) / kUpdRows) < 65535 ? (n + kUpdRows - 1) / kUpdRows : 65535));
+            (unsigned)(((rows + kUpdRows - 1) / kUpdRows) < 65535 ? (rows + kUpdRows - 1) / kUpdRows : 65535));
   for (int l = 0; l < a.nlam; ++l) {
     const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + l * L.panel_s);
     const cplx* S = reinterpret_cast<const cplx*>(ws + L.S + l * L.panel_s);
@@ -904,27 +918,28 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
       if (oz) {
         // p <= 4 on the tensor cores; the DFMA kernel below takes p > 4
         // without a tensor map (driver too old) the DFMA kernel below takes every p
-        if (launch_rank_update_ozaki(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl,
+        if (launch_rank_update_ozaki(G, a.lam[l].ldg, n, rows, L.pmax, C0, S, ctl,
                                      reinterpret_cast<uint8_t*>(ws + L.ozA), reinterpret_cast<int32_t*>(ws + L.ozE),
                                      reinterpret_cast<uint8_t*>(ws + L.ozB), reinterpret_cast<int32_t*>(ws + L.ozF),
                                      status, prof_p, a.sm_count, st))
           only_above = 4;
       }
       if (!oz || L.pmax > 4 || only_above == 0)
-        k_rank_update_f64<<<grid, kUpdThreads, 0, st>>>(G, a.lam[l].ldg, n, L.pmax, C0, S, ctl, only_above, prof_p);
+        k_rank_update_f64<<<grid, kUpdThreads, 0, st>>>(G, a.lam[l].ldg, n, rows, L.pmax, C0, S, ctl, only_above,
+                                                        prof_p);
     } else if (c64f32) {
-      launch_rank_update_c64_fp32(reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, L.pmax, C0, S, ctl, prof_p,
-                                  a.sm_count * 3, st);
+      launch_rank_update_c64_fp32(reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, rows, L.pmax, C0, S, ctl,
+                                  prof_p, a.sm_count * 3, st);
     } else if (c64tc) {
-      launch_rank_update_c64_tc(maps[l].b, reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, L, ws, l, status,
-                                prof_p, a.sm_count, st);
+      launch_rank_update_c64_tc(maps[l].b, reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, rows,
+                                a.lam[l].vrows, a.lam[l].ldv, L, ws, l, status, prof_p, a.sm_count, st);
     } else {
       k_rank_update_c64_ref<<<grid, kUpdThreads, 0, st>>>(reinterpret_cast<float2*>(a.lam[l].G),
-                                                          a.lam[l].ldg, n, L.pmax, C0, S, ctl, prof_p);
+                                                          a.lam[l].ldg, n, rows, L.pmax, C0, S, ctl, prof_p);
     }
     if (rec) {
       cudaEventRecord(timer->ev1[timer->used], st);
-      timer->n2[timer->used] = (double)n * (double)n;
+      timer->n2[timer->used] = (double)rows * (double)n;
       timer->bytes_per_entry[timer->used] = a.dtype == GF_C128 ? 32 : 16;
       timer->used++;
     }

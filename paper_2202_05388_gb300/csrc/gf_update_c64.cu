@@ -42,11 +42,12 @@ constexpr int kC64EpiWarps = 16;
 constexpr int kC64Threads = 32 * (kC64EpiWarps + 4);   // + G producer, MMA, storer, operand producer
 constexpr uint64_t kC64TimeoutNs = 2000000000ull;
 constexpr uint64_t kC64DrainNs = 100000000ull;
-// streaming raster: groups of 32 row tiles.  The 152 CTAs work on neighbouring tiles of about
-// five column pairs; a group's A chunks (32 x 128 KB at K = 256) stay in L2 and every B chunk is
-// fetched from DRAM once per group.  Measured at 320x320, K = 256: 39.7 ms per update with
-// groups of 8 (B fetched 100 times per launch), 35.6 ms with 32, 43.8 ms with 64 and an L2 prefetch.
-constexpr int kC64Group = 32;
+// streaming raster: groups of 64 row tiles.  The 152 CTAs work on neighbouring tiles of two or
+// three column pairs; a group's A chunks (64 x 128 KB at K = 256) stay in L2 and every B chunk is
+// fetched from DRAM once per group.  Measured at 320x320, K = 256, ms per update: groups of 8
+// 39.7 (B fetched 100 times per launch), 16 37.2, 24 35.9, 32 35.6, 48 33.5, 64 33.0-33.5; an L2
+// prefetch of the next tile's chunks made every size slower (41-44).
+constexpr int kC64Group = 64;
 constexpr int kC64Exp = 14;                    // scaled operands lie in (-2^14, 2^14)
 constexpr int kC64MinExp = -40;                // smallest scale exponent (keeps 2^(E+F-28) normal)
 
@@ -144,7 +145,9 @@ __global__ void k_c64_inverse(WsLayout L, char* ws, int lam, float2* __restrict_
 // ---- S = (D A^{-1}) G[V, :] in FP32, written as scaled split-FP16 B operand blocks ----------
 // One CTA per 64 complex columns (one 128-real-column tile, both tiles of the last pair are
 // written); thread (j, quarter of u range).
-__global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G, int64_t ldg, int64_t n,
+// Row v of the update set is read at R + rowof(v) ldr: from G (rowof = V[v]) or from a panel of the
+// set's rows (V == nullptr, rowof = v).
+__global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ R, int64_t ldr, int64_t n,
                                                     const float2* __restrict__ Mdai, const int32_t* __restrict__ V,
                                                     const UpdCtl* __restrict__ ctl, int nkc,
                                                     uint8_t* __restrict__ Bops, int32_t* __restrict__ Fcol) {
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ G
     float2 rv[16];
 #pragma unroll
     for (int vv = 0; vv < 16; ++vv)
-      rv[vv] = (j < n && v0 + vv < p) ? G[(int64_t)V[v0 + vv] * ldg + j] : make_float2(0.f, 0.f);
+      rv[vv] = (j < n && v0 + vv < p) ? R[(int64_t)(V ? V[v0 + vv] : v0 + vv) * ldr + j] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int vv = 0; vv < 16; ++vv) {
       const float2 r = rv[vv];
@@ -787,12 +790,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 c64_encode_fn() {
   return fn;
 }
 
-// complex64 G as a 2-D tensor of floats: 2n columns by n rows, row stride 8 ldg bytes; boxes of
-// 32 floats (128 B) x 128 rows, 128-byte swizzle.
-static bool make_tmap_G64(CUtensorMap* m, float2* G, int64_t ldg, int64_t n) {
+// complex64 G as a 2-D tensor of floats: 2n columns by `rows` rows (n, or a row block), row
+// stride 8 ldg bytes; boxes of 32 floats (128 B) x 128 rows, 128-byte swizzle.
+static bool make_tmap_G64(CUtensorMap* m, float2* G, int64_t ldg, int64_t n, int64_t rows) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = c64_encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)(2 * n), (cuuint64_t)n};
+  cuuint64_t dims[2] = {(cuuint64_t)(2 * n), (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(8 * ldg)};
   cuuint32_t box[2] = {32, (cuuint32_t)kC64M};
   cuuint32_t estr[2] = {1, 1};
@@ -801,14 +804,16 @@ static bool make_tmap_G64(CUtensorMap* m, float2* G, int64_t ldg, int64_t n) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool c64_tc_make_map(float2* G, int64_t ldg, int64_t n, void* map128) {
-  return make_tmap_G64(reinterpret_cast<CUtensorMap*>(map128), G, ldg, n);
+bool c64_tc_make_map(float2* G, int64_t ldg, int64_t n, int64_t rows, void* map128) {
+  return make_tmap_G64(reinterpret_cast<CUtensorMap*>(map128), G, ldg, n, rows);
 }
 
-void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64_t n, const WsLayout& L, char* ws,
-                               int lam, int32_t* status, int32_t* prof_p, int sm_count, cudaStream_t st) {
+void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64_t n, int64_t grows,
+                               const void* vrows, int64_t ldv, const WsLayout& L, char* ws, int lam,
+                               int32_t* status, int32_t* prof_p, int sm_count, cudaStream_t st) {
   const CUtensorMap& tmap = *reinterpret_cast<const CUtensorMap*>(map128);
-  const C64Layout o = c64_layout(n, L.pmax);
+  C64Layout o = c64_layout(n, L.pmax);
+  o.nrt = (grows + kC64M - 1) / kC64M;       // row tiles of the rows held (n, or a row block)
   const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
   float2* Mdai = reinterpret_cast<float2*>(ws + L.c64M);
   uint8_t* Aops = reinterpret_cast<uint8_t*>(ws + L.c64A);
@@ -817,12 +822,16 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
   k_c64_inverse<<<L.pmax, 128, 0, st>>>(L, ws, lam, Mdai);
   int32_t* Erow = reinterpret_cast<int32_t*>(ws + L.c64E);
   int32_t* Fcol = reinterpret_cast<int32_t*>(ws + L.c64F);
-  k_c64_s_gemm<<<(unsigned)(2 * o.ncp), 256, 0, st>>>(G, ldg, n, Mdai, reinterpret_cast<const int32_t*>(ws + L.V), ctl,
-                                                       (int)o.nkc, Bops, Fcol);
+  if (vrows)      // the rows G[V, :] from the caller's panel (a shard of G does not hold them)
+    k_c64_s_gemm<<<(unsigned)(2 * o.ncp), 256, 0, st>>>(reinterpret_cast<const float2*>(vrows), ldv, n, Mdai, nullptr,
+                                                         ctl, (int)o.nkc, Bops, Fcol);
+  else
+    k_c64_s_gemm<<<(unsigned)(2 * o.ncp), 256, 0, st>>>(G, ldg, n, Mdai, reinterpret_cast<const int32_t*>(ws + L.V),
+                                                         ctl, (int)o.nkc, Bops, Fcol);
   {
     int64_t rows = o.nrt * kC64M;
     int64_t b = (rows + 127) / 128;
-    k_c64_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, L.pmax, n, rows, ctl, (int)o.nkc, Aops,
+    k_c64_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, L.pmax, grows, rows, ctl, (int)o.nkc, Aops,
                                                                  Erow);
   }
   // once per device: shared-memory opt-in of both forms

@@ -608,10 +608,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // G as a 2-D tensor of doubles: 2n columns (re, im interleaved) by n rows, row stride 16 ldg
 // bytes; boxes of 16 doubles (128 B) x 128 rows with 128-byte swizzle.
-static bool make_tmap_G(CUtensorMap* m, double2* G, int64_t ldg, int64_t n) {
+// complex128 G as a 2-D tensor of doubles: 2n columns by `rows` rows (n, or a row block)
+static bool make_tmap_G(CUtensorMap* m, double2* G, int64_t ldg, int64_t n, int64_t rows) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)(2 * n), (cuuint64_t)n};
+  cuuint64_t dims[2] = {(cuuint64_t)(2 * n), (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(16 * ldg)};
   cuuint32_t box[2] = {16, (cuuint32_t)kOzM};
   cuuint32_t estr[2] = {1, 1};
@@ -621,18 +622,19 @@ static bool make_tmap_G(CUtensorMap* m, double2* G, int64_t ldg, int64_t n) {
   return r == CUDA_SUCCESS;
 }
 
-bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, const cplx* C0,
+bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int64_t grows, int pmax, const cplx* C0,
                               const cplx* S, const UpdCtl* ctl, uint8_t* ozA, int32_t* ozE,
                               uint8_t* ozB, int32_t* ozF, int32_t* status, int32_t* prof_p,
                               int sm_count, cudaStream_t st) {
   (void)ozF;
   CUtensorMap tmap;
-  if (!make_tmap_G(&tmap, G, ldg, n)) return false;
+  if (!make_tmap_G(&tmap, G, ldg, n, grows)) return false;
   const OzLayout o = oz_layout(n);
+  const int64_t nrt = (grows + kOzM - 1) / kOzM;          // row tiles of the rows held
   {
-    int64_t rows = o.nrow_tiles * kOzM;
+    int64_t rows = nrt * kOzM;
     int64_t b = (rows + 127) / 128;
-    k_oz_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, pmax, n, rows, ctl, ozA, ozE);
+    k_oz_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, pmax, grows, rows, ctl, ozA, ozE);
     int64_t cols = o.ncol_tiles * (kOzN / 2);
     b = (cols + 127) / 128;
     k_oz_prep_cols<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(S, n, cols, ctl, ozB);
@@ -648,9 +650,9 @@ bool launch_rank_update_ozaki(double2* G, int64_t ldg, int64_t n, int pmax, cons
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
-  const int64_t tiles = o.nrow_tiles * o.ncol_tiles;
+  const int64_t tiles = nrt * o.ncol_tiles;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  k_rank_update_ozaki<<<grid, kOzThreadsV2, kOzSmemV2, st>>>(tmap, n, o.nrow_tiles, o.ncol_tiles, ozA, ozE, ozB,
+  k_rank_update_ozaki<<<grid, kOzThreadsV2, kOzSmemV2, st>>>(tmap, n, nrt, o.ncol_tiles, ozA, ozE, ozB,
                                                             ctl, status, prof_p);
   return true;
 }
@@ -665,7 +667,7 @@ bool ozaki_batch_params(void* out, const BatchItem* it, int nprob) {
   P->nprob = nprob;
   for (int b = 0; b < nprob; ++b) {
     const int64_t n = it[b].L.n;
-    if (!make_tmap_G(&P->maps[b], reinterpret_cast<double2*>(it[b].G), it[b].ldg, n)) return false;
+    if (!make_tmap_G(&P->maps[b], reinterpret_cast<double2*>(it[b].G), it[b].ldg, n, n)) return false;
     const OzLayout o = oz_layout(n);
     P->probs[b] = OzProb{n, o.nrow_tiles, o.ncol_tiles, reinterpret_cast<const uint8_t*>(it[b].ws + it[b].L.ozA),
                          reinterpret_cast<const int32_t*>(it[b].ws + it[b].L.ozE),

@@ -36,7 +36,9 @@ EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_v
            "gf_lowrank_init", "gf_lowrank_eval", "gf_lowrank_update", "gf_lowrank_count",
            "gf_lowrank_materialize", "gf3_num_unknowns", "gf3_num_candidates", "gf3_workspace_size",
            "gf3_fill_g0", "gf3_eval_candidates", "gf3_select_topk", "gf3_apply_update", "gf_selftest_timeout",
-           "gf_fom", "gf3_fom", "gf_lowrank_fom", "gf_refresh_field"]
+           "gf_fom", "gf3_fom", "gf_lowrank_fom", "gf_refresh_field", "gf_shard_rows", "gf_shard_fill_g0",
+           "gf_shard_eval", "gf_shard_gather_rows", "gf_shard_apply_update", "gf_shard_pack_halo",
+           "gf_shard_unpack_halo"]
 
 
 class GfError(RuntimeError):
@@ -74,6 +76,11 @@ class gf_problem3d(C.Structure):
 class gf_lowrank(C.Structure):
     _fields_ = [("geom", gf_geom), ("E", C.c_void_p), ("bands", C.c_void_p), ("monrow", C.c_void_p),
                 ("U", C.c_void_p), ("max_cols", C.c_int32)]
+
+
+class gf_shard(C.Structure):
+    _fields_ = [("geom", gf_geom), ("y0", C.c_int32), ("y1", C.c_int32), ("G", C.c_void_p), ("ldg", C.c_int64),
+                ("E", C.c_void_p), ("bands", C.c_void_p), ("mon", C.c_void_p)]
 
 
 class gf_refresh_report(C.Structure):
@@ -156,6 +163,15 @@ def load(path: str = LIB_PATH):
             "gf_lowrank_count": (C.c_int32, [P, C.POINTER(gf_lowrank), P, C.c_size_t, C.POINTER(C.c_int32),
                                              C.POINTER(C.c_int32), P]),
             "gf_lowrank_materialize": (C.c_int32, [P, C.POINTER(gf_lowrank), P, C.c_int64, P, C.c_size_t, P]),
+            "gf_shard_rows": (C.c_int64, [C.POINTER(gf_shard)]),
+            "gf_shard_fill_g0": (C.c_int32, [P, C.POINTER(gf_shard), C.c_int32, P, C.c_size_t, P]),
+            "gf_shard_eval": (C.c_int32, [P, C.POINTER(gf_shard), C.c_int32, P, C.POINTER(gf_cand_spec), P, P]),
+            "gf_shard_gather_rows": (C.c_int32, [P, C.POINTER(gf_shard), C.c_int32, P, C.POINTER(gf_cand_spec), P, P,
+                                                 P, C.c_int64, P]),
+            "gf_shard_apply_update": (C.c_int32, [P, C.POINTER(gf_shard), C.c_int32, P, C.POINTER(gf_cand_spec), P, P,
+                                                  C.c_int64, P, P, P, P, C.c_size_t, P]),
+            "gf_shard_pack_halo": (C.c_int32, [P, C.POINTER(gf_shard), P, P]),
+            "gf_shard_unpack_halo": (C.c_int32, [P, C.POINTER(gf_shard), P, P]),
             "gf_batch_table_size": (C.c_size_t, [C.c_int32]),
             "gf_batch_create": (C.c_int32, [P, C.c_int32, C.POINTER(gf_batch_item), C.c_int32,
                                             C.POINTER(gf_cand_spec), P, C.c_size_t, P, C.POINTER(P)]),
@@ -387,6 +403,36 @@ class Handle:
     def gf_lowrank_materialize(self, lr: gf_lowrank, G, ldg, ws, ws_bytes, stream=None):
         self._check(self.lib.gf_lowrank_materialize(self.h, C.byref(lr), _ptr(G), int(ldg), _ptr(ws), int(ws_bytes),
                                                     _stream(stream)))
+
+    # ---- row-block shards
+    def gf_shard_rows(self, sh: gf_shard) -> int:
+        return int(self.lib.gf_shard_rows(C.byref(sh)))
+
+    def gf_shard_fill_g0(self, sh: gf_shard, dtype, ws, ws_bytes, stream=None):
+        self._check(self.lib.gf_shard_fill_g0(self.h, C.byref(sh), int(dtype), _ptr(ws), int(ws_bytes), _stream(stream)))
+
+    def gf_shard_eval(self, sh: gf_shard, dtype, state, spec, dfom, stream=None):
+        s = spec_struct(spec)
+        self._check(self.lib.gf_shard_eval(self.h, C.byref(sh), int(dtype), _ptr(state), C.byref(s), _ptr(dfom),
+                                           _stream(stream)))
+
+    def gf_shard_gather_rows(self, sh: gf_shard, dtype, state, spec, idx, status, panel, ldp, stream=None):
+        s = spec_struct(spec)
+        self._check(self.lib.gf_shard_gather_rows(self.h, C.byref(sh), int(dtype), _ptr(state), C.byref(s), _ptr(idx),
+                                                  _ptr(status), _ptr(panel), int(ldp), _stream(stream)))
+
+    def gf_shard_apply_update(self, sh: gf_shard, dtype, state, spec, idx, panel, ldp, status, fom_out, ws, ws_bytes,
+                              stream=None, applied=None):
+        s = spec_struct(spec)
+        self._check(self.lib.gf_shard_apply_update(self.h, C.byref(sh), int(dtype), _ptr(state), C.byref(s), _ptr(idx),
+                                                   _ptr(panel), int(ldp), _ptr(status), _ptr(fom_out), _ptr(applied),
+                                                   _ptr(ws), int(ws_bytes), _stream(stream)))
+
+    def gf_shard_pack_halo(self, sh: gf_shard, out, stream=None):
+        self._check(self.lib.gf_shard_pack_halo(self.h, C.byref(sh), _ptr(out), _stream(stream)))
+
+    def gf_shard_unpack_halo(self, sh: gf_shard, inp, stream=None):
+        self._check(self.lib.gf_shard_unpack_halo(self.h, C.byref(sh), _ptr(inp), _stream(stream)))
 
     # ---- batches
     def gf_batch_table_size(self, nitems: int) -> int:
