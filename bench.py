@@ -62,7 +62,7 @@ def parse():
 
 
 def workload(name):
-    return {"brush_192": W.brush_192, "plain_32": W.plain_32, "brush_64": W.brush_64,
+    return {"brush_192": W.brush_192, "plain_32": W.plain_32, "brush_64": W.brush_64, "brush_128": W.brush_128,
             "brush_128_topk": W.brush_128_topk, "brush_320_c128": W.brush_320_c128,
             "brush_320_c64_rank4": W.brush_320_c64_rank4, "brush_96_c64_rank4": W.brush_96_c64_rank4,
             "brush_320_topk": W.brush_320_topk, "multilambda_512x64": W.multi_lambda_512x64}[name]()

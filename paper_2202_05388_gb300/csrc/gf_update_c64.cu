@@ -48,6 +48,7 @@ constexpr uint64_t kC64DrainNs = 100000000ull;
 // 39.7 (B fetched 100 times per launch), 16 37.2, 24 35.9, 32 35.6, 48 33.5, 64 33.0-33.5; an L2
 // prefetch of the next tile's chunks made every size slower (41-44).
 constexpr int kC64Group = 64;
+static_assert(kC64Group >= 1, "raster groups hold at least one row tile");
 constexpr int kC64Exp = 14;                    // scaled operands lie in (-2^14, 2^14)
 constexpr int kC64MinExp = -40;                // smallest scale exponent (keeps 2^(E+F-28) normal)
 

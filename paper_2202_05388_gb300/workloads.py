@@ -137,6 +137,17 @@ def brush_64() -> Workload:
                     CandidateSpec(KIND_BRUSH2, DIR_FILL | DIR_CLEAR, 1), 200, "c128")
 
 
+def brush_128() -> Workload:
+    """128x128 member of the complex128 brush family (G = 4.3 GB): a capture-size case for the
+    DRAM counters of the update (larger than L2 by 33x, a few GB on the device)."""
+    nx = ny = 128
+    dx = 0.05
+    mx, my = _centre_line_monitor(nx, ny, dx, beyond_centre=5.0)
+    g = Geometry(nx, ny, dx, 1.0, mx, my)
+    return Workload("brush_128x128_p4_c128", (g,),
+                    CandidateSpec(KIND_BRUSH2, DIR_FILL | DIR_CLEAR, 1), 200, "c128")
+
+
 def brush_320_topk() -> Workload:
     """320x320 pixels, complex64 G (about 84 GB), top-32 brushes with a 3-pixel
     exclusion radius accepted per step as one rank-128 update, 1500 steps.  The focus is 5
