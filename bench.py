@@ -123,13 +123,14 @@ class ClockSampler:
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one update launch, from a
-# single-pass ncu capture of the full-size workload, valid only for the kernel source it was
-# taken on (SHA-256 over the files below); otherwise the line reports null.
+# single-pass ncu capture of the same kernel on the 128x128 member of the workload's family
+# (G = 4.3 GB, 33x the L2), scaled to the full-size launch by the entries updated (n^2); valid
+# only for the kernel source it was taken on (SHA-256 over the files below), otherwise null.
 TRAFFIC_SOURCES = ("paper_2202_05388_gb300/csrc/gf_update_tc.cu", "paper_2202_05388_gb300/csrc/gf_tc.cuh")
 TRAFFIC = {
-    "brush_192x192_p4_c128": {"sha256": "7db4f095d08bf6265dec088813df9ac40098300829d41afd685f7c2b83e7f6ca",
-                              "bytes": 21.79e9 + 21.69e9,
-                              "profile": "profiles/rank_update_tc_brush192_launches.md"},
+    "brush_192x192_p4_c128": {"sha256": "d2504f1291297eaa6e03c30152043e4e70babbf4718feebb7524707343b55abe",
+                              "capture_n": 16385, "capture_bytes": 4.3148e9 + 4.2402e9, "n": 36865,
+                              "profile": "profiles/rank_update_tc_brush128_traffic.md"},
 }
 
 
@@ -143,7 +144,9 @@ def measured_traffic(workload_name):
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(root, f), "rb") as fh:
             h.update(fh.read())
-    return rec["bytes"] if h.hexdigest() == rec["sha256"] else None
+    if h.hexdigest() != rec["sha256"]:
+        return None
+    return rec["capture_bytes"] * (rec["n"] / rec["capture_n"]) ** 2
 
 
 def measured_peaks():
@@ -793,7 +796,8 @@ def run_native(args):
         tr = measured_traffic(wl.name)
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
                 "frac": achieved_gbs / peak_hbm, "traffic": tr, "peak_kind": peak_kind,
-                "traffic_note": "bytes per launch, ncu single-pass capture of this workload on this kernel source"
+                "traffic_note": "bytes per launch: ncu capture of this kernel on the 128x128 member of the workload "
+                                "family (4.3 GB), scaled by n^2 to this size; kernel source unchanged since"
                                 if tr is not None else "no capture for this workload / kernel source",
                 "kernel": "k_rank_update_ozaki (tcgen05 digit products, TMA tiles) + operand prep",
                 "fp64_pipe_note": "the same update on native DFMA is FP64-pipe bound; see dfma_update"}

@@ -123,6 +123,10 @@ struct UpdCtl {
   double joint_dfom;  // dFOM of the applied set (FP64)
   double lam_df[kMaxLamCtl];     // per-wavelength dFOM of the joint set (parallel capacitance solve)
   int32_t lam_bad[kMaxLamCtl];   // per-wavelength singular flag (parallel capacitance solve)
+  // the multi-CTA factorisation of one large system (p > 64): size, singular flag, pivot threshold
+  int32_t lu_p;
+  int32_t lu_bad;
+  double lu_thresh;
 };
 
 struct WsLayout {

@@ -157,6 +157,105 @@ __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ pi
   return true;
 }
 
+// A = I - G_VV D (row-major p x p, Eq. 9) and y = E_V for one wavelength; returns the pivot
+// threshold kSingularRel ||A||_inf (every thread).
+__device__ double cap_build(const CapArgs& a, const UpdLam& U, int p, const int32_t* __restrict__ V,
+                            const double* __restrict__ dchi, cplx* A, cplx* y) {
+  __shared__ double s_red[32];
+  const int tid = threadIdx.x;
+  for (int t = tid; t < p * p; t += blockDim.x) {
+    int r = t / p, c = t % p;
+    cplx g = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, r, V[c]) : ldG(U.G, a.u.dtype, U.ldg, V[r], V[c]);
+    cplx e = mk(r == c ? 1.0 : 0.0, 0.0);
+    A[t] = e - dchi[c] * g;
+  }
+  for (int t = tid; t < p; t += blockDim.x) y[t] = U.E[V[t]];
+  __syncthreads();
+  // ||A||_inf
+  double rs = 0.0;
+  for (int r = tid; r < p; r += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < p; ++c) s += cabs1(A[r * p + c]);
+    rs = fmax(rs, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) rs = fmax(rs, __shfl_down_sync(0xffffffffu, rs, o));
+  if ((tid & 31) == 0) s_red[tid >> 5] = rs;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[w]);
+    s_red[0] = m;
+  }
+  __syncthreads();
+  const double thresh = kSingularRel * s_red[0];
+  __syncthreads();
+  return thresh;
+}
+
+// With the factors of A (L below the diagonal, U on and above, piv), y <- A^{-1} y after y was
+// permuted and reduced by L (y_is_lower: the unit-lower solve is still to do), the dFOM of Eq. 4
+// at the monitor's unknowns (Eq. 1) into the return value (every thread), and y <- D y.
+__device__ double cap_tail(const CapArgs& a, const UpdLam& U, int p, const int32_t* __restrict__ V,
+                           const double* __restrict__ dchi, const cplx* A, const int32_t* __restrict__ piv, cplx* y,
+                           bool lower_done) {
+  __shared__ double s_red[32];
+  __shared__ double s_bv[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (int)(blockDim.x >> 5);
+  if (!lower_done) {
+    // y = P E_V, then the unit-lower solve (column-oriented: one synchronisation per column)
+    if (tid == 0)
+      for (int c = 0; c < p; ++c) {
+        const int r = piv[c];
+        if (r != c) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
+      }
+    __syncthreads();
+    for (int c = 0; c < p; ++c) {
+      const cplx yc = y[c];
+      for (int r = c + 1 + tid; r < p; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
+      __syncthreads();
+    }
+  }
+  // upper solve for y (column-oriented: one synchronisation per column)
+  for (int c = p - 1; c >= 0; --c) {
+    if (tid == 0) y[c] = cdiv(y[c], A[c * p + c]);
+    __syncthreads();
+    const cplx yc = y[c];
+    for (int r = tid; r < c; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
+    __syncthreads();
+  }
+  // Eq. 4 at the monitor's unknowns (Eq. 1): the gathers of the monitor row are spread over
+  // the block and reduced
+  double df = 0.0;
+  for (int mc = 0; mc < a.u.mcount; ++mc) {
+    const int64_t m = a.u.mrow + mc;
+    cplx part = mk(0.0, 0.0);
+    // G[m, V[u]]; from the row panel as G[V[u], m] (reciprocity)
+    for (int u = tid; u < p; u += blockDim.x) {
+      const cplx gm = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, u, m) : ldG(U.G, a.u.dtype, U.ldg, m, V[u]);
+      part = part + dchi[u] * (gm * y[u]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      part.re += __shfl_down_sync(0xffffffffu, part.re, o);
+      part.im += __shfl_down_sync(0xffffffffu, part.im, o);
+    }
+    if (lane == 0) { s_bv[wid] = part.re; s_red[wid] = part.im; }
+    __syncthreads();
+    if (tid == 0) {
+      cplx dE = mk(0.0, 0.0);
+      for (int w = 0; w < nw; ++w) dE = dE + mk(s_bv[w], s_red[w]);
+      const cplx EN = U.E[m];
+      df += abs2(EN + dE) - abs2(EN);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) s_red[0] = df;
+  for (int u = tid; u < p; u += blockDim.x) y[u] = dchi[u] * y[u];      // D y for the field update
+  __syncthreads();
+  df = s_red[0];
+  __syncthreads();
+  return df;
+}
+
 // One wavelength of the capacitance solve for the set V (p pixels, contrasts dchi): A = I - G_VV D
 // (Eq. 9), its LU with partial pivoting, y = A^{-1} E_V and the dFOM of Eq. 4 at the monitor into
 // *df (every thread); the factors, pivots and D y go to the wavelength's workspace slots.  With sA
@@ -165,161 +264,91 @@ __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ pi
 // Returns false (in every thread) when A is singular.
 __device__ bool cap_lam(const CapArgs& a, const WsLayout& L, char* ws, int l, int p, const int32_t* __restrict__ V,
                         const double* __restrict__ dchi, cplx* sA, double* df_out) {
-  __shared__ double s_red[32];
   const int tid = threadIdx.x;
-    const UpdLam& U = a.u.lam[l];
-    cplx* Aw = reinterpret_cast<cplx*>(ws + L.lu + l * L.lu_s);
-    const bool in_smem = sA && p <= kCapSmemP;
-    cplx* A = in_smem ? sA : Aw;
-    int32_t* piv = reinterpret_cast<int32_t*>(ws + L.piv + l * L.piv_s);
-    cplx* yw = reinterpret_cast<cplx*>(ws + L.yd + l * L.yd_s);
-    cplx* y = in_smem ? sA + kCapSmemP * kCapSmemP : yw;
-    // A = I - G_VV D, row-major p x p;  y = E_V
-    for (int t = tid; t < p * p; t += blockDim.x) {
-      int r = t / p, c = t % p;
-      cplx g = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, r, V[c]) : ldG(U.G, a.u.dtype, U.ldg, V[r], V[c]);
-      cplx e = mk(r == c ? 1.0 : 0.0, 0.0);
-      A[t] = e - dchi[c] * g;
-    }
-    for (int t = tid; t < p; t += blockDim.x) y[t] = U.E[V[t]];
-    __syncthreads();
-    // ||A||_inf
-    double rs = 0.0;
-    for (int r = tid; r < p; r += blockDim.x) {
-      double s = 0.0;
-      for (int c = 0; c < p; ++c) s += cabs1(A[r * p + c]);
-      rs = fmax(rs, s);
-    }
-    for (int o = 16; o > 0; o >>= 1) rs = fmax(rs, __shfl_down_sync(0xffffffffu, rs, o));
-    if ((tid & 31) == 0) s_red[tid >> 5] = rs;
-    __syncthreads();
-    if (tid == 0) {
-      double m = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[w]);
-      s_red[0] = m;
-    }
-    __syncthreads();
-    const double thresh = kSingularRel * s_red[0];
-    __syncthreads();
-    // LU with partial pivoting (row-major, in place; L below the diagonal, unit diagonal).
-    __shared__ int s_piv;
-    __shared__ int s_bad;
-    __shared__ double s_bv[32];
-    __shared__ int s_br[32];
-    __shared__ cplx s_f[kLuMaxBlocked * kLuNB];   // blocked: the panel; unblocked: multipliers
-    if (tid == 0) s_bad = 0;
-    const int nw = (int)(blockDim.x >> 5), lane = tid & 31, wid = tid >> 5;
-    if (p <= kLuMaxBlocked) {
-      if (!lu_blocked(A, p, piv, thresh, s_f)) return false;
-      // y = P E_V, then the unit-lower solve (column-oriented: one synchronisation per column)
-      if (tid == 0)
-        for (int c = 0; c < p; ++c) {
-          const int r = piv[c];
-          if (r != c) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
-        }
-      __syncthreads();
-      for (int c = 0; c < p; ++c) {
-        const cplx yc = y[c];
-        for (int r = c + 1 + tid; r < p; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
-        __syncthreads();
-      }
-    } else {
-      // unblocked form for very large joint sets (p > 256): pivot search across the block,
-      // multipliers per row, trailing update with a warp per row and lanes along the columns
-      for (int c = 0; c < p; ++c) {
-        double bv = -1.0;
-        int br = 0x7fffffff;
-        for (int rr = c + tid; rr < p; rr += blockDim.x) {
-          const double m = cabs1(A[rr * p + c]);
-          if (m > bv) { bv = m; br = rr; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-          const int orr = __shfl_down_sync(0xffffffffu, br, o);
-          if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-        }
-        if (lane == 0) { s_bv[wid] = bv; s_br[wid] = br; }
-        __syncthreads();
-        if (tid == 0) {
-          double b = s_bv[0];
-          int r = s_br[0];
-          for (int w = 1; w < nw; ++w)
-            if (s_bv[w] > b || (s_bv[w] == b && s_br[w] < r)) { b = s_bv[w]; r = s_br[w]; }
-          if (!(b >= thresh) || !(b > 0.0)) s_bad = 1;
-          s_piv = r;
-          piv[c] = r;
-        }
-        __syncthreads();
-        const int r = s_piv;
-        if (s_bad) break;
-        if (r != c) {
-          for (int v = tid; v < p; v += blockDim.x) {
-            cplx t0 = A[c * p + v];
-            A[c * p + v] = A[r * p + v];
-            A[r * p + v] = t0;
-          }
-          if (tid == 0) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
-        }
-        __syncthreads();
-        const cplx pv = A[c * p + c];
-        const cplx yc = y[c];
-        for (int rr = c + 1 + tid; rr < p; rr += blockDim.x) {
-          const cplx f = cdiv(A[rr * p + c], pv);
-          s_f[rr] = f;
-          A[rr * p + c] = f;
-          y[rr] = y[rr] - f * yc;
-        }
-        __syncthreads();
-        for (int rr = c + 1 + wid; rr < p; rr += nw) {
-          const cplx f = s_f[rr];
-          for (int v = c + 1 + lane; v < p; v += 32) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
-        }
-        __syncthreads();
-      }
-      __syncthreads();
-      if (s_bad) return false;
-    }
-    // upper solve for y (column-oriented: one synchronisation per column)
-    for (int c = p - 1; c >= 0; --c) {
-      if (tid == 0) y[c] = cdiv(y[c], A[c * p + c]);
-      __syncthreads();
-      const cplx yc = y[c];
-      for (int r = tid; r < c; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
-      __syncthreads();
-    }
-    // Eq. 4 at the monitor's unknowns (Eq. 1): the gathers of the monitor row are spread over
-    // the block and reduced
-    double df = 0.0;
-    for (int mc = 0; mc < a.u.mcount; ++mc) {
-      const int64_t m = a.u.mrow + mc;
-      cplx part = mk(0.0, 0.0);
-      // G[m, V[u]]; from the row panel as G[V[u], m] (reciprocity)
-      for (int u = tid; u < p; u += blockDim.x) {
-        const cplx gm = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, u, m) : ldG(U.G, a.u.dtype, U.ldg, m, V[u]);
-        part = part + dchi[u] * (gm * y[u]);
+  const UpdLam& U = a.u.lam[l];
+  cplx* Aw = reinterpret_cast<cplx*>(ws + L.lu + l * L.lu_s);
+  const bool in_smem = sA && p <= kCapSmemP;
+  cplx* A = in_smem ? sA : Aw;
+  int32_t* piv = reinterpret_cast<int32_t*>(ws + L.piv + l * L.piv_s);
+  cplx* yw = reinterpret_cast<cplx*>(ws + L.yd + l * L.yd_s);
+  cplx* y = in_smem ? sA + kCapSmemP * kCapSmemP : yw;
+  const double thresh = cap_build(a, U, p, V, dchi, A, y);
+  // LU with partial pivoting (row-major, in place; L below the diagonal, unit diagonal).
+  __shared__ int s_piv;
+  __shared__ int s_bad;
+  __shared__ double s_bv[32];
+  __shared__ int s_br[32];
+  __shared__ cplx s_f[kLuMaxBlocked * kLuNB];   // blocked: the panel; unblocked: multipliers
+  if (tid == 0) s_bad = 0;
+  const int nw = (int)(blockDim.x >> 5), lane = tid & 31, wid = tid >> 5;
+  bool lower_done = false;
+  if (p <= kLuMaxBlocked) {
+    if (!lu_blocked(A, p, piv, thresh, s_f)) return false;
+  } else {
+    // unblocked form for very large joint sets (p > 256): pivot search across the block,
+    // multipliers per row, trailing update with a warp per row and lanes along the columns; y
+    // is permuted and reduced alongside
+    lower_done = true;
+    for (int c = 0; c < p; ++c) {
+      double bv = -1.0;
+      int br = 0x7fffffff;
+      for (int rr = c + tid; rr < p; rr += blockDim.x) {
+        const double m = cabs1(A[rr * p + c]);
+        if (m > bv) { bv = m; br = rr; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        part.re += __shfl_down_sync(0xffffffffu, part.re, o);
-        part.im += __shfl_down_sync(0xffffffffu, part.im, o);
+        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int orr = __shfl_down_sync(0xffffffffu, br, o);
+        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
       }
-      if (lane == 0) { s_bv[wid] = part.re; s_red[wid] = part.im; }
+      if (lane == 0) { s_bv[wid] = bv; s_br[wid] = br; }
       __syncthreads();
       if (tid == 0) {
-        cplx dE = mk(0.0, 0.0);
-        for (int w = 0; w < nw; ++w) dE = dE + mk(s_bv[w], s_red[w]);
-        const cplx EN = U.E[m];
-        df += abs2(EN + dE) - abs2(EN);
+        double b = s_bv[0];
+        int r = s_br[0];
+        for (int w = 1; w < nw; ++w)
+          if (s_bv[w] > b || (s_bv[w] == b && s_br[w] < r)) { b = s_bv[w]; r = s_br[w]; }
+        if (!(b >= thresh) || !(b > 0.0)) s_bad = 1;
+        s_piv = r;
+        piv[c] = r;
+      }
+      __syncthreads();
+      const int r = s_piv;
+      if (s_bad) break;
+      if (r != c) {
+        for (int v = tid; v < p; v += blockDim.x) {
+          cplx t0 = A[c * p + v];
+          A[c * p + v] = A[r * p + v];
+          A[r * p + v] = t0;
+        }
+        if (tid == 0) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
+      }
+      __syncthreads();
+      const cplx pv = A[c * p + c];
+      const cplx yc = y[c];
+      for (int rr = c + 1 + tid; rr < p; rr += blockDim.x) {
+        const cplx f = cdiv(A[rr * p + c], pv);
+        s_f[rr] = f;
+        A[rr * p + c] = f;
+        y[rr] = y[rr] - f * yc;
+      }
+      __syncthreads();
+      for (int rr = c + 1 + wid; rr < p; rr += nw) {
+        const cplx f = s_f[rr];
+        for (int v = c + 1 + lane; v < p; v += 32) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
       }
       __syncthreads();
     }
-    if (tid == 0) s_red[0] = df;
-    for (int u = tid; u < p; u += blockDim.x) y[u] = dchi[u] * y[u];      // D y for the field update
-    if (in_smem) {                                 // the factors and D y for the later kernels
-      for (int t = tid; t < p * p; t += blockDim.x) Aw[t] = A[t];
-      for (int t = tid; t < p; t += blockDim.x) yw[t] = y[t];
-    }
     __syncthreads();
-  *df_out = s_red[0];
+    if (s_bad) return false;
+  }
+  const double df = cap_tail(a, U, p, V, dchi, A, piv, y, lower_done);
+  if (in_smem) {                                 // the factors and D y for the later kernels
+    for (int t = tid; t < p * p; t += blockDim.x) Aw[t] = A[t];
+    for (int t = tid; t < p; t += blockDim.x) yw[t] = y[t];
+  }
+  __syncthreads();
+  *df_out = df;
   __syncthreads();
   return true;
 }
@@ -452,6 +481,190 @@ __global__ void k_capacitance_lam(CapArgs a, WsLayout L, char* ws, const uint8_t
   if (threadIdx.x == 0) {
     ctl->lam_df[l] = df;
     ctl->lam_bad[l] = ok ? 0 : 1;
+  }
+}
+
+// ---- one large system (a single wavelength with p_max > kCapSmemP) factorised by many CTAs.
+// One CTA per solve is bound by that SM's FP64 pipe (p = 128: 1.9 ms).  Here the blocked
+// right-looking LU of lu_blocked runs as a sequence of launches, with the same operations in the
+// same order (so the same factors): per 8-column panel, one CTA factors the panel, applies its row
+// interchanges to the other columns and solves U12 = L11^{-1} A12; then a grid of 16 x 16 tiles
+// applies A22 -= L21 U12.  No launch waits on another CTA: the stream orders them.
+// k_cap_lu_prep forms V, A and y = E_V (and the pivot threshold); k_cap_lu_finish solves for y
+// and writes the dFOM and the singular flag where k_capacitance's first attempt reads them.
+constexpr int kLuTile = 16;
+
+__global__ void k_cap_lu_prep(CapArgs a, WsLayout L, char* ws, const uint8_t* __restrict__ state,
+                              const int32_t* __restrict__ idx, const int32_t* __restrict__ status) {
+  __shared__ int s_nv;
+  UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
+  int32_t* V = reinterpret_cast<int32_t*>(ws + L.V);
+  double* dchi = reinterpret_cast<double*>(ws + L.dchi);
+  if (threadIdx.x == 0) {
+    int nv = 0;
+    if (*status == GF_OK)
+      for (int c = 0; c < a.k; ++c) {
+        const int32_t id = idx[c];
+        if (id < 0) break;
+        nv += cand_pixels(id, a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V + nv, dchi + nv, a.u.nz);
+      }
+    s_nv = nv;
+  }
+  __syncthreads();
+  const int p = s_nv;
+  double thresh = 0.0;
+  if (p > 0)
+    thresh = cap_build(a, a.u.lam[0], p, V, dchi, reinterpret_cast<cplx*>(ws + L.lu), reinterpret_cast<cplx*>(ws + L.yd));
+  if (threadIdx.x == 0) {
+    ctl->lu_p = p;
+    ctl->lu_bad = 0;
+    ctl->lu_thresh = thresh;
+  }
+}
+
+__global__ void k_lu_panel(WsLayout L, char* ws, int q) {
+  __shared__ cplx sP[kLuMaxBlocked * kLuNB];
+  __shared__ int s_pv[kLuNB];
+  __shared__ int s_pr;
+  __shared__ cplx s_inv;
+  UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
+  const int p = ctl->lu_p;
+  const int c0 = q * kLuNB;
+  if (p <= 0 || c0 >= p || ctl->lu_bad) return;
+  cplx* A = reinterpret_cast<cplx*>(ws + L.lu);
+  int32_t* piv = reinterpret_cast<int32_t*>(ws + L.piv);
+  const double thresh = ctl->lu_thresh;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  const int nb = p - c0 < kLuNB ? p - c0 : kLuNB;
+  const int m = p - c0;
+  for (int t = tid; t < m * nb; t += nt) {
+    const int r = t / nb, j = t - r * nb;
+    sP[r * kLuNB + j] = A[(int64_t)(c0 + r) * p + c0 + j];
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (wid == 0) {
+      double bv = -1.0;
+      int br = 0x7fffffff;
+      for (int r = j + lane; r < m; r += 32) {
+        const double v = abs2(sP[r * kLuNB + j]);
+        if (v > bv) { bv = v; br = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int orr = __shfl_down_sync(0xffffffffu, br, o);
+        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+      }
+      if (lane == 0) {
+        if (!(bv >= thresh * thresh) || !(bv > 0.0)) {
+          ctl->lu_bad = 1;
+          s_pr = -1;
+        } else {
+          const cplx pv = sP[br * kLuNB + j];
+          const double d = 1.0 / bv;
+          s_inv = mk(pv.re * d, -pv.im * d);
+          s_pr = br;
+        }
+        s_pv[j] = c0 + br;
+        piv[c0 + j] = c0 + br;
+      }
+    }
+    __syncthreads();
+    const int pr = s_pr;
+    if (pr < 0) return;
+    if (pr != j && tid < nb) {
+      const cplx t0 = sP[j * kLuNB + tid];
+      sP[j * kLuNB + tid] = sP[pr * kLuNB + tid];
+      sP[pr * kLuNB + tid] = t0;
+    }
+    __syncthreads();
+    const cplx inv = s_inv;
+    for (int r = j + 1 + tid; r < m; r += nt) {
+      const cplx f = sP[r * kLuNB + j] * inv;
+      sP[r * kLuNB + j] = f;
+      for (int k = j + 1; k < nb; ++k) sP[r * kLuNB + k] = sP[r * kLuNB + k] - f * sP[j * kLuNB + k];
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < m * nb; t += nt) {
+    const int r = t / nb, j = t - r * nb;
+    A[(int64_t)(c0 + r) * p + c0 + j] = sP[r * kLuNB + j];
+  }
+  // the panel's interchanges on the columns outside it, then U12 (one thread per column)
+  for (int v = tid; v < p; v += nt) {
+    if (v >= c0 && v < c0 + nb) continue;
+    for (int j = 0; j < nb; ++j) {
+      const int r = s_pv[j];
+      if (r != c0 + j) {
+        const cplx t0 = A[(int64_t)(c0 + j) * p + v];
+        A[(int64_t)(c0 + j) * p + v] = A[(int64_t)r * p + v];
+        A[(int64_t)r * p + v] = t0;
+      }
+    }
+    if (v >= c0 + nb) {
+      cplx x[kLuNB];
+#pragma unroll
+      for (int j = 0; j < kLuNB; ++j)
+        if (j < nb) x[j] = A[(int64_t)(c0 + j) * p + v];
+#pragma unroll
+      for (int j = 1; j < kLuNB; ++j)
+        if (j < nb)
+#pragma unroll
+          for (int i = 0; i < kLuNB; ++i)
+            if (i < j) x[j] = x[j] - sP[j * kLuNB + i] * x[i];
+#pragma unroll
+      for (int j = 1; j < kLuNB; ++j)
+        if (j < nb) A[(int64_t)(c0 + j) * p + v] = x[j];
+    }
+  }
+}
+
+// A22 -= L21 U12 on one 16 x 16 tile of the trailing matrix of panel q (blockIdx: column tile, row
+// tile), each element with the panel's terms in order.
+__global__ void k_lu_trail(WsLayout L, char* ws, int q) {
+  __shared__ cplx sL[kLuTile][kLuNB];
+  __shared__ cplx sU[kLuNB][kLuTile];
+  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
+  const int p = ctl->lu_p;
+  const int c0 = q * kLuNB;
+  if (p <= 0 || c0 >= p || ctl->lu_bad) return;
+  const int nb = p - c0 < kLuNB ? p - c0 : kLuNB;
+  const int w = p - c0 - nb;
+  const int v0 = blockIdx.x * kLuTile, i0 = blockIdx.y * kLuTile;
+  if (v0 >= w || i0 >= w) return;
+  cplx* A = reinterpret_cast<cplx*>(ws + L.lu);
+  const int tid = threadIdx.x;
+  for (int t = tid; t < kLuTile * kLuNB; t += blockDim.x) {
+    const int r = t / kLuNB, j = t % kLuNB;
+    sL[r][j] = (i0 + r < w && j < nb) ? A[(int64_t)(c0 + nb + i0 + r) * p + c0 + j] : mk(0.0, 0.0);
+    const int jj = t / kLuTile, c = t % kLuTile;
+    sU[jj][c] = (v0 + c < w && jj < nb) ? A[(int64_t)(c0 + jj) * p + c0 + nb + v0 + c] : mk(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int t = tid; t < kLuTile * kLuTile; t += blockDim.x) {
+    const int r = t / kLuTile, c = t % kLuTile;
+    if (i0 + r >= w || v0 + c >= w) continue;
+    const int64_t o = (int64_t)(c0 + nb + i0 + r) * p + c0 + nb + v0 + c;
+    cplx acc = A[o];
+#pragma unroll
+    for (int j = 0; j < kLuNB; ++j)
+      if (j < nb) acc = acc - sL[r][j] * sU[j][c];
+    A[o] = acc;
+  }
+}
+
+__global__ void k_cap_lu_finish(CapArgs a, WsLayout L, char* ws) {
+  UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
+  const int p = ctl->lu_p;
+  double df = 0.0;
+  bool ok = !ctl->lu_bad;
+  if (p > 0 && ok)
+    df = cap_tail(a, a.u.lam[0], p, reinterpret_cast<const int32_t*>(ws + L.V),
+                  reinterpret_cast<const double*>(ws + L.dchi), reinterpret_cast<const cplx*>(ws + L.lu),
+                  reinterpret_cast<const int32_t*>(ws + L.piv), reinterpret_cast<cplx*>(ws + L.yd), false);
+  if (threadIdx.x == 0) {
+    ctl->lam_df[0] = df;
+    ctl->lam_bad[0] = ok ? 0 : 1;
   }
 }
 
@@ -874,9 +1087,24 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
-  // several wavelengths: their joint solves run side by side, one CTA each
-  const int pre = a.nlam > 1 && L.pmax <= kCapSmemP ? 1 : 0;
-  if (pre) k_capacitance_lam<<<a.nlam, 256, cap_smem, st>>>(ca, L, ws, state, idx, status);
+  // several wavelengths: their joint solves run side by side, one CTA each; one wavelength with
+  // a large set: the first attempt's solve factorised by many CTAs
+  const bool multi = a.nlam == 1 && L.pmax > kCapSmemP && L.pmax <= kLuMaxBlocked;
+  const int pre = (a.nlam > 1 && L.pmax <= kCapSmemP) || multi ? 1 : 0;
+  if (multi) {
+    k_cap_lu_prep<<<1, 256, 0, st>>>(ca, L, ws, state, idx, status);
+    for (int q = 0; q * kLuNB < L.pmax; ++q) {
+      k_lu_panel<<<1, 256, 0, st>>>(L, ws, q);
+      const int w = L.pmax - q * kLuNB - kLuNB;        // trailing width at p = p_max (smaller p: tiles exit)
+      if (w > 0) {
+        const unsigned t = (unsigned)((w + kLuTile - 1) / kLuTile);
+        k_lu_trail<<<dim3(t, t), 256, 0, st>>>(L, ws, q);
+      }
+    }
+    k_cap_lu_finish<<<1, 256, 0, st>>>(ca, L, ws);
+  } else if (pre) {
+    k_capacitance_lam<<<a.nlam, 256, cap_smem, st>>>(ca, L, ws, state, idx, status);
+  }
   k_capacitance<<<1, 256, cap_smem, st>>>(ca, L, ws, state, idx, status, pre);
   const int64_t n = L.n;
   const int64_t rows = a.lam[0].rows;       // rows of G held (n, or a shard's row block)

@@ -42,12 +42,13 @@ constexpr int kC64EpiWarps = 16;
 constexpr int kC64Threads = 32 * (kC64EpiWarps + 4);   // + G producer, MMA, storer, operand producer
 constexpr uint64_t kC64TimeoutNs = 2000000000ull;
 constexpr uint64_t kC64DrainNs = 100000000ull;
-// streaming raster: groups of 64 row tiles.  The 152 CTAs work on neighbouring tiles of two or
-// three column pairs; a group's A chunks (64 x 128 KB at K = 256) stay in L2 and every B chunk is
+// streaming raster: groups of 96 row tiles.  The 152 CTAs work on neighbouring tiles of one or
+// two column pairs; a group's A chunks (96 x 128 KB at K = 256) stay in L2 and every B chunk is
 // fetched from DRAM once per group.  Measured at 320x320, K = 256, ms per update: groups of 8
-// 39.7 (B fetched 100 times per launch), 16 37.2, 24 35.9, 32 35.6, 48 33.5, 64 33.0-33.5; an L2
+// 39.7 (B fetched 100 times per launch), 16 37.2, 24 35.9, 32 35.6, 48 33.5, 64 33.0-33.5,
+// 96 32.0-32.5, 128 39.5-41.2, 256 40.4-41.2 (every CTA on the same B chunks at once); an L2
 // prefetch of the next tile's chunks made every size slower (41-44).
-constexpr int kC64Group = 64;
+constexpr int kC64Group = 96;
 static_assert(kC64Group >= 1, "raster groups hold at least one row tile");
 constexpr int kC64Exp = 14;                    // scaled operands lie in (-2^14, 2^14)
 constexpr int kC64MinExp = -40;                // smallest scale exponent (keeps 2^(E+F-28) normal)

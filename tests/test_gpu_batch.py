@@ -152,3 +152,36 @@ def test_batch_create_validates_every_item():
     with pytest.raises(B.GfError):
         h.gf_batch_set_schedule(b, -1)
     h.gf_batch_destroy(b)
+
+
+def test_c64_batch_against_the_fp64_oracle():
+    """The complex64 batch (FP32 stream update, FP64 field and FOM) step by step against the FP64
+    oracle directly, not only through the single-problem runs: every problem takes the oracle's
+    choices and its G, E and FOM stay within the complex64 tolerance of the oracle's.  The
+    monitors sit off the centre line by 0.37 dx, so no mirror-symmetric pair of candidates ties
+    exactly (complex64 rounding would otherwise pick either twin)."""
+    rng = np.random.default_rng(11)
+    wls = []
+    for b in range(6):
+        side = int(rng.choice([8, 10, 12]))
+        wl = W.small(side, side, kind=W.KIND_SINGLE, dir_mask=3, ratio=20,
+                     beyond_edge=float(rng.uniform(2.0, 4.0)), steps=4, dtype="c64")
+        g = wl.geoms[0]
+        g = W.with_monitor(g, g.mon_x + 0.37 * g.dx, g.mon_y)
+        wls.append(W.Workload(wl.name, (g,), wl.spec, wl.steps, "c64"))
+    bo = BatchOptimizer(wls, dtype="c64")
+    bo.fill()
+    bo.capture(2)                # one warm-up step runs during capture set-up
+    bo.replay()
+    torch.cuda.synchronize()
+    moved = 0
+    for wl, opt in zip(wls, bo.opts):
+        orc = O.OracleProblem(wl.geoms, wl.spec)
+        for _ in range(3):
+            orc.step()
+        assert np.array_equal(opt.state.cpu().numpy(), orc.state)
+        assert rel_err(opt.G[0][:, :opt.n].cpu().numpy().astype(np.complex128), orc.Gs[0]) <= 2e-5
+        assert rel_err(opt.E[0].cpu().numpy(), orc.Es[0]) <= 2e-5
+        assert abs(float(opt.fom.cpu()[0]) - orc.fom()) <= 2e-5 * orc.fom()
+        moved += int(orc.state.sum())
+    assert moved > 0
