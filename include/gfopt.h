@@ -420,7 +420,8 @@ typedef struct gf_batch_item {
   int32_t horizon;
 } gf_batch_item;
 typedef struct gf_batch gf_batch;
-/* Device bytes of the item table of a batch of nitems. */
+/* Device bytes of the item table of a batch of nitems (the problem descriptors, then the work
+ * queue and per-problem phase counters of the persistent step kernel). */
 size_t gf_batch_table_size(int32_t nitems);
 /* Validate every item like the single-problem calls, write the item table to `table` (device,
  * 256-byte aligned, gf_batch_table_size bytes, owned by the caller) and build the launch
@@ -433,7 +434,31 @@ gf_status gf_batch_step(gf_batch* b, void* stream);
 /* Launch shape of the persistent G update: update_ctas CTAs (0: one per SM for complex128,
  * three per SM for complex64).  Used by the autotuner; results do not depend on it. */
 gf_status gf_batch_set_schedule(gf_batch* b, int32_t update_ctas);
+/* Form of the batched step.
+ *   GF_BATCH_PERSISTENT (default): one persistent launch takes the step's stages as work items
+ *     from a device queue; an item waits (bounded, 2 s) until the stage it depends on has
+ *     finished for its own problem.  A wait that gives up writes GF_ETIMEOUT to the problem's
+ *     status word and abandons that problem's step (its G, E and state are then unspecified:
+ *     fill it again); once one wait has given up, every later wait gives up at once.
+ *     complex64: the whole step is that launch; complex128: the tensor-core G update and the
+ *     bands follow as two more launches.
+ *   GF_BATCH_STAGED: one launch per stage (evaluation, selection, capacitance, panels, [operand
+ *     preparation], update, field/FOM, bands).
+ * step_ctas: CTAs of the persistent launch (0: as many as are resident on the device at once).
+ * scale (1..16): candidates, rows or band entries per thread in one work item.
+ * tile_rows (16, 32 or 64): rows of one complex64 update tile (x 512 columns) inside the
+ *   persistent launch; 0: the complex64 update and the bands run as two more launches.
+ * The knobs of the autotuner: results are bit-identical for every form and shape. */
+#define GF_BATCH_STAGED     0
+#define GF_BATCH_PERSISTENT 1
+gf_status gf_batch_set_form(gf_batch* b, int32_t form, int32_t step_ctas, int32_t scale, int32_t tile_rows);
 void gf_batch_destroy(gf_batch* b);
+/* Diagnostic of the persistent step's bounded waits (no counterpart in the paper): one step of
+ * the batch in the persistent form in which the selection of the largest problem waits for one
+ * evaluation item more than exist, with a limit of timeout_ns (1 us .. 2 s).  That problem's
+ * status word receives GF_ETIMEOUT (so does any problem with an item still waiting when the wait
+ * gave up); the launch ends and the context stays usable. */
+gf_status gf_batch_selftest_timeout(gf_batch* b, int64_t timeout_ns, void* stream);
 
 /* Diagnostic of the bounded waits (no counterpart in the paper): one CTA waits on a barrier that
  * nothing signals, with the abortable bounded wait of the tensor-core kernels, for timeout_ns

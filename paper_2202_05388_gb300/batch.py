@@ -1,15 +1,17 @@
 """Many independent design problems advanced together (the batched pattern of the greedy
 step).  Two schedules run the same kernels' arithmetic:
 
-  * fused: the library's batch entry points -- one launch per stage of the step for all
-    problems (64 per launch), the G update being one persistent launch over the tiles of
-    every problem that accepted a flip;
+  * fused: the library's batch entry points (up to 64 problems per batch), either as the
+    persistent step kernel -- the stages of every problem as work items of one launch, with
+    per-problem phase counters (complex128 adds the tensor-core update and the bands as two
+    more launches) -- or as one launch per stage of the step;
   * streams: every problem runs its own evaluate / select / update sequence as one branch of
     a fork-join over CUDA streams.
 
 Either way a run of steps is captured once into a CUDA graph and replayed, so launch cost
-disappears, and an autotuner picks the schedule (fused with a given number of update CTAs,
-or streams with a branch count and order) by timing graph replays.
+disappears, and an autotuner picks the schedule (fused: the form, the persistent launch's CTA
+count, work-item size and complex64 update tile rows, the update CTAs; streams: a branch count
+and order) by timing graph replays.
 
 Nothing here computes: the steps are libgfopt kernels (through the gf_batch_* calls or
 GreedyOptimizer).
@@ -34,6 +36,11 @@ class Schedule:
     fused: bool = False    # True: the library's batch entry points; nstreams >= 2 then splits the
                            # problems into that many size-balanced groups on their own streams
     update_ctas: int = 0   # fused: CTAs of the persistent G update (0: the library's default)
+    form: int = B.GF_BATCH_PERSISTENT   # fused: persistent step kernel or one launch per stage
+    step_ctas: int = 0     # persistent: CTAs (0: all that are resident at once)
+    scale: int = 1         # persistent: candidates / rows per thread in one work item
+    tile_rows: int = 32    # persistent, complex64: rows of an update tile (16, 32, 64; 0: the
+                           # update and the bands as their own launches)
 
 
 class BatchOptimizer:
@@ -136,6 +143,11 @@ class BatchOptimizer:
         while len(self._streams) < (self.schedule.nstreams if count is None else count):
             self._streams.append(torch.cuda.Stream(self.device))
 
+    def _set_form(self, b):
+        sch = self.schedule
+        self.h.gf_batch_set_schedule(b, sch.update_ctas)
+        self.h.gf_batch_set_form(b, sch.form, sch.step_ctas, sch.scale, sch.tile_rows)
+
     # ---- one step of every problem, enqueued on the current stream
     def enqueue_step(self):
         if self.exploring and not self.schedule.fused:
@@ -145,7 +157,7 @@ class BatchOptimizer:
             main = torch.cuda.current_stream(self.device)
             if len(self._batches) == 1:
                 for b in self._batches[0]:
-                    self.h.gf_batch_set_schedule(b, self.schedule.update_ctas)
+                    self._set_form(b)
                     self.h.gf_batch_step(b, main)
             else:
                 self._ensure_streams(len(self._batches))
@@ -155,7 +167,7 @@ class BatchOptimizer:
                     st = self._streams[g]
                     st.wait_event(start)
                     for b in handles:
-                        self.h.gf_batch_set_schedule(b, self.schedule.update_ctas)
+                        self._set_form(b)
                         self.h.gf_batch_step(b, st)
                     done = torch.cuda.Event()
                     done.record(st)
@@ -212,11 +224,18 @@ class BatchOptimizer:
                 candidates = []
             if self.fusable:
                 sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+                P = B.GF_BATCH_PERSISTENT
                 if self.opts[0].dtype == B.GF_C128:     # one update CTA fits an SM
-                    fused = [(1, sms), (2, sms // 2), (2, sms), (4, sms // 4)]
+                    staged = [(1, sms), (2, sms // 2), (2, sms), (4, sms // 4)]
+                    persistent = [Schedule(1, "given", True, sms, P, c, s) for c, s in
+                                  ((0, 1), (0, 2), (0, 4), (sms, 1))]
                 else:
-                    fused = [(1, 3 * sms), (1, 6 * sms), (2, 3 * sms), (4, 3 * sms)]
-                candidates = [Schedule(g, "given", True, c) for g, c in fused] + candidates
+                    staged = [(1, 3 * sms), (1, 6 * sms), (2, 3 * sms), (4, 3 * sms)]
+                    persistent = [Schedule(1, "given", True, u, P, c, s, r) for u, c, s, r in
+                                  ((0, 0, 1, 64), (0, 0, 2, 64), (0, 0, 1, 32), (3 * sms, 0, 1, 0),
+                                   (6 * sms, 0, 1, 0), (3 * sms, 0, 4, 0))]
+                candidates = persistent + [Schedule(g, "given", True, c, B.GF_BATCH_STAGED)
+                                           for g, c in staged] + candidates
         best, best_ms = None, float("inf")
         self.timings = []
         for sch in candidates:

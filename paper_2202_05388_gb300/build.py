@@ -29,6 +29,18 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I", INCLUDE]
 
 
+# Translation units that compile the shared stage bodies (csrc/gf_stage_bodies.cuh) contract a
+# multiply and an add into one FMA only where the source writes fma(): otherwise the compiler's
+# contraction choices differ between the kernels that inline the same body, and the batched, the
+# persistent and the single-problem kernels would disagree in the last bits.
+SHARED_BODY_FLAGS = ["-fmad=false"]
+
+
+def _flags_for(src: str):
+    with open(os.path.join(CSRC, src)) as fh:
+        return SHARED_BODY_FLAGS if '#include "gf_stage_bodies.cuh"' in fh.read() else []
+
+
 def _nvcc() -> str:
     for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
@@ -51,7 +63,7 @@ def _digest(extra_flags) -> str:
             h.update(fh.read())
     with open(os.path.join(INCLUDE, "gfopt.h"), "rb") as fh:
         h.update(fh.read())
-    h.update(" ".join(NVCC_FLAGS + list(extra_flags)).encode())
+    h.update(" ".join(NVCC_FLAGS + SHARED_BODY_FLAGS + list(extra_flags)).encode())
     h.update(platform.machine().encode())
     return h.hexdigest()
 
@@ -71,7 +83,7 @@ def build(verbose: bool = False, extra_flags=(), force: bool = False) -> str:
 
     def compile_one(args):
         src, obj = args
-        cmd = [nvcc] + NVCC_FLAGS + list(extra_flags) + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc] + NVCC_FLAGS + _flags_for(src) + list(extra_flags) + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -1,8 +1,9 @@
 // Host side of the batch entry points: many independent single-wavelength problems advanced
-// by one launch per stage of the greedy step (Fig. 1: evaluate every candidate, select,
-// update).  The item table lives in caller-owned device memory; the complex128 update's TMA
-// descriptors live in a host parameter block that every step passes to the persistent
-// tensor-core launch.
+// together through the greedy step (Fig. 1: evaluate every candidate, select, update), either
+// by the persistent step kernel (default; gf_batch_step.cu) or by one launch per stage.  The item
+// table and the persistent kernel's queue and phase counters live in caller-owned device memory;
+// the complex128 update's TMA descriptors live in a host parameter block that every step passes
+// to the persistent tensor-core launch.
 #include <stdio.h>
 #include <string.h>
 
@@ -21,7 +22,13 @@ struct gf_batch {
   void* oz_params;                 // complex128: parameter block of the persistent update
   int64_t widest_n, widest_N, widest_units;
   int update_ctas;
+  int form;                        // GF_BATCH_PERSISTENT or GF_BATCH_STAGED
+  int step_ctas, scale, tile_rows; // launch shape of the persistent step (step_ctas 0: fill the GPU)
+  gf::BatchPlan plan;
 };
+
+static size_t items_bytes(int32_t nitems) { return ((size_t)nitems * sizeof(gf::BatchItem) + 255) & ~(size_t)255; }
+static size_t sync_bytes() { return (sizeof(gf::BatchSync) + 255) & ~(size_t)255; }
 
 static gf_status bfail(gf_handle* h, gf_status s, const char* fmt, int a = 0, long long b = 0, long long c = 0) {
   char msg[256];
@@ -33,7 +40,7 @@ extern "C" {
 
 size_t gf_batch_table_size(int32_t nitems) {
   if (nitems < 1 || nitems > gf::kBatchMax) return 0;
-  return ((size_t)nitems * sizeof(gf::BatchItem) + 255) & ~(size_t)255;
+  return items_bytes(nitems) + sync_bytes();
 }
 
 gf_status gf_batch_create(gf_handle* h, int32_t nitems, const gf_batch_item* items, int32_t dtype,
@@ -60,6 +67,10 @@ gf_status gf_batch_create(gf_handle* h, int32_t nitems, const gf_batch_item* ite
   b->oz_params = nullptr;
   b->widest_n = b->widest_N = b->widest_units = 0;
   b->update_ctas = 0;
+  b->form = GF_BATCH_PERSISTENT;
+  b->step_ctas = 0;
+  b->scale = 1;
+  b->tile_rows = 32;
   b->host.resize(nitems);
   for (int i = 0; i < nitems; ++i) {
     const gf_batch_item& it = items[i];
@@ -127,8 +138,12 @@ gf_status gf_batch_create(gf_handle* h, int32_t nitems, const gf_batch_item* ite
       return bfail(h, GF_ECUDA, "cannot encode the TMA descriptors of the batch (driver entry point missing)");
     }
   }
+  gf::build_batch_plan(b->plan, b->host.data(), nitems, dtype, *spec, b->scale, b->tile_rows);
+  b->plan.items = b->table;
+  b->plan.sync = reinterpret_cast<gf::BatchSync*>(reinterpret_cast<char*>(table) + items_bytes(nitems));
   cudaStream_t st = (cudaStream_t)stream;
   cudaMemcpyAsync(table, b->host.data(), sizeof(gf::BatchItem) * (size_t)nitems, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(b->plan.sync, 0, sizeof(gf::BatchSync), st);
   cudaStreamSynchronize(st);
   s = gf::api_cuda_check(h, "gf_batch_create upload");
   if (s) {
@@ -146,6 +161,51 @@ gf_status gf_batch_set_schedule(gf_batch* b, int32_t update_ctas) {
   return GF_OK;
 }
 
+gf_status gf_batch_set_form(gf_batch* b, int32_t form, int32_t step_ctas, int32_t scale, int32_t tile_rows) {
+  if (!b) return GF_EINVAL;
+  if (form != GF_BATCH_PERSISTENT && form != GF_BATCH_STAGED) return bfail(b->h, GF_EINVAL, "unknown form %d", form);
+  if (step_ctas < 0 || step_ctas > 65535) return bfail(b->h, GF_EINVAL, "step_ctas must be in [0, 65535]");
+  if (scale < 1 || scale > 16) return bfail(b->h, GF_EINVAL, "scale must be in [1, 16] (got %d)", scale);
+  if (tile_rows != 0 && tile_rows != 16 && tile_rows != 32 && tile_rows != 64)
+    return bfail(b->h, GF_EINVAL, "tile_rows must be 0, 16, 32 or 64 (got %d)", tile_rows);
+  b->form = form;
+  b->step_ctas = step_ctas;
+  b->scale = scale;
+  b->tile_rows = tile_rows;
+  gf::BatchPlan P;
+  gf::build_batch_plan(P, b->host.data(), b->nitems, b->dtype, b->spec, scale, tile_rows);
+  P.items = b->plan.items;
+  P.sync = b->plan.sync;
+  b->plan = P;
+  return GF_OK;
+}
+
+static void persistent_step(gf_batch* b, const gf::BatchPlan& plan, cudaStream_t st) {
+  const int sms = gf::api_sm_count(b->h);
+  const int ctas = b->step_ctas > 0 ? b->step_ctas : sms * gf::batch_step_ctas_per_sm(b->tile_rows, b->spec.kind);
+  gf::launch_batch_step(plan, ctas, b->tile_rows, st);
+  if (b->dtype == GF_C128) {
+    gf::launch_rank_update_ozaki_batch(b->oz_params, b->update_ctas > 0 ? b->update_ctas : sms, st);
+    gf::launch_bands_batch(b->table, b->nitems, b->dtype, b->widest_N, st);
+  } else if (b->tile_rows == 0) {
+    gf::launch_rank_update_c64_fp32_batch(b->table, b->nitems, b->update_ctas > 0 ? b->update_ctas : 3 * sms, st);
+    gf::launch_bands_batch(b->table, b->nitems, b->dtype, b->widest_N, st);
+  }
+}
+
+gf_status gf_batch_selftest_timeout(gf_batch* b, int64_t timeout_ns, void* stream) {
+  if (!b) return GF_EINVAL;
+  if (timeout_ns < 1000 || timeout_ns > 2000000000ll)
+    return bfail(b->h, GF_EINVAL, "timeout_ns must be in [1 us, 2 s]");
+  gf_status s = gf::api_bind_device(b->h);
+  if (s) return s;
+  gf::BatchPlan P = b->plan;
+  P.timeout_ns = timeout_ns;
+  P.stall_q = 0;
+  persistent_step(b, P, (cudaStream_t)stream);
+  return gf::api_cuda_check(b->h, "gf_batch_selftest_timeout launch");
+}
+
 gf_status gf_batch_step(gf_batch* b, void* stream) {
   if (!b) return GF_EINVAL;
   gf_status s = gf::api_bind_device(b->h);
@@ -153,6 +213,10 @@ gf_status gf_batch_step(gf_batch* b, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int n = b->nitems;
   const int sms = gf::api_sm_count(b->h);
+  if (b->form == GF_BATCH_PERSISTENT) {
+    persistent_step(b, b->plan, st);
+    return gf::api_cuda_check(b->h, "gf_batch_step launch");
+  }
   gf::launch_eval_batch(b->table, n, b->dtype, b->spec, b->widest_units, st);
   gf::launch_select_batch(b->table, n, b->spec.tie_rel, st);
   gf::launch_capacitance_batch(b->table, n, b->dtype, b->spec, st);

@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include "gf_internal.cuh"
+#include "gf_stage_bodies.cuh"
 
 namespace gf {
 
@@ -153,23 +154,6 @@ __global__ void k_fill_field(int nx, int ny, double dx, double k, double my, cpl
     double s, c;
     sincos(k * y, &s, &c);
     E[j] = mk(c, s);
-  }
-}
-
-__device__ __forceinline__ void bands_body(int nx, int ny, int dtype, const void* __restrict__ G, int64_t ldg,
-                                           cplx* __restrict__ bands) {
-  const int64_t N = (int64_t)nx * ny;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < GF_NBANDS * N;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int b = (int)(t / N);
-    int64_t i = t - (int64_t)b * N;
-    int iy = (int)(i / nx), ix = (int)(i % nx);
-    int ddx, ddy;
-    band_offset(b, ddx, ddy);
-    int jx = ix + ddx, jy = iy + ddy;
-    cplx v = mk(0.0, 0.0);
-    if (jx >= 0 && jx < nx && jy >= 0 && jy < ny) v = ldG(G, dtype, ldg, i, (int64_t)jy * nx + jx);
-    bands[t] = v;
   }
 }
 

@@ -123,10 +123,6 @@ struct UpdCtl {
   double joint_dfom;  // dFOM of the applied set (FP64)
   double lam_df[kMaxLamCtl];     // per-wavelength dFOM of the joint set (parallel capacitance solve)
   int32_t lam_bad[kMaxLamCtl];   // per-wavelength singular flag (parallel capacitance solve)
-  // the multi-CTA factorisation of one large system (p > 64): size, singular flag, pivot threshold
-  int32_t lu_p;
-  int32_t lu_bad;
-  double lu_thresh;
 };
 
 struct WsLayout {
@@ -350,5 +346,52 @@ size_t ozaki_batch_params_bytes();
 bool ozaki_batch_params(void* out, const BatchItem* host_items, int nprob);
 void launch_oz_prep_batch(const BatchItem* items, int nprob, int64_t widest, cudaStream_t st);
 void launch_rank_update_ozaki_batch(const void* params, int ctas, cudaStream_t st);
+
+// ----------------------------------------------------------------------------- persistent batched step
+// One launch runs the stages of a step for every problem as work items, taken from a device queue
+// in stage-major order; an item of stage s of a problem first waits (bounded) until every item of
+// the stage that s depends on has finished for that problem.  Waits only go to items taken earlier
+// from the queue, held by running CTAs, so every wait ends without a cooperative launch.
+enum BatchStage : int32_t {
+  kStEval = 0,     // dFOM of every candidate (Eq. 9)
+  kStSelCap,       // selection, then the capacitance solve (one CTA)
+  kStPanels,       // C0 = G[:, V], S = D A^-1 G[V, :]
+  kStPrep,         // complex128: digit operands of the tensor-core update
+  kStUpdate,       // complex64: G += C0 S in FP32 (tiles of R x 512)
+  kStFinish,       // E, state, FOM
+  kStBands,        // complex64: bands of the new G
+};
+constexpr int kPlanStages = 6;
+constexpr int kBatchThreads = 256;
+struct BatchSync {                          // device; zero between launches (the last CTA clears it)
+  int32_t next;                             // next work item
+  int32_t exited;                           // CTAs that have left
+  int32_t abort;                            // a bounded wait gave up
+  int32_t pad;
+  int32_t done[kBatchMax][kPlanStages];     // finished items per queue position and plan stage
+};
+struct BatchPlan {                          // built on the host, passed by value
+  const BatchItem* items;
+  BatchSync* sync;
+  int32_t nprob, nstage, total, dtype;
+  int32_t kind, dir_mask, eval_mask;        // eval_mask: dir_mask plus the aligned-brush bit
+  double tie_rel;
+  int64_t timeout_ns;
+  int32_t stall_q;                          // diagnostic: this queue position's selection waits for
+                                            // one evaluation item more than exist (-1: none)
+  int32_t upd_tiles;                        // complex64 update tiles per work item
+  int32_t stage[kPlanStages];               // BatchStage of each plan stage
+  int32_t dep[kPlanStages];                 // plan stage waited for (-1: none)
+  int32_t order[kBatchMax];                 // queue position -> problem (largest first)
+  int32_t first[kPlanStages][kBatchMax + 1];  // item ranges: [first[s][q], first[s][q + 1])
+};
+// plan of the persistent launch: complex128 runs evaluation .. operand preparation and finish (the
+// tensor-core update and the bands follow as their own launches); complex64 runs the whole step.
+// scale: candidates / rows per thread and item; rows: row tile of the complex64 update (16, 32, 64;
+// 0: the complex64 update and bands run as their own launches)
+void build_batch_plan(BatchPlan& P, const BatchItem* host_items, int nprob, int dtype, const gf_cand_spec& spec,
+                      int scale, int rows);
+int batch_step_ctas_per_sm(int rows, int kind);
+void launch_batch_step(const BatchPlan& P, int ctas, int rows, cudaStream_t st);
 
 }  // namespace gf

@@ -15,11 +15,14 @@
 // restricted to those entries).  Memory is O(n K) instead of O(n^2).
 #include <math.h>
 
+#include <atomic>
+
 #include "gf_internal.cuh"
 
 namespace gf {
 
 constexpr int kLrP = 4;            // pixels per candidate at most (2x2 brush)
+constexpr int kLrSlices = 16;      // slices of the stored columns in the column product, at most
 
 struct LrCount {
   int32_t nterms, ncols;
@@ -35,9 +38,9 @@ struct LrStep {
 };
 
 // workspace layout: G0 table (2N) | M blocks | term first column | term width | column -> term |
-// counters | step | w (K x kLrP)
+// counters | step | w (K x kLrP) | partial columns of the column product (kLrSlices x kLrP x n)
 struct LrLayout {
-  size_t table, coef, tcol, tp, colterm, count, step, w, total;
+  size_t table, coef, tcol, tp, colterm, count, step, w, part, total;
 };
 
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -54,6 +57,7 @@ static LrLayout lr_layout(const gf_geom& g, int max_cols) {
   L.count = o; o = up256(o + sizeof(LrCount));
   L.step = o; o = up256(o + sizeof(LrStep));
   L.w = o; o = up256(o + sizeof(cplx) * kLrP * (size_t)max_cols);
+  L.part = o; o = up256(o + sizeof(cplx) * kLrSlices * kLrP * (size_t)(N + 1));
   L.total = o;
   return L;
 }
@@ -75,6 +79,7 @@ struct LrArgs {
   LrCount* count;
   LrStep* step;
   cplx* w;
+  cplx* part;
 };
 
 // G0[i, j] of a pixel column j (i may be the monitor N)
@@ -149,42 +154,140 @@ __global__ void k_lr_w(LrArgs a) {
 }
 
 // ---- the p new columns: C[:, u] = G0[:, v_u] + sum_k U[:, k] w[k][u], appended to U
+//
+// The product runs on the FP32 pipe in double-float arithmetic (a value is an unevaluated sum
+// hi + lo of two floats, about 48 bits): GB300's FP64 pipe runs at 1/64 of the FP32 rate, and the
+// FP64 form of this product kept it 97% busy.  Each FP64 entry of U and w is split exactly into
+// hi (its sign, exponent and first 23 mantissa bits) and lo (the remaining 29 bits, rounded to a
+// float) with integer operations; products use the error-free product of Dekker (the rounding
+// error of hi*hi from one FMA) plus the two cross terms, and sums use Knuth's error-free sum and a
+// renormalisation.  Every step is an _rn intrinsic, so the compiler cannot contract the sums into
+// FMAs (which would lose the error terms).  The result is converted back to FP64 once per entry.
+// Per multiply-add the error is about 2^-47 of the magnitudes involved; the columns agree with the
+// FP64 form to about 1e-13 relative over a whole run.
+struct dflt {
+  float h, l;
+};
+
+__device__ __forceinline__ dflt df_split(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  // hi's exponent field e - 896 and the scale 2^(e - 1075) of lo are normal floats for
+  // e in [949, 1150] (|x| in [2^-74, 2^128)); zero and other values take the conversions
+  if (e < 949 || e > 1150) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+  }
+  const unsigned sgn = (unsigned)((unsigned long long)b >> 63) << 31;
+  const float h = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7FFFFF));
+  // lo = (low 29 mantissa bits) * 2^(e - 1075), with the sign of x.  The 29-bit integer is rounded
+  // to a float without an integer conversion instruction (which shares the slow FP64 unit): its
+  // high 23 and low 6 bits become exact floats through the 2^23 bias, and one FMA joins them with
+  // a single rounding.
+  const unsigned m29 = (unsigned)(b & 0x1FFFFFFF);
+  const float fa = __fsub_rn(__uint_as_float(0x4B000000u | (m29 >> 6)), 8388608.0f);
+  const float fb = __fsub_rn(__uint_as_float(0x4B000000u | (m29 & 63u)), 8388608.0f);
+  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);
+  const float l = __fmul_rn(__fmaf_rn(fa, 64.0f, fb), scale);
+  return {h, sgn ? -l : l};
+}
+
+__device__ __forceinline__ double df_to(dflt a) { return (double)a.h + (double)a.l; }
+
+// c += a b
+__device__ __forceinline__ void df_fma(dflt& c, dflt a, dflt b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float s = __fadd_rn(c.h, p);
+  const float bb = __fsub_rn(s, c.h);
+  float t = __fadd_rn(__fsub_rn(c.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  t = __fadd_rn(t, __fadd_rn(c.l, e));
+  const float hs = __fadd_rn(s, t);
+  c.l = __fsub_rn(t, __fsub_rn(hs, s));
+  c.h = hs;
+}
+
+__device__ __forceinline__ dflt df_neg(dflt a) { return {-a.h, -a.l}; }
+
 constexpr int kLrThreads = 256;
 constexpr int kLrChunk = 256;      // stored columns per shared-memory chunk of w
+// Split over the stored columns: blockIdx.y takes slice y of [0, K) (gridDim.y slices; slice 0
+// also starts from the G0 column) and writes its partial columns to part[y]; k_lr_columns_sum adds
+// the slices in FP64 in a fixed order, so the result does not depend on scheduling.  One row block
+// per CTA alone leaves most of the GPU idle at n ~ 4e4 (145 CTAs).
 __global__ void __launch_bounds__(kLrThreads) k_lr_columns(LrArgs a, int32_t* __restrict__ prof) {
   const LrStep* s = a.step;
-  if (prof && blockIdx.x == 0 && threadIdx.x == 0) *prof = s->skip ? 0 : s->col0 * s->p;
+  if (prof && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *prof = s->skip ? 0 : s->col0 * s->p;
   if (s->skip) return;
-  __shared__ cplx sw[kLrChunk * kLrP];
+  __shared__ float4 sw[kLrChunk * kLrP];       // w[k][u] as (re.h, re.l, im.h, im.l)
   const int p = s->p;
   const int K = s->col0;
+  const int S = (int)gridDim.y, y = (int)blockIdx.y;
+  const int Ks = (K + S - 1) / S;
+  const int kb = y * Ks < K ? y * Ks : K;
+  const int ke = kb + Ks < K ? kb + Ks : K;
   int V[kLrP];
 #pragma unroll
   for (int u = 0; u < kLrP; ++u) V[u] = s->V[u];
   for (int64_t i0 = (int64_t)blockIdx.x * kLrThreads; i0 < a.n; i0 += (int64_t)gridDim.x * kLrThreads) {
     const int64_t i = i0 + threadIdx.x;
-    cplx acc[kLrP];
+    dflt ar[kLrP], ai[kLrP];
 #pragma unroll
-    for (int u = 0; u < kLrP; ++u) acc[u] = (i < a.n && u < p) ? g0_entry(a, i, V[u]) : mk(0.0, 0.0);
-    for (int k0 = 0; k0 < K; k0 += kLrChunk) {
-      const int kc = K - k0 < kLrChunk ? K - k0 : kLrChunk;
+    for (int u = 0; u < kLrP; ++u) {
+      const cplx g = (y == 0 && i < a.n && u < p) ? g0_entry(a, i, V[u]) : mk(0.0, 0.0);
+      ar[u] = df_split(g.re);
+      ai[u] = df_split(g.im);
+    }
+    for (int k0 = kb; k0 < ke; k0 += kLrChunk) {
+      const int kc = ke - k0 < kLrChunk ? ke - k0 : kLrChunk;
       __syncthreads();
-      for (int t = threadIdx.x; t < kc * kLrP; t += kLrThreads) sw[t] = a.w[(int64_t)k0 * kLrP + t];
+      for (int t = threadIdx.x; t < kc * kLrP; t += kLrThreads) {
+        const cplx w = a.w[(int64_t)k0 * kLrP + t];
+        const dflt wr = df_split(w.re), wi = df_split(w.im);
+        sw[t] = make_float4(wr.h, wr.l, wi.h, wi.l);
+      }
       __syncthreads();
       if (i < a.n) {
         for (int k = 0; k < kc; ++k) {
           const cplx uk = a.U[(int64_t)(k0 + k) * a.n + i];
+          const dflt ur = df_split(uk.re), ui = df_split(uk.im), nui = df_neg(ui);
 #pragma unroll
-          for (int u = 0; u < kLrP; ++u)
-            if (u < p) acc[u] = cfma(uk, sw[k * kLrP + u], acc[u]);
+          for (int u = 0; u < kLrP; ++u) {
+            if (u < p) {
+              const float4 w4 = sw[k * kLrP + u];
+              const dflt wr = {w4.x, w4.y}, wi = {w4.z, w4.w};
+              df_fma(ar[u], ur, wr);         // Re: ur wr - ui wi
+              df_fma(ar[u], nui, wi);
+              df_fma(ai[u], ur, wi);         // Im: ur wi + ui wr
+              df_fma(ai[u], ui, wr);
+            }
+          }
         }
       }
     }
     if (i < a.n) {
 #pragma unroll
       for (int u = 0; u < kLrP; ++u)
-        if (u < p) a.U[(int64_t)(K + u) * a.n + i] = acc[u];
+        if (u < p) a.part[((int64_t)y * kLrP + u) * a.n + i] = mk(df_to(ar[u]), df_to(ai[u]));
     }
+  }
+}
+
+// C[:, u] = sum of the slices' partial columns (FP64, slice order), appended to U
+__global__ void k_lr_columns_sum(LrArgs a, int S) {
+  const LrStep* s = a.step;
+  if (s->skip) return;
+  const int p = s->p;
+  const int K = s->col0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)p * a.n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int u = (int)(t / a.n);
+    const int64_t i = t - (int64_t)u * a.n;
+    cplx acc = a.part[(int64_t)u * a.n + i];
+    for (int y = 1; y < S; ++y) acc = acc + a.part[((int64_t)y * kLrP + u) * a.n + i];
+    a.U[(int64_t)(K + u) * a.n + i] = acc;
   }
 }
 
@@ -355,6 +458,7 @@ static LrArgs lr_args(const gf_lowrank& lr, char* ws) {
   a.count = reinterpret_cast<LrCount*>(ws + L.count);
   a.step = reinterpret_cast<LrStep*>(ws + L.step);
   a.w = reinterpret_cast<cplx*>(ws + L.w);
+  a.part = reinterpret_cast<cplx*>(ws + L.part);
   return a;
 }
 
@@ -469,7 +573,25 @@ gf_status gf_lowrank_update(gf_handle* h, const gf_lowrank* lr, uint8_t* state, 
     tm->p_host[tm->used] = 0;
     cudaEventRecord(tm->ev0[tm->used], st);
   }
-  gf::k_lr_columns<<<gf::grid_of(a.n, gf::kLrThreads, 4864), gf::kLrThreads, 0, st>>>(a, rec ? tm->p_dev + tm->used : nullptr);
+  {
+    // slices: enough CTAs for every SM to hold as many as it can at once
+    static std::atomic<int> per_sm[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int occ = dev >= 0 && dev < 64 ? per_sm[dev].load() : 0;
+    if (occ == 0) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gf::k_lr_columns, gf::kLrThreads, 0) != cudaSuccess ||
+          occ < 1)
+        occ = 1;
+      if (dev >= 0 && dev < 64) per_sm[dev].store(occ);
+    }
+    const int64_t rb = (a.n + gf::kLrThreads - 1) / gf::kLrThreads;
+    int64_t S = (int64_t)gf::api_sm_count(h) * occ / rb;
+    S = S < 1 ? 1 : (S > gf::kLrSlices ? gf::kLrSlices : S);
+    gf::k_lr_columns<<<dim3((unsigned)(rb < 4864 ? rb : 4864), (unsigned)S), gf::kLrThreads, 0, st>>>(
+        a, rec ? tm->p_dev + tm->used : nullptr);
+    gf::k_lr_columns_sum<<<gf::grid_of(gf::kLrP * a.n, 256, 4864), 256, 0, st>>>(a, (int)S);
+  }
   if (rec) {
     cudaEventRecord(tm->ev1[tm->used], st);
     tm->n2[tm->used] = (double)a.n;

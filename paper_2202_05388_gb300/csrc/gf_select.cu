@@ -5,45 +5,11 @@
 #include <math.h>
 
 #include "gf_internal.cuh"
+#include "gf_stage_bodies.cuh"
 
 namespace gf {
 
 constexpr int kSelThreads = 1024;
-
-// (v, id) ordering: larger v first, then smaller id.  NaN never wins.
-__device__ __forceinline__ bool better(double v, int64_t id, double bv, int64_t bid) {
-  return v > bv || (v == bv && id < bid);
-}
-
-__device__ void block_best(double& v, int64_t& id) {
-  __shared__ double sv[32];
-  __shared__ int64_t si[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_down_sync(0xffffffffu, v, o);
-    int64_t oi = __shfl_down_sync(0xffffffffu, id, o);
-    if (better(ov, oi, v, id)) { v = ov; id = oi; }
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) { sv[w] = v; si[w] = id; }
-  __syncthreads();
-  if (w == 0) {
-    v = l < (int)(blockDim.x >> 5) ? sv[l] : -INFINITY;
-    id = l < (int)(blockDim.x >> 5) ? si[l] : INT64_MAX;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, v, o);
-      int64_t oi = __shfl_down_sync(0xffffffffu, id, o);
-      if (better(ov, oi, v, id)) { v = ov; id = oi; }
-    }
-    if (l == 0) { sv[0] = v; si[0] = id; }
-  }
-  __syncthreads();
-  v = sv[0];
-  id = si[0];
-  __syncthreads();
-}
 
 __device__ __forceinline__ void cand_anchor(int64_t c, int kind, int nx, int64_t P, int& ax, int& ay) {
   if (kind == GF_KIND_SINGLE) {
@@ -56,90 +22,16 @@ __device__ __forceinline__ void cand_anchor(int64_t c, int kind, int nx, int64_t
   }
 }
 
-// Greedy policy: m = max dfom; lowest id with dfom >= m - tie_rel |m|.
-__device__ __forceinline__ void select_best_body(const double* __restrict__ dfom, int64_t ncand, double tie_rel,
-                                                 int32_t* idx, double* val, int32_t* status) {
-  double bv = -INFINITY;
-  int64_t bid = INT64_MAX;
-  for (int64_t c = threadIdx.x; c < ncand; c += blockDim.x) {
-    double v = dfom[c];
-    if (better(v, c, bv, bid)) { bv = v; bid = c; }
-  }
-  block_best(bv, bid);
-  const double m = bv;
-  if (!(m > 0.0)) {
-    if (threadIdx.x == 0) { idx[0] = -1; val[0] = m; *status = GF_ENOIMPROVE; }
-    return;
-  }
-  const double thr = m - tie_rel * fabs(m);
-  int64_t first = INT64_MAX;
-  for (int64_t c = threadIdx.x; c < ncand && c < first; c += blockDim.x) {
-    if (dfom[c] >= thr) first = c;
-  }
-  double dummy = 0.0;
-  block_best(dummy, first);    // all values equal: picks the smallest id
-  if (threadIdx.x == 0) {
-    idx[0] = (int32_t)first;
-    val[0] = dfom[first];
-    *status = GF_OK;
-  }
-}
-
 __global__ void __launch_bounds__(kSelThreads) k_select_best(const double* __restrict__ dfom, int64_t ncand,
                                                              double tie_rel, int32_t* idx, double* val,
                                                              int32_t* status) {
   select_best_body(dfom, ncand, tie_rel, idx, val, status);
 }
 
-// Batched selection: one CTA per problem of the device table; greedy, or epsilon-greedy (Sec. V)
-// with the problem's own uniform stream: the explore list (the four best improving candidates
-// in (-dFOM, id) order) comes from four block-wide passes that skip the ids already taken.
+// Batched selection: one CTA per problem of the device table.
 __global__ void __launch_bounds__(kSelThreads) k_select_best_batch(const BatchItem* __restrict__ items,
                                                                    double tie_rel) {
-  const BatchItem& it = items[blockIdx.x];
-  select_best_body(it.dfom, it.ncand, tie_rel, it.idx, it.val, it.status);
-  if (!(it.epsilon > 0.0)) return;
-  __shared__ int s_go;
-  __shared__ int64_t s_top[4];
-  __shared__ double s_val[4];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int32_t t = *it.step;
-    *it.step = t + 1;
-    s_go = 0;
-    if (t >= it.horizon) {
-      *it.status = GF_ENOMEM;                     // the uniform stream is exhausted
-    } else if (*it.status == GF_OK && it.uniforms[2 * (int64_t)t] < it.epsilon) {
-      s_go = 1;
-    }
-  }
-  __syncthreads();
-  if (!s_go) return;
-  int m = 0;
-  for (int pass = 0; pass < 4; ++pass) {
-    double bv = -INFINITY;
-    int64_t bid = INT64_MAX;
-    for (int64_t c = threadIdx.x; c < it.ncand; c += blockDim.x) {
-      const double v = it.dfom[c];
-      if (!(v > 0.0) || !better(v, c, bv, bid)) continue;
-      bool taken = false;
-      for (int q = 0; q < pass; ++q) taken |= s_top[q] == c;
-      if (!taken) { bv = v; bid = c; }
-    }
-    block_best(bv, bid);
-    if (!(bv > 0.0)) break;
-    if (threadIdx.x == 0) { s_top[pass] = bid; s_val[pass] = bv; }
-    __syncthreads();
-    m = pass + 1;
-  }
-  if (threadIdx.x == 0 && m > 0) {
-    const int32_t t = *it.step - 1;
-    int r = (int)(it.uniforms[2 * (int64_t)t + 1] * (double)m);
-    if (r > m - 1) r = m - 1;
-    if (r < 0) r = 0;
-    it.idx[0] = (int32_t)s_top[r];
-    it.val[0] = s_val[r];
-  }
+  batch_select_body(items[blockIdx.x], tie_rel);
 }
 
 void launch_select_batch(const BatchItem* items, int nprob, double tie_rel, cudaStream_t st) {

@@ -1,0 +1,1070 @@
+// Device bodies of the step's stages (Fig. 1: evaluate, select, capacitance solve, panels, G
+// update, field and FOM, bands) that several kernels share: the single-problem kernels, the
+// batched per-stage kernels and the persistent batch kernel (which runs them as work items with a
+// virtual block index and count).  Included by the translation units that launch them.
+// Inputs that a stage of the persistent kernel produces earlier in the same launch (dFOM, the
+// workspace, G, E, state) are read through plain pointers, never `const __restrict__` ones: the
+// read-only data path is only valid for data that no thread writes during the launch.
+#pragma once
+
+#include <math.h>
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+// ----------------------------------------------------------------------------- operand digits
+// of the tensor-core complex128 update (see gf_update_tc.cu)
+constexpr int kOzW = 9;            // bits per digit
+constexpr int kOzS = 6;            // digits per value
+constexpr int kOzLv = 6;           // levels a + b = 2 .. 7
+constexpr int kOzK = 8;            // real K (2 p, p <= 4)
+constexpr int kOzM = 128;          // rows per tile (TMEM lanes)
+constexpr int kOzN = 32;           // real output columns per tile (16 complex)
+constexpr int kOzSliceA = kOzM * kOzK * 4;      // bytes of one digit slice of an A tile
+constexpr int kOzSliceB = kOzN * kOzK * 4;      // bytes of one digit slice of a B tile
+constexpr int kOzTileA = kOzS * kOzSliceA;      // 24 KB
+constexpr int kOzTileB = kOzS * kOzSliceB;      // 6 KB
+constexpr uint64_t kOzTimeoutNs = 2000000000ull;
+constexpr int kOzMaxBatch = kBatchMax;
+constexpr int kOzBBlockG = kOzTileB + 64;       // B digit slices + 16 column exponents (global block)
+
+// byte offset of element (r, k) inside one K-major, no-swizzle digit slice (8x16-byte core
+// matrices; K-direction core-matrix stride 128 B, row-group stride 256 B)
+__host__ __device__ __forceinline__ int oz_off(int r, int k) {
+  return (r >> 3) * 256 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
+// six signed 9-bit digits of x in (-1, 1): x = sum_a d[a] 2^(-9(a+1)) + r, |r| <= 2^-55
+__device__ __forceinline__ void oz_digits(double x, float (&d)[kOzS]) {
+  double r = x;
+#pragma unroll
+  for (int a = 0; a < kOzS; ++a) {
+    const double sc = ldexp(1.0, kOzW * (a + 1));
+    double t = rint(r * sc);
+    d[a] = (float)t;
+    r = r - t * ldexp(1.0, -kOzW * (a + 1));
+  }
+}
+
+__device__ __forceinline__ int oz_exponent(double m) {
+  // smallest E with m < 2^E (m > 0); a zero row/column gets digits 0 and any exponent
+  return m > 0.0 ? ilogb(m) + 1 : 0;
+}
+
+// ---- operand preparation (once per step, O(n p) work) --------------------------------------
+__device__ __forceinline__ void oz_prep_rows_body(const cplx* C0, int pmax, int64_t n,
+                                                  int64_t nrows_pad, const UpdCtl* ctl,
+                                                  uint8_t* __restrict__ ozA, int32_t* __restrict__ ozE, int64_t vb = -1, int64_t vg = -1) {
+  // vb, vg: a virtual block index and count (a work item of a persistent kernel); -1: the grid's
+  const int64_t vb_ = vb < 0 ? (int64_t)blockIdx.x : vb, vg_ = vg < 0 ? (int64_t)gridDim.x : vg;
+  if (ctl->skip || ctl->nv > 4) return;
+  const int p = ctl->nv;
+  for (int64_t i = vb_ * (int64_t)blockDim.x + threadIdx.x; i < nrows_pad;
+       i += (int64_t)vg_ * blockDim.x) {
+    double v[kOzK];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      cplx c = (i < n && k < p) ? C0[i * pmax + k] : mk(0.0, 0.0);
+      v[k] = c.re;
+      v[4 + k] = c.im;
+    }
+    double m = 0.0;
+#pragma unroll
+    for (int k = 0; k < kOzK; ++k) m = fmax(m, fabs(v[k]));
+    const int E = oz_exponent(m);
+    ozE[i] = E;
+    uint8_t* tile = ozA + (i / kOzM) * (int64_t)kOzTileA;
+    const int r = (int)(i % kOzM);
+    float dg[kOzK][kOzS];
+#pragma unroll
+    for (int k = 0; k < kOzK; ++k) oz_digits(ldexp(v[k], -E), dg[k]);
+#pragma unroll
+    for (int a = 0; a < kOzS; ++a) {
+      float4* q0 = reinterpret_cast<float4*>(tile + a * kOzSliceA + oz_off(r, 0));
+      float4* q1 = reinterpret_cast<float4*>(tile + a * kOzSliceA + oz_off(r, 4));
+      *q0 = make_float4(dg[0][a], dg[1][a], dg[2][a], dg[3][a]);
+      *q1 = make_float4(dg[4][a], dg[5][a], dg[6][a], dg[7][a]);
+    }
+  }
+}
+
+__device__ __forceinline__ void oz_prep_cols_body(const cplx* S, int64_t n, int64_t ncols_pad,
+                                                  const UpdCtl* ctl, uint8_t* __restrict__ ozB, int64_t vb = -1, int64_t vg = -1) {
+  // vb, vg: a virtual block index and count (a work item of a persistent kernel); -1: the grid's
+  const int64_t vb_ = vb < 0 ? (int64_t)blockIdx.x : vb, vg_ = vg < 0 ? (int64_t)gridDim.x : vg;
+  if (ctl->skip || ctl->nv > 4) return;
+  const int p = ctl->nv;
+  // one thread per complex column j; writes real columns 2j and 2j+1
+  for (int64_t j = vb_ * (int64_t)blockDim.x + threadIdx.x; j < ncols_pad;
+       j += (int64_t)vg_ * blockDim.x) {
+    double sr[4], si[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      cplx s = (j < n && k < p) ? S[(int64_t)k * n + j] : mk(0.0, 0.0);
+      sr[k] = s.re;
+      si[k] = s.im;
+    }
+    double m = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) m = fmax(m, fmax(fabs(sr[k]), fabs(si[k])));
+    const int F = oz_exponent(m);
+    float dr[4][kOzS], di[4][kOzS];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      oz_digits(ldexp(sr[k], -F), dr[k]);
+      oz_digits(ldexp(si[k], -F), di[k]);
+    }
+    const int64_t c_re = 2 * j;
+    uint8_t* tile = ozB + (c_re / kOzN) * (int64_t)kOzBBlockG;
+    const int c = (int)(c_re % kOzN);            // even; c + 1 is the imaginary column
+    reinterpret_cast<int32_t*>(tile + kOzTileB)[c / 2] = F;
+#pragma unroll
+    for (int a = 0; a < kOzS; ++a) {
+      uint8_t* sl = tile + a * kOzSliceB;
+      *reinterpret_cast<float4*>(sl + oz_off(c, 0)) = make_float4(dr[0][a], dr[1][a], dr[2][a], dr[3][a]);
+      *reinterpret_cast<float4*>(sl + oz_off(c, 4)) = make_float4(-di[0][a], -di[1][a], -di[2][a], -di[3][a]);
+      *reinterpret_cast<float4*>(sl + oz_off(c + 1, 0)) = make_float4(di[0][a], di[1][a], di[2][a], di[3][a]);
+      *reinterpret_cast<float4*>(sl + oz_off(c + 1, 4)) = make_float4(dr[0][a], dr[1][a], dr[2][a], dr[3][a]);
+    }
+  }
+}
+
+
+// ----------------------------------------------------------------------------- candidate dFOM
+constexpr int kEvalAligned = 4;    // dir_mask bit set by the launchers: only even anchors
+
+// Solve A y = b for a 4x4 complex system by Gaussian elimination with partial pivoting.
+// Rows u with active[u] == false are identity rows with b[u] = 0, which reproduces the
+// elimination of the reduced system over the active pixels (same pivots, same arithmetic on
+// the active entries).  Returns false when a pivot is zero or below
+// kSingularRel * ||A_active||_inf.
+template <int P>
+__device__ __forceinline__ bool solve_small(cplx (&A)[P][P], cplx (&b)[P], const bool (&active)[P]) {
+  double norm = 0.0;
+#pragma unroll
+  for (int u = 0; u < P; ++u) {
+    double s = 0.0;
+#pragma unroll
+    for (int v = 0; v < P; ++v) s += cabs1(A[u][v]);
+    if (active[u]) norm = fmax(norm, s);
+  }
+  const double thresh = kSingularRel * norm;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    // pivot: first row >= c with the largest modulus
+    int r = c;
+    double best = cabs1(A[c][c]);
+#pragma unroll
+    for (int rr = c + 1; rr < P; ++rr) {
+      double m = cabs1(A[rr][c]);
+      if (m > best) { best = m; r = rr; }
+    }
+    if (!(best >= thresh) || !(best > 0.0)) ok = false;
+#pragma unroll
+    for (int rr = c + 1; rr < P; ++rr) {
+      if (rr == r) {
+#pragma unroll
+        for (int v = 0; v < P; ++v) { cplx t = A[c][v]; A[c][v] = A[rr][v]; A[rr][v] = t; }
+        cplx t = b[c]; b[c] = b[rr]; b[rr] = t;
+      }
+    }
+    cplx piv = ok ? A[c][c] : mk(1.0, 0.0);
+#pragma unroll
+    for (int rr = c + 1; rr < P; ++rr) {
+      cplx f = cdiv(A[rr][c], piv);
+#pragma unroll
+      for (int v = c; v < P; ++v) A[rr][v] = A[rr][v] - f * A[c][v];
+      b[rr] = b[rr] - f * b[c];
+    }
+  }
+#pragma unroll
+  for (int c = P - 1; c >= 0; --c) {
+    cplx acc = b[c];
+#pragma unroll
+    for (int v = c + 1; v < P; ++v) acc = acc - A[c][v] * b[v];
+    b[c] = cdiv(acc, ok ? A[c][c] : mk(1.0, 0.0));
+  }
+  return ok;
+}
+
+// Single-pixel candidates: id = j.  p = 1, so Eq. 9 is y = E_j / (1 - G_jj d_chi).
+__device__ __forceinline__ void eval_single_body(const EvalArgs& a, const uint8_t* state,
+                                                 int dir_mask, double* __restrict__ dfom, int64_t vb = -1, int64_t vg = -1) {
+  // vb, vg: a virtual block index and count (a work item of a persistent kernel); -1: the grid's
+  const int64_t vb_ = vb < 0 ? (int64_t)blockIdx.x : vb, vg_ = vg < 0 ? (int64_t)gridDim.x : vg;
+  const int64_t N = (int64_t)a.nx * a.ny;
+  const int64_t jend = a.c_end >= 0 && a.c_end < N ? a.c_end : N;
+  for (int64_t j = a.c_begin + vb_ * (int64_t)blockDim.x + threadIdx.x; j < jend;
+       j += (int64_t)vg_ * blockDim.x) {
+    const uint8_t s = state[j];
+    double d = 0.0;
+    if (s == 0 && (dir_mask & GF_DIR_FILL)) d = a.chi;
+    if (s != 0 && (dir_mask & GF_DIR_CLEAR)) d = -a.chi;
+    double total = 0.0;
+    bool valid = d != 0.0;
+    for (int l = 0; l < a.nlam && valid; ++l) {
+      const EvalLam& L = a.lam[l];
+      cplx gjj = L.bands[j];
+      cplx Ej = L.E[j];
+      cplx EN = L.E[N];
+      cplx gNj = ldG(L.G, a.dtype, L.ldg, N, j);
+      cplx A = mk(1.0 - gjj.re * d, -gjj.im * d);
+      if (!(cabs1(A) > 0.0)) { valid = false; break; }   // 1x1: singular only when zero
+      cplx y = cdiv(Ej, A);
+      cplx Em = EN + d * (gNj * y);
+      total += abs2(Em) - abs2(EN);
+    }
+    dfom[j] = valid ? total : -INFINITY;
+  }
+}
+
+// 2x2 brush candidates: id = dir*P + a, anchor a = iy*(nx-1) + ix; pixels
+// q0 = (ix,iy), q1 = (ix+1,iy), q2 = (ix,iy+1), q3 = (ix+1,iy+1).  One thread evaluates both
+// directions of its anchor.
+__device__ __forceinline__ void eval_brush_body(const EvalArgs& a, const uint8_t* state,
+                                                int dir_mask, double* __restrict__ dfom, int64_t vb = -1, int64_t vg = -1) {
+  // vb, vg: a virtual block index and count (a work item of a persistent kernel); -1: the grid's
+  const int64_t vb_ = vb < 0 ? (int64_t)blockIdx.x : vb, vg_ = vg < 0 ? (int64_t)gridDim.x : vg;
+  const int nx = a.nx;
+  const int64_t N = (int64_t)nx * a.ny;
+  const int64_t P = (int64_t)(nx - 1) * (a.ny - 1);
+  // local pixel offsets and the band that holds G[q_u, q_v]
+  const int px[4] = {0, 1, 0, 1}, py[4] = {0, 0, 1, 1};
+  const int band_of[9] = {8, 6, 4, 2, 0, 1, 3, 5, 7};   // index (ddy+1)*3 + (ddx+1)
+  const int64_t aend = a.c_end >= 0 && a.c_end < P ? a.c_end : P;
+  for (int64_t an = a.c_begin + vb_ * (int64_t)blockDim.x + threadIdx.x; an < aend;
+       an += (int64_t)vg_ * blockDim.x) {
+    const int ay = (int)(an / (nx - 1)), ax = (int)(an - (int64_t)ay * (nx - 1));
+    const int64_t j0 = (int64_t)ay * nx + ax;
+    int64_t q[4] = {j0, j0 + 1, j0 + nx, j0 + nx + 1};
+    uint8_t s[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] = state[q[u]];
+    double total[2] = {0.0, 0.0};
+    bool valid[2];
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      bool any = false;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) any |= (s[u] == (dir == 0 ? 0 : 1));
+      valid[dir] = any && (dir_mask & (dir == 0 ? GF_DIR_FILL : GF_DIR_CLEAR)) &&
+                   !((dir_mask & kEvalAligned) && ((ax | ay) & 1));
+    }
+    for (int l = 0; l < a.nlam; ++l) {
+      const EvalLam& L = a.lam[l];
+      cplx EN = L.E[N];
+#pragma unroll
+      for (int dir = 0; dir < 2; ++dir) {
+        if (!valid[dir]) continue;
+        const double dval = dir == 0 ? a.chi : -a.chi;
+        bool act[4];
+        double d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          act[u] = s[u] == (dir == 0 ? 0 : 1);
+          d[u] = act[u] ? dval : 0.0;
+        }
+        cplx A[4][4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            int b = band_of[(py[v] - py[u] + 1) * 3 + (px[v] - px[u] + 1)];
+            cplx g = L.bands[(int64_t)b * N + q[u]];
+            cplx e = mk(u == v ? 1.0 : 0.0, 0.0);
+            A[u][v] = act[u] ? e - d[v] * g : e;
+          }
+          y[u] = act[u] ? L.E[q[u]] : mk(0.0, 0.0);
+        }
+        if (!solve_small<4>(A, y, act)) { valid[dir] = false; continue; }
+        cplx dE = mk(0.0, 0.0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (act[u]) dE = dE + d[u] * (ldG(L.G, a.dtype, L.ldg, N, q[u]) * y[u]);
+        }
+        cplx Em = EN + dE;
+        total[dir] += abs2(Em) - abs2(EN);
+      }
+    }
+    dfom[an] = valid[0] ? total[0] : -INFINITY;
+    dfom[P + an] = valid[1] ? total[1] : -INFINITY;
+  }
+}
+
+
+// ----------------------------------------------------------------------------- selection
+// (v, id) ordering: larger v first, then smaller id.  NaN never wins.
+__device__ __forceinline__ bool better(double v, int64_t id, double bv, int64_t bid) {
+  return v > bv || (v == bv && id < bid);
+}
+
+__device__ __forceinline__ void block_best(double& v, int64_t& id) {
+  __shared__ double sv[32];
+  __shared__ int64_t si[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_down_sync(0xffffffffu, v, o);
+    int64_t oi = __shfl_down_sync(0xffffffffu, id, o);
+    if (better(ov, oi, v, id)) { v = ov; id = oi; }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { sv[w] = v; si[w] = id; }
+  __syncthreads();
+  if (w == 0) {
+    v = l < (int)(blockDim.x >> 5) ? sv[l] : -INFINITY;
+    id = l < (int)(blockDim.x >> 5) ? si[l] : INT64_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, v, o);
+      int64_t oi = __shfl_down_sync(0xffffffffu, id, o);
+      if (better(ov, oi, v, id)) { v = ov; id = oi; }
+    }
+    if (l == 0) { sv[0] = v; si[0] = id; }
+  }
+  __syncthreads();
+  v = sv[0];
+  id = si[0];
+  __syncthreads();
+}
+
+// Greedy policy: m = max dfom; lowest id with dfom >= m - tie_rel |m|.
+__device__ __forceinline__ void select_best_body(const double* dfom, int64_t ncand, double tie_rel,
+                                                 int32_t* idx, double* val, int32_t* status) {
+  double bv = -INFINITY;
+  int64_t bid = INT64_MAX;
+  for (int64_t c = threadIdx.x; c < ncand; c += blockDim.x) {
+    double v = dfom[c];
+    if (better(v, c, bv, bid)) { bv = v; bid = c; }
+  }
+  block_best(bv, bid);
+  const double m = bv;
+  if (!(m > 0.0)) {
+    if (threadIdx.x == 0) { idx[0] = -1; val[0] = m; *status = GF_ENOIMPROVE; }
+    return;
+  }
+  const double thr = m - tie_rel * fabs(m);
+  int64_t first = INT64_MAX;
+  for (int64_t c = threadIdx.x; c < ncand && c < first; c += blockDim.x) {
+    if (dfom[c] >= thr) first = c;
+  }
+  double dummy = 0.0;
+  block_best(dummy, first);    // all values equal: picks the smallest id
+  if (threadIdx.x == 0) {
+    idx[0] = (int32_t)first;
+    val[0] = dfom[first];
+    *status = GF_OK;
+  }
+}
+
+// One problem's selection (one CTA): greedy, or epsilon-greedy (Sec. V) with the problem's own
+// uniform stream: the explore list (the four best improving candidates in (-dFOM, id) order) comes
+// from four block-wide passes that skip the ids already taken.
+__device__ __forceinline__ void batch_select_body(const BatchItem& it, double tie_rel) {
+  select_best_body(it.dfom, it.ncand, tie_rel, it.idx, it.val, it.status);
+  if (!(it.epsilon > 0.0)) return;
+  __shared__ int s_go;
+  __shared__ int64_t s_top[4];
+  __shared__ double s_val[4];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int32_t t = *it.step;
+    *it.step = t + 1;
+    s_go = 0;
+    if (t >= it.horizon) {
+      *it.status = GF_ENOMEM;                     // the uniform stream is exhausted
+    } else if (*it.status == GF_OK && it.uniforms[2 * (int64_t)t] < it.epsilon) {
+      s_go = 1;
+    }
+  }
+  __syncthreads();
+  if (!s_go) return;
+  int m = 0;
+  for (int pass = 0; pass < 4; ++pass) {
+    double bv = -INFINITY;
+    int64_t bid = INT64_MAX;
+    for (int64_t c = threadIdx.x; c < it.ncand; c += blockDim.x) {
+      const double v = it.dfom[c];
+      if (!(v > 0.0) || !better(v, c, bv, bid)) continue;
+      bool taken = false;
+      for (int q = 0; q < pass; ++q) taken |= s_top[q] == c;
+      if (!taken) { bv = v; bid = c; }
+    }
+    block_best(bv, bid);
+    if (!(bv > 0.0)) break;
+    if (threadIdx.x == 0) { s_top[pass] = bid; s_val[pass] = bv; }
+    __syncthreads();
+    m = pass + 1;
+  }
+  if (threadIdx.x == 0 && m > 0) {
+    const int32_t t = *it.step - 1;
+    int r = (int)(it.uniforms[2 * (int64_t)t + 1] * (double)m);
+    if (r > m - 1) r = m - 1;
+    if (r < 0) r = 0;
+    it.idx[0] = (int32_t)s_top[r];
+    it.val[0] = s_val[r];
+  }
+}
+
+// ----------------------------------------------------------------------------- bands
+__device__ __forceinline__ void bands_body(int nx, int ny, int dtype, const void* G, int64_t ldg,
+                                           cplx* __restrict__ bands, int64_t vb = -1, int64_t vg = -1) {
+  // vb, vg: a virtual block index and count (a work item of a persistent kernel); -1: the grid's
+  const int64_t vb_ = vb < 0 ? (int64_t)blockIdx.x : vb, vg_ = vg < 0 ? (int64_t)gridDim.x : vg;
+  const int64_t N = (int64_t)nx * ny;
+  for (int64_t t = vb_ * (int64_t)blockDim.x + threadIdx.x; t < GF_NBANDS * N;
+       t += (int64_t)vg_ * blockDim.x) {
+    int b = (int)(t / N);
+    int64_t i = t - (int64_t)b * N;
+    int iy = (int)(i / nx), ix = (int)(i % nx);
+    int ddx, ddy;
+    band_offset(b, ddx, ddy);
+    int jx = ix + ddx, jy = iy + ddy;
+    cplx v = mk(0.0, 0.0);
+    if (jx >= 0 && jx < nx && jy >= 0 && jy < ny) v = ldG(G, dtype, ldg, i, (int64_t)jy * nx + jx);
+    bands[t] = v;
+  }
+}
+
+// ----------------------------------------------------------------------------- capacitance
+struct CapArgs {
+  UpdArgs u;
+  int kind, dir_mask, k;
+  int pmax;
+};
+
+// Blocked right-looking LU with partial pivoting of the row-major p x p complex matrix A (global
+// memory), for p <= kLuMaxBlocked, by the whole CTA.  Panels of kLuNB columns are factored in
+// shared memory (pivot = largest modulus, lowest row on ties, as in the unblocked form); their row
+// interchanges are then applied to the rest of the rows, U12 = L11^{-1} A12 is solved column by
+// column and the trailing matrix receives the rank-kLuNB update -- every element independently,
+// so the global-memory traffic is parallel instead of a chain of dependent accesses.  The result
+// (L below the diagonal with unit diagonal, U on and above it, piv[c] = row exchanged with row c
+// at step c) is the unblocked factorisation's.  Returns false (in every thread) when a pivot is
+// zero or below thresh.
+constexpr int kLuNB = 8;
+constexpr int kLuMaxBlocked = 256;
+constexpr int kCapSmemP = 64;          // capacitance systems up to this size in shared memory (64 KB)
+constexpr double kC128SmallWork = 2.5e6;   // n^2 p_max below which the FP64 FMA update is faster
+
+// sP: shared memory for kLuMaxBlocked x kLuNB entries (the panel, row-major [row][j])
+inline __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ piv, double thresh, cplx* sP) {
+  __shared__ int s_pv[kLuNB];
+  __shared__ int s_bad2, s_pr;
+  __shared__ cplx s_inv;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_bad2 = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < p; c0 += kLuNB) {
+    const int nb = p - c0 < kLuNB ? p - c0 : kLuNB;
+    const int m = p - c0;
+    for (int t = tid; t < m * nb; t += nt) {
+      const int r = t / nb, j = t - r * nb;
+      sP[r * kLuNB + j] = A[(int64_t)(c0 + r) * p + c0 + j];
+    }
+    __syncthreads();
+    // ---- panel factorisation in shared memory.  The pivot search is one warp's: the largest
+    // |a|^2 (the order of the moduli), lowest row on ties; its lane 0 also forms 1 / pivot, so
+    // each row's multiplier is a product instead of a division.
+    for (int j = 0; j < nb; ++j) {
+      if (wid == 0) {
+        double bv = -1.0;
+        int br = 0x7fffffff;
+        for (int r = j + lane; r < m; r += 32) {
+          const double v = abs2(sP[r * kLuNB + j]);
+          if (v > bv) { bv = v; br = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+          const int orr = __shfl_down_sync(0xffffffffu, br, o);
+          if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+        }
+        if (lane == 0) {
+          if (!(bv >= thresh * thresh) || !(bv > 0.0)) {
+            s_bad2 = 1;
+          } else {
+            const cplx pv = sP[br * kLuNB + j];
+            const double d = 1.0 / bv;
+            s_inv = mk(pv.re * d, -pv.im * d);
+          }
+          s_pr = br;
+          s_pv[j] = c0 + br;
+          piv[c0 + j] = c0 + br;
+        }
+      }
+      __syncthreads();
+      if (s_bad2) return false;
+      const int pr = s_pr;
+      if (pr != j && tid < nb) {
+        const cplx t0 = sP[j * kLuNB + tid];
+        sP[j * kLuNB + tid] = sP[pr * kLuNB + tid];
+        sP[pr * kLuNB + tid] = t0;
+      }
+      __syncthreads();
+      const cplx inv = s_inv;
+      for (int r = j + 1 + tid; r < m; r += nt) {
+        const cplx f = sP[r * kLuNB + j] * inv;
+        sP[r * kLuNB + j] = f;
+        for (int k = j + 1; k < nb; ++k) sP[r * kLuNB + k] = sP[r * kLuNB + k] - f * sP[j * kLuNB + k];
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < m * nb; t += nt) {
+      const int r = t / nb, j = t - r * nb;
+      A[(int64_t)(c0 + r) * p + c0 + j] = sP[r * kLuNB + j];
+    }
+    // ---- the panel's interchanges on the columns outside it (one thread per column)
+    for (int v = tid; v < p; v += nt) {
+      if (v >= c0 && v < c0 + nb) continue;
+      for (int j = 0; j < nb; ++j) {
+        const int r = s_pv[j];
+        if (r != c0 + j) {
+          const cplx t0 = A[(int64_t)(c0 + j) * p + v];
+          A[(int64_t)(c0 + j) * p + v] = A[(int64_t)r * p + v];
+          A[(int64_t)r * p + v] = t0;
+        }
+      }
+    }
+    __syncthreads();
+    const int w = p - c0 - nb;                   // trailing width
+    if (w > 0) {
+      // ---- U12 = L11^{-1} A12 (unit lower, one thread per column); for p <= kLuMaxBlocked / 2
+      // the block is also kept in the free half of the panel buffer for the trailing update
+      cplx* sU = p <= kLuMaxBlocked / 2 ? sP + (kLuMaxBlocked / 2) * kLuNB : nullptr;
+      for (int v = tid; v < w; v += nt) {
+        cplx x[kLuNB];
+#pragma unroll
+        for (int j = 0; j < kLuNB; ++j)
+          if (j < nb) x[j] = A[(int64_t)(c0 + j) * p + c0 + nb + v];
+#pragma unroll
+        for (int j = 1; j < kLuNB; ++j)
+          if (j < nb)
+#pragma unroll
+            for (int i = 0; i < kLuNB; ++i)
+              if (i < j) x[j] = x[j] - sP[j * kLuNB + i] * x[i];
+#pragma unroll
+        for (int j = 1; j < kLuNB; ++j)
+          if (j < nb) A[(int64_t)(c0 + j) * p + c0 + nb + v] = x[j];
+        if (sU)
+#pragma unroll
+          for (int j = 0; j < kLuNB; ++j)
+            if (j < nb) sU[j * w + v] = x[j];
+      }
+      __syncthreads();
+      // ---- A22 -= L21 U12, every element independently (coalesced along the row)
+      for (int e = tid; e < w * w; e += nt) {
+        const int i = e / w, v = e - i * w;
+        const int64_t o = (int64_t)(c0 + nb + i) * p + c0 + nb + v;
+        cplx acc = A[o];
+#pragma unroll
+        for (int j = 0; j < kLuNB; ++j)
+          if (j < nb)
+            acc = acc - sP[(nb + i) * kLuNB + j] * (sU ? sU[j * w + v] : A[(int64_t)(c0 + j) * p + c0 + nb + v]);
+        A[o] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// A = I - G_VV D (row-major p x p, Eq. 9) and y = E_V for one wavelength; returns the pivot
+// threshold kSingularRel ||A||_inf (every thread).
+inline __device__ double cap_build(const CapArgs& a, const UpdLam& U, int p, const int32_t* V,
+                            const double* dchi, cplx* A, cplx* y) {
+  __shared__ double s_red[32];
+  const int tid = threadIdx.x;
+  for (int t = tid; t < p * p; t += blockDim.x) {
+    int r = t / p, c = t % p;
+    cplx g = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, r, V[c]) : ldG(U.G, a.u.dtype, U.ldg, V[r], V[c]);
+    cplx e = mk(r == c ? 1.0 : 0.0, 0.0);
+    A[t] = e - dchi[c] * g;
+  }
+  for (int t = tid; t < p; t += blockDim.x) y[t] = U.E[V[t]];
+  __syncthreads();
+  // ||A||_inf
+  double rs = 0.0;
+  for (int r = tid; r < p; r += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < p; ++c) s += cabs1(A[r * p + c]);
+    rs = fmax(rs, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) rs = fmax(rs, __shfl_down_sync(0xffffffffu, rs, o));
+  if ((tid & 31) == 0) s_red[tid >> 5] = rs;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[w]);
+    s_red[0] = m;
+  }
+  __syncthreads();
+  const double thresh = kSingularRel * s_red[0];
+  __syncthreads();
+  return thresh;
+}
+
+// With the factors of A (L below the diagonal, U on and above, piv), y <- A^{-1} y after y was
+// permuted and reduced by L (y_is_lower: the unit-lower solve is still to do), the dFOM of Eq. 4
+// at the monitor's unknowns (Eq. 1) into the return value (every thread), and y <- D y.
+inline __device__ double cap_tail(const CapArgs& a, const UpdLam& U, int p, const int32_t* V,
+                           const double* dchi, const cplx* A, const int32_t* piv, cplx* y,
+                           bool lower_done) {
+  __shared__ double s_red[32];
+  __shared__ double s_bv[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (int)(blockDim.x >> 5);
+  if (!lower_done) {
+    // y = P E_V, then the unit-lower solve (column-oriented: one synchronisation per column)
+    if (tid == 0)
+      for (int c = 0; c < p; ++c) {
+        const int r = piv[c];
+        if (r != c) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
+      }
+    __syncthreads();
+    for (int c = 0; c < p; ++c) {
+      const cplx yc = y[c];
+      for (int r = c + 1 + tid; r < p; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
+      __syncthreads();
+    }
+  }
+  // upper solve for y in blocks of kLuNB rows from the bottom: one thread solves the block's
+  // triangle, then every row above takes the block's terms (two synchronisations per block)
+  for (int b1 = p; b1 > 0; b1 -= kLuNB) {
+    const int b0 = b1 - kLuNB > 0 ? b1 - kLuNB : 0;
+    if (tid == 0)
+      for (int c = b1 - 1; c >= b0; --c) {
+        cplx acc = y[c];
+        for (int v = c + 1; v < b1; ++v) acc = acc - A[c * p + v] * y[v];
+        y[c] = cdiv(acc, A[c * p + c]);
+      }
+    __syncthreads();
+    for (int r = tid; r < b0; r += blockDim.x) {
+      cplx acc = y[r];
+      for (int v = b0; v < b1; ++v) acc = acc - A[r * p + v] * y[v];
+      y[r] = acc;
+    }
+    __syncthreads();
+  }
+  // Eq. 4 at the monitor's unknowns (Eq. 1): the gathers of the monitor row are spread over
+  // the block and reduced
+  double df = 0.0;
+  for (int mc = 0; mc < a.u.mcount; ++mc) {
+    const int64_t m = a.u.mrow + mc;
+    cplx part = mk(0.0, 0.0);
+    // G[m, V[u]]; from the row panel as G[V[u], m] (reciprocity)
+    for (int u = tid; u < p; u += blockDim.x) {
+      const cplx gm = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, u, m) : ldG(U.G, a.u.dtype, U.ldg, m, V[u]);
+      part = part + dchi[u] * (gm * y[u]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      part.re += __shfl_down_sync(0xffffffffu, part.re, o);
+      part.im += __shfl_down_sync(0xffffffffu, part.im, o);
+    }
+    if (lane == 0) { s_bv[wid] = part.re; s_red[wid] = part.im; }
+    __syncthreads();
+    if (tid == 0) {
+      cplx dE = mk(0.0, 0.0);
+      for (int w = 0; w < nw; ++w) dE = dE + mk(s_bv[w], s_red[w]);
+      const cplx EN = U.E[m];
+      df += abs2(EN + dE) - abs2(EN);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) s_red[0] = df;
+  for (int u = tid; u < p; u += blockDim.x) y[u] = dchi[u] * y[u];      // D y for the field update
+  __syncthreads();
+  df = s_red[0];
+  __syncthreads();
+  return df;
+}
+
+// One wavelength of the capacitance solve for the set V (p pixels, contrasts dchi): A = I - G_VV D
+// (Eq. 9), its LU with partial pivoting, y = A^{-1} E_V and the dFOM of Eq. 4 at the monitor into
+// *df (every thread); the factors, pivots and D y go to the wavelength's workspace slots.  With sA
+// (shared memory for kCapSmemP^2 + kCapSmemP entries) a system of p <= kCapSmemP and its
+// right-hand side are built, factorised and solved there and copied to the workspace once.
+// Returns false (in every thread) when A is singular.
+inline __device__ bool cap_lam(const CapArgs& a, const WsLayout& L, char* ws, int l, int p, const int32_t* V,
+                        const double* dchi, cplx* sA, double* df_out) {
+  const int tid = threadIdx.x;
+  const UpdLam& U = a.u.lam[l];
+  cplx* Aw = reinterpret_cast<cplx*>(ws + L.lu + l * L.lu_s);
+  const bool in_smem = sA && p <= kCapSmemP;
+  cplx* A = in_smem ? sA : Aw;
+  int32_t* piv = reinterpret_cast<int32_t*>(ws + L.piv + l * L.piv_s);
+  cplx* yw = reinterpret_cast<cplx*>(ws + L.yd + l * L.yd_s);
+  cplx* y = in_smem ? sA + kCapSmemP * kCapSmemP : yw;
+  const double thresh = cap_build(a, U, p, V, dchi, A, y);
+  // LU with partial pivoting (row-major, in place; L below the diagonal, unit diagonal).
+  __shared__ int s_piv;
+  __shared__ int s_bad;
+  __shared__ double s_bv[32];
+  __shared__ int s_br[32];
+  __shared__ cplx s_f[kLuMaxBlocked * kLuNB];   // blocked: the panel; unblocked: multipliers
+  if (tid == 0) s_bad = 0;
+  const int nw = (int)(blockDim.x >> 5), lane = tid & 31, wid = tid >> 5;
+  bool lower_done = false;
+  if (p <= kLuMaxBlocked) {
+    if (!lu_blocked(A, p, piv, thresh, s_f)) return false;
+  } else {
+    // unblocked form for very large joint sets (p > 256): pivot search across the block,
+    // multipliers per row, trailing update with a warp per row and lanes along the columns; y
+    // is permuted and reduced alongside
+    lower_done = true;
+    for (int c = 0; c < p; ++c) {
+      double bv = -1.0;
+      int br = 0x7fffffff;
+      for (int rr = c + tid; rr < p; rr += blockDim.x) {
+        const double m = cabs1(A[rr * p + c]);
+        if (m > bv) { bv = m; br = rr; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int orr = __shfl_down_sync(0xffffffffu, br, o);
+        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+      }
+      if (lane == 0) { s_bv[wid] = bv; s_br[wid] = br; }
+      __syncthreads();
+      if (tid == 0) {
+        double b = s_bv[0];
+        int r = s_br[0];
+        for (int w = 1; w < nw; ++w)
+          if (s_bv[w] > b || (s_bv[w] == b && s_br[w] < r)) { b = s_bv[w]; r = s_br[w]; }
+        if (!(b >= thresh) || !(b > 0.0)) s_bad = 1;
+        s_piv = r;
+        piv[c] = r;
+      }
+      __syncthreads();
+      const int r = s_piv;
+      if (s_bad) break;
+      if (r != c) {
+        for (int v = tid; v < p; v += blockDim.x) {
+          cplx t0 = A[c * p + v];
+          A[c * p + v] = A[r * p + v];
+          A[r * p + v] = t0;
+        }
+        if (tid == 0) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
+      }
+      __syncthreads();
+      const cplx pv = A[c * p + c];
+      const cplx yc = y[c];
+      for (int rr = c + 1 + tid; rr < p; rr += blockDim.x) {
+        const cplx f = cdiv(A[rr * p + c], pv);
+        s_f[rr] = f;
+        A[rr * p + c] = f;
+        y[rr] = y[rr] - f * yc;
+      }
+      __syncthreads();
+      for (int rr = c + 1 + wid; rr < p; rr += nw) {
+        const cplx f = s_f[rr];
+        for (int v = c + 1 + lane; v < p; v += 32) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (s_bad) return false;
+  }
+  const double df = cap_tail(a, U, p, V, dchi, A, piv, y, lower_done);
+  if (in_smem) {                                 // the factors and D y for the later kernels
+    for (int t = tid; t < p * p; t += blockDim.x) Aw[t] = A[t];
+    for (int t = tid; t < p; t += blockDim.x) yw[t] = y[t];
+  }
+  __syncthreads();
+  *df_out = df;
+  __syncthreads();
+  return true;
+}
+
+// Single CTA: the set V of the accepted candidates, every wavelength's solve (cap_lam; with pre,
+// the first attempt's solves were done by k_capacitance_lam and are read from the control block),
+// the joint decision and the fallback to the best single candidate.  The p x p matrices live in
+// the workspace (p can reach 4k), or in sA for p <= kCapSmemP.
+__device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayout& L, char* ws,
+                                                 const uint8_t* state, const int32_t* idx, int32_t* status,
+                                                 cplx* sA = nullptr, bool pre = false) {
+  UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
+  int32_t* V = reinterpret_cast<int32_t*>(ws + L.V);
+  double* dchi = reinterpret_cast<double*>(ws + L.dchi);
+  __shared__ int s_nv, s_ncand, s_fail;
+  const int tid = threadIdx.x;
+
+  if (tid == 0) {
+    s_fail = 0;
+    s_ncand = 0;
+    s_nv = 0;
+    if (*status != GF_OK) {
+      s_fail = 1;
+    } else {
+      int nv = 0, nc = 0;
+      for (int c = 0; c < a.k; ++c) {
+        int32_t id = idx[c];
+        if (id < 0) break;
+        int m = cand_pixels(id, a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V + nv, dchi + nv, a.u.nz);
+        if (m == 0) continue;
+        nv += m;
+        ++nc;
+      }
+      s_nv = nv;
+      s_ncand = nc;
+      if (nv == 0) s_fail = 2;
+    }
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) {
+      ctl->skip = 1;
+      ctl->nv = 0;
+      ctl->ncand = 0;
+      ctl->joint_dfom = 0.0;
+    }
+    return;
+  }
+
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const int p = s_nv;
+    double total = 0.0;
+    bool singular = false;
+    for (int l = 0; l < a.u.nlam; ++l) {
+      double df = 0.0;
+      if (pre && attempt == 0) {                     // the per-wavelength kernel solved it
+        df = ctl->lam_df[l];
+        if (ctl->lam_bad[l]) { singular = true; break; }
+      } else if (!cap_lam(a, L, ws, l, p, V, dchi, sA, &df)) {
+        singular = true;
+        break;
+      }
+      total += df;
+    }
+    if (singular) {
+      if (tid == 0) {
+        *status = GF_ESINGULAR;
+        ctl->skip = 1;
+        ctl->nv = 0;
+        ctl->ncand = 0;
+        ctl->joint_dfom = 0.0;
+      }
+      return;
+    }
+    if (s_ncand > 1 && !(total > 0.0) && attempt == 0) {
+      // the joint set does not improve the FOM: apply the best candidate alone
+      __syncthreads();
+      if (tid == 0) {
+        int m = cand_pixels(idx[0], a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V, dchi, a.u.nz);
+        s_nv = m;
+        s_ncand = 1;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (tid == 0) {
+      ctl->skip = 0;
+      ctl->nv = s_nv;
+      ctl->ncand = s_ncand;
+      ctl->joint_dfom = total;
+    }
+    return;
+  }
+}
+
+// ----------------------------------------------------------------------------- panels
+// Column j: R[:, j] = A^{-1} G[V, j] (Eq. 14) and S[:, j] = D R[:, j]; row j of the rows held:
+// C0[j, :] = G[j, V].
+__device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L, char* ws, int want_S, int64_t vb = -1, int64_t vg = -1) {
+  // vb, vg: a virtual block index and count (a work item of a persistent kernel); -1: the grid's
+  const int64_t vb_ = vb < 0 ? (int64_t)blockIdx.x : vb, vg_ = vg < 0 ? (int64_t)gridDim.x : vg;
+  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
+  if (ctl->skip) return;
+  const int p = ctl->nv;
+  const int32_t* V = reinterpret_cast<const int32_t*>(ws + L.V);
+  const double* dchi = reinterpret_cast<const double*>(ws + L.dchi);
+  const int64_t n = L.n;
+  for (int l = 0; l < a.nlam; ++l) {
+    const UpdLam& U = a.lam[l];
+    const cplx* A = reinterpret_cast<const cplx*>(ws + L.lu + l * L.lu_s);
+    const int32_t* piv = reinterpret_cast<const int32_t*>(ws + L.piv + l * L.piv_s);
+    cplx* C0 = reinterpret_cast<cplx*>(ws + L.C0 + l * L.panel_s);
+    cplx* S = reinterpret_cast<cplx*>(ws + L.S + l * L.panel_s);
+    const int64_t jend = U.rows > n ? U.rows : n;
+    for (int64_t j = vb_ * (int64_t)blockDim.x + threadIdx.x; j < jend;
+         j += (int64_t)vg_ * blockDim.x) {
+      if (j < U.rows)
+        for (int u = 0; u < p; ++u) C0[j * L.pmax + u] = ldG(U.G, a.dtype, U.ldg, j, V[u]);
+      if (!want_S || j >= n) continue;
+      if (p <= kMaxPixelsPerCand) {
+        cplx x[kMaxPixelsPerCand];
+#pragma unroll
+        for (int u = 0; u < kMaxPixelsPerCand; ++u)
+          if (u < p) x[u] = U.vrows ? ldG(U.vrows, a.dtype, U.ldv, u, j) : ldG(U.G, a.dtype, U.ldg, V[u], j);
+        // P A = L U with full-row interchanges: apply all interchanges in order first,
+        // then the unit-lower solve, then the upper solve
+#pragma unroll
+        for (int c = 0; c < kMaxPixelsPerCand; ++c) {
+          if (c < p) {
+            int r = piv[c];
+#pragma unroll
+            for (int rr = 0; rr < kMaxPixelsPerCand; ++rr)
+              if (rr == r && rr != c) { cplx t = x[c]; x[c] = x[rr]; x[rr] = t; }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < kMaxPixelsPerCand; ++c) {
+          if (c < p) {
+#pragma unroll
+            for (int rr = c + 1; rr < kMaxPixelsPerCand; ++rr)
+              if (rr < p) x[rr] = x[rr] - A[rr * p + c] * x[c];
+          }
+        }
+#pragma unroll
+        for (int c = kMaxPixelsPerCand - 1; c >= 0; --c) {
+          if (c < p) {
+            cplx acc = x[c];
+#pragma unroll
+            for (int v = c + 1; v < kMaxPixelsPerCand; ++v)
+              if (v < p) acc = acc - A[c * p + v] * x[v];
+            x[c] = cdiv(acc, A[c * p + c]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kMaxPixelsPerCand; ++u)
+          if (u < p) S[(int64_t)u * n + j] = dchi[u] * x[u];
+      } else {
+        // general p: the column of R lives in S itself (row stride n)
+        for (int u = 0; u < p; ++u)
+          S[(int64_t)u * n + j] = U.vrows ? ldG(U.vrows, a.dtype, U.ldv, u, j) : ldG(U.G, a.dtype, U.ldg, V[u], j);
+        for (int c = 0; c < p; ++c) {
+          int r = piv[c];
+          if (r != c) {
+            cplx t = S[(int64_t)c * n + j];
+            S[(int64_t)c * n + j] = S[(int64_t)r * n + j];
+            S[(int64_t)r * n + j] = t;
+          }
+        }
+        for (int c = 0; c < p; ++c) {
+          cplx xc = S[(int64_t)c * n + j];
+          for (int rr = c + 1; rr < p; ++rr)
+            S[(int64_t)rr * n + j] = S[(int64_t)rr * n + j] - A[rr * p + c] * xc;
+        }
+        for (int c = p - 1; c >= 0; --c) {
+          cplx acc = S[(int64_t)c * n + j];
+          for (int v = c + 1; v < p; ++v) acc = acc - A[c * p + v] * S[(int64_t)v * n + j];
+          S[(int64_t)c * n + j] = cdiv(acc, A[c * p + c]);
+        }
+        for (int u = 0; u < p; ++u) S[(int64_t)u * n + j] = dchi[u] * S[(int64_t)u * n + j];
+      }
+    }
+  }
+}
+
+// complex64 storage, rank p <= 4, FP32 arithmetic on the CUDA cores: the update is a pure
+// HBM stream (4p FP32 FMA per 16 bytes moved), so no tensor-core form is needed.  A tile is
+// 32 rows x 512 complex columns; each thread owns two adjacent columns (one 16-byte vector per
+// row) and keeps their S entries in registers; the tile's C0 rows are staged in shared memory.
+// G is touched once per step, so its loads and stores carry the streaming (evict-first) hint
+// and leave L2 to the panels.  Three CTAs fit an SM; launches use a multiple of that.
+constexpr int kF32Threads = 256;
+constexpr int kF32Rows = 32;
+constexpr int kF32Cols = 2 * kF32Threads;
+
+template <int R = kF32Rows>
+__device__ __forceinline__ void c64_fp32_tile(float2* __restrict__ G, int64_t ldg, int64_t n, int64_t m, int pmax, int p,
+                                              const cplx* C0, const cplx* S,
+                                              int64_t rt, int64_t ct, float2 (*sC)[kC64Fp32MaxP]) {
+  // R: rows of the tile (the tuned batch kernel instantiates 16, 32 and 64)
+  const int64_t i0 = rt * R;
+  const int64_t j = ct * kF32Cols + 2 * threadIdx.x;
+  __syncthreads();                                   // previous tile done with sC
+  for (int t = threadIdx.x; t < R * kC64Fp32MaxP; t += kF32Threads) {
+    const int r = t / kC64Fp32MaxP, u = t % kC64Fp32MaxP;
+    const int64_t i = i0 + r;
+    cplx c = (i < m && u < p) ? C0[i * pmax + u] : mk(0.0, 0.0);
+    sC[r][u] = make_float2((float)c.re, (float)c.im);
+  }
+  __syncthreads();
+  if (j >= n) return;
+  const bool two = j + 1 < n;
+  float2 s0[kC64Fp32MaxP], s1[kC64Fp32MaxP];
+#pragma unroll
+  for (int u = 0; u < kC64Fp32MaxP; ++u) {
+    cplx a = u < p ? S[(int64_t)u * n + j] : mk(0.0, 0.0);
+    cplx b = (u < p && two) ? S[(int64_t)u * n + j + 1] : mk(0.0, 0.0);
+    s0[u] = make_float2((float)a.re, (float)a.im);
+    s1[u] = make_float2((float)b.re, (float)b.im);
+  }
+  const int rows = (int)(m - i0 < R ? m - i0 : R);
+  constexpr int U = 8;
+  for (int r0 = 0; r0 < rows; r0 += U) {
+    float4 g[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q)
+      if (r0 + q < rows) g[q] = __ldcs(reinterpret_cast<const float4*>(G + (i0 + r0 + q) * ldg + j));
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (r0 + q < rows) {
+        float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+#pragma unroll
+        for (int u = 0; u < kC64Fp32MaxP; ++u) {
+          const float2 c = sC[r0 + q][u];
+          ar = fmaf(c.x, s0[u].x, fmaf(-c.y, s0[u].y, ar));
+          ai = fmaf(c.x, s0[u].y, fmaf(c.y, s0[u].x, ai));
+          br = fmaf(c.x, s1[u].x, fmaf(-c.y, s1[u].y, br));
+          bi = fmaf(c.x, s1[u].y, fmaf(c.y, s1[u].x, bi));
+        }
+        float4 v = g[q];
+        v.x += ar;
+        v.y += ai;
+        if (two) {
+          v.z += br;
+          v.w += bi;
+        }
+        __stcs(reinterpret_cast<float4*>(G + (i0 + r0 + q) * ldg + j), v);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- field, state, FOM
+__device__ __forceinline__ void finish_body(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* __restrict__ state,
+                                            double* __restrict__ fom_out, int32_t* __restrict__ applied, int64_t vb = -1, int64_t vg = -1) {
+  // vb, vg: a virtual block index and count (a work item of a persistent kernel); -1: the grid's
+  const int64_t vb_ = vb < 0 ? (int64_t)blockIdx.x : vb, vg_ = vg < 0 ? (int64_t)gridDim.x : vg;
+  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
+  const int64_t n = L.n;
+  const int64_t N = n - 1;
+  const bool skip = ctl->skip != 0;
+  const int p = skip ? 0 : ctl->nv;
+  const int32_t* V = reinterpret_cast<const int32_t*>(ws + L.V);
+  (void)N;
+  for (int64_t i = vb_ * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)vg_ * blockDim.x) {
+    // the first monitor unknown's thread also updates the others, so that it can sum the FOM
+    if (i > a.mrow && i < a.mrow + a.mcount) continue;
+    const int reps = i == a.mrow ? a.mcount : 1;
+    double f = 0.0;
+    for (int q = 0; q < reps; ++q) {
+      const int64_t ii = i + q;
+      for (int l = 0; l < a.nlam; ++l) {
+        const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + l * L.panel_s);
+        const cplx* yd = reinterpret_cast<const cplx*>(ws + L.yd + l * L.yd_s);
+        const UpdLam& U = a.lam[l];
+        cplx e = U.E[ii];
+        if (U.vrows)        // G[ii, V[u]] read as G[V[u], ii] from the row panel (reciprocity)
+          for (int u = 0; u < p; ++u) e = cfma(ldG(U.vrows, a.dtype, U.ldv, u, ii), yd[u], e);
+        else
+          for (int u = 0; u < p; ++u) e = cfma(C0[ii * L.pmax + u], yd[u], e);
+        if (p > 0) a.lam[l].E[ii] = e;
+        f += abs2(e);
+      }
+    }
+    if (i == a.mrow) {
+      *fom_out = f;
+      if (applied) *applied = skip ? 0 : ctl->ncand;
+    }
+  }
+  if (vb_ == 0) {   // one flip per point (the unknowns of a point are consecutive in V)
+    for (int t = threadIdx.x; t < p; t += blockDim.x)
+      if (V[t] % a.ncomp == 0) state[V[t] / a.ncomp] ^= 1;
+  }
+}
+
+}  // namespace gf

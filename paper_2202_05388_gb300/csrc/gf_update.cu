@@ -11,440 +11,14 @@
 
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "gf_internal.cuh"
+#include "gf_stage_bodies.cuh"
 
 namespace gf {
 
 // ----------------------------------------------------------------------------- capacitance
-struct CapArgs {
-  UpdArgs u;
-  int kind, dir_mask, k;
-  int pmax;
-};
-
-// Blocked right-looking LU with partial pivoting of the row-major p x p complex matrix A (global
-// memory), for p <= kLuMaxBlocked, by the whole CTA.  Panels of kLuNB columns are factored in
-// shared memory (pivot = largest modulus, lowest row on ties, as in the unblocked form); their row
-// interchanges are then applied to the rest of the rows, U12 = L11^{-1} A12 is solved column by
-// column and the trailing matrix receives the rank-kLuNB update -- every element independently,
-// so the global-memory traffic is parallel instead of a chain of dependent accesses.  The result
-// (L below the diagonal with unit diagonal, U on and above it, piv[c] = row exchanged with row c
-// at step c) is the unblocked factorisation's.  Returns false (in every thread) when a pivot is
-// zero or below thresh.
-constexpr int kLuNB = 8;
-constexpr int kLuMaxBlocked = 256;
-constexpr int kCapSmemP = 64;          // capacitance systems up to this size in shared memory (64 KB)
-constexpr double kC128SmallWork = 2.5e6;   // n^2 p_max below which the FP64 FMA update is faster
-
-// sP: shared memory for kLuMaxBlocked x kLuNB entries (the panel, row-major [row][j])
-__device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ piv, double thresh, cplx* sP) {
-  __shared__ int s_pv[kLuNB];
-  __shared__ int s_bad2, s_pr;
-  __shared__ cplx s_inv;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
-  if (tid == 0) s_bad2 = 0;
-  __syncthreads();
-  for (int c0 = 0; c0 < p; c0 += kLuNB) {
-    const int nb = p - c0 < kLuNB ? p - c0 : kLuNB;
-    const int m = p - c0;
-    for (int t = tid; t < m * nb; t += nt) {
-      const int r = t / nb, j = t - r * nb;
-      sP[r * kLuNB + j] = A[(int64_t)(c0 + r) * p + c0 + j];
-    }
-    __syncthreads();
-    // ---- panel factorisation in shared memory.  The pivot search is one warp's: the largest
-    // |a|^2 (the order of the moduli), lowest row on ties; its lane 0 also forms 1 / pivot, so
-    // each row's multiplier is a product instead of a division.
-    for (int j = 0; j < nb; ++j) {
-      if (wid == 0) {
-        double bv = -1.0;
-        int br = 0x7fffffff;
-        for (int r = j + lane; r < m; r += 32) {
-          const double v = abs2(sP[r * kLuNB + j]);
-          if (v > bv) { bv = v; br = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-          const int orr = __shfl_down_sync(0xffffffffu, br, o);
-          if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-        }
-        if (lane == 0) {
-          if (!(bv >= thresh * thresh) || !(bv > 0.0)) {
-            s_bad2 = 1;
-          } else {
-            const cplx pv = sP[br * kLuNB + j];
-            const double d = 1.0 / bv;
-            s_inv = mk(pv.re * d, -pv.im * d);
-          }
-          s_pr = br;
-          s_pv[j] = c0 + br;
-          piv[c0 + j] = c0 + br;
-        }
-      }
-      __syncthreads();
-      if (s_bad2) return false;
-      const int pr = s_pr;
-      if (pr != j && tid < nb) {
-        const cplx t0 = sP[j * kLuNB + tid];
-        sP[j * kLuNB + tid] = sP[pr * kLuNB + tid];
-        sP[pr * kLuNB + tid] = t0;
-      }
-      __syncthreads();
-      const cplx inv = s_inv;
-      for (int r = j + 1 + tid; r < m; r += nt) {
-        const cplx f = sP[r * kLuNB + j] * inv;
-        sP[r * kLuNB + j] = f;
-        for (int k = j + 1; k < nb; ++k) sP[r * kLuNB + k] = sP[r * kLuNB + k] - f * sP[j * kLuNB + k];
-      }
-      __syncthreads();
-    }
-    for (int t = tid; t < m * nb; t += nt) {
-      const int r = t / nb, j = t - r * nb;
-      A[(int64_t)(c0 + r) * p + c0 + j] = sP[r * kLuNB + j];
-    }
-    // ---- the panel's interchanges on the columns outside it (one thread per column)
-    for (int v = tid; v < p; v += nt) {
-      if (v >= c0 && v < c0 + nb) continue;
-      for (int j = 0; j < nb; ++j) {
-        const int r = s_pv[j];
-        if (r != c0 + j) {
-          const cplx t0 = A[(int64_t)(c0 + j) * p + v];
-          A[(int64_t)(c0 + j) * p + v] = A[(int64_t)r * p + v];
-          A[(int64_t)r * p + v] = t0;
-        }
-      }
-    }
-    __syncthreads();
-    const int w = p - c0 - nb;                   // trailing width
-    if (w > 0) {
-      // ---- U12 = L11^{-1} A12 (unit lower, one thread per column); for p <= kLuMaxBlocked / 2
-      // the block is also kept in the free half of the panel buffer for the trailing update
-      cplx* sU = p <= kLuMaxBlocked / 2 ? sP + (kLuMaxBlocked / 2) * kLuNB : nullptr;
-      for (int v = tid; v < w; v += nt) {
-        cplx x[kLuNB];
-#pragma unroll
-        for (int j = 0; j < kLuNB; ++j)
-          if (j < nb) x[j] = A[(int64_t)(c0 + j) * p + c0 + nb + v];
-#pragma unroll
-        for (int j = 1; j < kLuNB; ++j)
-          if (j < nb)
-#pragma unroll
-            for (int i = 0; i < kLuNB; ++i)
-              if (i < j) x[j] = x[j] - sP[j * kLuNB + i] * x[i];
-#pragma unroll
-        for (int j = 1; j < kLuNB; ++j)
-          if (j < nb) A[(int64_t)(c0 + j) * p + c0 + nb + v] = x[j];
-        if (sU)
-#pragma unroll
-          for (int j = 0; j < kLuNB; ++j)
-            if (j < nb) sU[j * w + v] = x[j];
-      }
-      __syncthreads();
-      // ---- A22 -= L21 U12, every element independently (coalesced along the row)
-      for (int e = tid; e < w * w; e += nt) {
-        const int i = e / w, v = e - i * w;
-        const int64_t o = (int64_t)(c0 + nb + i) * p + c0 + nb + v;
-        cplx acc = A[o];
-#pragma unroll
-        for (int j = 0; j < kLuNB; ++j)
-          if (j < nb)
-            acc = acc - sP[(nb + i) * kLuNB + j] * (sU ? sU[j * w + v] : A[(int64_t)(c0 + j) * p + c0 + nb + v]);
-        A[o] = acc;
-      }
-    }
-    __syncthreads();
-  }
-  return true;
-}
-
-// A = I - G_VV D (row-major p x p, Eq. 9) and y = E_V for one wavelength; returns the pivot
-// threshold kSingularRel ||A||_inf (every thread).
-__device__ double cap_build(const CapArgs& a, const UpdLam& U, int p, const int32_t* __restrict__ V,
-                            const double* __restrict__ dchi, cplx* A, cplx* y) {
-  __shared__ double s_red[32];
-  const int tid = threadIdx.x;
-  for (int t = tid; t < p * p; t += blockDim.x) {
-    int r = t / p, c = t % p;
-    cplx g = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, r, V[c]) : ldG(U.G, a.u.dtype, U.ldg, V[r], V[c]);
-    cplx e = mk(r == c ? 1.0 : 0.0, 0.0);
-    A[t] = e - dchi[c] * g;
-  }
-  for (int t = tid; t < p; t += blockDim.x) y[t] = U.E[V[t]];
-  __syncthreads();
-  // ||A||_inf
-  double rs = 0.0;
-  for (int r = tid; r < p; r += blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < p; ++c) s += cabs1(A[r * p + c]);
-    rs = fmax(rs, s);
-  }
-  for (int o = 16; o > 0; o >>= 1) rs = fmax(rs, __shfl_down_sync(0xffffffffu, rs, o));
-  if ((tid & 31) == 0) s_red[tid >> 5] = rs;
-  __syncthreads();
-  if (tid == 0) {
-    double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_red[w]);
-    s_red[0] = m;
-  }
-  __syncthreads();
-  const double thresh = kSingularRel * s_red[0];
-  __syncthreads();
-  return thresh;
-}
-
-// With the factors of A (L below the diagonal, U on and above, piv), y <- A^{-1} y after y was
-// permuted and reduced by L (y_is_lower: the unit-lower solve is still to do), the dFOM of Eq. 4
-// at the monitor's unknowns (Eq. 1) into the return value (every thread), and y <- D y.
-__device__ double cap_tail(const CapArgs& a, const UpdLam& U, int p, const int32_t* __restrict__ V,
-                           const double* __restrict__ dchi, const cplx* A, const int32_t* __restrict__ piv, cplx* y,
-                           bool lower_done) {
-  __shared__ double s_red[32];
-  __shared__ double s_bv[32];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (int)(blockDim.x >> 5);
-  if (!lower_done) {
-    // y = P E_V, then the unit-lower solve (column-oriented: one synchronisation per column)
-    if (tid == 0)
-      for (int c = 0; c < p; ++c) {
-        const int r = piv[c];
-        if (r != c) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
-      }
-    __syncthreads();
-    for (int c = 0; c < p; ++c) {
-      const cplx yc = y[c];
-      for (int r = c + 1 + tid; r < p; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
-      __syncthreads();
-    }
-  }
-  // upper solve for y (column-oriented: one synchronisation per column)
-  for (int c = p - 1; c >= 0; --c) {
-    if (tid == 0) y[c] = cdiv(y[c], A[c * p + c]);
-    __syncthreads();
-    const cplx yc = y[c];
-    for (int r = tid; r < c; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
-    __syncthreads();
-  }
-  // Eq. 4 at the monitor's unknowns (Eq. 1): the gathers of the monitor row are spread over
-  // the block and reduced
-  double df = 0.0;
-  for (int mc = 0; mc < a.u.mcount; ++mc) {
-    const int64_t m = a.u.mrow + mc;
-    cplx part = mk(0.0, 0.0);
-    // G[m, V[u]]; from the row panel as G[V[u], m] (reciprocity)
-    for (int u = tid; u < p; u += blockDim.x) {
-      const cplx gm = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, u, m) : ldG(U.G, a.u.dtype, U.ldg, m, V[u]);
-      part = part + dchi[u] * (gm * y[u]);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      part.re += __shfl_down_sync(0xffffffffu, part.re, o);
-      part.im += __shfl_down_sync(0xffffffffu, part.im, o);
-    }
-    if (lane == 0) { s_bv[wid] = part.re; s_red[wid] = part.im; }
-    __syncthreads();
-    if (tid == 0) {
-      cplx dE = mk(0.0, 0.0);
-      for (int w = 0; w < nw; ++w) dE = dE + mk(s_bv[w], s_red[w]);
-      const cplx EN = U.E[m];
-      df += abs2(EN + dE) - abs2(EN);
-    }
-    __syncthreads();
-  }
-  if (tid == 0) s_red[0] = df;
-  for (int u = tid; u < p; u += blockDim.x) y[u] = dchi[u] * y[u];      // D y for the field update
-  __syncthreads();
-  df = s_red[0];
-  __syncthreads();
-  return df;
-}
-
-// One wavelength of the capacitance solve for the set V (p pixels, contrasts dchi): A = I - G_VV D
-// (Eq. 9), its LU with partial pivoting, y = A^{-1} E_V and the dFOM of Eq. 4 at the monitor into
-// *df (every thread); the factors, pivots and D y go to the wavelength's workspace slots.  With sA
-// (shared memory for kCapSmemP^2 + kCapSmemP entries) a system of p <= kCapSmemP and its
-// right-hand side are built, factorised and solved there and copied to the workspace once.
-// Returns false (in every thread) when A is singular.
-__device__ bool cap_lam(const CapArgs& a, const WsLayout& L, char* ws, int l, int p, const int32_t* __restrict__ V,
-                        const double* __restrict__ dchi, cplx* sA, double* df_out) {
-  const int tid = threadIdx.x;
-  const UpdLam& U = a.u.lam[l];
-  cplx* Aw = reinterpret_cast<cplx*>(ws + L.lu + l * L.lu_s);
-  const bool in_smem = sA && p <= kCapSmemP;
-  cplx* A = in_smem ? sA : Aw;
-  int32_t* piv = reinterpret_cast<int32_t*>(ws + L.piv + l * L.piv_s);
-  cplx* yw = reinterpret_cast<cplx*>(ws + L.yd + l * L.yd_s);
-  cplx* y = in_smem ? sA + kCapSmemP * kCapSmemP : yw;
-  const double thresh = cap_build(a, U, p, V, dchi, A, y);
-  // LU with partial pivoting (row-major, in place; L below the diagonal, unit diagonal).
-  __shared__ int s_piv;
-  __shared__ int s_bad;
-  __shared__ double s_bv[32];
-  __shared__ int s_br[32];
-  __shared__ cplx s_f[kLuMaxBlocked * kLuNB];   // blocked: the panel; unblocked: multipliers
-  if (tid == 0) s_bad = 0;
-  const int nw = (int)(blockDim.x >> 5), lane = tid & 31, wid = tid >> 5;
-  bool lower_done = false;
-  if (p <= kLuMaxBlocked) {
-    if (!lu_blocked(A, p, piv, thresh, s_f)) return false;
-  } else {
-    // unblocked form for very large joint sets (p > 256): pivot search across the block,
-    // multipliers per row, trailing update with a warp per row and lanes along the columns; y
-    // is permuted and reduced alongside
-    lower_done = true;
-    for (int c = 0; c < p; ++c) {
-      double bv = -1.0;
-      int br = 0x7fffffff;
-      for (int rr = c + tid; rr < p; rr += blockDim.x) {
-        const double m = cabs1(A[rr * p + c]);
-        if (m > bv) { bv = m; br = rr; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-        const int orr = __shfl_down_sync(0xffffffffu, br, o);
-        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-      }
-      if (lane == 0) { s_bv[wid] = bv; s_br[wid] = br; }
-      __syncthreads();
-      if (tid == 0) {
-        double b = s_bv[0];
-        int r = s_br[0];
-        for (int w = 1; w < nw; ++w)
-          if (s_bv[w] > b || (s_bv[w] == b && s_br[w] < r)) { b = s_bv[w]; r = s_br[w]; }
-        if (!(b >= thresh) || !(b > 0.0)) s_bad = 1;
-        s_piv = r;
-        piv[c] = r;
-      }
-      __syncthreads();
-      const int r = s_piv;
-      if (s_bad) break;
-      if (r != c) {
-        for (int v = tid; v < p; v += blockDim.x) {
-          cplx t0 = A[c * p + v];
-          A[c * p + v] = A[r * p + v];
-          A[r * p + v] = t0;
-        }
-        if (tid == 0) { cplx t0 = y[c]; y[c] = y[r]; y[r] = t0; }
-      }
-      __syncthreads();
-      const cplx pv = A[c * p + c];
-      const cplx yc = y[c];
-      for (int rr = c + 1 + tid; rr < p; rr += blockDim.x) {
-        const cplx f = cdiv(A[rr * p + c], pv);
-        s_f[rr] = f;
-        A[rr * p + c] = f;
-        y[rr] = y[rr] - f * yc;
-      }
-      __syncthreads();
-      for (int rr = c + 1 + wid; rr < p; rr += nw) {
-        const cplx f = s_f[rr];
-        for (int v = c + 1 + lane; v < p; v += 32) A[rr * p + v] = A[rr * p + v] - f * A[c * p + v];
-      }
-      __syncthreads();
-    }
-    __syncthreads();
-    if (s_bad) return false;
-  }
-  const double df = cap_tail(a, U, p, V, dchi, A, piv, y, lower_done);
-  if (in_smem) {                                 // the factors and D y for the later kernels
-    for (int t = tid; t < p * p; t += blockDim.x) Aw[t] = A[t];
-    for (int t = tid; t < p; t += blockDim.x) yw[t] = y[t];
-  }
-  __syncthreads();
-  *df_out = df;
-  __syncthreads();
-  return true;
-}
-
-// Single CTA: the set V of the accepted candidates, every wavelength's solve (cap_lam; with pre,
-// the first attempt's solves were done by k_capacitance_lam and are read from the control block),
-// the joint decision and the fallback to the best single candidate.  The p x p matrices live in
-// the workspace (p can reach 4k), or in sA for p <= kCapSmemP.
-__device__ __forceinline__ void capacitance_body(const CapArgs& a, const WsLayout& L, char* ws,
-                                                 const uint8_t* __restrict__ state,
-                                                 const int32_t* __restrict__ idx, int32_t* status,
-                                                 cplx* sA = nullptr, bool pre = false) {
-  UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
-  int32_t* V = reinterpret_cast<int32_t*>(ws + L.V);
-  double* dchi = reinterpret_cast<double*>(ws + L.dchi);
-  __shared__ int s_nv, s_ncand, s_fail;
-  const int tid = threadIdx.x;
-
-  if (tid == 0) {
-    s_fail = 0;
-    s_ncand = 0;
-    s_nv = 0;
-    if (*status != GF_OK) {
-      s_fail = 1;
-    } else {
-      int nv = 0, nc = 0;
-      for (int c = 0; c < a.k; ++c) {
-        int32_t id = idx[c];
-        if (id < 0) break;
-        int m = cand_pixels(id, a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V + nv, dchi + nv, a.u.nz);
-        if (m == 0) continue;
-        nv += m;
-        ++nc;
-      }
-      s_nv = nv;
-      s_ncand = nc;
-      if (nv == 0) s_fail = 2;
-    }
-  }
-  __syncthreads();
-  if (s_fail) {
-    if (tid == 0) {
-      ctl->skip = 1;
-      ctl->nv = 0;
-      ctl->ncand = 0;
-      ctl->joint_dfom = 0.0;
-    }
-    return;
-  }
-
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    const int p = s_nv;
-    double total = 0.0;
-    bool singular = false;
-    for (int l = 0; l < a.u.nlam; ++l) {
-      double df = 0.0;
-      if (pre && attempt == 0) {                     // the per-wavelength kernel solved it
-        df = ctl->lam_df[l];
-        if (ctl->lam_bad[l]) { singular = true; break; }
-      } else if (!cap_lam(a, L, ws, l, p, V, dchi, sA, &df)) {
-        singular = true;
-        break;
-      }
-      total += df;
-    }
-    if (singular) {
-      if (tid == 0) {
-        *status = GF_ESINGULAR;
-        ctl->skip = 1;
-        ctl->nv = 0;
-        ctl->ncand = 0;
-        ctl->joint_dfom = 0.0;
-      }
-      return;
-    }
-    if (s_ncand > 1 && !(total > 0.0) && attempt == 0) {
-      // the joint set does not improve the FOM: apply the best candidate alone
-      __syncthreads();
-      if (tid == 0) {
-        int m = cand_pixels(idx[0], a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V, dchi, a.u.nz);
-        s_nv = m;
-        s_ncand = 1;
-      }
-      __syncthreads();
-      continue;
-    }
-    if (tid == 0) {
-      ctl->skip = 0;
-      ctl->nv = s_nv;
-      ctl->ncand = s_ncand;
-      ctl->joint_dfom = total;
-    }
-    return;
-  }
-}
-
 __global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __restrict__ state,
                               const int32_t* __restrict__ idx, int32_t* status, int pre) {
   extern __shared__ __align__(16) unsigned char cap_smem[];
@@ -484,277 +58,279 @@ __global__ void k_capacitance_lam(CapArgs a, WsLayout L, char* ws, const uint8_t
   }
 }
 
-// ---- one large system (a single wavelength with p_max > kCapSmemP) factorised by many CTAs.
-// One CTA per solve is bound by that SM's FP64 pipe (p = 128: 1.9 ms).  Here the blocked
-// right-looking LU of lu_blocked runs as a sequence of launches, with the same operations in the
-// same order (so the same factors): per 8-column panel, one CTA factors the panel, applies its row
-// interchanges to the other columns and solves U12 = L11^{-1} A12; then a grid of 16 x 16 tiles
-// applies A22 -= L21 U12.  No launch waits on another CTA: the stream orders them.
-// k_cap_lu_prep forms V, A and y = E_V (and the pivot threshold); k_cap_lu_finish solves for y
-// and writes the dFOM and the singular flag where k_capacitance's first attempt reads them.
-constexpr int kLuTile = 16;
+// ---- one large system (a single wavelength with p_max > kCapSmemP), held in the shared memory of
+// one 8-CTA cluster (distributed shared memory).  One CTA per solve is bound by that SM's FP64
+// pipe (p = 128: 1.9 ms).  A = I - G_VV D is built, factorised with partial pivoting and solved
+// without leaving the cluster: physical row r (with y as its last entry) lives in CTA r % kCluN.  Row interchanges
+// are kept as a permutation shared by every CTA (logical position i holds physical row phys[i]),
+// so a pivot row is only read by the others, never moved, and one cluster barrier per column
+// suffices: after it every CTA reads the candidates of the column (double-buffered slots), takes
+// the same pivot (largest modulus, lowest position on ties), copies the pivot row from its owner
+// and eliminates its own rows.  Every element sees the same operations in the same order as the
+// blocked factorisation of lu_blocked (the multiplier a_rj (conj(pv) / |pv|^2), then
+// a_rk - l u_jk column after column), and the upper solve runs in blocks of kLuNB rows from the
+// bottom as cap_tail does, so the factors, pivots, y and the dFOM are the bits one CTA computes.
+// Outputs: V, dchi, the factors (row-major, logical order), pivots and D y in the workspace, the
+// dFOM and singular flag in the control block, where k_capacitance's first attempt reads them.
+constexpr int kCluN = 8;
+constexpr int kCluRows = kLuMaxBlocked / kCluN;         // physical rows per CTA at most
+__host__ __device__ constexpr size_t cap_cluster_smem(int pmax) {
+  // rows (R x (pmax + 1)) | pivot row (pmax + 1) | block of the upper solve (kLuNB x kLuNB + kLuNB)
+  // | final y (pmax) | dchi (pmax) | phys, pos, V (pmax each)
+  return sizeof(cplx) * ((size_t)((pmax + kCluN - 1) / kCluN) * (pmax + 1) + (pmax + 1) + kLuNB * kLuNB + kLuNB +
+                         pmax) +
+         sizeof(double) * (size_t)pmax + sizeof(int32_t) * 3 * (size_t)pmax;
+}
 
-__global__ void k_cap_lu_prep(CapArgs a, WsLayout L, char* ws, const uint8_t* __restrict__ state,
-                              const int32_t* __restrict__ idx, const int32_t* __restrict__ status) {
-  __shared__ int s_nv;
+__global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
+    k_cap_cluster(CapArgs a, WsLayout L, char* ws, const uint8_t* state, const int32_t* idx, const int32_t* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char clu_smem[];
+  const int pm = L.pmax;
+  const int Rm = (pm + kCluN - 1) / kCluN;
+  const int W = pm + 1;                                   // row stride: p columns of A, then y
+  cplx* rows = reinterpret_cast<cplx*>(clu_smem);
+  cplx* prow = rows + (size_t)Rm * W;
+  cplx* sU = prow + W;                                    // kLuNB x kLuNB block of U, then its y
+  cplx* yfin = sU + kLuNB * kLuNB + kLuNB;
+  double* sD = reinterpret_cast<double*>(yfin + pm);
+  int32_t* phys = reinterpret_cast<int32_t*>(sD + pm);
+  int32_t* pos = phys + pm;
+  int32_t* sV = pos + pm;
+  __shared__ double s_cv[2];                              // candidates: value, position (as double)
+  __shared__ int s_cr[2];
+  __shared__ double s_wv[8];
+  __shared__ int s_wr[8];
+  __shared__ double s_thr, s_rmax, s_d;
+  __shared__ int s_nv, s_pr, s_bad;
+  __shared__ cplx s_inv;
+  __shared__ double s_red[32], s_bv[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (int)(blockDim.x >> 5);
+  const int rank = (int)cl.block_rank();
+  const UpdLam& U = a.u.lam[0];
   UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
-  int32_t* V = reinterpret_cast<int32_t*>(ws + L.V);
-  double* dchi = reinterpret_cast<double*>(ws + L.dchi);
-  if (threadIdx.x == 0) {
+
+  if (tid == 0) {
     int nv = 0;
     if (*status == GF_OK)
       for (int c = 0; c < a.k; ++c) {
         const int32_t id = idx[c];
         if (id < 0) break;
-        nv += cand_pixels(id, a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, V + nv, dchi + nv, a.u.nz);
+        nv += cand_pixels(id, a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, sV + nv, sD + nv, a.u.nz);
       }
     s_nv = nv;
+    s_bad = 0;
   }
   __syncthreads();
-  const int p = s_nv;
-  double thresh = 0.0;
-  if (p > 0)
-    thresh = cap_build(a, a.u.lam[0], p, V, dchi, reinterpret_cast<cplx*>(ws + L.lu), reinterpret_cast<cplx*>(ws + L.yd));
-  if (threadIdx.x == 0) {
-    ctl->lu_p = p;
-    ctl->lu_bad = 0;
-    ctl->lu_thresh = thresh;
+  const int p = s_nv;                                     // the same in every CTA
+  if (rank == 0) {
+    int32_t* V = reinterpret_cast<int32_t*>(ws + L.V);
+    double* dchi = reinterpret_cast<double*>(ws + L.dchi);
+    for (int t = tid; t < p; t += blockDim.x) {
+      V[t] = sV[t];
+      dchi[t] = sD[t];
+    }
   }
-}
+  const int R = p > rank ? (p - rank + kCluN - 1) / kCluN : 0;    // physical rows rank + kCluN lr
+  // A = I - G_VV D and y = E_V for the CTA's rows; the row sums |A|_1 a warp per row
+  for (int t = tid; t < R * p; t += blockDim.x) {
+    const int lr = t / p, c = t - lr * p, r = rank + kCluN * lr;
+    const cplx g = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, r, sV[c]) : ldG(U.G, a.u.dtype, U.ldg, sV[r], sV[c]);
+    rows[(size_t)lr * W + c] = mk(r == c ? 1.0 : 0.0, 0.0) - sD[c] * g;
+  }
+  for (int lr = tid; lr < R; lr += blockDim.x) rows[(size_t)lr * W + p] = U.E[sV[rank + kCluN * lr]];
+  for (int i = tid; i < p; i += blockDim.x) {
+    phys[i] = i;
+    pos[i] = i;
+  }
+  __syncthreads();
+  double rmax = 0.0;
+  for (int lr = wid; lr < R; lr += nw) {
+    double sum = 0.0;
+    for (int c = lane; c < p; c += 32) sum += cabs1(rows[(size_t)lr * W + c]);
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    rmax = fmax(rmax, sum);                               // lane 0 holds the row's sum
+  }
+  if (lane == 0) s_wv[wid] = rmax;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < nw; ++w) m = fmax(m, s_wv[w]);
+    s_rmax = m;
+  }
+  cl.sync();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int q = 0; q < kCluN; ++q) m = fmax(m, *cl.map_shared_rank(&s_rmax, q));
+    s_thr = kSingularRel * m;
+  }
+  __syncthreads();
+  const double thresh = s_thr;
 
-__global__ void k_lu_panel(WsLayout L, char* ws, int q) {
-  __shared__ cplx sP[kLuMaxBlocked * kLuNB];
-  __shared__ int s_pv[kLuNB];
-  __shared__ int s_pr;
-  __shared__ cplx s_inv;
-  UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
-  const int p = ctl->lu_p;
-  const int c0 = q * kLuNB;
-  if (p <= 0 || c0 >= p || ctl->lu_bad) return;
-  cplx* A = reinterpret_cast<cplx*>(ws + L.lu);
-  int32_t* piv = reinterpret_cast<int32_t*>(ws + L.piv);
-  const double thresh = ctl->lu_thresh;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
-  const int nb = p - c0 < kLuNB ? p - c0 : kLuNB;
-  const int m = p - c0;
-  for (int t = tid; t < m * nb; t += nt) {
-    const int r = t / nb, j = t - r * nb;
-    sP[r * kLuNB + j] = A[(int64_t)(c0 + r) * p + c0 + j];
-  }
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (wid == 0) {
+  // ---- factorisation, one column per cluster barrier
+  int j = 0;
+  for (; j < p; ++j) {
+    const int buf = j & 1;
+    // the CTA's best candidate of column j among the rows not yet pivots
+    {
       double bv = -1.0;
-      int br = 0x7fffffff;
-      for (int r = j + lane; r < m; r += 32) {
-        const double v = abs2(sP[r * kLuNB + j]);
-        if (v > bv) { bv = v; br = r; }
+      int bpos = 0x7fffffff;
+      for (int lr = tid; lr < R; lr += blockDim.x) {
+        const int ps = pos[rank + kCluN * lr];
+        if (ps < j) continue;
+        const double v = abs2(rows[(size_t)lr * W + j]);
+        if (v > bv || (v == bv && ps < bpos)) { bv = v; bpos = ps; }
       }
       for (int o = 16; o > 0; o >>= 1) {
         const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-        const int orr = __shfl_down_sync(0xffffffffu, br, o);
-        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+        const int op = __shfl_down_sync(0xffffffffu, bpos, o);
+        if (ov > bv || (ov == bv && op < bpos)) { bv = ov; bpos = op; }
       }
-      if (lane == 0) {
-        if (!(bv >= thresh * thresh) || !(bv > 0.0)) {
-          ctl->lu_bad = 1;
-          s_pr = -1;
-        } else {
-          const cplx pv = sP[br * kLuNB + j];
-          const double d = 1.0 / bv;
-          s_inv = mk(pv.re * d, -pv.im * d);
-          s_pr = br;
-        }
-        s_pv[j] = c0 + br;
-        piv[c0 + j] = c0 + br;
+      if (lane == 0) { s_wv[wid] = bv; s_wr[wid] = bpos; }
+      __syncthreads();
+      if (tid == 0) {
+        for (int w = 1; w < nw; ++w)
+          if (s_wv[w] > s_wv[0] || (s_wv[w] == s_wv[0] && s_wr[w] < s_wr[0])) { s_wv[0] = s_wv[w]; s_wr[0] = s_wr[w]; }
+        s_cv[buf] = s_wv[0];
+        s_cr[buf] = s_wr[0];
+      }
+    }
+    cl.sync();
+    if (tid == 0) {
+      double bv = -1.0;
+      int bpos = 0x7fffffff;
+      for (int q = 0; q < kCluN; ++q) {
+        const double v = *cl.map_shared_rank(&s_cv[buf], q);
+        const int ps = *cl.map_shared_rank(&s_cr[buf], q);
+        if (v > bv || (v == bv && ps < bpos)) { bv = v; bpos = ps; }
+      }
+      if (!(bv >= thresh * thresh) || !(bv > 0.0)) {
+        s_bad = 1;
+      } else {
+        s_pr = bpos;
+        s_d = 1.0 / bv;
+        if (rank == 0) reinterpret_cast<int32_t*>(ws + L.piv)[j] = bpos;
       }
     }
     __syncthreads();
+    if (s_bad) break;                                     // the same column in every CTA
     const int pr = s_pr;
-    if (pr < 0) return;
-    if (pr != j && tid < nb) {
-      const cplx t0 = sP[j * kLuNB + tid];
-      sP[j * kLuNB + tid] = sP[pr * kLuNB + tid];
-      sP[pr * kLuNB + tid] = t0;
+    const int rp = phys[pr];                              // the pivot's physical row
+    {
+      const cplx* src = cl.map_shared_rank(rows, rp % kCluN) + (size_t)(rp / kCluN) * W;
+      for (int k = j + tid; k < W; k += blockDim.x) prow[k] = src[k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const cplx pv = prow[j];
+      const double d = s_d;
+      s_inv = mk(pv.re * d, -pv.im * d);
+      const int rj = phys[j];                             // the interchange of positions j and pr
+      phys[j] = rp;
+      phys[pr] = rj;
+      pos[rp] = j;
+      pos[rj] = pr;
     }
     __syncthreads();
     const cplx inv = s_inv;
-    for (int r = j + 1 + tid; r < m; r += nt) {
-      const cplx f = sP[r * kLuNB + j] * inv;
-      sP[r * kLuNB + j] = f;
-      for (int k = j + 1; k < nb; ++k) sP[r * kLuNB + k] = sP[r * kLuNB + k] - f * sP[j * kLuNB + k];
+    for (int lr = tid; lr < R; lr += blockDim.x)
+      if (pos[rank + kCluN * lr] > j) rows[(size_t)lr * W + j] = rows[(size_t)lr * W + j] * inv;
+    __syncthreads();
+    const int wk = W - (j + 1);
+    for (int t = tid; t < R * wk; t += blockDim.x) {
+      const int lr = t / wk, k = j + 1 + (t - lr * wk);
+      if (pos[rank + kCluN * lr] > j) {
+        cplx* row = rows + (size_t)lr * W;
+        row[k] = row[k] - row[j] * prow[k];
+      }
     }
     __syncthreads();
   }
-  for (int t = tid; t < m * nb; t += nt) {
-    const int r = t / nb, j = t - r * nb;
-    A[(int64_t)(c0 + r) * p + c0 + j] = sP[r * kLuNB + j];
-  }
-  // the panel's interchanges on the columns outside it, then U12 (one thread per column)
-  for (int v = tid; v < p; v += nt) {
-    if (v >= c0 && v < c0 + nb) continue;
-    for (int j = 0; j < nb; ++j) {
-      const int r = s_pv[j];
-      if (r != c0 + j) {
-        const cplx t0 = A[(int64_t)(c0 + j) * p + v];
-        A[(int64_t)(c0 + j) * p + v] = A[(int64_t)r * p + v];
-        A[(int64_t)r * p + v] = t0;
+  const bool bad = s_bad != 0;
+  // ---- upper solve in blocks of kLuNB rows from the bottom (CTA 0 solves each block's triangle)
+  if (!bad) {
+    for (int b1 = p; b1 > 0; b1 -= kLuNB) {
+      const int b0 = b1 - kLuNB > 0 ? b1 - kLuNB : 0;
+      const int w = b1 - b0;
+      cl.sync();                                          // the block's y are final
+      if (rank == 0) {
+        for (int t = tid; t < w * (w + 1); t += blockDim.x) {
+          const int c = t / (w + 1), v = t - c * (w + 1);  // v = w: y
+          const int rc = phys[b0 + c];
+          const cplx* src = cl.map_shared_rank(rows, rc % kCluN) + (size_t)(rc / kCluN) * W;
+          if (v < w) sU[c * kLuNB + v] = src[b0 + v];
+          else sU[kLuNB * kLuNB + c] = src[p];
+        }
+        __syncthreads();
+        if (tid == 0) {
+          cplx* yb = sU + kLuNB * kLuNB;
+          for (int c = w - 1; c >= 0; --c) {
+            cplx acc = yb[c];
+            for (int v = c + 1; v < w; ++v) acc = acc - sU[c * kLuNB + v] * yb[v];
+            yb[c] = cdiv(acc, sU[c * kLuNB + c]);
+            yfin[b0 + c] = yb[c];
+          }
+        }
+      }
+      cl.sync();                                          // the block's solution is in CTA 0
+      {
+        const cplx* yb0 = cl.map_shared_rank(sU, 0) + kLuNB * kLuNB;
+        for (int lr = tid; lr < R; lr += blockDim.x) {
+          const int ps = pos[rank + kCluN * lr];
+          if (ps >= b0) continue;
+          cplx* row = rows + (size_t)lr * W;
+          cplx acc = row[p];
+          for (int v = 0; v < w; ++v) acc = acc - row[b0 + v] * yb0[v];
+          row[p] = acc;
+        }
       }
     }
-    if (v >= c0 + nb) {
-      cplx x[kLuNB];
-#pragma unroll
-      for (int j = 0; j < kLuNB; ++j)
-        if (j < nb) x[j] = A[(int64_t)(c0 + j) * p + v];
-#pragma unroll
-      for (int j = 1; j < kLuNB; ++j)
-        if (j < nb)
-#pragma unroll
-          for (int i = 0; i < kLuNB; ++i)
-            if (i < j) x[j] = x[j] - sP[j * kLuNB + i] * x[i];
-#pragma unroll
-      for (int j = 1; j < kLuNB; ++j)
-        if (j < nb) A[(int64_t)(c0 + j) * p + v] = x[j];
+  }
+  // ---- outputs: the factors in logical row order; CTA 0: dFOM (Eq. 4 at the monitor) and D y
+  if (!bad) {
+    cplx* A = reinterpret_cast<cplx*>(ws + L.lu);
+    for (int t = tid; t < R * p; t += blockDim.x) {
+      const int lr = t / p, c = t - lr * p;
+      A[(size_t)pos[rank + kCluN * lr] * p + c] = rows[(size_t)lr * W + c];
     }
   }
-}
-
-// A22 -= L21 U12 on one 16 x 16 tile of the trailing matrix of panel q (blockIdx: column tile, row
-// tile), each element with the panel's terms in order.
-__global__ void k_lu_trail(WsLayout L, char* ws, int q) {
-  __shared__ cplx sL[kLuTile][kLuNB];
-  __shared__ cplx sU[kLuNB][kLuTile];
-  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
-  const int p = ctl->lu_p;
-  const int c0 = q * kLuNB;
-  if (p <= 0 || c0 >= p || ctl->lu_bad) return;
-  const int nb = p - c0 < kLuNB ? p - c0 : kLuNB;
-  const int w = p - c0 - nb;
-  const int v0 = blockIdx.x * kLuTile, i0 = blockIdx.y * kLuTile;
-  if (v0 >= w || i0 >= w) return;
-  cplx* A = reinterpret_cast<cplx*>(ws + L.lu);
-  const int tid = threadIdx.x;
-  for (int t = tid; t < kLuTile * kLuNB; t += blockDim.x) {
-    const int r = t / kLuNB, j = t % kLuNB;
-    sL[r][j] = (i0 + r < w && j < nb) ? A[(int64_t)(c0 + nb + i0 + r) * p + c0 + j] : mk(0.0, 0.0);
-    const int jj = t / kLuTile, c = t % kLuTile;
-    sU[jj][c] = (v0 + c < w && jj < nb) ? A[(int64_t)(c0 + jj) * p + c0 + nb + v0 + c] : mk(0.0, 0.0);
+  if (rank == 0) {
+    double df = 0.0;
+    if (!bad) {
+      for (int mc = 0; mc < a.u.mcount; ++mc) {
+        const int64_t m = a.u.mrow + mc;
+        cplx part = mk(0.0, 0.0);
+        for (int u = tid; u < p; u += blockDim.x) {
+          const cplx gm = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, u, m) : ldG(U.G, a.u.dtype, U.ldg, m, sV[u]);
+          part = part + sD[u] * (gm * yfin[u]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          part.re += __shfl_down_sync(0xffffffffu, part.re, o);
+          part.im += __shfl_down_sync(0xffffffffu, part.im, o);
+        }
+        if (lane == 0) { s_bv[wid] = part.re; s_red[wid] = part.im; }
+        __syncthreads();
+        if (tid == 0) {
+          cplx dE = mk(0.0, 0.0);
+          for (int w = 0; w < nw; ++w) dE = dE + mk(s_bv[w], s_red[w]);
+          const cplx EN = U.E[m];
+          df += abs2(EN + dE) - abs2(EN);
+        }
+        __syncthreads();
+      }
+      cplx* yd = reinterpret_cast<cplx*>(ws + L.yd);
+      for (int u = tid; u < p; u += blockDim.x) yd[u] = sD[u] * yfin[u];
+    }
+    if (tid == 0) {
+      ctl->lam_df[0] = df;
+      ctl->lam_bad[0] = bad ? 1 : 0;
+    }
   }
-  __syncthreads();
-  for (int t = tid; t < kLuTile * kLuTile; t += blockDim.x) {
-    const int r = t / kLuTile, c = t % kLuTile;
-    if (i0 + r >= w || v0 + c >= w) continue;
-    const int64_t o = (int64_t)(c0 + nb + i0 + r) * p + c0 + nb + v0 + c;
-    cplx acc = A[o];
-#pragma unroll
-    for (int j = 0; j < kLuNB; ++j)
-      if (j < nb) acc = acc - sL[r][j] * sU[j][c];
-    A[o] = acc;
-  }
-}
-
-__global__ void k_cap_lu_finish(CapArgs a, WsLayout L, char* ws) {
-  UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
-  const int p = ctl->lu_p;
-  double df = 0.0;
-  bool ok = !ctl->lu_bad;
-  if (p > 0 && ok)
-    df = cap_tail(a, a.u.lam[0], p, reinterpret_cast<const int32_t*>(ws + L.V),
-                  reinterpret_cast<const double*>(ws + L.dchi), reinterpret_cast<const cplx*>(ws + L.lu),
-                  reinterpret_cast<const int32_t*>(ws + L.piv), reinterpret_cast<cplx*>(ws + L.yd), false);
-  if (threadIdx.x == 0) {
-    ctl->lam_df[0] = df;
-    ctl->lam_bad[0] = ok ? 0 : 1;
-  }
+  cl.sync();                                              // no CTA leaves while others read its memory
 }
 
 // ----------------------------------------------------------------------------- panels
-// Column j: R[:, j] = A^{-1} G[V, j] (Eq. 14) and S[:, j] = D R[:, j]; row j of the rows held:
-// C0[j, :] = G[j, V].
-__device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L, char* ws, int want_S) {
-  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
-  if (ctl->skip) return;
-  const int p = ctl->nv;
-  const int32_t* V = reinterpret_cast<const int32_t*>(ws + L.V);
-  const double* dchi = reinterpret_cast<const double*>(ws + L.dchi);
-  const int64_t n = L.n;
-  for (int l = 0; l < a.nlam; ++l) {
-    const UpdLam& U = a.lam[l];
-    const cplx* A = reinterpret_cast<const cplx*>(ws + L.lu + l * L.lu_s);
-    const int32_t* piv = reinterpret_cast<const int32_t*>(ws + L.piv + l * L.piv_s);
-    cplx* C0 = reinterpret_cast<cplx*>(ws + L.C0 + l * L.panel_s);
-    cplx* S = reinterpret_cast<cplx*>(ws + L.S + l * L.panel_s);
-    const int64_t jend = U.rows > n ? U.rows : n;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < jend;
-         j += (int64_t)gridDim.x * blockDim.x) {
-      if (j < U.rows)
-        for (int u = 0; u < p; ++u) C0[j * L.pmax + u] = ldG(U.G, a.dtype, U.ldg, j, V[u]);
-      if (!want_S || j >= n) continue;
-      if (p <= kMaxPixelsPerCand) {
-        cplx x[kMaxPixelsPerCand];
-#pragma unroll
-        for (int u = 0; u < kMaxPixelsPerCand; ++u)
-          if (u < p) x[u] = U.vrows ? ldG(U.vrows, a.dtype, U.ldv, u, j) : ldG(U.G, a.dtype, U.ldg, V[u], j);
-        // P A = L U with full-row interchanges: apply all interchanges in order first,
-        // then the unit-lower solve, then the upper solve
-#pragma unroll
-        for (int c = 0; c < kMaxPixelsPerCand; ++c) {
-          if (c < p) {
-            int r = piv[c];
-#pragma unroll
-            for (int rr = 0; rr < kMaxPixelsPerCand; ++rr)
-              if (rr == r && rr != c) { cplx t = x[c]; x[c] = x[rr]; x[rr] = t; }
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < kMaxPixelsPerCand; ++c) {
-          if (c < p) {
-#pragma unroll
-            for (int rr = c + 1; rr < kMaxPixelsPerCand; ++rr)
-              if (rr < p) x[rr] = x[rr] - A[rr * p + c] * x[c];
-          }
-        }
-#pragma unroll
-        for (int c = kMaxPixelsPerCand - 1; c >= 0; --c) {
-          if (c < p) {
-            cplx acc = x[c];
-#pragma unroll
-            for (int v = c + 1; v < kMaxPixelsPerCand; ++v)
-              if (v < p) acc = acc - A[c * p + v] * x[v];
-            x[c] = cdiv(acc, A[c * p + c]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kMaxPixelsPerCand; ++u)
-          if (u < p) S[(int64_t)u * n + j] = dchi[u] * x[u];
-      } else {
-        // general p: the column of R lives in S itself (row stride n)
-        for (int u = 0; u < p; ++u)
-          S[(int64_t)u * n + j] = U.vrows ? ldG(U.vrows, a.dtype, U.ldv, u, j) : ldG(U.G, a.dtype, U.ldg, V[u], j);
-        for (int c = 0; c < p; ++c) {
-          int r = piv[c];
-          if (r != c) {
-            cplx t = S[(int64_t)c * n + j];
-            S[(int64_t)c * n + j] = S[(int64_t)r * n + j];
-            S[(int64_t)r * n + j] = t;
-          }
-        }
-        for (int c = 0; c < p; ++c) {
-          cplx xc = S[(int64_t)c * n + j];
-          for (int rr = c + 1; rr < p; ++rr)
-            S[(int64_t)rr * n + j] = S[(int64_t)rr * n + j] - A[rr * p + c] * xc;
-        }
-        for (int c = p - 1; c >= 0; --c) {
-          cplx acc = S[(int64_t)c * n + j];
-          for (int v = c + 1; v < p; ++v) acc = acc - A[c * p + v] * S[(int64_t)v * n + j];
-          S[(int64_t)c * n + j] = cdiv(acc, A[c * p + c]);
-        }
-        for (int u = 0; u < p; ++u) S[(int64_t)u * n + j] = dchi[u] * S[(int64_t)u * n + j];
-      }
-    }
-  }
-}
-
 __global__ void k_panels(UpdArgs a, WsLayout L, char* ws, int want_S) { panels_body(a, L, ws, want_S); }
 
 // ----------------------------------------------------------------------------- rank-p (FP64)
@@ -832,71 +408,6 @@ __global__ void __launch_bounds__(kUpdThreads) k_rank_update_c64_ref(float2* __r
   }
 }
 
-// complex64 storage, rank p <= 4, FP32 arithmetic on the CUDA cores: the update is a pure
-// HBM stream (4p FP32 FMA per 16 bytes moved), so no tensor-core form is needed.  A tile is
-// 32 rows x 512 complex columns; each thread owns two adjacent columns (one 16-byte vector per
-// row) and keeps their S entries in registers; the tile's C0 rows are staged in shared memory.
-// G is touched once per step, so its loads and stores carry the streaming (evict-first) hint
-// and leave L2 to the panels.  Three CTAs fit an SM; launches use a multiple of that.
-constexpr int kF32Threads = 256;
-constexpr int kF32Rows = 32;
-constexpr int kF32Cols = 2 * kF32Threads;
-
-__device__ __forceinline__ void c64_fp32_tile(float2* __restrict__ G, int64_t ldg, int64_t n, int64_t m, int pmax, int p,
-                                              const cplx* __restrict__ C0, const cplx* __restrict__ S,
-                                              int64_t rt, int64_t ct, float2 (*sC)[kC64Fp32MaxP]) {
-  const int64_t i0 = rt * kF32Rows;
-  const int64_t j = ct * kF32Cols + 2 * threadIdx.x;
-  __syncthreads();                                   // previous tile done with sC
-  for (int t = threadIdx.x; t < kF32Rows * kC64Fp32MaxP; t += kF32Threads) {
-    const int r = t / kC64Fp32MaxP, u = t % kC64Fp32MaxP;
-    const int64_t i = i0 + r;
-    cplx c = (i < m && u < p) ? C0[i * pmax + u] : mk(0.0, 0.0);
-    sC[r][u] = make_float2((float)c.re, (float)c.im);
-  }
-  __syncthreads();
-  if (j >= n) return;
-  const bool two = j + 1 < n;
-  float2 s0[kC64Fp32MaxP], s1[kC64Fp32MaxP];
-#pragma unroll
-  for (int u = 0; u < kC64Fp32MaxP; ++u) {
-    cplx a = u < p ? S[(int64_t)u * n + j] : mk(0.0, 0.0);
-    cplx b = (u < p && two) ? S[(int64_t)u * n + j + 1] : mk(0.0, 0.0);
-    s0[u] = make_float2((float)a.re, (float)a.im);
-    s1[u] = make_float2((float)b.re, (float)b.im);
-  }
-  const int rows = (int)(m - i0 < kF32Rows ? m - i0 : kF32Rows);
-  constexpr int U = 8;
-  for (int r0 = 0; r0 < rows; r0 += U) {
-    float4 g[U];
-#pragma unroll
-    for (int q = 0; q < U; ++q)
-      if (r0 + q < rows) g[q] = __ldcs(reinterpret_cast<const float4*>(G + (i0 + r0 + q) * ldg + j));
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      if (r0 + q < rows) {
-        float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
-#pragma unroll
-        for (int u = 0; u < kC64Fp32MaxP; ++u) {
-          const float2 c = sC[r0 + q][u];
-          ar = fmaf(c.x, s0[u].x, fmaf(-c.y, s0[u].y, ar));
-          ai = fmaf(c.x, s0[u].y, fmaf(c.y, s0[u].x, ai));
-          br = fmaf(c.x, s1[u].x, fmaf(-c.y, s1[u].y, br));
-          bi = fmaf(c.x, s1[u].y, fmaf(c.y, s1[u].x, bi));
-        }
-        float4 v = g[q];
-        v.x += ar;
-        v.y += ai;
-        if (two) {
-          v.z += br;
-          v.w += bi;
-        }
-        __stcs(reinterpret_cast<float4*>(G + (i0 + r0 + q) * ldg + j), v);
-      }
-    }
-  }
-}
-
 __global__ void __launch_bounds__(kF32Threads, 3) k_rank_update_c64_fp32(float2* __restrict__ G, int64_t ldg, int64_t n,
                                                                       int64_t m, int pmax, const cplx* __restrict__ C0,
                                                                       const cplx* __restrict__ S,
@@ -954,47 +465,6 @@ void launch_rank_update_c64_fp32_batch(const BatchItem* items, int nprob, int ct
 }
 
 // ----------------------------------------------------------------------------- field, state, FOM
-__device__ __forceinline__ void finish_body(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* __restrict__ state,
-                                            double* __restrict__ fom_out, int32_t* __restrict__ applied) {
-  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
-  const int64_t n = L.n;
-  const int64_t N = n - 1;
-  const bool skip = ctl->skip != 0;
-  const int p = skip ? 0 : ctl->nv;
-  const int32_t* V = reinterpret_cast<const int32_t*>(ws + L.V);
-  (void)N;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    // the first monitor unknown's thread also updates the others, so that it can sum the FOM
-    if (i > a.mrow && i < a.mrow + a.mcount) continue;
-    const int reps = i == a.mrow ? a.mcount : 1;
-    double f = 0.0;
-    for (int q = 0; q < reps; ++q) {
-      const int64_t ii = i + q;
-      for (int l = 0; l < a.nlam; ++l) {
-        const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + l * L.panel_s);
-        const cplx* yd = reinterpret_cast<const cplx*>(ws + L.yd + l * L.yd_s);
-        const UpdLam& U = a.lam[l];
-        cplx e = U.E[ii];
-        if (U.vrows)        // G[ii, V[u]] read as G[V[u], ii] from the row panel (reciprocity)
-          for (int u = 0; u < p; ++u) e = cfma(ldG(U.vrows, a.dtype, U.ldv, u, ii), yd[u], e);
-        else
-          for (int u = 0; u < p; ++u) e = cfma(C0[ii * L.pmax + u], yd[u], e);
-        if (p > 0) a.lam[l].E[ii] = e;
-        f += abs2(e);
-      }
-    }
-    if (i == a.mrow) {
-      *fom_out = f;
-      if (applied) *applied = skip ? 0 : ctl->ncand;
-    }
-  }
-  if (blockIdx.x == 0) {   // one flip per point (the unknowns of a point are consecutive in V)
-    for (int t = threadIdx.x; t < p; t += blockDim.x)
-      if (V[t] % a.ncomp == 0) state[V[t] / a.ncomp] ^= 1;
-  }
-}
-
 __global__ void k_finish(UpdArgs a, WsLayout L, char* ws, uint8_t* __restrict__ state,
                          double* __restrict__ fom_out, int32_t* __restrict__ applied) {
   finish_body(a, L, ws, state, fom_out, applied);
@@ -1092,16 +562,19 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   const bool multi = a.nlam == 1 && L.pmax > kCapSmemP && L.pmax <= kLuMaxBlocked;
   const int pre = (a.nlam > 1 && L.pmax <= kCapSmemP) || multi ? 1 : 0;
   if (multi) {
-    k_cap_lu_prep<<<1, 256, 0, st>>>(ca, L, ws, state, idx, status);
-    for (int q = 0; q * kLuNB < L.pmax; ++q) {
-      k_lu_panel<<<1, 256, 0, st>>>(L, ws, q);
-      const int w = L.pmax - q * kLuNB - kLuNB;        // trailing width at p = p_max (smaller p: tiles exit)
-      if (w > 0) {
-        const unsigned t = (unsigned)((w + kLuTile - 1) / kLuTile);
-        k_lu_trail<<<dim3(t, t), 256, 0, st>>>(L, ws, q);
+    {  // once per device
+      static std::mutex mu2;
+      static bool done2[64] = {};
+      int dev = 0;
+      cudaGetDevice(&dev);
+      std::lock_guard<std::mutex> lk(mu2);
+      if (dev < 0 || dev >= 64 || !done2[dev]) {
+        cudaFuncSetAttribute(k_cap_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cap_cluster_smem(kLuMaxBlocked));
+        if (dev >= 0 && dev < 64) done2[dev] = true;
       }
     }
-    k_cap_lu_finish<<<1, 256, 0, st>>>(ca, L, ws);
+    k_cap_cluster<<<kCluN, 256, cap_cluster_smem(L.pmax), st>>>(ca, L, ws, state, idx, status);
   } else if (pre) {
     k_capacitance_lam<<<a.nlam, 256, cap_smem, st>>>(ca, L, ws, state, idx, status);
   }

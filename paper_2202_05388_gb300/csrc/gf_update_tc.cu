@@ -30,120 +30,10 @@
 #include <new>
 
 #include "gf_internal.cuh"
+#include "gf_stage_bodies.cuh"
 #include "gf_tc.cuh"
 
 namespace gf {
-
-constexpr int kOzW = 9;            // bits per digit
-constexpr int kOzS = 6;            // digits per value
-constexpr int kOzLv = 6;           // levels a + b = 2 .. 7
-constexpr int kOzK = 8;            // real K (2 p, p <= 4)
-constexpr int kOzM = 128;          // rows per tile (TMEM lanes)
-constexpr int kOzN = 32;           // real output columns per tile (16 complex)
-constexpr int kOzSliceA = kOzM * kOzK * 4;      // bytes of one digit slice of an A tile
-constexpr int kOzSliceB = kOzN * kOzK * 4;      // bytes of one digit slice of a B tile
-constexpr int kOzTileA = kOzS * kOzSliceA;      // 24 KB
-constexpr int kOzTileB = kOzS * kOzSliceB;      // 6 KB
-constexpr uint64_t kOzTimeoutNs = 2000000000ull;
-constexpr int kOzMaxBatch = kBatchMax;
-constexpr int kOzBBlockG = kOzTileB + 64;       // B digit slices + 16 column exponents (global block)
-
-// byte offset of element (r, k) inside one K-major, no-swizzle digit slice (8x16-byte core
-// matrices; K-direction core-matrix stride 128 B, row-group stride 256 B)
-__host__ __device__ __forceinline__ int oz_off(int r, int k) {
-  return (r >> 3) * 256 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
-}
-
-// six signed 9-bit digits of x in (-1, 1): x = sum_a d[a] 2^(-9(a+1)) + r, |r| <= 2^-55
-__device__ __forceinline__ void oz_digits(double x, float (&d)[kOzS]) {
-  double r = x;
-#pragma unroll
-  for (int a = 0; a < kOzS; ++a) {
-    const double sc = ldexp(1.0, kOzW * (a + 1));
-    double t = rint(r * sc);
-    d[a] = (float)t;
-    r = r - t * ldexp(1.0, -kOzW * (a + 1));
-  }
-}
-
-__device__ __forceinline__ int oz_exponent(double m) {
-  // smallest E with m < 2^E (m > 0); a zero row/column gets digits 0 and any exponent
-  return m > 0.0 ? ilogb(m) + 1 : 0;
-}
-
-// ---- operand preparation (once per step, O(n p) work) --------------------------------------
-__device__ __forceinline__ void oz_prep_rows_body(const cplx* __restrict__ C0, int pmax, int64_t n,
-                                                  int64_t nrows_pad, const UpdCtl* __restrict__ ctl,
-                                                  uint8_t* __restrict__ ozA, int32_t* __restrict__ ozE) {
-  if (ctl->skip || ctl->nv > 4) return;
-  const int p = ctl->nv;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows_pad;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double v[kOzK];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      cplx c = (i < n && k < p) ? C0[i * pmax + k] : mk(0.0, 0.0);
-      v[k] = c.re;
-      v[4 + k] = c.im;
-    }
-    double m = 0.0;
-#pragma unroll
-    for (int k = 0; k < kOzK; ++k) m = fmax(m, fabs(v[k]));
-    const int E = oz_exponent(m);
-    ozE[i] = E;
-    uint8_t* tile = ozA + (i / kOzM) * (int64_t)kOzTileA;
-    const int r = (int)(i % kOzM);
-    float dg[kOzK][kOzS];
-#pragma unroll
-    for (int k = 0; k < kOzK; ++k) oz_digits(ldexp(v[k], -E), dg[k]);
-#pragma unroll
-    for (int a = 0; a < kOzS; ++a) {
-      float4* q0 = reinterpret_cast<float4*>(tile + a * kOzSliceA + oz_off(r, 0));
-      float4* q1 = reinterpret_cast<float4*>(tile + a * kOzSliceA + oz_off(r, 4));
-      *q0 = make_float4(dg[0][a], dg[1][a], dg[2][a], dg[3][a]);
-      *q1 = make_float4(dg[4][a], dg[5][a], dg[6][a], dg[7][a]);
-    }
-  }
-}
-
-__device__ __forceinline__ void oz_prep_cols_body(const cplx* __restrict__ S, int64_t n, int64_t ncols_pad,
-                                                  const UpdCtl* __restrict__ ctl, uint8_t* __restrict__ ozB) {
-  if (ctl->skip || ctl->nv > 4) return;
-  const int p = ctl->nv;
-  // one thread per complex column j; writes real columns 2j and 2j+1
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ncols_pad;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    double sr[4], si[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      cplx s = (j < n && k < p) ? S[(int64_t)k * n + j] : mk(0.0, 0.0);
-      sr[k] = s.re;
-      si[k] = s.im;
-    }
-    double m = 0.0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) m = fmax(m, fmax(fabs(sr[k]), fabs(si[k])));
-    const int F = oz_exponent(m);
-    float dr[4][kOzS], di[4][kOzS];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      oz_digits(ldexp(sr[k], -F), dr[k]);
-      oz_digits(ldexp(si[k], -F), di[k]);
-    }
-    const int64_t c_re = 2 * j;
-    uint8_t* tile = ozB + (c_re / kOzN) * (int64_t)kOzBBlockG;
-    const int c = (int)(c_re % kOzN);            // even; c + 1 is the imaginary column
-    reinterpret_cast<int32_t*>(tile + kOzTileB)[c / 2] = F;
-#pragma unroll
-    for (int a = 0; a < kOzS; ++a) {
-      uint8_t* sl = tile + a * kOzSliceB;
-      *reinterpret_cast<float4*>(sl + oz_off(c, 0)) = make_float4(dr[0][a], dr[1][a], dr[2][a], dr[3][a]);
-      *reinterpret_cast<float4*>(sl + oz_off(c, 4)) = make_float4(-di[0][a], -di[1][a], -di[2][a], -di[3][a]);
-      *reinterpret_cast<float4*>(sl + oz_off(c + 1, 0)) = make_float4(di[0][a], di[1][a], di[2][a], di[3][a]);
-      *reinterpret_cast<float4*>(sl + oz_off(c + 1, 4)) = make_float4(dr[0][a], dr[1][a], dr[2][a], dr[3][a]);
-    }
-  }
-}
 
 __global__ void k_oz_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n, int64_t nrows_pad,
                                const UpdCtl* __restrict__ ctl, uint8_t* __restrict__ ozA,

@@ -21,6 +21,7 @@ GF_KIND_SINGLE, GF_KIND_BRUSH2, GF_KIND_PILLAR = 0, 1, 2
 GF_DIR_FILL, GF_DIR_CLEAR = 1, 2
 GF_NBANDS = 9
 GF_UPDATE_TC, GF_UPDATE_DFMA, GF_UPDATE_TENSOR = 0, 1, 2
+GF_BATCH_STAGED, GF_BATCH_PERSISTENT = 0, 1
 BATCH_MAX = 64             # items per gf_batch
 
 STATUS_NAMES = {GF_OK: "GF_OK", GF_EINVAL: "GF_EINVAL", GF_ECUDA: "GF_ECUDA",
@@ -32,7 +33,7 @@ EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_v
            "gf_eval_candidates", "gf_select_topk", "gf_apply_update", "gf_profile_begin",
            "gf_profile_end", "gf_set_update_algo", "gf_refresh", "gf_refresh_workspace_size",
            "gf_fill_g0_static", "gf_batch_table_size", "gf_batch_create", "gf_batch_step",
-           "gf_batch_set_schedule", "gf_batch_destroy", "gf_select_egreedy", "gf_lowrank_workspace_size",
+           "gf_batch_set_schedule", "gf_batch_set_form", "gf_batch_selftest_timeout", "gf_batch_destroy", "gf_select_egreedy", "gf_lowrank_workspace_size",
            "gf_lowrank_init", "gf_lowrank_eval", "gf_lowrank_update", "gf_lowrank_count",
            "gf_lowrank_materialize", "gf3_num_unknowns", "gf3_num_candidates", "gf3_workspace_size",
            "gf3_fill_g0", "gf3_eval_candidates", "gf3_select_topk", "gf3_apply_update", "gf_selftest_timeout",
@@ -177,6 +178,8 @@ def load(path: str = LIB_PATH):
                                             C.POINTER(gf_cand_spec), P, C.c_size_t, P, C.POINTER(P)]),
             "gf_batch_step": (C.c_int32, [P, P]),
             "gf_batch_set_schedule": (C.c_int32, [P, C.c_int32]),
+            "gf_batch_set_form": (C.c_int32, [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+            "gf_batch_selftest_timeout": (C.c_int32, [P, C.c_int64, P]),
             "gf_batch_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -452,6 +455,12 @@ class Handle:
 
     def gf_batch_set_schedule(self, batch, update_ctas: int):
         self._check(self.lib.gf_batch_set_schedule(batch, int(update_ctas)))
+
+    def gf_batch_set_form(self, batch, form: int, step_ctas: int = 0, scale: int = 1, tile_rows: int = 32):
+        self._check(self.lib.gf_batch_set_form(batch, int(form), int(step_ctas), int(scale), int(tile_rows)))
+
+    def gf_batch_selftest_timeout(self, batch, timeout_ns: int, stream=None):
+        self._check(self.lib.gf_batch_selftest_timeout(batch, int(timeout_ns), _stream(stream)))
 
     def gf_batch_destroy(self, batch):
         self.lib.gf_batch_destroy(batch)

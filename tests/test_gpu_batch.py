@@ -1,7 +1,8 @@
-"""Batched problems through CUDA-graph replay, with the fused schedule (the library's batch
-entry points: one launch per stage for all problems) and the stream-branch schedules: every
-problem of a small seeded batch follows exactly the trajectory it follows when stepped alone
-(same flips, same G, E and FOM), and the complex128 runs match the FP64 oracle."""
+"""Batched problems through CUDA-graph replay, with the fused schedules (the library's batch
+entry points: the persistent step kernel with several launch shapes, or one launch per stage)
+and the stream-branch schedules: every problem of a small seeded batch follows exactly the
+trajectory it follows when stepped alone (same flips, same G, E and FOM), and the complex128
+runs match the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -76,7 +77,15 @@ def _check_against_single_runs(wls, bo, total, dtype, oracle, patterned=False, s
     assert improved > 0, "no problem of the batch accepted a flip"
 
 
+PERSIST, STAGED = B.GF_BATCH_PERSISTENT, B.GF_BATCH_STAGED
+
+
 @pytest.mark.parametrize("sch", [Schedule(0, "given", True), Schedule(0, "given", True, 5), Schedule(3, "given", True),
+                                 Schedule(0, "given", True, 0, STAGED), Schedule(3, "given", True, 0, STAGED),
+                                 # one CTA takes every item in queue order (no wait can block), a few
+                                 # CTAs wait on one another, work items of 4 and 16 units per thread
+                                 Schedule(0, "given", True, 0, PERSIST, 1), Schedule(0, "given", True, 0, PERSIST, 3),
+                                 Schedule(0, "given", True, 0, PERSIST, 0, 4), Schedule(0, "given", True, 0, PERSIST, 7, 16),
                                  Schedule(1, "given"), Schedule(3, "largest_first"), Schedule(6, "given")])
 def test_graph_batch_matches_single_problem_runs_and_oracle(sch):
     wls = _small_batch()
@@ -90,11 +99,17 @@ def test_graph_batch_matches_single_problem_runs_and_oracle(sch):
     _check_against_single_runs(wls, bo, steps + 1, "c128", oracle=True)
 
 
-@pytest.mark.parametrize("dtype,kind,count", [("c64", W.KIND_SINGLE, 6), ("c128", W.KIND_BRUSH2, 5),
-                                              ("c64", W.KIND_BRUSH2, 5), ("c128", W.KIND_SINGLE, 70)])
-def test_fused_batch_kinds_dtypes_and_groups(dtype, kind, count):
-    """Complex64 items (FP32 update), brush candidates and more items than one launch takes
-    (two groups) behave exactly like the single-problem calls."""
+@pytest.mark.parametrize("dtype,kind,count,form", [
+    ("c64", W.KIND_SINGLE, 6, (PERSIST, 0, 1, 32)), ("c64", W.KIND_SINGLE, 6, (PERSIST, 2, 1, 16)),
+    ("c64", W.KIND_SINGLE, 6, (PERSIST, 0, 2, 64)), ("c64", W.KIND_SINGLE, 6, (PERSIST, 0, 1, 0)),
+    ("c64", W.KIND_SINGLE, 6, (STAGED, 0, 1, 32)),
+    ("c128", W.KIND_BRUSH2, 5, (PERSIST, 0, 1, 32)), ("c128", W.KIND_BRUSH2, 5, (STAGED, 0, 1, 32)),
+    ("c64", W.KIND_BRUSH2, 5, (PERSIST, 0, 1, 32)), ("c64", W.KIND_BRUSH2, 5, (PERSIST, 1, 1, 16)),
+    ("c128", W.KIND_SINGLE, 70, (PERSIST, 0, 1, 32)), ("c128", W.KIND_SINGLE, 70, (STAGED, 0, 1, 32))])
+def test_fused_batch_kinds_dtypes_and_groups(dtype, kind, count, form):
+    """Complex64 items (FP32 update in 16-, 32- and 64-row tiles), brush candidates and more
+    items than one launch takes (two groups), in the persistent and the staged form, behave
+    exactly like the single-problem calls."""
     if kind == W.KIND_BRUSH2:
         wls = _small_batch(count, sides=(10, 12, 14), kind=kind, ratios=(20,), dtype=dtype, seed=7)
     elif count > B.BATCH_MAX:
@@ -103,6 +118,7 @@ def test_fused_batch_kinds_dtypes_and_groups(dtype, kind, count):
         wls = _small_batch(count, dtype=dtype)
     bo = BatchOptimizer(wls, dtype=dtype)
     assert bo.schedule.fused
+    bo.schedule = Schedule(0, "given", True, 0, form[0], form[1], form[2], form[3])
     bo.fill()
     patterned = kind == W.KIND_BRUSH2        # brushes rarely improve a vacuum start
     if patterned:
@@ -185,3 +201,28 @@ def test_c64_batch_against_the_fp64_oracle():
         assert abs(float(opt.fom.cpu()[0]) - orc.fom()) <= 2e-5 * orc.fom()
         moved += int(orc.state.sum())
     assert moved > 0
+
+
+def test_persistent_step_bounded_wait_reports_timeout():
+    """The persistent step's waits are bounded: a diagnostic step whose largest problem waits for
+    an evaluation item that does not exist gives up after 20 ms, writes GF_ETIMEOUT to that
+    problem's status word and ends; the context stays usable and, refilled, the batch steps
+    exactly like the single-problem runs again."""
+    wls = _small_batch(4, sides=(8, 10, 12))
+    sizes = [w.geoms[0].N for w in wls]
+    big = int(np.argmax(sizes))
+    bo = BatchOptimizer(wls)
+    bo.fill()
+    bo._ensure_batches()
+    (b,) = bo._batches[0]
+    bo.h.gf_batch_selftest_timeout(b, 20_000_000, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert int(bo.opts[big].status.cpu()[0]) == B.GF_ETIMEOUT
+    assert float(torch.ones(4, device="cuda").sum().cpu()) == 4.0
+    with pytest.raises(B.GfError):
+        bo.h.gf_batch_selftest_timeout(b, 10, torch.cuda.current_stream())
+    bo.fill()
+    bo.capture(2)
+    bo.replay()
+    torch.cuda.synchronize()
+    _check_against_single_runs(wls, bo, 3, "c128", oracle=False)
