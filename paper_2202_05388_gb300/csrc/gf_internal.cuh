@@ -37,6 +37,30 @@ __device__ __forceinline__ cplx cfma(cplx a, cplx b, cplx acc) {
   return acc;
 }
 
+// 1 / v for a positive normal v whose reciprocal is normal: Newton's iteration y <- y + y (1 - m y)
+// on the mantissa m in [1, 2), seeded with the correctly rounded FP32 reciprocal of m (relative
+// error <= 2^-24, squared by each step: two steps reach the FP64 rounding), then scaled by the
+// exact power of two.  Six FP64 operations instead of the division routine, which sits on the
+// per-column critical path of the pivoting and costs microseconds on GB300's narrow FP64 pipe.
+// Error <= 1 ulp; correctly rounded for random mantissas in the CPU model of these operations (not
+// at every value: just above a power of two the result may round to that power).  The pivot
+// reciprocal of the capacitance factorisations, one CTA or a cluster (so they agree bit for bit).
+__device__ __forceinline__ double rcp_nr(double v) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+  double y = (double)__frcp_rn((float)m);
+  double r = fma(-m, y, 1.0);
+  y = fma(y, r, y);
+  r = fma(-m, y, 1.0);
+  y = fma(y, r, y);
+  return y * __longlong_as_double((long long)(1023 - e) << 52);
+}
+
+// a - l u with fused multiply-adds: the elimination step (and forward solve) of the capacitance
+// factorisations, in one CTA or over a cluster, which therefore agree bit for bit
+__device__ __forceinline__ cplx cfms(cplx l, cplx u, cplx a) { return cfma(mk(-l.re, -l.im), u, a); }
+
 __device__ __forceinline__ cplx ldc(const void* base, int64_t idx) {
   double2 v = reinterpret_cast<const double2*>(base)[idx];
   return {v.x, v.y};

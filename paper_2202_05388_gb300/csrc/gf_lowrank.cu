@@ -157,9 +157,9 @@ __global__ void k_lr_w(LrArgs a) {
 //
 // The product runs on the FP32 pipe in double-float arithmetic (a value is an unevaluated sum
 // hi + lo of two floats, about 48 bits): GB300's FP64 pipe runs at 1/64 of the FP32 rate, and the
-// FP64 form of this product kept it 97% busy.  Each FP64 entry of U and w is split exactly into
-// hi (its sign, exponent and first 23 mantissa bits) and lo (the remaining 29 bits, rounded to a
-// float) with integer operations; products use the error-free product of Dekker (the rounding
+// FP64 form of this product kept it 97% busy.  Each FP64 entry of U and w is split into hi (its
+// sign, exponent and first 23 mantissa bits) and lo (the remaining 29 bits, rounded to a float)
+// with integer and FP32 operations only; products use the error-free product of Dekker (the rounding
 // error of hi*hi from one FMA) plus the two cross terms, and sums use Knuth's error-free sum and a
 // renormalisation.  Every step is an _rn intrinsic, so the compiler cannot contract the sums into
 // FMAs (which would lose the error terms).  The result is converted back to FP64 once per entry.
@@ -172,24 +172,23 @@ struct dflt {
 __device__ __forceinline__ dflt df_split(double x) {
   const long long b = __double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7FF);
-  // hi's exponent field e - 896 and the scale 2^(e - 1075) of lo are normal floats for
-  // e in [949, 1150] (|x| in [2^-74, 2^128)); zero and other values take the conversions
-  if (e < 949 || e > 1150) {
-    const float h = (float)x;
-    return {h, (float)(x - (double)h)};
-  }
   const unsigned sgn = (unsigned)((unsigned long long)b >> 63) << 31;
-  const float h = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7FFFFF));
-  // lo = (low 29 mantissa bits) * 2^(e - 1075), with the sign of x.  The 29-bit integer is rounded
-  // to a float without an integer conversion instruction (which shares the slow FP64 unit): its
-  // high 23 and low 6 bits become exact floats through the 2^23 bias, and one FMA joins them with
-  // a single rounding.
+  // hi: sign, exponent and the first 23 mantissa bits, exact for |x| in [2^-126, 2^128); below
+  // that 0, above it inf.  Only integer and FP32 operations: a branch to a conversion would be
+  // predicated into every split and keep GB300's narrow FP64 pipe busy.
+  const unsigned hb = e < 897 ? sgn
+                    : e > 1150 ? (sgn | 0x7F800000u)
+                               : (sgn | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7FFFFF));
+  // lo = (low 29 mantissa bits) * 2^(e - 1075), with the sign of x, rounded once: the 29-bit
+  // integer's high 23 and low 6 bits become exact floats through the 2^23 bias and one FMA joins
+  // them.  Where 2^(e - 1075) is not a normal float (|x| < 2^-74) lo is 0: an absolute error
+  // below 2^-97 |x|.
   const unsigned m29 = (unsigned)(b & 0x1FFFFFFF);
   const float fa = __fsub_rn(__uint_as_float(0x4B000000u | (m29 >> 6)), 8388608.0f);
   const float fb = __fsub_rn(__uint_as_float(0x4B000000u | (m29 & 63u)), 8388608.0f);
-  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);
-  const float l = __fmul_rn(__fmaf_rn(fa, 64.0f, fb), scale);
-  return {h, sgn ? -l : l};
+  const int se = (e < 949 || e > 1150) ? 0 : e - 948;          // biased exponent of 2^(e - 1075)
+  const float l = __fmul_rn(__fmaf_rn(fa, 64.0f, fb), __uint_as_float((unsigned)se << 23));
+  return {__uint_as_float(hb), sgn ? -l : l};
 }
 
 __device__ __forceinline__ double df_to(dflt a) { return (double)a.h + (double)a.l; }

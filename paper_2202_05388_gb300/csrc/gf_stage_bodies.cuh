@@ -486,7 +486,7 @@ inline __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restri
             s_bad2 = 1;
           } else {
             const cplx pv = sP[br * kLuNB + j];
-            const double d = 1.0 / bv;
+            const double d = rcp_nr(bv);
             s_inv = mk(pv.re * d, -pv.im * d);
           }
           s_pr = br;
@@ -507,7 +507,7 @@ inline __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restri
       for (int r = j + 1 + tid; r < m; r += nt) {
         const cplx f = sP[r * kLuNB + j] * inv;
         sP[r * kLuNB + j] = f;
-        for (int k = j + 1; k < nb; ++k) sP[r * kLuNB + k] = sP[r * kLuNB + k] - f * sP[j * kLuNB + k];
+        for (int k = j + 1; k < nb; ++k) sP[r * kLuNB + k] = cfms(f, sP[j * kLuNB + k], sP[r * kLuNB + k]);
       }
       __syncthreads();
     }
@@ -543,7 +543,7 @@ inline __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restri
           if (j < nb)
 #pragma unroll
             for (int i = 0; i < kLuNB; ++i)
-              if (i < j) x[j] = x[j] - sP[j * kLuNB + i] * x[i];
+              if (i < j) x[j] = cfms(sP[j * kLuNB + i], x[i], x[j]);
 #pragma unroll
         for (int j = 1; j < kLuNB; ++j)
           if (j < nb) A[(int64_t)(c0 + j) * p + c0 + nb + v] = x[j];
@@ -561,7 +561,7 @@ inline __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restri
 #pragma unroll
         for (int j = 0; j < kLuNB; ++j)
           if (j < nb)
-            acc = acc - sP[(nb + i) * kLuNB + j] * (sU ? sU[j * w + v] : A[(int64_t)(c0 + j) * p + c0 + nb + v]);
+            acc = cfms(sP[(nb + i) * kLuNB + j], sU ? sU[j * w + v] : A[(int64_t)(c0 + j) * p + c0 + nb + v], acc);
         A[o] = acc;
       }
     }
@@ -624,7 +624,7 @@ inline __device__ double cap_tail(const CapArgs& a, const UpdLam& U, int p, cons
     __syncthreads();
     for (int c = 0; c < p; ++c) {
       const cplx yc = y[c];
-      for (int r = c + 1 + tid; r < p; r += blockDim.x) y[r] = y[r] - A[r * p + c] * yc;
+      for (int r = c + 1 + tid; r < p; r += blockDim.x) y[r] = cfms(A[r * p + c], yc, y[r]);
       __syncthreads();
     }
   }

@@ -59,36 +59,69 @@ __global__ void k_capacitance_lam(CapArgs a, WsLayout L, char* ws, const uint8_t
 }
 
 // ---- one large system (a single wavelength with p_max > kCapSmemP), held in the shared memory of
-// one 8-CTA cluster (distributed shared memory).  One CTA per solve is bound by that SM's FP64
+// one cluster of CTAs (distributed shared memory).  One CTA per solve is bound by that SM's FP64
 // pipe (p = 128: 1.9 ms).  A = I - G_VV D is built, factorised with partial pivoting and solved
-// without leaving the cluster: physical row r (with y as its last entry) lives in CTA r % kCluN.  Row interchanges
+// without leaving the cluster: physical row r (with y as its last entry) lives in CTA r % CN.  Row interchanges
 // are kept as a permutation shared by every CTA (logical position i holds physical row phys[i]),
 // so a pivot row is only read by the others, never moved, and one cluster barrier per column
 // suffices: after it every CTA reads the candidates of the column (double-buffered slots), takes
 // the same pivot (largest modulus, lowest position on ties), copies the pivot row from its owner
 // and eliminates its own rows.  Every element sees the same operations in the same order as the
 // blocked factorisation of lu_blocked (the multiplier a_rj (conj(pv) / |pv|^2), then
-// a_rk - l u_jk column after column), and the upper solve runs in blocks of kLuNB rows from the
-// bottom as cap_tail does, so the factors, pivots, y and the dFOM are the bits one CTA computes.
+// cfms(l, u_jk, a_rk) column after column, y included), and the upper solve runs in blocks of
+// kLuNB rows from the bottom as cap_tail does, so the factors, pivots, y and the dFOM are the bits
+// one CTA computes.  A pivot's value travels with its candidate, so a column costs one cluster
+// barrier and two rounds of distributed-shared-memory loads (candidates, pivot row).
 // Outputs: V, dchi, the factors (row-major, logical order), pivots and D y in the workspace, the
 // dFOM and singular flag in the control block, where k_capacitance's first attempt reads them.
-constexpr int kCluN = 8;
-constexpr int kCluRows = kLuMaxBlocked / kCluN;         // physical rows per CTA at most
-__host__ __device__ constexpr size_t cap_cluster_smem(int pmax) {
+// CN = 16 CTAs where the device can hold such a cluster (a non-portable size), else 8.
+// Candidates are compared as integers: |a|^2 >= 0, and the bit patterns of non-negative doubles
+// order as the values do, so the key is the bit pattern (-1 for NaN, which never wins).  The
+// comparisons stay off GB300's narrow FP64 pipe, where every one on the per-column critical path
+// cost a warp instruction's worth of FP64 issue.
+struct CluSlot {                 // a CTA's best candidate of a column: key, position, conj(a) / |a|^2
+  cplx inv;
+  long long key;
+  int pos;
+};
+__device__ __forceinline__ long long clu_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return (b & 0x7FFFFFFFFFFFFFFFll) > 0x7FF0000000000000ll ? -1ll : b;
+}
+__device__ __forceinline__ bool clu_better(long long k, int ps, long long bk, int bps) {
+  return k > bk || (k == bk && ps < bps);
+}
+// the CTA's best of its warps' candidates into its slot, with the reciprocal the multipliers use
+// (formed here, before the cluster barrier, as the one-CTA factorisation forms it: conj(pv) / |pv|^2)
+__device__ __forceinline__ void clu_publish(long long* wk, int* wr, cplx* wa, int nw, CluSlot& slot) {
+  int b = 0;
+  for (int w = 1; w < nw; ++w)
+    if (clu_better(wk[w], wr[w], wk[b], wr[b])) b = w;
+  slot.key = wk[b];
+  slot.pos = wr[b];
+  if (wk[b] > 0) {
+    const cplx pv = wa[b];
+    const double d = rcp_nr(__longlong_as_double(wk[b]));
+    slot.inv = mk(pv.re * d, -pv.im * d);
+  } else {
+    slot.inv = mk(0.0, 0.0);
+  }
+}
+__host__ __device__ constexpr size_t cap_cluster_smem(int pmax, int cn) {
   // rows (R x (pmax + 1)) | pivot row (pmax + 1) | block of the upper solve (kLuNB x kLuNB + kLuNB)
   // | final y (pmax) | dchi (pmax) | phys, pos, V (pmax each)
-  return sizeof(cplx) * ((size_t)((pmax + kCluN - 1) / kCluN) * (pmax + 1) + (pmax + 1) + kLuNB * kLuNB + kLuNB +
-                         pmax) +
+  return sizeof(cplx) * ((size_t)((pmax + cn - 1) / cn) * (pmax + 1) + (pmax + 1) + kLuNB * kLuNB + kLuNB + pmax) +
          sizeof(double) * (size_t)pmax + sizeof(int32_t) * 3 * (size_t)pmax;
 }
 
-__global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
+template <int CN>
+__global__ void __launch_bounds__(256)
     k_cap_cluster(CapArgs a, WsLayout L, char* ws, const uint8_t* state, const int32_t* idx, const int32_t* status) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char clu_smem[];
   const int pm = L.pmax;
-  const int Rm = (pm + kCluN - 1) / kCluN;
+  const int Rm = (pm + CN - 1) / CN;
   const int W = pm + 1;                                   // row stride: p columns of A, then y
   cplx* rows = reinterpret_cast<cplx*>(clu_smem);
   cplx* prow = rows + (size_t)Rm * W;
@@ -98,11 +131,11 @@ __global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
   int32_t* phys = reinterpret_cast<int32_t*>(sD + pm);
   int32_t* pos = phys + pm;
   int32_t* sV = pos + pm;
-  __shared__ double s_cv[2];                              // candidates: value, position (as double)
-  __shared__ int s_cr[2];
-  __shared__ double s_wv[8];
+  __shared__ CluSlot s_slot[2];                           // double-buffered: columns j, j + 1
+  __shared__ long long s_wk[8];
   __shared__ int s_wr[8];
-  __shared__ double s_thr, s_rmax, s_d;
+  __shared__ cplx s_wa[8];
+  __shared__ double s_thr, s_rmax;
   __shared__ int s_nv, s_pr, s_bad;
   __shared__ cplx s_inv;
   __shared__ double s_red[32], s_bv[32];
@@ -132,14 +165,14 @@ __global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
       dchi[t] = sD[t];
     }
   }
-  const int R = p > rank ? (p - rank + kCluN - 1) / kCluN : 0;    // physical rows rank + kCluN lr
+  const int R = p > rank ? (p - rank + CN - 1) / CN : 0;  // physical rows rank + CN lr
   // A = I - G_VV D and y = E_V for the CTA's rows; the row sums |A|_1 a warp per row
   for (int t = tid; t < R * p; t += blockDim.x) {
-    const int lr = t / p, c = t - lr * p, r = rank + kCluN * lr;
+    const int lr = t / p, c = t - lr * p, r = rank + CN * lr;
     const cplx g = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, r, sV[c]) : ldG(U.G, a.u.dtype, U.ldg, sV[r], sV[c]);
     rows[(size_t)lr * W + c] = mk(r == c ? 1.0 : 0.0, 0.0) - sD[c] * g;
   }
-  for (int lr = tid; lr < R; lr += blockDim.x) rows[(size_t)lr * W + p] = U.E[sV[rank + kCluN * lr]];
+  for (int lr = tid; lr < R; lr += blockDim.x) rows[(size_t)lr * W + p] = U.E[sV[rank + CN * lr]];
   for (int i = tid; i < p; i += blockDim.x) {
     phys[i] = i;
     pos[i] = i;
@@ -152,65 +185,68 @@ __global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
     rmax = fmax(rmax, sum);                               // lane 0 holds the row's sum
   }
-  if (lane == 0) s_wv[wid] = rmax;
+  // the candidates of column 0 (every row), a lane per row
+  long long bk = -1;
+  int bp = 0x7fffffff;
+  cplx ba = mk(0.0, 0.0);
+  for (int lr = tid; lr < R; lr += blockDim.x) {
+    const cplx a0 = rows[(size_t)lr * W];
+    const long long k = clu_key(abs2(a0));
+    const int ps = rank + CN * lr;
+    if (clu_better(k, ps, bk, bp)) { bk = k; bp = ps; ba = a0; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ok = __shfl_down_sync(0xffffffffu, bk, o);
+    const int op = __shfl_down_sync(0xffffffffu, bp, o);
+    const double ore = __shfl_down_sync(0xffffffffu, ba.re, o), oim = __shfl_down_sync(0xffffffffu, ba.im, o);
+    if (clu_better(ok, op, bk, bp)) { bk = ok; bp = op; ba = mk(ore, oim); }
+  }
+  if (lane == 0) { s_wk[wid] = bk; s_wr[wid] = bp; s_wa[wid] = ba; s_red[wid] = rmax; }
   __syncthreads();
   if (tid == 0) {
     double m = 0.0;
-    for (int w = 0; w < nw; ++w) m = fmax(m, s_wv[w]);
+    for (int w = 0; w < nw; ++w) m = fmax(m, s_red[w]);
     s_rmax = m;
+    clu_publish(s_wk, s_wr, s_wa, nw, s_slot[0]);
   }
   cl.sync();
-  if (tid == 0) {
-    double m = 0.0;
-    for (int q = 0; q < kCluN; ++q) m = fmax(m, *cl.map_shared_rank(&s_rmax, q));
-    s_thr = kSingularRel * m;
+  if (wid == 0) {                                         // the pivot threshold kSingularRel ||A||_inf
+    double m = lane < CN ? *cl.map_shared_rank(&s_rmax, lane) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if (lane == 0) s_thr = kSingularRel * m;
   }
   __syncthreads();
-  const double thresh = s_thr;
+  const long long thr2_key = clu_key(s_thr * s_thr);
 
-  // ---- factorisation, one column per cluster barrier
-  int j = 0;
-  for (; j < p; ++j) {
+  // ---- factorisation, one cluster barrier per column
+  for (int j = 0; j < p; ++j) {
     const int buf = j & 1;
-    // the CTA's best candidate of column j among the rows not yet pivots
-    {
-      double bv = -1.0;
-      int bpos = 0x7fffffff;
-      for (int lr = tid; lr < R; lr += blockDim.x) {
-        const int ps = pos[rank + kCluN * lr];
-        if (ps < j) continue;
-        const double v = abs2(rows[(size_t)lr * W + j]);
-        if (v > bv || (v == bv && ps < bpos)) { bv = v; bpos = ps; }
+    if (j > 0) cl.sync();                                 // column j's candidates are published
+    if (wid == 0) {                                       // lane q reads CTA q's candidate
+      long long k = -1;
+      int ps = 0x7fffffff;
+      cplx iv = mk(0.0, 0.0);
+      if (lane < CN) {
+        const CluSlot* sl = cl.map_shared_rank(&s_slot[buf], lane);
+        k = sl->key;
+        ps = sl->pos;
+        iv = sl->inv;
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-        const int op = __shfl_down_sync(0xffffffffu, bpos, o);
-        if (ov > bv || (ov == bv && op < bpos)) { bv = ov; bpos = op; }
+        const long long ok = __shfl_down_sync(0xffffffffu, k, o);
+        const int op = __shfl_down_sync(0xffffffffu, ps, o);
+        const double ore = __shfl_down_sync(0xffffffffu, iv.re, o), oim = __shfl_down_sync(0xffffffffu, iv.im, o);
+        if (clu_better(ok, op, k, ps)) { k = ok; ps = op; iv = mk(ore, oim); }
       }
-      if (lane == 0) { s_wv[wid] = bv; s_wr[wid] = bpos; }
-      __syncthreads();
-      if (tid == 0) {
-        for (int w = 1; w < nw; ++w)
-          if (s_wv[w] > s_wv[0] || (s_wv[w] == s_wv[0] && s_wr[w] < s_wr[0])) { s_wv[0] = s_wv[w]; s_wr[0] = s_wr[w]; }
-        s_cv[buf] = s_wv[0];
-        s_cr[buf] = s_wr[0];
-      }
-    }
-    cl.sync();
-    if (tid == 0) {
-      double bv = -1.0;
-      int bpos = 0x7fffffff;
-      for (int q = 0; q < kCluN; ++q) {
-        const double v = *cl.map_shared_rank(&s_cv[buf], q);
-        const int ps = *cl.map_shared_rank(&s_cr[buf], q);
-        if (v > bv || (v == bv && ps < bpos)) { bv = v; bpos = ps; }
-      }
-      if (!(bv >= thresh * thresh) || !(bv > 0.0)) {
-        s_bad = 1;
-      } else {
-        s_pr = bpos;
-        s_d = 1.0 / bv;
-        if (rank == 0) reinterpret_cast<int32_t*>(ws + L.piv)[j] = bpos;
+      if (lane == 0) {
+        // |pv|^2 >= thresh^2 and > 0 (a NaN key is -1 and fails both)
+        if (k < thr2_key || k <= 0) {
+          s_bad = 1;
+        } else {
+          s_pr = ps;
+          s_inv = iv;
+          if (rank == 0) reinterpret_cast<int32_t*>(ws + L.piv)[j] = ps;
+        }
       }
     }
     __syncthreads();
@@ -218,15 +254,12 @@ __global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
     const int pr = s_pr;
     const int rp = phys[pr];                              // the pivot's physical row
     {
-      const cplx* src = cl.map_shared_rank(rows, rp % kCluN) + (size_t)(rp / kCluN) * W;
-      for (int k = j + tid; k < W; k += blockDim.x) prow[k] = src[k];
+      const cplx* src = cl.map_shared_rank(rows, rp % CN) + (size_t)(rp / CN) * W;
+      for (int k = j + 1 + tid; k < W; k += blockDim.x) prow[k] = src[k];
     }
-    __syncthreads();
-    if (tid == 0) {
-      const cplx pv = prow[j];
-      const double d = s_d;
-      s_inv = mk(pv.re * d, -pv.im * d);
-      const int rj = phys[j];                             // the interchange of positions j and pr
+    __syncthreads();                                      // every thread has rp and the pivot row
+    if (tid == 0) {                                       // the interchange of positions j and pr
+      const int rj = phys[j];
       phys[j] = rp;
       phys[pr] = rj;
       pos[rp] = j;
@@ -234,18 +267,30 @@ __global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
     }
     __syncthreads();
     const cplx inv = s_inv;
-    for (int lr = tid; lr < R; lr += blockDim.x)
-      if (pos[rank + kCluN * lr] > j) rows[(size_t)lr * W + j] = rows[(size_t)lr * W + j] * inv;
-    __syncthreads();
-    const int wk = W - (j + 1);
-    for (int t = tid; t < R * wk; t += blockDim.x) {
-      const int lr = t / wk, k = j + 1 + (t - lr * wk);
-      if (pos[rank + kCluN * lr] > j) {
-        cplx* row = rows + (size_t)lr * W;
-        row[k] = row[k] - row[j] * prow[k];
+    // elimination, a warp per row (y included); lane 0 keeps the rows' candidates of column j + 1
+    bk = -1;
+    bp = 0x7fffffff;
+    ba = mk(0.0, 0.0);
+    for (int lr = wid; lr < R; lr += nw) {
+      const int ps = pos[rank + CN * lr];
+      if (ps <= j) continue;
+      cplx* row = rows + (size_t)lr * W;
+      const cplx l = row[j] * inv;
+      __syncwarp();
+      for (int k = j + 1 + lane; k < W; k += 32) row[k] = cfms(l, prow[k], row[k]);
+      if (lane == 0) {
+        row[j] = l;
+        if (j + 1 < p) {
+          const cplx a1 = row[j + 1];
+          const long long k1 = clu_key(abs2(a1));
+          if (clu_better(k1, ps, bk, bp)) { bk = k1; bp = ps; ba = a1; }
+        }
       }
+      __syncwarp();
     }
+    if (lane == 0) { s_wk[wid] = bk; s_wr[wid] = bp; s_wa[wid] = ba; }
     __syncthreads();
+    if (tid == 0 && j + 1 < p) clu_publish(s_wk, s_wr, s_wa, nw, s_slot[buf ^ 1]);
   }
   const bool bad = s_bad != 0;
   // ---- upper solve in blocks of kLuNB rows from the bottom (CTA 0 solves each block's triangle)
@@ -258,7 +303,7 @@ __global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
         for (int t = tid; t < w * (w + 1); t += blockDim.x) {
           const int c = t / (w + 1), v = t - c * (w + 1);  // v = w: y
           const int rc = phys[b0 + c];
-          const cplx* src = cl.map_shared_rank(rows, rc % kCluN) + (size_t)(rc / kCluN) * W;
+          const cplx* src = cl.map_shared_rank(rows, rc % CN) + (size_t)(rc / CN) * W;
           if (v < w) sU[c * kLuNB + v] = src[b0 + v];
           else sU[kLuNB * kLuNB + c] = src[p];
         }
@@ -277,7 +322,7 @@ __global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
       {
         const cplx* yb0 = cl.map_shared_rank(sU, 0) + kLuNB * kLuNB;
         for (int lr = tid; lr < R; lr += blockDim.x) {
-          const int ps = pos[rank + kCluN * lr];
+          const int ps = pos[rank + CN * lr];
           if (ps >= b0) continue;
           cplx* row = rows + (size_t)lr * W;
           cplx acc = row[p];
@@ -292,7 +337,7 @@ __global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
     cplx* A = reinterpret_cast<cplx*>(ws + L.lu);
     for (int t = tid; t < R * p; t += blockDim.x) {
       const int lr = t / p, c = t - lr * p;
-      A[(size_t)pos[rank + kCluN * lr] * p + c] = rows[(size_t)lr * W + c];
+      A[(size_t)pos[rank + CN * lr] * p + c] = rows[(size_t)lr * W + c];
     }
   }
   if (rank == 0) {
@@ -328,6 +373,62 @@ __global__ void __cluster_dims__(kCluN, 1, 1) __launch_bounds__(256)
     }
   }
   cl.sync();                                              // no CTA leaves while others read its memory
+}
+
+// Launch on a cluster of 16 CTAs where the device holds one (checked once per device), else 8.
+static void launch_cap_cluster(const CapArgs& ca, const WsLayout& L, char* ws, const uint8_t* state,
+                               const int32_t* idx, const int32_t* status, cudaStream_t st) {
+  static std::mutex mu;
+  static int cn_of[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int cn = 8;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || cn_of[dev] == 0) {
+      cudaFuncSetAttribute(k_cap_cluster<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)cap_cluster_smem(kLuMaxBlocked, 8));
+      cudaFuncSetAttribute(k_cap_cluster<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)cap_cluster_smem(kLuMaxBlocked, 16));
+      int ok16 = 0;
+      if (cudaFuncSetAttribute(k_cap_cluster<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = cap_cluster_smem(kLuMaxBlocked, 16);
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, k_cap_cluster<16>, &cfg) == cudaSuccess && nc >= 1) ok16 = 1;
+      }
+      cudaGetLastError();                                 // a refused size leaves no error behind
+      if (dev >= 0 && dev < 64) cn_of[dev] = ok16 ? 16 : 8;
+      cn = ok16 ? 16 : 8;
+    } else {
+      cn = cn_of[dev];
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cn;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)cn);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = cap_cluster_smem(L.pmax, cn);
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cn == 16)
+    cudaLaunchKernelEx(&cfg, k_cap_cluster<16>, ca, L, ws, state, idx, status);
+  else
+    cudaLaunchKernelEx(&cfg, k_cap_cluster<8>, ca, L, ws, state, idx, status);
 }
 
 // ----------------------------------------------------------------------------- panels
@@ -562,19 +663,7 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   const bool multi = a.nlam == 1 && L.pmax > kCapSmemP && L.pmax <= kLuMaxBlocked;
   const int pre = (a.nlam > 1 && L.pmax <= kCapSmemP) || multi ? 1 : 0;
   if (multi) {
-    {  // once per device
-      static std::mutex mu2;
-      static bool done2[64] = {};
-      int dev = 0;
-      cudaGetDevice(&dev);
-      std::lock_guard<std::mutex> lk(mu2);
-      if (dev < 0 || dev >= 64 || !done2[dev]) {
-        cudaFuncSetAttribute(k_cap_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)cap_cluster_smem(kLuMaxBlocked));
-        if (dev >= 0 && dev < 64) done2[dev] = true;
-      }
-    }
-    k_cap_cluster<<<kCluN, 256, cap_cluster_smem(L.pmax), st>>>(ca, L, ws, state, idx, status);
+    launch_cap_cluster(ca, L, ws, state, idx, status, st);
   } else if (pre) {
     k_capacitance_lam<<<a.nlam, 256, cap_smem, st>>>(ca, L, ws, state, idx, status);
   }
