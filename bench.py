@@ -334,7 +334,7 @@ def sched_json(s):
     return {"fused": False, "streams": s.nstreams, "order": s.order}
 
 
-def launches_per_step(s, nprob, dtype):
+def launches_per_step(s, nprob, dtype, c128_fma=False):
     """Library kernels per batched step, per group of 64 problems: persistent = the step kernel
     (complex128, or complex64 with tile_rows 0: + the G update and the bands); staged = one launch per stage (eval,
     select, capacitance, panels, [digit prep], update, finish, bands); stream branches = the
@@ -345,9 +345,9 @@ def launches_per_step(s, nprob, dtype):
         groups = max(1, s.nstreams)
         per_group = -(-nprob // groups)
         if s.form == B.GF_BATCH_PERSISTENT:
-            per = 3 if (dtype == "c128" or s.tile_rows == 0) else 1
+            per = 3 if ((dtype == "c128" and not c128_fma) or (dtype != "c128" and s.tile_rows == 0)) else 1
         else:
-            per = 8 if dtype == "c128" else 7
+            per = 8 if (dtype == "c128" and not c128_fma) else 7
         return groups * ((per_group + 63) // 64) * per
     return nprob * (9 if dtype == "c128" else 7)
 
@@ -414,7 +414,7 @@ def run_batch(args):
                        "graph": f"{args.steps} steps of all problems in one CUDA graph",
                        "l2": "inputs larger than L2 (sum of G %.1f GB)" % (sumG / 1e9)},
             "accepted_flips": flips,
-            "gpu_launches": launches_per_step(best, len(wls), dtype) * args.steps,
+            "gpu_launches": launches_per_step(best, len(wls), dtype, bo.c128_fma) * args.steps,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s", "frac": gbs / peak_hbm,
                          "traffic": None, "peak_kind": peak_kind,
                          "note": "whole step (all kernels of all problems): algorithmic G bytes / step time"},
@@ -922,6 +922,7 @@ def run_egreedy(args):
     ms = e0.elapsed_time(e1)
     enq = res.pop("_steps_enqueued")
     flips = sum(r["steps_mean"] * r["trajectories"] for r in res.values())
+    per_step = egreedy_step_forms()
     line = {"metric": METRIC + " [epsilon-greedy study, 61 trajectories batched]", "value": flips / (ms / 1e3),
             "unit": UNIT, "n_gpus": 1, "steps": int(enq), "warmup": 1, "ms_per_step": ms / max(enq, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -930,9 +931,49 @@ def run_egreedy(args):
                        "note": "ms_per_step is per batched step of all 61 trajectories"},
             "accepted_flips": int(round(flips)),
             "study": {str(e): {k: v for k, v in r.items() if k != "finals"} for e, r in res.items()},
-            "gpu_launches": int(enq) * 8, "clocks": clk}
+            "batched_step_ms_by_form": per_step,
+            "gpu_launches": int(enq) * 1, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def egreedy_step_forms(steps: int = 32):
+    """Device time of one batched step of the study's 61 problems (a graph of `steps` steps from
+    the filled start, replayed once after a warm-up replay from the same start), per fused form:
+    the persistent launch with the FP64 FMA update (the default for these small problems, one
+    launch per step), the same update in one launch per stage, and the persistent front launch
+    with the tensor-core update (three launches per step)."""
+    import torch
+    from paper_2202_05388_gb300 import gfopt as B
+    from paper_2202_05388_gb300.batch import BatchOptimizer, Schedule
+    from paper_2202_05388_gb300.egreedy import metalens_21, _seed
+
+    wl = metalens_21()
+    pols = [None] + [(eps, _seed(0, e_i, t)) for e_i, eps in enumerate((0.1, 0.2, 0.3), start=1) for t in range(20)]
+    out = {}
+    for name, algo, form in (("persistent, FP64 FMA update (1 launch)", None, B.GF_BATCH_PERSISTENT),
+                             ("staged, FP64 FMA update (7 launches)", None, B.GF_BATCH_STAGED),
+                             ("persistent, tensor-core update (3 launches)", B.GF_UPDATE_TENSOR, B.GF_BATCH_PERSISTENT)):
+        bo = BatchOptimizer([wl] * len(pols), dtype=wl.dtype, policies=pols, horizon=4 * steps + 8, update_algo=algo)
+        bo.schedule = Schedule(0, "given", True, 0, form)
+        times = []
+        for _ in range(2):
+            bo.fill()
+            bo._policy_steps.zero_()
+            bo.capture(steps)
+            bo.fill()
+            bo._policy_steps.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bo.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / steps)
+        out[name] = min(times)
+        bo.close()
+        del bo
+    return out
 
 
 def run_deferred(args):

@@ -23,6 +23,8 @@ struct gf_batch {
   int64_t widest_n, widest_N, widest_units;
   int update_ctas;
   int form;                        // GF_BATCH_PERSISTENT or GF_BATCH_STAGED
+  bool c128_fma;                   // complex128 with the FP64 FMA update (every problem small, or
+                                   // GF_UPDATE_DFMA), else the tensor-core update
   int step_ctas, scale, tile_rows; // launch shape of the persistent step (step_ctas 0: fill the GPU)
   gf::BatchPlan plan;
 };
@@ -129,7 +131,21 @@ gf_status gf_batch_create(gf_handle* h, int32_t nitems, const gf_batch_item* ite
   }
   gf_status s = gf::api_bind_device(h);
   if (s) { delete b; return s; }
+  // the update arithmetic follows the handle's setting as the single-problem calls do: GF_UPDATE_DFMA
+  // the FP64 FMA form; GF_UPDATE_TC that form when every problem is small (n^2 p_max within
+  // kC128SmallWork, where a single problem takes it too), else the tensor cores; GF_UPDATE_TENSOR
+  // the tensor cores
+  b->c128_fma = false;
   if (dtype == GF_C128) {
+    const int algo = gf::api_update_algo(h);
+    bool small = true;
+    for (int i = 0; i < nitems; ++i) {
+      const double n = (double)b->host[i].L.n;
+      small = small && n * n * b->host[i].L.pmax <= gf::kC128SmallWork;
+    }
+    b->c128_fma = algo == GF_UPDATE_DFMA || (algo == GF_UPDATE_TC && small);
+  }
+  if (dtype == GF_C128 && !b->c128_fma) {
     b->oz_params = ::operator new(gf::ozaki_batch_params_bytes(), std::align_val_t(64), std::nothrow);
     if (!b->oz_params) { delete b; return bfail(h, GF_ENOMEM, "out of host memory"); }
     if (!gf::ozaki_batch_params(b->oz_params, b->host.data(), nitems)) {
@@ -138,7 +154,7 @@ gf_status gf_batch_create(gf_handle* h, int32_t nitems, const gf_batch_item* ite
       return bfail(h, GF_ECUDA, "cannot encode the TMA descriptors of the batch (driver entry point missing)");
     }
   }
-  gf::build_batch_plan(b->plan, b->host.data(), nitems, dtype, *spec, b->scale, b->tile_rows);
+  gf::build_batch_plan(b->plan, b->host.data(), nitems, dtype, *spec, b->scale, b->tile_rows, b->c128_fma);
   b->plan.items = b->table;
   b->plan.sync = reinterpret_cast<gf::BatchSync*>(reinterpret_cast<char*>(table) + items_bytes(nitems));
   cudaStream_t st = (cudaStream_t)stream;
@@ -173,7 +189,7 @@ gf_status gf_batch_set_form(gf_batch* b, int32_t form, int32_t step_ctas, int32_
   b->scale = scale;
   b->tile_rows = tile_rows;
   gf::BatchPlan P;
-  gf::build_batch_plan(P, b->host.data(), b->nitems, b->dtype, b->spec, scale, tile_rows);
+  gf::build_batch_plan(P, b->host.data(), b->nitems, b->dtype, b->spec, scale, tile_rows, b->c128_fma);
   P.items = b->plan.items;
   P.sync = b->plan.sync;
   b->plan = P;
@@ -184,7 +200,7 @@ static void persistent_step(gf_batch* b, const gf::BatchPlan& plan, cudaStream_t
   const int sms = gf::api_sm_count(b->h);
   const int ctas = b->step_ctas > 0 ? b->step_ctas : sms * gf::batch_step_ctas_per_sm(b->tile_rows, b->spec.kind);
   gf::launch_batch_step(plan, ctas, b->tile_rows, st);
-  if (b->dtype == GF_C128) {
+  if (b->dtype == GF_C128 && !b->c128_fma) {
     gf::launch_rank_update_ozaki_batch(b->oz_params, b->update_ctas > 0 ? b->update_ctas : sms, st);
     gf::launch_bands_batch(b->table, b->nitems, b->dtype, b->widest_N, st);
   } else if (b->tile_rows == 0) {
@@ -221,7 +237,9 @@ gf_status gf_batch_step(gf_batch* b, void* stream) {
   gf::launch_select_batch(b->table, n, b->spec.tie_rel, st);
   gf::launch_capacitance_batch(b->table, n, b->dtype, b->spec, st);
   gf::launch_panels_batch(b->table, n, b->dtype, b->widest_n, st);
-  if (b->dtype == GF_C128) {
+  if (b->dtype == GF_C128 && b->c128_fma) {
+    gf::launch_rank_update_f64_batch(b->table, n, b->widest_n, st);
+  } else if (b->dtype == GF_C128) {
     gf::launch_oz_prep_batch(b->table, n, b->widest_n, st);
     gf::launch_rank_update_ozaki_batch(b->oz_params, b->update_ctas > 0 ? b->update_ctas : sms, st);
   } else {

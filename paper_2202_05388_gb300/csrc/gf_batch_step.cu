@@ -7,9 +7,10 @@
 //
 // complex64 runs the whole step in this launch (evaluation, selection + capacitance, panels, the
 // FP32 G update in R x 512 tiles, field/FOM, bands), or everything up to the field/FOM with the
-// update and the bands as their own launches.  complex128 runs evaluation .. digit-operand
-// preparation and the field/FOM; the warp-specialised tensor-core update and the bands follow as
-// their own launches.
+// update and the bands as their own launches.  complex128 with small problems runs the whole step
+// too, its G update the FP64 FMA form in 64 x 256 tiles; otherwise evaluation .. digit-operand
+// preparation and the field/FOM, the warp-specialised tensor-core update and the bands following
+// as their own launches.
 #include <math.h>
 
 #include <algorithm>
@@ -156,7 +157,16 @@ __global__ void __launch_bounds__(kBatchThreads, kBrush ? 1 : 2) k_batch_step(co
           char* ws = it.ws;
           const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + it.L.ctl);
           const int p = ctl->skip ? 0 : ctl->nv;
-          if (p >= 1 && p <= kC64Fp32MaxP) {
+          if (P.dtype == GF_C128) {
+            if (p >= 1) {
+              const int64_t n = it.L.n, nct = (n + 255) / 256, nt = ((n + kF64BatchRows - 1) / kF64BatchRows) * nct;
+              double2* G = reinterpret_cast<double2*>(it.G);
+              const cplx* C0 = reinterpret_cast<const cplx*>(ws + it.L.C0);
+              const cplx* S = reinterpret_cast<const cplx*>(ws + it.L.S);
+              for (int64_t tile = vb * P.upd_tiles; tile < (vb + 1) * P.upd_tiles && tile < nt; ++tile)
+                f64_update_tile(G, it.ldg, n, it.L.pmax, p, C0, S, tile / nct, tile % nct);
+            }
+          } else if (p >= 1 && p <= kC64Fp32MaxP) {
             const int64_t n = it.L.n, nct = (n + kF32Cols - 1) / kF32Cols, nt = ((n + R - 1) / R) * nct;
             const int pmax = it.L.pmax;
             float2* G = reinterpret_cast<float2*>(it.G);
@@ -201,7 +211,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBrush ? 1 : 2) k_batch_step(co
 static int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 void build_batch_plan(BatchPlan& P, const BatchItem* host_items, int nprob, int dtype, const gf_cand_spec& spec,
-                      int scale, int rows) {
+                      int scale, int rows, bool c128_fma) {
   P = BatchPlan{};
   P.nprob = nprob;
   P.dtype = dtype;
@@ -212,7 +222,12 @@ void build_batch_plan(BatchPlan& P, const BatchItem* host_items, int nprob, int 
   P.timeout_ns = 2000000000ll;
   P.stall_q = -1;
   P.upd_tiles = scale;
-  if (dtype == GF_C128) {
+  if (dtype == GF_C128 && c128_fma) {      // the whole step, the FP64 FMA update in the launch
+    const int32_t st[] = {kStEval, kStSelCap, kStPanels, kStUpdate, kStFinish, kStBands};
+    const int32_t dp[] = {-1, 0, 1, 2, 2, 3};
+    P.nstage = 6;
+    for (int s = 0; s < P.nstage; ++s) { P.stage[s] = st[s]; P.dep[s] = dp[s]; }
+  } else if (dtype == GF_C128) {
     const int32_t st[] = {kStEval, kStSelCap, kStPanels, kStPrep, kStFinish};
     const int32_t dp[] = {-1, 0, 1, 2, 2};
     P.nstage = 5;
@@ -247,7 +262,10 @@ void build_batch_plan(BatchPlan& P, const BatchItem* host_items, int nprob, int 
         case kStSelCap: c = 1; break;
         case kStPanels: c = cdiv64(n, per); break;
         case kStPrep: c = cdiv64(std::max(cdiv64(n, kOzM) * kOzM, cdiv64(2 * n, kOzN) * (kOzN / 2)), per); break;
-        case kStUpdate: c = cdiv64(cdiv64(n, rows) * cdiv64(n, kF32Cols), P.upd_tiles); break;
+        case kStUpdate:
+          c = dtype == GF_C128 ? cdiv64(cdiv64(n, kF64BatchRows) * cdiv64(n, 256), P.upd_tiles)
+                               : cdiv64(cdiv64(n, rows) * cdiv64(n, kF32Cols), P.upd_tiles);
+          break;
         case kStFinish: c = cdiv64(n, per); break;
         case kStBands: c = cdiv64((int64_t)GF_NBANDS * N, per); break;
         default: break;

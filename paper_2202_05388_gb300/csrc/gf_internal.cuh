@@ -28,6 +28,10 @@ __host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
   double d = 1.0 / abs2(b);
   return {(a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d};
 }
+// cdiv with the reciprocal d = 1 / |b|^2 formed beforehand (the same bits as cdiv(a, b))
+__host__ __device__ __forceinline__ cplx cdiv_r(cplx a, cplx b, double d) {
+  return {(a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d};
+}
 // acc + a*b with fused multiply-adds
 __device__ __forceinline__ cplx cfma(cplx a, cplx b, cplx acc) {
   acc.re = fma(a.re, b.re, acc.re);
@@ -363,6 +367,10 @@ void launch_rank_update_c64_fp32_batch(const BatchItem* items, int nprob, int ct
 void launch_rank_update_c64_fp32(float2* G, int64_t ldg, int64_t n, int64_t rows, int pmax, const cplx* C0, const cplx* S,
                                  const UpdCtl* ctl, int32_t* prof_p, int ctas, cudaStream_t st);
 constexpr int kC64Fp32MaxP = 4;
+// complex128: n^2 p_max below which the FP64 FMA update beats the tensor-core pipeline's fixed cost
+// (G resident in L2; 32x32 single pixel: 19 vs 44 us)
+constexpr double kC128SmallWork = 2.5e6;
+void launch_rank_update_f64_batch(const BatchItem* items, int nprob, int64_t widest_n, cudaStream_t st);
 // complex128 rank <= 4 update on the tensor cores for a whole batch: the operand preparation
 // of every problem, then one persistent launch over all problems' tiles.  The parameter block
 // (tensor maps and descriptors) is built once per batch by ozaki_batch_params.
@@ -381,9 +389,9 @@ enum BatchStage : int32_t {
   kStSelCap,       // selection, then the capacitance solve (one CTA)
   kStPanels,       // C0 = G[:, V], S = D A^-1 G[V, :]
   kStPrep,         // complex128: digit operands of the tensor-core update
-  kStUpdate,       // complex64: G += C0 S in FP32 (tiles of R x 512)
+  kStUpdate,       // G += C0 S: complex64 in FP32 (tiles of R x 512), complex128 in FP64 FMA (64 x 256)
   kStFinish,       // E, state, FOM
-  kStBands,        // complex64: bands of the new G
+  kStBands,        // bands of the new G (when the update runs in the launch)
 };
 constexpr int kPlanStages = 6;
 constexpr int kBatchThreads = 256;
@@ -413,8 +421,9 @@ struct BatchPlan {                          // built on the host, passed by valu
 // tensor-core update and the bands follow as their own launches); complex64 runs the whole step.
 // scale: candidates / rows per thread and item; rows: row tile of the complex64 update (16, 32, 64;
 // 0: the complex64 update and bands run as their own launches)
+// c128_fma: complex128 with the FP64 FMA update stage in the persistent launch (small problems)
 void build_batch_plan(BatchPlan& P, const BatchItem* host_items, int nprob, int dtype, const gf_cand_spec& spec,
-                      int scale, int rows);
+                      int scale, int rows, bool c128_fma);
 int batch_step_ctas_per_sm(int rows, int kind);
 void launch_batch_step(const BatchPlan& P, int ctas, int rows, cudaStream_t st);
 

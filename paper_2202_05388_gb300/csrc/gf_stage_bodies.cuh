@@ -447,7 +447,6 @@ struct CapArgs {
 constexpr int kLuNB = 8;
 constexpr int kLuMaxBlocked = 256;
 constexpr int kCapSmemP = 64;          // capacitance systems up to this size in shared memory (64 KB)
-constexpr double kC128SmallWork = 2.5e6;   // n^2 p_max below which the FP64 FMA update is faster
 
 // sP: shared memory for kLuMaxBlocked x kLuNB entries (the panel, row-major [row][j])
 inline __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ piv, double thresh, cplx* sP) {
@@ -953,6 +952,55 @@ __device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L,
         for (int u = 0; u < p; ++u) S[(int64_t)u * n + j] = dchi[u] * S[(int64_t)u * n + j];
       }
     }
+  }
+}
+
+// complex128, the FP64 FMA update of column j for rows [i0, i1): G[i, j] += sum_u C0[i, u] S[u, j]
+// in the order of k_rank_update_f64 (the same bits).  P > 0: compile-time rank; P == 0: runtime p.
+template <int P>
+__device__ __forceinline__ void f64_update_rows(double2* G, int64_t ldg, int64_t n, int64_t i0, int64_t i1, int pmax,
+                                                int p, const cplx* C0, const cplx* S, int64_t j) {
+  cplx s[P > 0 ? P : 1];
+  if (P > 0) {
+#pragma unroll
+    for (int u = 0; u < P; ++u) s[u] = S[(int64_t)u * n + j];
+  }
+  // eight rows' loads in flight before their arithmetic (one row at a time, each thread waited a
+  // full memory latency per row)
+  constexpr int U = 8;
+  for (int64_t i = i0; i < i1; i += U) {
+    double2 g[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q)
+      if (i + q < i1) g[q] = G[(i + q) * ldg + j];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (i + q < i1) {
+        const int64_t r = i + q;
+        cplx acc = mk(g[q].x, g[q].y);
+        if (P > 0) {
+#pragma unroll
+          for (int u = 0; u < P; ++u) acc = cfma(C0[r * pmax + u], s[u], acc);
+        } else {
+          for (int u = 0; u < p; ++u) acc = cfma(C0[r * pmax + u], S[(int64_t)u * n + j], acc);
+        }
+        G[r * ldg + j] = make_double2(acc.re, acc.im);
+      }
+    }
+  }
+}
+constexpr int kF64BatchRows = 64;                 // rows of one batched FP64 update tile (x 256 columns)
+__device__ __forceinline__ void f64_update_tile(double2* G, int64_t ldg, int64_t n, int pmax, int p, const cplx* C0,
+                                                const cplx* S, int64_t rt, int64_t ct) {
+  const int64_t j = ct * 256 + threadIdx.x;       // 256 threads: one column each
+  if (j >= n || threadIdx.x >= 256) return;
+  const int64_t i0 = rt * kF64BatchRows, i1 = i0 + kF64BatchRows < n ? i0 + kF64BatchRows : n;
+  switch (p) {
+    case 1: f64_update_rows<1>(G, ldg, n, i0, i1, pmax, p, C0, S, j); break;
+    case 2: f64_update_rows<2>(G, ldg, n, i0, i1, pmax, p, C0, S, j); break;
+    case 3: f64_update_rows<3>(G, ldg, n, i0, i1, pmax, p, C0, S, j); break;
+    case 4: f64_update_rows<4>(G, ldg, n, i0, i1, pmax, p, C0, S, j); break;
+    default: f64_update_rows<0>(G, ldg, n, i0, i1, pmax, p, C0, S, j); break;
   }
 }
 

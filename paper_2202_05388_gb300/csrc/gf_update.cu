@@ -91,21 +91,21 @@ __device__ __forceinline__ long long clu_key(double v) {
 __device__ __forceinline__ bool clu_better(long long k, int ps, long long bk, int bps) {
   return k > bk || (k == bk && ps < bps);
 }
-// the CTA's best of its warps' candidates into its slot, with the reciprocal the multipliers use
-// (formed here, before the cluster barrier, as the one-CTA factorisation forms it: conj(pv) / |pv|^2)
-__device__ __forceinline__ void clu_publish(long long* wk, int* wr, cplx* wa, int nw, CluSlot& slot) {
+// conj(a) / |a|^2 with the pivot reciprocal of the one-CTA factorisation (0 for no candidate);
+// each warp forms it for its own best candidate, so the reciprocals of a column run side by side
+__device__ __forceinline__ cplx clu_inv(long long key, cplx a) {
+  if (key <= 0) return mk(0.0, 0.0);
+  const double d = rcp_nr(__longlong_as_double(key));
+  return mk(a.re * d, -a.im * d);
+}
+// the CTA's best of its warps' candidates (with their reciprocals) into its slot
+__device__ __forceinline__ void clu_publish(const long long* wk, const int* wr, const cplx* wi, int nw, CluSlot& slot) {
   int b = 0;
   for (int w = 1; w < nw; ++w)
     if (clu_better(wk[w], wr[w], wk[b], wr[b])) b = w;
   slot.key = wk[b];
   slot.pos = wr[b];
-  if (wk[b] > 0) {
-    const cplx pv = wa[b];
-    const double d = rcp_nr(__longlong_as_double(wk[b]));
-    slot.inv = mk(pv.re * d, -pv.im * d);
-  } else {
-    slot.inv = mk(0.0, 0.0);
-  }
+  slot.inv = wi[b];
 }
 __host__ __device__ constexpr size_t cap_cluster_smem(int pmax, int cn) {
   // rows (R x (pmax + 1)) | pivot row (pmax + 1) | block of the upper solve (kLuNB x kLuNB + kLuNB)
@@ -135,6 +135,9 @@ __global__ void __launch_bounds__(256)
   __shared__ long long s_wk[8];
   __shared__ int s_wr[8];
   __shared__ cplx s_wa[8];
+  __shared__ cplx s_l[kLuMaxBlocked / 8];                 // the column's multipliers, by local row
+  __shared__ double s_dv[kLuMaxBlocked / 8];              // 1 / |u_cc|^2 of the CTA's rows (upper solve)
+  __shared__ double s_db[kLuNB];                          // CTA 0: those of the current block
   __shared__ double s_thr, s_rmax;
   __shared__ int s_nv, s_pr, s_bad;
   __shared__ cplx s_inv;
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(256)
     const double ore = __shfl_down_sync(0xffffffffu, ba.re, o), oim = __shfl_down_sync(0xffffffffu, ba.im, o);
     if (clu_better(ok, op, bk, bp)) { bk = ok; bp = op; ba = mk(ore, oim); }
   }
-  if (lane == 0) { s_wk[wid] = bk; s_wr[wid] = bp; s_wa[wid] = ba; s_red[wid] = rmax; }
+  if (lane == 0) { s_wk[wid] = bk; s_wr[wid] = bp; s_wa[wid] = clu_inv(bk, ba); s_red[wid] = rmax; }
   __syncthreads();
   if (tid == 0) {
     double m = 0.0;
@@ -267,45 +270,77 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const cplx inv = s_inv;
-    // elimination, a warp per row (y included); lane 0 keeps the rows' candidates of column j + 1
-    bk = -1;
-    bp = 0x7fffffff;
-    ba = mk(0.0, 0.0);
-    for (int lr = wid; lr < R; lr += nw) {
-      const int ps = pos[rank + CN * lr];
-      if (ps <= j) continue;
-      cplx* row = rows + (size_t)lr * W;
-      const cplx l = row[j] * inv;
-      __syncwarp();
-      for (int k = j + 1 + lane; k < W; k += 32) row[k] = cfms(l, prow[k], row[k]);
-      if (lane == 0) {
-        row[j] = l;
+    // the multipliers, warp 0 with a lane per row (one FP64 pass for all rows of the CTA)
+    if (wid == 0)
+      for (int lr = lane; lr < R; lr += 32)
+        if (pos[rank + CN * lr] > j) {
+          const cplx l = rows[(size_t)lr * W + j] * inv;
+          rows[(size_t)lr * W + j] = l;
+          s_l[lr] = l;
+        }
+    __syncthreads();
+    if (wid == 0) {
+      // column j + 1 of every row first (lane per row), then its candidates and the winner's
+      // reciprocal -- the chain to the next barrier -- while warps 1.. eliminate the rest
+      bk = -1;
+      bp = 0x7fffffff;
+      ba = mk(0.0, 0.0);
+      for (int lr = lane; lr < R; lr += 32) {
+        const int ps = pos[rank + CN * lr];
+        if (ps <= j) continue;
+        cplx* row = rows + (size_t)lr * W;
+        const cplx a1 = cfms(s_l[lr], prow[j + 1], row[j + 1]);
+        row[j + 1] = a1;
         if (j + 1 < p) {
-          const cplx a1 = row[j + 1];
           const long long k1 = clu_key(abs2(a1));
           if (clu_better(k1, ps, bk, bp)) { bk = k1; bp = ps; ba = a1; }
         }
       }
-      __syncwarp();
+      if (j + 1 < p) {
+        for (int o = 16; o > 0; o >>= 1) {
+          const long long ok = __shfl_down_sync(0xffffffffu, bk, o);
+          const int op = __shfl_down_sync(0xffffffffu, bp, o);
+          const double ore = __shfl_down_sync(0xffffffffu, ba.re, o), oim = __shfl_down_sync(0xffffffffu, ba.im, o);
+          if (clu_better(ok, op, bk, bp)) { bk = ok; bp = op; ba = mk(ore, oim); }
+        }
+        if (lane == 0) {
+          s_slot[buf ^ 1].key = bk;
+          s_slot[buf ^ 1].pos = bp;
+          s_slot[buf ^ 1].inv = clu_inv(bk, ba);
+        }
+      }
+    } else if (wid & 3) {
+      // columns j + 2 .. W - 1 (y included), a row per warp; the warps that share warp 0's
+      // scheduler (wid % 4 == 0) stay out, so that its chain does not queue behind them
+      const int bw = wid - 1 - (wid >> 2), nb = nw - (nw + 3) / 4;
+      for (int lr = bw; lr < R; lr += nb) {
+        if (pos[rank + CN * lr] <= j) continue;
+        cplx* __restrict__ row = rows + (size_t)lr * W;
+        const cplx* __restrict__ pv = prow;
+        const cplx l = s_l[lr];
+#pragma unroll 4
+        for (int k = j + 2 + lane; k < W; k += 32) row[k] = cfms(l, pv[k], row[k]);
+      }
     }
-    if (lane == 0) { s_wk[wid] = bk; s_wr[wid] = bp; s_wa[wid] = ba; }
     __syncthreads();
-    if (tid == 0 && j + 1 < p) clu_publish(s_wk, s_wr, s_wa, nw, s_slot[buf ^ 1]);
   }
   const bool bad = s_bad != 0;
   // ---- upper solve in blocks of kLuNB rows from the bottom (CTA 0 solves each block's triangle)
   if (!bad) {
+    // the diagonal's reciprocals 1 / |u_cc|^2, every row at once (as cdiv forms them)
+    for (int lr = tid; lr < R; lr += blockDim.x) s_dv[lr] = 1.0 / abs2(rows[(size_t)lr * W + pos[rank + CN * lr]]);
     for (int b1 = p; b1 > 0; b1 -= kLuNB) {
       const int b0 = b1 - kLuNB > 0 ? b1 - kLuNB : 0;
       const int w = b1 - b0;
-      cl.sync();                                          // the block's y are final
+      cl.sync();                                          // the block's y (and the reciprocals) are final
       if (rank == 0) {
-        for (int t = tid; t < w * (w + 1); t += blockDim.x) {
-          const int c = t / (w + 1), v = t - c * (w + 1);  // v = w: y
+        for (int t = tid; t < w * (w + 2); t += blockDim.x) {
+          const int c = t / (w + 2), v = t - c * (w + 2);  // v = w: y, v = w + 1: the reciprocal
           const int rc = phys[b0 + c];
           const cplx* src = cl.map_shared_rank(rows, rc % CN) + (size_t)(rc / CN) * W;
           if (v < w) sU[c * kLuNB + v] = src[b0 + v];
-          else sU[kLuNB * kLuNB + c] = src[p];
+          else if (v == w) sU[kLuNB * kLuNB + c] = src[p];
+          else s_db[c] = *cl.map_shared_rank(&s_dv[rc / CN], rc % CN);
         }
         __syncthreads();
         if (tid == 0) {
@@ -313,7 +348,7 @@ __global__ void __launch_bounds__(256)
           for (int c = w - 1; c >= 0; --c) {
             cplx acc = yb[c];
             for (int v = c + 1; v < w; ++v) acc = acc - sU[c * kLuNB + v] * yb[v];
-            yb[c] = cdiv(acc, sU[c * kLuNB + c]);
+            yb[c] = cdiv_r(acc, sU[c * kLuNB + c], s_db[c]);
             yfin[b0 + c] = yb[c];
           }
         }
@@ -321,12 +356,17 @@ __global__ void __launch_bounds__(256)
       cl.sync();                                          // the block's solution is in CTA 0
       {
         const cplx* yb0 = cl.map_shared_rank(sU, 0) + kLuNB * kLuNB;
+        cplx ybl[kLuNB];
+#pragma unroll
+        for (int v = 0; v < kLuNB; ++v) ybl[v] = v < w ? yb0[v] : mk(0.0, 0.0);
         for (int lr = tid; lr < R; lr += blockDim.x) {
           const int ps = pos[rank + CN * lr];
           if (ps >= b0) continue;
           cplx* row = rows + (size_t)lr * W;
           cplx acc = row[p];
-          for (int v = 0; v < w; ++v) acc = acc - row[b0 + v] * yb0[v];
+#pragma unroll
+          for (int v = 0; v < kLuNB; ++v)
+            if (v < w) acc = acc - row[b0 + v] * ybl[v];
           row[p] = acc;
         }
       }
@@ -451,16 +491,26 @@ __device__ __forceinline__ void rank_update_f64_body(double2* __restrict__ G, in
   }
   for (int64_t i0 = (int64_t)blockIdx.y * kUpdRows; i0 < rows; i0 += (int64_t)gridDim.y * kUpdRows) {
     const int64_t iend = i0 + kUpdRows < rows ? i0 + kUpdRows : rows;
-    for (int64_t i = i0; i < iend; ++i) {
-      double2 g = G[i * ldg + j];
-      cplx acc = mk(g.x, g.y);
-      if (P > 0) {
+    constexpr int U = 8;                         // eight rows' loads in flight before their arithmetic
+    for (int64_t i = i0; i < iend; i += U) {
+      double2 g[U];
 #pragma unroll
-        for (int u = 0; u < P; ++u) acc = cfma(C0[i * pmax + u], s[u], acc);
-      } else {
-        for (int u = 0; u < p; ++u) acc = cfma(C0[i * pmax + u], S[(int64_t)u * n + j], acc);
+      for (int q = 0; q < U; ++q)
+        if (i + q < iend) g[q] = G[(i + q) * ldg + j];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (i + q < iend) {
+          const int64_t r = i + q;
+          cplx acc = mk(g[q].x, g[q].y);
+          if (P > 0) {
+#pragma unroll
+            for (int u = 0; u < P; ++u) acc = cfma(C0[r * pmax + u], s[u], acc);
+          } else {
+            for (int u = 0; u < p; ++u) acc = cfma(C0[r * pmax + u], S[(int64_t)u * n + j], acc);
+          }
+          G[r * ldg + j] = make_double2(acc.re, acc.im);
+        }
       }
-      G[i * ldg + j] = make_double2(acc.re, acc.im);
     }
   }
 }
@@ -559,6 +609,25 @@ __global__ void __launch_bounds__(kF32Threads, 3) k_rank_update_c64_fp32_batch(c
 void launch_rank_update_c64_fp32(float2* G, int64_t ldg, int64_t n, int64_t rows, int pmax, const cplx* C0, const cplx* S,
                                  const UpdCtl* ctl, int32_t* prof_p, int ctas, cudaStream_t st) {
   k_rank_update_c64_fp32<<<ctas, kF32Threads, 0, st>>>(G, ldg, n, rows, pmax, C0, S, ctl, prof_p);
+}
+
+// Batched complex128 FP64 FMA update (small problems): blockIdx.z selects the problem.
+__global__ void __launch_bounds__(256) k_rank_update_f64_batch(const BatchItem* __restrict__ items) {
+  const BatchItem& it = items[blockIdx.z];
+  const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(it.ws + it.L.ctl);
+  const int p = ctl->skip ? 0 : ctl->nv;
+  const int64_t n = it.L.n;
+  if (p < 1 || (int64_t)blockIdx.x * 256 >= n) return;
+  for (int64_t rt = blockIdx.y; rt * kF64BatchRows < n; rt += gridDim.y)
+    f64_update_tile(reinterpret_cast<double2*>(it.G), it.ldg, n, it.L.pmax, p,
+                    reinterpret_cast<const cplx*>(it.ws + it.L.C0), reinterpret_cast<const cplx*>(it.ws + it.L.S), rt,
+                    blockIdx.x);
+}
+
+void launch_rank_update_f64_batch(const BatchItem* items, int nprob, int64_t widest_n, cudaStream_t st) {
+  int64_t rt = (widest_n + kF64BatchRows - 1) / kF64BatchRows;
+  if (rt > 65535) rt = 65535;
+  k_rank_update_f64_batch<<<dim3((unsigned)((widest_n + 255) / 256), (unsigned)rt, (unsigned)nprob), 256, 0, st>>>(items);
 }
 
 void launch_rank_update_c64_fp32_batch(const BatchItem* items, int nprob, int ctas, cudaStream_t st) {

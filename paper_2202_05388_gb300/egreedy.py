@@ -47,8 +47,8 @@ def egreedy_study(epsilons: Sequence[float] = (0.0, 0.1, 0.2, 0.3), trajectories
                   max_steps: int = 4000, device: int = 0, update_algo: Optional[int] = None) -> Dict[float, dict]:
     """Final-FOM statistics per epsilon over seeded trajectories (epsilon = 0 is the greedy
     policy; its trajectories are all the same).  update_algo: the G update's arithmetic
-    (gf_set_update_algo; the library default when None -- GF_UPDATE_TENSOR gives the fused
-    batch's arithmetic exactly)."""
+    (gf_set_update_algo; the library default when None, which for these small problems is the
+    FP64 FMA form -- the fused batch's arithmetic exactly)."""
     wl = metalens_21()
     out = {}
     for e_i, eps in enumerate(epsilons):

@@ -49,11 +49,12 @@ def _pattern(opt, seed):
 
 def _check_against_single_runs(wls, bo, total, dtype, oracle, patterned=False, start=None):
     """Each problem of the batch against its own single-problem run with the batch's update
-    arithmetic (the tensor-core forms at every size, GF_UPDATE_TENSOR, on every schedule)."""
+    arithmetic (the same on every schedule: the FP64 FMA form for these small complex128
+    problems by default, or the tensor-core forms)."""
     improved = 0
     for b, (wl, opt) in enumerate(zip(wls, bo.opts)):
         ref = GreedyOptimizer(wl.geoms, wl.spec, dtype=dtype)
-        ref.h.gf_set_update_algo(B.GF_UPDATE_TENSOR)
+        ref.h.gf_set_update_algo(bo.update_algo)
         ref.fill()
         if patterned:
             _pattern(ref, 100 + b)
@@ -80,7 +81,8 @@ def _check_against_single_runs(wls, bo, total, dtype, oracle, patterned=False, s
 PERSIST, STAGED = B.GF_BATCH_PERSISTENT, B.GF_BATCH_STAGED
 
 
-@pytest.mark.parametrize("sch", [Schedule(0, "given", True), Schedule(0, "given", True, 5), Schedule(3, "given", True),
+@pytest.mark.parametrize("sch", [Schedule(0, "given", True), Schedule(0, "given", True, 0, PERSIST, 0, 2),
+                                 Schedule(3, "given", True),
                                  Schedule(0, "given", True, 0, STAGED), Schedule(3, "given", True, 0, STAGED),
                                  # one CTA takes every item in queue order (no wait can block), a few
                                  # CTAs wait on one another, work items of 4 and 16 units per thread
@@ -90,6 +92,7 @@ PERSIST, STAGED = B.GF_BATCH_PERSISTENT, B.GF_BATCH_STAGED
 def test_graph_batch_matches_single_problem_runs_and_oracle(sch):
     wls = _small_batch()
     bo = BatchOptimizer(wls)
+    assert bo.c128_fma                          # small problems: the FP64 FMA update in the batch
     bo.schedule = sch
     bo.fill()
     steps = 3
@@ -226,3 +229,19 @@ def test_persistent_step_bounded_wait_reports_timeout():
     bo.replay()
     torch.cuda.synchronize()
     _check_against_single_runs(wls, bo, 3, "c128", oracle=False)
+
+
+@pytest.mark.parametrize("sch", [Schedule(0, "given", True), Schedule(0, "given", True, 5), Schedule(3, "given", True),
+                                 Schedule(0, "given", True, 0, STAGED), Schedule(0, "given", True, 0, PERSIST, 3)])
+def test_tensor_core_batch_update_matches_single_runs_and_oracle(sch):
+    """The same small batch with the tensor-core update forced (GF_UPDATE_TENSOR): the persistent
+    front launch + the batched tensor-core update + the bands, or the staged launches."""
+    wls = _small_batch()
+    bo = BatchOptimizer(wls, update_algo=B.GF_UPDATE_TENSOR)
+    assert not bo.c128_fma
+    bo.schedule = sch
+    bo.fill()
+    bo.capture(3)
+    bo.replay()
+    torch.cuda.synchronize()
+    _check_against_single_runs(wls, bo, 4, "c128", oracle=True)

@@ -108,7 +108,7 @@ def test_batched_egreedy_matches_single_problem_runs():
     total = 1 + 8
     for pol, opt in zip(pols, bo.opts):
         ref = GreedyOptimizer(wl.geoms, wl.spec)
-        ref.h.gf_set_update_algo(B.GF_UPDATE_TENSOR)      # the fused batch's update arithmetic
+        ref.h.gf_set_update_algo(bo.update_algo)          # the fused batch's update arithmetic
         ref.fill()
         if pol is not None:
             ref.set_egreedy(pol[0], seed=pol[1], horizon=64)
@@ -122,7 +122,7 @@ def test_batched_egreedy_matches_single_problem_runs():
 
 def test_batched_study_equals_sequential_study():
     from paper_2202_05388_gb300.egreedy import egreedy_study_batched
-    a = egreedy_study(epsilons=(0.0, 0.3), trajectories=3, seed=4, max_steps=3000, update_algo=B.GF_UPDATE_TENSOR)
+    a = egreedy_study(epsilons=(0.0, 0.3), trajectories=3, seed=4, max_steps=3000, update_algo=B.GF_UPDATE_TC)
     b = egreedy_study_batched(epsilons=(0.0, 0.3), trajectories=3, seed=4, max_steps=3000)
     for e in (0.0, 0.3):
         assert np.allclose(a[e]["finals"], b[e]["finals"], rtol=1e-12, atol=0), e
