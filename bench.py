@@ -128,8 +128,8 @@ class ClockSampler:
 # only for the kernel source it was taken on (SHA-256 over the files below), otherwise null.
 TRAFFIC_SOURCES = ("paper_2202_05388_gb300/csrc/gf_update_tc.cu", "paper_2202_05388_gb300/csrc/gf_tc.cuh")
 TRAFFIC = {
-    "brush_192x192_p4_c128": {"sha256": "d2504f1291297eaa6e03c30152043e4e70babbf4718feebb7524707343b55abe",
-                              "capture_n": 16385, "capture_bytes": 4.3148e9 + 4.2402e9, "n": 36865,
+    "brush_192x192_p4_c128": {"sha256": "6c1886356d87ea31483e27df8969e62f0a796bacaa4abd80518d8267bed4315a",
+                              "capture_n": 16385, "capture_bytes": 4.3147e9 + 4.2401e9, "n": 36865,
                               "profile": "profiles/rank_update_tc_brush128_traffic.md"},
 }
 
@@ -899,8 +899,8 @@ def run_native(args):
 def run_egreedy(args):
     """Sec. V exploration study on the 21x21 metalens analogue: the greedy trajectory and
     20 seeded epsilon-greedy trajectories for each of epsilon = 0.1, 0.2, 0.3, every one run to
-    termination, all 61 as problems of one fused batch (one launch per stage of the step, 32
-    steps per CUDA graph replay).  Reported: accepted flips per second over the whole study
+    termination, all 61 as problems of one fused batch (the persistent step kernel, one launch
+    per step, 32 steps per CUDA graph replay).  Reported: accepted flips per second over the whole study
     (device-timed) and the final-FOM statistics per epsilon."""
     import torch
     from paper_2202_05388_gb300 import build as BLD

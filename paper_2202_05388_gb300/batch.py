@@ -50,23 +50,22 @@ class BatchOptimizer:
         """policies: per problem None (greedy) or (epsilon, seed) for the epsilon-greedy policy;
         epsilon-greedy batches run on the fused schedule only (its device step counters keep
         drawing new uniforms across graph replays).  update_algo: the G update's arithmetic for
-        every schedule (default: the FP64 FMA form where every complex128 problem is small,
-        n^2 p_max <= 2.5e6, which is also the single-problem choice there, else the tensor-core
-        forms at every size)."""
+        every schedule (default: the FP64 FMA form where the complex128 batch is small, the sum
+        of n^2 p_max within 2.5e6 -- each problem alone then takes that form too -- else the
+        tensor-core forms at every size)."""
         self.device = torch.device("cuda", device)
         self.h = B.Handle(device)
         self.workloads = list(workloads)
         # every schedule (fused launches or per-problem stream branches) updates G with the same
         # arithmetic, so that the autotuner's choice of schedule cannot change a single bit of the
         # results
+        work = sum((w.geoms[0].N + 1) ** 2 * (1 if w.spec.kind == B.GF_KIND_SINGLE else 4) * max(1, w.spec.k)
+                   for w in self.workloads)
         if update_algo is None:
-            small = all((w.geoms[0].N + 1) ** 2 * (1 if w.spec.kind == B.GF_KIND_SINGLE else 4) * max(1, w.spec.k)
-                        <= 2.5e6 for w in self.workloads)
-            update_algo = B.GF_UPDATE_TC if (dtype == "c128" and small) else B.GF_UPDATE_TENSOR
+            update_algo = B.GF_UPDATE_TC if (dtype == "c128" and work <= 2.5e6) else B.GF_UPDATE_TENSOR
         self.update_algo = update_algo
-        self.c128_fma = dtype == "c128" and (update_algo == B.GF_UPDATE_DFMA or (
-            update_algo == B.GF_UPDATE_TC and all((w.geoms[0].N + 1) ** 2 * (1 if w.spec.kind == B.GF_KIND_SINGLE else 4)
-                                                  * max(1, w.spec.k) <= 2.5e6 for w in self.workloads)))
+        self.c128_fma = dtype == "c128" and (update_algo == B.GF_UPDATE_DFMA or
+                                             (update_algo == B.GF_UPDATE_TC and work <= 2.5e6))
         self.h.gf_set_update_algo(update_algo)
         self.opts = [GreedyOptimizer(w.geoms, w.spec, dtype=dtype, device=device, handle=self.h)
                      for w in self.workloads]

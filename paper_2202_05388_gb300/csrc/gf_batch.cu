@@ -131,19 +131,19 @@ gf_status gf_batch_create(gf_handle* h, int32_t nitems, const gf_batch_item* ite
   }
   gf_status s = gf::api_bind_device(h);
   if (s) { delete b; return s; }
-  // the update arithmetic follows the handle's setting as the single-problem calls do: GF_UPDATE_DFMA
-  // the FP64 FMA form; GF_UPDATE_TC that form when every problem is small (n^2 p_max within
-  // kC128SmallWork, where a single problem takes it too), else the tensor cores; GF_UPDATE_TENSOR
-  // the tensor cores
+  // the update arithmetic follows the handle's setting: GF_UPDATE_DFMA the FP64 FMA form;
+  // GF_UPDATE_TC that form when the whole batch is small (the sum of n^2 p_max within
+  // kC128SmallWork, so every problem is small too and a single problem would take it as well),
+  // else the tensor cores; GF_UPDATE_TENSOR the tensor cores
   b->c128_fma = false;
   if (dtype == GF_C128) {
     const int algo = gf::api_update_algo(h);
-    bool small = true;
+    double work = 0.0;
     for (int i = 0; i < nitems; ++i) {
       const double n = (double)b->host[i].L.n;
-      small = small && n * n * b->host[i].L.pmax <= gf::kC128SmallWork;
+      work += n * n * b->host[i].L.pmax;
     }
-    b->c128_fma = algo == GF_UPDATE_DFMA || (algo == GF_UPDATE_TC && small);
+    b->c128_fma = algo == GF_UPDATE_DFMA || (algo == GF_UPDATE_TC && work <= gf::kC128SmallWork);
   }
   if (dtype == GF_C128 && !b->c128_fma) {
     b->oz_params = ::operator new(gf::ozaki_batch_params_bytes(), std::align_val_t(64), std::nothrow);

@@ -77,9 +77,10 @@ def _seed(seed: int, e_i: int, t: int) -> int:
 
 def egreedy_study_batched(epsilons: Sequence[float] = (0.0, 0.1, 0.2, 0.3), trajectories: int = 20,
                           seed: int = 0, max_steps: int = 4000, device: int = 0, chunk: int = 32) -> Dict[float, dict]:
-    """The same study with every trajectory a problem of one fused batch (one launch per stage
-    of the step for all of them, chunk steps per CUDA graph), run until every trajectory has no
-    improving action left.  Same seeds as egreedy_study, so the same trajectories."""
+    """The same study with every trajectory a problem of one fused batch (the persistent step
+    kernel: one launch per step of all of them, chunk steps per CUDA graph), run until every
+    trajectory has no improving action left.  Same seeds as egreedy_study, so the same
+    trajectories."""
     wl = metalens_21()
     pols, owner = [], []
     for e_i, eps in enumerate(epsilons):
