@@ -334,6 +334,34 @@ def sched_json(s):
     return {"fused": False, "streams": s.nstreams, "order": s.order}
 
 
+def persistent_single_problem(wl, args):
+    """The same problem as a batch of one on the persistent step kernel (for a small complex128
+    problem the whole step, FP64 FMA update included, is one launch), K steps in one CUDA graph
+    after W steps from the filled start: the per-step cost without the stage launches."""
+    import torch
+    from paper_2202_05388_gb300 import gfopt as B
+    from paper_2202_05388_gb300.batch import BatchOptimizer, Schedule
+    bo = BatchOptimizer([wl], dtype=wl.dtype)
+    bo.schedule = Schedule(0, "given", True, 0, B.GF_BATCH_PERSISTENT)
+    bo.fill()
+    for _ in range(max(0, args.warmup - 1)):
+        bo.enqueue_step()
+    bo.capture(args.steps)                    # one more step runs before the capture
+    before = bo.total_applied()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    bo.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"ms_per_step": ms / args.steps, "steps_per_s": args.steps / (ms / 1e3),
+           "accepted_flips": bo.total_applied() - before,
+           "launches_per_step": 1 if (bo.c128_fma or wl.dtype == "c64") else 3,
+           "update": "FP64 FMA" if bo.c128_fma else ("FP32 stream" if wl.dtype == "c64" else "tensor cores")}
+    bo.close()
+    return out
+
+
 def launches_per_step(s, nprob, dtype, c128_fma=False):
     """Library kernels per batched step, per group of 64 problems: persistent = the step kernel
     (complex128, or complex64 with tile_rows 0: + the G update and the bands); staged = one launch per stage (eval,
@@ -693,6 +721,7 @@ def run_native(args):
         for _ in range(args.steps):
             opt.step()
         kern_ms, kern_launches, kern_bytes, kern_flops = opt.h.gf_profile_end()
+        persistent_one = persistent_single_problem(wl, args) if (nlam == 1 and wl.spec.k == 1) else None
     else:
         opt.h.gf_profile_begin(args.steps * nlam + 4)
         torch.cuda.synchronize()
@@ -882,6 +911,8 @@ def run_native(args):
             "e2e": e2e}
     if breakdown is not None:
         line["step_breakdown_ms"] = breakdown
+    if args.graph and persistent_one is not None:
+        line["persistent_batch_of_one"] = persistent_one
     if dfma is not None:
         line["dfma_update"] = dfma
     if refresh is not None:

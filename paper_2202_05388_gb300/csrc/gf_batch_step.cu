@@ -8,7 +8,7 @@
 // complex64 runs the whole step in this launch (evaluation, selection + capacitance, panels, the
 // FP32 G update in R x 512 tiles, field/FOM, bands), or everything up to the field/FOM with the
 // update and the bands as their own launches.  complex128 with small problems runs the whole step
-// too, its G update the FP64 FMA form in 64 x 256 tiles; otherwise evaluation .. digit-operand
+// too, its G update the FP64 FMA form in 16 x 256 tiles; otherwise evaluation .. digit-operand
 // preparation and the field/FOM, the warp-specialised tensor-core update and the bands following
 // as their own launches.
 #include <math.h>

@@ -389,7 +389,7 @@ enum BatchStage : int32_t {
   kStSelCap,       // selection, then the capacitance solve (one CTA)
   kStPanels,       // C0 = G[:, V], S = D A^-1 G[V, :]
   kStPrep,         // complex128: digit operands of the tensor-core update
-  kStUpdate,       // G += C0 S: complex64 in FP32 (tiles of R x 512), complex128 in FP64 FMA (64 x 256)
+  kStUpdate,       // G += C0 S: complex64 in FP32 (tiles of R x 512), complex128 in FP64 FMA (16 x 256)
   kStFinish,       // E, state, FOM
   kStBands,        // bands of the new G (when the update runs in the launch)
 };

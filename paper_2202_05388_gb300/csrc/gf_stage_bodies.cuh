@@ -989,7 +989,7 @@ __device__ __forceinline__ void f64_update_rows(double2* G, int64_t ldg, int64_t
     }
   }
 }
-constexpr int kF64BatchRows = 64;                 // rows of one batched FP64 update tile (x 256 columns)
+constexpr int kF64BatchRows = 16;                 // rows of one batched FP64 update tile (x 256 columns)
 __device__ __forceinline__ void f64_update_tile(double2* G, int64_t ldg, int64_t n, int pmax, int p, const cplx* C0,
                                                 const cplx* S, int64_t rt, int64_t ct) {
   const int64_t j = ct * 256 + threadIdx.x;       // 256 threads: one column each

@@ -170,6 +170,14 @@ def test_batch_create_validates_every_item():
     b = h.gf_batch_create([item], o.dtype, o.spec, table, tb)
     with pytest.raises(B.GfError):
         h.gf_batch_set_schedule(b, -1)
+    for bad in ((7, 0, 1, 32), (B.GF_BATCH_PERSISTENT, -1, 1, 32), (B.GF_BATCH_PERSISTENT, 0, 0, 32),
+                (B.GF_BATCH_PERSISTENT, 0, 17, 32), (B.GF_BATCH_PERSISTENT, 0, 1, 48)):
+        with pytest.raises(B.GfError) as e:
+            h.gf_batch_set_form(b, *bad)
+        assert e.value.status == B.GF_EINVAL, bad
+    h.gf_batch_set_form(b, B.GF_BATCH_STAGED, 0, 1, 32)
+    with pytest.raises(B.GfError):
+        h.gf_batch_selftest_timeout(b, 10)            # below the 1 us floor
     h.gf_batch_destroy(b)
 
 
