@@ -277,8 +277,10 @@ gf_status gf_lowrank_fom(gf_handle* h, const gf_lowrank* lr, double* fom_out, vo
 /* dFOM of every candidate (as gf_eval_candidates). */
 gf_status gf_lowrank_eval(gf_handle* h, const gf_lowrank* lr, const uint8_t* state, const gf_cand_spec* spec,
                           double* dfom, void* stream);
-/* Apply idx[0] (as gf_apply_update with k = 1): new columns G[:, V], capacitance solve,
- * append the term, update bands, monitor row, E, state and *fom_out. */
+/* Apply idx[0 .. spec->k) as gf_apply_update does (top-k candidates applied jointly when their
+ * joint dFOM is positive, else idx[0] alone; *applied = candidates applied): new columns
+ * G[:, V], capacitance solve, append the term, update bands, monitor row, E, state and
+ * *fom_out.  At most 32 pixels per step: k <= 32 single pixels or k <= 8 brushes. */
 gf_status gf_lowrank_update(gf_handle* h, const gf_lowrank* lr, uint8_t* state, const gf_cand_spec* spec,
                             const int32_t* idx, int32_t* status, double* fom_out, int32_t* applied,
                             void* ws, size_t ws_bytes, void* stream);

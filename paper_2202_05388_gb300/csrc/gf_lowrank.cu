@@ -22,25 +22,28 @@
 namespace gf {
 
 constexpr int kLrP = 4;            // pixels per candidate at most (2x2 brush)
-constexpr int kLrSlices = 16;      // slices of the stored columns in the column product, at most
+constexpr int kLrPMax = 32;        // pixels per step at most (k candidates: k p <= 32)
+constexpr int kLrSlices = 16;      // slices x column groups of the column product, at most
 
 struct LrCount {
-  int32_t nterms, ncols;
+  int32_t nterms, ncols, ncoef, pad;
 };
 
 // Per-step scratch written by the pixel / capacitance kernels.
 struct LrStep {
-  int32_t skip, p, col0, pad;
-  int32_t V[kLrP];
-  double dchi[kLrP];
-  cplx dy[kLrP];          // D y, y = A^{-1} E_V
-  cplx M[kLrP * kLrP];    // D A^{-1}, row-major p x p (stride kLrP)
+  int32_t skip, p, col0, p1;     // p1: pixels of the best candidate (the set applied alone on fallback)
+  int32_t ncand, pad[3];         // candidates applied
+  int32_t V[kLrPMax];
+  double dchi[kLrPMax];
+  cplx dy[kLrPMax];              // D y, y = A^{-1} E_V
+  cplx M[kLrPMax * kLrPMax];     // D A^{-1}, row-major p x p (stride p)
 };
 
-// workspace layout: G0 table (2N) | M blocks | term first column | term width | column -> term |
-// counters | step | w (K x kLrP) | partial columns of the column product (kLrSlices x kLrP x n)
+// workspace layout: G0 table (2N) | M blocks (packed, p_s x p_s per term) | term first column |
+// term width | term block offset | column -> term | counters | step | w (K x kLrPMax) | partial
+// columns of the column product (kLrSlices x 4 x n)
 struct LrLayout {
-  size_t table, coef, tcol, tp, colterm, count, step, w, part, total;
+  size_t table, coef, tcol, tp, tco, colterm, count, step, w, part, total;
 };
 
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -50,13 +53,14 @@ static LrLayout lr_layout(const gf_geom& g, int max_cols) {
   LrLayout L;
   size_t o = 0;
   L.table = o; o = up256(o + sizeof(cplx) * (size_t)(2 * N));
-  L.coef = o; o = up256(o + sizeof(cplx) * kLrP * kLrP * (size_t)max_cols);
+  L.coef = o; o = up256(o + sizeof(cplx) * kLrPMax * (size_t)max_cols);   // sum of p_s^2 <= kLrPMax K
   L.tcol = o; o = up256(o + sizeof(int32_t) * (size_t)max_cols);
   L.tp = o; o = up256(o + sizeof(int32_t) * (size_t)max_cols);
+  L.tco = o; o = up256(o + sizeof(int32_t) * (size_t)max_cols);
   L.colterm = o; o = up256(o + sizeof(int32_t) * (size_t)max_cols);
   L.count = o; o = up256(o + sizeof(LrCount));
   L.step = o; o = up256(o + sizeof(LrStep));
-  L.w = o; o = up256(o + sizeof(cplx) * kLrP * (size_t)max_cols);
+  L.w = o; o = up256(o + sizeof(cplx) * kLrPMax * (size_t)max_cols);
   L.part = o; o = up256(o + sizeof(cplx) * kLrSlices * kLrP * (size_t)(N + 1));
   L.total = o;
   return L;
@@ -75,6 +79,7 @@ struct LrArgs {
   cplx* coef;
   int32_t* tcol;
   int32_t* tp;
+  int32_t* tco;
   int32_t* colterm;
   LrCount* count;
   LrStep* step;
@@ -110,25 +115,37 @@ __global__ void k_lr_init(LrArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.count->nterms = 0;
     a.count->ncols = 0;
+    a.count->ncoef = 0;
   }
 }
 
-// ---- the chosen candidate's pixels (device status and capacity checks)
+// ---- the chosen candidates' pixels, in selection order (device status and capacity checks)
 __global__ void k_lr_pixels(LrArgs a, int kind, int dir_mask, const uint8_t* __restrict__ state,
-                            const int32_t* __restrict__ idx, int32_t* status) {
+                            const int32_t* __restrict__ idx, int k, int32_t* status) {
   if (threadIdx.x != 0) return;
   LrStep* s = a.step;
   s->skip = 1;
   s->p = 0;
+  s->ncand = 0;
   if (*status != GF_OK || idx[0] < 0) return;
-  const int p = cand_pixels(idx[0], kind, dir_mask, a.nx, a.ny, a.chi, state, s->V, s->dchi);
+  int p = 0, nc = 0, p1 = 0;
+  for (int c = 0; c < k; ++c) {
+    if (idx[c] < 0) break;
+    const int m = cand_pixels(idx[c], kind, dir_mask, a.nx, a.ny, a.chi, state, s->V + p, s->dchi + p);
+    if (m == 0) continue;
+    if (nc == 0) p1 = m;
+    p += m;
+    ++nc;
+  }
   if (p == 0) return;
   const LrCount c = *a.count;
-  if (c.ncols + p > a.max_cols || c.nterms + 1 > a.max_cols) {
+  if (c.ncols + p > a.max_cols || c.nterms + 1 > a.max_cols || c.ncoef + p * p > kLrPMax * a.max_cols) {
     *status = GF_ENOMEM;        // term storage full: materialise (gf_lowrank_materialize) and restart
     return;
   }
   s->p = p;
+  s->p1 = p1;
+  s->ncand = nc;
   s->col0 = c.ncols;
   s->skip = 0;
 }
@@ -141,14 +158,13 @@ __global__ void k_lr_w(LrArgs a) {
   const int K = s->col0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t info = a.colterm[k];
-    const int term = info >> 2, row = info & 3;
+    const int term = info >> 5, row = info & 31;
     const int c0 = a.tcol[term], pt = a.tp[term];
-    const cplx* M = a.coef + (int64_t)term * kLrP * kLrP;
-    for (int u = 0; u < kLrP; ++u) {
+    const cplx* M = a.coef + a.tco[term];
+    for (int u = 0; u < p; ++u) {
       cplx acc = mk(0.0, 0.0);
-      if (u < p)
-        for (int b = 0; b < pt; ++b) acc = cfma(M[row * kLrP + b], a.U[(int64_t)(c0 + b) * a.n + s->V[u]], acc);
-      a.w[k * kLrP + u] = acc;
+      for (int b = 0; b < pt; ++b) acc = cfma(M[row * pt + b], a.U[(int64_t)(c0 + b) * a.n + s->V[u]], acc);
+      a.w[(int64_t)k * kLrPMax + u] = acc;
     }
   }
 }
@@ -215,21 +231,26 @@ constexpr int kLrChunk = 256;      // stored columns per shared-memory chunk of 
 // Split over the stored columns: blockIdx.y takes slice y of [0, K) (gridDim.y slices; slice 0
 // also starts from the G0 column) and writes its partial columns to part[y]; k_lr_columns_sum adds
 // the slices in FP64 in a fixed order, so the result does not depend on scheduling.  One row block
-// per CTA alone leaves most of the GPU idle at n ~ 4e4 (145 CTAs).
+// per CTA alone leaves most of the GPU idle at n ~ 4e4 (145 CTAs).  blockIdx.z takes the step's
+// new columns 4 z .. 4 z + 3 (several candidates per step).
 __global__ void __launch_bounds__(kLrThreads) k_lr_columns(LrArgs a, int32_t* __restrict__ prof) {
   const LrStep* s = a.step;
-  if (prof && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *prof = s->skip ? 0 : s->col0 * s->p;
+  if (prof && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+    *prof = s->skip ? 0 : s->col0 * s->p;
   if (s->skip) return;
   __shared__ float4 sw[kLrChunk * kLrP];       // w[k][u] as (re.h, re.l, im.h, im.l)
-  const int p = s->p;
+  const int u0 = (int)blockIdx.z * kLrP;       // the group's first new column
+  if (u0 >= s->p) return;
+  const int p = s->p - u0 < kLrP ? s->p - u0 : kLrP;
   const int K = s->col0;
   const int S = (int)gridDim.y, y = (int)blockIdx.y;
+  const int gz = (int)blockIdx.z, G = (int)gridDim.z;
   const int Ks = (K + S - 1) / S;
   const int kb = y * Ks < K ? y * Ks : K;
   const int ke = kb + Ks < K ? kb + Ks : K;
   int V[kLrP];
 #pragma unroll
-  for (int u = 0; u < kLrP; ++u) V[u] = s->V[u];
+  for (int u = 0; u < kLrP; ++u) V[u] = u < p ? s->V[u0 + u] : 0;
   for (int64_t i0 = (int64_t)blockIdx.x * kLrThreads; i0 < a.n; i0 += (int64_t)gridDim.x * kLrThreads) {
     const int64_t i = i0 + threadIdx.x;
     dflt ar[kLrP], ai[kLrP];
@@ -243,7 +264,8 @@ __global__ void __launch_bounds__(kLrThreads) k_lr_columns(LrArgs a, int32_t* __
       const int kc = ke - k0 < kLrChunk ? ke - k0 : kLrChunk;
       __syncthreads();
       for (int t = threadIdx.x; t < kc * kLrP; t += kLrThreads) {
-        const cplx w = a.w[(int64_t)k0 * kLrP + t];
+        const int uu = t & (kLrP - 1);
+        const cplx w = uu < p ? a.w[(int64_t)(k0 + (t >> 2)) * kLrPMax + u0 + uu] : mk(0.0, 0.0);
         const dflt wr = df_split(w.re), wi = df_split(w.im);
         sw[t] = make_float4(wr.h, wr.l, wi.h, wi.l);
       }
@@ -269,13 +291,13 @@ __global__ void __launch_bounds__(kLrThreads) k_lr_columns(LrArgs a, int32_t* __
     if (i < a.n) {
 #pragma unroll
       for (int u = 0; u < kLrP; ++u)
-        if (u < p) a.part[((int64_t)y * kLrP + u) * a.n + i] = mk(df_to(ar[u]), df_to(ai[u]));
+        if (u < p) a.part[(((int64_t)y * G + gz) * kLrP + u) * a.n + i] = mk(df_to(ar[u]), df_to(ai[u]));
     }
   }
 }
 
 // C[:, u] = sum of the slices' partial columns (FP64, slice order), appended to U
-__global__ void k_lr_columns_sum(LrArgs a, int S) {
+__global__ void k_lr_columns_sum(LrArgs a, int S, int G) {
   const LrStep* s = a.step;
   if (s->skip) return;
   const int p = s->p;
@@ -284,113 +306,191 @@ __global__ void k_lr_columns_sum(LrArgs a, int S) {
        t += (int64_t)gridDim.x * blockDim.x) {
     const int u = (int)(t / a.n);
     const int64_t i = t - (int64_t)u * a.n;
-    cplx acc = a.part[(int64_t)u * a.n + i];
-    for (int y = 1; y < S; ++y) acc = acc + a.part[((int64_t)y * kLrP + u) * a.n + i];
+    const int g = u / kLrP, uu = u - g * kLrP;
+    cplx acc = a.part[((int64_t)g * kLrP + uu) * a.n + i];
+    for (int y = 1; y < S; ++y) acc = acc + a.part[(((int64_t)y * G + g) * kLrP + uu) * a.n + i];
     a.U[(int64_t)(K + u) * a.n + i] = acc;
   }
 }
 
-// ---- capacitance: A = I - G_VV D from the new columns, y = A^{-1} E_V, M = D A^{-1} (one thread;
-// p <= 4, Gaussian elimination with partial pivoting as in the candidate kernels)
-__global__ void k_lr_capacitance(LrArgs a, int32_t* status) {
-  if (threadIdx.x != 0) return;
+// ---- capacitance: A = I - G_VV D from the new columns, y = A^{-1} E_V, M = D A^{-1} (one CTA:
+// Gaussian elimination with partial pivoting on [A | I | E_V], one thread picks each pivot (largest
+// |a| as in the candidate kernels, first on ties) and forms the rows' multipliers, every element is
+// then updated by its own thread; the back substitution runs column by column over all right-hand
+// sides at once).  Several candidates: applied jointly only if the joint dFOM is positive, else
+// the best candidate alone (its columns lead the new ones).
+__global__ void __launch_bounds__(256) k_lr_capacitance(LrArgs a, int32_t* status) {
   LrStep* s = a.step;
   if (s->skip) return;
-  const int p = s->p;
+  __shared__ cplx A[kLrPMax][kLrPMax];
+  __shared__ cplx X[kLrPMax][kLrPMax + 1];
+  __shared__ cplx F[kLrPMax];
+  __shared__ double s_norm;
+  __shared__ int s_piv, s_bad, s_p, s_redo;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int K = s->col0;
-  cplx A[kLrP][kLrP], X[kLrP][kLrP + 1];
-  double norm = 0.0;
-  for (int r = 0; r < p; ++r) {
-    double rs = 0.0;
-    for (int c = 0; c < p; ++c) {
+  if (tid == 0) { s_p = s->p; s_redo = 0; }
+  __syncthreads();
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const int p = s_p;
+    for (int t = tid; t < p * p; t += nt) {
+      const int r = t / p, c = t - r * p;
       const cplx g = a.U[(int64_t)(K + c) * a.n + s->V[r]];      // G[v_r, v_c]
       A[r][c] = mk(r == c ? 1.0 : 0.0, 0.0) - s->dchi[c] * g;
-      rs += cabs1(A[r][c]);
+      X[r][c] = mk(r == c ? 1.0 : 0.0, 0.0);
     }
-    norm = fmax(norm, rs);
-  }
-  // right-hand sides: the identity (for A^{-1}) and E_V (for y)
-  for (int r = 0; r < p; ++r) {
-    for (int c = 0; c < p; ++c) X[r][c] = mk(r == c ? 1.0 : 0.0, 0.0);
-    X[r][p] = a.E[s->V[r]];
-  }
-  const double thresh = kSingularRel * norm;
-  for (int c = 0; c < p; ++c) {
-    int piv = c;
-    double best = cabs1(A[c][c]);
-    for (int r = c + 1; r < p; ++r)
-      if (cabs1(A[r][c]) > best) { best = cabs1(A[r][c]); piv = r; }
-    if (!(best >= thresh) || !(best > 0.0)) {
-      *status = GF_ESINGULAR;
-      s->skip = 1;
+    for (int r = tid; r < p; r += nt) X[r][p] = a.E[s->V[r]];
+    __syncthreads();
+    if (tid == 0) {
+      double norm = 0.0;
+      for (int r = 0; r < p; ++r) {
+        double rs = 0.0;
+        for (int c = 0; c < p; ++c) rs += cabs1(A[r][c]);
+        norm = fmax(norm, rs);
+      }
+      s_norm = norm;
+      s_bad = 0;
+    }
+    __syncthreads();
+    const double thresh = kSingularRel * s_norm;
+    for (int c = 0; c < p; ++c) {
+      if (tid == 0) {
+        int piv = c;
+        double best = cabs1(A[c][c]);
+        for (int r = c + 1; r < p; ++r)
+          if (cabs1(A[r][c]) > best) { best = cabs1(A[r][c]); piv = r; }
+        s_piv = piv;
+        if (!(best >= thresh) || !(best > 0.0)) s_bad = 1;
+      }
+      __syncthreads();
+      if (s_bad) break;
+      const int piv = s_piv;
+      if (piv != c) {
+        for (int v = tid; v < p; v += nt) { const cplx t0 = A[c][v]; A[c][v] = A[piv][v]; A[piv][v] = t0; }
+        for (int v = tid; v <= p; v += nt) { const cplx t0 = X[c][v]; X[c][v] = X[piv][v]; X[piv][v] = t0; }
+      }
+      for (int r = c + 1 + tid; r < p; r += nt) F[r] = cdiv(A[r][c], A[c][c]);
+      __syncthreads();
+      // row r >= c + 1: a_rv -= f_r a_cv (v >= c), x_rv -= f_r x_cv
+      const int w = 2 * p + 1 - c;               // columns c..p-1 of A, then 0..p of X
+      for (int t = tid; t < (p - 1 - c) * w; t += nt) {
+        const int r = c + 1 + t / w, q = t - (t / w) * w;
+        const cplx f = F[r];
+        if (q < p - c) {
+          const int v = c + q;
+          A[r][v] = A[r][v] - f * A[c][v];
+        } else {
+          const int v = q - (p - c);
+          X[r][v] = X[r][v] - f * X[c][v];
+        }
+      }
+      __syncthreads();
+    }
+    if (s_bad) {
+      if (tid == 0) {
+        *status = GF_ESINGULAR;
+        s->skip = 1;
+      }
       return;
     }
-    if (piv != c) {
-      for (int v = 0; v < p; ++v) { cplx t = A[c][v]; A[c][v] = A[piv][v]; A[piv][v] = t; }
-      for (int v = 0; v <= p; ++v) { cplx t = X[c][v]; X[c][v] = X[piv][v]; X[piv][v] = t; }
+    // back substitution, column by column from the bottom, every right-hand side at once
+    for (int c = p - 1; c >= 0; --c) {
+      for (int v = tid; v <= p; v += nt) X[c][v] = cdiv(X[c][v], A[c][c]);
+      __syncthreads();
+      for (int t = tid; t < c * (p + 1); t += nt) {
+        const int r = t / (p + 1), v = t - r * (p + 1);
+        X[r][v] = X[r][v] - A[r][c] * X[c][v];
+      }
+      __syncthreads();
     }
-    for (int r = c + 1; r < p; ++r) {
-      const cplx f = cdiv(A[r][c], A[c][c]);
-      for (int v = c; v < p; ++v) A[r][v] = A[r][v] - f * A[c][v];
-      for (int v = 0; v <= p; ++v) X[r][v] = X[r][v] - f * X[c][v];
+    if (attempt == 0 && s->ncand > 1) {           // the joint decision (Eq. 4 at the monitor)
+      if (tid == 0) {
+        cplx dE = mk(0.0, 0.0);
+        for (int u = 0; u < p; ++u)
+          dE = dE + s->dchi[u] * (a.U[(int64_t)(K + u) * a.n + a.N] * X[u][p]);
+        const cplx EN = a.E[a.N];
+        const double joint = abs2(EN + dE) - abs2(EN);
+        if (!(joint > 0.0)) {
+          s_p = s->p1;
+          s_redo = 1;
+        }
+      }
+      __syncthreads();
+      if (s_redo) continue;
     }
+    break;
   }
-  for (int c = p - 1; c >= 0; --c)
-    for (int v = 0; v <= p; ++v) {
-      cplx acc = X[c][v];
-      for (int q = c + 1; q < p; ++q) acc = acc - A[c][q] * X[q][v];
-      X[c][v] = cdiv(acc, A[c][c]);
-    }
+  const int p = s_p;
   const int term = a.count->nterms;
-  cplx* M = a.coef + (int64_t)term * kLrP * kLrP;
-  for (int r = 0; r < kLrP; ++r)
-    for (int c = 0; c < kLrP; ++c) {
-      const cplx m = (r < p && c < p) ? s->dchi[r] * X[r][c] : mk(0.0, 0.0);
-      M[r * kLrP + c] = m;
-      s->M[r * kLrP + c] = m;
-    }
-  for (int r = 0; r < p; ++r) s->dy[r] = s->dchi[r] * X[r][p];
-  a.tcol[term] = K;
-  a.tp[term] = p;
-  for (int u = 0; u < p; ++u) a.colterm[K + u] = (term << 2) | u;
-  a.count->nterms = term + 1;
-  a.count->ncols = K + p;
+  const int off = a.count->ncoef;
+  cplx* M = a.coef + off;
+  for (int t = tid; t < p * p; t += nt) {
+    const int r = t / p, c = t - r * p;
+    const cplx m = s->dchi[r] * X[r][c];
+    M[t] = m;
+    s->M[t] = m;
+  }
+  for (int r = tid; r < p; r += nt) {
+    s->dy[r] = s->dchi[r] * X[r][p];
+    a.colterm[K + r] = (term << 5) | r;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (s_redo) s->ncand = 1;
+    s->p = p;
+    a.tcol[term] = K;
+    a.tp[term] = p;
+    a.tco[term] = off;
+    a.count->nterms = term + 1;
+    a.count->ncols = K + p;
+    a.count->ncoef = off + p * p;
+  }
 }
 
-// ---- Eq. 10 on the explicit entries (bands, monitor row) and Eq. 4 on E; state, FOM
-__global__ void k_lr_apply(LrArgs a, uint8_t* __restrict__ state, double* __restrict__ fom_out,
-                           int32_t* __restrict__ applied) {
+// ---- Eq. 10 on the explicit entries (bands, monitor row) and Eq. 4 on E; state, FOM.  PM bounds
+// the step's p (4: one candidate, held in registers; kLrPMax: several, M and q_N in shared memory)
+template <int PM>
+__global__ void __launch_bounds__(256) k_lr_apply(LrArgs a, uint8_t* __restrict__ state, double* __restrict__ fom_out,
+                                                  int32_t* __restrict__ applied) {
   const LrStep* s = a.step;
   const bool skip = s->skip != 0;
   const int p = skip ? 0 : s->p;
   const int K = s->col0;
   const cplx* C = a.U + (int64_t)K * a.n;        // the new columns, C[u * n + i]
-  cplx M[kLrP * kLrP];
-#pragma unroll
-  for (int t = 0; t < kLrP * kLrP; ++t) M[t] = skip ? mk(0.0, 0.0) : s->M[t];
-  // q_N = C[N, :] M (row vector) for the monitor row
-  cplx qN[kLrP];
-#pragma unroll
-  for (int c = 0; c < kLrP; ++c) {
-    qN[c] = mk(0.0, 0.0);
-    for (int r = 0; r < p; ++r) qN[c] = cfma(C[(int64_t)r * a.n + a.N], M[r * kLrP + c], qN[c]);
+  __shared__ cplx sM[PM * PM];
+  __shared__ cplx sq[PM];
+  __shared__ cplx sdy[PM];
+  for (int t = threadIdx.x; t < PM * PM; t += blockDim.x) {
+    const int r = t / PM, c = t - r * PM;
+    sM[t] = (r < p && c < p) ? s->M[r * p + c] : mk(0.0, 0.0);
   }
+  for (int c = threadIdx.x; c < PM; c += blockDim.x) sdy[c] = c < p ? s->dy[c] : mk(0.0, 0.0);
+  __syncthreads();
+  // q_N = C[N, :] M (row vector) for the monitor row
+  for (int c = threadIdx.x; c < PM; c += blockDim.x) {
+    cplx q = mk(0.0, 0.0);
+    for (int r = 0; r < p; ++r) q = cfma(C[(int64_t)r * a.n + a.N], sM[r * PM + c], q);
+    sq[c] = q;
+  }
+  __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
     if (p > 0) {
-      cplx ri[kLrP], qi[kLrP];
+      cplx ri[PM], qi[PM];
 #pragma unroll
-      for (int u = 0; u < kLrP; ++u) ri[u] = u < p ? C[(int64_t)u * a.n + i] : mk(0.0, 0.0);
+      for (int u = 0; u < PM; ++u) ri[u] = u < p ? C[(int64_t)u * a.n + i] : mk(0.0, 0.0);
 #pragma unroll
-      for (int c = 0; c < kLrP; ++c) {
+      for (int c = 0; c < PM; ++c) {
         qi[c] = mk(0.0, 0.0);
+        if (c < p)
 #pragma unroll
-        for (int r = 0; r < kLrP; ++r) qi[c] = cfma(ri[r], M[r * kLrP + c], qi[c]);
+          for (int r = 0; r < PM; ++r)
+            if (r < p) qi[c] = cfma(ri[r], sM[r * PM + c], qi[c]);
       }
       cplx e = a.E[i];
-      for (int u = 0; u < p; ++u) e = cfma(ri[u], s->dy[u], e);
+      for (int u = 0; u < p; ++u) e = cfma(ri[u], sdy[u], e);
       a.E[i] = e;
       cplx dm = mk(0.0, 0.0);
-      for (int c = 0; c < p; ++c) dm = cfma(qN[c], ri[c], dm);
+      for (int c = 0; c < p; ++c) dm = cfma(sq[c], ri[c], dm);
       a.mon[i] = a.mon[i] + dm;
       if (i < a.N) {
         const int iy = (int)(i / a.nx), ix = (int)(i % a.nx);
@@ -401,17 +501,20 @@ __global__ void k_lr_apply(LrArgs a, uint8_t* __restrict__ state, double* __rest
           if (jx < 0 || jx >= a.nx || jy < 0 || jy >= a.ny) continue;
           const int64_t j = (int64_t)jy * a.nx + jx;
           cplx d = mk(0.0, 0.0);
-          for (int c = 0; c < p; ++c) d = cfma(qi[c], C[(int64_t)c * a.n + j], d);
+#pragma unroll
+          for (int c = 0; c < PM; ++c)
+            if (c < p) d = cfma(qi[c], C[(int64_t)c * a.n + j], d);
           a.bands[(int64_t)b * a.N + i] = a.bands[(int64_t)b * a.N + i] + d;
         }
       }
     }
     if (i == a.N) {
       *fom_out = abs2(a.E[a.N]);
-      if (applied) *applied = p > 0 ? 1 : 0;
+      if (applied) *applied = p > 0 ? s->ncand : 0;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x < p) state[s->V[threadIdx.x]] ^= 1;
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < p; t += blockDim.x) state[s->V[t]] ^= 1;
 }
 
 // ---- dense G = G0 + sum_s C_s M_s C_s^T (checks and flushes; O(n^2 K))
@@ -426,10 +529,11 @@ __global__ void k_lr_materialize(LrArgs a, double2* __restrict__ G, int64_t ldg)
     else v = g0_entry(a, i, j);
     for (int k = 0; k < K; ++k) {
       const int32_t info = a.colterm[k];
-      const int term = info >> 2, row = info & 3;
+      const int term = info >> 5, row = info & 31;
       const int c0 = a.tcol[term], pt = a.tp[term];
+      const cplx* M = a.coef + a.tco[term];
       cplx mj = mk(0.0, 0.0);
-      for (int b = 0; b < pt; ++b) mj = cfma(a.coef[(int64_t)term * kLrP * kLrP + row * kLrP + b], a.U[(int64_t)(c0 + b) * a.n + j], mj);
+      for (int b = 0; b < pt; ++b) mj = cfma(M[row * pt + b], a.U[(int64_t)(c0 + b) * a.n + j], mj);
       v = cfma(a.U[(int64_t)k * a.n + i], mj, v);
     }
     G[i * ldg + j] = make_double2(v.re, v.im);
@@ -453,6 +557,7 @@ static LrArgs lr_args(const gf_lowrank& lr, char* ws) {
   a.coef = reinterpret_cast<cplx*>(ws + L.coef);
   a.tcol = reinterpret_cast<int32_t*>(ws + L.tcol);
   a.tp = reinterpret_cast<int32_t*>(ws + L.tp);
+  a.tco = reinterpret_cast<int32_t*>(ws + L.tco);
   a.colterm = reinterpret_cast<int32_t*>(ws + L.colterm);
   a.count = reinterpret_cast<LrCount*>(ws + L.count);
   a.step = reinterpret_cast<LrStep*>(ws + L.step);
@@ -558,11 +663,13 @@ gf_status gf_lowrank_update(gf_handle* h, const gf_lowrank* lr, uint8_t* state, 
   if (s) return s;
   if (!spec) return gf::api_fail_msg(h, GF_EINVAL, "candidate spec is NULL");
   if ((s = gf::api_check_spec(h, &lr->geom, spec))) return s;
-  if (spec->k != 1) return gf::api_fail_msg(h, GF_EINVAL, "the deferred form applies one candidate per step (k = 1)");
+  const int per = spec->kind == GF_KIND_SINGLE ? 1 : gf::kLrP;
+  if (spec->k < 1 || spec->k * per > gf::kLrPMax)
+    return gf::api_fail_msg(h, GF_EINVAL, "the deferred form applies at most 32 pixels per step (k <= 32 single pixels, k <= 8 brushes)");
   if (!state || !idx || !status || !fom_out) return gf::api_fail_msg(h, GF_EINVAL, "state, idx, status and fom_out must be non-NULL");
   cudaStream_t st = (cudaStream_t)stream;
   gf::LrArgs a = gf::lr_args(*lr, reinterpret_cast<char*>(ws));
-  gf::k_lr_pixels<<<1, 32, 0, st>>>(a, spec->kind, spec->dir_mask, state, idx, status);
+  gf::k_lr_pixels<<<1, 32, 0, st>>>(a, spec->kind, spec->dir_mask, state, idx, spec->k, status);
   gf::k_lr_w<<<gf::grid_of(lr->max_cols, 256, 1216), 256, 0, st>>>(a);
   // timed like the dense G update when profiling is armed: the record's rank is K p (columns
   // read x columns written), so the recorded flops 8 (K p) n are the product's
@@ -584,12 +691,16 @@ gf_status gf_lowrank_update(gf_handle* h, const gf_lowrank* lr, uint8_t* state, 
         occ = 1;
       if (dev >= 0 && dev < 64) per_sm[dev].store(occ);
     }
+    // column groups: 4 new columns each, for the step's largest p; slices x groups <= kLrSlices
+    const int pmax = spec->k * per;
+    const int G = (pmax + gf::kLrP - 1) / gf::kLrP;
     const int64_t rb = (a.n + gf::kLrThreads - 1) / gf::kLrThreads;
-    int64_t S = (int64_t)gf::api_sm_count(h) * occ / rb;
-    S = S < 1 ? 1 : (S > gf::kLrSlices ? gf::kLrSlices : S);
-    gf::k_lr_columns<<<dim3((unsigned)(rb < 4864 ? rb : 4864), (unsigned)S), gf::kLrThreads, 0, st>>>(
+    int64_t S = (int64_t)gf::api_sm_count(h) * occ / (rb * G);
+    const int64_t smax = gf::kLrSlices / G;
+    S = S < 1 ? 1 : (S > smax ? smax : S);
+    gf::k_lr_columns<<<dim3((unsigned)(rb < 4864 ? rb : 4864), (unsigned)S, (unsigned)G), gf::kLrThreads, 0, st>>>(
         a, rec ? tm->p_dev + tm->used : nullptr);
-    gf::k_lr_columns_sum<<<gf::grid_of(gf::kLrP * a.n, 256, 4864), 256, 0, st>>>(a, (int)S);
+    gf::k_lr_columns_sum<<<gf::grid_of((int64_t)pmax * a.n, 256, 4864), 256, 0, st>>>(a, (int)S, G);
   }
   if (rec) {
     cudaEventRecord(tm->ev1[tm->used], st);
@@ -597,8 +708,11 @@ gf_status gf_lowrank_update(gf_handle* h, const gf_lowrank* lr, uint8_t* state, 
     tm->bytes_per_entry[tm->used] = 0;
     tm->used++;
   }
-  gf::k_lr_capacitance<<<1, 32, 0, st>>>(a, status);
-  gf::k_lr_apply<<<gf::grid_of(a.n, 256, 4864), 256, 0, st>>>(a, state, fom_out, applied);
+  gf::k_lr_capacitance<<<1, 256, 0, st>>>(a, status);
+  if (spec->k * per <= gf::kLrP)
+    gf::k_lr_apply<gf::kLrP><<<gf::grid_of(a.n, 256, 4864), 256, 0, st>>>(a, state, fom_out, applied);
+  else
+    gf::k_lr_apply<gf::kLrPMax><<<gf::grid_of(a.n, 256, 4864), 256, 0, st>>>(a, state, fom_out, applied);
   return gf::api_cuda_check(h, "gf_lowrank_update launch");
 }
 

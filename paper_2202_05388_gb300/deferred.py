@@ -19,8 +19,10 @@ class DeferredOptimizer:
     def __init__(self, geom: Geometry, spec: CandidateSpec, max_cols: int, device: int = 0, handle=None):
         if not torch.cuda.is_available():
             raise B.GfError(B.GF_ECUDA, "DeferredOptimizer needs a CUDA device (no CPU fallback)")
-        if spec.k != 1:
-            raise B.GfError(B.GF_EINVAL, "the deferred form applies one candidate per step (k = 1)")
+        per = 1 if spec.kind == B.GF_KIND_SINGLE else 4
+        if spec.k < 1 or spec.k * per > 32:
+            raise B.GfError(B.GF_EINVAL, "the deferred form applies at most 32 pixels per step "
+                                         "(k <= 32 single pixels, k <= 8 brushes)")
         self.geom = geom
         self.spec = spec
         self.device = torch.device("cuda", device)
@@ -42,8 +44,9 @@ class DeferredOptimizer:
         self.state = torch.zeros(N, dtype=torch.uint8, device=dev)
         self.ncand = self.h.gf_num_candidates(geom, spec)
         self.dfom = torch.empty(self.ncand, dtype=torch.float64, device=dev)
-        self.idx = torch.full((1,), -1, dtype=torch.int32, device=dev)
-        self.val = torch.empty(1, dtype=torch.float64, device=dev)
+        self.k = max(1, spec.k)
+        self.idx = torch.full((self.k,), -1, dtype=torch.int32, device=dev)
+        self.val = torch.empty(self.k, dtype=torch.float64, device=dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
         self.fom = torch.zeros(1, dtype=torch.float64, device=dev)
         self.applied = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -73,14 +76,16 @@ class DeferredOptimizer:
         self.update()
 
     def force(self, ids: Sequence[int]):
-        self.idx.fill_(int(ids[0]))
+        self.idx.fill_(-1)
+        self.idx[0] = int(ids[0])
         self.status.zero_()
         self.update()
 
     def read_step(self) -> StepResult:
+        k = self.k
         packed = torch.cat([self.idx.to(torch.float64), self.val, self.status.to(torch.float64), self.fom]).cpu().numpy()
-        ids = [int(packed[0])] if packed[0] >= 0 else []
-        return StepResult(ids, [float(packed[1])] if ids else [], int(packed[2]), float(packed[3]))
+        ids = [int(x) for x in packed[:k] if x >= 0]
+        return StepResult(ids, [float(x) for x in packed[k:k + len(ids)]], int(packed[2 * k]), float(packed[2 * k + 1]))
 
     def run(self, steps: int) -> List[StepResult]:
         out = []

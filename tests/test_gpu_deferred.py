@@ -1,8 +1,8 @@
 """Deferred (low-rank) form on the GPU: every step's dFOM, choice, E, FOM, bands and monitor
-row agree with the dense FP64 oracle, the materialised G = G0 + sum_s C_s M_s C_s^T agrees
-with the oracle's G, the full-size 192x192 brush workload (no dense G stored) agrees with the
-dense GPU path step by step, and a full term store reports GF_ENOMEM without changing
-anything."""
+row agree with the dense FP64 oracle, with one candidate per step and with top-k sets applied
+jointly, the materialised G = G0 + sum_s C_s M_s C_s^T agrees with the oracle's G, the
+full-size 192x192 brush workload (no dense G stored) agrees with the dense GPU path step by
+step, and a full term store reports GF_ENOMEM without changing anything."""
 import numpy as np
 import pytest
 
@@ -140,9 +140,50 @@ def test_deferred_validation():
     with pytest.raises(B.GfError, match="max_cols"):
         opt.h.gf_lowrank_init(few, opt.ws, opt.ws_bytes)
     opt.init()
-    with pytest.raises(B.GfError, match="k = 1"):
-        opt.h.gf_lowrank_update(opt.lr, opt.state, W.CandidateSpec(W.KIND_SINGLE, 3, 4), opt.idx, opt.status,
+    with pytest.raises(B.GfError, match="at most 32 pixels"):
+        opt.h.gf_lowrank_update(opt.lr, opt.state, W.CandidateSpec(W.KIND_SINGLE, 3, 33), opt.idx, opt.status,
                                 opt.fom, opt.ws, opt.ws_bytes)
     with pytest.raises(B.GfError) as e:
-        DeferredOptimizer(g, W.CandidateSpec(W.KIND_SINGLE, 3, 2), max_cols=8)
+        DeferredOptimizer(g, W.CandidateSpec(W.KIND_BRUSH2, 3, 9), max_cols=8)
     assert e.value.status == B.GF_EINVAL
+
+
+@pytest.mark.parametrize("nx,ny,kind,k,ratio,steps", [(16, 12, W.KIND_BRUSH2, 4, 6, 10),
+                                                      (14, 12, W.KIND_SINGLE, 6, 20, 12),
+                                                      (20, 16, W.KIND_BRUSH2, 8, 6, 6)])
+def test_deferred_topk_matches_dense_oracle(nx, ny, kind, k, ratio, steps):
+    """Several candidates per step (top-k with exclusion zones, applied jointly when their joint
+    dFOM is positive, else the best alone): every step's dFOM, choice, applied set, E, FOM, bands
+    and monitor row against the dense FP64 oracle, and the materialised G at the end."""
+    wl = W.small(nx, ny, kind=kind, dir_mask=3, k=k, excl_radius=2, ratio=ratio, beyond_edge=2.0)
+    g = wl.geoms[0]
+    per = 1 if kind == W.KIND_SINGLE else 4
+    opt = DeferredOptimizer(g, wl.spec, max_cols=per * k * steps + 8)
+    opt.init()
+    orc = O.OracleProblem(wl.geoms, wl.spec)
+    done, joint = 0, 0
+    for t in range(steps):
+        opt.evaluate()
+        opt.select()
+        d = orc.evaluate()
+        compare_dfom(opt.dfom.cpu().numpy(), d, tag=f"step {t}")
+        want = orc.choose(d)
+        r = opt.read_step()
+        if not want:
+            assert r.status == B.GF_ENOIMPROVE
+            break
+        if r.ids != want:                       # a near tie decided the other way: take the oracle's
+            top = np.sort(d[np.isfinite(d)])[::-1]
+            assert np.min(np.abs(np.diff(top[:len(want) + 1]))) <= GAP * abs(top[0]), (t, r.ids, want)
+            opt.idx.fill_(-1)
+            opt.idx[:len(want)] = torch.tensor(want, dtype=torch.int32, device=opt.idx.device)
+        applied = orc.accept(want)
+        opt.update()
+        torch.cuda.synchronize()
+        assert int(opt.status.cpu()[0]) == B.GF_OK
+        assert int(opt.applied.cpu()[0]) == len(applied), (t, int(opt.applied.cpu()[0]), applied)
+        _check_explicit(opt, orc, f"step {t}")
+        joint += len(applied) > 1
+        done += 1
+    assert done >= 3 and joint >= 1
+    assert rel_err(opt.materialize().cpu().numpy(), orc.Gs[0]) <= TOL
