@@ -362,6 +362,12 @@ def persistent_single_problem(wl, args):
     return out
 
 
+def select_launches(ncand):
+    """Launches of the greedy (k = 1) selection with a workspace: one CTA, or from 32768
+    candidates a pass over many CTAs and a finishing CTA."""
+    return 2 if ncand >= 32768 else 1
+
+
 def launches_per_step(s, nprob, dtype, c128_fma=False):
     """Library kernels per batched step, per group of 64 problems: persistent = the step kernel
     (complex128, or complex64 with tile_rows 0: + the G update and the bands); staged = one launch per stage (eval,
@@ -647,7 +653,8 @@ def run_sharded(args):
                 # per step on each rank: -inf fill + dFOM, selection, row gather, capacitance, panels,
                 # the update's launches (digit preparation of rows and columns + the tensor-core
                 # update, or one FP64 FMA launch), field/FOM, band read-back, halo pack and unpack
-                "gpu_launches": args.steps * (10 + (3 if wl.dtype == "c128" and wl.spec.k == 1 else 1)),
+                "gpu_launches": args.steps * (9 + select_launches(sh.ncand) +
+                                              (3 if wl.dtype == "c128" and wl.spec.k == 1 else 1)),
                 "clocks": clk,
                 "e2e": {"value": done / t_e2e, "unit": UNIT, "h2d_bytes_per_step": g.N / args.steps,
                         "d2h_bytes_per_step": host_rec.numel() * 8,
@@ -879,10 +886,11 @@ def run_native(args):
     roof["algorithmic_bytes_per_launch"] = bytes_per_launch
     roof["kernel_ms_avg"] = kern_avg_ms
     roof["kernel_share_of_step"] = kern_ms / ms
-    # library kernels per step: eval, select (k = 1: one; top-k: begin + k passes + end),
+    # library kernels per step: eval, select (k = 1: one, two from 32768 candidates; top-k: begin
+    # + k passes + end),
     # capacitance, panels, finish, then per wavelength the update's launches and the bands
     pmax = wl.spec.k * (4 if wl.spec.kind == 1 else 1)
-    sel = 1 if wl.spec.k <= 1 else wl.spec.k + 2
+    sel = select_launches(ncand_main) if wl.spec.k <= 1 else wl.spec.k + 2
     if wl.dtype == "c128":
         upd = 3 if oz else 1                       # digit prep rows + cols + tensor-core update, or DFMA
     else:
@@ -1068,7 +1076,7 @@ def run_deferred(args):
                          "kernel_share_of_step": kern_ms / ms,
                          "hbm_achieved_gbs_approx": bytes_cols / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else 0.0,
                          "hbm_peak_gbs": peak_hbm},
-            "gpu_launches": 7 * args.steps,
+            "gpu_launches": (6 + select_launches(opt.ncand)) * args.steps,
             "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
@@ -1145,7 +1153,7 @@ def run_full(args, deferred: bool):
             "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms / max(flips, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": cfg, "job_ms": ms, "accepted_flips": flips, "clocks": clk,
-            "gpu_launches": steps * (7 if deferred else 9)}
+            "gpu_launches": steps * ((6 if deferred else 8) + select_launches(opt.ncand))}
     print(json.dumps(line), flush=True)
     return 0
 

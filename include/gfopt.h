@@ -159,7 +159,10 @@ gf_status gf_eval_candidates(gf_handle* h, const gf_problem* probs, int32_t nlam
 /* Reduction of dFOM to the accepted candidate ids (Sec. III, CombineGlobally).  k == 1:
  * idx[0] = the lowest id with dfom >= m - tie_rel*|m| where m = max dfom.  k > 1: up to k
  * ids in (-dfom, id) order skipping conflicts; unused slots are -1.  val[] gets their dFOM.
- * *status (device) = GF_OK, or GF_ENOIMPROVE when m <= 0 (idx[0] = -1). */
+ * *status (device) = GF_OK, or GF_ENOIMPROVE when m <= 0 (idx[0] = -1).
+ * ws (optional; gf_workspace_size bytes, 256-byte aligned, else NULL): its selection area lets
+ * the k == 1 reduction run over many CTAs (from 32768 candidates: two launches) and holds the
+ * top-k passes' state; without it one CTA sweeps dfom (the same result). */
 gf_status gf_select_topk(gf_handle* h, const gf_geom* geom, const gf_cand_spec* spec,
                          const double* dfom, int64_t ncand, int32_t* idx, double* val,
                          int32_t* status, void* ws, size_t ws_bytes, void* stream);

@@ -323,9 +323,10 @@ gf_status gf_select_topk(gf_handle* h, const gf_geom* geom, const gf_cand_spec* 
                 (long long)gf_num_candidates(geom, spec));
   if (!dfom || !idx || !val || !status) return fail(h, GF_EINVAL, "dfom, idx, val and status must be non-NULL");
   if ((s = bind_device(h))) return s;
-  // the pooled top-k uses the workspace's selection area when a workspace is given
+  // the greedy choice over many CTAs and the pooled top-k use the workspace's selection area when
+  // a workspace is given
   void* sel = nullptr;
-  if (ws && spec->k > 1) {
+  if (ws) {
     const gf::WsLayout L = gf::ws_layout(*geom, 1, GF_C128, *spec);
     if (((uintptr_t)ws & 255u) == 0 && ws_bytes >= L.sel + gf::topk_scratch_bytes()) sel = (char*)ws + L.sel;
   }

@@ -1,7 +1,8 @@
 // Reduction of the candidate dFOM array to the accepted candidate ids (Sec. III: the
 // CombineGlobally stage that emits a single proposal V*; Sec. V for the top-k variant).
-// The arrays are small (one FP64 per candidate), so one CTA sweeps them with warp-shuffle
-// (value, id) reductions and writes the result and the device status word.
+// The arrays are small (one FP64 per candidate): with a workspace, the greedy choice is a pass of
+// many CTAs over contiguous chunks and one CTA that finishes it; without one (and for each
+// problem of a batch) one CTA sweeps the array.  Comparisons are on integer keys of the doubles.
 #include <math.h>
 
 #include "gf_internal.cuh"
@@ -10,6 +11,7 @@
 namespace gf {
 
 constexpr int kSelThreads = 1024;
+constexpr int64_t kSelMultiMin = 32768;   // greedy choice over many CTAs from this many candidates
 
 __device__ __forceinline__ void cand_anchor(int64_t c, int kind, int nx, int64_t P, int& ax, int& ay) {
   if (kind == GF_KIND_SINGLE) {
@@ -220,10 +222,71 @@ void launch_select_egreedy(const gf_geom& g, const gf_cand_spec& spec, const dou
                                    status);
 }
 
+// The greedy choice over many CTAs: CTA b takes the contiguous chunk [b chunk, (b + 1) chunk)
+// and writes its best (key, id); the finishing CTA reduces those to the maximum m, and the lowest
+// id with dfom >= m - tie_rel |m| lies in the first chunk whose best reaches that threshold (the
+// chunks before it hold nothing that does), so only that chunk is scanned again.  The same ids
+// and values as select_best_body.
+__global__ void __launch_bounds__(256) k_select_part(const double* __restrict__ dfom, int64_t ncand, int64_t chunk,
+                                                     long long* __restrict__ pk, int64_t* __restrict__ pi) {
+  const int64_t c0 = blockIdx.x * chunk, c1 = c0 + chunk < ncand ? c0 + chunk : ncand;
+  long long bk = ord_key(-INFINITY);
+  int64_t bid = INT64_MAX;
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) key_better(ord_key(dfom[c]), c, bk, bid);
+  block_best_key(bk, bid);
+  if (threadIdx.x == 0) {
+    pk[blockIdx.x] = bk;
+    pi[blockIdx.x] = bid;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_select_finish(const double* __restrict__ dfom, int64_t ncand, int64_t chunk,
+                                                       const long long* __restrict__ pk,
+                                                       const int64_t* __restrict__ pi, int nb, double tie_rel,
+                                                       int32_t* idx, double* val, int32_t* status) {
+  long long bk = ord_key(-INFINITY);
+  int64_t bid = INT64_MAX;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) key_better(pk[b], pi[b], bk, bid);
+  block_best_key(bk, bid);
+  const double m = key_value(bk);
+  if (!(m > 0.0)) {
+    if (threadIdx.x == 0) { idx[0] = -1; val[0] = m; *status = GF_ENOIMPROVE; }
+    return;
+  }
+  double thr = m - tie_rel * fabs(m);
+  if (!(thr <= m)) thr = m;                               // m = +inf
+  const long long tk = ord_key(thr);
+  int64_t fb = INT64_MAX;                                 // the first chunk reaching the threshold
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    if (pk[b] >= tk && b < fb) fb = b;
+  long long same = 0;
+  block_best_key(same, fb);
+  const int64_t c0 = fb * chunk, c1 = c0 + chunk < ncand ? c0 + chunk : ncand;
+  int64_t first = INT64_MAX;
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+    if (ord_key(dfom[c]) >= tk) { first = c; break; }
+  same = 0;
+  block_best_key(same, first);
+  if (threadIdx.x == 0) {
+    idx[0] = (int32_t)first;
+    val[0] = dfom[first];
+    *status = GF_OK;
+  }
+}
+
 void launch_select(const gf_geom& g, const gf_cand_spec& spec, const double* dfom, int64_t ncand,
                    int32_t* idx, double* val, int32_t* status, void* ws, cudaStream_t st) {
   if (spec.k <= 1) {
-    k_select_best<<<1, kSelThreads, 0, st>>>(dfom, ncand, spec.tie_rel, idx, val, status);
+    if (ws == nullptr || ncand < kSelMultiMin) {
+      k_select_best<<<1, kSelThreads, 0, st>>>(dfom, ncand, spec.tie_rel, idx, val, status);
+      return;
+    }
+    long long* pk = reinterpret_cast<long long*>(reinterpret_cast<char*>(ws) + topk_part_off());
+    int64_t* pi = reinterpret_cast<int64_t*>(pk + kTopkBlocks);
+    const int64_t chunk = (ncand + kTopkBlocks - 1) / kTopkBlocks;
+    const int nb = (int)((ncand + chunk - 1) / chunk);
+    k_select_part<<<nb, 256, 0, st>>>(dfom, ncand, chunk, pk, pi);
+    k_select_finish<<<1, 256, 0, st>>>(dfom, ncand, chunk, pk, pi, nb, spec.tie_rel, idx, val, status);
     return;
   }
   if (ws == nullptr) {

@@ -7,6 +7,7 @@
 // read-only data path is only valid for data that no thread writes during the launch.
 #pragma once
 
+#include <limits.h>
 #include <math.h>
 
 #include "gf_internal.cuh"
@@ -151,6 +152,7 @@ __device__ __forceinline__ bool solve_small(cplx (&A)[P][P], cplx (&b)[P], const
   }
   const double thresh = kSingularRel * norm;
   bool ok = true;
+  double dinv[P];
 #pragma unroll
   for (int c = 0; c < P; ++c) {
     // pivot: first row >= c with the largest modulus
@@ -171,9 +173,10 @@ __device__ __forceinline__ bool solve_small(cplx (&A)[P][P], cplx (&b)[P], const
       }
     }
     cplx piv = ok ? A[c][c] : mk(1.0, 0.0);
+    dinv[c] = 1.0 / abs2(piv);
 #pragma unroll
     for (int rr = c + 1; rr < P; ++rr) {
-      cplx f = cdiv(A[rr][c], piv);
+      cplx f = cdiv_r(A[rr][c], piv, dinv[c]);
 #pragma unroll
       for (int v = c; v < P; ++v) A[rr][v] = A[rr][v] - f * A[c][v];
       b[rr] = b[rr] - f * b[c];
@@ -184,9 +187,77 @@ __device__ __forceinline__ bool solve_small(cplx (&A)[P][P], cplx (&b)[P], const
     cplx acc = b[c];
 #pragma unroll
     for (int v = c + 1; v < P; ++v) acc = acc - A[c][v] * b[v];
-    b[c] = cdiv(acc, ok ? A[c][c] : mk(1.0, 0.0));
+    b[c] = cdiv_r(acc, ok ? A[c][c] : mk(1.0, 0.0), dinv[c]);
   }
   return ok;
+}
+
+// The same elimination with the pivot rule decided without square roots and the arithmetic in
+// fused multiply-adds: pivots are searched on |a|^2, and the rule |pivot| >= kSingularRel
+// ||A_active||_inf is decided against bounds of the norm (with s = sum of |re| + |im| over a row,
+// s / sqrt 2 <= sum |z| <= s, so a pivot clears the rule when |pivot|^2 >= (kSingularRel s_max)^2
+// and fails it when |pivot|^2 < (kSingularRel s_max)^2 / 2).  Returns 1 (solved), 0 (singular by
+// the rule) or -1 when a pivot falls between the two, where only the exact norm decides: the
+// caller then solves the system again with solve_small.  (On GB300 every square root, division
+// and unfused multiply-add is work on the narrow FP64 pipe, which bounds the evaluation.)
+template <int P>
+__device__ __forceinline__ int solve_small_fast(cplx (&A)[P][P], cplx (&b)[P], const bool (&active)[P]) {
+  double nu = 0.0;
+#pragma unroll
+  for (int u = 0; u < P; ++u) {
+    double su = 0.0;
+#pragma unroll
+    for (int v = 0; v < P; ++v) su += fabs(A[u][v].re) + fabs(A[u][v].im);
+    if (active[u]) nu = fmax(nu, su);
+  }
+  // squared thresholds, widened by a relative 1e-9 against the rounding of the squares
+  const double t2 = (kSingularRel * nu) * (kSingularRel * nu);
+  const double tu2 = t2 * (1.0 + 1e-9), tl2 = t2 * (0.5 * (1.0 - 1e-9));
+  int st = 1;
+  double dinv[P];
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    int r = c;
+    double best = fma(A[c][c].re, A[c][c].re, A[c][c].im * A[c][c].im);
+#pragma unroll
+    for (int rr = c + 1; rr < P; ++rr) {
+      const double m = fma(A[rr][c].re, A[rr][c].re, A[rr][c].im * A[rr][c].im);
+      if (m > best) { best = m; r = rr; }
+    }
+    if (!(best > 0.0) || best < tl2) st = 0;
+    else if (!(best >= tu2) && st == 1) st = -1;
+#pragma unroll
+    for (int rr = c + 1; rr < P; ++rr) {
+      if (rr == r) {
+#pragma unroll
+        for (int v = 0; v < P; ++v) { cplx t = A[c][v]; A[c][v] = A[rr][v]; A[rr][v] = t; }
+        cplx t = b[c]; b[c] = b[rr]; b[rr] = t;
+      }
+    }
+    if (st == 0) A[c][c] = mk(1.0, 0.0);
+    const cplx piv = A[c][c];
+    dinv[c] = 1.0 / fma(piv.re, piv.re, piv.im * piv.im);
+    // multipliers a conj(piv) / |piv|^2, then the eliminations a - f u
+    const cplx pc = mk(piv.re * dinv[c], -piv.im * dinv[c]);
+#pragma unroll
+    for (int rr = c + 1; rr < P; ++rr) {
+      const cplx a0 = A[rr][c];
+      const cplx f = mk(fma(a0.re, pc.re, -(a0.im * pc.im)), fma(a0.re, pc.im, a0.im * pc.re));
+#pragma unroll
+      for (int v = c + 1; v < P; ++v) A[rr][v] = cfms(f, A[c][v], A[rr][v]);
+      b[rr] = cfms(f, b[c], b[rr]);
+    }
+  }
+#pragma unroll
+  for (int c = P - 1; c >= 0; --c) {
+    cplx acc = b[c];
+#pragma unroll
+    for (int v = c + 1; v < P; ++v) acc = cfms(A[c][v], b[v], acc);
+    const cplx pv = A[c][c];
+    const cplx pc = mk(pv.re * dinv[c], -pv.im * dinv[c]);
+    b[c] = mk(fma(acc.re, pc.re, -(acc.im * pc.im)), fma(acc.re, pc.im, acc.im * pc.re));
+  }
+  return st;
 }
 
 // Single-pixel candidates: id = j.  p = 1, so Eq. 9 is y = E_j / (1 - G_jj d_chi).
@@ -255,6 +326,9 @@ __device__ __forceinline__ void eval_brush_body(const EvalArgs& a, const uint8_t
     for (int l = 0; l < a.nlam; ++l) {
       const EvalLam& L = a.lam[l];
       cplx EN = L.E[N];
+      cplx gN[4];                                         // the monitor row, both directions
+#pragma unroll
+      for (int u = 0; u < 4; ++u) gN[u] = ldG(L.G, a.dtype, L.ldg, N, q[u]);
 #pragma unroll
       for (int dir = 0; dir < 2; ++dir) {
         if (!valid[dir]) continue;
@@ -267,22 +341,30 @@ __device__ __forceinline__ void eval_brush_body(const EvalArgs& a, const uint8_t
           d[u] = act[u] ? dval : 0.0;
         }
         cplx A[4][4], y[4];
+        auto build = [&]() {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < 4; ++u) {
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            int b = band_of[(py[v] - py[u] + 1) * 3 + (px[v] - px[u] + 1)];
-            cplx g = L.bands[(int64_t)b * N + q[u]];
-            cplx e = mk(u == v ? 1.0 : 0.0, 0.0);
-            A[u][v] = act[u] ? e - d[v] * g : e;
+            for (int v = 0; v < 4; ++v) {
+              int b = band_of[(py[v] - py[u] + 1) * 3 + (px[v] - px[u] + 1)];
+              const cplx g = L.bands[(int64_t)b * N + q[u]];
+              const double e = u == v ? 1.0 : 0.0;
+              A[u][v] = act[u] ? mk(fma(-d[v], g.re, e), -(d[v] * g.im)) : mk(e, 0.0);
+            }
+            y[u] = act[u] ? L.E[q[u]] : mk(0.0, 0.0);
           }
-          y[u] = act[u] ? L.E[q[u]] : mk(0.0, 0.0);
+        };
+        build();
+        int st = solve_small_fast<4>(A, y, act);
+        if (st < 0) {                                     // a pivot near the threshold: the exact rule
+          build();
+          st = solve_small<4>(A, y, act) ? 1 : 0;
         }
-        if (!solve_small<4>(A, y, act)) { valid[dir] = false; continue; }
+        if (st == 0) { valid[dir] = false; continue; }
         cplx dE = mk(0.0, 0.0);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          if (act[u]) dE = dE + d[u] * (ldG(L.G, a.dtype, L.ldg, N, q[u]) * y[u]);
+          if (act[u]) dE = cfma(gN[u], mk(d[u] * y[u].re, d[u] * y[u].im), dE);
         }
         cplx Em = EN + dE;
         total[dir] += abs2(Em) - abs2(EN);
@@ -331,27 +413,84 @@ __device__ __forceinline__ void block_best(double& v, int64_t& id) {
 }
 
 // Greedy policy: m = max dfom; lowest id with dfom >= m - tie_rel |m|.
+// An integer key that orders as the doubles do (-0 equal to +0, NaN below everything), so that
+// the comparisons of a selection run on the integer units: the bit pattern, with the magnitude
+// bits of negative values inverted.  key_value inverts it.
+__device__ __forceinline__ long long ord_key(double v) {
+  long long b = __double_as_longlong(v);
+  if ((b & 0x7FFFFFFFFFFFFFFFll) > 0x7FF0000000000000ll) return LLONG_MIN;
+  if (b == (long long)0x8000000000000000ull) b = 0;
+  return b >= 0 ? b : b ^ 0x7FFFFFFFFFFFFFFFll;
+}
+__device__ __forceinline__ double key_value(long long k) {
+  return __longlong_as_double(k >= 0 ? k : k ^ 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ void key_better(long long k, int64_t id, long long& bk, int64_t& bid) {
+  if (k > bk || (k == bk && id < bid)) { bk = k; bid = id; }
+}
+// the block's best (key, id), in every thread
+__device__ __forceinline__ void block_best_key(long long& k, int64_t& id) {
+  __shared__ long long sk[32];
+  __shared__ int64_t si[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) key_better(__shfl_down_sync(0xffffffffu, k, o), __shfl_down_sync(0xffffffffu, id, o), k, id);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { sk[w] = k; si[w] = id; }
+  __syncthreads();
+  if (w == 0) {
+    k = l < (int)(blockDim.x >> 5) ? sk[l] : LLONG_MIN;
+    id = l < (int)(blockDim.x >> 5) ? si[l] : INT64_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) key_better(__shfl_down_sync(0xffffffffu, k, o), __shfl_down_sync(0xffffffffu, id, o), k, id);
+    if (l == 0) { sk[0] = k; si[0] = id; }
+  }
+  __syncthreads();
+  k = sk[0];
+  id = si[0];
+}
+
+// The greedy choice (Sec. II): the largest dFOM, and among the candidates within tie_rel of it
+// (relative) the lowest id.  One CTA; each thread keeps four loads in flight, and the comparisons
+// are on integer keys (on GB300 a double comparison is an instruction on the narrow FP64 pipe).
 __device__ __forceinline__ void select_best_body(const double* dfom, int64_t ncand, double tie_rel,
                                                  int32_t* idx, double* val, int32_t* status) {
-  double bv = -INFINITY;
+  const int64_t st = blockDim.x;
+  long long bk = ord_key(-INFINITY);
   int64_t bid = INT64_MAX;
-  for (int64_t c = threadIdx.x; c < ncand; c += blockDim.x) {
-    double v = dfom[c];
-    if (better(v, c, bv, bid)) { bv = v; bid = c; }
+  int64_t c = threadIdx.x;
+  for (; c + 3 * st < ncand; c += 4 * st) {
+    const double v0 = dfom[c], v1 = dfom[c + st], v2 = dfom[c + 2 * st], v3 = dfom[c + 3 * st];
+    key_better(ord_key(v0), c, bk, bid);
+    key_better(ord_key(v1), c + st, bk, bid);
+    key_better(ord_key(v2), c + 2 * st, bk, bid);
+    key_better(ord_key(v3), c + 3 * st, bk, bid);
   }
-  block_best(bv, bid);
-  const double m = bv;
+  for (; c < ncand; c += st) key_better(ord_key(dfom[c]), c, bk, bid);
+  block_best_key(bk, bid);
+  const double m = key_value(bk);
   if (!(m > 0.0)) {
     if (threadIdx.x == 0) { idx[0] = -1; val[0] = m; *status = GF_ENOIMPROVE; }
     return;
   }
-  const double thr = m - tie_rel * fabs(m);
+  double thr = m - tie_rel * fabs(m);
+  if (!(thr <= m)) thr = m;                               // m = +inf
+  const long long tk = ord_key(thr);
+  // each thread's first candidate at or above the threshold
   int64_t first = INT64_MAX;
-  for (int64_t c = threadIdx.x; c < ncand && c < first; c += blockDim.x) {
-    if (dfom[c] >= thr) first = c;
+  c = threadIdx.x;
+  for (; c + 3 * st < ncand; c += 4 * st) {
+    const double v0 = dfom[c], v1 = dfom[c + st], v2 = dfom[c + 2 * st], v3 = dfom[c + 3 * st];
+    if (ord_key(v0) >= tk) { first = c; break; }
+    if (ord_key(v1) >= tk) { first = c + st; break; }
+    if (ord_key(v2) >= tk) { first = c + 2 * st; break; }
+    if (ord_key(v3) >= tk) { first = c + 3 * st; break; }
   }
-  double dummy = 0.0;
-  block_best(dummy, first);    // all values equal: picks the smallest id
+  if (first == INT64_MAX)
+    for (; c < ncand; c += st)
+      if (ord_key(dfom[c]) >= tk) { first = c; break; }
+  long long same = 0;
+  block_best_key(same, first);                            // equal keys: the smallest id
   if (threadIdx.x == 0) {
     idx[0] = (int32_t)first;
     val[0] = dfom[first];

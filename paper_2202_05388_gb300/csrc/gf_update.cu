@@ -61,93 +61,152 @@ __global__ void k_capacitance_lam(CapArgs a, WsLayout L, char* ws, const uint8_t
 // ---- one large system (a single wavelength with p_max > kCapSmemP), held in the shared memory of
 // one cluster of CTAs (distributed shared memory).  One CTA per solve is bound by that SM's FP64
 // pipe (p = 128: 1.9 ms).  A = I - G_VV D is built, factorised with partial pivoting and solved
-// without leaving the cluster: physical row r (with y as its last entry) lives in CTA r % CN.  Row interchanges
-// are kept as a permutation shared by every CTA (logical position i holds physical row phys[i]),
-// so a pivot row is only read by the others, never moved, and one cluster barrier per column
-// suffices: after it every CTA reads the candidates of the column (double-buffered slots), takes
-// the same pivot (largest modulus, lowest position on ties), copies the pivot row from its owner
-// and eliminates its own rows.  Every element sees the same operations in the same order as the
-// blocked factorisation of lu_blocked (the multiplier a_rj (conj(pv) / |pv|^2), then
-// cfms(l, u_jk, a_rk) column after column, y included), and the upper solve runs in blocks of
-// kLuNB rows from the bottom as cap_tail does, so the factors, pivots, y and the dFOM are the bits
-// one CTA computes.  A pivot's value travels with its candidate, so a column costs one cluster
-// barrier and two rounds of distributed-shared-memory loads (candidates, pivot row).
-// Outputs: V, dchi, the factors (row-major, logical order), pivots and D y in the workspace, the
-// dFOM and singular flag in the control block, where k_capacitance's first attempt reads them.
-// CN = 16 CTAs where the device can hold such a cluster (a non-portable size), else 8.
-// Candidates are compared as integers: |a|^2 >= 0, and the bit patterns of non-negative doubles
-// order as the values do, so the key is the bit pattern (-1 for NaN, which never wins).  The
-// comparisons stay off GB300's narrow FP64 pipe, where every one on the per-column critical path
-// cost a warp instruction's worth of FP64 issue.
-struct CluSlot {                 // a CTA's best candidate of a column: key, position, conj(a) / |a|^2
-  cplx inv;
-  long long key;
-  int pos;
+// without leaving the cluster: physical row r (with y as its last entry) lives in CTA r % CN and
+// is never moved; the logical order is recorded per row.
+//
+// GB300's FP64 pipe is shared by the SM's four schedulers (a dependent FP64 operation of one warp
+// takes 32 ns; eight warps with dependent chains take 77 ns per operation each), so the per-column
+// chain of one warp slows down whenever other warps keep the pipe busy.  A column therefore runs in
+// two halves around one split cluster barrier:
+//   before the arrive (the chain): warp 0 reads every CTA's candidate (key, physical row,
+//   reciprocal, the entry after the pivot column) and takes the pivot (largest modulus, lowest
+//   physical row on ties), then forms the multipliers of its CTA's rows, eliminates the next column
+//   of every row, and picks the CTA's candidate for the next column, whose reciprocal it forms for
+//   every row at once while the keys are reduced.  Meanwhile warps 1-7 copy the pivot row from
+//   its owner's published candidate row.  The candidate row is then eliminated in full by warps
+//   1-7 and published with its key (a CTA's candidate is the only row others read);
+//   after the arrive (the bulk): every warp eliminates the remaining rows, while the barrier
+//   gathers the other CTAs' candidates.
+// So a column costs one cluster barrier, two rounds of distributed-shared-memory loads and one
+// chain of six dependent FP64 operations; the bulk elimination overlaps the barrier.  The
+// candidate rows and keys are double-buffered by column parity: a buffer is rewritten two columns
+// later, after a barrier that every reader of it has passed.
+// Upper solve: the inverses of the 8 x 8 diagonal blocks of U are formed in parallel (a block per
+// CTA), after which a block of x costs one barrier: every CTA computes x_b = U_bb^{-1} y_b from the
+// owners' y entries (the same bits everywhere) and updates y of its own rows above the block.
+// Outputs: V, dchi, the factors (row-major, logical order), pivots (as row interchanges in order)
+// and D y in the workspace, the dFOM and singular flag in the control block, where k_capacitance's
+// first attempt reads them.  CN = 16 CTAs where the device can hold such a cluster (a non-portable
+// size), else 8.  Candidates are compared as integers: |a|^2 >= 0, and the bit patterns of
+// non-negative doubles order as the values do, so the key is the bit pattern (-1 for NaN, which
+// never wins), off the FP64 pipe.
+struct CluSlot {                 // a CTA's candidate for the next pivot
+  cplx inv;                      // conj(a) / |a|^2 of its entry a in the pivot column
+  cplx un;                       // its entry in the column after the pivot column
+  long long key;                 // bit pattern of |a|^2 (-1: no candidate)
+  int ph;                        // its physical row (0x7fffffff: none)
 };
 __device__ __forceinline__ long long clu_key(double v) {
   const long long b = __double_as_longlong(v);
   return (b & 0x7FFFFFFFFFFFFFFFll) > 0x7FF0000000000000ll ? -1ll : b;
 }
-__device__ __forceinline__ bool clu_better(long long k, int ps, long long bk, int bps) {
-  return k > bk || (k == bk && ps < bps);
+__device__ __forceinline__ bool clu_better(long long k, int ph, long long bk, int bph) {
+  return k > bk || (k == bk && ph < bph);
 }
-// conj(a) / |a|^2 with the pivot reciprocal of the one-CTA factorisation (0 for no candidate);
-// each warp forms it for its own best candidate, so the reciprocals of a column run side by side
+// conj(a) / |a|^2 (without a branch: for no candidate, key <= 0, the value is not used)
 __device__ __forceinline__ cplx clu_inv(long long key, cplx a) {
-  if (key <= 0) return mk(0.0, 0.0);
-  const double d = rcp_nr(__longlong_as_double(key));
+  const double d = rcp_nr_i(__longlong_as_double(key > 0 ? key : 0x3FF0000000000000ll));
   return mk(a.re * d, -a.im * d);
 }
-// the CTA's best of its warps' candidates (with their reciprocals) into its slot
-__device__ __forceinline__ void clu_publish(const long long* wk, const int* wr, const cplx* wi, int nw, CluSlot& slot) {
-  int b = 0;
-  for (int w = 1; w < nw; ++w)
-    if (clu_better(wk[w], wr[w], wk[b], wr[b])) b = w;
-  slot.key = wk[b];
-  slot.pos = wr[b];
-  slot.inv = wi[b];
+// a b and |a|^2 with fused multiply-adds (two dependent FP64 operations each)
+__device__ __forceinline__ cplx clu_mul(cplx a, cplx b) {
+  return mk(fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re));
 }
+__device__ __forceinline__ double clu_abs2(cplx a) { return fma(a.re, a.re, a.im * a.im); }
+// the best (key, physical row) over lanes [0, 2 o0) of the warp, in each of those lanes (an
+// exchange butterfly, o0 a power of two); the values that go with it are then fetched from the
+// winning lane, so the reduction does not wait for them
+__device__ __forceinline__ void clu_best(long long& k, int& ph, int o0) {
+  for (int o = o0; o > 0; o >>= 1) {
+    const long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+    const int op = __shfl_xor_sync(0xffffffffu, ph, o);
+    if (clu_better(ok, op, k, ph)) {
+      k = ok;
+      ph = op;
+    }
+  }
+}
+__device__ __forceinline__ cplx clu_from(cplx v, int src) {
+  return mk(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+}
+// the split cluster barrier: each thread arrives (releasing its writes) and later waits
+// (acquiring everyone's); every thread of every CTA runs the same sequence
+__device__ __forceinline__ void clu_arrive() { asm volatile("barrier.cluster.arrive.release;\n" ::: "memory"); }
+__device__ __forceinline__ void clu_wait() { asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory"); }
+
 __host__ __device__ constexpr size_t cap_cluster_smem(int pmax, int cn) {
-  // rows (R x (pmax + 1)) | pivot row (pmax + 1) | block of the upper solve (kLuNB x kLuNB + kLuNB)
-  // | final y (pmax) | dchi (pmax) | phys, pos, V (pmax each)
-  return sizeof(cplx) * ((size_t)((pmax + cn - 1) / cn) * (pmax + 1) + (pmax + 1) + kLuNB * kLuNB + kLuNB + pmax) +
-         sizeof(double) * (size_t)pmax + sizeof(int32_t) * 3 * (size_t)pmax;
+  // rows (R x W) | candidate rows (2 W) | pivot row (W) | inverted diagonal blocks of U
+  // (nb kLuNB^2) | x (pmax) | dchi (pmax) | V, permrow, phys, pos (pmax each) | posof (R)
+  return sizeof(cplx) * ((size_t)((pmax + cn - 1) / cn) * (pmax + 1) + 3 * (size_t)(pmax + 1) +
+                         (size_t)((pmax + kLuNB - 1) / kLuNB) * kLuNB * kLuNB + pmax) +
+         sizeof(double) * (size_t)pmax + sizeof(int32_t) * (4 * (size_t)pmax + (pmax + cn - 1) / cn);
 }
 
 template <int CN>
 __global__ void __launch_bounds__(256)
     k_cap_cluster(CapArgs a, WsLayout L, char* ws, const uint8_t* state, const int32_t* idx, const int32_t* status) {
   namespace cg = cooperative_groups;
+  static_assert(kLuNB == 8, "the upper solve maps 8 x 8 blocks onto groups of 8 lanes");
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char clu_smem[];
   const int pm = L.pmax;
-  const int Rm = (pm + CN - 1) / CN;
+  const int Rm = (pm + CN - 1) / CN;                      // <= 32 (pm <= kLuMaxBlocked, CN >= 8)
   const int W = pm + 1;                                   // row stride: p columns of A, then y
+  const int nbm = (pm + kLuNB - 1) / kLuNB;
   cplx* rows = reinterpret_cast<cplx*>(clu_smem);
-  cplx* prow = rows + (size_t)Rm * W;
-  cplx* sU = prow + W;                                    // kLuNB x kLuNB block of U, then its y
-  cplx* yfin = sU + kLuNB * kLuNB + kLuNB;
-  double* sD = reinterpret_cast<double*>(yfin + pm);
-  int32_t* phys = reinterpret_cast<int32_t*>(sD + pm);
+  cplx* crow = rows + (size_t)Rm * W;                     // candidate rows, by column parity
+  cplx* prow = crow + 2 * (size_t)W;
+  cplx* Zb = prow + W;                                    // block b: (U_bb)^{-1}, row-major 8 x 8
+  cplx* xfin = Zb + (size_t)nbm * kLuNB * kLuNB;
+  double* sD = reinterpret_cast<double*>(xfin + pm);
+  int32_t* sV = reinterpret_cast<int32_t*>(sD + pm);
+  int32_t* permrow = sV + pm;                             // the physical row at each logical position
+  int32_t* phys = permrow + pm;                           // CTA 0: the interchanges in order
   int32_t* pos = phys + pm;
-  int32_t* sV = pos + pm;
-  __shared__ CluSlot s_slot[2];                           // double-buffered: columns j, j + 1
-  __shared__ long long s_wk[8];
-  __shared__ int s_wr[8];
-  __shared__ cplx s_wa[8];
-  __shared__ cplx s_l[kLuMaxBlocked / 8];                 // the column's multipliers, by local row
-  __shared__ double s_dv[kLuMaxBlocked / 8];              // 1 / |u_cc|^2 of the CTA's rows (upper solve)
-  __shared__ double s_db[kLuNB];                          // CTA 0: those of the current block
+  int32_t* posof = pos + pm;                              // a local row's logical position (-1: live)
+  __shared__ CluSlot s_cands[2][CN];                      // every CTA's candidate, pushed by its owner
+  __shared__ cplx s_l[32];                                // the column's multipliers, by local row
+  __shared__ int s_bl[32];                                // the rows of the bulk elimination
+  __shared__ cplx s_inv, s_un;
+  __shared__ cplx s_T[kLuNB * kLuNB];
+  __shared__ double s_dd[kLuNB];
+  __shared__ double s_red[8], s_bv[8];
   __shared__ double s_thr, s_rmax;
-  __shared__ int s_nv, s_pr, s_bad;
-  __shared__ cplx s_inv;
-  __shared__ double s_red[32], s_bv[32];
+  __shared__ int s_nv, s_bad, s_ph, s_cand, s_nbulk;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (int)(blockDim.x >> 5);
   const int rank = (int)cl.block_rank();
   const UpdLam& U = a.u.lam[0];
   UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
+  int32_t* piv_out = reinterpret_cast<int32_t*>(ws + L.piv);
 
-  if (tid == 0) {
+  // ---- the joint set V: the candidates in order up to the first empty slot, a lane per
+  // candidate (pillars, whose pixel count has no small bound: one thread)
+  if (a.kind != GF_KIND_PILLAR && a.k <= 32) {
+    if (wid == 0) {
+      int32_t v4[kMaxPixelsPerCand];
+      double d4[kMaxPixelsPerCand];
+      const int32_t id = (lane < a.k && *status == GF_OK) ? idx[lane] : -1;
+      const unsigned neg = __ballot_sync(0xffffffffu, id < 0);
+      const int first = neg ? __ffs(neg) - 1 : 32;
+      int cnt = 0;
+      if (lane < first) cnt = cand_pixels(id, a.kind, a.dir_mask, a.u.nx, a.u.ny, a.u.chi, state, v4, d4, a.u.nz);
+      int off = cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, off, 31);
+      off -= cnt;
+      for (int u = 0; u < cnt; ++u) {
+        sV[off + u] = v4[u];
+        sD[off + u] = d4[u];
+      }
+      if (lane == 0) {
+        s_nv = total;
+        s_bad = 0;
+      }
+    }
+  } else if (tid == 0) {
     int nv = 0;
     if (*status == GF_OK)
       for (int c = 0; c < a.k; ++c) {
@@ -166,6 +225,8 @@ __global__ void __launch_bounds__(256)
     for (int t = tid; t < p; t += blockDim.x) {
       V[t] = sV[t];
       dchi[t] = sD[t];
+      phys[t] = t;
+      pos[t] = t;
     }
   }
   const int R = p > rank ? (p - rank + CN - 1) / CN : 0;  // physical rows rank + CN lr
@@ -176,10 +237,7 @@ __global__ void __launch_bounds__(256)
     rows[(size_t)lr * W + c] = mk(r == c ? 1.0 : 0.0, 0.0) - sD[c] * g;
   }
   for (int lr = tid; lr < R; lr += blockDim.x) rows[(size_t)lr * W + p] = U.E[sV[rank + CN * lr]];
-  for (int i = tid; i < p; i += blockDim.x) {
-    phys[i] = i;
-    pos[i] = i;
-  }
+  for (int lr = tid; lr < Rm; lr += blockDim.x) posof[lr] = -1;
   __syncthreads();
   double rmax = 0.0;
   for (int lr = wid; lr < R; lr += nw) {
@@ -188,31 +246,41 @@ __global__ void __launch_bounds__(256)
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
     rmax = fmax(rmax, sum);                               // lane 0 holds the row's sum
   }
-  // the candidates of column 0 (every row), a lane per row
-  long long bk = -1;
-  int bp = 0x7fffffff;
-  cplx ba = mk(0.0, 0.0);
-  for (int lr = tid; lr < R; lr += blockDim.x) {
-    const cplx a0 = rows[(size_t)lr * W];
-    const long long k = clu_key(abs2(a0));
-    const int ps = rank + CN * lr;
-    if (clu_better(k, ps, bk, bp)) { bk = k; bp = ps; ba = a0; }
+  if (lane == 0) s_red[wid] = rmax;
+  // the candidates of column 0, a lane per row
+  if (wid == 0) {
+    long long k = -1;
+    int ph = 0x7fffffff;
+    cplx iv = mk(0.0, 0.0), un = mk(0.0, 0.0);
+    if (lane < R) {
+      const cplx a0 = rows[(size_t)lane * W];
+      k = clu_key(clu_abs2(a0));
+      ph = rank + CN * lane;
+      iv = clu_inv(k, a0);
+      un = rows[(size_t)lane * W + 1];
+    }
+    clu_best(k, ph, 16);
+    const int src = ph != 0x7fffffff ? ph / CN : 0;
+    iv = clu_from(iv, src);
+    un = clu_from(un, src);
+    if (lane < CN) {                                      // lane q pushes the candidate to CTA q
+      CluSlot* d = cl.map_shared_rank(&s_cands[0][rank], lane);
+      d->key = k;
+      d->ph = ph;
+      d->inv = iv;
+      d->un = un;
+    }
+    if (lane == 0) s_cand = ph != 0x7fffffff ? ph / CN : -1;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long ok = __shfl_down_sync(0xffffffffu, bk, o);
-    const int op = __shfl_down_sync(0xffffffffu, bp, o);
-    const double ore = __shfl_down_sync(0xffffffffu, ba.re, o), oim = __shfl_down_sync(0xffffffffu, ba.im, o);
-    if (clu_better(ok, op, bk, bp)) { bk = ok; bp = op; ba = mk(ore, oim); }
-  }
-  if (lane == 0) { s_wk[wid] = bk; s_wr[wid] = bp; s_wa[wid] = clu_inv(bk, ba); s_red[wid] = rmax; }
   __syncthreads();
+  if (s_cand >= 0)
+    for (int c = tid; c <= p; c += blockDim.x) crow[c] = rows[(size_t)s_cand * W + c];
   if (tid == 0) {
     double m = 0.0;
     for (int w = 0; w < nw; ++w) m = fmax(m, s_red[w]);
     s_rmax = m;
-    clu_publish(s_wk, s_wr, s_wa, nw, s_slot[0]);
   }
-  cl.sync();
+  cl.sync();                                              // column 0's candidates, the row sums
   if (wid == 0) {                                         // the pivot threshold kSingularRel ||A||_inf
     double m = lane < CN ? *cl.map_shared_rank(&s_rmax, lane) : 0.0;
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -220,156 +288,231 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   const long long thr2_key = clu_key(s_thr * s_thr);
+  const int rspan = Rm > 16 ? 16 : Rm > 8 ? 8 : Rm > 4 ? 4 : Rm > 2 ? 2 : 1;   // lanes [0, 2 rspan) hold rows
 
-  // ---- factorisation, one cluster barrier per column
+  // ---- factorisation, one split cluster barrier per column
+  bool bad = false;
+  bool mine = lane < R;                                   // warp 0: this lane's row is not yet pivoted
   for (int j = 0; j < p; ++j) {
     const int buf = j & 1;
-    if (j > 0) cl.sync();                                 // column j's candidates are published
-    if (wid == 0) {                                       // lane q reads CTA q's candidate
+    if (j > 0) clu_wait();                                // column j's candidates are published
+    if (wid == 0) {                                       // lane q takes CTA q's candidate
       long long k = -1;
-      int ps = 0x7fffffff;
-      cplx iv = mk(0.0, 0.0);
+      int ph = 0x7fffffff;
+      cplx iv = mk(0.0, 0.0), un = mk(0.0, 0.0);
       if (lane < CN) {
-        const CluSlot* sl = cl.map_shared_rank(&s_slot[buf], lane);
-        k = sl->key;
-        ps = sl->pos;
-        iv = sl->inv;
+        const CluSlot& sl = s_cands[buf][lane];
+        k = sl.key;
+        ph = sl.ph;
+        iv = sl.inv;
+        un = sl.un;
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long ok = __shfl_down_sync(0xffffffffu, k, o);
-        const int op = __shfl_down_sync(0xffffffffu, ps, o);
-        const double ore = __shfl_down_sync(0xffffffffu, iv.re, o), oim = __shfl_down_sync(0xffffffffu, iv.im, o);
-        if (clu_better(ok, op, k, ps)) { k = ok; ps = op; iv = mk(ore, oim); }
-      }
+      clu_best(k, ph, CN / 2);
+      const int src = ph != 0x7fffffff ? ph % CN : 0;
+      iv = clu_from(iv, src);
+      un = clu_from(un, src);
       if (lane == 0) {
         // |pv|^2 >= thresh^2 and > 0 (a NaN key is -1 and fails both)
         if (k < thr2_key || k <= 0) {
           s_bad = 1;
         } else {
-          s_pr = ps;
+          s_ph = ph;
           s_inv = iv;
-          if (rank == 0) reinterpret_cast<int32_t*>(ws + L.piv)[j] = ps;
+          s_un = un;
         }
       }
     }
-    __syncthreads();
-    if (s_bad) break;                                     // the same column in every CTA
-    const int pr = s_pr;
-    const int rp = phys[pr];                              // the pivot's physical row
-    {
-      const cplx* src = cl.map_shared_rank(rows, rp % CN) + (size_t)(rp / CN) * W;
-      for (int k = j + 1 + tid; k < W; k += blockDim.x) prow[k] = src[k];
+    __syncthreads();                                      // the pivot; this CTA's bulk of column j - 1 is done
+    if (s_bad) {                                          // the same column in every CTA
+      bad = true;
+      break;
     }
-    __syncthreads();                                      // every thread has rp and the pivot row
-    if (tid == 0) {                                       // the interchange of positions j and pr
-      const int rj = phys[j];
-      phys[j] = rp;
-      phys[pr] = rj;
-      pos[rp] = j;
-      pos[rj] = pr;
-    }
-    __syncthreads();
-    const cplx inv = s_inv;
-    // the multipliers, warp 0 with a lane per row (one FP64 pass for all rows of the CTA)
-    if (wid == 0)
-      for (int lr = lane; lr < R; lr += 32)
-        if (pos[rank + CN * lr] > j) {
-          const cplx l = rows[(size_t)lr * W + j] * inv;
-          rows[(size_t)lr * W + j] = l;
-          s_l[lr] = l;
-        }
-    __syncthreads();
+    const int rp = s_ph, w = rp % CN, lw = rp / CN;       // the pivot's physical row, owner, local row
+    long long bk = -1;                                    // warp 0: the CTA's candidate for column j + 1
+    int bph = 0x7fffffff;
+    cplx iv = mk(0.0, 0.0);
     if (wid == 0) {
-      // column j + 1 of every row first (lane per row), then its candidates and the winner's
-      // reciprocal -- the chain to the next barrier -- while warps 1.. eliminate the rest
-      bk = -1;
-      bp = 0x7fffffff;
-      ba = mk(0.0, 0.0);
-      for (int lr = lane; lr < R; lr += 32) {
-        const int ps = pos[rank + CN * lr];
-        if (ps <= j) continue;
-        cplx* row = rows + (size_t)lr * W;
-        const cplx a1 = cfms(s_l[lr], prow[j + 1], row[j + 1]);
+      const cplx inv = s_inv, un = s_un;
+      const bool piv = w == rank && lane == lw;
+      const bool live = mine && !piv;
+      cplx l = mk(0.0, 0.0), a1 = mk(0.0, 0.0);
+      if (live) {
+        cplx* row = rows + (size_t)lane * W;
+        l = clu_mul(row[j], inv);
+        row[j] = l;
+        a1 = cfms(l, un, row[j + 1]);
         row[j + 1] = a1;
-        if (j + 1 < p) {
-          const long long k1 = clu_key(abs2(a1));
-          if (clu_better(k1, ps, bk, bp)) { bk = k1; bp = ps; ba = a1; }
-        }
       }
-      if (j + 1 < p) {
-        for (int o = 16; o > 0; o >>= 1) {
-          const long long ok = __shfl_down_sync(0xffffffffu, bk, o);
-          const int op = __shfl_down_sync(0xffffffffu, bp, o);
-          const double ore = __shfl_down_sync(0xffffffffu, ba.re, o), oim = __shfl_down_sync(0xffffffffu, ba.im, o);
-          if (clu_better(ok, op, bk, bp)) { bk = ok; bp = op; ba = mk(ore, oim); }
-        }
-        if (lane == 0) {
-          s_slot[buf ^ 1].key = bk;
-          s_slot[buf ^ 1].pos = bp;
-          s_slot[buf ^ 1].inv = clu_inv(bk, ba);
-        }
+      if (piv) {
+        posof[lane] = j;
+        mine = false;
       }
-    } else if (wid & 3) {
-      // columns j + 2 .. W - 1 (y included), a row per warp; the warps that share warp 0's
-      // scheduler (wid % 4 == 0) stay out, so that its chain does not queue behind them
-      const int bw = wid - 1 - (wid >> 2), nb = nw - (nw + 3) / 4;
-      for (int lr = bw; lr < R; lr += nb) {
-        if (pos[rank + CN * lr] <= j) continue;
-        cplx* __restrict__ row = rows + (size_t)lr * W;
-        const cplx* __restrict__ pv = prow;
-        const cplx l = s_l[lr];
-#pragma unroll 4
-        for (int k = j + 2 + lane; k < W; k += 32) row[k] = cfms(l, pv[k], row[k]);
+      s_l[lane] = l;
+      if (live && j + 1 < p) {
+        bk = clu_key(clu_abs2(a1));
+        bph = rank + CN * lane;
+      }
+      // every row's reciprocal is started before the reduction of the keys, which runs on the
+      // integer and shuffle units meanwhile; the winner's is taken after the barrier below
+      iv = clu_inv(bk, a1);
+      clu_best(bk, bph, rspan);
+      bk = __shfl_sync(0xffffffffu, bk, 0);
+      bph = __shfl_sync(0xffffffffu, bph, 0);
+      const int cand = (j + 1 < p && bph != 0x7fffffff) ? bph / CN : -1;
+      const bool bulk = live && lane != cand;
+      const unsigned bm = __ballot_sync(0xffffffffu, bulk);
+      if (bulk) s_bl[__popc(bm & ((1u << lane) - 1u))] = lane;
+      if (lane == 0) {
+        s_nbulk = __popc(bm);
+        s_cand = cand;
+      }
+    } else {
+      const cplx* src = cl.map_shared_rank(crow + (size_t)buf * W, w);
+      for (int c = j + 1 + tid - 32; c <= p; c += (int)blockDim.x - 32) prow[c] = src[c];
+      if (tid == 32) permrow[j] = rp;
+      if (rank == 0 && tid == 64) {                       // the interchange of positions j and pos[rp]
+        const int ps = pos[rp], rj = phys[j];
+        piv_out[j] = ps;
+        phys[j] = rp;
+        phys[ps] = rj;
+        pos[rp] = j;
+        pos[rj] = ps;
       }
     }
-    __syncthreads();
-  }
-  const bool bad = s_bad != 0;
-  // ---- upper solve in blocks of kLuNB rows from the bottom (CTA 0 solves each block's triangle)
-  if (!bad) {
-    // the diagonal's reciprocals 1 / |u_cc|^2, every row at once (as cdiv forms them)
-    for (int lr = tid; lr < R; lr += blockDim.x) s_dv[lr] = 1.0 / abs2(rows[(size_t)lr * W + pos[rank + CN * lr]]);
-    for (int b1 = p; b1 > 0; b1 -= kLuNB) {
-      const int b0 = b1 - kLuNB > 0 ? b1 - kLuNB : 0;
-      const int w = b1 - b0;
-      cl.sync();                                          // the block's y (and the reciprocals) are final
-      if (rank == 0) {
-        for (int t = tid; t < w * (w + 2); t += blockDim.x) {
-          const int c = t / (w + 2), v = t - c * (w + 2);  // v = w: y, v = w + 1: the reciprocal
-          const int rc = phys[b0 + c];
-          const cplx* src = cl.map_shared_rank(rows, rc % CN) + (size_t)(rc / CN) * W;
-          if (v < w) sU[c * kLuNB + v] = src[b0 + v];
-          else if (v == w) sU[kLuNB * kLuNB + c] = src[p];
-          else s_db[c] = *cl.map_shared_rank(&s_dv[rc / CN], rc % CN);
-        }
-        __syncthreads();
-        if (tid == 0) {
-          cplx* yb = sU + kLuNB * kLuNB;
-          for (int c = w - 1; c >= 0; --c) {
-            cplx acc = yb[c];
-            for (int v = c + 1; v < w; ++v) acc = acc - sU[c * kLuNB + v] * yb[v];
-            yb[c] = cdiv_r(acc, sU[c * kLuNB + c], s_db[c]);
-            yfin[b0 + c] = yb[c];
+    __syncthreads();                                      // pivot row, multipliers, the CTA's candidate
+    const int cand = s_cand;
+    if (wid == 0) {
+      if (j + 1 < p) {
+        // the candidate's entry in column j + 2 (every lane forms the same bits; lane 0 stores
+        // it), then key, row, reciprocal and that entry: lane q to CTA q
+        cplx un2 = mk(0.0, 0.0);
+        if (cand >= 0) {
+          cplx* row = rows + (size_t)cand * W;
+          un2 = cfms(s_l[cand], prow[j + 2], row[j + 2]);
+          __syncwarp();
+          if (lane == 0) {
+            row[j + 2] = un2;
+            crow[(size_t)(buf ^ 1) * W + j + 2] = un2;
           }
         }
-      }
-      cl.sync();                                          // the block's solution is in CTA 0
-      {
-        const cplx* yb0 = cl.map_shared_rank(sU, 0) + kLuNB * kLuNB;
-        cplx ybl[kLuNB];
-#pragma unroll
-        for (int v = 0; v < kLuNB; ++v) ybl[v] = v < w ? yb0[v] : mk(0.0, 0.0);
-        for (int lr = tid; lr < R; lr += blockDim.x) {
-          const int ps = pos[rank + CN * lr];
-          if (ps >= b0) continue;
-          cplx* row = rows + (size_t)lr * W;
-          cplx acc = row[p];
-#pragma unroll
-          for (int v = 0; v < kLuNB; ++v)
-            if (v < w) acc = acc - row[b0 + v] * ybl[v];
-          row[p] = acc;
+        const cplx ivw = clu_from(iv, cand >= 0 ? cand : 0);
+        if (lane < CN) {
+          CluSlot* d = cl.map_shared_rank(&s_cands[buf ^ 1][rank], lane);
+          d->key = bk;
+          d->ph = bph;
+          d->inv = ivw;
+          d->un = un2;
         }
       }
+    } else if (cand >= 0) {                               // the rest of the candidate row, published
+      cplx* row = rows + (size_t)cand * W;
+      cplx* dst = crow + (size_t)(buf ^ 1) * W;
+      const cplx lc = s_l[cand];
+      for (int c = j + 1 + tid - 32; c <= p; c += (int)blockDim.x - 32) {
+        if (c == j + 2) continue;                         // warp 0's
+        cplx v = row[c];
+        if (c > j + 1) {
+          v = cfms(lc, prow[c], v);
+          row[c] = v;
+        }
+        dst[c] = v;
+      }
+    }
+    clu_arrive();                                         // column j + 1's candidates are published
+    {
+      // the bulk: columns j + 2 .. p of the remaining rows, a warp per row
+      const int nl = s_nbulk;
+      for (int q = wid; q < nl; q += nw) {
+        const int lr = s_bl[q];
+        cplx* row = rows + (size_t)lr * W;
+        const cplx l = s_l[lr];
+#pragma unroll 4
+        for (int c = j + 2 + lane; c <= p; c += 32) row[c] = cfms(l, prow[c], row[c]);
+      }
+    }
+  }
+  if (p > 0 && !bad) clu_wait();                         // the last column's arrive
+  // ---- upper solve U x = y
+  if (!bad && p > 0) {
+    const int nb = (p + kLuNB - 1) / kLuNB;
+    // the diagonal blocks inverted, block b by CTA b % CN: column k of T^{-1} by thread k, from
+    // the bottom row up (T = U_bb upper triangular, its diagonal bounded away from 0 by the
+    // pivot threshold)
+    for (int b = rank; b < nb; b += CN) {
+      const int b0 = b * kLuNB, wb = p - b0 < kLuNB ? p - b0 : kLuNB;
+      if (tid < kLuNB * kLuNB) {
+        const int i = tid >> 3, m = tid & 7;
+        cplx v = mk(0.0, 0.0);
+        if (i < wb && m < wb && m >= i) {
+          const int rc = permrow[b0 + i];
+          v = cl.map_shared_rank(rows, rc % CN)[(size_t)(rc / CN) * W + b0 + m];
+        }
+        s_T[tid] = v;
+      }
+      __syncthreads();
+      if (tid < wb) s_dd[tid] = 1.0 / clu_abs2(s_T[tid * kLuNB + tid]);
+      __syncthreads();
+      cplx* Z = Zb + (size_t)b * kLuNB * kLuNB;
+      if (tid < kLuNB) {
+        const int k = tid;
+        for (int i = kLuNB - 1; i >= 0; --i) {
+          cplx z = mk(0.0, 0.0);
+          if (k < wb && i <= k) {
+            const cplx t = s_T[i * kLuNB + i];
+            const cplx ti = mk(t.re * s_dd[i], -t.im * s_dd[i]);   // 1 / T_ii
+            if (i == k) {
+              z = ti;
+            } else {
+              cplx s = mk(0.0, 0.0);
+              for (int m = i + 1; m <= k; ++m) s = cfma(s_T[i * kLuNB + m], Z[m * kLuNB + k], s);
+              z = clu_mul(s, ti);
+              z = mk(-z.re, -z.im);
+            }
+          }
+          Z[i * kLuNB + k] = z;
+        }
+      }
+      __syncthreads();
+    }
+    cl.sync();                                            // every block's inverse is with its CTA
+    for (int t = tid; t < nb * kLuNB * kLuNB; t += blockDim.x) {
+      const int b = t / (kLuNB * kLuNB);
+      if (b % CN != rank) Zb[t] = cl.map_shared_rank(Zb, b % CN)[t];
+    }
+    __syncthreads();
+    // the blocks from the bottom, one barrier each: x_b = U_bb^{-1} y_b in every CTA (the y
+    // entries of the block's rows are final once the blocks below have been applied), then
+    // y_r -= U_rb x_b for the CTA's rows above the block
+    for (int b = nb - 1; b >= 0; --b) {
+      const int b0 = b * kLuNB, wb = p - b0 < kLuNB ? p - b0 : kLuNB;
+      if (b < nb - 1) clu_wait();                         // the updates of the block below
+      if (tid < kLuNB * kLuNB) {                          // warps 0 and 1: lane group i, lane m
+        const int i = tid >> 3, m = tid & 7;
+        cplx pr = mk(0.0, 0.0);
+        if (i < wb && m < wb && m >= i) {
+          const int rc = permrow[b0 + m];
+          const cplx ym = cl.map_shared_rank(rows, rc % CN)[(size_t)(rc / CN) * W + p];
+          pr = clu_mul(Zb[(size_t)b * kLuNB * kLuNB + i * kLuNB + m], ym);
+        }
+        for (int o = 4; o > 0; o >>= 1) {
+          pr.re += __shfl_xor_sync(0xffffffffu, pr.re, o);
+          pr.im += __shfl_xor_sync(0xffffffffu, pr.im, o);
+        }
+        if (m == 0 && i < wb) xfin[b0 + i] = pr;
+      }
+      __syncthreads();
+      {                                                   // thread (local row tid / 8, block column tid % 8)
+        const int lr = tid >> 3, m = tid & 7;
+        const bool act = lr < R && posof[lr] < b0;
+        cplx pr = mk(0.0, 0.0);
+        if (act && m < wb) pr = clu_mul(rows[(size_t)lr * W + b0 + m], xfin[b0 + m]);
+        for (int o = 4; o > 0; o >>= 1) {
+          pr.re += __shfl_xor_sync(0xffffffffu, pr.re, o);
+          pr.im += __shfl_xor_sync(0xffffffffu, pr.im, o);
+        }
+        if (act && m == 0) rows[(size_t)lr * W + p] = rows[(size_t)lr * W + p] - pr;
+      }
+      if (b > 0) clu_arrive();                            // released to the next block's readers
     }
   }
   // ---- outputs: the factors in logical row order; CTA 0: dFOM (Eq. 4 at the monitor) and D y
@@ -377,7 +520,7 @@ __global__ void __launch_bounds__(256)
     cplx* A = reinterpret_cast<cplx*>(ws + L.lu);
     for (int t = tid; t < R * p; t += blockDim.x) {
       const int lr = t / p, c = t - lr * p;
-      A[(size_t)pos[rank + CN * lr] * p + c] = rows[(size_t)lr * W + c];
+      A[(size_t)posof[lr] * p + c] = rows[(size_t)lr * W + c];
     }
   }
   if (rank == 0) {
@@ -388,13 +531,16 @@ __global__ void __launch_bounds__(256)
         cplx part = mk(0.0, 0.0);
         for (int u = tid; u < p; u += blockDim.x) {
           const cplx gm = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, u, m) : ldG(U.G, a.u.dtype, U.ldg, m, sV[u]);
-          part = part + sD[u] * (gm * yfin[u]);
+          part = part + sD[u] * (gm * xfin[u]);
         }
         for (int o = 16; o > 0; o >>= 1) {
           part.re += __shfl_down_sync(0xffffffffu, part.re, o);
           part.im += __shfl_down_sync(0xffffffffu, part.im, o);
         }
-        if (lane == 0) { s_bv[wid] = part.re; s_red[wid] = part.im; }
+        if (lane == 0) {
+          s_bv[wid] = part.re;
+          s_red[wid] = part.im;
+        }
         __syncthreads();
         if (tid == 0) {
           cplx dE = mk(0.0, 0.0);
@@ -405,7 +551,7 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
       }
       cplx* yd = reinterpret_cast<cplx*>(ws + L.yd);
-      for (int u = tid; u < p; u += blockDim.x) yd[u] = sD[u] * yfin[u];
+      for (int u = tid; u < p; u += blockDim.x) yd[u] = sD[u] * xfin[u];
     }
     if (tid == 0) {
       ctl->lam_df[0] = df;

@@ -111,6 +111,16 @@ def test_topk_trajectory():
     assert done >= 2
 
 
+def test_top32_c128_trajectory():
+    """Top-32 brushes in complex128: every joint capacitance system (a workspace for up to 128
+    pixels) is factorised and solved in one cluster of CTAs, whose factors and row interchanges
+    then give the FP64 panels."""
+    wl = W.small(26, 22, kind=W.KIND_BRUSH2, dir_mask=3, k=32, excl_radius=2, steps=4)
+    state = W.random_state(26 * 22, seed=27, fill=0.3)
+    done, _ = run_parity(wl, 4, state=state)
+    assert done >= 2
+
+
 def test_multi_wavelength_trajectory():
     wl = W.small(10, 6, kind=W.KIND_BRUSH2, dir_mask=3, wavelengths=(0.9, 1.0, 1.1), steps=5)
     state = W.random_state(60, seed=25, fill=0.3)
@@ -245,6 +255,61 @@ def test_pooled_topk_selection_matches_oracle(nx, ny, k, seed):
         got = [int(x) for x in idx.cpu().numpy() if x >= 0]
         assert got == ref, (trial, got[:5], ref[:5])
         assert int(st.cpu()[0]) == (B.GF_OK if ref else B.GF_ENOIMPROVE)
+
+
+@pytest.mark.parametrize("nx,ny,kind,seed", [(200, 200, W.KIND_SINGLE, 81), (193, 192, W.KIND_BRUSH2, 82)])
+def test_greedy_selection_over_many_ctas_matches_oracle(nx, ny, kind, seed):
+    """The greedy choice (k = 1) from 32768 candidates runs as a pass of many CTAs over chunks and
+    a finishing CTA: against the oracle's select_best, and bit for bit against the one-CTA sweep
+    (no workspace), on random arrays, arrays with nothing improving, exact ties of the maximum
+    in several chunks, and a near tie (within tie_rel) in an earlier chunk than the maximum."""
+    g = W.small(nx, ny, kind=kind).geoms[0]
+    spec = W.CandidateSpec(kind, 3, k=1)
+    h = B.Handle(0)
+    nc = h.gf_num_candidates(g, spec)
+    assert nc >= 32768
+    rng = np.random.default_rng(seed)
+    ws_bytes = h.gf_workspace_size(g, 1, B.GF_C128, spec)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    chunk = -(-nc // 148)
+    for trial in range(6):
+        d = rng.normal(size=nc)
+        if trial == 1:
+            d = -np.abs(d)                                  # nothing improves
+        if trial == 2:
+            d[[nc - 5, 7 * chunk + 3, 2 * chunk - 1, 40 * chunk]] = 10.0      # exact ties of the max
+        if trial == 3:
+            d[nc - 1] = 10.0
+            d[3 * chunk] = 10.0 * (1.0 - 0.25 * spec.tie_rel)               # within tie_rel, earlier
+            d[chunk - 1] = 10.0 * (1.0 - 4.0 * spec.tie_rel)                # outside it
+        if trial == 4:
+            d[rng.random(nc) < 0.999] = -np.inf             # sparse improving set
+        if trial == 5:
+            d[rng.random(nc) < 0.01] = np.nan               # NaN never wins (GPU paths only)
+        out = []
+        for w in (ws, None):
+            dt = torch.tensor(d, dtype=torch.float64, device="cuda")
+            idx = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+            val = torch.empty(1, dtype=torch.float64, device="cuda")
+            st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+            h.gf_select_topk(g, spec, dt, nc, idx, val, st, w, ws_bytes if w is not None else 0)
+            torch.cuda.synchronize()
+            out.append((int(idx.cpu()[0]), float(val.cpu()[0]), int(st.cpu()[0])))
+        assert out[0][0] == out[1][0] and out[0][2] == out[1][2], (trial, out)
+        assert np.array_equal(np.float64(out[0][1]), np.float64(out[1][1])), (trial, out)
+        if trial == 5:
+            ref = O.select_best(np.where(np.isnan(d), -np.inf, d), spec.tie_rel)
+        else:
+            ref = O.select_best(d, spec.tie_rel)
+        got, v, s = out[0]
+        if ref is None:
+            assert s == B.GF_ENOIMPROVE and got == -1, (trial, out)
+        else:
+            assert s == B.GF_OK and got == ref and v == d[ref], (trial, got, ref)
+        if trial == 2:
+            assert got == 2 * chunk - 1
+        if trial == 3:
+            assert got == 3 * chunk
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
