@@ -267,7 +267,7 @@ void build_batch_plan(BatchPlan& P, const BatchItem* host_items, int nprob, int 
                                : cdiv64(cdiv64(n, rows) * cdiv64(n, kF32Cols), P.upd_tiles);
           break;
         case kStFinish: c = cdiv64(n, per); break;
-        case kStBands: c = cdiv64((int64_t)GF_NBANDS * N, per); break;
+        case kStBands: c = cdiv64(N, per); break;
         default: break;
       }
       P.first[s][q] = (int32_t)acc;

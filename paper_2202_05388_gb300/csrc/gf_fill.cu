@@ -169,7 +169,7 @@ __global__ void k_bands_batch(const BatchItem* __restrict__ items, int dtype) {
 }
 
 void launch_bands_batch(const BatchItem* items, int nprob, int dtype, int64_t widest, cudaStream_t st) {
-  int64_t b = (GF_NBANDS * widest + 255) / 256;      // widest: pixels of the largest problem
+  int64_t b = (widest + 255) / 256;                  // widest: pixels of the largest problem
   if (b > 1216) b = 1216;
   k_bands_batch<<<dim3((unsigned)(b < 1 ? 1 : b), (unsigned)nprob), 256, 0, st>>>(items, dtype);
 }
@@ -221,7 +221,7 @@ void launch_fill_field(const gf_geom& g, cplx* E, cudaStream_t st) {
 void launch_bands(const gf_geom& g, int dtype, const void* G, int64_t ldg, cplx* bands,
                   cudaStream_t st) {
   const int64_t N = (int64_t)g.nx * g.ny;
-  k_bands<<<grid_for(GF_NBANDS * N, 256), 256, 0, st>>>(g.nx, g.ny, dtype, G, ldg, bands);
+  k_bands<<<grid_for(N, 256), 256, 0, st>>>(g.nx, g.ny, dtype, G, ldg, bands);
 }
 
 }  // namespace gf

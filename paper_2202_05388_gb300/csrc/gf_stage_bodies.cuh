@@ -37,21 +37,51 @@ __host__ __device__ __forceinline__ int oz_off(int r, int k) {
 }
 
 // six signed 9-bit digits of x in (-1, 1): x = sum_a d[a] 2^(-9(a+1)) + r, |r| <= 2^-55
-__device__ __forceinline__ void oz_digits(double x, float (&d)[kOzS]) {
-  double r = x;
-#pragma unroll
-  for (int a = 0; a < kOzS; ++a) {
-    const double sc = ldexp(1.0, kOzW * (a + 1));
-    double t = rint(r * sc);
-    d[a] = (float)t;
-    r = r - t * ldexp(1.0, -kOzW * (a + 1));
+// The digits of x = v 2^-E (|v| < 2^E), six signed digits of kOzW = 9 bits from the top:
+// the FP64 sequence d_a = rint(r_a 2^(9(a+1))), r_(a+1) = r_a - d_a 2^(-9(a+1)) (r_0 = x, every
+// step exact) restated in integers, since on GB300 each of its FP64 operations, roundings and
+// conversions would run on the narrow FP64 pipe, which then bounds the preparation:
+// X = x 2^54 rounded to an integer (ties to even), then d_a = X_a / 2^(45 - 9a) rounded to the
+// nearest integer (ties to even), X_(a+1) = X_a - d_a 2^(45 - 9a), and the last digit is the
+// remainder.  The digits sum to x rounded at 2^-54, as the FP64 sequence's do, within the same
+// bounds (|d_0| <= 512, |d_a| <= 256); where the rounding at 2^-54 first makes a digit's
+// remainder an exact tie, the two resolve it differently from that digit on (about one value in
+// 2000, the same sum).  A CPU model of both is in tests/test_oz_digits_cpu.py.
+__device__ __forceinline__ void oz_digits_i(double v, int E, float (&d)[kOzS]) {
+  const long long b = __double_as_longlong(v);
+  const int ef = (int)((b >> 52) & 0x7FF);
+  const long long M = (b & 0x000FFFFFFFFFFFFFll) | (ef ? 0x0010000000000000ll : 0ll);
+  const int sh = (ef ? ef : 1) - 1075 + 54 - E;           // v 2^(54 - E) = M 2^sh
+  long long X;
+  if (sh >= 0) {
+    X = M << (sh < 63 ? sh : 63);                         // |v| < 2^E keeps M 2^sh below 2^54
+  } else if (sh > -54) {
+    const int s = -sh;
+    const long long q = M >> s, rem = M & ((1ll << s) - 1), half = 1ll << (s - 1);
+    X = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+  } else {
+    X = 0;                                                // below half a unit of 2^-54
   }
+  if (b < 0) X = -X;
+#pragma unroll
+  for (int a = 0; a < kOzS - 1; ++a) {
+    const int sft = 45 - kOzW * a;
+    const long long da = (X + (1ll << (sft - 1)) - 1 + ((X >> sft) & 1)) >> sft;
+    d[a] = (float)da;
+    X -= da << sft;
+  }
+  d[kOzS - 1] = (float)X;
 }
 
-__device__ __forceinline__ int oz_exponent(double m) {
-  // smallest E with m < 2^E (m > 0); a zero row/column gets digits 0 and any exponent
-  return m > 0.0 ? ilogb(m) + 1 : 0;
+// The smallest E with m < 2^E for the largest |v| of a row (column), m > 0, given as the bit
+// pattern of m (non-negative doubles order as their bit patterns do); 0 for a zero row, whose
+// digits are 0 under any exponent
+__device__ __forceinline__ int oz_exponent_bits(long long mb) {
+  if (mb <= 0) return 0;
+  const int ef = (int)(mb >> 52);
+  return (ef ? ef - 1023 : (63 - __clzll(mb)) - 1074) + 1;
 }
+__device__ __forceinline__ long long oz_mag(double v) { return __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFll; }
 
 // ---- operand preparation (once per step, O(n p) work) --------------------------------------
 __device__ __forceinline__ void oz_prep_rows_body(const cplx* C0, int pmax, int64_t n,
@@ -70,16 +100,16 @@ __device__ __forceinline__ void oz_prep_rows_body(const cplx* C0, int pmax, int6
       v[k] = c.re;
       v[4 + k] = c.im;
     }
-    double m = 0.0;
+    long long mb = 0;
 #pragma unroll
-    for (int k = 0; k < kOzK; ++k) m = fmax(m, fabs(v[k]));
-    const int E = oz_exponent(m);
+    for (int k = 0; k < kOzK; ++k) mb = oz_mag(v[k]) > mb ? oz_mag(v[k]) : mb;
+    const int E = oz_exponent_bits(mb);
     ozE[i] = E;
     uint8_t* tile = ozA + (i / kOzM) * (int64_t)kOzTileA;
     const int r = (int)(i % kOzM);
     float dg[kOzK][kOzS];
 #pragma unroll
-    for (int k = 0; k < kOzK; ++k) oz_digits(ldexp(v[k], -E), dg[k]);
+    for (int k = 0; k < kOzK; ++k) oz_digits_i(v[k], E, dg[k]);
 #pragma unroll
     for (int a = 0; a < kOzS; ++a) {
       float4* q0 = reinterpret_cast<float4*>(tile + a * kOzSliceA + oz_off(r, 0));
@@ -106,15 +136,18 @@ __device__ __forceinline__ void oz_prep_cols_body(const cplx* S, int64_t n, int6
       sr[k] = s.re;
       si[k] = s.im;
     }
-    double m = 0.0;
+    long long mb = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) m = fmax(m, fmax(fabs(sr[k]), fabs(si[k])));
-    const int F = oz_exponent(m);
+    for (int k = 0; k < 4; ++k) {
+      mb = oz_mag(sr[k]) > mb ? oz_mag(sr[k]) : mb;
+      mb = oz_mag(si[k]) > mb ? oz_mag(si[k]) : mb;
+    }
+    const int F = oz_exponent_bits(mb);
     float dr[4][kOzS], di[4][kOzS];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      oz_digits(ldexp(sr[k], -F), dr[k]);
-      oz_digits(ldexp(si[k], -F), di[k]);
+      oz_digits_i(sr[k], F, dr[k]);
+      oz_digits_i(si[k], F, di[k]);
     }
     const int64_t c_re = 2 * j;
     uint8_t* tile = ozB + (c_re / kOzN) * (int64_t)kOzBBlockG;
@@ -553,17 +586,20 @@ __device__ __forceinline__ void bands_body(int nx, int ny, int dtype, const void
   // vb, vg: a virtual block index and count (a work item of a persistent kernel); -1: the grid's
   const int64_t vb_ = vb < 0 ? (int64_t)blockIdx.x : vb, vg_ = vg < 0 ? (int64_t)gridDim.x : vg;
   const int64_t N = (int64_t)nx * ny;
-  for (int64_t t = vb_ * (int64_t)blockDim.x + threadIdx.x; t < GF_NBANDS * N;
-       t += (int64_t)vg_ * blockDim.x) {
-    int b = (int)(t / N);
-    int64_t i = t - (int64_t)b * N;
-    int iy = (int)(i / nx), ix = (int)(i % nx);
-    int ddx, ddy;
-    band_offset(b, ddx, ddy);
-    int jx = ix + ddx, jy = iy + ddy;
-    cplx v = mk(0.0, 0.0);
-    if (jx >= 0 && jx < nx && jy >= 0 && jy < ny) v = ldG(G, dtype, ldg, i, (int64_t)jy * nx + jx);
-    bands[t] = v;
+  // a thread per pixel: its nine entries lie in three runs of three neighbouring columns of row
+  // i, loaded together; each band is then written with consecutive pixels in consecutive threads
+  for (int64_t i = vb_ * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)vg_ * blockDim.x) {
+    const int iy = (int)(i / nx), ix = (int)(i - (int64_t)iy * nx);
+    cplx v[GF_NBANDS];
+#pragma unroll
+    for (int b = 0; b < GF_NBANDS; ++b) {
+      int ddx, ddy;
+      band_offset(b, ddx, ddy);
+      const int jx = ix + ddx, jy = iy + ddy;
+      v[b] = (jx >= 0 && jx < nx && jy >= 0 && jy < ny) ? ldG(G, dtype, ldg, i, (int64_t)jy * nx + jx) : mk(0.0, 0.0);
+    }
+#pragma unroll
+    for (int b = 0; b < GF_NBANDS; ++b) bands[(int64_t)b * N + i] = v[b];
   }
 }
 
@@ -817,6 +853,143 @@ inline __device__ double cap_tail(const CapArgs& a, const UpdLam& U, int p, cons
   return df;
 }
 
+// cap_lam for p <= kMaxPixelsPerCand (a candidate's pixels, one monitor unknown) in warp 0,
+// without block-wide barriers: lane (r, c) = 8 r + c holds entry (r, c) of [A | y] (c < 4: A,
+// c = 4: y) and, outside the interchanges, G[m, V[r]] (c = 5) and E[m] (lane 6), gathered in one
+// round of loads.  Each step of the general path (cap_build's row sums, lu_blocked's pivot,
+// reciprocal, interchange, multipliers and eliminations, cap_tail's forward and upper solves and
+// Eq. 4) is one warp instruction sequence over the lanes, with the operands of every element in
+// the general path's order -- the same bits (the forward solve's updates of y are its
+// eliminations; the upper solve's reciprocals are formed in parallel, cdiv_r giving cdiv's bits).
+// On GB300 a warp's FP64 instruction costs the SM's FP64 pipe the same with one lane or 32, so
+// one lane running the whole solve would take as long as the barriers it saves.  Returns as
+// cap_lam, after one barrier that gives every thread the outcome.
+inline __device__ bool cap_lam_small(const CapArgs& a, const WsLayout& L, char* ws, int l, int p,
+                                     const int32_t* V, const double* dchi, double* df_out) {
+  constexpr int Q = kMaxPixelsPerCand;
+  static_assert(Q == 4, "four rows of eight lanes");
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ double s_out;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    const UpdLam& U = a.u.lam[l];
+    const int lane = tid, r = lane >> 3, c = lane & 7;
+    const bool rowv = r < p;
+    const int64_t m = a.u.mrow;
+    const int32_t vr = rowv ? V[r] : 0;
+    const double dr = rowv ? dchi[r] : 0.0;
+    cplx x = mk(0.0, 0.0);
+    if (rowv && c < p) {
+      const int32_t vc = V[c];
+      const cplx g = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, r, vc) : ldG(U.G, a.u.dtype, U.ldg, vr, vc);
+      x = mk(r == c ? 1.0 : 0.0, 0.0) - dchi[c] * g;
+    } else if (rowv && c == 4) {
+      x = U.E[vr];
+    } else if (rowv && c == 5) {
+      x = U.vrows ? ldG(U.vrows, a.u.dtype, U.ldv, r, m) : ldG(U.G, a.u.dtype, U.ldg, m, vr);
+    } else if (lane == 6) {
+      x = U.E[m];
+    }
+    auto sh = [&](cplx v, int src) { return mk(__shfl_sync(FULL, v.re, src), __shfl_sync(FULL, v.im, src)); };
+    // cap_build's threshold: each row's sum of |a| in column order, the largest over the rows
+    const double ax = (rowv && c < p) ? cabs1(x) : 0.0;
+    double srow = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const double t = __shfl_sync(FULL, ax, (lane & ~7) + q);
+      if (q < p) srow += t;
+    }
+    double rs = 0.0;
+#pragma unroll
+    for (int rr = 0; rr < Q; ++rr) {
+      const double t = __shfl_sync(FULL, srow, rr * 8);
+      if (rr < p) rs = fmax(rs, t);
+    }
+    const double thresh = kSingularRel * rs;
+    bool ok = true;
+    int pv[Q] = {0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      if (j >= p || !ok) continue;
+      // the pivot: the largest |a|^2 of column j at or below row j, the lowest row on ties
+      const double v = abs2(x);
+      double bv = -1.0;
+      int br = j;
+#pragma unroll
+      for (int rr = 0; rr < Q; ++rr) {
+        const double t = __shfl_sync(FULL, v, rr * 8 + j);
+        if (rr >= j && rr < p && t > bv) { bv = t; br = rr; }
+      }
+      if (!(bv >= thresh * thresh) || !(bv > 0.0)) { ok = false; continue; }
+      const cplx pvv = sh(x, br * 8 + j);
+      const double d = rcp_nr(bv);
+      const cplx inv = mk(pvv.re * d, -pvv.im * d);
+      pv[j] = br;
+      // the interchange of rows j and br (A and y)
+      const cplx xj = sh(x, j * 8 + c), xb = sh(x, br * 8 + c);
+      if (c <= 4 && br != j) {
+        if (r == j) x = xb;
+        else if (r == br) x = xj;
+      }
+      // the multipliers, then the eliminations of the columns right of j and of y
+      if (r > j && r < p && c == j) x = x * inv;
+      const cplx f = sh(x, r * 8 + j), u = sh(x, j * 8 + c);
+      if (r > j && r < p && ((c > j && c < p) || c == 4)) x = cfms(f, u, x);
+    }
+    double df = 0.0;
+    if (ok) {
+      // the upper solve from the bottom, the solution in every lane
+      const double dd = (rowv && c == r) ? 1.0 / abs2(x) : 0.0;
+      cplx xs[Q];
+#pragma unroll
+      for (int cc = Q - 1; cc >= 0; --cc) {
+        xs[cc] = mk(0.0, 0.0);
+        if (cc >= p) continue;
+        cplx acc = sh(x, cc * 8 + 4);
+#pragma unroll
+        for (int v = 0; v < Q; ++v)
+          if (v > cc && v < p) acc = acc - sh(x, cc * 8 + v) * xs[v];
+        xs[cc] = cdiv_r(acc, sh(x, cc * 8 + cc), __shfl_sync(FULL, dd, cc * 8 + cc));
+      }
+      // Eq. 4 at the monitor: the block reduction's order for terms 0..3, (t0 + t2) + (t1 + t3)
+      cplx t[Q];
+#pragma unroll
+      for (int uu = 0; uu < Q; ++uu) {
+        const cplx gm = sh(x, uu * 8 + 5);
+        const double du = __shfl_sync(FULL, dr, uu * 8);
+        t[uu] = uu < p ? du * (gm * xs[uu]) : mk(0.0, 0.0);
+      }
+      const cplx dE = (t[0] + t[2]) + (t[1] + t[3]);
+      const cplx EN = sh(x, 6);
+      df = abs2(EN + dE) - abs2(EN);
+      // outputs: the factors, the interchanges, D y
+      cplx* Aw = reinterpret_cast<cplx*>(ws + L.lu + l * L.lu_s);
+      int32_t* piv = reinterpret_cast<int32_t*>(ws + L.piv + l * L.piv_s);
+      cplx* yw = reinterpret_cast<cplx*>(ws + L.yd + l * L.yd_s);
+      if (rowv && c < p) Aw[r * p + c] = x;
+      cplx xl = xs[0];
+      int pl = pv[0];
+#pragma unroll
+      for (int q = 1; q < Q; ++q)
+        if (lane == q) { xl = xs[q]; pl = pv[q]; }
+      if (lane < p) {
+        piv[lane] = pl;
+        yw[lane] = dchi[lane] * xl;
+      }
+    }
+    if (lane == 0) {
+      s_ok = ok ? 1 : 0;
+      s_out = df;
+    }
+  }
+  __syncthreads();
+  const bool ok = s_ok != 0;
+  *df_out = s_out;
+  __syncthreads();
+  return ok;
+}
+
 // One wavelength of the capacitance solve for the set V (p pixels, contrasts dchi): A = I - G_VV D
 // (Eq. 9), its LU with partial pivoting, y = A^{-1} E_V and the dFOM of Eq. 4 at the monitor into
 // *df (every thread); the factors, pivots and D y go to the wavelength's workspace slots.  With sA
@@ -825,6 +998,7 @@ inline __device__ double cap_tail(const CapArgs& a, const UpdLam& U, int p, cons
 // Returns false (in every thread) when A is singular.
 inline __device__ bool cap_lam(const CapArgs& a, const WsLayout& L, char* ws, int l, int p, const int32_t* V,
                         const double* dchi, cplx* sA, double* df_out) {
+  if (p <= kMaxPixelsPerCand && a.u.mcount == 1) return cap_lam_small(a, L, ws, l, p, V, dchi, df_out);
   const int tid = threadIdx.x;
   const UpdLam& U = a.u.lam[l];
   cplx* Aw = reinterpret_cast<cplx*>(ws + L.lu + l * L.lu_s);
@@ -1024,6 +1198,14 @@ __device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L,
     cplx* C0 = reinterpret_cast<cplx*>(ws + L.C0 + l * L.panel_s);
     cplx* S = reinterpret_cast<cplx*>(ws + L.S + l * L.panel_s);
     const int64_t jend = U.rows > n ? U.rows : n;
+    // the reciprocals 1 / |u_cc|^2 of the upper solve, once per CTA (cdiv_r with them gives
+    // cdiv's bits); the first barrier keeps the previous wavelength's or work item's readers
+    __shared__ double s_dinv[kMaxPixelsPerCand];
+    if (want_S && p <= kMaxPixelsPerCand) {
+      __syncthreads();
+      if (threadIdx.x < p) s_dinv[threadIdx.x] = 1.0 / abs2(A[threadIdx.x * p + threadIdx.x]);
+      __syncthreads();
+    }
     for (int64_t j = vb_ * (int64_t)blockDim.x + threadIdx.x; j < jend;
          j += (int64_t)vg_ * blockDim.x) {
       if (j < U.rows)
@@ -1060,7 +1242,7 @@ __device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L,
 #pragma unroll
             for (int v = c + 1; v < kMaxPixelsPerCand; ++v)
               if (v < p) acc = acc - A[c * p + v] * x[v];
-            x[c] = cdiv(acc, A[c * p + c]);
+            x[c] = cdiv_r(acc, A[c * p + c], s_dinv[c]);
           }
         }
 #pragma unroll

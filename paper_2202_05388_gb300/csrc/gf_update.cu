@@ -22,8 +22,9 @@ namespace gf {
 __global__ void k_capacitance(CapArgs a, WsLayout L, char* ws, const uint8_t* __restrict__ state,
                               const int32_t* __restrict__ idx, int32_t* status, int pre) {
   extern __shared__ __align__(16) unsigned char cap_smem[];
-  capacitance_body(a, L, ws, state, idx, status, L.pmax <= kCapSmemP ? reinterpret_cast<cplx*>(cap_smem) : nullptr,
-                   pre != 0);
+  // p_max <= kMaxPixelsPerCand: every system of the step takes the warp form (no shared matrix)
+  const bool smem = L.pmax > kMaxPixelsPerCand && L.pmax <= kCapSmemP;
+  capacitance_body(a, L, ws, state, idx, status, smem ? reinterpret_cast<cplx*>(cap_smem) : nullptr, pre != 0);
 }
 
 // The first attempt's per-wavelength solves of a multi-wavelength step in parallel, one CTA per
@@ -51,7 +52,8 @@ __global__ void k_capacitance_lam(CapArgs a, WsLayout L, char* ws, const uint8_t
   __syncthreads();
   const int p = s_nv;
   double df = 0.0;
-  const bool ok = p > 0 ? cap_lam(a, L, ws, l, p, sV, sD, reinterpret_cast<cplx*>(cap_smem), &df) : true;
+  cplx* sA = L.pmax > kMaxPixelsPerCand ? reinterpret_cast<cplx*>(cap_smem) : nullptr;
+  const bool ok = p > 0 ? cap_lam(a, L, ws, l, p, sV, sD, sA, &df) : true;
   if (threadIdx.x == 0) {
     ctl->lam_df[l] = df;
     ctl->lam_bad[l] = ok ? 0 : 1;
@@ -857,7 +859,10 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   ca.dir_mask = spec.dir_mask;
   ca.k = spec.k < 1 ? 1 : spec.k;
   ca.pmax = L.pmax;
-  const size_t cap_smem = L.pmax <= kCapSmemP ? sizeof(cplx) * ((size_t)kCapSmemP * kCapSmemP + kCapSmemP) : 0;
+  // the shared-memory system for kMaxPixelsPerCand < p_max <= kCapSmemP (a smaller set takes the
+  // warp form, which needs none: no carve-out change between the step's kernels)
+  const size_t cap_smem = L.pmax > kMaxPixelsPerCand && L.pmax <= kCapSmemP
+                              ? sizeof(cplx) * ((size_t)kCapSmemP * kCapSmemP + kCapSmemP) : 0;
   {
     // once per device: the opt-in above the default (48 KB less the static shared memory)
     static std::mutex mu;
@@ -885,8 +890,8 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
   k_capacitance<<<1, 256, cap_smem, st>>>(ca, L, ws, state, idx, status, pre);
   const int64_t n = L.n;
   const int64_t rows = a.lam[0].rows;       // rows of G held (n, or a shard's row block)
-  // complex64 on the tensor cores: S is formed from an explicit D A^{-1} by an FP32 GEMM, so
-  // the panels kernel only gathers C0
+  // complex64 on the tensor cores: S is formed from an explicit D A^{-1} by an FP32 GEMM and C0
+  // is gathered together with the operand rows, so the panels kernel does not run
   struct Map128 { alignas(64) unsigned char b[128]; };
   Map128 maps[kMaxLam];
   // rank <= 4 complex64: an FP32 stream on the CUDA cores (HBM-bound); larger ranks: tensor cores
@@ -900,10 +905,10 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
                   (a.algo == GF_UPDATE_TENSOR || (a.algo == GF_UPDATE_TC && (double)rows * (double)n * L.pmax > kC128SmallWork));
   for (int l = 0; c64tc && l < a.nlam; ++l)
     c64tc = c64_tc_make_map(reinterpret_cast<float2*>(a.lam[l].G), a.lam[l].ldg, n, rows, maps[l].b);
-  {
+  if (!c64tc) {         // complex64 on the tensor cores gathers C0 with its operand rows
     const int64_t w = rows > n ? rows : n;
     int64_t b = (w + 255) / 256;
-    k_panels<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(a, L, ws, c64tc ? 0 : 1);
+    k_panels<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(a, L, ws, 1);
   }
   const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
   dim3 grid((unsigned)((n + kUpdThreads - 1) / kUpdThreads),

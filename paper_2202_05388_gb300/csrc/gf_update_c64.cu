@@ -232,36 +232,65 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ R
   }
 }
 
-// ---- A operand blocks from C0 (n x pmax FP64): row i -> [Re C0[i, :P), Im C0[i, :P)], scaled
-// by 2^(14 - E_i) and split into FP16 hi + lo
-__global__ void k_c64_prep_rows(const cplx* __restrict__ C0, int pmax, int64_t n, int64_t nrows_pad,
-                                const UpdCtl* __restrict__ ctl, int nkc, uint8_t* __restrict__ Aops,
-                                int32_t* __restrict__ Erow) {
+// A float widened to FP64 by integer operations (exact: the FP64 conversion instruction runs on
+// GB300's narrow FP64 pipe, which a kernel that widens every entry of C0 would then be bound by).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  const uint64_t s = (uint64_t)(b >> 31) << 63;
+  if (e == 0xFFu) return __longlong_as_double((long long)(s | 0x7FF0000000000000ull | ((uint64_t)m << 29)));
+  if (e != 0u) return __longlong_as_double((long long)(s | ((uint64_t)(e + (1023 - 127)) << 52) | ((uint64_t)m << 29)));
+  if (m == 0u) return __longlong_as_double((long long)s);
+  const int t = 31 - __clz((int)m);                       // subnormal: m 2^-149, leading bit t
+  return __longlong_as_double((long long)(s | ((uint64_t)(t - 149 + 1023) << 52) |
+                                          (((uint64_t)m << (52 - t)) & 0x000FFFFFFFFFFFFFull)));
+}
+
+// ---- C0 = G[:, V] and the A operand blocks from it, a warp per row (lane l: u = 4l .. 4l + 3).
+// The rows held are gathered once: C0 (FP64, for the field update) and the row's scaled
+// split-FP16 operands, [Re C0[i, :P), Im C0[i, :P)] scaled by 2^(14 - E_i) -- in FP32, which
+// gives the bits of the FP64 scaling of C0 (its entries are complex64 values, so the conversion
+// is exact, and a power-of-two scaling rounds once either way).  Rows [grows, nrows_pad) are
+// zero.  A warp's loads of one row merge where the set's pixels are neighbours (a brush's pairs).
+__global__ void __launch_bounds__(256) k_c64_gather_rows(const float2* __restrict__ G, int64_t ldg,
+                                                         const int32_t* __restrict__ V, int pmax, int64_t grows,
+                                                         int64_t nrows_pad, const UpdCtl* __restrict__ ctl, int nkc,
+                                                         cplx* __restrict__ C0, uint8_t* __restrict__ Aops,
+                                                         int32_t* __restrict__ Erow) {
   if (ctl->skip) return;
   const int p = ctl->nv;
   const int P = (int)c64_padP(p);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows_pad;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    uint8_t* tile = Aops + (i / kC64M) * (int64_t)nkc * kC64Block;
-    const int r = (int)(i % kC64M);
-    double m = 0.0;
-    for (int u = 0; u < p && i < n; ++u) {
-      const cplx c = C0[i * pmax + u];
-      m = fmax(m, fmax(fabs(c.re), fabs(c.im)));
+  const int lane = threadIdx.x & 31, u0 = 4 * lane;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t vc[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) vc[e] = u0 + e < p ? V[u0 + e] : -1;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nrows_pad; i += nw) {
+    float2 c[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) c[e] = (i < grows && vc[e] >= 0) ? G[i * ldg + vc[e]] : make_float2(0.f, 0.f);
+    if (i < grows) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (vc[e] >= 0) C0[i * pmax + u0 + e] = mk(f2d_bits(c[e].x), f2d_bits(c[e].y));
     }
-    int E = m > 0.0 ? ilogb(m) + 1 : 0;
-    if (E < kC64MinExp) E = kC64MinExp;
-    Erow[i] = E;
-    for (int u0 = 0; u0 < P; u0 += 4) {
+    float m = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) m = fmaxf(m, fmaxf(fabsf(c[e].x), fabsf(c[e].y)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int E = scale_exp(m);
+    if (lane == 0) Erow[i] = E;
+    if (u0 < P) {
+      const float sc = __int_as_float((127 + kC64Exp - E) << 23);
       __half rh[4], rl[4], ih[4], il[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int u = u0 + e;
-        const cplx c = (i < n && u < p) ? C0[i * pmax + u] : mk(0.0, 0.0);
-        f16_split((float)ldexp(c.re, kC64Exp - E), rh[e], rl[e]);
-        f16_split((float)ldexp(c.im, kC64Exp - E), ih[e], il[e]);
+        f16_split(c[e].x * sc, rh[e], rl[e]);
+        f16_split(c[e].y * sc, ih[e], il[e]);
       }
-      const int kA = u0, kB = P + u0;
+      uint8_t* tile = Aops + (i / kC64M) * (int64_t)nkc * kC64Block;
+      const int r = (int)(i % kC64M), kA = u0, kB = P + u0;
       uint8_t* blkA = tile + (kA / kC64KC) * kC64Block;
       uint8_t* blkB = tile + (kB / kC64KC) * kC64Block;
       const int oa = c64_off(r, kA % kC64KC), ob = c64_off(r, kB % kC64KC);
@@ -831,10 +860,11 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
     k_c64_s_gemm<<<(unsigned)(2 * o.ncp), 256, 0, st>>>(G, ldg, n, Mdai, reinterpret_cast<const int32_t*>(ws + L.V),
                                                          ctl, (int)o.nkc, Bops, Fcol);
   {
-    int64_t rows = o.nrt * kC64M;
-    int64_t b = (rows + 127) / 128;
-    k_c64_prep_rows<<<(int)(b < 4864 ? b : 4864), 128, 0, st>>>(C0, L.pmax, grows, rows, ctl, (int)o.nkc, Aops,
-                                                                 Erow);
+    const int64_t rows = o.nrt * kC64M;
+    const int64_t b = (rows + 7) / 8;                       // eight rows (warps) per CTA
+    k_c64_gather_rows<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(G, ldg, reinterpret_cast<const int32_t*>(ws + L.V),
+                                                                   L.pmax, grows, rows, ctl, (int)o.nkc,
+                                                                   const_cast<cplx*>(C0), Aops, Erow);
   }
   // once per device: shared-memory opt-in of both forms
   static std::mutex mu;
