@@ -471,6 +471,16 @@ gf_status gf_batch_selftest_timeout(gf_batch* b, int64_t timeout_ns, void* strea
  * update reports -- without faulting the GPU; later calls on the context work as usual. */
 gf_status gf_selftest_timeout(gf_handle* h, int64_t timeout_ns, int32_t* status, void* stream);
 
+/* Diagnostic of the one-launch top-k selection's grid barrier (no counterpart in the paper): the
+ * cooperative top-k kernel runs on 4096 zero dFOM values in ws with a barrier that waits for one
+ * CTA more than the grid holds, each CTA's wait giving up after timeout_ns (1 us .. 2 s); its
+ * end writes GF_ETIMEOUT to *status (device int32), without faulting the GPU.  ws: 256-byte
+ * aligned, at least gf_select_selftest_bytes() bytes (scratch, values, outputs).  GF_ECUDA when
+ * the device cannot launch a cooperative kernel. */
+size_t gf_select_selftest_bytes(void);
+gf_status gf_select_selftest_timeout(gf_handle* h, int64_t timeout_ns, void* ws, size_t ws_bytes, int32_t* status,
+                                     void* stream);
+
 /* Kernel timing (no counterpart in the paper; it backs the per-step timers of the bench).
  * gf_profile_begin arms up to max_records CUDA-event pairs that the library records on the
  * launching stream around every launch of the G-update kernel (in the deferred form: of the

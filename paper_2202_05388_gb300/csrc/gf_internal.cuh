@@ -245,6 +245,8 @@ void launch_eval(const EvalArgs& a, const uint8_t* state, const gf_cand_spec& sp
                  cudaStream_t st);
 
 size_t topk_scratch_bytes();
+size_t topk_selftest_bytes();
+bool launch_topk_selftest(void* ws, uint64_t wait_ns, int32_t* status, cudaStream_t st);
 void launch_select(const gf_geom& g, const gf_cand_spec& spec, const double* dfom, int64_t ncand,
                    int32_t* idx, double* val, int32_t* status, void* ws, cudaStream_t st);
 void launch_select_egreedy(const gf_geom& g, const gf_cand_spec& spec, const double* dfom, int64_t ncand,

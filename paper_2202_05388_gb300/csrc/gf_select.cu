@@ -5,6 +5,8 @@
 // problem of a batch) one CTA sweeps the array.  Comparisons are on integer keys of the doubles.
 #include <math.h>
 
+#include <mutex>
+
 #include "gf_internal.cuh"
 #include "gf_stage_bodies.cuh"
 
@@ -93,6 +95,8 @@ struct TopkScratch {
   int32_t ntaken;
   int32_t done;         // no improving, non-conflicting candidate is left
   int32_t pad;
+  uint32_t arrive;      // one-launch form: arrivals at its grid barriers (monotonic)
+  int32_t err;          // one-launch form: a barrier wait gave up
   int32_t ax[256], ay[256];
 };
 constexpr int kTopkBlocks = 148;
@@ -164,20 +168,135 @@ __global__ void k_topk_begin(TopkScratch* sc) {
   sc->counter = 0;
   sc->ntaken = 0;
   sc->done = 0;
+  sc->arrive = 0u;
+  sc->err = 0;
 }
 
 __global__ void k_topk_end(const TopkScratch* sc, int k, int32_t* idx, double* val, int32_t* status) {
-  const int nt = sc->ntaken;
+  const int nt = sc->err ? 0 : sc->ntaken;
   for (int t = nt + threadIdx.x; t < k; t += blockDim.x) {
     idx[t] = -1;
     val[t] = -INFINITY;
   }
-  if (threadIdx.x == 0) *status = nt > 0 ? GF_OK : GF_ENOIMPROVE;
+  if (threadIdx.x == 0) *status = sc->err ? GF_ETIMEOUT : (nt > 0 ? GF_OK : GF_ENOIMPROVE);
 }
 
-// scratch: TopkScratch | per-CTA partials | the explore list of the epsilon-greedy policy
+// ---- the same passes in one cooperative launch ----------------------------------------------
+// CTA b keeps the best valid candidate of its chunk [b chunk, (b + 1) chunk) -- dFOM > 0, not
+// taken, outside every exclusion zone (excl < 0: only the taken ids are skipped).  A pass
+// publishes every CTA's best (double-buffered by pass parity), meets at a grid barrier, and every
+// CTA reduces the same nb entries to the same winner; then only a CTA whose best is the winner or
+// lies in the winner's zone scans its chunk again: a zone only removes candidates, so every other
+// CTA's best is still its chunk's best.  The winners are those of the passes of k_topk_pass, in
+// the same order.  The barrier is a monotonic arrival count with a bounded wait: a wait that gives
+// up sets the error word, every CTA leaves at its next barrier, and k_topk_end reports
+// GF_ETIMEOUT.  The cooperative launch guarantees that all CTAs are resident together.
+constexpr uint64_t kTopkWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint64_t topk_clock() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// the best valid candidate of [c0, c1) in every thread of the CTA (key LLONG_MIN: none)
+__device__ __forceinline__ void topk_chunk_best(const double* __restrict__ dfom, int64_t c0, int64_t c1, int kind,
+                                                int nx, int64_t P, int excl, int nt, const int* tax, const int* tay,
+                                                long long& bk, int64_t& bid) {
+  bk = LLONG_MIN;
+  bid = INT64_MAX;
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    const double v = dfom[c];
+    if (!(v > 0.0)) continue;
+    const long long kc = ord_key(v);
+    if (!(kc > bk || (kc == bk && c < bid))) continue;
+    bool clash = false;
+    if (excl < 0) {
+      for (int q = 0; q < nt && !clash; ++q) clash = c == (int64_t)tax[q];
+    } else {
+      int ax, ay;
+      cand_anchor(c, kind, nx, P, ax, ay);
+      for (int q = 0; q < nt && !clash; ++q) clash = max(abs(ax - tax[q]), abs(ay - tay[q])) <= excl;
+    }
+    if (!clash) { bk = kc; bid = c; }
+  }
+  block_best_key(bk, bid);
+}
+
+__global__ void __launch_bounds__(kTopkThreads) k_topk_coop(const double* __restrict__ dfom, int64_t ncand,
+                                                           int64_t chunk, int kind, int nx, int ny, int excl, int k,
+                                                           TopkScratch* sc, long long* pk, int64_t* pi,
+                                                           int32_t* idx, double* val, uint32_t extra,
+                                                           uint64_t wait_ns) {
+  // extra: arrivals a barrier waits for beyond the grid's (0; the self-test's 1 never comes)
+  __shared__ int tax[256], tay[256];
+  __shared__ int s_stop;
+  const int nb = (int)gridDim.x, b = (int)blockIdx.x;
+  const int64_t P = (int64_t)(nx - 1) * (ny - 1);
+  const int64_t c0 = b * chunk, c1 = c0 + chunk < ncand ? c0 + chunk : ncand;
+  long long bk;
+  int64_t bid;
+  topk_chunk_best(dfom, c0, c1, kind, nx, P, excl, 0, tax, tay, bk, bid);
+  int nt = 0;
+  for (int t = 0; t < k; ++t) {
+    const int buf = t & 1;
+    if (threadIdx.x == 0) {
+      pk[buf * nb + b] = bk;
+      pi[buf * nb + b] = bid;
+      __threadfence();
+      atomicAdd(&sc->arrive, 1u);
+      const uint32_t target = (uint32_t)nb * (uint32_t)(t + 1) + extra;
+      const uint64_t t0 = topk_clock();
+      int stop = 0;
+      for (;;) {
+        uint32_t a;
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(a) : "l"(&sc->arrive) : "memory");
+        if ((int)(a - target) >= 0) break;
+        if (*reinterpret_cast<volatile int32_t*>(&sc->err)) { stop = 1; break; }
+        if (topk_clock() - t0 > wait_ns) { atomicExch(&sc->err, 1); stop = 1; break; }
+      }
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    long long wk = LLONG_MIN;
+    int64_t wi = INT64_MAX;
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) key_better(__ldcg(pk + buf * nb + q), __ldcg(pi + buf * nb + q), wk, wi);
+    block_best_key(wk, wi);
+    if (wk == LLONG_MIN) break;                           // nothing valid is left (every CTA)
+    int wax, way;
+    if (excl < 0) {
+      wax = (int)wi;
+      way = 0;
+    } else {
+      cand_anchor(wi, kind, nx, P, wax, way);
+    }
+    if (threadIdx.x == 0) {
+      tax[nt] = wax;
+      tay[nt] = way;
+      if (b == 0) {
+        idx[nt] = (int32_t)wi;
+        val[nt] = dfom[wi];
+      }
+    }
+    ++nt;
+    __syncthreads();
+    bool stale = bid == wi;
+    if (!stale && bid != INT64_MAX && excl >= 0) {
+      int ax, ay;
+      cand_anchor(bid, kind, nx, P, ax, ay);
+      stale = max(abs(ax - wax), abs(ay - way)) <= excl;
+    }
+    if (stale) topk_chunk_best(dfom, c0, c1, kind, nx, P, excl, nt, tax, tay, bk, bid);
+  }
+  if (b == 0 && threadIdx.x == 0) sc->ntaken = nt;
+}
+
+// scratch: TopkScratch | per-CTA partials | the one-launch form's bests (two buffers) | the
+// explore list of the epsilon-greedy policy
 static size_t topk_part_off() { return (sizeof(TopkScratch) + 63) & ~size_t(63); }
-static size_t explore_off() { return topk_part_off() + kTopkBlocks * (sizeof(double) + sizeof(int64_t)); }
+static size_t topk_coop_off() { return topk_part_off() + kTopkBlocks * (sizeof(double) + sizeof(int64_t)); }
+static size_t explore_off() { return topk_coop_off() + 2 * kTopkBlocks * (sizeof(long long) + sizeof(int64_t)); }
 constexpr int kExploreTop = 4;      // Sec. V: exploration draws among the four best improving actions
 
 size_t topk_scratch_bytes() { return explore_off() + kExploreTop * (sizeof(double) + sizeof(int32_t)) + 64; }
@@ -190,6 +309,42 @@ static void launch_topk_passes(const gf_geom& g, int kind, int k, int excl, cons
   int64_t blocks = (ncand + kTopkThreads - 1) / kTopkThreads;
   if (blocks > kTopkBlocks) blocks = kTopkBlocks;
   k_topk_begin<<<1, 1, 0, st>>>(sc);
+  // one cooperative launch where the device can hold every CTA at once (checked once per device)
+  static std::mutex mu;
+  static int coop_of[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int coop = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64) {
+      if (coop_of[dev] == 0) {
+        int attr = 0, per_sm = 0, sms = 0;
+        cudaDeviceGetAttribute(&attr, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_topk_coop, kTopkThreads, 0);
+        coop_of[dev] = (attr && per_sm * sms >= kTopkBlocks) ? 1 : -1;
+        cudaGetLastError();
+      }
+      coop = coop_of[dev] > 0;
+    }
+  }
+  if (coop) {
+    const int64_t chunk = (ncand + blocks - 1) / blocks;
+    const int nb = (int)((ncand + chunk - 1) / chunk);
+    long long* pk = reinterpret_cast<long long*>(reinterpret_cast<char*>(ws) + topk_coop_off());
+    int64_t* pi = reinterpret_cast<int64_t*>(pk + 2 * kTopkBlocks);
+    int gnx = g.nx, gny = g.ny;
+    uint32_t extra = 0;
+    uint64_t wait_ns = kTopkWaitNs;
+    void* args[] = {(void*)&dfom, (void*)&ncand, (void*)&chunk, (void*)&kind, (void*)&gnx, (void*)&gny, (void*)&excl,
+                    (void*)&k, (void*)&sc, (void*)&pk, (void*)&pi, (void*)&idx, (void*)&val, (void*)&extra,
+                    (void*)&wait_ns};
+    if (cudaLaunchCooperativeKernel((const void*)k_topk_coop, dim3((unsigned)nb), dim3(kTopkThreads), args, 0, st) ==
+        cudaSuccess)
+      return;
+    cudaGetLastError();                                  // refused: the passes below
+  }
   for (int t = 0; t < k; ++t)
     k_topk_pass<<<(unsigned)blocks, kTopkThreads, 0, st>>>(dfom, ncand, kind, g.nx, g.ny, excl, t, sc, part_v,
                                                            part_i, idx, val);
@@ -296,6 +451,40 @@ void launch_select(const gf_geom& g, const gf_cand_spec& spec, const double* dfo
   }
   launch_topk_passes(g, spec.kind, spec.k, spec.excl_radius, dfom, ncand, idx, val, ws, st);
   k_topk_end<<<1, 256, 0, st>>>(reinterpret_cast<const TopkScratch*>(ws), spec.k, idx, val, status);
+}
+
+// The one-launch top-k with a barrier that waits for one arrival more than the grid gives:
+// every CTA's wait runs out after wait_ns and the status word reports GF_ETIMEOUT, without a
+// fault.  ws: selection scratch, then 4096 zero dFOM values, 64 ids and 64 values.  False when
+// the device cannot launch the cooperative form.
+size_t topk_selftest_bytes() { return topk_scratch_bytes() + 4096 * sizeof(double) + 64 * (sizeof(int32_t) + sizeof(double)); }
+
+bool launch_topk_selftest(void* ws, uint64_t wait_ns, int32_t* status, cudaStream_t st) {
+  int dev = 0, attr = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&attr, cudaDevAttrCooperativeLaunch, dev);
+  if (!attr) return false;
+  char* base = reinterpret_cast<char*>(ws);
+  TopkScratch* sc = reinterpret_cast<TopkScratch*>(base);
+  const double* dfom = reinterpret_cast<const double*>(base + topk_scratch_bytes());
+  int32_t* idx = reinterpret_cast<int32_t*>(base + topk_scratch_bytes() + 4096 * sizeof(double));
+  double* val = reinterpret_cast<double*>(idx + 64);
+  cudaMemsetAsync(base + topk_scratch_bytes(), 0, 4096 * sizeof(double), st);
+  k_topk_begin<<<1, 1, 0, st>>>(sc);
+  int64_t ncand = 4096, chunk = 256;
+  int kind = GF_KIND_SINGLE, nx = 64, ny = 64, excl = 0, k = 2;
+  long long* pk = reinterpret_cast<long long*>(base + topk_coop_off());
+  int64_t* pi = reinterpret_cast<int64_t*>(pk + 2 * kTopkBlocks);
+  uint32_t extra = 1;
+  void* args[] = {(void*)&dfom, (void*)&ncand, (void*)&chunk, (void*)&kind, (void*)&nx, (void*)&ny, (void*)&excl,
+                  (void*)&k, (void*)&sc, (void*)&pk, (void*)&pi, (void*)&idx, (void*)&val, (void*)&extra,
+                  (void*)&wait_ns};
+  if (cudaLaunchCooperativeKernel((const void*)k_topk_coop, dim3(16), dim3(kTopkThreads), args, 0, st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  k_topk_end<<<1, 256, 0, st>>>(sc, k, idx, val, status);
+  return true;
 }
 
 }  // namespace gf

@@ -33,3 +33,20 @@ extern "C" gf_status gf_selftest_timeout(gf_handle* h, int64_t timeout_ns, int32
   gf::k_selftest_timeout<<<1, 32, 0, (cudaStream_t)stream>>>((uint64_t)timeout_ns, status);
   return gf::api_cuda_check(h, "gf_selftest_timeout launch");
 }
+
+extern "C" size_t gf_select_selftest_bytes(void) { return gf::topk_selftest_bytes(); }
+
+extern "C" gf_status gf_select_selftest_timeout(gf_handle* h, int64_t timeout_ns, void* ws, size_t ws_bytes,
+                                                int32_t* status, void* stream) {
+  if (!h) return GF_EINVAL;
+  if (!status || !ws || ((uintptr_t)ws & 255u) || timeout_ns < 1000 || timeout_ns > 2000000000ll)
+    return gf::api_fail_msg(h, GF_EINVAL,
+                            "status and a 256-byte aligned ws must be given and timeout_ns lie in [1 us, 2 s]");
+  if (ws_bytes < gf::topk_selftest_bytes())
+    return gf::api_fail_msg(h, GF_ENOMEM, "ws is smaller than gf_select_selftest_bytes()");
+  gf_status s = gf::api_bind_device(h);
+  if (s) return s;
+  if (!gf::launch_topk_selftest(ws, (uint64_t)timeout_ns, status, (cudaStream_t)stream))
+    return gf::api_fail_msg(h, GF_ECUDA, "the device cannot launch the one-launch top-k (cooperative launch)");
+  return gf::api_cuda_check(h, "gf_select_selftest_timeout launch");
+}

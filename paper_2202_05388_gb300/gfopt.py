@@ -36,7 +36,7 @@ EXPORTS = ["gf_create", "gf_destroy", "gf_last_error", "gf_status_string", "gf_v
            "gf_batch_set_schedule", "gf_batch_set_form", "gf_batch_selftest_timeout", "gf_batch_destroy", "gf_select_egreedy", "gf_lowrank_workspace_size",
            "gf_lowrank_init", "gf_lowrank_eval", "gf_lowrank_update", "gf_lowrank_count",
            "gf_lowrank_materialize", "gf3_num_unknowns", "gf3_num_candidates", "gf3_workspace_size",
-           "gf3_fill_g0", "gf3_eval_candidates", "gf3_select_topk", "gf3_apply_update", "gf_selftest_timeout",
+           "gf3_fill_g0", "gf3_eval_candidates", "gf3_select_topk", "gf3_apply_update", "gf_selftest_timeout", "gf_select_selftest_bytes", "gf_select_selftest_timeout",
            "gf_fom", "gf3_fom", "gf_lowrank_fom", "gf_refresh_field", "gf_shard_rows", "gf_shard_fill_g0",
            "gf_shard_eval", "gf_shard_gather_rows", "gf_shard_apply_update", "gf_shard_pack_halo",
            "gf_shard_unpack_halo"]
@@ -147,6 +147,8 @@ def load(path: str = LIB_PATH):
             "gf_select_egreedy": (C.c_int32, [P, C.POINTER(gf_geom), C.POINTER(gf_cand_spec), P, C.c_int64,
                                               C.c_double, P, P, P, P, P, C.c_size_t, P]),
             "gf_selftest_timeout": (C.c_int32, [P, C.c_int64, P, P]),
+            "gf_select_selftest_bytes": (C.c_size_t, []),
+            "gf_select_selftest_timeout": (C.c_int32, [P, C.c_int64, P, C.c_size_t, P, P]),
             "gf3_num_unknowns": (C.c_int64, [C.POINTER(gf_geom3d)]),
             "gf3_num_candidates": (C.c_int64, [C.POINTER(gf_geom3d)]),
             "gf3_workspace_size": (C.c_size_t, [C.POINTER(gf_geom3d), C.c_int32, C.POINTER(gf_cand_spec)]),
@@ -337,6 +339,13 @@ class Handle:
 
     def gf_selftest_timeout(self, timeout_ns: int, status, stream=None):
         self._check(self.lib.gf_selftest_timeout(self.h, int(timeout_ns), _ptr(status), _stream(stream)))
+
+    def gf_select_selftest_bytes(self) -> int:
+        return int(self.lib.gf_select_selftest_bytes())
+
+    def gf_select_selftest_timeout(self, timeout_ns: int, ws, ws_bytes: int, status, stream=None):
+        self._check(self.lib.gf_select_selftest_timeout(self.h, int(timeout_ns), _ptr(ws), int(ws_bytes), _ptr(status),
+                                                        _stream(stream)))
 
     # ---- 3-D form
     def gf3_num_unknowns(self, geom) -> int:

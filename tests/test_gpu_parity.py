@@ -329,3 +329,33 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     assert r[0].status == B.GF_OK and len(r[0].ids) == 1
     with pytest.raises(B.GfError):
         opt.h.gf_selftest_timeout(10, st)
+
+
+def test_topk_grid_barrier_timeout_reports_status_and_context_survives():
+    """The one-launch top-k's grid barrier waits for one CTA more than its grid holds: every
+    CTA's bounded wait gives up, the status word reports GF_ETIMEOUT (no fault), and a top-32
+    selection on the same context afterwards matches the oracle."""
+    import time
+    h = B.Handle(0)
+    nb = h.gf_select_selftest_bytes()
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    h.gf_select_selftest_timeout(50_000_000, ws, nb, st)    # 50 ms
+    torch.cuda.synchronize()
+    assert int(st.cpu()[0]) == B.GF_ETIMEOUT
+    assert time.perf_counter() - t0 >= 0.045
+    with pytest.raises(B.GfError):
+        h.gf_select_selftest_timeout(50_000_000, ws, nb - 8, st)
+    g = W.small(90, 70, kind=W.KIND_BRUSH2).geoms[0]
+    spec = W.CandidateSpec(W.KIND_BRUSH2, 3, k=32, excl_radius=3)
+    nc = h.gf_num_candidates(g, spec)
+    d = np.random.default_rng(5).normal(size=nc)
+    wsb = h.gf_workspace_size(g, 1, B.GF_C128, spec)
+    wsel = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    idx = torch.full((32,), -7, dtype=torch.int32, device="cuda")
+    val = torch.empty(32, dtype=torch.float64, device="cuda")
+    h.gf_select_topk(g, spec, torch.tensor(d, device="cuda"), nc, idx, val, st, wsel, wsb)
+    torch.cuda.synchronize()
+    assert [int(x) for x in idx.cpu().numpy() if x >= 0] == O.select_topk(g, spec, d)
+    assert int(st.cpu()[0]) == B.GF_OK
