@@ -106,47 +106,86 @@ C64Layout c64_layout(int64_t n, int pmax) {
   return o;
 }
 
-// ---- D A^{-1} (p x p, FP32) from the FP64 LU: one CTA per column --------------------------
-__global__ void k_c64_inverse(WsLayout L, char* ws, int lam, float2* __restrict__ Mout) {
+// ---- D A^{-1} (p x p, FP32) from the FP64 LU: one CTA per column, a thread per row ----------
+// The unit vector e_c under the row interchanges in order is e_pos (only the unit's position is
+// followed), so the unit-lower solve starts at column pos; the factor columns are staged 16 at a
+// time in shared memory (each step would otherwise wait on an L2 load), and the upper solve's
+// pivot reciprocals 1 / |u_qq|^2 are formed first, side by side (cdiv_r with them gives cdiv's
+// bits), so that a step is one barrier and one dependent complex update per row.
+constexpr int kInvCols = 16;
+__global__ void __launch_bounds__(128) k_c64_inverse(WsLayout L, char* ws, int lam, float2* __restrict__ Mout) {
   const UpdCtl* ctl = reinterpret_cast<const UpdCtl*>(ws + L.ctl);
   if (ctl->skip) return;
   const int p = ctl->nv;
   const int c = blockIdx.x;
-  if (c >= p) return;
+  if (c >= p || p > (int)blockDim.x) return;
   const cplx* A = reinterpret_cast<const cplx*>(ws + L.lu + lam * L.lu_s);
   const int32_t* piv = reinterpret_cast<const int32_t*>(ws + L.piv + lam * L.piv_s);
   const double* dchi = reinterpret_cast<const double*>(ws + L.dchi);
-  __shared__ cplx x[256];
+  __shared__ cplx x[kC64MaxP], xs[kC64MaxP];
+  __shared__ cplx blk[kInvCols][kC64MaxP];
+  __shared__ double dinv[kC64MaxP];
+  __shared__ int s_pos;
   const int t = threadIdx.x;
-  for (int r = t; r < p; r += blockDim.x) x[r] = mk(r == c ? 1.0 : 0.0, 0.0);
-  __syncthreads();
-  if (t == 0) {   // row interchanges in order
+  if (t < p) dinv[t] = 1.0 / abs2(A[t * p + t]);
+  if (t == 0) {
+    int pos = c;
     for (int q = 0; q < p; ++q) {
-      int r = piv[q];
-      if (r != q) { cplx tt = x[q]; x[q] = x[r]; x[r] = tt; }
+      const int r = piv[q];
+      if (pos == q) pos = r;
+      else if (pos == r) pos = q;
+    }
+    s_pos = pos;
+  }
+  __syncthreads();
+  const int pos = s_pos;
+  if (t < p) x[t] = mk(t == pos ? 1.0 : 0.0, 0.0);
+  // unit lower, columns pos .. p - 1
+  for (int q0 = pos - pos % kInvCols; q0 < p; q0 += kInvCols) {
+    __syncthreads();                                      // the previous block's readers are done
+    for (int e = t; e < kInvCols * p; e += blockDim.x) {
+      const int qq = e / p, r = e - qq * p;
+      if (q0 + qq < p) blk[qq][r] = A[r * p + q0 + qq];
+    }
+    __syncthreads();
+    for (int qq = 0; qq < kInvCols; ++qq) {
+      const int q = q0 + qq;
+      if (q >= p) break;
+      if (q < pos) continue;
+      const cplx xq = x[q];
+      if (t > q && t < p) x[t] = x[t] - blk[qq][t] * xq;
+      __syncthreads();
     }
   }
-  __syncthreads();
-  for (int q = 0; q < p; ++q) {            // unit lower
-    const cplx xq = x[q];
-    for (int r = q + 1 + t; r < p; r += blockDim.x) x[r] = x[r] - A[r * p + q] * xq;
+  // upper, from the bottom; the solved entries go to xs, so that no thread reads an entry that
+  // another is overwriting
+  for (int q0 = ((p - 1) / kInvCols) * kInvCols; q0 >= 0; q0 -= kInvCols) {
     __syncthreads();
-  }
-  for (int q = p - 1; q >= 0; --q) {       // upper
-    if (t == 0) x[q] = cdiv(x[q], A[q * p + q]);
+    for (int e = t; e < kInvCols * p; e += blockDim.x) {
+      const int qq = e / p, r = e - qq * p;
+      if (q0 + qq < p) blk[qq][r] = A[r * p + q0 + qq];
+    }
     __syncthreads();
-    const cplx xq = x[q];
-    for (int r = t; r < q; r += blockDim.x) x[r] = x[r] - A[r * p + q] * xq;
-    __syncthreads();
+    for (int qq = kInvCols - 1; qq >= 0; --qq) {
+      const int q = q0 + qq;
+      if (q >= p) continue;
+      const cplx xq = cdiv_r(x[q], blk[qq][q], dinv[q]);
+      if (t == q) xs[q] = xq;
+      if (t < q) x[t] = x[t] - blk[qq][t] * xq;
+      __syncthreads();
+    }
   }
   // column c of A^{-1}; row u scaled by d_chi[u]
-  for (int u = t; u < p; u += blockDim.x)
-    Mout[u * p + c] = make_float2((float)(dchi[u] * x[u].re), (float)(dchi[u] * x[u].im));
+  if (t < p) Mout[t * p + c] = make_float2((float)(dchi[t] * xs[t].re), (float)(dchi[t] * xs[t].im));
 }
 
 // ---- S = (D A^{-1}) G[V, :] in FP32, written as scaled split-FP16 B operand blocks ----------
 // One CTA per 64 complex columns (one 128-real-column tile, both tiles of the last pair are
-// written); thread (j, quarter of u range).
+// written); thread (u group ug, column group cg): u = 4 ug .. 4 ug + 3 and columns cg + 8 b
+// (b < 8), so that per v 12 shared-memory loads (4 of M, 8 of the rows) feed 32 complex FMAs,
+// the eight column groups of a warp reading 64 contiguous bytes and the M rows padded to 17
+// entries (no bank conflicts).  Each chunk of 16 v of M and of the rows is staged in shared
+// memory; the sum over v runs in the same order for every entry.
 // Row v of the update set is read at R + rowof(v) ldr: from G (rowof = V[v]) or from a panel of the
 // set's rows (V == nullptr, rowof = v).
 __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ R, int64_t ldr, int64_t n,
@@ -156,69 +195,81 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ R
   if (ctl->skip) return;
   const int p = ctl->nv;
   const int P = (int)c64_padP(p);            // this step's P: the blocks beyond K = 2P are not read
-  __shared__ float2 Ms[128 * 16];            // M[u][v0 .. v0+16)
-  __shared__ float smax[4][64];
+  __shared__ float2 Ms[128 * 17];            // M[u][v0 .. v0+16), rows padded to 17
+  __shared__ float2 Rs[16 * 64];             // rows v0 .. v0+16 of the tile's 64 columns
+  __shared__ float smax[32][65];
   const int t = threadIdx.x;
-  const int jl = t & 63, q = t >> 6;         // local complex column, u quarter
+  const int cg = t & 7, ug = t >> 3;         // columns cg + 8 b, u = 4 ug .. 4 ug + 3
   const int64_t ct = blockIdx.x;
-  const int64_t j = ct * 64 + jl;
-  const int uq = P / 4;                      // u values per thread (multiple of 4, <= 32)
-  float2 acc[32];
+  const int64_t j0 = ct * 64;
+  const bool act = 4 * ug < P;
+  float2 acc[4][8];
 #pragma unroll
-  for (int a = 0; a < 32; ++a) acc[a] = make_float2(0.f, 0.f);
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = make_float2(0.f, 0.f);
   for (int v0 = 0; v0 < p; v0 += 16) {
     __syncthreads();
     for (int e = t; e < 128 * 16; e += 256) {
-      int u = e >> 4, v = v0 + (e & 15);
-      Ms[e] = (u < p && v < p) ? Mdai[u * p + v] : make_float2(0.f, 0.f);
+      const int u = e >> 4, v = v0 + (e & 15);
+      Ms[u * 17 + (e & 15)] = (u < p && v < p) ? Mdai[u * p + v] : make_float2(0.f, 0.f);
+    }
+    for (int e = t; e < 16 * 64; e += 256) {
+      const int vv = e >> 6, jl = e & 63;
+      const int64_t j = j0 + jl;
+      Rs[e] = (j < n && v0 + vv < p) ? R[(int64_t)(V ? V[v0 + vv] : v0 + vv) * ldr + j] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    // the chunk's 16 entries of this column first (independent loads in flight), then the FMAs
-    float2 rv[16];
+    if (act) {
 #pragma unroll
-    for (int vv = 0; vv < 16; ++vv)
-      rv[vv] = (j < n && v0 + vv < p) ? R[(int64_t)(V ? V[v0 + vv] : v0 + vv) * ldr + j] : make_float2(0.f, 0.f);
+      for (int vv = 0; vv < 16; ++vv) {
+        float2 m[4], r[8];
 #pragma unroll
-    for (int vv = 0; vv < 16; ++vv) {
-      const float2 r = rv[vv];
+        for (int a = 0; a < 4; ++a) m[a] = Ms[(4 * ug + a) * 17 + vv];
 #pragma unroll
-      for (int a = 0; a < 32; ++a) {
-        if (a < uq) {
-          const float2 m = Ms[(q * uq + a) * 16 + vv];
-          acc[a].x = fmaf(m.x, r.x, fmaf(-m.y, r.y, acc[a].x));
-          acc[a].y = fmaf(m.x, r.y, fmaf(m.y, r.x, acc[a].y));
-        }
+        for (int b = 0; b < 8; ++b) r[b] = Rs[vv * 64 + cg + 8 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            acc[a][b].x = fmaf(m[a].x, r[b].x, fmaf(-m[a].y, r[b].y, acc[a][b].x));
+            acc[a][b].y = fmaf(m[a].x, r[b].y, fmaf(m[a].y, r[b].x, acc[a][b].y));
+          }
       }
     }
   }
-  // per-column scale 2^F_j over all u (the four quarters of column j)
-  float m = 0.f;
+  // per-column scale 2^F_j over all u: the largest magnitude of each column over the u groups
 #pragma unroll
-  for (int a = 0; a < 32; ++a)
-    if (a < uq) m = fmaxf(m, fmaxf(fabsf(acc[a].x), fabsf(acc[a].y)));
-  smax[q][jl] = m;
+  for (int b = 0; b < 8; ++b) {
+    float m = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) m = fmaxf(m, fmaxf(fabsf(acc[a][b].x), fabsf(acc[a][b].y)));
+    smax[ug][cg + 8 * b] = act ? m : 0.f;
+  }
   __syncthreads();
-  const float mm = fmaxf(fmaxf(smax[0][jl], smax[1][jl]), fmaxf(smax[2][jl], smax[3][jl]));
-  const int F = scale_exp(mm);
-  if (q == 0) Fcol[j] = F;
-  const float sc = ldexpf(1.0f, kC64Exp - F);
-  // columns 2j (re) and 2j+1 (im) of B':  k < P: (Re S, Im S);  k >= P: (-Im S, Re S)
+  if (!act) return;
   uint8_t* pair = Bops + (ct >> 1) * (int64_t)nkc * kC64PairBlock + (ct & 1) * kC64Half;
-  const int c_re = 2 * jl, c_im = 2 * jl + 1;
+  const int u0 = 4 * ug;
+  const int kA = u0, kB = P + u0;
+  uint8_t* blkA = pair + (kA / kC64KC) * kC64PairBlock;   // hi part; lo part at + kC64Block
+  uint8_t* blkB = pair + (kB / kC64KC) * kC64PairBlock;
 #pragma unroll
-  for (int a4 = 0; a4 < 32; a4 += 4) {
-    if (a4 >= uq) break;
-    const int u0 = q * uq + a4;               // 4 consecutive u in one 8-aligned half of a core row
+  for (int b = 0; b < 8; ++b) {
+    const int jl = cg + 8 * b;
+    float mm = 0.f;
+    for (int g = 0; g < 32; ++g) mm = fmaxf(mm, smax[g][jl]);
+    const int F = scale_exp(mm);
+    if (ug == 0) Fcol[j0 + jl] = F;
+    const float sc = ldexpf(1.0f, kC64Exp - F);
+    // columns 2j (re) and 2j+1 (im) of B':  k < P: (Re S, Im S);  k >= P: (-Im S, Re S)
+    const int c_re = 2 * jl, c_im = 2 * jl + 1;
     __half rh[4], rl[4], ih[4], il[4], nh[4], nl[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      f16_split(acc[a4 + e].x * sc, rh[e], rl[e]);
-      f16_split(acc[a4 + e].y * sc, ih[e], il[e]);
-      f16_split(-acc[a4 + e].y * sc, nh[e], nl[e]);
+      f16_split(acc[e][b].x * sc, rh[e], rl[e]);
+      f16_split(acc[e][b].y * sc, ih[e], il[e]);
+      f16_split(-acc[e][b].y * sc, nh[e], nl[e]);
     }
-    const int kA = u0, kB = P + u0;
-    uint8_t* blkA = pair + (kA / kC64KC) * kC64PairBlock;     // hi part; lo part at + kC64Block
-    uint8_t* blkB = pair + (kB / kC64KC) * kC64PairBlock;
     const int oRa = c64_off(c_re, kA % kC64KC), oIa = c64_off(c_im, kA % kC64KC);
     const int oRb = c64_off(c_re, kB % kC64KC), oIb = c64_off(c_im, kB % kC64KC);
     st4h(blkA + oRa, rh[0], rh[1], rh[2], rh[3]);
