@@ -60,8 +60,9 @@ __global__ void k_capacitance_lam(CapArgs a, WsLayout L, char* ws, const uint8_t
   }
 }
 
-// ---- one large system (a single wavelength with p_max > kCapSmemP), held in the shared memory of
-// one cluster of CTAs (distributed shared memory).  One CTA per solve is bound by that SM's FP64
+// ---- one large system per wavelength (one wavelength with p_max > kCapSmemP, or several with
+// p_max > kCapClusterMinP), held in the shared memory of one cluster of CTAs per wavelength
+// (distributed shared memory; cluster l of the grid solves wavelength l).  One CTA per solve is bound by that SM's FP64
 // pipe (p = 128: 1.9 ms).  A = I - G_VV D is built, factorised with partial pivoting and solved
 // without leaving the cluster: physical row r (with y as its last entry) lives in CTA r % CN and
 // is never moved; the logical order is recorded per row.
@@ -177,9 +178,10 @@ __global__ void __launch_bounds__(256)
   __shared__ int s_nv, s_bad, s_ph, s_cand, s_nbulk;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (int)(blockDim.x >> 5);
   const int rank = (int)cl.block_rank();
-  const UpdLam& U = a.u.lam[0];
+  const int lam = (int)(blockIdx.x / CN);                 // cluster l solves wavelength l
+  const UpdLam& U = a.u.lam[lam];
   UpdCtl* ctl = reinterpret_cast<UpdCtl*>(ws + L.ctl);
-  int32_t* piv_out = reinterpret_cast<int32_t*>(ws + L.piv);
+  int32_t* piv_out = reinterpret_cast<int32_t*>(ws + L.piv + lam * L.piv_s);
 
   // ---- the joint set V: the candidates in order up to the first empty slot, a lane per
   // candidate (pillars, whose pixel count has no small bound: one thread)
@@ -225,8 +227,10 @@ __global__ void __launch_bounds__(256)
     int32_t* V = reinterpret_cast<int32_t*>(ws + L.V);
     double* dchi = reinterpret_cast<double*>(ws + L.dchi);
     for (int t = tid; t < p; t += blockDim.x) {
-      V[t] = sV[t];
-      dchi[t] = sD[t];
+      if (lam == 0) {                                     // the set, shared by the wavelengths
+        V[t] = sV[t];
+        dchi[t] = sD[t];
+      }
       phys[t] = t;
       pos[t] = t;
     }
@@ -519,7 +523,7 @@ __global__ void __launch_bounds__(256)
   }
   // ---- outputs: the factors in logical row order; CTA 0: dFOM (Eq. 4 at the monitor) and D y
   if (!bad) {
-    cplx* A = reinterpret_cast<cplx*>(ws + L.lu);
+    cplx* A = reinterpret_cast<cplx*>(ws + L.lu + lam * L.lu_s);
     for (int t = tid; t < R * p; t += blockDim.x) {
       const int lr = t / p, c = t - lr * p;
       A[(size_t)posof[lr] * p + c] = rows[(size_t)lr * W + c];
@@ -552,12 +556,12 @@ __global__ void __launch_bounds__(256)
         }
         __syncthreads();
       }
-      cplx* yd = reinterpret_cast<cplx*>(ws + L.yd);
+      cplx* yd = reinterpret_cast<cplx*>(ws + L.yd + lam * L.yd_s);
       for (int u = tid; u < p; u += blockDim.x) yd[u] = sD[u] * xfin[u];
     }
     if (tid == 0) {
-      ctl->lam_df[0] = df;
-      ctl->lam_bad[0] = bad ? 1 : 0;
+      ctl->lam_df[lam] = df;
+      ctl->lam_bad[lam] = bad ? 1 : 0;
     }
   }
   cl.sync();                                              // no CTA leaves while others read its memory
@@ -607,7 +611,7 @@ static void launch_cap_cluster(const CapArgs& ca, const WsLayout& L, char* ws, c
   at[0].val.clusterDim.x = (unsigned)cn;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3((unsigned)cn);
+  cfg.gridDim = dim3((unsigned)(cn * ca.u.nlam));            // one cluster per wavelength
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = cap_cluster_smem(L.pmax, cn);
   cfg.stream = st;
@@ -878,9 +882,11 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
-  // several wavelengths: their joint solves run side by side, one CTA each; one wavelength with
-  // a large set: the first attempt's solve factorised by many CTAs
-  const bool multi = a.nlam == 1 && L.pmax > kCapSmemP && L.pmax <= kLuMaxBlocked;
+  // the first attempt's solves: one cluster of CTAs per wavelength for a large set (one
+  // wavelength above kCapSmemP pixels, several above kCapClusterMinP), else one CTA per
+  // wavelength side by side (several wavelengths); k_capacitance decides and runs any fallback
+  const bool multi = L.pmax <= kLuMaxBlocked &&
+                     ((a.nlam == 1 && L.pmax > kCapSmemP) || (a.nlam > 1 && L.pmax > kCapClusterMinP));
   const int pre = (a.nlam > 1 && L.pmax <= kCapSmemP) || multi ? 1 : 0;
   if (multi) {
     launch_cap_cluster(ca, L, ws, state, idx, status, st);

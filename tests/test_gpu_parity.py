@@ -128,6 +128,16 @@ def test_multi_wavelength_trajectory():
     assert done >= 2
 
 
+def test_multi_wavelength_topk_cluster_trajectory():
+    """Three wavelengths, top-12 brushes (joint sets up to 48 pixels per wavelength): each
+    wavelength's system is factorised and solved in its own cluster of CTAs, whose factors then
+    give that wavelength's FP64 panels; lock-step with the oracle."""
+    wl = W.small(20, 16, kind=W.KIND_BRUSH2, dir_mask=3, k=12, excl_radius=2, wavelengths=(0.9, 1.0, 1.1), steps=3)
+    state = W.random_state(20 * 16, seed=28, fill=0.3)
+    done, _ = run_parity(wl, 3, state=state)
+    assert done >= 2
+
+
 def test_no_improving_candidate_sets_status_and_changes_nothing():
     # From vacuum, no 2x2 brush of eps = 12.25 helps this small lens: the oracle stops at once.
     wl = W.small(12, 10, kind=W.KIND_BRUSH2, dir_mask=3)
