@@ -622,7 +622,7 @@ struct CapArgs {
 constexpr int kLuNB = 8;
 constexpr int kLuMaxBlocked = 256;
 constexpr int kCapSmemP = 64;          // capacitance systems up to this size in shared memory (64 KB)
-constexpr int kCapClusterMinP = 32;    // several wavelengths: a cluster per wavelength above this size
+constexpr int kCapClusterMinP = 32;    // joint sets above this size: a cluster of CTAs per wavelength
 
 // sP: shared memory for kLuMaxBlocked x kLuNB entries (the panel, row-major [row][j])
 inline __device__ bool lu_blocked(cplx* __restrict__ A, int p, int32_t* __restrict__ piv, double thresh, cplx* sP) {

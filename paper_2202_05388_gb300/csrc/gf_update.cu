@@ -60,9 +60,9 @@ __global__ void k_capacitance_lam(CapArgs a, WsLayout L, char* ws, const uint8_t
   }
 }
 
-// ---- one large system per wavelength (one wavelength with p_max > kCapSmemP, or several with
-// p_max > kCapClusterMinP), held in the shared memory of one cluster of CTAs per wavelength
-// (distributed shared memory; cluster l of the grid solves wavelength l).  One CTA per solve is bound by that SM's FP64
+// ---- one large system per wavelength (p_max > kCapClusterMinP), held in the shared memory of one
+// cluster of CTAs per wavelength (distributed shared memory; cluster l of the grid solves
+// wavelength l).  One CTA per solve is bound by that SM's FP64
 // pipe (p = 128: 1.9 ms).  A = I - G_VV D is built, factorised with partial pivoting and solved
 // without leaving the cluster: physical row r (with y as its last entry) lives in CTA r % CN and
 // is never moved; the logical order is recorded per row.
@@ -882,11 +882,10 @@ void launch_update(const UpdArgs& a, const WsLayout& L, char* ws, uint8_t* state
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
   }
-  // the first attempt's solves: one cluster of CTAs per wavelength for a large set (one
-  // wavelength above kCapSmemP pixels, several above kCapClusterMinP), else one CTA per
-  // wavelength side by side (several wavelengths); k_capacitance decides and runs any fallback
-  const bool multi = L.pmax <= kLuMaxBlocked &&
-                     ((a.nlam == 1 && L.pmax > kCapSmemP) || (a.nlam > 1 && L.pmax > kCapClusterMinP));
+  // the first attempt's solves: one cluster of CTAs per wavelength for a set above
+  // kCapClusterMinP pixels (a 64-pixel system: 0.18 ms against 0.47 ms on one CTA), else one CTA
+  // per wavelength side by side (several wavelengths); k_capacitance decides and runs any fallback
+  const bool multi = L.pmax > kCapClusterMinP && L.pmax <= kLuMaxBlocked;
   const int pre = (a.nlam > 1 && L.pmax <= kCapSmemP) || multi ? 1 : 0;
   if (multi) {
     launch_cap_cluster(ca, L, ws, state, idx, status, st);
