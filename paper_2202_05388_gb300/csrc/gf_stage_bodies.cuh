@@ -1199,8 +1199,8 @@ __device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L,
     cplx* C0 = reinterpret_cast<cplx*>(ws + L.C0 + l * L.panel_s);
     cplx* S = reinterpret_cast<cplx*>(ws + L.S + l * L.panel_s);
     const int64_t jend = U.rows > n ? U.rows : n;
-    // the reciprocals 1 / |u_cc|^2 of the upper solve, once per CTA (cdiv_r with them gives
-    // cdiv's bits); the first barrier keeps the previous wavelength's or work item's readers
+    // the reciprocals 1 / |u_cc|^2 of the upper solve, once per CTA instead of a division per
+    // column; the first barrier keeps the previous wavelength's or work item's readers
     __shared__ double s_dinv[kMaxPixelsPerCand];
     if (want_S && p <= kMaxPixelsPerCand) {
       __syncthreads();
@@ -1218,7 +1218,8 @@ __device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L,
         for (int u = 0; u < kMaxPixelsPerCand; ++u)
           if (u < p) x[u] = U.vrows ? ldG(U.vrows, a.dtype, U.ldv, u, j) : ldG(U.G, a.dtype, U.ldg, V[u], j);
         // P A = L U with full-row interchanges: apply all interchanges in order first,
-        // then the unit-lower solve, then the upper solve
+        // then the unit-lower solve, then the upper solve (fused multiply-adds: the panels of
+        // a step run this for every column of G, on the narrow FP64 pipe)
 #pragma unroll
         for (int c = 0; c < kMaxPixelsPerCand; ++c) {
           if (c < p) {
@@ -1233,7 +1234,7 @@ __device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L,
           if (c < p) {
 #pragma unroll
             for (int rr = c + 1; rr < kMaxPixelsPerCand; ++rr)
-              if (rr < p) x[rr] = x[rr] - A[rr * p + c] * x[c];
+              if (rr < p) x[rr] = cfms(A[rr * p + c], x[c], x[rr]);
           }
         }
 #pragma unroll
@@ -1242,8 +1243,9 @@ __device__ __forceinline__ void panels_body(const UpdArgs& a, const WsLayout& L,
             cplx acc = x[c];
 #pragma unroll
             for (int v = c + 1; v < kMaxPixelsPerCand; ++v)
-              if (v < p) acc = acc - A[c * p + v] * x[v];
-            x[c] = cdiv_r(acc, A[c * p + c], s_dinv[c]);
+              if (v < p) acc = cfms(A[c * p + v], x[v], acc);
+            const cplx u = A[c * p + c];
+            x[c] = mk(fma(acc.re, u.re, acc.im * u.im) * s_dinv[c], fma(acc.im, u.re, -(acc.re * u.im)) * s_dinv[c]);
           }
         }
 #pragma unroll
