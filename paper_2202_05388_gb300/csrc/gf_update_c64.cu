@@ -184,10 +184,18 @@ __global__ void __launch_bounds__(128) k_c64_inverse(WsLayout L, char* ws, int l
 // written); thread (u group ug, column group cg): u = 4 ug .. 4 ug + 3 and columns cg + 8 b
 // (b < 8), so that per v 12 shared-memory loads (4 of M, 8 of the rows) feed 32 complex FMAs,
 // the eight column groups of a warp reading 64 contiguous bytes and the M rows padded to 17
-// entries (no bank conflicts).  Each chunk of 16 v of M and of the rows is staged in shared
-// memory; the sum over v runs in the same order for every entry.
+// entries (no bank conflicts).  Chunks of 16 v of M and of the rows are double-buffered in
+// shared memory by asynchronous copies (chunk i + 1 arrives while chunk i is summed); the sum
+// over v runs in the same order for every entry.
 // Row v of the update set is read at R + rowof(v) ldr: from G (rowof = V[v]) or from a panel of the
 // set's rows (V == nullptr, rowof = v).
+constexpr int kSgMs = 128 * 17, kSgRs = 16 * 64;           // float2 entries per buffer
+constexpr size_t kSgSmem = 2 * (kSgMs + kSgRs) * sizeof(float2);
+__device__ __forceinline__ void sg_copy8(void* dst, const void* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const int n = valid ? 8 : 0;                              // 0: zero-fill, nothing is read
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
 __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ R, int64_t ldr, int64_t n,
                                                     const float2* __restrict__ Mdai, const int32_t* __restrict__ V,
                                                     const UpdCtl* __restrict__ ctl, int nkc,
@@ -195,31 +203,50 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ R
   if (ctl->skip) return;
   const int p = ctl->nv;
   const int P = (int)c64_padP(p);            // this step's P: the blocks beyond K = 2P are not read
-  __shared__ float2 Ms[128 * 17];            // M[u][v0 .. v0+16), rows padded to 17
-  __shared__ float2 Rs[16 * 64];             // rows v0 .. v0+16 of the tile's 64 columns
+  extern __shared__ __align__(16) float2 sg_smem[];
   __shared__ float smax[32][65];
+  __shared__ int64_t rowof[kC64MaxP];
   const int t = threadIdx.x;
   const int cg = t & 7, ug = t >> 3;         // columns cg + 8 b, u = 4 ug .. 4 ug + 3
   const int64_t ct = blockIdx.x;
   const int64_t j0 = ct * 64;
   const bool act = 4 * ug < P;
+  for (int v = t; v < p; v += blockDim.x) rowof[v] = (int64_t)(V ? V[v] : v) * ldr;
+  __syncthreads();
+  // the copies of chunk v0 into buffer bf: M[u][v0 .. v0+16) (rows padded to 17), the rows' 64 columns
+  auto stage = [&](int v0, int bf) {
+    float2* Ms = sg_smem + bf * (kSgMs + kSgRs);
+    float2* Rs = Ms + kSgMs;
+    for (int e = t; e < 128 * 16; e += 256) {
+      const int u = e >> 4, v = v0 + (e & 15);
+      const bool ok = u < p && v < p;
+      sg_copy8(Ms + u * 17 + (e & 15), ok ? (const void*)(Mdai + u * p + v) : (const void*)Mdai, ok);
+    }
+    for (int e = t; e < 16 * 64; e += 256) {
+      const int vv = e >> 6, jl = e & 63;
+      const int64_t j = j0 + jl;
+      const bool ok = j < n && v0 + vv < p;
+      sg_copy8(Rs + e, ok ? (const void*)(R + rowof[v0 + vv] + j) : (const void*)R, ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
   float2 acc[4][8];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[a][b] = make_float2(0.f, 0.f);
-  for (int v0 = 0; v0 < p; v0 += 16) {
-    __syncthreads();
-    for (int e = t; e < 128 * 16; e += 256) {
-      const int u = e >> 4, v = v0 + (e & 15);
-      Ms[u * 17 + (e & 15)] = (u < p && v < p) ? Mdai[u * p + v] : make_float2(0.f, 0.f);
-    }
-    for (int e = t; e < 16 * 64; e += 256) {
-      const int vv = e >> 6, jl = e & 63;
-      const int64_t j = j0 + jl;
-      Rs[e] = (j < n && v0 + vv < p) ? R[(int64_t)(V ? V[v0 + vv] : v0 + vv) * ldr + j] : make_float2(0.f, 0.f);
+  const int nch = (p + 15) / 16;
+  if (nch > 0) stage(0, 0);
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) {
+      stage(16 * (ch + 1), (ch + 1) & 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // chunk ch has landed
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     }
     __syncthreads();
+    const float2* Ms = sg_smem + (ch & 1) * (kSgMs + kSgRs);
+    const float2* Rs = Ms + kSgMs;
     if (act) {
 #pragma unroll
       for (int vv = 0; vv < 16; ++vv) {
@@ -237,6 +264,7 @@ __global__ void __launch_bounds__(256) k_c64_s_gemm(const float2* __restrict__ R
           }
       }
     }
+    __syncthreads();                         // buffer ch & 1 is free for chunk ch + 2
   }
   // per-column scale 2^F_j over all u: the largest magnitude of each column over the u groups
 #pragma unroll
@@ -901,23 +929,7 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
   uint8_t* Aops = reinterpret_cast<uint8_t*>(ws + L.c64A);
   uint8_t* Bops = reinterpret_cast<uint8_t*>(ws + L.c64B);
   const cplx* C0 = reinterpret_cast<const cplx*>(ws + L.C0 + lam * L.panel_s);
-  k_c64_inverse<<<L.pmax, 128, 0, st>>>(L, ws, lam, Mdai);
-  int32_t* Erow = reinterpret_cast<int32_t*>(ws + L.c64E);
-  int32_t* Fcol = reinterpret_cast<int32_t*>(ws + L.c64F);
-  if (vrows)      // the rows G[V, :] from the caller's panel (a shard of G does not hold them)
-    k_c64_s_gemm<<<(unsigned)(2 * o.ncp), 256, 0, st>>>(reinterpret_cast<const float2*>(vrows), ldv, n, Mdai, nullptr,
-                                                         ctl, (int)o.nkc, Bops, Fcol);
-  else
-    k_c64_s_gemm<<<(unsigned)(2 * o.ncp), 256, 0, st>>>(G, ldg, n, Mdai, reinterpret_cast<const int32_t*>(ws + L.V),
-                                                         ctl, (int)o.nkc, Bops, Fcol);
-  {
-    const int64_t rows = o.nrt * kC64M;
-    const int64_t b = (rows + 7) / 8;                       // eight rows (warps) per CTA
-    k_c64_gather_rows<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(G, ldg, reinterpret_cast<const int32_t*>(ws + L.V),
-                                                                   L.pmax, grows, rows, ctl, (int)o.nkc,
-                                                                   const_cast<cplx*>(C0), Aops, Erow);
-  }
-  // once per device: shared-memory opt-in of both forms
+  // once per device: shared-memory opt-in of both update forms and of the S GEMM's buffers
   static std::mutex mu;
   static bool done[64] = {};
   int dev = 0;
@@ -927,8 +939,26 @@ void launch_rank_update_c64_tc(const void* map128, float2* G, int64_t ldg, int64
     if (dev < 0 || dev >= 64 || !done[dev]) {
       cudaFuncSetAttribute(k_rank_update_c64_ra, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
       cudaFuncSetAttribute(k_rank_update_c64_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, kC64Smem);
+      cudaFuncSetAttribute(k_c64_s_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSgSmem);
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
+  }
+  k_c64_inverse<<<L.pmax, 128, 0, st>>>(L, ws, lam, Mdai);
+  int32_t* Erow = reinterpret_cast<int32_t*>(ws + L.c64E);
+  int32_t* Fcol = reinterpret_cast<int32_t*>(ws + L.c64F);
+  if (vrows)      // the rows G[V, :] from the caller's panel (a shard of G does not hold them)
+    k_c64_s_gemm<<<(unsigned)(2 * o.ncp), 256, kSgSmem, st>>>(reinterpret_cast<const float2*>(vrows), ldv, n, Mdai,
+                                                               nullptr, ctl, (int)o.nkc, Bops, Fcol);
+  else
+    k_c64_s_gemm<<<(unsigned)(2 * o.ncp), 256, kSgSmem, st>>>(G, ldg, n, Mdai,
+                                                               reinterpret_cast<const int32_t*>(ws + L.V), ctl,
+                                                               (int)o.nkc, Bops, Fcol);
+  {
+    const int64_t rows = o.nrt * kC64M;
+    const int64_t b = (rows + 7) / 8;                       // eight rows (warps) per CTA
+    k_c64_gather_rows<<<(int)(b < 4864 ? b : 4864), 256, 0, st>>>(G, ldg, reinterpret_cast<const int32_t*>(ws + L.V),
+                                                                   L.pmax, grows, rows, ctl, (int)o.nkc,
+                                                                   const_cast<cplx*>(C0), Aops, Erow);
   }
   // joint rank p <= 48 (decided on the device): the resident-A form; larger p: the streaming
   // form, launched only where the workspace allows p > 48 (each returns at once when the other
