@@ -36,7 +36,8 @@ def combine(level_bits):
 
 
 def to_double(D: int, u: int) -> float:
-    """oz_to_double: two's-complement 64-bit steps of the kernel."""
+    """oz_to_double: two's-complement 64-bit steps of the kernel (its D == 0 test is the case
+    lz == 64 here)."""
     sg = -1 if D < 0 else 0
     M = ((D ^ sg) - sg) & MASK64
     lz = 64 - M.bit_length()
