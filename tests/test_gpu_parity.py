@@ -177,6 +177,54 @@ def test_singular_capacitance_is_reported_not_applied():
     assert opt.state.cpu().numpy()[j] == 0
 
 
+@pytest.mark.parametrize("k,dtype", [(8, "c128"), (12, "c128"), (32, "c128"), (12, "c64"), (32, "c64")])
+def test_singular_joint_system_is_reported_not_applied(k, dtype):
+    """Host-side fault injection into a joint set of k 2x2 brushes (p = 4k pixels): row j of
+    A = I - G_VV D is made exactly zero (G[V_j, V_c] = 0 for c != j, G[V_j, V_j] = 1/d_chi with
+    d_chi = 8), so A is singular whatever the pivot order.  p = 32 takes the one-CTA blocked
+    solve, p = 48 and 128 the cluster solve (complex64: the resident-A update at 48, the
+    streaming update at 128).  Every CTA must see the same failed pivot, the status must read
+    GF_ESINGULAR and G, E and the design must be unchanged."""
+    import dataclasses
+    nx = ny = 24
+    wl0 = W.small(nx, ny, kind=W.KIND_BRUSH2, dir_mask=W.DIR_FILL, k=k, excl_radius=0)
+    g = dataclasses.replace(wl0.geoms[0], eps_mat=9.0)
+    wl = dataclasses.replace(wl0, geoms=(g,))
+    opt = GreedyOptimizer(wl.geoms, wl.spec, dtype=dtype)
+    opt.fill()
+    torch.cuda.synchronize()
+    # k disjoint brushes on even anchors, in a seeded order; V in the kernels' order
+    rng = np.random.default_rng(40 + k)
+    anchors = [(2 * a, 2 * b) for b in range((ny - 1) // 2) for a in range((nx - 1) // 2)]
+    pick = rng.permutation(len(anchors))[:k]
+    ids = [anchors[i][1] * (nx - 1) + anchors[i][0] for i in pick]
+    state0 = np.zeros(g.N, dtype=np.uint8)
+    V = np.concatenate([O.candidate(g, wl.spec, state0, cid)[0] for cid in ids])
+    assert V.size == 4 * k and np.unique(V).size == V.size
+    jv = int(V[V.size // 2 + 1])
+    chi = g.eps_mat - g.eps_bg
+    assert chi == 8.0
+    Vt = torch.as_tensor(V, device=opt.G[0].device)
+    opt.G[0][jv, Vt] = 0
+    opt.G[0][jv, jv] = complex(1.0 / chi, 0.0)
+    torch.cuda.synchronize()
+    G_before = opt.G[0].clone()
+    E_before = opt.E[0].clone()
+    opt.force(ids)
+    torch.cuda.synchronize()
+    assert int(opt.status.cpu()[0]) == B.GF_ESINGULAR
+    assert torch.equal(opt.G[0], G_before)
+    assert torch.equal(opt.E[0], E_before)
+    assert not opt.state.cpu().numpy().any()
+    # the library stays usable: the first brush alone (its 4 x 4 system does not hold row j)
+    # is applied by the next call
+    assert jv not in set(V[:4].tolist())
+    opt.force([ids[0]])
+    torch.cuda.synchronize()
+    assert int(opt.status.cpu()[0]) == B.GF_OK
+    assert int(opt.state.cpu().numpy().sum()) == 4
+
+
 def test_host_validation_rejects_bad_arguments():
     wl = W.plain_32()
     opt = GreedyOptimizer(wl.geoms, wl.spec)
