@@ -177,19 +177,24 @@ def test_singular_capacitance_is_reported_not_applied():
     assert opt.state.cpu().numpy()[j] == 0
 
 
-@pytest.mark.parametrize("k,dtype", [(8, "c128"), (12, "c128"), (32, "c128"), (12, "c64"), (32, "c64")])
-def test_singular_joint_system_is_reported_not_applied(k, dtype):
+@pytest.mark.parametrize("k,dtype,nlam", [(8, "c128", 1), (12, "c128", 1), (32, "c128", 1), (12, "c64", 1),
+                                          (32, "c64", 1), (12, "c128", 3), (16, "c64", 3)])
+def test_singular_joint_system_is_reported_not_applied(k, dtype, nlam):
     """Host-side fault injection into a joint set of k 2x2 brushes (p = 4k pixels): row j of
     A = I - G_VV D is made exactly zero (G[V_j, V_c] = 0 for c != j, G[V_j, V_j] = 1/d_chi with
     d_chi = 8), so A is singular whatever the pivot order.  p = 32 takes the one-CTA blocked
     solve, p = 48 and 128 the cluster solve (complex64: the resident-A update at 48, the
-    streaming update at 128).  Every CTA must see the same failed pivot, the status must read
-    GF_ESINGULAR and G, E and the design must be unchanged."""
+    streaming update at 128).  With several wavelengths only the middle one's system is made
+    singular (each wavelength's system has its own cluster and flag).  Every CTA must see the
+    same failed pivot, the status must read GF_ESINGULAR and every wavelength's G and E and the
+    design must be unchanged."""
     import dataclasses
     nx = ny = 24
-    wl0 = W.small(nx, ny, kind=W.KIND_BRUSH2, dir_mask=W.DIR_FILL, k=k, excl_radius=0)
-    g = dataclasses.replace(wl0.geoms[0], eps_mat=9.0)
-    wl = dataclasses.replace(wl0, geoms=(g,))
+    wl0 = W.small(nx, ny, kind=W.KIND_BRUSH2, dir_mask=W.DIR_FILL, k=k, excl_radius=0,
+                  wavelengths=(0.9, 1.0, 1.1)[:nlam] if nlam > 1 else (1.0,))
+    wl = dataclasses.replace(wl0, geoms=tuple(dataclasses.replace(gg, eps_mat=9.0) for gg in wl0.geoms))
+    g = wl.geoms[0]
+    lb = nlam // 2                                          # the wavelength made singular
     opt = GreedyOptimizer(wl.geoms, wl.spec, dtype=dtype)
     opt.fill()
     torch.cuda.synchronize()
@@ -204,17 +209,18 @@ def test_singular_joint_system_is_reported_not_applied(k, dtype):
     jv = int(V[V.size // 2 + 1])
     chi = g.eps_mat - g.eps_bg
     assert chi == 8.0
-    Vt = torch.as_tensor(V, device=opt.G[0].device)
-    opt.G[0][jv, Vt] = 0
-    opt.G[0][jv, jv] = complex(1.0 / chi, 0.0)
+    Vt = torch.as_tensor(V, device=opt.G[lb].device)
+    opt.G[lb][jv, Vt] = 0
+    opt.G[lb][jv, jv] = complex(1.0 / chi, 0.0)
     torch.cuda.synchronize()
-    G_before = opt.G[0].clone()
-    E_before = opt.E[0].clone()
+    G_before = [G.clone() for G in opt.G]
+    E_before = [E.clone() for E in opt.E]
     opt.force(ids)
     torch.cuda.synchronize()
     assert int(opt.status.cpu()[0]) == B.GF_ESINGULAR
-    assert torch.equal(opt.G[0], G_before)
-    assert torch.equal(opt.E[0], E_before)
+    for lam in range(nlam):
+        assert torch.equal(opt.G[lam], G_before[lam])
+        assert torch.equal(opt.E[lam], E_before[lam])
     assert not opt.state.cpu().numpy().any()
     # the library stays usable: the first brush alone (its 4 x 4 system does not hold row j)
     # is applied by the next call
