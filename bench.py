@@ -309,7 +309,7 @@ def run_reference(args):
     g = wl.geoms[0]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": wl.name, "nx": g.nx, "ny": g.ny, "n": g.N + 1,
                        "candidates": W.CandidateSpec(wl.spec.kind, wl.spec.dir_mask).ncand(g)},
@@ -917,7 +917,9 @@ def run_native(args):
     per_step_launches = 2 + sel + cap + panels + nlam * (upd + 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.dtype == "c128" else "f32",
+            # one GPU: the same problem the row-sharded runs split (strong scaling); replicas: weak
+            "scaling": "weak" if world > 1 else "strong", "vs_baseline": None,
+            "dtype": "f64" if wl.dtype == "c128" else "f32",
             "data": "synthetic",
             "config": {"workload": wl.name, "nx": g.nx, "ny": g.ny, "n": g.N + 1,
                        "candidates": ncand_main, "G_GB": G_GB_main,
