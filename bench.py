@@ -128,8 +128,8 @@ class ClockSampler:
 # only for the kernel source it was taken on (SHA-256 over the files below), otherwise null.
 TRAFFIC_SOURCES = ("paper_2202_05388_gb300/csrc/gf_update_tc.cu", "paper_2202_05388_gb300/csrc/gf_tc.cuh")
 TRAFFIC = {
-    "brush_192x192_p4_c128": {"sha256": "6c1886356d87ea31483e27df8969e62f0a796bacaa4abd80518d8267bed4315a",
-                              "capture_n": 16385, "capture_bytes": 4.3147e9 + 4.2401e9, "n": 36865,
+    "brush_192x192_p4_c128": {"sha256": "fbd391f1ecb93c65d7da81de0c34bb3324ec1789146d47ad4e298ba945b261e3",
+                              "capture_n": 16385, "capture_bytes": 4.3094e9 + 4.2393e9, "n": 36865,
                               "profile": "profiles/rank_update_tc_brush128_traffic.md"},
 }
 
