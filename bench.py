@@ -609,7 +609,7 @@ def run_sharded(args):
         tt = tt.cpu()
     dist.all_reduce(tt, op=dist.ReduceOp.MAX)
     t_max = float(tt.item())
-    # end to end through the driver: H2D of the design state, K steps each with a D2H of the step record
+    # end to end through the sharded optimizer: H2D of the design state, K steps each with a D2H of the step record
     host_state = torch.zeros(g.N, dtype=torch.uint8).pin_memory()
     rec = sh.step_record()
     host_rec = torch.empty(rec.numel(), dtype=torch.float64).pin_memory()
